@@ -1,0 +1,190 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module holds only *inputs*: macro meshes (vertex coordinates and
+tetrahedra with their vertex order), coefficient fields, right-hand sides and
+Dirichlet data.  It contains none of the discretisation arithmetic of the
+method (no stiffness, no stencils, no refinement); both the CPU oracle and the
+CUDA path receive the arrays produced here.
+
+Random nodal fields are defined on a regular (N+1)^3 grid over the bounding
+box of the mesh and sampled at node coordinates, so a value depends only on
+where a node is, never on how an implementation numbers its nodes.
+"""
+
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# macro meshes
+# --------------------------------------------------------------------------
+
+KUHN_PERMS = tuple(itertools.permutations(range(3)))
+
+
+def unit_tet():
+    """One macro tetrahedron (0, e1, e2, e3) in this vertex order."""
+    xyz = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    tets = np.array([[0, 1, 2, 3]], dtype=np.int64)
+    return xyz, tets
+
+
+def kuhn_cube(m: int = 1):
+    """Unit cube cut into m^3 sub-cubes, each split into 6 Kuhn tetrahedra.
+
+    Every tetrahedron is (c, c+e_a, c+e_a+e_b, c+(1,1,1)) (scaled by 1/m) for a
+    permutation (a, b, c) of the axes, listed in that vertex order, so all of
+    them share the main diagonal of their sub-cube.  m = 1 gives the 6-macro
+    cube; m = 4 gives the 384-macro cube of the elastostatics benchmark
+    (Sec. 5.1.2).
+    """
+    grid = {}
+    xyz = []
+
+    def vid(p):
+        if p not in grid:
+            grid[p] = len(xyz)
+            xyz.append([p[0] / m, p[1] / m, p[2] / m])
+        return grid[p]
+
+    tets = []
+    for cz in range(m):
+        for cy in range(m):
+            for cx in range(m):
+                c = (cx, cy, cz)
+                for perm in KUHN_PERMS:
+                    p0 = c
+                    p1 = list(p0)
+                    p1[perm[0]] += 1
+                    p2 = list(p1)
+                    p2[perm[1]] += 1
+                    p3 = (cx + 1, cy + 1, cz + 1)
+                    tets.append([vid(tuple(p0)), vid(tuple(p1)), vid(tuple(p2)), vid(p3)])
+    return np.array(xyz, dtype=np.float64), np.array(tets, dtype=np.int64)
+
+
+def skewed_pair():
+    """Two non-degenerate, non-axis-aligned macro tetrahedra sharing one face.
+
+    Used to exercise general affine macro maps and a macro interface whose
+    refinement lattices meet at an arbitrary orientation.
+    """
+    xyz = np.array(
+        [
+            [0.0, 0.0, 0.0],
+            [1.1, 0.1, -0.05],
+            [0.2, 0.9, 0.1],
+            [0.15, 0.2, 1.05],
+            [1.0, 1.0, 0.9],
+        ]
+    )
+    tets = np.array([[0, 1, 2, 3], [4, 3, 2, 1]], dtype=np.int64)
+    return xyz, tets
+
+
+# --------------------------------------------------------------------------
+# coefficient fields (functions of coordinates)
+# --------------------------------------------------------------------------
+
+
+def young_sine(x):
+    """E(x) = 1 + 0.5 sin(2 pi x) sin(2 pi y) sin(2 pi z)."""
+    x = np.asarray(x)
+    return 1.0 + 0.5 * np.sin(2 * np.pi * x[..., 0]) * np.sin(2 * np.pi * x[..., 1]) * np.sin(
+        2 * np.pi * x[..., 2]
+    )
+
+
+def young_cos(x, m: int):
+    """E(x) = cos(m pi x y z) + 2, the elastostatics benchmark (Sec. 5.1.2)."""
+    x = np.asarray(x)
+    return np.cos(m * np.pi * x[..., 0] * x[..., 1] * x[..., 2]) + 2.0
+
+
+def viscosity_sphere(x, mu_in=1.0, mu_out=1.0e3, radius=0.25, width=0.02):
+    """mu = mu_in inside a sphere of the given radius around (1/2,1/2,1/2), mu_out outside,
+    blended by a tanh of the given width."""
+    x = np.asarray(x)
+    r = np.sqrt(((x - 0.5) ** 2).sum(axis=-1))
+    return mu_in + (mu_out - mu_in) * 0.5 * (1.0 + np.tanh((r - radius) / width))
+
+
+def affine_field(x, a0, a):
+    x = np.asarray(x)
+    return a0 + x @ np.asarray(a)
+
+
+# --------------------------------------------------------------------------
+# seeded grid fields sampled at node coordinates
+# --------------------------------------------------------------------------
+
+
+def grid_index(x, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    """Nearest (N+1)^3 grid point of each coordinate (the nodes of the meshes used here lie
+    exactly on such a grid)."""
+    x = np.asarray(x, dtype=np.float64)
+    lo = np.asarray(lo)
+    hi = np.asarray(hi)
+    t = (x - lo) / (hi - lo) * N
+    idx = np.rint(t).astype(np.int64)
+    if np.any(np.abs(t - idx) > 1e-6) or idx.min() < 0 or idx.max() > N:
+        raise ValueError("coordinates are not on the sampling grid")
+    return idx
+
+
+def uniform_grid(N, seed, comps=3, lo=-1.0, hi=1.0):
+    """i.i.d. uniform values on an (N+1)^3 grid, shape (N+1, N+1, N+1, comps), indexed [x,y,z]."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=(N + 1, N + 1, N + 1, comps))
+
+
+def sample_grid(grid, x):
+    N = grid.shape[0] - 1
+    idx = grid_index(x, N)
+    return grid[idx[..., 0], idx[..., 1], idx[..., 2]]
+
+
+def lognormal_grid(N, seed, corr=0.1, sigma=1.0):
+    """exp of a smoothed Gaussian random field on an (N+1)^3 grid over the unit cube.
+
+    i.i.d. N(0,1) values are convolved separably with a Gaussian kernel whose
+    standard deviation is ``corr`` (in domain units, i.e. corr*N grid cells),
+    rescaled to standard deviation ``sigma`` and exponentiated.
+    """
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((N + 1, N + 1, N + 1))
+    s = corr * N
+    half = int(math.ceil(4 * s))
+    t = np.arange(-half, half + 1, dtype=np.float64)
+    ker = np.exp(-0.5 * (t / s) ** 2)
+    ker /= ker.sum()
+    from scipy.ndimage import convolve1d
+
+    for ax in range(3):
+        g = convolve1d(g, ker, axis=ax, mode="reflect")
+    g = (g - g.mean()) / g.std() * sigma
+    return np.exp(g)
+
+
+# --------------------------------------------------------------------------
+# manufactured solution of the elastostatics benchmark (Sec. 5.1.2)
+# --------------------------------------------------------------------------
+
+
+def u_star(x):
+    """u*(x,y,z) = (x^3 y + z^2, x^4 y + 2 z, 3 x + y z^3) / (x y z + 1)."""
+    x = np.asarray(x)
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    d = X * Y * Z + 1.0
+    return np.stack([(X**3 * Y + Z**2) / d, (X**4 * Y + 2 * Z) / d, (3 * X + Y * Z**3) / d], axis=-1)
+
+
+def lid_velocity(x):
+    """Lid-driven cavity data: u = 16 x(1-x) y(1-y) (1,0,0) on z = 1, zero elsewhere."""
+    x = np.asarray(x)
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    s = np.where(np.abs(Z - 1.0) < 1e-12, 16.0 * X * (1 - X) * Y * (1 - Y), 0.0)
+    return np.stack([s, np.zeros_like(s), np.zeros_like(s)], axis=-1)
