@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark of the scaled-stencil vector operator apply (physical stencil scaling, Sec. 2 of
+arXiv 1908.08666) on one GB300, through the libhhgs C ABI.
+
+Workload: 3D linear elasticity (nu = 0.3) on the unit cube split into 6 Kuhn macro
+tetrahedra, refined to level 7 (129^3 = 2,146,689 nodes, 6.44 MDoF); Young's modulus a
+lognormal field (exp of a Gaussian random field smoothed with correlation length 0.1,
+sigma = 1, seed 2); input vector i.i.d. uniform[-1, 1] (seed 3).  One step = one full FP32
+operator application y = A x: the macro-interior scaled-stencil kernels plus the macro
+skeleton (interface) kernel.  The L2 cache is flushed (256 MB write, outside the timed
+events) before every timed step.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle instead (the
+reference arm of this build: the paper has no code; its FP64 definition-level oracle is
+the baseline).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+LEVEL = 7
+NU = 0.3
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+# algorithmic cost of one macro-interior node of the FP32 apply
+BYTES_PER_NODE_F32 = 28  # read x (12 B) and k (4 B), write y (12 B)
+FLOPS_PER_NODE = 723     # FMA = 2 flops, as the kernel evaluates the scaled stencil
+METRIC = "scaled-stencil vector matvec GDoF/s & % of HBM peak; time to 1e-8 residual"
+WORKLOAD = "elasticity, 6-macro Kuhn unit cube, level 7 (129^3 nodes), lognormal E, FP32 physical-scaling apply"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--level", type=int, default=LEVEL)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------- clocks
+
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- workload
+
+
+def workload_fields(coords, level):
+    import hhg_inputs as hi
+
+    N = 1 << level
+    kgrid = hi.lognormal_grid(N, seed=2)
+    xgrid = hi.uniform_grid(N, seed=3)
+    return hi.sample_grid(kgrid[..., None], coords)[:, 0], hi.sample_grid(xgrid, coords)
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("hhg_sweep.cu", "hhg_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1908_08666_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per interior-kernel launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "interior_apply_f32_cube6_l7.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+_GRIDS = {}
+
+
+def _grids(level):
+    import hhg_inputs as hi
+
+    if level not in _GRIDS:
+        N = 1 << level
+        _GRIDS[level] = (hi.lognormal_grid(N, seed=2), hi.uniform_grid(N, seed=3))
+    return _GRIDS[level]
+
+
+def cpu_baseline(level, budget_s=15.0, seed=0):
+    """The FP64 oracle (single-row definition by local refinement), timed on this host's
+    cores on a bounded random sample of rows of the same workload."""
+    import hhg_inputs as hi
+    from oracle import fem, mesh, rows
+
+    xyz, tets = hi.kuhn_cube(1)
+    mm = mesh.MacroMesh.build(xyz, tets)
+    N = 1 << level
+    kgrid, xgrid = _grids(level)
+    kf = lambda c: hi.sample_grid(kgrid[..., None], c)[:, 0]
+    xf = lambda c: hi.sample_grid(xgrid, c)
+    ce, cd = fem.elasticity_coefficients(NU)
+    rng = np.random.default_rng(seed)
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s or done < 8:
+        m = int(rng.integers(0, 6))
+        while True:
+            i, j, k = (int(v) for v in rng.integers(1, N, size=3))
+            if i + j + k <= N - 1:
+                break
+        rows.row(mm, level, m, (i, j, k), kf, xf, ce, cd)
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": 3.0 * done / dt / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+            "sample": "%d random macro-interior rows of the level-%d cube operator, FP64 single-row oracle "
+                      "(local Bey refinement + definition of the scaled blocks), %.1f s on 1 host core"
+                      % (done, level, dt)}
+
+
+# ---------------------------------------------------------------------------- our arm
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1908_08666_gb300 import binding as B
+    import hhg_inputs as hi
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    level = args.level
+    xyz, tets = hi.kuhn_cube(1)
+    h = B.hhg_create(dev, stream.cuda_stream)
+    B.hhg_set_macro_mesh(h, xyz, tets)
+    B.hhg_refine(h, level)
+    B.hhg_set_problem(h, nu=NU)
+    E, U, F = B.hhg_num_nodes(h, level)
+    coords_e = B.hhg_entry_coords(h, level)
+    e2u, _ = B.hhg_entry_to_unique(h, level)
+    first = np.full(U, -1, dtype=np.int64)
+    first[e2u[::-1]] = np.arange(E)[::-1]
+    k_u, x_u = workload_fields(coords_e[first], level)
+    ku = torch.as_tensor(k_u, dtype=torch.float64, device="cuda")
+    kl = torch.empty(E, dtype=torch.float64, device="cuda")
+    B.hhg_scatter_unique(h, level, B.F64, 1, ku, kl)
+    B.hhg_set_coefficient(h, kl, B.F64)
+    xu = torch.as_tensor(np.ascontiguousarray(x_u.T).reshape(-1), dtype=torch.float32, device="cuda")
+    x = torch.empty(3 * E, dtype=torch.float32, device="cuda")
+    B.hhg_scatter_unique(h, level, B.F32, 3, xu, x)
+    y = torch.empty_like(x)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 2x L2
+    n = 1 << level
+    nmacro = tets.shape[0]
+    interior_per_macro = (n - 1) * (n - 2) * (n - 3) // 6
+    dofs = 3 * U
+
+    for _ in range(max(3, args.warmup)):
+        B.hhg_apply(h, level, B.F32, x, y)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(dev)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    B.hhg_profile(h, 1)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        starts[s].record(stream)
+        B.hhg_apply(h, level, B.F32, x, y)
+        ends[s].record(stream)
+    torch.cuda.synchronize()
+    prof_ms, prof_launches = B.hhg_profile(h, 0, read=True)
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    # end-to-end: host buffers through the C ABI (H2D copy, apply, D2H copy, wait)
+    xh = torch.empty(3 * E, dtype=torch.float32, pin_memory=True)
+    xh.copy_(x.cpu())
+    yh = torch.empty_like(xh, pin_memory=True)
+    for _ in range(2):
+        B.hhg_apply_host(h, level, B.F32, xh, yh)
+    e2e_steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        B.hhg_apply_host(h, level, B.F32, xh, yh)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    time.sleep(0.2)
+    clk = clocks.stop()
+    assert torch.isfinite(y).all()
+    B.hhg_destroy(h)
+
+    ms_per_step = total_ms / args.steps
+    value = world * dofs / (ms_per_step * 1e-3) / 1e9
+    hbm_peak, peak_kind = measured_peaks()
+    launch_ms = prof_ms[0] / max(1, prof_launches[0])
+    bytes_per_launch = interior_per_macro * BYTES_PER_NODE_F32
+    flops_per_launch = interior_per_macro * FLOPS_PER_NODE
+    hbm_achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    alu_achieved = flops_per_launch / (launch_ms * 1e-3) / 1e12
+    traffic = profiled_traffic()
+    hbm_frac = hbm_achieved / hbm_peak
+    alu_frac = alu_achieved / alu_peak
+    if alu_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": round(alu_achieved, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
+                "frac": round(alu_frac, 4),
+                "peak_source": "FP32 FMA lanes: %d SMs x %d lanes x 2 flop x median SM clock %.0f MHz"
+                               % (SM_COUNT, FP32_LANES_PER_SM, sm_mhz)}
+    else:
+        roof = {"bound": "hbm", "achieved": round(hbm_achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(hbm_frac, 4), "peak_source": peak_kind}
+    roof.update({"kernel": "k_interior<float, APPLY> (one launch per macro)",
+                 "traffic": traffic,
+                 "algorithmic_bytes_per_launch": bytes_per_launch,
+                 "algorithmic_flops_per_launch": flops_per_launch,
+                 "launch_ms": round(launch_ms, 5),
+                 "hbm": {"achieved_gbs": round(hbm_achieved, 1), "peak_gbs": hbm_peak, "frac": round(hbm_frac, 4),
+                         "peak_source": peak_kind},
+                 "alu": {"achieved_tflops": round(alu_achieved, 3), "peak_tflops": round(alu_peak, 2),
+                         "frac": round(alu_frac, 4)},
+                 "skeleton_ms_per_step": round(prof_ms[1] / args.steps, 5)})
+    out = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "GDoF/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "level": level, "macros": int(nmacro), "nodes": int(U),
+                   "dofs": int(dofs), "entries": int(E), "l2": "flushed before every step (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "e2e": {"value": round(world * dofs / e2e_s / 1e9, 3), "unit": "GDoF/s",
+                "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4)},
+        "gpu_launches": int(prof_launches[0] + prof_launches[1]),
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(level)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------- reference arm
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    level = args.level
+    for _ in range(max(0, args.warmup)):
+        cpu_baseline(level, budget_s=0.5, seed=99)
+    times, rows_total = [], 0
+    per_step = max(1.0, min(8.0, 120.0 / max(1, args.steps)))
+    vals = []
+    for s in range(args.steps):
+        cb = cpu_baseline(level, budget_s=per_step, seed=s)
+        vals.append(cb["value"])
+    value = statistics.mean(vals)
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "GDoF/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": None,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("FP32", "FP64 oracle"), "level": level},
+        "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step: random macro-interior rows for %.1f s via the FP64 single-row oracle"
+                                   % per_step},
+        "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

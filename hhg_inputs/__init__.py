@@ -188,3 +188,17 @@ def lid_velocity(x):
     X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
     s = np.where(np.abs(Z - 1.0) < 1e-12, 16.0 * X * (1 - X) * Y * (1 - Y), 0.0)
     return np.stack([s, np.zeros_like(s), np.zeros_like(s)], axis=-1)
+
+
+def node_noise(coords, seed, comps=3, lo=-1.0, hi=1.0):
+    """i.i.d. uniform values attached to a set of node coordinates independently of their
+    order: the nodes are ranked lexicographically by their coordinates (rounded to 1e-9) and
+    the k-th ranked node gets the k-th draw.  Both implementations that hold the same node
+    set therefore see the same value at the same node."""
+    c = np.rint(np.asarray(coords, dtype=np.float64) * 1e9).astype(np.int64)
+    order = np.lexsort(c.T[::-1])
+    rng = np.random.default_rng(seed)
+    vals = rng.uniform(lo, hi, size=(c.shape[0], comps))
+    out = np.empty_like(vals)
+    out[order] = vals
+    return out if comps > 1 else out[:, 0]

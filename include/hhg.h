@@ -1,0 +1,174 @@
+/*
+ * hhg.h -- C ABI of libhhgs: scaled-stencil P1 finite element operators for
+ * vector-valued PDEs on hierarchical hybrid grids, on one sm_103a GPU.
+ *
+ * The method is the "physical stencil scaling" of Drzisga, Ruede and Wohlmuth,
+ * "Stencil scaling for vector-valued PDEs on hybrid grids with applications to
+ * generalized Newtonian fluids" (arXiv 1908.08666):
+ *   - the domain is an unstructured mesh of macro tetrahedra, each refined
+ *     uniformly (Sec. 2, Bey's rule);
+ *   - inside a macro every node sees the same 15-point stencil of 3x3 blocks
+ *     (Sec. 2.4, Fig. subtypes_and_stencil);
+ *   - for a nodal coefficient k the off-centre block of the edge (i, j) is
+ *       S_ij = khat_ij * Shat_ij + R_ij                     (Lemma 2.1)
+ *     with the patch mean khat (eq. patchmean) and the antisymmetric
+ *     correction R_ij = sum_c (k_{r_c} - k_{r_c^m}) S^c_ij (eq. correctionterm3D);
+ *     the centre block is minus the row sum;
+ *   - rows of nodes on macro faces/edges/vertices follow the interface
+ *     definition of Sec. 2.2.
+ *
+ * Conventions used by every entry point below.
+ *
+ * Layout.  A level stores each macro's closed tetrahedral lattice
+ * {(i,j,k): i,j,k >= 0, i+j+k <= n}, n = 2^level, in compact order
+ *     idx(i,j,k) = S(k) + R_k(j) + i,   S(k) = T(n+1) - T(n+1-k),
+ *     R_k(j) = j (2(n-k) + 3 - j) / 2,  T(a) = a(a+1)(a+2)/6,
+ * macros concatenated (macro m starts at m * T(n+1)); hhg_num_nodes returns
+ * the number of entries E = M * T(n+1).  Lattice point (i,j,k) of macro m
+ * with vertices (v0,v1,v2,v3) sits at v0 + (i(v1-v0) + j(v2-v0) + k(v3-v0))/n.
+ * A vector field is stored component-major: component c of entry e at
+ * [c*E + e] (3 components for velocity/displacement).  A scalar field
+ * (coefficient, pressure) has one component.  Nodes on the macro skeleton
+ * appear once per incident macro; every routine that writes a field writes
+ * all copies identically, and every input field must have consistent copies
+ * (hhg_scatter_unique produces such fields).
+ *
+ * Pointers.  Arguments named *_dev are device pointers owned by the caller,
+ * sized as stated; *_host are host pointers.  The library owns everything
+ * else (mesh, stencils, hierarchy, workspaces) and frees it in hhg_destroy.
+ *
+ * Execution.  All device work runs on the stream given to hhg_create, in
+ * order.  Calls that return host scalars wait for the stream with a bounded
+ * wait (hhg_set_timeout) and return HHG_ERR_TIMEOUT when it runs out.
+ *
+ * Errors.  Every call returns an hhg_status; nothing aborts.  hhg_last_error
+ * gives a message for the last failing call on the context.
+ *
+ * Dirichlet rows.  x holds the Dirichlet values at Dirichlet nodes.  The
+ * operator applied to x returns x on Dirichlet rows (identity rows, columns
+ * kept); residuals are 0 there.
+ */
+#ifndef HHG_H
+#define HHG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hhg_ctx hhg_ctx;
+
+typedef enum {
+  HHG_OK = 0,
+  HHG_ERR_ARG = 1,
+  HHG_ERR_CUDA = 2,
+  HHG_ERR_OOM = 3,
+  HHG_ERR_UNSUPPORTED = 4,
+  HHG_ERR_NOT_CONVERGED = 5,
+  HHG_ERR_NUMERIC = 6,
+  HHG_ERR_TIMEOUT = 7,
+  HHG_ERR_STATE = 8
+} hhg_status;
+
+/* Arithmetic type of a call's vectors. */
+typedef enum { HHG_F64 = 0, HHG_F32 = 1, HHG_BF16 = 2 } hhg_dtype;
+
+/* Operator families (Sec. 5.1.2 elasticity, Sec. 5.2 Stokes). */
+typedef enum { HHG_ELASTICITY = 0, HHG_STOKES = 1 } hhg_problem_kind;
+
+/* Sec. 2: physical scaling (Lemma 2.1), unphysical scaling (eq.
+ * stencilscalingwithoutcorr, R = 0), or nodal integration everywhere
+ * (eq. nodalintegration). */
+typedef enum { HHG_PHYSICAL = 0, HHG_UNPHYSICAL = 1, HHG_NODAL = 2 } hhg_variant;
+
+/* khat: patch mean (eq. patchmean) or edge mean (k_i + k_j)/2 (Remark after Sec. 2.2). */
+typedef enum { HHG_KHAT_PATCH = 0, HHG_KHAT_EDGE = 1 } hhg_khat;
+
+/* Sec. 2.2 interface rows: SYMMETRIC uses a_h for pairs of skeleton nodes and
+ * the scaled block otherwise, with a zero-row-sum centre block on skeleton
+ * rows; PRACTICAL uses the a_h row for every skeleton node. */
+typedef enum { HHG_IFACE_SYMMETRIC = 0, HHG_IFACE_PRACTICAL = 1 } hhg_iface;
+
+typedef struct {
+  hhg_problem_kind kind;
+  double nu;          /* Poisson ratio (elasticity): a^{E=1} = 1/(1+nu)(eps,eps) + nu/((1+nu)(1-2nu))(div,div) */
+  hhg_variant variant;
+  hhg_khat khat;
+  hhg_iface iface;
+} hhg_problem;
+
+/* Create a context on CUDA device `device`; all work is issued on `cuda_stream`
+ * (a cudaStream_t, may be NULL for the legacy default stream). */
+hhg_status hhg_create(hhg_ctx** ctx, int device, void* cuda_stream);
+hhg_status hhg_destroy(hhg_ctx* ctx);
+const char* hhg_last_error(hhg_ctx* ctx);
+/* Bound for every host wait on the stream, in milliseconds (default 120000). */
+hhg_status hhg_set_timeout(hhg_ctx* ctx, int64_t milliseconds);
+
+/* Macro mesh T_H (Sec. 2): nverts vertices xyz_host[3*nverts], ntets tetrahedra
+ * tets_host[4*ntets] (vertex ids; the order of each tetrahedron's vertices fixes
+ * its refinement, Bey's rule).  dirichlet_face_flags_host is NULL (every face of
+ * exactly one macro is Dirichlet) or int32[4*ntets]: face f of tetrahedron t
+ * (the face opposite its vertex f) is Dirichlet when non-zero.  Errors: ARG for
+ * degenerate tetrahedra or bad ids. */
+hhg_status hhg_set_macro_mesh(hhg_ctx* ctx, const double* xyz_host, int64_t nverts, const int64_t* tets_host,
+                              int64_t ntets, const int32_t* dirichlet_face_flags_host);
+
+/* Build levels 2..level_max (n = 4 .. 2^level_max intervals per macro edge;
+ * level 2 has one interior node per macro, the coarsest level of Sec. 2). */
+hhg_status hhg_refine(hhg_ctx* ctx, int level_max);
+
+/* Select the operator (computes the per-macro reference stencils Shat and the
+ * correction stencils S^1..3 of eq. correctionterm3D from element stiffness
+ * in FP64 on the host, and uploads them). */
+hhg_status hhg_set_problem(hhg_ctx* ctx, const hhg_problem* problem);
+
+/* Sizes of a level: entries (vector length E), unique nodes, free (non-Dirichlet) nodes. */
+hhg_status hhg_num_nodes(hhg_ctx* ctx, int level, int64_t* entries, int64_t* unique_nodes, int64_t* free_nodes);
+
+/* Coordinates of every entry of a level: xyz_host[3*E] (row per entry). */
+hhg_status hhg_entry_coords(hhg_ctx* ctx, int level, double* xyz_host);
+/* Unique node of every entry: map_host[E]; unique nodes are numbered macro
+ * interiors first (macro by macro, compact order), then skeleton nodes.
+ * dirichlet_host (nullable) receives int8[unique] Dirichlet flags. */
+hhg_status hhg_entry_to_unique(hhg_ctx* ctx, int level, int64_t* map_host, int8_t* dirichlet_host);
+
+/* Field conversion between the library layout and unique-node order.
+ * gather: dst_dev[c*U + u] = src_dev[c*E + first entry of u]; scatter: the
+ * reverse, writing every copy.  comps = 1 or 3 (or 4 for Stokes velocity+pressure
+ * stored as 4 components). */
+hhg_status hhg_gather_unique(hhg_ctx* ctx, int level, hhg_dtype dt, int comps, const void* src_dev, void* dst_dev);
+hhg_status hhg_scatter_unique(hhg_ctx* ctx, int level, hhg_dtype dt, int comps, const void* src_dev, void* dst_dev);
+
+/* Nodal coefficient k (E for elasticity, mu for Stokes; Sec. 2, eq. nodalquad)
+ * on the finest level, k_dev[E] in the library layout (dtype F64 or F32).
+ * Coarser levels receive the injection (coarse nodes are fine nodes). */
+hhg_status hhg_set_coefficient(hhg_ctx* ctx, const void* k_dev, hhg_dtype dt);
+
+/* y = A x on `level` (eq. residuallinalg without f): x_dev, y_dev are 3*E
+ * vectors of type dt; Dirichlet rows return x. */
+hhg_status hhg_apply(hhg_ctx* ctx, int level, hhg_dtype dt, const void* x_dev, void* y_dev);
+
+/* r = f - A x on free rows, 0 on Dirichlet rows (eq. residuallinalg).
+ * norm2_host (nullable) receives sum over unique free nodes of |r|^2 in FP64
+ * (this waits for the stream). */
+hhg_status hhg_residual(hhg_ctx* ctx, int level, hhg_dtype dt, const void* f_dev, const void* x_dev, void* r_dev,
+                        double* norm2_host);
+
+/* End-to-end apply with host buffers: copies x_host (3*E values of type dt,
+ * library layout; pinned memory gives full copy bandwidth) to a library-owned
+ * device buffer, applies A (as hhg_apply) and copies the result to y_host, then
+ * waits for the stream (bounded wait). */
+hhg_status hhg_apply_host(hhg_ctx* ctx, int level, hhg_dtype dt, const void* x_host, void* y_host);
+
+/* Kernel timing.  enable != 0 starts (and resets) recording CUDA events around
+ * the macro-interior launches and the skeleton launch of every sweep; ms_host[2]
+ * and launches_host[2] (nullable) receive the accumulated device time and launch
+ * counts of [interior, skeleton] since the last call (this waits for the stream). */
+hhg_status hhg_profile(hhg_ctx* ctx, int enable, double* ms_host, int64_t* launches_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HHG_H */

@@ -1,0 +1,198 @@
+"""Thin ctypes binding of libhhgs (include/hhg.h): same names, argument marshalling only.
+
+Every numeric step runs in the library's CUDA kernels.  Loading fails loudly when
+the shared library has not been built; there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libhhgs.so")
+
+HHG_OK = 0
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_UNSUPPORTED", 5: "ERR_NOT_CONVERGED",
+          6: "ERR_NUMERIC", 7: "ERR_TIMEOUT", 8: "ERR_STATE"}
+F64, F32, BF16 = 0, 1, 2
+ELASTICITY, STOKES = 0, 1
+PHYSICAL, UNPHYSICAL, NODAL = 0, 1, 2
+KHAT_PATCH, KHAT_EDGE = 0, 1
+IFACE_SYMMETRIC, IFACE_PRACTICAL = 0, 1
+
+
+class HhgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class hhg_problem(C.Structure):
+    _fields_ = [("kind", C.c_int), ("nu", C.c_double), ("variant", C.c_int), ("khat", C.c_int), ("iface", C.c_int)]
+
+
+_lib = None
+
+# name -> argtypes (all return int status unless listed in _RESTYPE)
+_SIGS = {
+    "hhg_create": [C.POINTER(C.c_void_p), C.c_int, C.c_void_p],
+    "hhg_destroy": [C.c_void_p],
+    "hhg_last_error": [C.c_void_p],
+    "hhg_set_timeout": [C.c_void_p, C.c_int64],
+    "hhg_set_macro_mesh": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p],
+    "hhg_refine": [C.c_void_p, C.c_int],
+    "hhg_set_problem": [C.c_void_p, C.POINTER(hhg_problem)],
+    "hhg_num_nodes": [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+    "hhg_entry_coords": [C.c_void_p, C.c_int, C.c_void_p],
+    "hhg_entry_to_unique": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+    "hhg_gather_unique": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+    "hhg_scatter_unique": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+    "hhg_set_coefficient": [C.c_void_p, C.c_void_p, C.c_int],
+    "hhg_apply": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+    "hhg_residual": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)],
+    "hhg_apply_host": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+    "hhg_profile": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+}
+_RESTYPE = {"hhg_last_error": C.c_char_p}
+
+
+def declared_symbols():
+    """Names declared in include/hhg.h (parsed from the header)."""
+    import re
+
+    hdr = open(os.path.join(os.path.dirname(HERE), "include", "hhg.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(hhg_[a-z0-9_]+)\s*\(", hdr)))
+
+
+def load(path=None):
+    """Load libhhgs.so (raises if it is missing: the library has no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libhhgs.so not built (%s); run __graft_entry__.build()" % p)
+    lib = C.CDLL(p)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = _RESTYPE.get(name, C.c_int)
+    _lib = lib
+    return lib
+
+
+def _check(ctx, st):
+    if st != HHG_OK:
+        msg = _lib.hhg_last_error(ctx).decode() if ctx else ""
+        raise HhgError(st, msg)
+
+
+def _ptr(a):
+    """Device/host address of a torch tensor, numpy array or int."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    raise TypeError(type(a))
+
+
+def hhg_create(device=0, stream=0):
+    lib = load()
+    h = C.c_void_p()
+    _check(None, lib.hhg_create(C.byref(h), device, stream or None))
+    return h.value
+
+
+def hhg_destroy(ctx):
+    _check(None, load().hhg_destroy(ctx))
+
+
+def hhg_last_error(ctx):
+    return load().hhg_last_error(ctx).decode()
+
+
+def hhg_set_timeout(ctx, ms):
+    _check(ctx, load().hhg_set_timeout(ctx, int(ms)))
+
+
+def hhg_set_macro_mesh(ctx, xyz, tets, dirichlet_face_flags=None):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int64)
+    fl = None if dirichlet_face_flags is None else np.ascontiguousarray(dirichlet_face_flags, dtype=np.int32)
+    _check(ctx, load().hhg_set_macro_mesh(ctx, xyz.ctypes.data, xyz.shape[0], tets.ctypes.data, tets.shape[0],
+                                          None if fl is None else fl.ctypes.data))
+
+
+def hhg_refine(ctx, level_max):
+    _check(ctx, load().hhg_refine(ctx, level_max))
+
+
+def hhg_set_problem(ctx, kind=ELASTICITY, nu=0.3, variant=PHYSICAL, khat=KHAT_PATCH, iface=IFACE_SYMMETRIC):
+    p = hhg_problem(kind, nu, variant, khat, iface)
+    _check(ctx, load().hhg_set_problem(ctx, C.byref(p)))
+
+
+def hhg_num_nodes(ctx, level):
+    e, u, f = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(ctx, load().hhg_num_nodes(ctx, level, C.byref(e), C.byref(u), C.byref(f)))
+    return e.value, u.value, f.value
+
+
+def hhg_entry_coords(ctx, level):
+    E, _, _ = hhg_num_nodes(ctx, level)
+    out = np.empty((E, 3))
+    _check(ctx, load().hhg_entry_coords(ctx, level, out.ctypes.data))
+    return out
+
+
+def hhg_entry_to_unique(ctx, level):
+    E, U, _ = hhg_num_nodes(ctx, level)
+    m = np.empty(E, dtype=np.int64)
+    d = np.empty(U, dtype=np.int8)
+    _check(ctx, load().hhg_entry_to_unique(ctx, level, m.ctypes.data, d.ctypes.data))
+    return m, d.astype(bool)
+
+
+def hhg_gather_unique(ctx, level, dt, comps, src, dst):
+    _check(ctx, load().hhg_gather_unique(ctx, level, dt, comps, _ptr(src), _ptr(dst)))
+
+
+def hhg_scatter_unique(ctx, level, dt, comps, src, dst):
+    _check(ctx, load().hhg_scatter_unique(ctx, level, dt, comps, _ptr(src), _ptr(dst)))
+
+
+def hhg_set_coefficient(ctx, k, dt):
+    _check(ctx, load().hhg_set_coefficient(ctx, _ptr(k), dt))
+
+
+def hhg_apply(ctx, level, dt, x, y):
+    _check(ctx, load().hhg_apply(ctx, level, dt, _ptr(x), _ptr(y)))
+
+
+def hhg_residual(ctx, level, dt, f, x, r, want_norm=False):
+    nrm = C.c_double()
+    _check(ctx, load().hhg_residual(ctx, level, dt, _ptr(f), _ptr(x), _ptr(r), C.byref(nrm) if want_norm else None))
+    return nrm.value if want_norm else None
+
+
+def hhg_apply_host(ctx, level, dt, x_host, y_host):
+    _check(ctx, load().hhg_apply_host(ctx, level, dt, _ptr(x_host), _ptr(y_host)))
+
+
+def hhg_profile(ctx, enable, read=False):
+    """Start/stop kernel timing; with read=True returns ([interior_ms, skeleton_ms], [launches])."""
+    if read:
+        ms = np.zeros(2)
+        nl = np.zeros(2, dtype=np.int64)
+        _check(ctx, load().hhg_profile(ctx, int(enable), ms.ctypes.data, nl.ctypes.data))
+        return ms, nl
+    _check(ctx, load().hhg_profile(ctx, int(enable), None, None))
+    return None

@@ -1,0 +1,1047 @@
+// libhhgs host side: context, macro mesh, refinement levels, skeleton
+// (interface) bookkeeping, per-macro stencil precomputation in FP64, and the
+// C ABI declared in include/hhg.h.
+//
+// Stencil precomputation (Sec. 2, Lemma 2.1; Sec. 2.4, eq. correctionterm3D):
+// inside a macro the refined mesh is the affine image of the Freudenthal
+// lattice, so every interior node sees the same 24 elements of 6 shapes (one
+// per Kuhn permutation).  For each of the 14 stencil directions d the patch
+// of the edge (0, d) is the set of elements containing both end points;
+//   Shat_d = sum_{t in patch} sym(K^t_{0d})                        (eq. stiffcontribution)
+//   R_d    = 1/2 sum_t (kbar^t - kbar^{t^m}) antisym(K^t_{0d})      (eq. corrtermgeneral)
+// with t^m the point reflection of t through the edge midpoint.  Writing
+// kbar^t - kbar^{t^m} as a combination of nodal k values turns R_d into
+// sum_c (k_{r_c} - k_{r_c^m}) C_{d,c} over the ring pairs of the edge; the
+// axial vectors of the antisymmetric C_{d,c} are what the kernels store.
+// Everything here is derived from the element stiffness matrices, computed
+// from the closed-form P1 gradients.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <set>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/hhg.h"
+#include "hhg_internal.h"
+#include "hhg_launch.h"
+
+using namespace hhg;
+
+namespace {
+
+struct DevMem {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevMem() = default;
+  DevMem(const DevMem&) = delete;
+  DevMem& operator=(const DevMem&) = delete;
+  ~DevMem() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t b) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = b;
+    if (b == 0) return cudaSuccess;
+    return cudaMalloc(&p, b);
+  }
+  template <typename T>
+  T* as() const {
+    return (T*)p;
+  }
+};
+
+struct HhgError {
+  hhg_status st;
+  std::string msg;
+};
+
+#define THROW(st, ...)                                      \
+  do {                                                      \
+    char _b[512];                                           \
+    snprintf(_b, sizeof(_b), __VA_ARGS__);                  \
+    throw HhgError{st, std::string(_b)};                    \
+  } while (0)
+
+#define CK(...)                                                                                      \
+  do {                                                                                               \
+    cudaError_t _e = (cudaError_t)(__VA_ARGS__);                                                         \
+    if (_e != cudaSuccess) {                                                                         \
+      hhg_status _s = (_e == cudaErrorMemoryAllocation) ? HHG_ERR_OOM : HHG_ERR_CUDA;                \
+      THROW(_s, "%s failed: %s (%s:%d)", #__VA_ARGS__, cudaGetErrorString(_e), __FILE__, __LINE__);        \
+    }                                                                                                \
+  } while (0)
+
+template <typename T>
+void upload(DevMem& d, const std::vector<T>& h) {
+  CK(d.alloc(h.size() * sizeof(T)));
+  if (!h.empty()) CK(cudaMemcpy(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+struct Vec3d {
+  double x, y, z;
+};
+
+// element stiffness K[a][b][m][l] = |t| (c_eps eps(phi_b e_l):eps(phi_a e_m) + c_div div(phi_b e_l) div(phi_a e_m))
+void element_stiffness(const Vec3d v[4], double c_eps, double c_div, double K[4][4][9]) {
+  double J[3][3];
+  for (int r = 0; r < 3; ++r) {
+    J[r][0] = (r == 0 ? v[1].x : r == 1 ? v[2].x : v[3].x) - v[0].x;
+    J[r][1] = (r == 0 ? v[1].y : r == 1 ? v[2].y : v[3].y) - v[0].y;
+    J[r][2] = (r == 0 ? v[1].z : r == 1 ? v[2].z : v[3].z) - v[0].z;
+  }
+  const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                     J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  if (std::fabs(det) < 1e-300) THROW(HHG_ERR_ARG, "degenerate element");
+  // inverse of J; gradient of barycentric a (a=1..3) = column a-1 of J^{-1}
+  double inv[3][3];
+  inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+  inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+  inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+  inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  double g[4][3];
+  for (int a = 1; a < 4; ++a)
+    for (int c = 0; c < 3; ++c) g[a][c] = inv[c][a - 1];
+  for (int c = 0; c < 3; ++c) g[0][c] = -(g[1][c] + g[2][c] + g[3][c]);
+  const double vol = std::fabs(det) / 6.0;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      const double gg = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
+      for (int m = 0; m < 3; ++m)
+        for (int l = 0; l < 3; ++l) {
+          const double eps = 0.5 * ((l == m ? gg : 0.0) + g[a][l] * g[b][m]);
+          const double dv = g[b][l] * g[a][m];
+          K[a][b][m * 3 + l] = vol * (c_eps * eps + c_div * dv);
+        }
+    }
+}
+
+struct MacroGeom {
+  Vec3d v[4];
+  Vec3d kuhn_to_x(double X, double Y, double Z, int n) const {
+    // x = v0 + (X (v1-v0) + Y (v2-v1) + Z (v3-v2)) / n
+    Vec3d r;
+    r.x = v[0].x + (X * (v[1].x - v[0].x) + Y * (v[2].x - v[1].x) + Z * (v[3].x - v[2].x)) / n;
+    r.y = v[0].y + (X * (v[1].y - v[0].y) + Y * (v[2].y - v[1].y) + Z * (v[3].y - v[2].y)) / n;
+    r.z = v[0].z + (X * (v[1].z - v[0].z) + Y * (v[2].z - v[1].z) + Z * (v[3].z - v[2].z)) / n;
+    return r;
+  }
+};
+
+void kuhn_vertices(int p, int P[4][3]) {
+  int a0, a1, a2;
+  kuhn_perm(p, a0, a1, a2);
+  for (int v = 0; v < 4; ++v)
+    for (int c = 0; c < 3; ++c) P[v][c] = (v == 3) ? 1 : 0;
+  P[1][a0] = 1;
+  P[2][a0] = 1;
+  P[2][a1] = 1;
+}
+
+// Kuhn coordinates of stencil direction d
+void dir_kuhn(int d, int out[3]) {
+  const int di = dir_di(d), dj = dir_dj(d), dk = dir_dk(d);
+  out[0] = di + dj + dk;
+  out[1] = dj + dk;
+  out[2] = dk;
+}
+
+int dir_from_kuhn(const int v[3]) {
+  for (int d = 0; d < NDIR; ++d) {
+    int w[3];
+    dir_kuhn(d, w);
+    if (w[0] == v[0] && w[1] == v[1] && w[2] == v[2]) return d;
+  }
+  return -1;
+}
+
+// Per-macro constants at intervals n: element stiffness of the 6 Kuhn element
+// types and the interior stencil (Shat and the correction axial vectors).
+void macro_constants(const MacroGeom& G, int n, double c_eps, double c_div, MacroConsts<double>& out) {
+  double KE[6][4][4][9];
+  for (int p = 0; p < 6; ++p) {
+    int P[4][3];
+    kuhn_vertices(p, P);
+    Vec3d v[4];
+    for (int a = 0; a < 4; ++a) v[a] = G.kuhn_to_x(P[a][0], P[a][1], P[a][2], n);
+    element_stiffness(v, c_eps, c_div, KE[p]);
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b)
+        for (int q = 0; q < 9; ++q) out.ke[p][a][b][q] = KE[p][a][b][q];
+  }
+  // patches of the 14 directions
+  for (int d = 0; d < NDIR; ++d) {
+    int dk[3];
+    dir_kuhn(d, dk);
+    double Sh[9] = {0};
+    // coefficient matrix of k at each neighbour offset (index = direction, 14 = centre)
+    double C[NDIR + 1][9];
+    double wk[NDIR + 1];
+    std::memset(C, 0, sizeof(C));
+    std::memset(wk, 0, sizeof(wk));
+    int count = 0;
+    struct PatchEl {
+      int p, a, b;
+      int c[3];
+    };
+    std::vector<PatchEl> patch;
+    for (int p = 0; p < 6; ++p) {
+      int P[4][3];
+      kuhn_vertices(p, P);
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          if (a == b) continue;
+          if (P[b][0] - P[a][0] == dk[0] && P[b][1] - P[a][1] == dk[1] && P[b][2] - P[a][2] == dk[2]) {
+            PatchEl e;
+            e.p = p;
+            e.a = a;
+            e.b = b;
+            for (int c = 0; c < 3; ++c) e.c[c] = -P[a][c];
+            patch.push_back(e);
+          }
+        }
+    }
+    count = (int)patch.size();
+    if (count != (dir_red(d) ? 6 : 4)) THROW(HHG_ERR_STATE, "patch of direction %d has %d elements", d, count);
+    auto node_of = [&](const int off[3]) -> int {
+      if (off[0] == 0 && off[1] == 0 && off[2] == 0) return NDIR;
+      return dir_from_kuhn(off);
+    };
+    for (const PatchEl& e : patch) {
+      const double* K = KE[e.p][e.a][e.b];
+      for (int m = 0; m < 3; ++m)
+        for (int l = 0; l < 3; ++l) Sh[m * 3 + l] += 0.5 * (K[m * 3 + l] + K[l * 3 + m]);
+      int P[4][3];
+      kuhn_vertices(e.p, P);
+      // vertices of t and of its reflection t^m (d - v)
+      for (int v = 0; v < 4; ++v) {
+        int off[3] = {e.c[0] + P[v][0], e.c[1] + P[v][1], e.c[2] + P[v][2]};
+        int ref[3] = {dk[0] - off[0], dk[1] - off[1], dk[2] - off[2]};
+        const int iv = node_of(off), ir = node_of(ref);
+        if (iv < 0 || ir < 0) THROW(HHG_ERR_STATE, "patch vertex is not a stencil neighbour");
+        wk[iv] += 0.25 / count;
+        for (int m = 0; m < 3; ++m)
+          for (int l = 0; l < 3; ++l) {
+            const double an = 0.5 * (K[m * 3 + l] - K[l * 3 + m]);
+            C[iv][m * 3 + l] += 0.5 * 0.25 * an;
+            C[ir][m * 3 + l] -= 0.5 * 0.25 * an;
+          }
+      }
+    }
+    // checks: Shat symmetric, khat weights, ring structure, pair antisymmetry
+    for (int m = 0; m < 3; ++m)
+      for (int l = 0; l < 3; ++l) {
+        double full = 0;
+        for (const PatchEl& e : patch) full += KE[e.p][e.a][e.b][m * 3 + l];
+        if (std::fabs(full - Sh[m * 3 + l]) > 1e-12 * (1 + std::fabs(full)))
+          THROW(HHG_ERR_STATE, "reference stencil of direction %d is not symmetric", d);
+      }
+    const double wr = dir_red(d) ? 1.0 / 12.0 : 0.125;
+    double cmax = 0;
+    for (int q = 0; q <= NDIR; ++q)
+      for (int r = 0; r < 9; ++r) cmax = std::max(cmax, std::fabs(C[q][r]));
+    for (int q = 0; q <= NDIR; ++q) {
+      bool ring = false;
+      for (int c = 0; c < ring_count(d); ++c) ring |= (q == ring_a(d, c) || q == ring_b(d, c));
+      const double want = (q == NDIR || q == d) ? 0.25 : (ring ? wr : 0.0);
+      if (std::fabs(wk[q] - want) > 1e-14) THROW(HHG_ERR_STATE, "patch-mean weight mismatch (dir %d)", d);
+      if (!ring) {
+        for (int r = 0; r < 9; ++r)
+          if (std::fabs(C[q][r]) > 1e-12 * cmax) THROW(HHG_ERR_STATE, "correction outside the ring (dir %d)", d);
+      }
+    }
+    for (int c = 0; c < 3; ++c) {
+      for (int r = 0; r < 3; ++r) out.st.s[d][c][r] = 0;
+      if (c >= ring_count(d)) continue;
+      const double* A = C[ring_a(d, c)];
+      const double* B = C[ring_b(d, c)];
+      for (int r = 0; r < 9; ++r)
+        if (std::fabs(A[r] + B[r]) > 1e-12 * (cmax + 1e-300))
+          THROW(HHG_ERR_STATE, "ring pair is not antisymmetric (dir %d)", d);
+      // axial vector of A: [a]_x = [[0,-a3,a2],[a3,0,-a1],[-a2,a1,0]]
+      out.st.s[d][c][0] = A[7];
+      out.st.s[d][c][1] = A[2];
+      out.st.s[d][c][2] = A[3];
+    }
+    if (d < 7) {
+      out.st.S[d][0] = Sh[0];
+      out.st.S[d][1] = Sh[4];
+      out.st.S[d][2] = Sh[8];
+      out.st.S[d][3] = Sh[1];
+      out.st.S[d][4] = Sh[2];
+      out.st.S[d][5] = Sh[5];
+    } else {
+      const double* S = out.st.S[d - 7];
+      const double want[6] = {Sh[0], Sh[4], Sh[8], Sh[1], Sh[2], Sh[5]};
+      for (int r = 0; r < 6; ++r)
+        if (std::fabs(S[r] - want[r]) > 1e-12 * (1 + std::fabs(want[r])))
+          THROW(HHG_ERR_STATE, "Shat(-d) != Shat(d) for direction %d", d);
+    }
+  }
+}
+
+template <typename T>
+MacroConsts<T> cast_consts(const MacroConsts<double>& c) {
+  MacroConsts<T> o;
+  const double* s = (const double*)&c;
+  T* d = (T*)&o;
+  static_assert(sizeof(MacroConsts<double>) / sizeof(double) == sizeof(MacroConsts<T>) / sizeof(T), "layout");
+  for (size_t q = 0; q < sizeof(MacroConsts<double>) / sizeof(double); ++q) d[q] = (T)s[q];
+  return o;
+}
+
+struct KeyHash {
+  size_t operator()(const std::array<int64_t, 3>& k) const {
+    size_t h = 1469598103934665603ull;
+    for (int q = 0; q < 3; ++q) h = (h ^ (size_t)k[q]) * 1099511628211ull;
+    return h;
+  }
+};
+
+struct LevelHost {
+  int level = 0, n = 0;
+  int64_t nt = 0, entries = 0;
+  std::vector<int32_t> tiles_int, tiles_all;
+  std::vector<int32_t> skel_ptr;
+  std::vector<SkelInc> skel_inc;
+  std::vector<int8_t> skel_dir;
+  std::vector<std::array<int64_t, 3>> skel_key;
+  std::vector<uint8_t> mask;
+  std::vector<int64_t> entry_to_unique, unique_first;
+  std::vector<int8_t> unique_dir;
+  int64_t nunique = 0, nfree = 0;
+  // restriction lists for the skeleton nodes of this level as the coarse level
+  std::vector<int32_t> rptr;
+  std::vector<int64_t> rent;
+  std::vector<double> rw;
+  // device
+  DevMem d_tiles_int, d_tiles_all, d_skel_ptr, d_skel_inc, d_skel_dir, d_mask, d_first, d_e2u;
+  DevMem d_rptr, d_rent, d_rw64, d_rw32;
+  DevMem d_mc64, d_mc32;
+  DevMem d_k64, d_k32;
+  std::vector<MacroStencil<double>> st64;
+  std::vector<MacroStencil<float>> st32;
+  LevelDev dev{};
+};
+
+}  // namespace
+
+struct hhg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int64_t timeout_ms = 120000;
+  std::string err;
+  // macro mesh
+  std::vector<Vec3d> xyz;
+  std::vector<std::array<int64_t, 4>> tets;
+  std::set<std::array<int64_t, 3>> dir_faces;
+  std::set<std::array<int64_t, 2>> dir_edges;
+  std::set<int64_t> dir_verts;
+  bool have_mesh = false;
+  int level_min = 2, level_max = -1;
+  std::vector<std::unique_ptr<LevelHost>> levels;  // index = level
+  hhg_problem prob{};
+  bool have_problem = false;
+  bool have_coeff = false;
+  OpFlags flags{1, 0, 0};
+  DevMem scratch;   // reduction partials
+  DevMem scalar;    // device scalars
+  double* pinned = nullptr;
+  // host-buffer apply (hhg_apply_host)
+  DevMem hx, hy;
+  // kernel timing (hhg_profile): event pairs per part (0 interior, 1 skeleton)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::array<cudaEvent_t, 2>> prof_ev[2];
+  int64_t prof_launches[2] = {0, 0};
+  ~hhg_ctx() {
+    if (pinned) cudaFreeHost(pinned);
+    for (auto e : ev_pool) cudaEventDestroy(e);
+    for (int q = 0; q < 2; ++q)
+      for (auto& pr : prof_ev[q]) {
+        cudaEventDestroy(pr[0]);
+        cudaEventDestroy(pr[1]);
+      }
+  }
+  cudaEvent_t take_event() {
+    if (!ev_pool.empty()) {
+      cudaEvent_t e = ev_pool.back();
+      ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) throw HhgError{HHG_ERR_CUDA, "cudaEventCreate failed"};
+    return e;
+  }
+  LevelHost& lv(int l) {
+    if (l < level_min || l > level_max || !levels[l]) THROW(HHG_ERR_ARG, "level %d not built", l);
+    return *levels[l];
+  }
+};
+
+namespace {
+
+void build_level(hhg_ctx* c, int level) {
+  auto L = std::make_unique<LevelHost>();
+  const int n = 1 << level;
+  const int M = (int)c->tets.size();
+  L->level = level;
+  L->n = n;
+  L->nt = lattice_size(n);
+  L->entries = L->nt * M;
+  // tiles
+  for (int k = 1; k <= n - 3; ++k)
+    for (int j0 = 1; j0 <= n - 2 - k; j0 += TILE_J)
+      for (int i0 = 1; i0 <= n - 1 - k - j0; i0 += TILE_I) L->tiles_int.push_back((k << 20) | (j0 << 10) | i0);
+  for (int k = 0; k <= n; ++k)
+    for (int j0 = 0; j0 <= n - k; j0 += TILE_J)
+      for (int i0 = 0; i0 <= n - k - j0; i0 += TILE_I) L->tiles_all.push_back((k << 20) | (j0 << 10) | i0);
+  // skeleton nodes
+  std::unordered_map<std::array<int64_t, 3>, int32_t, KeyHash> skel_id;
+  std::vector<std::vector<SkelInc>> incs;
+  L->entry_to_unique.assign(L->entries, -1);
+  int64_t nint = 0;
+  for (int m = 0; m < M; ++m)
+    for (int k = 0; k <= n; ++k)
+      for (int j = 0; j <= n - k; ++j)
+        for (int i = 0; i <= n - k - j; ++i) {
+          const int64_t e = (int64_t)m * L->nt + lattice_index(n, i, j, k);
+          if (lattice_interior(n, i, j, k)) {
+            L->entry_to_unique[e] = nint++;
+            continue;
+          }
+          const int64_t w[4] = {n - i - j - k, i, j, k};
+          std::vector<std::pair<int64_t, int64_t>> kv;
+          for (int q = 0; q < 4; ++q)
+            if (w[q] > 0) kv.push_back({c->tets[m][q], w[q]});
+          std::sort(kv.begin(), kv.end());
+          std::array<int64_t, 3> key = {-1, -1, -1};
+          for (size_t q = 0; q < kv.size(); ++q) key[q] = kv[q].first * 4096 + kv[q].second;
+          auto it = skel_id.find(key);
+          int32_t sid;
+          if (it == skel_id.end()) {
+            sid = (int32_t)incs.size();
+            skel_id.emplace(key, sid);
+            incs.emplace_back();
+            L->skel_key.push_back(key);
+            // Dirichlet if the node's support lies in a Dirichlet face
+            bool dir = false;
+            if (kv.size() == 3) {
+              dir = c->dir_faces.count({kv[0].first, kv[1].first, kv[2].first}) > 0;
+            } else if (kv.size() == 2) {
+              dir = c->dir_edges.count({kv[0].first, kv[1].first}) > 0;
+            } else {
+              dir = c->dir_verts.count(kv[0].first) > 0;
+            }
+            L->skel_dir.push_back(dir ? 1 : 0);
+          } else {
+            sid = it->second;
+          }
+          SkelInc I;
+          I.macro = m;
+          I.i = (int16_t)i;
+          I.j = (int16_t)j;
+          I.k = (int16_t)k;
+          I.pad = 0;
+          incs[sid].push_back(I);
+        }
+  const int64_t nskel = (int64_t)incs.size();
+  L->skel_ptr.assign(nskel + 1, 0);
+  for (int64_t s = 0; s < nskel; ++s) L->skel_ptr[s + 1] = L->skel_ptr[s] + (int32_t)incs[s].size();
+  L->skel_inc.reserve(L->skel_ptr[nskel]);
+  for (auto& v : incs)
+    for (auto& I : v) L->skel_inc.push_back(I);
+  L->nunique = nint + nskel;
+  L->unique_first.assign(L->nunique, -1);
+  L->unique_dir.assign(L->nunique, 0);
+  L->mask.assign(L->entries, 0);
+  for (int64_t e = 0; e < L->entries; ++e) {
+    const int64_t u = L->entry_to_unique[e];
+    if (u >= 0) {
+      L->unique_first[u] = e;
+      L->mask[e] = 1;
+    }
+  }
+  for (int64_t s = 0; s < nskel; ++s) {
+    const int64_t u = nint + s;
+    for (int q = L->skel_ptr[s]; q < L->skel_ptr[s + 1]; ++q) {
+      const SkelInc& I = L->skel_inc[q];
+      const int64_t e = (int64_t)I.macro * L->nt + lattice_index(n, I.i, I.j, I.k);
+      L->entry_to_unique[e] = u;
+      if (q == L->skel_ptr[s]) {
+        L->unique_first[u] = e;
+        L->mask[e] = L->skel_dir[s] ? 0 : 1;
+      }
+    }
+    L->unique_dir[u] = L->skel_dir[s];
+  }
+  L->nfree = L->nunique;
+  for (int64_t s = 0; s < nskel; ++s) L->nfree -= L->skel_dir[s];
+  for (int64_t e = 0; e < L->entries; ++e)
+    if (L->entry_to_unique[e] < 0) THROW(HHG_ERR_STATE, "entry without node");
+  c->levels[level] = std::move(L);
+}
+
+// restriction lists: coarse level lc, fine level lc+1
+void build_restriction(hhg_ctx* c, int lc) {
+  LevelHost& C = *c->levels[lc];
+  LevelHost& F = *c->levels[lc + 1];
+  const int nf = F.n;
+  const int64_t nskel = (int64_t)C.skel_dir.size();
+  C.rptr.assign(nskel + 1, 0);
+  C.rent.clear();
+  C.rw.clear();
+  for (int64_t s = 0; s < nskel; ++s) {
+    std::map<int64_t, std::pair<int64_t, double>> fine;  // unique fine node -> (entry, weight)
+    if (!C.skel_dir[s]) {
+      for (int q = C.skel_ptr[s]; q < C.skel_ptr[s + 1]; ++q) {
+        const SkelInc& I = C.skel_inc[q];
+        const int fi = 2 * I.i, fj = 2 * I.j, fk = 2 * I.k;
+        for (int d = -1; d < NDIR; ++d) {
+          const int qi = fi + (d < 0 ? 0 : dir_di(d)), qj = fj + (d < 0 ? 0 : dir_dj(d)),
+                    qk = fk + (d < 0 ? 0 : dir_dk(d));
+          if (!lattice_inside(nf, qi, qj, qk)) continue;
+          const int64_t e = (int64_t)I.macro * F.nt + lattice_index(nf, qi, qj, qk);
+          const int64_t u = F.entry_to_unique[e];
+          if (F.unique_dir[u]) continue;
+          fine.emplace(u, std::make_pair(e, d < 0 ? 1.0 : 0.5));
+        }
+      }
+    }
+    for (auto& kv : fine) {
+      C.rent.push_back(kv.second.first);
+      C.rw.push_back(kv.second.second);
+    }
+    C.rptr[s + 1] = (int32_t)C.rent.size();
+  }
+}
+
+void upload_level(hhg_ctx* c, LevelHost& L) {
+  upload(L.d_tiles_int, L.tiles_int);
+  upload(L.d_tiles_all, L.tiles_all);
+  upload(L.d_skel_ptr, L.skel_ptr);
+  upload(L.d_skel_inc, L.skel_inc);
+  upload(L.d_skel_dir, L.skel_dir);
+  upload(L.d_mask, L.mask);
+  upload(L.d_first, L.unique_first);
+  upload(L.d_e2u, L.entry_to_unique);
+  if (!L.rptr.empty()) {
+    upload(L.d_rptr, L.rptr);
+    upload(L.d_rent, L.rent);
+    upload(L.d_rw64, L.rw);
+    std::vector<float> rw32(L.rw.begin(), L.rw.end());
+    upload(L.d_rw32, rw32);
+  }
+  CK(L.d_k64.alloc(L.entries * sizeof(double)));
+  CK(L.d_k32.alloc(L.entries * sizeof(float)));
+  LevelDev& D = L.dev;
+  D.n = L.n;
+  D.nmacro = (int)c->tets.size();
+  D.nt = L.nt;
+  D.entries = L.entries;
+  D.ntiles_int = (int32_t)L.tiles_int.size();
+  D.ntiles_all = (int32_t)L.tiles_all.size();
+  D.tiles_int = L.d_tiles_int.as<int32_t>();
+  D.tiles_all = L.d_tiles_all.as<int32_t>();
+  D.nskel = (int32_t)L.skel_dir.size();
+  D.skel_ptr = L.d_skel_ptr.as<int32_t>();
+  D.skel_inc = L.d_skel_inc.as<SkelInc>();
+  D.skel_dir = L.d_skel_dir.as<int8_t>();
+  D.mask = L.d_mask.as<uint8_t>();
+}
+
+int64_t max_partials(hhg_ctx* c) {
+  int64_t mx = 1024;
+  for (int l = c->level_min; l <= c->level_max; ++l) {
+    const LevelHost& L = *c->levels[l];
+    mx = std::max<int64_t>(mx, (int64_t)L.tiles_int.size() * (int64_t)c->tets.size() + (L.skel_dir.size() + 3) / 4 + 8);
+  }
+  return mx;
+}
+
+void wait_stream(hhg_ctx* c) {
+  cudaEvent_t ev;
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(ev, c->stream);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(ev);
+    CK(e);
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    e = cudaEventQuery(ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) {
+      cudaEventDestroy(ev);
+      CK(e);
+    }
+    const auto ms =
+        std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+    if (ms > c->timeout_ms) {
+      cudaEventDestroy(ev);
+      THROW(HHG_ERR_TIMEOUT, "stream did not finish within %lld ms", (long long)c->timeout_ms);
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  cudaEventDestroy(ev);
+}
+
+template <typename F>
+hhg_status guard(hhg_ctx* c, F&& f) {
+  if (!c) return HHG_ERR_ARG;
+  try {
+    CK(cudaSetDevice(c->device));
+    f();
+    return HHG_OK;
+  } catch (const HhgError& e) {
+    c->err = e.msg;
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    c->err = "host allocation failed";
+    return HHG_ERR_OOM;
+  } catch (...) {
+    c->err = "unknown error";
+    return HHG_ERR_STATE;
+  }
+}
+
+void need_ready(hhg_ctx* c, bool coeff) {
+  if (!c->have_mesh || c->level_max < 0) THROW(HHG_ERR_STATE, "mesh/levels not set");
+  if (!c->have_problem) THROW(HHG_ERR_STATE, "problem not set");
+  if (coeff && !c->have_coeff) THROW(HHG_ERR_STATE, "coefficient not set");
+}
+
+template <typename T>
+const T* kptr(LevelHost& L);
+template <>
+const double* kptr<double>(LevelHost& L) {
+  return L.d_k64.as<double>();
+}
+template <>
+const float* kptr<float>(LevelHost& L) {
+  return L.d_k32.as<float>();
+}
+template <typename T>
+const MacroStencil<T>* stencils(LevelHost& L);
+template <>
+const MacroStencil<double>* stencils<double>(LevelHost& L) {
+  return L.st64.data();
+}
+template <>
+const MacroStencil<float>* stencils<float>(LevelHost& L) {
+  return L.st32.data();
+}
+template <typename T>
+const MacroConsts<T>* consts_dev(LevelHost& L);
+template <>
+const MacroConsts<double>* consts_dev<double>(LevelHost& L) {
+  return L.d_mc64.as<MacroConsts<double>>();
+}
+template <>
+const MacroConsts<float>* consts_dev<float>(LevelHost& L) {
+  return L.d_mc32.as<MacroConsts<float>>();
+}
+
+template <typename T>
+void sweep(hhg_ctx* c, int level, OpKind op, SweepArgs<T> a, double* norm2) {
+  LevelHost& L = c->lv(level);
+  a.k = kptr<T>(L);
+  int64_t np = 0;
+  if (norm2) a.partial = c->scratch.as<double>();
+  if (!c->prof) {
+    CK(launch_sweep<T>(L.dev, stencils<T>(L), consts_dev<T>(L), op, c->flags, a, c->stream, 3, 0, &np));
+  } else {
+    int64_t off = 0;
+    for (int part = 0; part < 2; ++part) {
+      std::array<cudaEvent_t, 2> pr = {c->take_event(), c->take_event()};
+      CK(cudaEventRecord(pr[0], c->stream));
+      int64_t used = 0;
+      CK(launch_sweep<T>(L.dev, stencils<T>(L), consts_dev<T>(L), op, c->flags, a, c->stream, part + 1, off,
+                         &used));
+      CK(cudaEventRecord(pr[1], c->stream));
+      off += used;
+      c->prof_ev[part].push_back(pr);
+      c->prof_launches[part] += part == 0 ? (L.dev.ntiles_int > 0 ? L.dev.nmacro : 0) : (L.dev.nskel > 0 ? 1 : 0);
+    }
+    np = off;
+  }
+  if (norm2) {
+    CK(launch_reduce(c->scratch.as<double>(), np, c->scalar.as<double>(), c->stream));
+    CK(cudaMemcpyAsync(c->pinned, c->scalar.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    wait_stream(c);
+    *norm2 = c->pinned[0];
+  }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+hhg_status hhg_create(hhg_ctx** out, int device, void* stream) {
+  if (!out) return HHG_ERR_ARG;
+  *out = nullptr;
+  hhg_ctx* c = nullptr;
+  try {
+    c = new hhg_ctx();
+  } catch (...) {
+    return HHG_ERR_OOM;
+  }
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  hhg_status st = guard(c, [&] {
+    CK(c->scalar.alloc(64 * sizeof(double)));
+    CK(cudaMallocHost((void**)&c->pinned, 64 * sizeof(double)));
+  });
+  if (st != HHG_OK) {
+    delete c;
+    return st;
+  }
+  *out = c;
+  return HHG_OK;
+}
+
+hhg_status hhg_destroy(hhg_ctx* c) {
+  if (!c) return HHG_ERR_ARG;
+  cudaSetDevice(c->device);
+  delete c;
+  return HHG_OK;
+}
+
+const char* hhg_last_error(hhg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+hhg_status hhg_set_timeout(hhg_ctx* c, int64_t ms) {
+  return guard(c, [&] {
+    if (ms <= 0) THROW(HHG_ERR_ARG, "timeout must be positive");
+    c->timeout_ms = ms;
+  });
+}
+
+hhg_status hhg_set_macro_mesh(hhg_ctx* c, const double* xyz, int64_t nverts, const int64_t* tets, int64_t ntets,
+                              const int32_t* dflags) {
+  return guard(c, [&] {
+    if (!xyz || !tets || nverts < 4 || ntets < 1) THROW(HHG_ERR_ARG, "empty mesh");
+    if (nverts >= (1LL << 40)) THROW(HHG_ERR_ARG, "too many vertices");
+    c->xyz.resize(nverts);
+    for (int64_t v = 0; v < nverts; ++v) c->xyz[v] = {xyz[3 * v], xyz[3 * v + 1], xyz[3 * v + 2]};
+    c->tets.resize(ntets);
+    std::map<std::array<int64_t, 3>, int> fcount;
+    for (int64_t t = 0; t < ntets; ++t) {
+      for (int q = 0; q < 4; ++q) {
+        const int64_t v = tets[4 * t + q];
+        if (v < 0 || v >= nverts) THROW(HHG_ERR_ARG, "tet %lld has bad vertex id", (long long)t);
+        c->tets[t][q] = v;
+      }
+      MacroGeom G;
+      for (int q = 0; q < 4; ++q) G.v[q] = c->xyz[c->tets[t][q]];
+      double K[4][4][9];
+      element_stiffness(G.v, 1.0, 0.0, K);  // throws on degenerate tets
+      for (int f = 0; f < 4; ++f) {
+        std::array<int64_t, 3> key;
+        int r = 0;
+        for (int q = 0; q < 4; ++q)
+          if (q != f) key[r++] = c->tets[t][q];
+        std::sort(key.begin(), key.end());
+        fcount[key]++;
+      }
+    }
+    c->dir_faces.clear();
+    c->dir_edges.clear();
+    c->dir_verts.clear();
+    for (int64_t t = 0; t < ntets; ++t)
+      for (int f = 0; f < 4; ++f) {
+        std::array<int64_t, 3> key;
+        int r = 0;
+        for (int q = 0; q < 4; ++q)
+          if (q != f) key[r++] = c->tets[t][q];
+        std::sort(key.begin(), key.end());
+        const bool dir = dflags ? dflags[4 * t + f] != 0 : fcount[key] == 1;
+        if (dir) c->dir_faces.insert(key);
+      }
+    for (const auto& f : c->dir_faces) {
+      c->dir_edges.insert({f[0], f[1]});
+      c->dir_edges.insert({f[0], f[2]});
+      c->dir_edges.insert({f[1], f[2]});
+      for (int q = 0; q < 3; ++q) c->dir_verts.insert(f[q]);
+    }
+    c->have_mesh = true;
+    c->levels.clear();
+    c->level_max = -1;
+    c->have_problem = false;
+    c->have_coeff = false;
+  });
+}
+
+hhg_status hhg_refine(hhg_ctx* c, int level_max) {
+  return guard(c, [&] {
+    if (!c->have_mesh) THROW(HHG_ERR_STATE, "mesh not set");
+    if (level_max < c->level_min || level_max > 9) THROW(HHG_ERR_ARG, "level_max must be in [2, 9]");
+    c->levels.clear();
+    c->levels.resize(level_max + 1);
+    c->level_max = level_max;
+    for (int l = c->level_min; l <= level_max; ++l) build_level(c, l);
+    for (int l = c->level_min; l < level_max; ++l) build_restriction(c, l);
+    for (int l = c->level_min; l <= level_max; ++l) upload_level(c, *c->levels[l]);
+    CK(c->scratch.alloc(max_partials(c) * sizeof(double)));
+    c->have_problem = false;
+    c->have_coeff = false;
+  });
+}
+
+hhg_status hhg_set_problem(hhg_ctx* c, const hhg_problem* p) {
+  return guard(c, [&] {
+    if (!p) THROW(HHG_ERR_ARG, "null problem");
+    if (!c->have_mesh || c->level_max < 0) THROW(HHG_ERR_STATE, "refine first");
+    double ce, cd;
+    if (p->kind == HHG_ELASTICITY) {
+      if (!(p->nu > -1.0 && p->nu < 0.5)) THROW(HHG_ERR_ARG, "Poisson ratio out of range");
+      ce = 1.0 / (1.0 + p->nu);
+      cd = p->nu / ((1.0 + p->nu) * (1.0 - 2.0 * p->nu));
+    } else if (p->kind == HHG_STOKES) {
+      ce = 2.0;
+      cd = 0.0;
+    } else {
+      THROW(HHG_ERR_ARG, "unknown problem kind");
+    }
+    if (p->variant == HHG_NODAL) THROW(HHG_ERR_UNSUPPORTED, "nodal-integration interior kernel not built");
+    if (p->variant != HHG_PHYSICAL && p->variant != HHG_UNPHYSICAL) THROW(HHG_ERR_ARG, "bad variant");
+    if (p->khat != HHG_KHAT_PATCH && p->khat != HHG_KHAT_EDGE) THROW(HHG_ERR_ARG, "bad khat");
+    if (p->iface != HHG_IFACE_SYMMETRIC && p->iface != HHG_IFACE_PRACTICAL) THROW(HHG_ERR_ARG, "bad iface");
+    for (int l = c->level_min; l <= c->level_max; ++l) {
+      LevelHost& L = *c->levels[l];
+      const int M = (int)c->tets.size();
+      std::vector<MacroConsts<double>> mc64(M);
+      std::vector<MacroConsts<float>> mc32(M);
+      L.st64.resize(M);
+      L.st32.resize(M);
+      for (int m = 0; m < M; ++m) {
+        MacroGeom G;
+        for (int q = 0; q < 4; ++q) G.v[q] = c->xyz[c->tets[m][q]];
+        macro_constants(G, L.n, ce, cd, mc64[m]);
+        mc32[m] = cast_consts<float>(mc64[m]);
+        L.st64[m] = mc64[m].st;
+        L.st32[m] = mc32[m].st;
+      }
+      upload(L.d_mc64, mc64);
+      upload(L.d_mc32, mc32);
+    }
+    c->prob = *p;
+    c->flags.physical = p->variant == HHG_PHYSICAL ? 1 : 0;
+    c->flags.khat_edge = p->khat == HHG_KHAT_EDGE ? 1 : 0;
+    c->flags.practical = p->iface == HHG_IFACE_PRACTICAL ? 1 : 0;
+    c->have_problem = true;
+  });
+}
+
+hhg_status hhg_num_nodes(hhg_ctx* c, int level, int64_t* entries, int64_t* unique_nodes, int64_t* free_nodes) {
+  return guard(c, [&] {
+    LevelHost& L = c->lv(level);
+    if (entries) *entries = L.entries;
+    if (unique_nodes) *unique_nodes = L.nunique;
+    if (free_nodes) *free_nodes = L.nfree;
+  });
+}
+
+hhg_status hhg_entry_coords(hhg_ctx* c, int level, double* xyz) {
+  return guard(c, [&] {
+    LevelHost& L = c->lv(level);
+    if (!xyz) THROW(HHG_ERR_ARG, "null output");
+    const int n = L.n;
+    for (size_t m = 0; m < c->tets.size(); ++m) {
+      Vec3d v[4];
+      for (int q = 0; q < 4; ++q) v[q] = c->xyz[c->tets[m][q]];
+      for (int k = 0; k <= n; ++k)
+        for (int j = 0; j <= n - k; ++j)
+          for (int i = 0; i <= n - k - j; ++i) {
+            const int64_t e = (int64_t)m * L.nt + lattice_index(n, i, j, k);
+            const double a = (double)i / n, b = (double)j / n, g = (double)k / n;
+            xyz[3 * e] = v[0].x + a * (v[1].x - v[0].x) + b * (v[2].x - v[0].x) + g * (v[3].x - v[0].x);
+            xyz[3 * e + 1] = v[0].y + a * (v[1].y - v[0].y) + b * (v[2].y - v[0].y) + g * (v[3].y - v[0].y);
+            xyz[3 * e + 2] = v[0].z + a * (v[1].z - v[0].z) + b * (v[2].z - v[0].z) + g * (v[3].z - v[0].z);
+          }
+    }
+  });
+}
+
+hhg_status hhg_entry_to_unique(hhg_ctx* c, int level, int64_t* map, int8_t* dir) {
+  return guard(c, [&] {
+    LevelHost& L = c->lv(level);
+    if (!map) THROW(HHG_ERR_ARG, "null output");
+    std::memcpy(map, L.entry_to_unique.data(), L.entries * sizeof(int64_t));
+    if (dir) std::memcpy(dir, L.unique_dir.data(), L.nunique);
+  });
+}
+
+hhg_status hhg_gather_unique(hhg_ctx* c, int level, hhg_dtype dt, int comps, const void* src, void* dst) {
+  return guard(c, [&] {
+    LevelHost& L = c->lv(level);
+    if (!src || !dst || comps < 1 || comps > 4) THROW(HHG_ERR_ARG, "bad arguments");
+    if (dt == HHG_F64)
+      CK(launch_gather<double>(L.nunique, comps, L.entries, L.nunique, L.d_first.as<int64_t>(), (const double*)src,
+                               (double*)dst, c->stream));
+    else if (dt == HHG_F32)
+      CK(launch_gather<float>(L.nunique, comps, L.entries, L.nunique, L.d_first.as<int64_t>(), (const float*)src,
+                              (float*)dst, c->stream));
+    else
+      THROW(HHG_ERR_ARG, "dtype");
+  });
+}
+
+hhg_status hhg_scatter_unique(hhg_ctx* c, int level, hhg_dtype dt, int comps, const void* src, void* dst) {
+  return guard(c, [&] {
+    LevelHost& L = c->lv(level);
+    if (!src || !dst || comps < 1 || comps > 4) THROW(HHG_ERR_ARG, "bad arguments");
+    if (dt == HHG_F64)
+      CK(launch_gather<double>(L.entries, comps, L.nunique, L.entries, L.d_e2u.as<int64_t>(), (const double*)src,
+                               (double*)dst, c->stream));
+    else if (dt == HHG_F32)
+      CK(launch_gather<float>(L.entries, comps, L.nunique, L.entries, L.d_e2u.as<int64_t>(), (const float*)src,
+                              (float*)dst, c->stream));
+    else
+      THROW(HHG_ERR_ARG, "dtype");
+  });
+}
+
+hhg_status hhg_set_coefficient(hhg_ctx* c, const void* k, hhg_dtype dt) {
+  return guard(c, [&] {
+    if (!c->have_mesh || c->level_max < 0) THROW(HHG_ERR_STATE, "refine first");
+    if (!k) THROW(HHG_ERR_ARG, "null coefficient");
+    LevelHost& F = *c->levels[c->level_max];
+    if (dt == HHG_F64) {
+      CK(cudaMemcpyAsync(F.d_k64.p, k, F.entries * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    } else if (dt == HHG_F32) {
+      CK(launch_convert<float, double>(F.entries, (const float*)k, F.d_k64.as<double>(), c->stream));
+    } else {
+      THROW(HHG_ERR_ARG, "coefficient dtype");
+    }
+    for (int l = c->level_max; l > c->level_min; --l) {
+      LevelHost& Lf = *c->levels[l];
+      LevelHost& Lc = *c->levels[l - 1];
+      CK(launch_inject<double>(Lf.dev, Lc.dev, Lf.d_k64.as<double>(), Lc.d_k64.as<double>(), c->stream));
+    }
+    for (int l = c->level_min; l <= c->level_max; ++l) {
+      LevelHost& L = *c->levels[l];
+      CK(launch_convert<double, float>(L.entries, L.d_k64.as<double>(), L.d_k32.as<float>(), c->stream));
+    }
+    c->have_coeff = true;
+  });
+}
+
+hhg_status hhg_apply(hhg_ctx* c, int level, hhg_dtype dt, const void* x, void* y) {
+  return guard(c, [&] {
+    need_ready(c, true);
+    if (!x || !y || x == y) THROW(HHG_ERR_ARG, "x and y must be distinct device buffers");
+    if (dt == HHG_F64) {
+      SweepArgs<double> a{};
+      a.x = (const double*)x;
+      a.out = (double*)y;
+      sweep<double>(c, level, OP_APPLY, a, nullptr);
+    } else if (dt == HHG_F32) {
+      SweepArgs<float> a{};
+      a.x = (const float*)x;
+      a.out = (float*)y;
+      sweep<float>(c, level, OP_APPLY, a, nullptr);
+    } else {
+      THROW(HHG_ERR_ARG, "dtype");
+    }
+  });
+}
+
+hhg_status hhg_residual(hhg_ctx* c, int level, hhg_dtype dt, const void* f, const void* x, void* r, double* norm2) {
+  return guard(c, [&] {
+    need_ready(c, true);
+    if (!x || !r || !f || x == r || f == r) THROW(HHG_ERR_ARG, "bad buffers");
+    if (dt == HHG_F64) {
+      SweepArgs<double> a{};
+      a.x = (const double*)x;
+      a.f = (const double*)f;
+      a.out = (double*)r;
+      sweep<double>(c, level, OP_RESID, a, norm2);
+    } else if (dt == HHG_F32) {
+      SweepArgs<float> a{};
+      a.x = (const float*)x;
+      a.f = (const float*)f;
+      a.out = (float*)r;
+      sweep<float>(c, level, OP_RESID, a, norm2);
+    } else {
+      THROW(HHG_ERR_ARG, "dtype");
+    }
+  });
+}
+
+hhg_status hhg_apply_host(hhg_ctx* c, int level, hhg_dtype dt, const void* x_host, void* y_host) {
+  return guard(c, [&] {
+    need_ready(c, true);
+    if (!x_host || !y_host) THROW(HHG_ERR_ARG, "null host buffer");
+    LevelHost& L = c->lv(level);
+    const size_t es = dt == HHG_F64 ? sizeof(double) : dt == HHG_F32 ? sizeof(float) : 0;
+    if (!es) THROW(HHG_ERR_ARG, "dtype");
+    const size_t bytes = 3 * (size_t)L.entries * es;
+    if (c->hx.bytes < bytes) {
+      CK(c->hx.alloc(bytes));
+      CK(c->hy.alloc(bytes));
+    }
+    CK(cudaMemcpyAsync(c->hx.p, x_host, bytes, cudaMemcpyHostToDevice, c->stream));
+    if (dt == HHG_F64) {
+      SweepArgs<double> a{};
+      a.x = c->hx.as<double>();
+      a.out = c->hy.as<double>();
+      sweep<double>(c, level, OP_APPLY, a, nullptr);
+    } else {
+      SweepArgs<float> a{};
+      a.x = c->hx.as<float>();
+      a.out = c->hy.as<float>();
+      sweep<float>(c, level, OP_APPLY, a, nullptr);
+    }
+    CK(cudaMemcpyAsync(y_host, c->hy.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+    wait_stream(c);
+  });
+}
+
+hhg_status hhg_profile(hhg_ctx* c, int enable, double* ms_host, int64_t* launches_host) {
+  return guard(c, [&] {
+    if (ms_host || launches_host) {
+      wait_stream(c);
+      for (int part = 0; part < 2; ++part) {
+        double tot = 0.0;
+        for (auto& pr : c->prof_ev[part]) {
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, pr[0], pr[1]));
+          tot += ms;
+        }
+        if (ms_host) ms_host[part] = tot;
+        if (launches_host) launches_host[part] = c->prof_launches[part];
+      }
+    }
+    for (int part = 0; part < 2; ++part) {
+      for (auto& pr : c->prof_ev[part]) {
+        c->ev_pool.push_back(pr[0]);
+        c->ev_pool.push_back(pr[1]);
+      }
+      c->prof_ev[part].clear();
+      c->prof_launches[part] = 0;
+    }
+    c->prof = enable != 0;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,128 @@
+// Internal structures shared by the host setup (hhg_host.cpp) and the CUDA
+// kernels (hhg_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+
+#ifdef __CUDACC__
+#define HHG_HD __host__ __device__ __forceinline__
+#else
+#define HHG_HD inline
+#endif
+
+namespace hhg {
+
+// ---------------------------------------------------------------------------
+// Lattice of one refined macro.  Corner coordinates (i, j, k) with i+j+k <= n
+// address the point v0 + (i (v1-v0) + j (v2-v0) + k (v3-v0)) / n.  In the
+// coordinates X = i+j+k, Y = j+k, Z = k the macro is {0 <= Z <= Y <= X <= n}
+// and Bey's refinement is the Freudenthal (Kuhn) lattice: its edges are the
+// seven 0/1 vectors and their negatives, its elements the Kuhn simplices
+// c, c+e_p0, c+e_p0+e_p1, c+(1,1,1) for the 6 permutations p (Sec. 2.4).
+// ---------------------------------------------------------------------------
+
+// The 14 stencil directions in corner coordinates.  d < 7 are the Kuhn 0/1
+// vectors (1,0,0) (0,1,0) (0,0,1) (1,1,0) (0,1,1) (1,0,1) (1,1,1); d+7 = -d.
+// Directions 0,1,2,6 (and negatives) lie in six elements ("red" edges),
+// directions 3,4,5 (and negatives) in four.
+constexpr int NDIR = 14;
+HHG_HD int dir_di(int d) {
+  const int t[7] = {1, -1, 0, 0, -1, 1, 0};
+  return d < 7 ? t[d] : -t[d - 7];
+}
+HHG_HD int dir_dj(int d) {
+  const int t[7] = {0, 1, -1, 1, 0, -1, 0};
+  return d < 7 ? t[d] : -t[d - 7];
+}
+HHG_HD int dir_dk(int d) {
+  const int t[7] = {0, 0, 1, 0, 1, 1, 1};
+  return d < 7 ? t[d] : -t[d - 7];
+}
+HHG_HD int dir_neg(int d) { return d < 7 ? d + 7 : d - 7; }
+HHG_HD bool dir_red(int d) {
+  int e = d < 7 ? d : d - 7;
+  return e == 0 || e == 1 || e == 2 || e == 6;
+}
+// Ring pairs of the edge (0, d): for every c the nodes r_c and its point
+// reflection r_c^m = d - r_c through the edge midpoint, both neighbours of 0
+// (stencil direction indices).  Red edges have three pairs, the others two.
+HHG_HD int ring_count(int d) { return dir_red(d) ? 3 : 2; }
+HHG_HD int ring_a(int d, int c) {
+  const int t[7][3] = {{3, 5, 6}, {3, 4, 6}, {5, 4, 6}, {0, 6, -1}, {1, 6, -1}, {0, 6, -1}, {0, 1, 2}};
+  return d < 7 ? t[d][c] : dir_neg(t[d - 7][c]);
+}
+HHG_HD int ring_b(int d, int c) {
+  const int t[7][3] = {{8, 9, 11}, {7, 9, 12}, {7, 8, 10}, {1, 9, -1}, {2, 7, -1}, {2, 8, -1}, {4, 5, 3}};
+  return d < 7 ? t[d][c] : dir_neg(t[d - 7][c]);
+}
+
+HHG_HD int64_t tetnum(int64_t a) { return a * (a + 1) * (a + 2) / 6; }
+HHG_HD int64_t lattice_size(int n) { return tetnum(n + 1); }
+// compact index of (i, j, k) inside one macro
+HHG_HD int64_t lattice_index(int n, int i, int j, int k) {
+  const int64_t m = n - k;
+  return tetnum(n + 1) - tetnum(n + 1 - k) + (int64_t)j * (2 * m + 3 - j) / 2 + i;
+}
+HHG_HD bool lattice_inside(int n, int i, int j, int k) { return i >= 0 && j >= 0 && k >= 0 && i + j + k <= n; }
+HHG_HD bool lattice_interior(int n, int i, int j, int k) {
+  return i >= 1 && j >= 1 && k >= 1 && i + j + k <= n - 1;
+}
+
+// Kuhn element of permutation p: vertex a = c + P_a(p) (Kuhn coordinates).
+HHG_HD void kuhn_perm(int p, int& a0, int& a1, int& a2) {
+  const int t[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  a0 = t[p][0];
+  a1 = t[p][1];
+  a2 = t[p][2];
+}
+
+// ---------------------------------------------------------------------------
+// per-macro constants
+// ---------------------------------------------------------------------------
+
+// Interior stencil of one macro (kernel parameter).  Shat for the 7 positive
+// directions (Shat_{-d} = Shat_d), symmetric 3x3 stored xx yy zz xy xz yz; axial
+// vectors of the correction matrices (eq. correctionterm3D): the antisymmetric
+// matrix of ring pair c of direction d is [s[d][c]]_x, acting as s x v.
+template <typename T>
+struct MacroStencil {
+  T S[7][6];
+  T s[NDIR][3][3];
+};
+
+// Constants of one macro for the skeleton kernel (global memory): the interior
+// stencil plus the 6 element stiffness matrices K[type][a][b][m][l] (test
+// vertex a, trial vertex b) of the Kuhn element types.
+template <typename T>
+struct MacroConsts {
+  MacroStencil<T> st;
+  T ke[6][4][4][9];
+};
+
+// one incidence of a skeleton node in a macro
+struct SkelInc {
+  int32_t macro;
+  int16_t i, j, k;
+  int16_t pad;
+};
+
+// device view of one level
+struct LevelDev {
+  int n;
+  int nmacro;
+  int64_t nt;          // entries per macro
+  int64_t entries;     // nmacro * nt
+  int32_t ntiles_int;  // interior tiles
+  int32_t ntiles_all;  // tiles over all lattice points
+  const int32_t* tiles_int;  // packed (k << 20) | (j0 << 10) | i0
+  const int32_t* tiles_all;
+  int32_t nskel;
+  const int32_t* skel_ptr;   // [nskel+1]
+  const SkelInc* skel_inc;   // incidences
+  const int8_t* skel_dir;    // Dirichlet flag per skeleton node
+  const uint8_t* mask;       // [entries] 1 = owned copy of a free node (dot products)
+};
+
+constexpr int TILE_I = 32;
+constexpr int TILE_J = 4;
+
+}  // namespace hhg

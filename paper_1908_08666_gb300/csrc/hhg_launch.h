@@ -1,0 +1,70 @@
+// Kernel launchers (C++ linkage, internal).  Each returns a cudaError_t as int.
+#pragma once
+#include <cstdint>
+
+#include "hhg_internal.h"
+
+namespace hhg {
+
+enum OpKind { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_CHEBY = 3 };
+
+// Flags of the operator variant, uniform per launch.
+struct OpFlags {
+  int physical;   // 1: add the correction R (physical scaling); 0: unphysical
+  int khat_edge;  // 1: khat = (k_i + k_j)/2; 0: patch mean
+  int practical;  // 1: skeleton rows are the a_h rows; 0: symmetric interface rows
+};
+
+// Arguments of one stencil sweep.  Vectors are component-major over the level
+// (component stride = entries).  Scalars for the smoothers:
+//   JACOBI: x_out = x + omega * D^{-1} (f - A x)
+//   CHEBY:  d_out = rho1 * d + rho2 * D^{-1} (f - A x);  x_out = x + d_out
+template <typename T>
+struct SweepArgs {
+  const T* x;
+  const T* f;
+  const T* k;
+  const T* d;
+  T* out;   // y (APPLY), r (RESID), x_out (JACOBI, CHEBY)
+  T* dout;  // CHEBY only
+  double* partial;  // RESID: per-block partial sums of |r|^2 (nullable)
+  double omega, rho1, rho2;
+};
+
+// parts: 1 = macro-interior kernels (one launch per macro), 2 = skeleton kernel, 3 = both.
+// partial_offset: first partial slot used (the interior launches take ntiles_int slots per
+// macro, then the skeleton kernel one per block); *partial_count returns the slots used.
+template <typename T>
+int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev, OpKind op,
+                 const OpFlags& fl, const SweepArgs<T>& a, void* stream, int parts, int64_t partial_offset,
+                 int64_t* partial_count);
+
+// sum of partials[0..count) into out[0] (single block), deterministic
+int launch_reduce(const double* partials, int64_t count, double* out, void* stream);
+
+// dot over unique free nodes: sum_e mask[e] * sum_c a[c][e] b[c][e]
+template <typename T>
+int launch_dot(const LevelDev& L, int comps, const T* a, const T* b, double* partials, int64_t* partial_count,
+               void* stream);
+
+// multigrid transfers and coefficient injection (all on the fine level's lattice)
+template <typename T>
+int launch_prolong_add(const LevelDev& Lf, const LevelDev& Lc, const T* ec, T* ef, void* stream);
+template <typename T>
+int launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const int32_t* rptr, const int64_t* rent, const T* rw,
+                    const T* rf, T* rc, void* stream);
+template <typename T>
+int launch_inject(const LevelDev& Lf, const LevelDev& Lc, const T* kf, T* kc, void* stream);
+
+// vector kernels over n elements
+template <typename T>
+int launch_axpby(int64_t n, T a, const T* x, T b, T* y, void* stream);  // y = a x + b y
+template <typename T, typename U>
+int launch_convert(int64_t n, const T* src, U* dst, void* stream);
+template <typename T>
+int launch_gather(int64_t count, int comps, int64_t src_stride, int64_t dst_stride, const int64_t* idx, const T* src,
+                  T* dst, void* stream);  // dst[c*dst_stride + u] = src[c*src_stride + idx[u]]
+template <typename T>
+int launch_fill(int64_t n, T v, T* dst, void* stream);
+
+}  // namespace hhg

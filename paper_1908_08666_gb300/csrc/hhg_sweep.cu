@@ -1,0 +1,378 @@
+// Scaled-stencil sweeps on one level: operator apply, residual, Jacobi and
+// Chebyshev smoothing steps (Sec. 2 and Sec. 4.1 of arXiv 1908.08666).
+//
+// Macro-interior rows (k_interior): for the interior node i and each of the 14
+// stencil directions d (edge (i, i+d) lies in 6 or 4 elements, Sec. 2.4)
+//     khat_d = (k_i + k_{i+d})/4 + w_d * sum_{ring nodes r of the edge} k_r
+// with w_d = 1/12 for six-element edges and 1/8 for four-element edges (this is
+// the patch mean of the element means, eq. patchmean), and
+//     S_d = khat_d * Shat_d + sum_c (k_{r_c} - k_{r_c^m}) [s_{d,c}]_x
+// (Lemma 2.1 with the correction of eq. correctionterm3D written as the cross
+// product with an axial vector).  The centre block is -sum_d S_d, so
+//     (A x)_i = sum_d S_d (x_{i+d} - x_i).
+// Shat_{-d} = Shat_d, so the symmetric part is applied once per direction pair:
+// Shat_d (khat_d dx_d + khat_{-d} dx_{-d}).
+//
+// Skeleton rows (k_skeleton, nodes on macro faces/edges/vertices, Sec. 2.2):
+// pairs of skeleton nodes use nodal integration a_h, summed over the incident
+// elements of every incident macro; pairs with a macro-interior neighbour use
+// that macro's scaled block; the centre block is minus the off-diagonal row
+// sum.  With the practical interface rule the whole row is the a_h row.
+#include <cuda_runtime.h>
+
+#include "hhg_internal.h"
+#include "hhg_launch.h"
+
+namespace hhg {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ void block_sum_store(double v, double* out) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nw = (blockDim.x * blockDim.y + 31) / 32;
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  if (tid < 32) {
+    double s = tid < nw ? red[tid] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (tid == 0) *out = s;
+  }
+}
+
+template <typename T, int OP>
+__device__ __forceinline__ void epilogue(const SweepArgs<T>& a, int64_t e, int64_t E, T ax, T ay, T az, T dgx, T dgy,
+                                         T dgz, T x0, T y0, T z0, double& r2) {
+  if (OP == OP_APPLY) {
+    a.out[e] = ax;
+    a.out[e + E] = ay;
+    a.out[e + 2 * E] = az;
+  } else {
+    const T rx = a.f[e] - ax, ry = a.f[e + E] - ay, rz = a.f[e + 2 * E] - az;
+    if (OP == OP_RESID) {
+      a.out[e] = rx;
+      a.out[e + E] = ry;
+      a.out[e + 2 * E] = rz;
+      r2 += (double)rx * rx + (double)ry * ry + (double)rz * rz;
+    } else if (OP == OP_JACOBI) {
+      const T om = (T)a.omega;
+      a.out[e] = x0 + om * rx / dgx;
+      a.out[e + E] = y0 + om * ry / dgy;
+      a.out[e + 2 * E] = z0 + om * rz / dgz;
+    } else {  // OP_CHEBY
+      const T r1 = (T)a.rho1, r2c = (T)a.rho2;
+      const T ux = r1 * a.d[e] + r2c * rx / dgx;
+      const T uy = r1 * a.d[e + E] + r2c * ry / dgy;
+      const T uz = r1 * a.d[e + 2 * E] + r2c * rz / dgz;
+      a.dout[e] = ux;
+      a.dout[e + E] = uy;
+      a.dout[e + 2 * E] = uz;
+      a.out[e] = x0 + ux;
+      a.out[e + E] = y0 + uy;
+      a.out[e + 2 * E] = z0 + uz;
+    }
+  }
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(TILE_I* TILE_J) k_interior(const LevelDev L, const MacroStencil<T> st,
+                                                              const int macro, const OpFlags fl,
+                                                              const SweepArgs<T> a) {
+  const int32_t tile = L.tiles_int[blockIdx.x];
+  const int n = L.n;
+  const int k = tile >> 20;
+  const int j = ((tile >> 10) & 1023) + threadIdx.y;
+  const int i = (tile & 1023) + threadIdx.x;
+  double r2 = 0.0;
+  if (i + j + k <= n - 1) {  // i, j, k >= 1 by construction of the interior tiles
+    const int64_t E = L.entries;
+    const int64_t base = (int64_t)macro * L.nt;
+    const T* __restrict__ px = a.x + base;
+    const T* __restrict__ py = px + E;
+    const T* __restrict__ pz = py + E;
+    const T* __restrict__ pk = a.k + base;
+    // row starts of the seven lattice rows the stencil touches
+    const int m = n - k;
+    const int r00 = (int)(tetnum(n + 1) - tetnum(n + 1 - k)) + j * (2 * m + 3 - j) / 2;
+    const int r10 = r00 + (m + 1 - j);
+    const int rm0 = r00 - (m + 2 - j);
+    const int sz = (m + 1) * (m + 2) / 2;
+    const int szm = (m + 2) * (m + 3) / 2;
+    const int r01 = r00 + sz - j;
+    const int r0m = r00 - szm + j;
+    const int rm1 = rm0 + sz - j + 1;
+    const int r1m = r10 - szm + j + 1;
+    int nb[NDIR];
+    nb[0] = r00 + i + 1;
+    nb[1] = r10 + i - 1;
+    nb[2] = rm1 + i;
+    nb[3] = r10 + i;
+    nb[4] = r01 + i - 1;
+    nb[5] = rm1 + i + 1;
+    nb[6] = r01 + i;
+    nb[7] = r00 + i - 1;
+    nb[8] = rm0 + i + 1;
+    nb[9] = r1m + i;
+    nb[10] = rm0 + i;
+    nb[11] = r0m + i + 1;
+    nb[12] = r1m + i - 1;
+    nb[13] = r0m + i;
+    const int c0 = r00 + i;
+    const T x0 = px[c0], y0 = py[c0], z0 = pz[c0], k0 = pk[c0];
+    T kk[NDIR], dx[NDIR], dy[NDIR], dz[NDIR];
+#pragma unroll
+    for (int d = 0; d < NDIR; ++d) {
+      const int o = nb[d];
+      kk[d] = pk[o];
+      dx[d] = px[o] - x0;
+      dy[d] = py[o] - y0;
+      dz[d] = pz[o] - z0;
+    }
+    T ax = 0, ay = 0, az = 0, dgx = 0, dgy = 0, dgz = 0;
+#pragma unroll
+    for (int d = 0; d < 7; ++d) {
+      const int e = d + 7;
+      const T wr = dir_red(d) ? (T)(1.0 / 12.0) : (T)0.125;
+      T rsp = 0, rsm = 0;
+      T wpx = 0, wpy = 0, wpz = 0, wmx = 0, wmy = 0, wmz = 0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (c < ring_count(d)) {
+          const T ka = kk[ring_a(d, c)], kb = kk[ring_b(d, c)];
+          const T la = kk[ring_a(e, c)], lb = kk[ring_b(e, c)];
+          rsp += ka + kb;
+          rsm += la + lb;
+          const T dp = ka - kb, dm = la - lb;
+          wpx += dp * st.s[d][c][0];
+          wpy += dp * st.s[d][c][1];
+          wpz += dp * st.s[d][c][2];
+          wmx += dm * st.s[e][c][0];
+          wmy += dm * st.s[e][c][1];
+          wmz += dm * st.s[e][c][2];
+        }
+      }
+      T khp, khm;
+      if (fl.khat_edge) {
+        khp = (T)0.5 * (k0 + kk[d]);
+        khm = (T)0.5 * (k0 + kk[e]);
+      } else {
+        khp = (T)0.25 * (k0 + kk[d]) + wr * rsp;
+        khm = (T)0.25 * (k0 + kk[e]) + wr * rsm;
+      }
+      const T vx = khp * dx[d] + khm * dx[e];
+      const T vy = khp * dy[d] + khm * dy[e];
+      const T vz = khp * dz[d] + khm * dz[e];
+      const T* S = st.S[d];
+      ax += S[0] * vx + S[3] * vy + S[4] * vz;
+      ay += S[3] * vx + S[1] * vy + S[5] * vz;
+      az += S[4] * vx + S[5] * vy + S[2] * vz;
+      if (fl.physical) {
+        ax += wpy * dz[d] - wpz * dy[d] + wmy * dz[e] - wmz * dy[e];
+        ay += wpz * dx[d] - wpx * dz[d] + wmz * dx[e] - wmx * dz[e];
+        az += wpx * dy[d] - wpy * dx[d] + wmx * dy[e] - wmy * dx[e];
+      }
+      if (OP == OP_JACOBI || OP == OP_CHEBY) {
+        const T ks = khp + khm;
+        dgx -= ks * S[0];
+        dgy -= ks * S[1];
+        dgz -= ks * S[2];
+      }
+    }
+    epilogue<T, OP>(a, base + c0, E, ax, ay, az, dgx, dgy, dgz, x0, y0, z0, r2);
+  }
+  if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
+}
+
+// Kuhn coordinates of corner (i, j, k): X = i+j+k, Y = j+k, Z = k.
+__device__ __forceinline__ bool kuhn_inside(int n, int X, int Y, int Z) {
+  return 0 <= Z && Z <= Y && Y <= X && X <= n;
+}
+__device__ __forceinline__ bool kuhn_interior(int n, int X, int Y, int Z) {
+  return 1 <= Z && Z < Y && Y < X && X <= n - 1;
+}
+
+// One warp per skeleton node.  Lanes 0..23 take the 24 candidate elements
+// (Kuhn permutation p = lane / 4, position of the node av = lane % 4) of each
+// incident macro, lanes 0..13 the 14 stencil directions; the row is summed
+// over the warp and written to every copy of the node.
+template <typename T, int OP>
+__global__ void __launch_bounds__(128) k_skeleton(const LevelDev L, const MacroConsts<T>* __restrict__ mc,
+                                                   const OpFlags fl, const SweepArgs<T> a) {
+  const int lane = threadIdx.x & 31;
+  const int s = blockIdx.x * 4 + (threadIdx.x >> 5);
+  double r2 = 0.0;
+  if (s < L.nskel) {
+    const int n = L.n;
+    const int64_t E = L.entries;
+    const int b0 = L.skel_ptr[s], b1 = L.skel_ptr[s + 1];
+    const SkelInc I0 = L.skel_inc[b0];
+    const int64_t e0 = (int64_t)I0.macro * L.nt + lattice_index(n, I0.i, I0.j, I0.k);
+    const T x0 = a.x[e0], y0 = a.x[e0 + E], z0 = a.x[e0 + 2 * E];
+    if (L.skel_dir[s]) {
+      for (int q = b0 + lane; q < b1; q += 32) {
+        const SkelInc I = L.skel_inc[q];
+        const int64_t e = (int64_t)I.macro * L.nt + lattice_index(n, I.i, I.j, I.k);
+        if (OP == OP_RESID) {
+          a.out[e] = 0;
+          a.out[e + E] = 0;
+          a.out[e + 2 * E] = 0;
+        } else {
+          a.out[e] = x0;
+          a.out[e + E] = y0;
+          a.out[e + 2 * E] = z0;
+          if (OP == OP_CHEBY) {
+            a.dout[e] = 0;
+            a.dout[e + E] = 0;
+            a.dout[e + 2 * E] = 0;
+          }
+        }
+      }
+    } else {
+      T ax = 0, ay = 0, az = 0, dgx = 0, dgy = 0, dgz = 0;
+      for (int q = b0; q < b1; ++q) {
+        const SkelInc I = L.skel_inc[q];
+        const MacroConsts<T>& C = mc[I.macro];
+        const int64_t base = (int64_t)I.macro * L.nt;
+        const T* px = a.x + base;
+        const T* pk = a.k + base;
+        const int X = I.i + I.j + I.k, Y = I.j + I.k, Z = I.k;
+        if (lane < 24) {
+          // a_h part: one candidate element of this macro around the node
+          const int p = lane >> 2, av = lane & 3;
+          int a0, a1, a2;
+          kuhn_perm(p, a0, a1, a2);
+          int PX[4] = {0, 0, 0, 1}, PY[4] = {0, 0, 0, 1}, PZ[4] = {0, 0, 0, 1};
+          PX[1] = a0 == 0; PY[1] = a0 == 1; PZ[1] = a0 == 2;
+          PX[2] = (a0 == 0) | (a1 == 0); PY[2] = (a0 == 1) | (a1 == 1); PZ[2] = (a0 == 2) | (a1 == 2);
+          const int cX = X - PX[av], cY = Y - PY[av], cZ = Z - PZ[av];
+          bool ok = true;
+          int64_t idx[4];
+          bool inner[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int VX = cX + PX[v], VY = cY + PY[v], VZ = cZ + PZ[v];
+            ok = ok && kuhn_inside(n, VX, VY, VZ);
+            idx[v] = ok ? lattice_index(n, VX - VY, VY - VZ, VZ) : 0;
+            inner[v] = kuhn_interior(n, VX, VY, VZ);
+          }
+          if (ok) {
+            const T kb = (T)0.25 * (pk[idx[0]] + pk[idx[1]] + pk[idx[2]] + pk[idx[3]]);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              if (v == av) continue;
+              if (!fl.practical && inner[v]) continue;
+              const T* K = C.ke[p][av][v];
+              const T ddx = px[idx[v]] - x0, ddy = px[idx[v] + E] - y0, ddz = px[idx[v] + 2 * E] - z0;
+              ax += kb * (K[0] * ddx + K[1] * ddy + K[2] * ddz);
+              ay += kb * (K[3] * ddx + K[4] * ddy + K[5] * ddz);
+              az += kb * (K[6] * ddx + K[7] * ddy + K[8] * ddz);
+              dgx -= kb * K[0];
+              dgy -= kb * K[4];
+              dgz -= kb * K[8];
+            }
+          }
+        }
+        if (!fl.practical && lane < NDIR) {
+          // scaled block towards a macro-interior neighbour in direction d = lane
+          const int d = lane;
+          const int qi = I.i + dir_di(d), qj = I.j + dir_dj(d), qk = I.k + dir_dk(d);
+          if (lattice_interior(n, qi, qj, qk)) {
+            const T k0 = pk[lattice_index(n, I.i, I.j, I.k)];
+            const int64_t qe = lattice_index(n, qi, qj, qk);
+            T rs = 0, wx = 0, wy = 0, wz = 0;
+            for (int c = 0; c < ring_count(d); ++c) {
+              const int ra = ring_a(d, c), rb = ring_b(d, c);
+              const T ka = pk[lattice_index(n, I.i + dir_di(ra), I.j + dir_dj(ra), I.k + dir_dk(ra))];
+              const T kb = pk[lattice_index(n, I.i + dir_di(rb), I.j + dir_dj(rb), I.k + dir_dk(rb))];
+              rs += ka + kb;
+              const T dk = ka - kb;
+              wx += dk * C.st.s[d][c][0];
+              wy += dk * C.st.s[d][c][1];
+              wz += dk * C.st.s[d][c][2];
+            }
+            const T kq = pk[qe];
+            const T kh = fl.khat_edge ? (T)0.5 * (k0 + kq)
+                                      : (T)0.25 * (k0 + kq) + (dir_red(d) ? (T)(1.0 / 12.0) : (T)0.125) * rs;
+            const T* S = C.st.S[d < 7 ? d : d - 7];
+            const T ddx = px[qe] - x0, ddy = px[qe + E] - y0, ddz = px[qe + 2 * E] - z0;
+            ax += kh * (S[0] * ddx + S[3] * ddy + S[4] * ddz);
+            ay += kh * (S[3] * ddx + S[1] * ddy + S[5] * ddz);
+            az += kh * (S[4] * ddx + S[5] * ddy + S[2] * ddz);
+            if (fl.physical) {
+              ax += wy * ddz - wz * ddy;
+              ay += wz * ddx - wx * ddz;
+              az += wx * ddy - wy * ddx;
+            }
+            dgx -= kh * S[0];
+            dgy -= kh * S[1];
+            dgz -= kh * S[2];
+          }
+        }
+      }
+      // sum over the warp (same order on every lane: all lanes get identical sums)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+        dgx += __shfl_xor_sync(0xffffffffu, dgx, o);
+        dgy += __shfl_xor_sync(0xffffffffu, dgy, o);
+        dgz += __shfl_xor_sync(0xffffffffu, dgz, o);
+      }
+      for (int q = b0 + lane; q < b1; q += 32) {
+        const SkelInc I = L.skel_inc[q];
+        const int64_t e = (int64_t)I.macro * L.nt + lattice_index(n, I.i, I.j, I.k);
+        double tmp = 0.0;
+        epilogue<T, OP>(a, e, E, ax, ay, az, dgx, dgy, dgz, x0, y0, z0, tmp);
+        if (q == b0) r2 = tmp;
+      }
+    }
+  }
+  if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
+}
+
+}  // namespace
+
+template <typename T>
+int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev, OpKind op,
+                 const OpFlags& fl, const SweepArgs<T>& a, void* stream, int parts, int64_t partial_offset,
+                 int64_t* partial_count) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const dim3 blk(TILE_I, TILE_J);
+  int64_t used = partial_offset;
+  for (int m = 0; m < L.nmacro && (parts & 1); ++m) {
+    if (L.ntiles_int == 0) break;
+    SweepArgs<T> am = a;
+    if (a.partial) am.partial = a.partial + used;
+    switch (op) {
+      case OP_APPLY: k_interior<T, OP_APPLY><<<L.ntiles_int, blk, 0, s>>>(L, st_host[m], m, fl, am); break;
+      case OP_RESID: k_interior<T, OP_RESID><<<L.ntiles_int, blk, 0, s>>>(L, st_host[m], m, fl, am); break;
+      case OP_JACOBI: k_interior<T, OP_JACOBI><<<L.ntiles_int, blk, 0, s>>>(L, st_host[m], m, fl, am); break;
+      case OP_CHEBY: k_interior<T, OP_CHEBY><<<L.ntiles_int, blk, 0, s>>>(L, st_host[m], m, fl, am); break;
+    }
+    used += L.ntiles_int;
+  }
+  if (L.nskel > 0 && (parts & 2)) {
+    const int nb = (L.nskel + 3) / 4;
+    SweepArgs<T> am = a;
+    if (a.partial) am.partial = a.partial + used;
+    switch (op) {
+      case OP_APPLY: k_skeleton<T, OP_APPLY><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
+      case OP_RESID: k_skeleton<T, OP_RESID><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
+      case OP_JACOBI: k_skeleton<T, OP_JACOBI><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
+      case OP_CHEBY: k_skeleton<T, OP_CHEBY><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
+    }
+    used += nb;
+  }
+  if (partial_count) *partial_count = used - partial_offset;
+  return (int)cudaGetLastError();
+}
+
+template int launch_sweep<float>(const LevelDev&, const MacroStencil<float>*, const MacroConsts<float>*, OpKind,
+                                 const OpFlags&, const SweepArgs<float>&, void*, int, int64_t, int64_t*);
+template int launch_sweep<double>(const LevelDev&, const MacroStencil<double>*, const MacroConsts<double>*, OpKind,
+                                  const OpFlags&, const SweepArgs<double>&, void*, int, int64_t, int64_t*);
+
+}  // namespace hhg

@@ -1,0 +1,254 @@
+// Reductions, multigrid transfers and vector kernels on the HHG lattice layout.
+//
+// Transfers (Sec. 5: matrix-free linear interpolation and its transpose):
+// a fine lattice point q either coincides with the coarse point q/2 or is the
+// midpoint of the coarse edge (q - d, q + d)/2, where d is the stencil
+// direction whose Kuhn coordinates are the parities (X mod 2, Y mod 2, Z mod 2)
+// of q.  Prolongation takes 1 resp. 1/2 of the parents; restriction is the
+// exact transpose: coarse point p collects r(2p) + 1/2 sum_d r(2p + d).
+#include <cuda_runtime.h>
+
+#include "hhg_internal.h"
+#include "hhg_launch.h"
+
+namespace hhg {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void block_store(double v, double* out) {
+  __shared__ double red[32];
+  v = warp_sum(v);
+  const int tid = threadIdx.x;
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  if (tid < 32) {
+    double s = tid < (int)((blockDim.x + 31) / 32) ? red[tid] : 0.0;
+    s = warp_sum(s);
+    if (tid == 0) *out = s;
+  }
+}
+
+__global__ void k_reduce(const double* __restrict__ p, int64_t count, double* out) {
+  double v = 0.0;
+  for (int64_t q = threadIdx.x; q < count; q += blockDim.x) v += p[q];
+  block_store(v, out);
+}
+
+template <typename T>
+__global__ void k_dot(const uint8_t* __restrict__ mask, int64_t E, int comps, const T* __restrict__ a,
+                      const T* __restrict__ b, double* partials) {
+  double v = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    if (mask[e]) {
+      for (int c = 0; c < comps; ++c) v += (double)a[e + c * E] * (double)b[e + c * E];
+    }
+  }
+  block_store(v, partials + blockIdx.x);
+}
+
+// fine point (i, j, k) of macro `m` of the fine level; adds P e_c
+template <typename T>
+__global__ void k_prolong_add(const LevelDev Lf, const LevelDev Lc, const T* __restrict__ ec, T* __restrict__ ef) {
+  const int m = blockIdx.y;
+  const int32_t tile = Lf.tiles_all[blockIdx.x];
+  const int k = tile >> 20;
+  const int j = ((tile >> 10) & 1023) + threadIdx.y;
+  const int i = (tile & 1023) + threadIdx.x;
+  const int n = Lf.n, nc = Lc.n;
+  if (i + j + k > n) return;
+  const int X = i + j + k, Y = j + k, Z = k;
+  const int pX = X & 1, pY = Y & 1, pZ = Z & 1;
+  const int64_t ef0 = (int64_t)m * Lf.nt + lattice_index(n, i, j, k);
+  const int64_t cb = (int64_t)m * Lc.nt;
+  if (!(pX | pY | pZ)) {
+    const int64_t c = cb + lattice_index(nc, i >> 1, j >> 1, k >> 1);
+    for (int q = 0; q < 3; ++q) ef[ef0 + q * Lf.entries] += ec[c + q * Lc.entries];
+  } else {
+    const int di = pX - pY, dj = pY - pZ, dk = pZ;
+    const int64_t ca = cb + lattice_index(nc, (i - di) >> 1, (j - dj) >> 1, (k - dk) >> 1);
+    const int64_t cc = cb + lattice_index(nc, (i + di) >> 1, (j + dj) >> 1, (k + dk) >> 1);
+    for (int q = 0; q < 3; ++q)
+      ef[ef0 + q * Lf.entries] += (T)0.5 * (ec[ca + q * Lc.entries] + ec[cc + q * Lc.entries]);
+  }
+}
+
+// coarse macro-interior points: rc(p) = rf(2p) + 1/2 sum_d rf(2p + d)
+template <typename T>
+__global__ void k_restrict_interior(const LevelDev Lf, const LevelDev Lc, const T* __restrict__ rf,
+                                    T* __restrict__ rc) {
+  const int m = blockIdx.y;
+  const int32_t tile = Lc.tiles_int[blockIdx.x];
+  const int k = tile >> 20;
+  const int j = ((tile >> 10) & 1023) + threadIdx.y;
+  const int i = (tile & 1023) + threadIdx.x;
+  const int n = Lf.n, nc = Lc.n;
+  if (i + j + k > nc - 1) return;
+  const int64_t fb = (int64_t)m * Lf.nt;
+  const int64_t c = (int64_t)m * Lc.nt + lattice_index(nc, i, j, k);
+  const int64_t f0 = fb + lattice_index(n, 2 * i, 2 * j, 2 * k);
+  for (int q = 0; q < 3; ++q) {
+    const T* r = rf + q * Lf.entries;
+    T s = 0;
+#pragma unroll
+    for (int d = 0; d < NDIR; ++d) s += r[fb + lattice_index(n, 2 * i + dir_di(d), 2 * j + dir_dj(d), 2 * k + dir_dk(d))];
+    rc[c + q * Lc.entries] = r[f0] + (T)0.5 * s;
+  }
+}
+
+// coarse skeleton points: precomputed list of unique fine points and weights
+template <typename T>
+__global__ void k_restrict_skeleton(const LevelDev Lc, const int32_t* __restrict__ rptr,
+                                    const int64_t* __restrict__ rent, const T* __restrict__ rw, int64_t Ef,
+                                    const T* __restrict__ rf, T* __restrict__ rc) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= Lc.nskel) return;
+  T acc[3] = {0, 0, 0};
+  if (!Lc.skel_dir[s]) {
+    for (int q = rptr[s]; q < rptr[s + 1]; ++q) {
+      const int64_t e = rent[q];
+      const T w = rw[q];
+      for (int c = 0; c < 3; ++c) acc[c] += w * rf[e + c * Ef];
+    }
+  }
+  for (int q = Lc.skel_ptr[s]; q < Lc.skel_ptr[s + 1]; ++q) {
+    const SkelInc I = Lc.skel_inc[q];
+    const int64_t e = (int64_t)I.macro * Lc.nt + lattice_index(Lc.n, I.i, I.j, I.k);
+    for (int c = 0; c < 3; ++c) rc[e + c * Lc.entries] = acc[c];
+  }
+}
+
+// coefficient injection: coarse points are fine points
+template <typename T>
+__global__ void k_inject(const LevelDev Lf, const LevelDev Lc, const T* __restrict__ kf, T* __restrict__ kc) {
+  const int m = blockIdx.y;
+  const int32_t tile = Lc.tiles_all[blockIdx.x];
+  const int k = tile >> 20;
+  const int j = ((tile >> 10) & 1023) + threadIdx.y;
+  const int i = (tile & 1023) + threadIdx.x;
+  if (i + j + k > Lc.n) return;
+  kc[(int64_t)m * Lc.nt + lattice_index(Lc.n, i, j, k)] =
+      kf[(int64_t)m * Lf.nt + lattice_index(Lf.n, 2 * i, 2 * j, 2 * k)];
+}
+
+template <typename T>
+__global__ void k_axpby(int64_t n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = a * x[e] + b * y[e];
+}
+
+template <typename T, typename U>
+__global__ void k_convert(int64_t n, const T* __restrict__ s, U* __restrict__ d) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = (U)s[e];
+}
+
+template <typename T>
+__global__ void k_gather(int64_t count, int comps, int64_t ss, int64_t ds, const int64_t* __restrict__ idx,
+                         const T* __restrict__ src, T* __restrict__ dst) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < count; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = idx[u];
+    for (int c = 0; c < comps; ++c) dst[c * ds + u] = src[c * ss + e];
+  }
+}
+
+template <typename T>
+__global__ void k_fill(int64_t n, T v, T* __restrict__ d) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = v;
+}
+
+inline int grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+int launch_reduce(const double* partials, int64_t count, double* out, void* stream) {
+  k_reduce<<<1, 1024, 0, (cudaStream_t)stream>>>(partials, count, out);
+  return (int)cudaGetLastError();
+}
+
+constexpr int DOT_BLOCKS = 1024;
+
+template <typename T>
+int launch_dot(const LevelDev& L, int comps, const T* a, const T* b, double* partials, int64_t* partial_count,
+               void* stream) {
+  k_dot<T><<<DOT_BLOCKS, 256, 0, (cudaStream_t)stream>>>(L.mask, L.entries, comps, a, b, partials);
+  *partial_count = DOT_BLOCKS;
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_prolong_add(const LevelDev& Lf, const LevelDev& Lc, const T* ec, T* ef, void* stream) {
+  dim3 grid(Lf.ntiles_all, Lf.nmacro);
+  k_prolong_add<T><<<grid, dim3(TILE_I, TILE_J), 0, (cudaStream_t)stream>>>(Lf, Lc, ec, ef);
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const int32_t* rptr, const int64_t* rent, const T* rw,
+                    const T* rf, T* rc, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (Lc.ntiles_int > 0) {
+    dim3 grid(Lc.ntiles_int, Lc.nmacro);
+    k_restrict_interior<T><<<grid, dim3(TILE_I, TILE_J), 0, s>>>(Lf, Lc, rf, rc);
+  }
+  if (Lc.nskel > 0) k_restrict_skeleton<T><<<(Lc.nskel + 127) / 128, 128, 0, s>>>(Lc, rptr, rent, rw, Lf.entries, rf, rc);
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_inject(const LevelDev& Lf, const LevelDev& Lc, const T* kf, T* kc, void* stream) {
+  dim3 grid(Lc.ntiles_all, Lc.nmacro);
+  k_inject<T><<<grid, dim3(TILE_I, TILE_J), 0, (cudaStream_t)stream>>>(Lf, Lc, kf, kc);
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_axpby(int64_t n, T a, const T* x, T b, T* y, void* stream) {
+  k_axpby<T><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(n, a, x, b, y);
+  return (int)cudaGetLastError();
+}
+
+template <typename T, typename U>
+int launch_convert(int64_t n, const T* src, U* dst, void* stream) {
+  k_convert<T, U><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(n, src, dst);
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_gather(int64_t count, int comps, int64_t ss, int64_t ds, const int64_t* idx, const T* src, T* dst,
+                  void* stream) {
+  k_gather<T><<<grid_for(count, 256), 256, 0, (cudaStream_t)stream>>>(count, comps, ss, ds, idx, src, dst);
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_fill(int64_t n, T v, T* dst, void* stream) {
+  k_fill<T><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(n, v, dst);
+  return (int)cudaGetLastError();
+}
+
+#define HHG_INST(T)                                                                                              \
+  template int launch_dot<T>(const LevelDev&, int, const T*, const T*, double*, int64_t*, void*);               \
+  template int launch_prolong_add<T>(const LevelDev&, const LevelDev&, const T*, T*, void*);                     \
+  template int launch_restrict<T>(const LevelDev&, const LevelDev&, const int32_t*, const int64_t*, const T*,   \
+                                  const T*, T*, void*);                                                          \
+  template int launch_inject<T>(const LevelDev&, const LevelDev&, const T*, T*, void*);                          \
+  template int launch_axpby<T>(int64_t, T, const T*, T, T*, void*);                                              \
+  template int launch_gather<T>(int64_t, int, int64_t, int64_t, const int64_t*, const T*, T*, void*);            \
+  template int launch_fill<T>(int64_t, T, T*, void*);
+HHG_INST(float)
+HHG_INST(double)
+template int launch_convert<double, float>(int64_t, const double*, float*, void*);
+template int launch_convert<float, double>(int64_t, const float*, double*, void*);
+
+}  // namespace hhg

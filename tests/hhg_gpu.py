@@ -1,0 +1,64 @@
+"""Helpers for the GPU tests: set up a libhhgs context and move fields between the library
+layout (entries, component-major) and unique-node order, all through the C ABI."""
+
+import numpy as np
+
+from paper_1908_08666_gb300 import binding as B
+
+
+def torch_cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        import pytest
+
+        pytest.skip("no CUDA device")
+    return torch
+
+
+class Ctx:
+    def __init__(self, xyz, tets, level, problem=None, dirichlet_face_flags=None):
+        self.torch = torch_cuda()
+        self.stream = self.torch.cuda.current_stream().cuda_stream
+        self.h = B.hhg_create(0, self.stream)
+        B.hhg_set_macro_mesh(self.h, xyz, tets, dirichlet_face_flags)
+        B.hhg_refine(self.h, level)
+        B.hhg_set_problem(self.h, **(problem or {}))
+        self.level = level
+        self.E, self.U, self.F = B.hhg_num_nodes(self.h, level)
+        self.coords_e = B.hhg_entry_coords(self.h, level)
+        self.e2u, self.udir = B.hhg_entry_to_unique(self.h, level)
+        first = np.full(self.U, -1, dtype=np.int64)
+        first[self.e2u[::-1]] = np.arange(self.E)[::-1]
+        self.coords_u = self.coords_e[first]
+
+    def close(self):
+        if self.h:
+            B.hhg_destroy(self.h)
+            self.h = None
+
+    def dev(self, a, dtype):
+        t = self.torch
+        return t.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+    def to_lib(self, unique_vals, dtype, comps):
+        """(U, comps) or (U,) host array in unique order -> device field in library layout."""
+        t = self.torch
+        u = np.asarray(unique_vals, dtype=np.float64).reshape(self.U, comps).T.copy()  # comp-major
+        src = self.dev(u.reshape(-1), dtype)
+        dst = t.empty(comps * self.E, dtype=dtype, device="cuda")
+        B.hhg_scatter_unique(self.h, self.level, B.F64 if dtype == t.float64 else B.F32, comps, src, dst)
+        return dst
+
+    def from_lib(self, field, comps):
+        t = self.torch
+        dst = t.empty(comps * self.U, dtype=field.dtype, device="cuda")
+        B.hhg_gather_unique(self.h, self.level, B.F64 if field.dtype == t.float64 else B.F32, comps, field, dst)
+        t.cuda.synchronize()
+        return dst.double().cpu().numpy().reshape(comps, self.U).T.copy()
+
+    def set_k(self, k_unique, dtype=None):
+        t = self.torch
+        kd = self.to_lib(k_unique, t.float64, 1)
+        B.hhg_set_coefficient(self.h, kd, B.F64)
+        t.cuda.synchronize()

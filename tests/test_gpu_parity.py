@@ -1,0 +1,173 @@
+"""Parity of the CUDA operator apply / residual against the FP64 CPU oracle, through the C ABI.
+
+Tolerances (stated here, derived in the design doc):
+  FP64: max |y_gpu - y_oracle| / max |y_oracle| <= 1e-12.
+  FP32: per row, |y32 - y_oracle|_i <= 64 * 2^-24 * sum_j |A_ij| |x_j - x_i|  (the scale of the
+        row's terms in the difference form the kernels evaluate), on free rows; Dirichlet rows
+        return x rounded to FP32.
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import hhg_inputs as hi
+from oracle import fem, mesh, operators as op, rows
+from paper_1908_08666_gb300 import binding as B
+
+from hhg_gpu import Ctx
+
+pytestmark = pytest.mark.gpu
+
+FP32_C = 64 * 2.0**-24
+
+
+def _oracle(xyz, tets, level, kfun, variant="physical", khat="patch", iface="symmetric", nu=0.3):
+    mm = mesh.MacroMesh.build(xyz, tets)
+    lv = mesh.build_level(mm, level)
+    ce, cd = fem.elasticity_coefficients(nu)
+    K = fem.element_stiffness(lv.coords[lv.elems], ce, cd)
+    A = op.scaled_operator(lv, K, kfun(lv.coords), variant, khat=khat, iface=iface)
+    return mm, lv, A
+
+
+def _kfun(c):
+    return 1.0 + 0.5 * np.sin(2 * np.pi * c[:, 0]) * np.sin(2 * np.pi * c[:, 1]) * np.sin(2 * np.pi * c[:, 2]) \
+        + 0.3 * c[:, 2]
+
+
+def _fp32_scale(A, x, lv):
+    """sum_j |A_ij| |x_j - x_i| per node (3 components)."""
+    N = lv.num_nodes
+    Ac = A.tocoo()
+    ni, nj = Ac.row // 3, Ac.col // 3
+    diff = np.abs(x.reshape(-1)[Ac.col] - x.reshape(N, 3)[ni, Ac.col % 3])
+    s = np.zeros(3 * N)
+    np.add.at(s, Ac.row, np.abs(Ac.data) * diff)
+    return s.reshape(N, 3)
+
+
+CASES = [
+    ("unit_tet_l5", hi.unit_tet, 5, {}),
+    ("cube_l4", hi.kuhn_cube, 4, {}),
+    ("cube_l4_unphysical", hi.kuhn_cube, 4, {"variant": "unphysical"}),
+    ("cube_l4_khat_edge", hi.kuhn_cube, 4, {"khat": "edge"}),
+    ("cube_l4_practical", hi.kuhn_cube, 4, {"iface": "practical"}),
+    ("skewed_l4", hi.skewed_pair, 4, {}),
+    ("cube2_l3", lambda: hi.kuhn_cube(2), 3, {}),
+]
+
+_VAR = {"physical": B.PHYSICAL, "unphysical": B.UNPHYSICAL}
+_KH = {"patch": B.KHAT_PATCH, "edge": B.KHAT_EDGE}
+_IF = {"symmetric": B.IFACE_SYMMETRIC, "practical": B.IFACE_PRACTICAL}
+
+
+@pytest.mark.parametrize("name,builder,level,opt", CASES, ids=[c[0] for c in CASES])
+def test_apply_and_residual_parity(name, builder, level, opt):
+    xyz, tets = builder()
+    variant = opt.get("variant", "physical")
+    khat = opt.get("khat", "patch")
+    iface = opt.get("iface", "symmetric")
+    mm, lv, A = _oracle(xyz, tets, level, _kfun, variant, khat, iface)
+    A_bc = op.with_dirichlet_rows(A, lv.dirichlet)
+    ctx = Ctx(xyz, tets, level, dict(nu=0.3, variant=_VAR[variant], khat=_KH[khat], iface=_IF[iface]))
+    try:
+        t = ctx.torch
+        perm = mesh.match_nodes(lv.coords, ctx.coords_u)  # oracle node i == gpu unique node perm[i]
+        assert np.array_equal(ctx.udir[perm], lv.dirichlet)
+        ctx.set_k(_kfun(ctx.coords_u))
+        x_or = hi.node_noise(lv.coords, seed=7)
+        f_or = hi.node_noise(lv.coords, seed=8)
+        x_u = np.empty_like(x_or)
+        x_u[perm] = x_or
+        f_u = np.empty_like(f_or)
+        f_u[perm] = f_or
+        y_or = op.apply(A_bc, x_or)
+        r_or = op.residual(A, f_or, x_or, lv.dirichlet)
+        scale = _fp32_scale(A, x_or, lv)
+        free = ~lv.dirichlet
+        for dt, tdt in ((B.F64, t.float64), (B.F32, t.float32)):
+            x = ctx.to_lib(x_u, tdt, 3)
+            f = ctx.to_lib(f_u, tdt, 3)
+            y = t.empty_like(x)
+            r = t.empty_like(x)
+            B.hhg_apply(ctx.h, level, dt, x, y)
+            nrm = B.hhg_residual(ctx.h, level, dt, f, x, r, want_norm=True)
+            yg = ctx.from_lib(y, 3)[perm]
+            rg = ctx.from_lib(r, 3)[perm]
+            if dt == B.F64:
+                assert np.abs(yg - y_or).max() <= 1e-12 * np.abs(y_or).max()
+                assert np.abs(rg - r_or).max() <= 1e-12 * np.abs(r_or).max()
+                assert abs(nrm - (r_or[free] ** 2).sum()) <= 1e-11 * (r_or[free] ** 2).sum()
+            else:
+                assert np.all(np.abs(yg - y_or)[free] <= FP32_C * scale[free] + 1e-30)
+                assert np.all(np.abs(rg - r_or)[free] <= FP32_C * (scale[free] + np.abs(f_or[free])) + 1e-30)
+                assert np.abs(yg - y_or)[~free].max(initial=0) <= 2**-24 * np.abs(x_or).max()
+                assert np.all(rg[~free] == 0)
+                assert abs(nrm - (r_or[free] ** 2).sum()) <= 1e-4 * (r_or[free] ** 2).sum()
+            # every copy of a skeleton node holds the same value
+            full = y.double().cpu().numpy().reshape(3, ctx.E).T
+            assert np.array_equal(full, ctx.from_lib(y, 3)[ctx.e2u])
+    finally:
+        ctx.close()
+
+
+def test_full_size_sampled_rows_cube_level7():
+    """The 6-macro cube at level 7 (129^3 nodes), the launch configuration of the benchmark:
+    sampled interior, face, edge and vertex rows against the single-row oracle (FP64 exact to
+    1e-12 of the row scale, FP32 within the stated bound)."""
+    xyz, tets = hi.kuhn_cube(1)
+    level = 7
+    ctx = Ctx(xyz, tets, level, dict(nu=0.3))
+    try:
+        t = ctx.torch
+        grid_k = hi.lognormal_grid(1 << level, seed=2)
+        kf = lambda c: hi.sample_grid(grid_k[..., None], c)[:, 0]
+        grid_x = hi.uniform_grid(1 << level, seed=3)
+        xf = lambda c: hi.sample_grid(grid_x, c)
+        ctx.set_k(kf(ctx.coords_u))
+        xu = xf(ctx.coords_u)
+        ce, cd = fem.elasticity_coefficients(0.3)
+        mm = mesh.MacroMesh.build(xyz, tets)
+        rng = np.random.default_rng(0)
+        # pick rows: random interior entries + skeleton nodes of each kind
+        pick = list(rng.choice(ctx.U, 24, replace=False))
+        nodes_per_inc = np.bincount(ctx.e2u, minlength=ctx.U)
+        for cnt in np.unique(nodes_per_inc):
+            cand = np.nonzero((nodes_per_inc == cnt) & ~ctx.udir)[0]
+            if len(cand):
+                pick += list(rng.choice(cand, min(3, len(cand)), replace=False))
+        first = np.full(ctx.U, -1, dtype=np.int64)
+        first[ctx.e2u[::-1]] = np.arange(ctx.E)[::-1]
+        for dt, tdt in ((B.F64, t.float64), (B.F32, t.float32)):
+            x = ctx.to_lib(xu, tdt, 3)
+            y = t.empty_like(x)
+            B.hhg_apply(ctx.h, level, dt, x, y)
+            yg = ctx.from_lib(y, 3)
+            for u in pick:
+                u = int(u)
+                if ctx.udir[u]:
+                    continue
+                e = first[u]
+                nt = (ctx.E // 6)
+                m, loc = divmod(e, nt)
+                ijk = _decode(1 << level, loc)
+                yr, _ = rows.row(mm, level, m, ijk, kf, xf, ce, cd)
+                tol = 1e-12 * (np.abs(yr).max() + 1e-3) if dt == B.F64 else 2e-4 * (np.abs(yr).max() + 1e-3)
+                assert np.abs(yg[u] - yr).max() <= tol, (u, yg[u], yr)
+    finally:
+        ctx.close()
+
+
+def _decode(n, loc):
+    for k in range(n + 1):
+        m = n - k
+        sz = (m + 1) * (m + 2) // 2
+        if loc < sz:
+            for j in range(m + 1):
+                L = m - j + 1
+                if loc < L:
+                    return (loc, j, k)
+                loc -= L
+        loc -= sz
+    raise ValueError
