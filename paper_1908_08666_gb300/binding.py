@@ -196,3 +196,4 @@ def hhg_profile(ctx, enable, read=False):
         return ms, nl
     _check(ctx, load().hhg_profile(ctx, int(enable), None, None))
     return None
+

@@ -320,7 +320,11 @@ struct LevelHost {
   std::vector<int32_t> skel_ptr;
   std::vector<SkelInc> skel_inc;
   std::vector<int8_t> skel_dir;
+  std::vector<int8_t> skel_support;  // number of macro vertices spanning the node's primitive
   std::vector<std::array<int64_t, 3>> skel_key;
+  std::vector<FaceItem> face_items;
+  std::vector<int32_t> face_nodes, ev_nodes, dir_nodes;
+  uint32_t face_mask[4] = {0, 0, 0, 0};
   std::vector<uint8_t> mask;
   std::vector<int64_t> entry_to_unique, unique_first;
   std::vector<int8_t> unique_dir;
@@ -331,6 +335,7 @@ struct LevelHost {
   std::vector<double> rw;
   // device
   DevMem d_tiles_int, d_tiles_all, d_skel_ptr, d_skel_inc, d_skel_dir, d_mask, d_first, d_e2u;
+  DevMem d_face_items, d_face_nodes, d_ev_nodes, d_dir_nodes, d_acc32, d_acc64;
   DevMem d_rptr, d_rent, d_rw64, d_rw32;
   DevMem d_mc64, d_mc32;
   DevMem d_k64, d_k32;
@@ -450,6 +455,7 @@ void build_level(hhg_ctx* c, int level) {
               dir = c->dir_verts.count(kv[0].first) > 0;
             }
             L->skel_dir.push_back(dir ? 1 : 0);
+            L->skel_support.push_back((int8_t)kv.size());
           } else {
             sid = it->second;
           }
@@ -493,6 +499,62 @@ void build_level(hhg_ctx* c, int level) {
   }
   L->nfree = L->nunique;
   for (int64_t s = 0; s < nskel; ++s) L->nfree -= L->skel_dir[s];
+  // skeleton split for the kernels
+  for (int64_t s = 0; s < nskel; ++s) {
+    if (L->skel_dir[s]) {
+      L->dir_nodes.push_back((int32_t)s);
+    } else if (L->skel_support[s] == 3) {
+      const int32_t fid = (int32_t)L->face_nodes.size();
+      L->face_nodes.push_back((int32_t)s);
+      for (int q = L->skel_ptr[s]; q < L->skel_ptr[s + 1]; ++q) {
+        const SkelInc& I = L->skel_inc[q];
+        const int w[4] = {n - I.i - I.j - I.k, I.i, I.j, I.k};
+        int f = -1, zeros = 0;
+        for (int c = 0; c < 4; ++c)
+          if (w[c] == 0) {
+            f = c;
+            ++zeros;
+          }
+        if (zeros != 1) THROW(HHG_ERR_STATE, "face node with %d zero barycentric weights", zeros);
+        FaceItem it;
+        it.macro = I.macro;
+        it.node = fid;
+        it.i = I.i;
+        it.j = I.j;
+        it.k = I.k;
+        it.f = (int16_t)f;
+        L->face_items.push_back(it);
+      }
+    } else {
+      L->ev_nodes.push_back((int32_t)s);
+    }
+  }
+  // candidate elements around a face-interior point that lie inside the macro (per face
+  // type); checked against every face item of this level
+  auto cand_inside = [](int nn, int i, int j, int k, int bit) {
+    const int p = bit >> 2, av = bit & 3;
+    int P[4][3];
+    kuhn_vertices(p, P);
+    const int X = i + j + k, Y = j + k, Z = k;
+    for (int v = 0; v < 4; ++v) {
+      const int VX = X - P[av][0] + P[v][0], VY = Y - P[av][1] + P[v][1], VZ = Z - P[av][2] + P[v][2];
+      if (!(0 <= VZ && VZ <= VY && VY <= VX && VX <= nn)) return false;
+    }
+    return true;
+  };
+  {
+    const int nn = 16;
+    const int rep[4][3] = {{5, 5, 6}, {0, 5, 5}, {5, 0, 5}, {5, 5, 0}};
+    for (int f = 0; f < 4; ++f) {
+      L->face_mask[f] = 0;
+      for (int bit = 0; bit < 24; ++bit)
+        if (cand_inside(nn, rep[f][0], rep[f][1], rep[f][2], bit)) L->face_mask[f] |= 1u << bit;
+    }
+    for (const FaceItem& it : L->face_items)
+      for (int bit = 0; bit < 24; ++bit)
+        if (cand_inside(n, it.i, it.j, it.k, bit) != (((L->face_mask[it.f] >> bit) & 1u) != 0))
+          THROW(HHG_ERR_STATE, "face candidate mask mismatch");
+  }
   for (int64_t e = 0; e < L->entries; ++e)
     if (L->entry_to_unique[e] < 0) THROW(HHG_ERR_STATE, "entry without node");
   c->levels[level] = std::move(L);
@@ -539,6 +601,14 @@ void upload_level(hhg_ctx* c, LevelHost& L) {
   upload(L.d_skel_inc, L.skel_inc);
   upload(L.d_skel_dir, L.skel_dir);
   upload(L.d_mask, L.mask);
+  upload(L.d_face_items, L.face_items);
+  upload(L.d_face_nodes, L.face_nodes);
+  upload(L.d_ev_nodes, L.ev_nodes);
+  upload(L.d_dir_nodes, L.dir_nodes);
+  CK(L.d_acc32.alloc(std::max<size_t>(1, L.face_nodes.size()) * 6 * sizeof(float)));
+  CK(L.d_acc64.alloc(std::max<size_t>(1, L.face_nodes.size()) * 6 * sizeof(double)));
+  CK(cudaMemset(L.d_acc32.p, 0, L.d_acc32.bytes));
+  CK(cudaMemset(L.d_acc64.p, 0, L.d_acc64.bytes));
   upload(L.d_first, L.unique_first);
   upload(L.d_e2u, L.entry_to_unique);
   if (!L.rptr.empty()) {
@@ -564,13 +634,25 @@ void upload_level(hhg_ctx* c, LevelHost& L) {
   D.skel_inc = L.d_skel_inc.as<SkelInc>();
   D.skel_dir = L.d_skel_dir.as<int8_t>();
   D.mask = L.d_mask.as<uint8_t>();
+  D.nface_items = (int32_t)L.face_items.size();
+  D.nface_nodes = (int32_t)L.face_nodes.size();
+  D.nev = (int32_t)L.ev_nodes.size();
+  D.ndir = (int32_t)L.dir_nodes.size();
+  D.face_items = L.d_face_items.as<FaceItem>();
+  D.face_nodes = L.d_face_nodes.as<int32_t>();
+  D.ev_nodes = L.d_ev_nodes.as<int32_t>();
+  D.dir_nodes = L.d_dir_nodes.as<int32_t>();
+  for (int f = 0; f < 4; ++f) D.face_mask[f] = L.face_mask[f];
+  D.acc32 = L.d_acc32.as<float>();
+  D.acc64 = L.d_acc64.as<double>();
 }
 
 int64_t max_partials(hhg_ctx* c) {
   int64_t mx = 1024;
   for (int l = c->level_min; l <= c->level_max; ++l) {
     const LevelHost& L = *c->levels[l];
-    mx = std::max<int64_t>(mx, (int64_t)L.tiles_int.size() * (int64_t)c->tets.size() + (L.skel_dir.size() + 3) / 4 + 8);
+    mx = std::max<int64_t>(mx, (int64_t)L.tiles_int.size() * (int64_t)c->tets.size() + (L.face_nodes.size() + 127) / 128 +
+                                   L.ev_nodes.size() + 8);
   }
   return mx;
 }
@@ -677,7 +759,9 @@ void sweep(hhg_ctx* c, int level, OpKind op, SweepArgs<T> a, double* norm2) {
       CK(cudaEventRecord(pr[1], c->stream));
       off += used;
       c->prof_ev[part].push_back(pr);
-      c->prof_launches[part] += part == 0 ? (L.dev.ntiles_int > 0 ? L.dev.nmacro : 0) : (L.dev.nskel > 0 ? 1 : 0);
+      c->prof_launches[part] += part == 0 ? (L.dev.ntiles_int > 0 ? L.dev.nmacro : 0)
+                                          : (L.dev.nface_items > 0) + (L.dev.nface_nodes > 0) + (L.dev.nev > 0) +
+                                                (L.dev.ndir > 0);
     }
     np = off;
   }
@@ -711,6 +795,7 @@ hhg_status hhg_create(hhg_ctx** out, int device, void* stream) {
   hhg_status st = guard(c, [&] {
     CK(c->scalar.alloc(64 * sizeof(double)));
     CK(cudaMallocHost((void**)&c->pinned, 64 * sizeof(double)));
+    CK(upload_direction_tables());
   });
   if (st != HHG_OK) {
     delete c;

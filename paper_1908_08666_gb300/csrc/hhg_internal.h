@@ -62,6 +62,12 @@ HHG_HD int64_t lattice_index(int n, int i, int j, int k) {
   const int64_t m = n - k;
   return tetnum(n + 1) - tetnum(n + 1 - k) + (int64_t)j * (2 * m + 3 - j) / 2 + i;
 }
+// 32-bit version for kernels (valid for n <= 1000)
+HHG_HD int lattice_index32(int n, int i, int j, int k) {
+  const int m = n - k;
+  const int a = n + 1, b = n + 1 - k;
+  return a * (a + 1) * (a + 2) / 6 - b * (b + 1) * (b + 2) / 6 + ((j * (2 * m + 3 - j)) >> 1) + i;
+}
 HHG_HD bool lattice_inside(int n, int i, int j, int k) { return i >= 0 && j >= 0 && k >= 0 && i + j + k <= n; }
 HHG_HD bool lattice_interior(int n, int i, int j, int k) {
   return i >= 1 && j >= 1 && k >= 1 && i + j + k <= n - 1;
@@ -105,6 +111,15 @@ struct SkelInc {
   int16_t pad;
 };
 
+// one incidence of a node on a macro face (face-interior node) in a macro;
+// f = which barycentric coordinate vanishes (0: i+j+k = n, 1: i = 0, 2: j = 0, 3: k = 0)
+struct FaceItem {
+  int32_t macro;
+  int32_t node;  // index into the face-node list
+  int16_t i, j, k;
+  int16_t f;
+};
+
 // device view of one level
 struct LevelDev {
   int n;
@@ -120,6 +135,16 @@ struct LevelDev {
   const SkelInc* skel_inc;   // incidences
   const int8_t* skel_dir;    // Dirichlet flag per skeleton node
   const uint8_t* mask;       // [entries] 1 = owned copy of a free node (dot products)
+  // skeleton split: free face-interior nodes (per-incidence items + accumulator),
+  // free edge/vertex nodes (warp kernel), Dirichlet nodes
+  int32_t nface_items, nface_nodes, nev, ndir;
+  const FaceItem* face_items;
+  const int32_t* face_nodes;  // skeleton id of each face node
+  const int32_t* ev_nodes;    // skeleton ids
+  const int32_t* dir_nodes;   // skeleton ids
+  uint32_t face_mask[4];      // candidate elements (bit 4p+av) inside the macro, per face type
+  float* acc32;               // [nface_nodes * 6] accumulators, zero between sweeps
+  double* acc64;
 };
 
 constexpr int TILE_I = 32;

@@ -39,6 +39,9 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
                  const OpFlags& fl, const SweepArgs<T>& a, void* stream, int parts, int64_t partial_offset,
                  int64_t* partial_count);
 
+// constant-memory direction tables of the skeleton kernels (once per device)
+int upload_direction_tables();
+
 // sum of partials[0..count) into out[0] (single block), deterministic
 int launch_reduce(const double* partials, int64_t count, double* out, void* stream);
 

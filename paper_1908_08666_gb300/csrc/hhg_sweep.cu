@@ -193,142 +193,340 @@ __device__ __forceinline__ bool kuhn_interior(int n, int X, int Y, int Z) {
   return 1 <= Z && Z < Y && Y < X && X <= n - 1;
 }
 
-// One warp per skeleton node.  Lanes 0..23 take the 24 candidate elements
-// (Kuhn permutation p = lane / 4, position of the node av = lane % 4) of each
-// incident macro, lanes 0..13 the 14 stencil directions; the row is summed
-// over the warp and written to every copy of the node.
-template <typename T, int OP>
-__global__ void __launch_bounds__(128) k_skeleton(const LevelDev L, const MacroConsts<T>* __restrict__ mc,
-                                                   const OpFlags fl, const SweepArgs<T> a) {
-  const int lane = threadIdx.x & 31;
-  const int s = blockIdx.x * 4 + (threadIdx.x >> 5);
-  double r2 = 0.0;
-  if (s < L.nskel) {
-    const int n = L.n;
-    const int64_t E = L.entries;
-    const int b0 = L.skel_ptr[s], b1 = L.skel_ptr[s + 1];
-    const SkelInc I0 = L.skel_inc[b0];
-    const int64_t e0 = (int64_t)I0.macro * L.nt + lattice_index(n, I0.i, I0.j, I0.k);
-    const T x0 = a.x[e0], y0 = a.x[e0 + E], z0 = a.x[e0 + 2 * E];
-    if (L.skel_dir[s]) {
-      for (int q = b0 + lane; q < b1; q += 32) {
-        const SkelInc I = L.skel_inc[q];
-        const int64_t e = (int64_t)I.macro * L.nt + lattice_index(n, I.i, I.j, I.k);
-        if (OP == OP_RESID) {
-          a.out[e] = 0;
-          a.out[e + E] = 0;
-          a.out[e + 2 * E] = 0;
-        } else {
-          a.out[e] = x0;
-          a.out[e + E] = y0;
-          a.out[e + 2 * E] = z0;
-          if (OP == OP_CHEBY) {
-            a.dout[e] = 0;
-            a.dout[e + E] = 0;
-            a.dout[e + 2 * E] = 0;
-          }
-        }
-      }
-    } else {
-      T ax = 0, ay = 0, az = 0, dgx = 0, dgy = 0, dgz = 0;
-      for (int q = b0; q < b1; ++q) {
-        const SkelInc I = L.skel_inc[q];
-        const MacroConsts<T>& C = mc[I.macro];
-        const int64_t base = (int64_t)I.macro * L.nt;
-        const T* px = a.x + base;
-        const T* pk = a.k + base;
-        const int X = I.i + I.j + I.k, Y = I.j + I.k, Z = I.k;
-        if (lane < 24) {
-          // a_h part: one candidate element of this macro around the node
-          const int p = lane >> 2, av = lane & 3;
-          int a0, a1, a2;
-          kuhn_perm(p, a0, a1, a2);
-          int PX[4] = {0, 0, 0, 1}, PY[4] = {0, 0, 0, 1}, PZ[4] = {0, 0, 0, 1};
-          PX[1] = a0 == 0; PY[1] = a0 == 1; PZ[1] = a0 == 2;
-          PX[2] = (a0 == 0) | (a1 == 0); PY[2] = (a0 == 1) | (a1 == 1); PZ[2] = (a0 == 2) | (a1 == 2);
-          const int cX = X - PX[av], cY = Y - PY[av], cZ = Z - PZ[av];
-          bool ok = true;
-          int64_t idx[4];
-          bool inner[4];
+// Contribution of one incident macro to the row of a skeleton node at corner
+// (i, j, k) of that macro: a_h terms over the candidate elements `cand` (bit
+// 4p+av: Kuhn permutation p, node at vertex av) for partner vertices on the
+// skeleton (every partner with the practical rule), and the scaled blocks of
+// the directions that end at a macro-interior node (symmetric rule).
+template <typename T>
+__device__ __forceinline__ void incidence_row(const MacroConsts<T>& C, const T* __restrict__ px,
+                                              const T* __restrict__ pk, int64_t E, int n, int i, int j, int k,
+                                              uint32_t cand, uint32_t dirs, T x0, T y0, T z0, const OpFlags& fl,
+                                              T& ax, T& ay, T& az, T& dgx, T& dgy, T& dgz) {
+  const int X = i + j + k, Y = j + k, Z = k;
+  // fully unrolled over the 24 candidates so that permutation, vertex offsets and
+  // stiffness offsets are compile-time constants
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int VX = cX + PX[v], VY = cY + PY[v], VZ = cZ + PZ[v];
-            ok = ok && kuhn_inside(n, VX, VY, VZ);
-            idx[v] = ok ? lattice_index(n, VX - VY, VY - VZ, VZ) : 0;
-            inner[v] = kuhn_interior(n, VX, VY, VZ);
-          }
-          if (ok) {
-            const T kb = (T)0.25 * (pk[idx[0]] + pk[idx[1]] + pk[idx[2]] + pk[idx[3]]);
+  for (int bit = 0; bit < 24; ++bit) {
+    if (!((cand >> bit) & 1u)) continue;
+    const int p = bit >> 2, av = bit & 3;
+    int a0, a1, a2;
+    kuhn_perm(p, a0, a1, a2);
+    int PX[4], PY[4], PZ[4];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              if (v == av) continue;
-              if (!fl.practical && inner[v]) continue;
-              const T* K = C.ke[p][av][v];
-              const T ddx = px[idx[v]] - x0, ddy = px[idx[v] + E] - y0, ddz = px[idx[v] + 2 * E] - z0;
-              ax += kb * (K[0] * ddx + K[1] * ddy + K[2] * ddz);
-              ay += kb * (K[3] * ddx + K[4] * ddy + K[5] * ddz);
-              az += kb * (K[6] * ddx + K[7] * ddy + K[8] * ddz);
-              dgx -= kb * K[0];
-              dgy -= kb * K[4];
-              dgz -= kb * K[8];
-            }
-          }
-        }
-        if (!fl.practical && lane < NDIR) {
-          // scaled block towards a macro-interior neighbour in direction d = lane
-          const int d = lane;
-          const int qi = I.i + dir_di(d), qj = I.j + dir_dj(d), qk = I.k + dir_dk(d);
-          if (lattice_interior(n, qi, qj, qk)) {
-            const T k0 = pk[lattice_index(n, I.i, I.j, I.k)];
-            const int64_t qe = lattice_index(n, qi, qj, qk);
-            T rs = 0, wx = 0, wy = 0, wz = 0;
-            for (int c = 0; c < ring_count(d); ++c) {
-              const int ra = ring_a(d, c), rb = ring_b(d, c);
-              const T ka = pk[lattice_index(n, I.i + dir_di(ra), I.j + dir_dj(ra), I.k + dir_dk(ra))];
-              const T kb = pk[lattice_index(n, I.i + dir_di(rb), I.j + dir_dj(rb), I.k + dir_dk(rb))];
-              rs += ka + kb;
-              const T dk = ka - kb;
-              wx += dk * C.st.s[d][c][0];
-              wy += dk * C.st.s[d][c][1];
-              wz += dk * C.st.s[d][c][2];
-            }
-            const T kq = pk[qe];
-            const T kh = fl.khat_edge ? (T)0.5 * (k0 + kq)
-                                      : (T)0.25 * (k0 + kq) + (dir_red(d) ? (T)(1.0 / 12.0) : (T)0.125) * rs;
-            const T* S = C.st.S[d < 7 ? d : d - 7];
-            const T ddx = px[qe] - x0, ddy = px[qe + E] - y0, ddz = px[qe + 2 * E] - z0;
-            ax += kh * (S[0] * ddx + S[3] * ddy + S[4] * ddz);
-            ay += kh * (S[3] * ddx + S[1] * ddy + S[5] * ddz);
-            az += kh * (S[4] * ddx + S[5] * ddy + S[2] * ddz);
-            if (fl.physical) {
-              ax += wy * ddz - wz * ddy;
-              ay += wz * ddx - wx * ddz;
-              az += wx * ddy - wy * ddx;
-            }
-            dgx -= kh * S[0];
-            dgy -= kh * S[1];
-            dgz -= kh * S[2];
-          }
-        }
-      }
-      // sum over the warp (same order on every lane: all lanes get identical sums)
+    for (int v = 0; v < 4; ++v) {
+      PX[v] = (v >= 1 && a0 == 0) + (v >= 2 && a1 == 0) + (v >= 3 && a2 == 0);
+      PY[v] = (v >= 1 && a0 == 1) + (v >= 2 && a1 == 1) + (v >= 3 && a2 == 1);
+      PZ[v] = (v >= 1 && a0 == 2) + (v >= 2 && a1 == 2) + (v >= 3 && a2 == 2);
+    }
+    const int cX = X - PX[av], cY = Y - PY[av], cZ = Z - PZ[av];
+    bool ok = true;
+    int idx[4];
+    bool inner[4];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        ax += __shfl_xor_sync(0xffffffffu, ax, o);
-        ay += __shfl_xor_sync(0xffffffffu, ay, o);
-        az += __shfl_xor_sync(0xffffffffu, az, o);
-        dgx += __shfl_xor_sync(0xffffffffu, dgx, o);
-        dgy += __shfl_xor_sync(0xffffffffu, dgy, o);
-        dgz += __shfl_xor_sync(0xffffffffu, dgz, o);
-      }
-      for (int q = b0 + lane; q < b1; q += 32) {
-        const SkelInc I = L.skel_inc[q];
-        const int64_t e = (int64_t)I.macro * L.nt + lattice_index(n, I.i, I.j, I.k);
-        double tmp = 0.0;
-        epilogue<T, OP>(a, e, E, ax, ay, az, dgx, dgy, dgz, x0, y0, z0, tmp);
-        if (q == b0) r2 = tmp;
+    for (int v = 0; v < 4; ++v) {
+      const int VX = cX + PX[v], VY = cY + PY[v], VZ = cZ + PZ[v];
+      ok = ok && kuhn_inside(n, VX, VY, VZ);
+      idx[v] = ok ? lattice_index32(n, VX - VY, VY - VZ, VZ) : 0;
+      inner[v] = kuhn_interior(n, VX, VY, VZ);
+    }
+    if (!ok) continue;
+    const T kb = (T)0.25 * (pk[idx[0]] + pk[idx[1]] + pk[idx[2]] + pk[idx[3]]);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      if (v == av) continue;
+      if (!fl.practical && inner[v]) continue;
+      const T* K = C.ke[p][av][v];
+      const T ddx = px[idx[v]] - x0, ddy = px[idx[v] + E] - y0, ddz = px[idx[v] + 2 * E] - z0;
+      ax += kb * (K[0] * ddx + K[1] * ddy + K[2] * ddz);
+      ay += kb * (K[3] * ddx + K[4] * ddy + K[5] * ddz);
+      az += kb * (K[6] * ddx + K[7] * ddy + K[8] * ddz);
+      dgx -= kb * K[0];
+      dgy -= kb * K[4];
+      dgz -= kb * K[8];
+    }
+  }
+  if (fl.practical || !dirs) return;
+  const T k0 = pk[lattice_index32(n, i, j, k)];
+#pragma unroll
+  for (int d = 0; d < NDIR; ++d) {
+    if (!((dirs >> d) & 1u)) continue;
+    const int qi = i + dir_di(d), qj = j + dir_dj(d), qk = k + dir_dk(d);
+    if (!lattice_interior(n, qi, qj, qk)) continue;
+    const int qe = lattice_index32(n, qi, qj, qk);
+    T rs = 0, wx = 0, wy = 0, wz = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (c >= ring_count(d)) continue;
+      const int ra = ring_a(d, c), rb = ring_b(d, c);
+      const T ka = pk[lattice_index32(n, i + dir_di(ra), j + dir_dj(ra), k + dir_dk(ra))];
+      const T kb = pk[lattice_index32(n, i + dir_di(rb), j + dir_dj(rb), k + dir_dk(rb))];
+      rs += ka + kb;
+      const T dk = ka - kb;
+      wx += dk * C.st.s[d][c][0];
+      wy += dk * C.st.s[d][c][1];
+      wz += dk * C.st.s[d][c][2];
+    }
+    const T kq = pk[qe];
+    const T kh = fl.khat_edge ? (T)0.5 * (k0 + kq)
+                              : (T)0.25 * (k0 + kq) + (dir_red(d) ? (T)(1.0 / 12.0) : (T)0.125) * rs;
+    const T* S = C.st.S[d < 7 ? d : d - 7];
+    const T ddx = px[qe] - x0, ddy = px[qe + E] - y0, ddz = px[qe + 2 * E] - z0;
+    ax += kh * (S[0] * ddx + S[3] * ddy + S[4] * ddz);
+    ay += kh * (S[3] * ddx + S[1] * ddy + S[5] * ddz);
+    az += kh * (S[4] * ddx + S[5] * ddy + S[2] * ddz);
+    if (fl.physical) {
+      ax += wy * ddz - wz * ddy;
+      ay += wz * ddx - wx * ddz;
+      az += wx * ddy - wy * ddx;
+    }
+    dgx -= kh * S[0];
+    dgy -= kh * S[1];
+    dgz -= kh * S[2];
+  }
+}
+
+__constant__ int c_dir[NDIR][3];
+__constant__ int c_ring[NDIR][3][2];
+__constant__ int c_ring_n[NDIR];
+
+// Lane version of incidence_row for the block kernels: lane l evaluates candidate
+// element l (l < 24) and stencil direction l (l < 14) with run-time indices, so
+// the lanes of a warp run the same element/direction body concurrently.
+template <typename T>
+__device__ __forceinline__ void incidence_lane(const MacroConsts<T>& C, const T* __restrict__ px,
+                                               const T* __restrict__ pk, int64_t E, int n, int i, int j, int k,
+                                               int lane, T x0, T y0, T z0, const OpFlags& fl, T& ax, T& ay, T& az,
+                                               T& dgx, T& dgy, T& dgz) {
+  if (lane < 24) {
+    const int X = i + j + k, Y = j + k, Z = k;
+    const int p = lane >> 2, av = lane & 3;
+    // Kuhn permutation p (lexicographic order 012 021 102 120 201 210)
+    const int a0 = p >> 1;
+    const int lo = a0 == 0 ? 1 : 0, hi = a0 == 2 ? 1 : 2;
+    const int a1 = (p & 1) ? hi : lo, a2 = (p & 1) ? lo : hi;
+    const int oX = (av >= 1 && a0 == 0) + (av >= 2 && a1 == 0) + (av >= 3 && a2 == 0);
+    const int oY = (av >= 1 && a0 == 1) + (av >= 2 && a1 == 1) + (av >= 3 && a2 == 1);
+    const int oZ = (av >= 1 && a0 == 2) + (av >= 2 && a1 == 2) + (av >= 3 && a2 == 2);
+    bool ok = true;
+    int idx[4];
+    bool inner[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int VX = X - oX + (v >= 1 && a0 == 0) + (v >= 2 && a1 == 0) + (v >= 3 && a2 == 0);
+      const int VY = Y - oY + (v >= 1 && a0 == 1) + (v >= 2 && a1 == 1) + (v >= 3 && a2 == 1);
+      const int VZ = Z - oZ + (v >= 1 && a0 == 2) + (v >= 2 && a1 == 2) + (v >= 3 && a2 == 2);
+      ok = ok && kuhn_inside(n, VX, VY, VZ);
+      idx[v] = ok ? lattice_index32(n, VX - VY, VY - VZ, VZ) : 0;
+      inner[v] = kuhn_interior(n, VX, VY, VZ);
+    }
+    if (ok) {
+      const T kb = (T)0.25 * (pk[idx[0]] + pk[idx[1]] + pk[idx[2]] + pk[idx[3]]);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        if (v == av) continue;
+        if (!fl.practical && inner[v]) continue;
+        const T* K = C.ke[p][av][v];
+        const T ddx = px[idx[v]] - x0, ddy = px[idx[v] + E] - y0, ddz = px[idx[v] + 2 * E] - z0;
+        ax += kb * (K[0] * ddx + K[1] * ddy + K[2] * ddz);
+        ay += kb * (K[3] * ddx + K[4] * ddy + K[5] * ddz);
+        az += kb * (K[6] * ddx + K[7] * ddy + K[8] * ddz);
+        dgx -= kb * K[0];
+        dgy -= kb * K[4];
+        dgz -= kb * K[8];
       }
     }
+  }
+  if (fl.practical || lane >= NDIR) return;
+  const int d = lane;
+  const int qi = i + c_dir[d][0], qj = j + c_dir[d][1], qk = k + c_dir[d][2];
+  if (!lattice_interior(n, qi, qj, qk)) return;
+  const T k0 = pk[lattice_index32(n, i, j, k)];
+  const int qe = lattice_index32(n, qi, qj, qk);
+  T rs = 0, wx = 0, wy = 0, wz = 0;
+  for (int c = 0; c < c_ring_n[d]; ++c) {
+    const int ra = c_ring[d][c][0], rb = c_ring[d][c][1];
+    const T ka = pk[lattice_index32(n, i + c_dir[ra][0], j + c_dir[ra][1], k + c_dir[ra][2])];
+    const T kb = pk[lattice_index32(n, i + c_dir[rb][0], j + c_dir[rb][1], k + c_dir[rb][2])];
+    rs += ka + kb;
+    const T dk = ka - kb;
+    wx += dk * C.st.s[d][c][0];
+    wy += dk * C.st.s[d][c][1];
+    wz += dk * C.st.s[d][c][2];
+  }
+  const T kq = pk[qe];
+  const T kh = fl.khat_edge ? (T)0.5 * (k0 + kq)
+                            : (T)0.25 * (k0 + kq) + (c_ring_n[d] == 3 ? (T)(1.0 / 12.0) : (T)0.125) * rs;
+  const T* S = C.st.S[d < 7 ? d : d - 7];
+  const T ddx = px[qe] - x0, ddy = px[qe + E] - y0, ddz = px[qe + 2 * E] - z0;
+  ax += kh * (S[0] * ddx + S[3] * ddy + S[4] * ddz);
+  ay += kh * (S[3] * ddx + S[1] * ddy + S[5] * ddz);
+  az += kh * (S[4] * ddx + S[5] * ddy + S[2] * ddz);
+  if (fl.physical) {
+    ax += wy * ddz - wz * ddy;
+    ay += wz * ddx - wx * ddz;
+    az += wx * ddy - wy * ddx;
+  }
+  dgx -= kh * S[0];
+  dgy -= kh * S[1];
+  dgz -= kh * S[2];
+}
+
+template <typename T>
+__device__ __forceinline__ T* acc_of(const LevelDev& L);
+template <>
+__device__ __forceinline__ float* acc_of<float>(const LevelDev& L) {
+  return L.acc32;
+}
+template <>
+__device__ __forceinline__ double* acc_of<double>(const LevelDev& L) {
+  return L.acc64;
+}
+
+// Free face-interior skeleton nodes, one thread per (node, incident macro):
+// the macro's part of the row is added to the node's accumulator.  A face node
+// has at most two incidences, so 0 + a + b is the same in either order.
+template <typename T>
+__global__ void __launch_bounds__(128) k_face_items(const LevelDev L, const MacroConsts<T>* __restrict__ mc,
+                                                     const OpFlags fl, const T* __restrict__ x,
+                                                     const T* __restrict__ kc) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L.nface_items) return;
+  const FaceItem it = L.face_items[t];
+  const int n = L.n;
+  const int64_t E = L.entries;
+  const int64_t base = (int64_t)it.macro * L.nt;
+  const T* px = x + base;
+  const T* pk = kc + base;
+  const int c0 = lattice_index32(n, it.i, it.j, it.k);
+  const T x0 = px[c0], y0 = px[c0 + E], z0 = px[c0 + 2 * E];
+  T ax = 0, ay = 0, az = 0, dgx = 0, dgy = 0, dgz = 0;
+  incidence_row<T>(mc[it.macro], px, pk, E, n, it.i, it.j, it.k, L.face_mask[it.f], (1u << NDIR) - 1u, x0, y0, z0,
+                   fl, ax, ay, az, dgx, dgy, dgz);
+  T* acc = acc_of<T>(L) + 6 * (int64_t)it.node;
+  atomicAdd(acc + 0, ax);
+  atomicAdd(acc + 1, ay);
+  atomicAdd(acc + 2, az);
+  atomicAdd(acc + 3, dgx);
+  atomicAdd(acc + 4, dgy);
+  atomicAdd(acc + 5, dgz);
+}
+
+// Face nodes: finish the row from the accumulator (which is reset to zero) and
+// write every copy.
+template <typename T, int OP>
+__global__ void __launch_bounds__(128) k_face_finalize(const LevelDev L, const SweepArgs<T> a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double r2 = 0.0;
+  if (t < L.nface_nodes) {
+    const int n = L.n;
+    const int64_t E = L.entries;
+    T* acc = acc_of<T>(L) + 6 * (int64_t)t;
+    const T ax = acc[0], ay = acc[1], az = acc[2], dgx = acc[3], dgy = acc[4], dgz = acc[5];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[c] = 0;
+    const int s = L.face_nodes[t];
+    const int b0 = L.skel_ptr[s], b1 = L.skel_ptr[s + 1];
+    const SkelInc I0 = L.skel_inc[b0];
+    const int64_t e0 = (int64_t)I0.macro * L.nt + lattice_index32(n, I0.i, I0.j, I0.k);
+    const T x0 = a.x[e0], y0 = a.x[e0 + E], z0 = a.x[e0 + 2 * E];
+    for (int q = b0; q < b1; ++q) {
+      const SkelInc I = L.skel_inc[q];
+      const int64_t e = (int64_t)I.macro * L.nt + lattice_index32(n, I.i, I.j, I.k);
+      double tmp = 0.0;
+      epilogue<T, OP>(a, e, E, ax, ay, az, dgx, dgy, dgz, x0, y0, z0, tmp);
+      if (q == b0) r2 = tmp;
+    }
+  }
+  if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
+}
+
+// Dirichlet skeleton nodes: identity rows (residual 0), every copy.
+template <typename T, int OP>
+__global__ void __launch_bounds__(128) k_dirichlet(const LevelDev L, const SweepArgs<T> a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L.ndir) return;
+  const int n = L.n;
+  const int64_t E = L.entries;
+  const int s = L.dir_nodes[t];
+  const int b0 = L.skel_ptr[s], b1 = L.skel_ptr[s + 1];
+  const SkelInc I0 = L.skel_inc[b0];
+  const int64_t e0 = (int64_t)I0.macro * L.nt + lattice_index32(n, I0.i, I0.j, I0.k);
+  const T x0 = a.x[e0], y0 = a.x[e0 + E], z0 = a.x[e0 + 2 * E];
+  for (int q = b0; q < b1; ++q) {
+    const SkelInc I = L.skel_inc[q];
+    const int64_t e = (int64_t)I.macro * L.nt + lattice_index32(n, I.i, I.j, I.k);
+    if (OP == OP_RESID) {
+      a.out[e] = 0;
+      a.out[e + E] = 0;
+      a.out[e + 2 * E] = 0;
+    } else {
+      a.out[e] = x0;
+      a.out[e + E] = y0;
+      a.out[e + 2 * E] = z0;
+      if (OP == OP_CHEBY) {
+        a.dout[e] = 0;
+        a.dout[e + E] = 0;
+        a.dout[e + 2 * E] = 0;
+      }
+    }
+  }
+}
+
+// Free nodes on macro edges and vertices: one 128-thread block per node; warp w
+// takes incidences w, w+4, ...; lanes take candidate elements and directions
+// (incidence_lane).  Warp sums are combined in a fixed order, so the row is
+// deterministic, and it is written to every copy of the node.
+template <typename T, int OP>
+__global__ void __launch_bounds__(128) k_skeleton_ev(const LevelDev L, const MacroConsts<T>* __restrict__ mc,
+                                                      const OpFlags fl, const SweepArgs<T> a) {
+  __shared__ T part[4][6];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double r2 = 0.0;
+  const int s = L.ev_nodes[blockIdx.x];
+  const int n = L.n;
+  const int64_t E = L.entries;
+  const int b0 = L.skel_ptr[s], b1 = L.skel_ptr[s + 1];
+  const SkelInc I0 = L.skel_inc[b0];
+  const int64_t e0 = (int64_t)I0.macro * L.nt + lattice_index32(n, I0.i, I0.j, I0.k);
+  const T x0 = a.x[e0], y0 = a.x[e0 + E], z0 = a.x[e0 + 2 * E];
+  T ax = 0, ay = 0, az = 0, dgx = 0, dgy = 0, dgz = 0;
+  for (int q = b0 + warp; q < b1; q += 4) {
+    const SkelInc I = L.skel_inc[q];
+    const int64_t base = (int64_t)I.macro * L.nt;
+    incidence_lane<T>(mc[I.macro], a.x + base, a.k + base, E, n, I.i, I.j, I.k, lane, x0, y0, z0, fl, ax, ay, az,
+                      dgx, dgy, dgz);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    az += __shfl_xor_sync(0xffffffffu, az, o);
+    dgx += __shfl_xor_sync(0xffffffffu, dgx, o);
+    dgy += __shfl_xor_sync(0xffffffffu, dgy, o);
+    dgz += __shfl_xor_sync(0xffffffffu, dgz, o);
+  }
+  if (lane == 0) {
+    part[warp][0] = ax;
+    part[warp][1] = ay;
+    part[warp][2] = az;
+    part[warp][3] = dgx;
+    part[warp][4] = dgy;
+    part[warp][5] = dgz;
+  }
+  __syncthreads();
+  ax = (part[0][0] + part[1][0]) + (part[2][0] + part[3][0]);
+  ay = (part[0][1] + part[1][1]) + (part[2][1] + part[3][1]);
+  az = (part[0][2] + part[1][2]) + (part[2][2] + part[3][2]);
+  dgx = (part[0][3] + part[1][3]) + (part[2][3] + part[3][3]);
+  dgy = (part[0][4] + part[1][4]) + (part[2][4] + part[3][4]);
+  dgz = (part[0][5] + part[1][5]) + (part[2][5] + part[3][5]);
+  for (int q = b0 + threadIdx.x; q < b1; q += blockDim.x) {
+    const SkelInc I = L.skel_inc[q];
+    const int64_t e = (int64_t)I.macro * L.nt + lattice_index32(n, I.i, I.j, I.k);
+    double tmp = 0.0;
+    epilogue<T, OP>(a, e, E, ax, ay, az, dgx, dgy, dgz, x0, y0, z0, tmp);
+    if (q == b0) r2 = tmp;
   }
   if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
 }
@@ -354,20 +552,66 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
     }
     used += L.ntiles_int;
   }
-  if (L.nskel > 0 && (parts & 2)) {
-    const int nb = (L.nskel + 3) / 4;
-    SweepArgs<T> am = a;
-    if (a.partial) am.partial = a.partial + used;
-    switch (op) {
-      case OP_APPLY: k_skeleton<T, OP_APPLY><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
-      case OP_RESID: k_skeleton<T, OP_RESID><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
-      case OP_JACOBI: k_skeleton<T, OP_JACOBI><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
-      case OP_CHEBY: k_skeleton<T, OP_CHEBY><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
+  if (parts & 2) {
+    if (L.nface_items > 0) {
+      const int nb = (L.nface_items + 127) / 128;
+      k_face_items<T><<<nb, 128, 0, s>>>(L, mc_dev, fl, a.x, a.k);
     }
-    used += nb;
+    if (L.nface_nodes > 0) {
+      const int nb = (L.nface_nodes + 127) / 128;
+      SweepArgs<T> am = a;
+      if (a.partial) am.partial = a.partial + used;
+      switch (op) {
+        case OP_APPLY: k_face_finalize<T, OP_APPLY><<<nb, 128, 0, s>>>(L, am); break;
+        case OP_RESID: k_face_finalize<T, OP_RESID><<<nb, 128, 0, s>>>(L, am); break;
+        case OP_JACOBI: k_face_finalize<T, OP_JACOBI><<<nb, 128, 0, s>>>(L, am); break;
+        case OP_CHEBY: k_face_finalize<T, OP_CHEBY><<<nb, 128, 0, s>>>(L, am); break;
+      }
+      used += nb;
+    }
+    if (L.nev > 0) {
+      const int nb = L.nev;
+      SweepArgs<T> am = a;
+      if (a.partial) am.partial = a.partial + used;
+      switch (op) {
+        case OP_APPLY: k_skeleton_ev<T, OP_APPLY><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
+        case OP_RESID: k_skeleton_ev<T, OP_RESID><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
+        case OP_JACOBI: k_skeleton_ev<T, OP_JACOBI><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
+        case OP_CHEBY: k_skeleton_ev<T, OP_CHEBY><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
+      }
+      used += nb;
+    }
+    if (L.ndir > 0) {
+      const int nb = (L.ndir + 127) / 128;
+      switch (op) {
+        case OP_APPLY: k_dirichlet<T, OP_APPLY><<<nb, 128, 0, s>>>(L, a); break;
+        case OP_RESID: k_dirichlet<T, OP_RESID><<<nb, 128, 0, s>>>(L, a); break;
+        case OP_JACOBI: k_dirichlet<T, OP_JACOBI><<<nb, 128, 0, s>>>(L, a); break;
+        case OP_CHEBY: k_dirichlet<T, OP_CHEBY><<<nb, 128, 0, s>>>(L, a); break;
+      }
+    }
   }
   if (partial_count) *partial_count = used - partial_offset;
   return (int)cudaGetLastError();
+}
+
+// fills the direction / ring tables used with run-time indices
+int upload_direction_tables() {
+  int dir[NDIR][3], ring[NDIR][3][2], rn[NDIR];
+  for (int d = 0; d < NDIR; ++d) {
+    dir[d][0] = dir_di(d);
+    dir[d][1] = dir_dj(d);
+    dir[d][2] = dir_dk(d);
+    rn[d] = ring_count(d);
+    for (int c = 0; c < 3; ++c) {
+      ring[d][c][0] = c < rn[d] ? ring_a(d, c) : 0;
+      ring[d][c][1] = c < rn[d] ? ring_b(d, c) : 0;
+    }
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_dir, dir, sizeof(dir));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ring, ring, sizeof(ring));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ring_n, rn, sizeof(rn));
+  return (int)e;
 }
 
 template int launch_sweep<float>(const LevelDev&, const MacroStencil<float>*, const MacroConsts<float>*, OpKind,
