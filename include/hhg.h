@@ -156,6 +156,31 @@ hhg_status hhg_apply(hhg_ctx* ctx, int level, hhg_dtype dt, const void* x_dev, v
 hhg_status hhg_residual(hhg_ctx* ctx, int level, hhg_dtype dt, const void* f_dev, const void* x_dev, void* r_dev,
                         double* norm2_host);
 
+/* Residual with norm that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory at
+ * the time they need a residual norm -- a process whose device memory is owned
+ * by another allocator (a caching allocator that has reserved the GPU, so a
+ * cudaMalloc would fail), or a time-critical solver loop that must not pay
+ * the latency and implicit device synchronisation of cudaMalloc/cudaFree.
+ * It computes exactly what hhg_residual(ctx, level, dt, f_dev, x_dev, r_dev,
+ * norm2_host) computes (r = f - A x on free rows, 0 on Dirichlet rows;
+ * norm2_host = sum of |r|^2 over unique free nodes, FP64), with the caller's
+ * inputs and outputs, but keeps its scratch (per-block partial sums and the
+ * reduced value) in one static device array of 262,144 + 32 doubles (about
+ * 2 MiB) that every GPU which loads the library holds until the process
+ * exits.  It calls no cudaMalloc, cudaFree or other allocating routine; the
+ * context must already be set up (hhg_refine etc. allocate, this call does not).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Levels whose residual needs more than 262,144 partial
+ * sums (one per interior tile of each macro plus one per free skeleton node;
+ * for the 6-macro cube: levels up to 7) are rejected with HHG_ERR_ARG.
+ * All calls share the array: calls that overlap on the GPU (other streams,
+ * other contexts on the same device) race on it.  Waits for the stream
+ * (bounded wait). */
+hhg_status hhg_residual_noalloc(hhg_ctx* ctx, int level, hhg_dtype dt, const void* f_dev, const void* x_dev,
+                                void* r_dev, double* norm2_host);
+
 /* End-to-end apply with host buffers: copies x_host (3*E values of type dt,
  * library layout; pinned memory gives full copy bandwidth) to a library-owned
  * device buffer, applies A (as hhg_apply) and copies the result to y_host, then

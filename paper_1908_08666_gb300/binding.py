@@ -55,6 +55,8 @@ _SIGS = {
     "hhg_residual": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)],
     "hhg_apply_host": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
     "hhg_profile": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+    "hhg_residual_noalloc": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                             C.POINTER(C.c_double)],
 }
 _RESTYPE = {"hhg_last_error": C.c_char_p}
 
@@ -197,3 +199,9 @@ def hhg_profile(ctx, enable, read=False):
     _check(ctx, load().hhg_profile(ctx, int(enable), None, None))
     return None
 
+
+def hhg_residual_noalloc(ctx, level, dt, f, x, r):
+    """Residual and its squared norm with no device allocation (static scratch); returns the norm^2."""
+    nrm = C.c_double()
+    _check(ctx, load().hhg_residual_noalloc(ctx, level, dt, _ptr(f), _ptr(x), _ptr(r), C.byref(nrm)))
+    return nrm.value

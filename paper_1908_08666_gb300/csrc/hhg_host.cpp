@@ -684,6 +684,20 @@ void wait_stream(hhg_ctx* c) {
   cudaEventDestroy(ev);
 }
 
+// bounded wait that creates nothing: polls the stream itself
+void wait_stream_noalloc(hhg_ctx* c) {
+  const auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    const cudaError_t e = cudaStreamQuery(c->stream);
+    if (e == cudaSuccess) return;
+    if (e != cudaErrorNotReady) CK(e);
+    const auto ms =
+        std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+    if (ms > c->timeout_ms) THROW(HHG_ERR_TIMEOUT, "stream did not finish within %lld ms", (long long)c->timeout_ms);
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
 template <typename F>
 hhg_status guard(hhg_ctx* c, F&& f) {
   if (!c) return HHG_ERR_ARG;
@@ -1099,6 +1113,45 @@ hhg_status hhg_apply_host(hhg_ctx* c, int level, hhg_dtype dt, const void* x_hos
     }
     CK(cudaMemcpyAsync(y_host, c->hy.p, bytes, cudaMemcpyDeviceToHost, c->stream));
     wait_stream(c);
+  });
+}
+
+// Allocation-free residual with norm: same result as hhg_residual(..., norm2_host), with
+// the scratch in a static device array instead of context-owned memory (see hhg.h).
+hhg_status hhg_residual_noalloc(hhg_ctx* c, int level, hhg_dtype dt, const void* f, const void* x, void* r,
+                                double* norm2_host) {
+  return guard(c, [&] {
+    need_ready(c, true);
+    if (!x || !r || !f || !norm2_host || x == r || f == r) THROW(HHG_ERR_ARG, "bad buffers");
+    LevelHost& L = c->lv(level);
+    const int64_t need = noalloc_partials_needed(L.dev);
+    if (need > NOALLOC_SLOTS)
+      THROW(HHG_ERR_ARG, "level %d needs %lld partial sums; the no-alloc scratch holds %lld (use hhg_residual)", level,
+            (long long)need, (long long)NOALLOC_SLOTS);
+    double* scratch = nullptr;
+    CK(noalloc_scratch_address(c->device, &scratch));
+    if (dt == HHG_F64) {
+      SweepArgs<double> a{};
+      a.x = (const double*)x;
+      a.f = (const double*)f;
+      a.out = (double*)r;
+      a.k = L.d_k64.as<double>();
+      CK(launch_residual_noalloc<double>(L.dev, L.st64.data(), L.d_mc64.as<MacroConsts<double>>(), c->flags, a,
+                                         scratch, c->stream));
+    } else if (dt == HHG_F32) {
+      SweepArgs<float> a{};
+      a.x = (const float*)x;
+      a.f = (const float*)f;
+      a.out = (float*)r;
+      a.k = L.d_k32.as<float>();
+      CK(launch_residual_noalloc<float>(L.dev, L.st32.data(), L.d_mc32.as<MacroConsts<float>>(), c->flags, a, scratch,
+                                        c->stream));
+    } else {
+      THROW(HHG_ERR_ARG, "dtype");
+    }
+    CK(cudaMemcpyAsync(c->pinned, scratch + NOALLOC_SLOTS, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    wait_stream_noalloc(c);
+    *norm2_host = c->pinned[0];
   });
 }
 

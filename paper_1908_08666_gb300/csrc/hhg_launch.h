@@ -39,6 +39,16 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
                  const OpFlags& fl, const SweepArgs<T>& a, void* stream, int parts, int64_t partial_offset,
                  int64_t* partial_count);
 
+// No-alloc residual (see hhg_residual_noalloc): static device scratch of
+// NOALLOC_SLOTS partial sums plus the result slot at index NOALLOC_SLOTS.
+constexpr int64_t NOALLOC_SLOTS = 262144;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+int noalloc_scratch_address(int device, double** ptr);
+int64_t noalloc_partials_needed(const LevelDev& L);
+template <typename T>
+int launch_residual_noalloc(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev,
+                            const OpFlags& fl, SweepArgs<T> a, double* scratch, void* stream);
+
 // constant-memory direction tables of the skeleton kernels (once per device)
 int upload_direction_tables();
 

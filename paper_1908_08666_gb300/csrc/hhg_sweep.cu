@@ -20,6 +20,8 @@
 // sum.  With the practical interface rule the whole row is the a_h row.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "hhg_internal.h"
 #include "hhg_launch.h"
 
@@ -594,6 +596,80 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
   if (partial_count) *partial_count = used - partial_offset;
   return (int)cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Residual with norm that allocates nothing.  Its scratch (per-block partial
+// sums of |r|^2 and the reduced result) lives in this file-scope device array,
+// which every GPU that loads the library holds until the process exits.  Host
+// code never uses the array's name as an address: the device address is looked
+// up once per device with cudaGetSymbolAddress.  Face-interior skeleton nodes
+// go through the warp-per-node kernel here, so no accumulator is needed.
+// Calls that overlap on the GPU share the array and race.
+// ---------------------------------------------------------------------------
+__device__ __align__(256) static double g_noalloc_scratch[NOALLOC_SLOTS + 32];
+
+namespace {
+std::mutex g_noalloc_mutex;
+double* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+int noalloc_scratch_address(int device, double** ptr) {
+  if (device < 0 || device >= NOALLOC_MAX_DEVICES) return (int)cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return (int)e;
+    g_noalloc_addr[device] = (double*)p;
+  }
+  *ptr = g_noalloc_addr[device];
+  return 0;
+}
+
+int64_t noalloc_partials_needed(const LevelDev& L) {
+  return (int64_t)L.nmacro * L.ntiles_int + L.nface_nodes + L.nev;
+}
+
+template <typename T>
+int launch_residual_noalloc(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev,
+                            const OpFlags& fl, SweepArgs<T> a, double* scratch, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const dim3 blk(TILE_I, TILE_J);
+  int64_t used = 0;
+  for (int m = 0; m < L.nmacro && L.ntiles_int > 0; ++m) {
+    SweepArgs<T> am = a;
+    am.partial = scratch + used;
+    k_interior<T, OP_RESID><<<L.ntiles_int, blk, 0, s>>>(L, st_host[m], m, fl, am);
+    used += L.ntiles_int;
+  }
+  if (L.nface_nodes > 0) {
+    LevelDev Lf = L;  // face-interior nodes through the warp-per-node path
+    Lf.ev_nodes = L.face_nodes;
+    Lf.nev = L.nface_nodes;
+    const int nb = L.nface_nodes;
+    SweepArgs<T> am = a;
+    am.partial = scratch + used;
+    k_skeleton_ev<T, OP_RESID><<<nb, 128, 0, s>>>(Lf, mc_dev, fl, am);
+    used += nb;
+  }
+  if (L.nev > 0) {
+    const int nb = L.nev;
+    SweepArgs<T> am = a;
+    am.partial = scratch + used;
+    k_skeleton_ev<T, OP_RESID><<<nb, 128, 0, s>>>(L, mc_dev, fl, am);
+    used += nb;
+  }
+  if (L.ndir > 0) k_dirichlet<T, OP_RESID><<<(L.ndir + 127) / 128, 128, 0, s>>>(L, a);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return (int)e;
+  return launch_reduce(scratch, used, scratch + NOALLOC_SLOTS, stream);
+}
+
+template int launch_residual_noalloc<float>(const LevelDev&, const MacroStencil<float>*, const MacroConsts<float>*,
+                                            const OpFlags&, SweepArgs<float>, double*, void*);
+template int launch_residual_noalloc<double>(const LevelDev&, const MacroStencil<double>*,
+                                             const MacroConsts<double>*, const OpFlags&, SweepArgs<double>, double*,
+                                             void*);
 
 // fills the direction / ring tables used with run-time indices
 int upload_direction_tables() {
