@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--level", type=int, default=LEVEL)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
     return ap.parse_args()
 
 
@@ -183,6 +184,41 @@ def cpu_baseline(level, budget_s=15.0, seed=0):
                       % (done, level, dt)}
 
 
+def solve_times(B, torch, h, level, coords_u):
+    """Time to an FP64 relative residual of 1e-8 on the same workload (f ~ U[-1, 1], seed 3,
+    x0 = 0): FP64 iterative refinement around FP32 MG-CG, and plain FP64 MG-CG (V(2,2)
+    Chebyshev, exact coarse solve on level 2)."""
+    import hhg_inputs as hi
+
+    N = 1 << level
+    E, U, _ = B.hhg_num_nodes(h, level)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B.hhg_mg_setup(h)
+    setup_s = time.perf_counter() - t0
+    fu = hi.sample_grid(hi.uniform_grid(N, seed=3), coords_u)
+    src = torch.as_tensor(np.ascontiguousarray(fu.T).reshape(-1), dtype=torch.float64, device="cuda")
+    f = torch.empty(3 * E, dtype=torch.float64, device="cuda")
+    B.hhg_scatter_unique(h, level, B.F64, 3, src, f)
+    out = {"rtol": 1e-8, "setup_s": round(setup_s, 4)}
+    for name, method, kw in (("ir_fp64_over_fp32_mgcg", B.SOLVE_IR_MG_CG, dict(inner_rtol=1e-3, inner_max_iter=50)),
+                             ("fp64_mgcg", B.SOLVE_MG_CG, {})):
+        best = None
+        for _ in range(2):
+            x = torch.zeros_like(f)
+            torch.cuda.synchronize()
+            rep = B.hhg_solve(h, f, x, method=method, level=level, dt=B.F64, rtol=1e-8, max_iter=100, **kw)
+            if best is None or rep["seconds"] < best["seconds"]:
+                best = rep
+        r = torch.empty_like(f)
+        r2 = B.hhg_residual(h, level, B.F64, f, x, r, want_norm=True)
+        out[name] = {"seconds": round(best["seconds"], 5), "iterations": best["iterations"],
+                     "inner_iterations": best["inner_iterations"], "rel_residual_fp64": float(np.sqrt(r2)) /
+                     best["residual0"], "converged": bool(best["converged"])}
+    out["speedup_ir_vs_fp64"] = round(out["fp64_mgcg"]["seconds"] / out["ir_fp64_over_fp32_mgcg"]["seconds"], 3)
+    return out
+
+
 # ---------------------------------------------------------------------------- our arm
 
 
@@ -273,6 +309,7 @@ def run_ours(args):
     time.sleep(0.2)
     clk = clocks.stop()
     assert torch.isfinite(y).all()
+    solve = None if args.no_solve else solve_times(B, torch, h, level, coords_e[first])
     B.hhg_destroy(h)
 
     ms_per_step = total_ms / args.steps
@@ -326,6 +363,7 @@ def run_ours(args):
         "e2e": {"value": round(world * dofs / e2e_s / 1e9, 3), "unit": "GDoF/s",
                 "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4)},
         "gpu_launches": int(prof_launches[0] + prof_launches[1]),
+        "solve": solve,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

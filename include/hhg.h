@@ -156,6 +156,73 @@ hhg_status hhg_apply(hhg_ctx* ctx, int level, hhg_dtype dt, const void* x_dev, v
 hhg_status hhg_residual(hhg_ctx* ctx, int level, hhg_dtype dt, const void* f_dev, const void* x_dev, void* r_dev,
                         double* norm2_host);
 
+/* ---------------------------------------------------------------------------
+ * Smoothers, multigrid and solvers.  Sec. 5 solves with geometric multigrid:
+ * linear interpolation and its transpose between levels, coarse operators by
+ * rediscretisation with the injected coefficient, a smoother on every level
+ * and a coarse-grid solve; this library uses point-Jacobi or Chebyshev
+ * smoothing (bounds [lo, hi] * lambda_max(D^-1 A), lambda_max from power
+ * iterations) and an exact dense solve on the coarsest level (level 2).
+ * ------------------------------------------------------------------------- */
+typedef enum { HHG_SMOOTH_JACOBI = 0, HHG_SMOOTH_CHEBYSHEV = 1 } hhg_smoother;
+
+typedef struct {
+  hhg_smoother smoother;
+  int pre, post;          /* smoothing steps before / after the coarse correction (default 2, 2) */
+  double omega;           /* Jacobi damping */
+  double cheby_lo, cheby_hi; /* Chebyshev interval as fractions of lambda_max (default 1/8, 1.1) */
+  int power_iters;        /* power iterations for lambda_max */
+} hhg_mg_params;
+
+hhg_status hhg_set_mg_params(hhg_ctx* ctx, const hhg_mg_params* params);
+/* Diagonals, lambda_max of every level (unless set) and the dense coarse inverse
+ * (at most 3000 coarse DoFs).  Call after hhg_set_coefficient; waits for the stream. */
+hhg_status hhg_mg_setup(hhg_ctx* ctx);
+hhg_status hhg_get_lambda_max(hhg_ctx* ctx, int level, double* lambda);
+hhg_status hhg_set_lambda_max(hhg_ctx* ctx, int level, double lambda);
+/* Point diagonal of A on `level` (3*E, 1 on Dirichlet rows). */
+hhg_status hhg_diagonal(hhg_ctx* ctx, int level, hhg_dtype dt, void* d_dev);
+/* `steps` smoothing steps for A x = f on `level`, x updated in place (3*E). */
+hhg_status hhg_smooth(hhg_ctx* ctx, int level, hhg_dtype dt, int steps, const void* f_dev, void* x_dev);
+/* xf += P xc (linear interpolation from fine_level-1 to fine_level). */
+hhg_status hhg_prolongate_add(hhg_ctx* ctx, int fine_level, hhg_dtype dt, const void* xc_dev, void* xf_dev);
+/* rc = P^T rf (rc on fine_level-1; 0 on Dirichlet nodes). */
+hhg_status hhg_restrict(hhg_ctx* ctx, int fine_level, hhg_dtype dt, const void* rf_dev, void* rc_dev);
+/* One V(pre, post) cycle for A x = f on `level`, x updated in place. */
+hhg_status hhg_vcycle(hhg_ctx* ctx, int level, hhg_dtype dt, const void* f_dev, void* x_dev);
+
+typedef enum {
+  HHG_SOLVE_PCG_JACOBI = 0, /* point-Jacobi preconditioned CG */
+  HHG_SOLVE_MG_CG = 1,      /* CG preconditioned by one V-cycle */
+  HHG_SOLVE_IR_MG_CG = 2,   /* FP64 iterative refinement around FP32 MG-CG (f, x in FP64) */
+  HHG_SOLVE_MG = 3          /* stationary V-cycles */
+} hhg_solve_method;
+
+typedef struct {
+  hhg_solve_method method;
+  int level;
+  hhg_dtype dt;        /* type of f and x (F64 required for IR_MG_CG) */
+  double rtol;         /* stop when |f - A x| <= rtol |f - A x0| (2-norm over free unique DoFs) */
+  int max_iter;
+  double inner_rtol;   /* IR: relative tolerance of each FP32 inner solve */
+  int inner_max_iter;
+} hhg_solve_opts;
+
+typedef struct {
+  int iterations;        /* outer iterations (CG / V-cycles / refinement steps) */
+  int inner_iterations;  /* IR: total inner CG iterations */
+  double residual0;      /* |f - A x0| */
+  double rel_residual;   /* final |f - A x| / |f - A x0|, in the type of x */
+  double seconds;        /* host wall time of the call */
+  int converged;
+} hhg_solve_report;
+
+/* Solve A x = f on opts->level (x holds the initial guess and the Dirichlet
+ * values).  Returns HHG_ERR_NOT_CONVERGED (with x and the report filled) when
+ * max_iter is reached, HHG_ERR_NUMERIC on a non-finite residual. */
+hhg_status hhg_solve(hhg_ctx* ctx, const hhg_solve_opts* opts, const void* f_dev, void* x_dev,
+                     hhg_solve_report* report);
+
 /* Residual with norm that allocates nothing.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory at
  * the time they need a residual norm -- a process whose device memory is owned

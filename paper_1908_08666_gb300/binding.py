@@ -30,6 +30,28 @@ class HhgError(RuntimeError):
         self.status = status
 
 
+SMOOTH_JACOBI, SMOOTH_CHEBYSHEV = 0, 1
+SOLVE_PCG_JACOBI, SOLVE_MG_CG, SOLVE_IR_MG_CG, SOLVE_MG = 0, 1, 2, 3
+
+
+class hhg_mg_params(C.Structure):
+    _fields_ = [("smoother", C.c_int), ("pre", C.c_int), ("post", C.c_int), ("omega", C.c_double),
+                ("cheby_lo", C.c_double), ("cheby_hi", C.c_double), ("power_iters", C.c_int)]
+
+
+class hhg_solve_opts(C.Structure):
+    _fields_ = [("method", C.c_int), ("level", C.c_int), ("dt", C.c_int), ("rtol", C.c_double),
+                ("max_iter", C.c_int), ("inner_rtol", C.c_double), ("inner_max_iter", C.c_int)]
+
+
+class hhg_solve_report(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("inner_iterations", C.c_int), ("residual0", C.c_double),
+                ("rel_residual", C.c_double), ("seconds", C.c_double), ("converged", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class hhg_problem(C.Structure):
     _fields_ = [("kind", C.c_int), ("nu", C.c_double), ("variant", C.c_int), ("khat", C.c_int), ("iface", C.c_int)]
 
@@ -54,6 +76,16 @@ _SIGS = {
     "hhg_apply": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
     "hhg_residual": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)],
     "hhg_apply_host": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+    "hhg_set_mg_params": [C.c_void_p, C.POINTER(hhg_mg_params)],
+    "hhg_mg_setup": [C.c_void_p],
+    "hhg_get_lambda_max": [C.c_void_p, C.c_int, C.POINTER(C.c_double)],
+    "hhg_set_lambda_max": [C.c_void_p, C.c_int, C.c_double],
+    "hhg_diagonal": [C.c_void_p, C.c_int, C.c_int, C.c_void_p],
+    "hhg_smooth": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+    "hhg_prolongate_add": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+    "hhg_restrict": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+    "hhg_vcycle": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+    "hhg_solve": [C.c_void_p, C.POINTER(hhg_solve_opts), C.c_void_p, C.c_void_p, C.POINTER(hhg_solve_report)],
     "hhg_profile": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "hhg_residual_noalloc": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.POINTER(C.c_double)],
@@ -205,3 +237,55 @@ def hhg_residual_noalloc(ctx, level, dt, f, x, r):
     nrm = C.c_double()
     _check(ctx, load().hhg_residual_noalloc(ctx, level, dt, _ptr(f), _ptr(x), _ptr(r), C.byref(nrm)))
     return nrm.value
+
+
+def hhg_set_mg_params(ctx, smoother=SMOOTH_CHEBYSHEV, pre=2, post=2, omega=2.0 / 3.0, cheby_lo=1.0 / 8.0,
+                      cheby_hi=1.1, power_iters=15):
+    p = hhg_mg_params(smoother, pre, post, omega, cheby_lo, cheby_hi, power_iters)
+    _check(ctx, load().hhg_set_mg_params(ctx, C.byref(p)))
+
+
+def hhg_mg_setup(ctx):
+    _check(ctx, load().hhg_mg_setup(ctx))
+
+
+def hhg_get_lambda_max(ctx, level):
+    v = C.c_double()
+    _check(ctx, load().hhg_get_lambda_max(ctx, level, C.byref(v)))
+    return v.value
+
+
+def hhg_set_lambda_max(ctx, level, lam):
+    _check(ctx, load().hhg_set_lambda_max(ctx, level, float(lam)))
+
+
+def hhg_diagonal(ctx, level, dt, d):
+    _check(ctx, load().hhg_diagonal(ctx, level, dt, _ptr(d)))
+
+
+def hhg_smooth(ctx, level, dt, steps, f, x):
+    _check(ctx, load().hhg_smooth(ctx, level, dt, steps, _ptr(f), _ptr(x)))
+
+
+def hhg_prolongate_add(ctx, fine_level, dt, xc, xf):
+    _check(ctx, load().hhg_prolongate_add(ctx, fine_level, dt, _ptr(xc), _ptr(xf)))
+
+
+def hhg_restrict(ctx, fine_level, dt, rf, rc):
+    _check(ctx, load().hhg_restrict(ctx, fine_level, dt, _ptr(rf), _ptr(rc)))
+
+
+def hhg_vcycle(ctx, level, dt, f, x):
+    _check(ctx, load().hhg_vcycle(ctx, level, dt, _ptr(f), _ptr(x)))
+
+
+def hhg_solve(ctx, f, x, method=SOLVE_MG_CG, level=None, dt=F64, rtol=1e-8, max_iter=200, inner_rtol=1e-3,
+              inner_max_iter=50, allow_not_converged=False):
+    """Returns the report as a dict; raises unless converged (or allow_not_converged)."""
+    o = hhg_solve_opts(method, level, dt, rtol, max_iter, inner_rtol, inner_max_iter)
+    rep = hhg_solve_report()
+    st = load().hhg_solve(ctx, C.byref(o), _ptr(f), _ptr(x), C.byref(rep))
+    if st == 5 and allow_not_converged:
+        return rep.as_dict()
+    _check(ctx, st)
+    return rep.as_dict()

@@ -15,82 +15,9 @@
 // axial vectors of the antisymmetric C_{d,c} are what the kernels store.
 // Everything here is derived from the element stiffness matrices, computed
 // from the closed-form P1 gradients.
-#include <cuda_runtime.h>
-
-#include <algorithm>
-#include <array>
-#include <chrono>
-#include <cmath>
-#include <cstdio>
-#include <cstring>
-#include <map>
-#include <memory>
-#include <set>
-#include <string>
-#include <thread>
-#include <unordered_map>
-#include <vector>
-
-#include "../../include/hhg.h"
-#include "hhg_internal.h"
-#include "hhg_launch.h"
-
-using namespace hhg;
+#include "hhg_ctx.h"
 
 namespace {
-
-struct DevMem {
-  void* p = nullptr;
-  size_t bytes = 0;
-  DevMem() = default;
-  DevMem(const DevMem&) = delete;
-  DevMem& operator=(const DevMem&) = delete;
-  ~DevMem() {
-    if (p) cudaFree(p);
-  }
-  cudaError_t alloc(size_t b) {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = b;
-    if (b == 0) return cudaSuccess;
-    return cudaMalloc(&p, b);
-  }
-  template <typename T>
-  T* as() const {
-    return (T*)p;
-  }
-};
-
-struct HhgError {
-  hhg_status st;
-  std::string msg;
-};
-
-#define THROW(st, ...)                                      \
-  do {                                                      \
-    char _b[512];                                           \
-    snprintf(_b, sizeof(_b), __VA_ARGS__);                  \
-    throw HhgError{st, std::string(_b)};                    \
-  } while (0)
-
-#define CK(...)                                                                                      \
-  do {                                                                                               \
-    cudaError_t _e = (cudaError_t)(__VA_ARGS__);                                                         \
-    if (_e != cudaSuccess) {                                                                         \
-      hhg_status _s = (_e == cudaErrorMemoryAllocation) ? HHG_ERR_OOM : HHG_ERR_CUDA;                \
-      THROW(_s, "%s failed: %s (%s:%d)", #__VA_ARGS__, cudaGetErrorString(_e), __FILE__, __LINE__);        \
-    }                                                                                                \
-  } while (0)
-
-template <typename T>
-void upload(DevMem& d, const std::vector<T>& h) {
-  CK(d.alloc(h.size() * sizeof(T)));
-  if (!h.empty()) CK(cudaMemcpy(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
-}
-
-struct Vec3d {
-  double x, y, z;
-};
 
 // element stiffness K[a][b][m][l] = |t| (c_eps eps(phi_b e_l):eps(phi_a e_m) + c_div div(phi_b e_l) div(phi_a e_m))
 void element_stiffness(const Vec3d v[4], double c_eps, double c_div, double K[4][4][9]) {
@@ -305,102 +232,7 @@ MacroConsts<T> cast_consts(const MacroConsts<double>& c) {
   return o;
 }
 
-struct KeyHash {
-  size_t operator()(const std::array<int64_t, 3>& k) const {
-    size_t h = 1469598103934665603ull;
-    for (int q = 0; q < 3; ++q) h = (h ^ (size_t)k[q]) * 1099511628211ull;
-    return h;
-  }
-};
 
-struct LevelHost {
-  int level = 0, n = 0;
-  int64_t nt = 0, entries = 0;
-  std::vector<int32_t> tiles_int, tiles_all;
-  std::vector<int32_t> skel_ptr;
-  std::vector<SkelInc> skel_inc;
-  std::vector<int8_t> skel_dir;
-  std::vector<int8_t> skel_support;  // number of macro vertices spanning the node's primitive
-  std::vector<std::array<int64_t, 3>> skel_key;
-  std::vector<FaceItem> face_items;
-  std::vector<int32_t> face_nodes, ev_nodes, dir_nodes;
-  uint32_t face_mask[4] = {0, 0, 0, 0};
-  std::vector<uint8_t> mask;
-  std::vector<int64_t> entry_to_unique, unique_first;
-  std::vector<int8_t> unique_dir;
-  int64_t nunique = 0, nfree = 0;
-  // restriction lists for the skeleton nodes of this level as the coarse level
-  std::vector<int32_t> rptr;
-  std::vector<int64_t> rent;
-  std::vector<double> rw;
-  // device
-  DevMem d_tiles_int, d_tiles_all, d_skel_ptr, d_skel_inc, d_skel_dir, d_mask, d_first, d_e2u;
-  DevMem d_face_items, d_face_nodes, d_ev_nodes, d_dir_nodes, d_acc32, d_acc64;
-  DevMem d_rptr, d_rent, d_rw64, d_rw32;
-  DevMem d_mc64, d_mc32;
-  DevMem d_k64, d_k32;
-  std::vector<MacroStencil<double>> st64;
-  std::vector<MacroStencil<float>> st32;
-  LevelDev dev{};
-};
-
-}  // namespace
-
-struct hhg_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int64_t timeout_ms = 120000;
-  std::string err;
-  // macro mesh
-  std::vector<Vec3d> xyz;
-  std::vector<std::array<int64_t, 4>> tets;
-  std::set<std::array<int64_t, 3>> dir_faces;
-  std::set<std::array<int64_t, 2>> dir_edges;
-  std::set<int64_t> dir_verts;
-  bool have_mesh = false;
-  int level_min = 2, level_max = -1;
-  std::vector<std::unique_ptr<LevelHost>> levels;  // index = level
-  hhg_problem prob{};
-  bool have_problem = false;
-  bool have_coeff = false;
-  OpFlags flags{1, 0, 0};
-  DevMem scratch;   // reduction partials
-  DevMem scalar;    // device scalars
-  double* pinned = nullptr;
-  // host-buffer apply (hhg_apply_host)
-  DevMem hx, hy;
-  // kernel timing (hhg_profile): event pairs per part (0 interior, 1 skeleton)
-  bool prof = false;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::array<cudaEvent_t, 2>> prof_ev[2];
-  int64_t prof_launches[2] = {0, 0};
-  ~hhg_ctx() {
-    if (pinned) cudaFreeHost(pinned);
-    for (auto e : ev_pool) cudaEventDestroy(e);
-    for (int q = 0; q < 2; ++q)
-      for (auto& pr : prof_ev[q]) {
-        cudaEventDestroy(pr[0]);
-        cudaEventDestroy(pr[1]);
-      }
-  }
-  cudaEvent_t take_event() {
-    if (!ev_pool.empty()) {
-      cudaEvent_t e = ev_pool.back();
-      ev_pool.pop_back();
-      return e;
-    }
-    cudaEvent_t e;
-    cudaError_t r = cudaEventCreate(&e);
-    if (r != cudaSuccess) throw HhgError{HHG_ERR_CUDA, "cudaEventCreate failed"};
-    return e;
-  }
-  LevelHost& lv(int l) {
-    if (l < level_min || l > level_max || !levels[l]) THROW(HHG_ERR_ARG, "level %d not built", l);
-    return *levels[l];
-  }
-};
-
-namespace {
 
 void build_level(hhg_ctx* c, int level) {
   auto L = std::make_unique<LevelHost>();
@@ -647,147 +479,8 @@ void upload_level(hhg_ctx* c, LevelHost& L) {
   D.acc64 = L.d_acc64.as<double>();
 }
 
-int64_t max_partials(hhg_ctx* c) {
-  int64_t mx = 1024;
-  for (int l = c->level_min; l <= c->level_max; ++l) {
-    const LevelHost& L = *c->levels[l];
-    mx = std::max<int64_t>(mx, (int64_t)L.tiles_int.size() * (int64_t)c->tets.size() + (L.face_nodes.size() + 127) / 128 +
-                                   L.ev_nodes.size() + 8);
-  }
-  return mx;
-}
-
-void wait_stream(hhg_ctx* c) {
-  cudaEvent_t ev;
-  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-  cudaError_t e = cudaEventRecord(ev, c->stream);
-  if (e != cudaSuccess) {
-    cudaEventDestroy(ev);
-    CK(e);
-  }
-  const auto t0 = std::chrono::steady_clock::now();
-  while (true) {
-    e = cudaEventQuery(ev);
-    if (e == cudaSuccess) break;
-    if (e != cudaErrorNotReady) {
-      cudaEventDestroy(ev);
-      CK(e);
-    }
-    const auto ms =
-        std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
-    if (ms > c->timeout_ms) {
-      cudaEventDestroy(ev);
-      THROW(HHG_ERR_TIMEOUT, "stream did not finish within %lld ms", (long long)c->timeout_ms);
-    }
-    std::this_thread::sleep_for(std::chrono::microseconds(50));
-  }
-  cudaEventDestroy(ev);
-}
-
-// bounded wait that creates nothing: polls the stream itself
-void wait_stream_noalloc(hhg_ctx* c) {
-  const auto t0 = std::chrono::steady_clock::now();
-  while (true) {
-    const cudaError_t e = cudaStreamQuery(c->stream);
-    if (e == cudaSuccess) return;
-    if (e != cudaErrorNotReady) CK(e);
-    const auto ms =
-        std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
-    if (ms > c->timeout_ms) THROW(HHG_ERR_TIMEOUT, "stream did not finish within %lld ms", (long long)c->timeout_ms);
-    std::this_thread::sleep_for(std::chrono::microseconds(50));
-  }
-}
-
-template <typename F>
-hhg_status guard(hhg_ctx* c, F&& f) {
-  if (!c) return HHG_ERR_ARG;
-  try {
-    CK(cudaSetDevice(c->device));
-    f();
-    return HHG_OK;
-  } catch (const HhgError& e) {
-    c->err = e.msg;
-    return e.st;
-  } catch (const std::bad_alloc&) {
-    c->err = "host allocation failed";
-    return HHG_ERR_OOM;
-  } catch (...) {
-    c->err = "unknown error";
-    return HHG_ERR_STATE;
-  }
-}
-
-void need_ready(hhg_ctx* c, bool coeff) {
-  if (!c->have_mesh || c->level_max < 0) THROW(HHG_ERR_STATE, "mesh/levels not set");
-  if (!c->have_problem) THROW(HHG_ERR_STATE, "problem not set");
-  if (coeff && !c->have_coeff) THROW(HHG_ERR_STATE, "coefficient not set");
-}
-
-template <typename T>
-const T* kptr(LevelHost& L);
-template <>
-const double* kptr<double>(LevelHost& L) {
-  return L.d_k64.as<double>();
-}
-template <>
-const float* kptr<float>(LevelHost& L) {
-  return L.d_k32.as<float>();
-}
-template <typename T>
-const MacroStencil<T>* stencils(LevelHost& L);
-template <>
-const MacroStencil<double>* stencils<double>(LevelHost& L) {
-  return L.st64.data();
-}
-template <>
-const MacroStencil<float>* stencils<float>(LevelHost& L) {
-  return L.st32.data();
-}
-template <typename T>
-const MacroConsts<T>* consts_dev(LevelHost& L);
-template <>
-const MacroConsts<double>* consts_dev<double>(LevelHost& L) {
-  return L.d_mc64.as<MacroConsts<double>>();
-}
-template <>
-const MacroConsts<float>* consts_dev<float>(LevelHost& L) {
-  return L.d_mc32.as<MacroConsts<float>>();
-}
-
-template <typename T>
-void sweep(hhg_ctx* c, int level, OpKind op, SweepArgs<T> a, double* norm2) {
-  LevelHost& L = c->lv(level);
-  a.k = kptr<T>(L);
-  int64_t np = 0;
-  if (norm2) a.partial = c->scratch.as<double>();
-  if (!c->prof) {
-    CK(launch_sweep<T>(L.dev, stencils<T>(L), consts_dev<T>(L), op, c->flags, a, c->stream, 3, 0, &np));
-  } else {
-    int64_t off = 0;
-    for (int part = 0; part < 2; ++part) {
-      std::array<cudaEvent_t, 2> pr = {c->take_event(), c->take_event()};
-      CK(cudaEventRecord(pr[0], c->stream));
-      int64_t used = 0;
-      CK(launch_sweep<T>(L.dev, stencils<T>(L), consts_dev<T>(L), op, c->flags, a, c->stream, part + 1, off,
-                         &used));
-      CK(cudaEventRecord(pr[1], c->stream));
-      off += used;
-      c->prof_ev[part].push_back(pr);
-      c->prof_launches[part] += part == 0 ? (L.dev.ntiles_int > 0 ? L.dev.nmacro : 0)
-                                          : (L.dev.nface_items > 0) + (L.dev.nface_nodes > 0) + (L.dev.nev > 0) +
-                                                (L.dev.ndir > 0);
-    }
-    np = off;
-  }
-  if (norm2) {
-    CK(launch_reduce(c->scratch.as<double>(), np, c->scalar.as<double>(), c->stream));
-    CK(cudaMemcpyAsync(c->pinned, c->scalar.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    wait_stream(c);
-    *norm2 = c->pinned[0];
-  }
-}
-
 }  // namespace
+
 
 // ===========================================================================
 // C ABI

@@ -6,7 +6,7 @@
 
 namespace hhg {
 
-enum OpKind { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_CHEBY = 3 };
+enum OpKind { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_CHEBY = 3, OP_DIAG = 4 };
 
 // Flags of the operator variant, uniform per launch.
 struct OpFlags {
@@ -18,7 +18,8 @@ struct OpFlags {
 // Arguments of one stencil sweep.  Vectors are component-major over the level
 // (component stride = entries).  Scalars for the smoothers:
 //   JACOBI: x_out = x + omega * D^{-1} (f - A x)
-//   CHEBY:  d_out = rho1 * d + rho2 * D^{-1} (f - A x);  x_out = x + d_out
+//   CHEBY:  d_out = rho1 * d + rho2 * D^{-1} (f - A x);  x_out = x + d_out  (d may be null: 0)
+//   DIAG:   out = point diagonal of A (1 on Dirichlet rows)
 template <typename T>
 struct SweepArgs {
   const T* x;
@@ -79,5 +80,16 @@ int launch_gather(int64_t count, int comps, int64_t src_stride, int64_t dst_stri
                   T* dst, void* stream);  // dst[c*dst_stride + u] = src[c*src_stride + idx[u]]
 template <typename T>
 int launch_fill(int64_t n, T v, T* dst, void* stream);
+template <typename T>
+int launch_mul(int64_t n, const T* a, const T* b, T* out, void* stream);  // out = a * b
+template <typename T>
+int launch_recip(int64_t n, const T* a, T* out, void* stream);             // out = 1 / a
+int launch_add_f32_to_f64(int64_t n, const float* e, double* x, void* stream);  // x += e
+// unique-node vector of hashed values in [-1, 1), 0 on Dirichlet nodes
+template <typename T>
+int launch_hash_unique(int64_t U, int comps, const int8_t* udir, T* u, void* stream);
+// dst_u[idx[i]] = sum_j A[i*N + j] src_u[idx[j]]  (dense coarse solve)
+template <typename T>
+int launch_dense_matvec(int N, const T* A, const int64_t* idx, const T* src_u, T* dst_u, void* stream);
 
 }  // namespace hhg

@@ -1,0 +1,605 @@
+// libhhgs solvers: point-Jacobi / Chebyshev smoothing, geometric multigrid
+// V-cycles, (preconditioned) conjugate gradients and FP64 iterative refinement
+// around an FP32 multigrid-preconditioned CG.
+//
+// Sec. 5 of the paper solves with geometric multigrid V-cycles: matrix-free
+// linear interpolation between levels and its transpose as restriction, a
+// smoother on every level, and a coarse-grid solve on the mesh with one
+// interior node per macro.  Coarse operators are rediscretisations with the
+// injected nodal coefficient.  Here the smoother is point Jacobi or Chebyshev
+// (on D^-1 A, interval [lo, hi] * lambda_max with lambda_max from power
+// iterations), and the coarsest level (level 2) is solved exactly with a dense
+// inverse of its matrix restricted to the free degrees of freedom.
+#include "hhg_ctx.h"
+
+namespace {
+
+template <typename T>
+DevMem* work(LevelHost& L);
+template <>
+DevMem* work<double>(LevelHost& L) {
+  return L.w64;
+}
+template <>
+DevMem* work<float>(LevelHost& L) {
+  return L.w32;
+}
+template <typename T>
+DevMem& uvec(LevelHost& L);
+template <>
+DevMem& uvec<double>(LevelHost& L) {
+  return L.u64;
+}
+template <>
+DevMem& uvec<float>(LevelHost& L) {
+  return L.u32;
+}
+template <typename T>
+DevMem& dinv(LevelHost& L);
+template <>
+DevMem& dinv<double>(LevelHost& L) {
+  return L.dinv64;
+}
+template <>
+DevMem& dinv<float>(LevelHost& L) {
+  return L.dinv32;
+}
+template <typename T>
+DevMem& cinv(LevelHost& L);
+template <>
+DevMem& cinv<double>(LevelHost& L) {
+  return L.d_cinv64;
+}
+template <>
+DevMem& cinv<float>(LevelHost& L) {
+  return L.d_cinv32;
+}
+
+constexpr int NWORK = 12;
+
+template <typename T>
+void ensure_work(hhg_ctx* c, int l) {
+  LevelHost& L = c->lv(l);
+  DevMem* W = work<T>(L);
+  if (W[0].p) return;
+  for (int q = 0; q < NWORK; ++q) {
+    CK(W[q].alloc(3 * (size_t)L.entries * sizeof(T)));
+    CK(cudaMemsetAsync(W[q].p, 0, W[q].bytes, c->stream));
+  }
+  CK(uvec<T>(L).alloc(2 * 3 * (size_t)L.nunique * sizeof(T)));
+  CK(cudaMemsetAsync(uvec<T>(L).p, 0, uvec<T>(L).bytes, c->stream));
+  if (!L.d_udir.p) upload(L.d_udir, L.unique_dir);
+}
+
+template <typename T>
+double dot(hhg_ctx* c, int l, const T* a, const T* b) {
+  LevelHost& L = c->lv(l);
+  int64_t np = 0;
+  CK(launch_dot<T>(L.dev, 3, a, b, c->scratch.as<double>(), &np, c->stream));
+  CK(launch_reduce(c->scratch.as<double>(), np, c->scalar.as<double>(), c->stream));
+  CK(cudaMemcpyAsync(c->pinned, c->scalar.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  wait_stream(c);
+  return c->pinned[0];
+}
+
+template <typename T>
+void apply_op(hhg_ctx* c, int l, const T* x, T* y) {
+  SweepArgs<T> a{};
+  a.x = x;
+  a.out = y;
+  sweep<T>(c, l, OP_APPLY, a, nullptr);
+}
+
+template <typename T>
+double residual_op(hhg_ctx* c, int l, const T* f, const T* x, T* r, bool norm) {
+  SweepArgs<T> a{};
+  a.x = x;
+  a.f = f;
+  a.out = r;
+  double n2 = 0.0;
+  sweep<T>(c, l, OP_RESID, a, norm ? &n2 : nullptr);
+  return n2;
+}
+
+template <typename T>
+void compute_diag(hhg_ctx* c, int l) {
+  ensure_work<T>(c, l);
+  LevelHost& L = c->lv(l);
+  DevMem* W = work<T>(L);
+  SweepArgs<T> a{};
+  a.x = W[1].as<T>();  // read by the interface kernels, value irrelevant
+  a.out = W[0].as<T>();
+  sweep<T>(c, l, OP_DIAG, a, nullptr);
+  if (!dinv<T>(L).p) CK(dinv<T>(L).alloc(3 * (size_t)L.entries * sizeof(T)));
+  CK(launch_recip<T>(3 * L.entries, W[0].as<T>(), dinv<T>(L).template as<T>(), c->stream));
+}
+
+// lambda_max of D^{-1} A by power iterations from a hashed start vector (zero on
+// Dirichlet nodes), in FP64
+double power_lambda(hhg_ctx* c, int l, int iters) {
+  ensure_work<double>(c, l);
+  LevelHost& L = c->lv(l);
+  DevMem* W = work<double>(L);
+  double* v = W[0].as<double>();
+  double* y = W[1].as<double>();
+  double* u = uvec<double>(L).as<double>();
+  CK(launch_hash_unique<double>(L.nunique, 3, L.d_udir.as<int8_t>(), u, c->stream));
+  CK(launch_gather<double>(L.entries, 3, L.nunique, L.entries, L.d_e2u.as<int64_t>(), u, v, c->stream));
+  double lam = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    apply_op<double>(c, l, v, y);
+    CK(launch_mul<double>(3 * L.entries, y, L.dinv64.as<double>(), y, c->stream));
+    const double nv = dot<double>(c, l, v, v);
+    const double ny = dot<double>(c, l, y, y);
+    if (!(ny > 0.0) || !std::isfinite(ny)) THROW(HHG_ERR_NUMERIC, "power iteration failed on level %d", l);
+    lam = std::sqrt(ny / nv);
+    CK(launch_axpby<double>(3 * L.entries, 1.0 / std::sqrt(ny), y, 0.0, v, c->stream));
+  }
+  // leave the work vectors zero (the interface kernels read W[1] as a dummy input)
+  CK(cudaMemsetAsync(W[1].p, 0, W[1].bytes, c->stream));
+  return lam;
+}
+
+// dense inverse (Gauss-Jordan with partial pivoting), row-major N x N, FP64
+void invert_dense(std::vector<double>& A, int N) {
+  std::vector<double> I((size_t)N * N, 0.0);
+  for (int i = 0; i < N; ++i) I[(size_t)i * N + i] = 1.0;
+  for (int col = 0; col < N; ++col) {
+    int piv = col;
+    double best = std::fabs(A[(size_t)col * N + col]);
+    for (int r = col + 1; r < N; ++r)
+      if (std::fabs(A[(size_t)r * N + col]) > best) {
+        best = std::fabs(A[(size_t)r * N + col]);
+        piv = r;
+      }
+    if (!(best > 0.0)) THROW(HHG_ERR_NUMERIC, "singular coarse matrix");
+    if (piv != col)
+      for (int q = 0; q < N; ++q) {
+        std::swap(A[(size_t)piv * N + q], A[(size_t)col * N + q]);
+        std::swap(I[(size_t)piv * N + q], I[(size_t)col * N + q]);
+      }
+    const double inv = 1.0 / A[(size_t)col * N + col];
+    for (int q = 0; q < N; ++q) {
+      A[(size_t)col * N + q] *= inv;
+      I[(size_t)col * N + q] *= inv;
+    }
+    for (int r = 0; r < N; ++r) {
+      if (r == col) continue;
+      const double f = A[(size_t)r * N + col];
+      if (f == 0.0) continue;
+      for (int q = 0; q < N; ++q) {
+        A[(size_t)r * N + q] -= f * A[(size_t)col * N + q];
+        I[(size_t)r * N + q] -= f * I[(size_t)col * N + q];
+      }
+    }
+  }
+  A.swap(I);
+}
+
+constexpr int MAX_COARSE_DOFS = 3000;
+
+// coarse matrix by applying the operator to unit vectors of the free DoFs
+void coarse_setup(hhg_ctx* c) {
+  const int l = c->level_min;
+  ensure_work<double>(c, l);
+  ensure_work<float>(c, l);
+  LevelHost& L = c->lv(l);
+  std::vector<int64_t> cdof;
+  for (int64_t u = 0; u < L.nunique; ++u)
+    if (!L.unique_dir[u])
+      for (int q = 0; q < 3; ++q) cdof.push_back(q * L.nunique + u);
+  const int N = (int)cdof.size();
+  L.ncdof = N;
+  if (N == 0) return;
+  if (N > MAX_COARSE_DOFS) {
+    L.ncdof = -N;  // too large for the dense coarse solve
+    return;
+  }
+  DevMem* W = work<double>(L);
+  double* u = uvec<double>(L).as<double>();
+  std::vector<double> A((size_t)N * N), col(3 * L.nunique);
+  const double one = 1.0;
+  for (int j = 0; j < N; ++j) {
+    CK(cudaMemsetAsync(u, 0, 3 * L.nunique * sizeof(double), c->stream));
+    CK(cudaMemcpyAsync(u + cdof[j], &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(launch_gather<double>(L.entries, 3, L.nunique, L.entries, L.d_e2u.as<int64_t>(), u, W[0].as<double>(),
+                             c->stream));
+    apply_op<double>(c, l, W[0].as<double>(), W[1].as<double>());
+    CK(launch_gather<double>(L.nunique, 3, L.entries, L.nunique, L.d_first.as<int64_t>(), W[1].as<double>(), u,
+                             c->stream));
+    CK(cudaMemcpyAsync(col.data(), u, col.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    wait_stream(c);
+    for (int i = 0; i < N; ++i) A[(size_t)i * N + j] = col[cdof[i]];
+  }
+  CK(cudaMemsetAsync(W[0].p, 0, W[0].bytes, c->stream));
+  CK(cudaMemsetAsync(W[1].p, 0, W[1].bytes, c->stream));
+  invert_dense(A, N);
+  std::vector<float> A32(A.begin(), A.end());
+  upload(L.d_cdof, cdof);
+  upload(L.d_cinv64, A);
+  upload(L.d_cinv32, A32);
+}
+
+template <typename T>
+void coarse_solve(hhg_ctx* c, int l, const T* f, T* x) {
+  LevelHost& L = c->lv(l);
+  if (L.ncdof < 0) THROW(HHG_ERR_UNSUPPORTED, "coarse level has %d DoFs (dense solve limit %d)", -L.ncdof,
+                         MAX_COARSE_DOFS);
+  T* us = uvec<T>(L).template as<T>();
+  T* ud = us + 3 * L.nunique;
+  CK(launch_gather<T>(L.nunique, 3, L.entries, L.nunique, L.d_first.as<int64_t>(), f, us, c->stream));
+  CK(cudaMemsetAsync(ud, 0, 3 * L.nunique * sizeof(T), c->stream));
+  if (L.ncdof > 0)
+    CK(launch_dense_matvec<T>(L.ncdof, cinv<T>(L).template as<T>(), L.d_cdof.as<int64_t>(), us, ud, c->stream));
+  CK(launch_gather<T>(L.entries, 3, L.nunique, L.entries, L.d_e2u.as<int64_t>(), ud, x, c->stream));
+}
+
+template <typename T>
+void smooth(hhg_ctx* c, int l, int steps, const T* f, T* x) {
+  if (steps <= 0) return;
+  ensure_work<T>(c, l);
+  LevelHost& L = c->lv(l);
+  DevMem* W = work<T>(L);
+  T* cur = x;
+  T* oth = W[3].as<T>();
+  if (c->mg.smoother == HHG_SMOOTH_CHEBYSHEV) {
+    if (!L.lambda_set) THROW(HHG_ERR_STATE, "lambda_max of level %d unknown (call hhg_mg_setup)", l);
+    const double a = c->mg.cheby_lo * L.lambda_max, b = c->mg.cheby_hi * L.lambda_max;
+    const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    const T* dprev = nullptr;
+    T* dnext = W[4].as<T>();
+    for (int s = 0; s < steps; ++s) {
+      SweepArgs<T> a{};
+      if (s == 0) {
+        a.rho1 = 0.0;
+        a.rho2 = 1.0 / theta;
+      } else {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        a.rho1 = rn * rho;
+        a.rho2 = 2.0 * rn / delta;
+        rho = rn;
+      }
+      a.x = cur;
+      a.f = f;
+      a.d = dprev;
+      a.out = oth;
+      a.dout = dnext;
+      sweep<T>(c, l, OP_CHEBY, a, nullptr);
+      std::swap(cur, oth);
+      dprev = dnext;
+      dnext = dnext == W[4].as<T>() ? W[5].as<T>() : W[4].as<T>();
+    }
+  } else {
+    for (int s = 0; s < steps; ++s) {
+      SweepArgs<T> a{};
+      a.x = cur;
+      a.f = f;
+      a.out = oth;
+      a.omega = c->mg.omega;
+      sweep<T>(c, l, OP_JACOBI, a, nullptr);
+      std::swap(cur, oth);
+    }
+  }
+  if (cur != x) CK(cudaMemcpyAsync(x, cur, 3 * L.entries * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+}
+
+template <typename T>
+void restrict_op(hhg_ctx* c, int lf, const T* rf, T* rc);
+template <>
+void restrict_op<double>(hhg_ctx* c, int lf, const double* rf, double* rc) {
+  LevelHost& F = c->lv(lf);
+  LevelHost& C = c->lv(lf - 1);
+  CK(launch_restrict<double>(F.dev, C.dev, C.d_rptr.as<int32_t>(), C.d_rent.as<int64_t>(), C.d_rw64.as<double>(), rf,
+                             rc, c->stream));
+}
+template <>
+void restrict_op<float>(hhg_ctx* c, int lf, const float* rf, float* rc) {
+  LevelHost& F = c->lv(lf);
+  LevelHost& C = c->lv(lf - 1);
+  CK(launch_restrict<float>(F.dev, C.dev, C.d_rptr.as<int32_t>(), C.d_rent.as<int64_t>(), C.d_rw32.as<float>(), rf,
+                            rc, c->stream));
+}
+
+template <typename T>
+void vcycle(hhg_ctx* c, int l, const T* f, T* x) {
+  if (l == c->level_min) {
+    coarse_solve<T>(c, l, f, x);
+    return;
+  }
+  ensure_work<T>(c, l);
+  ensure_work<T>(c, l - 1);
+  LevelHost& L = c->lv(l);
+  LevelHost& C = c->lv(l - 1);
+  DevMem* W = work<T>(L);
+  DevMem* Wc = work<T>(C);
+  smooth<T>(c, l, c->mg.pre, f, x);
+  residual_op<T>(c, l, f, x, W[0].as<T>(), false);
+  restrict_op<T>(c, l, W[0].as<T>(), Wc[1].as<T>());
+  CK(cudaMemsetAsync(Wc[2].p, 0, 3 * C.entries * sizeof(T), c->stream));
+  vcycle<T>(c, l - 1, Wc[1].as<T>(), Wc[2].as<T>());
+  CK(launch_prolong_add<T>(L.dev, C.dev, Wc[2].as<T>(), x, c->stream));
+  smooth<T>(c, l, c->mg.post, f, x);
+}
+
+template <typename T>
+void precondition(hhg_ctx* c, int l, bool mg, const T* r, T* z) {
+  LevelHost& L = c->lv(l);
+  if (mg) {
+    CK(cudaMemsetAsync(z, 0, 3 * L.entries * sizeof(T), c->stream));
+    vcycle<T>(c, l, r, z);
+  } else {
+    CK(launch_mul<T>(3 * L.entries, dinv<T>(L).template as<T>(), r, z, c->stream));
+  }
+}
+
+struct CgResult {
+  int iterations = 0;
+  double r0 = 0.0, rel = 0.0;
+  bool converged = false;
+};
+
+// (preconditioned) CG on A x = f, x updated in place; uses work vectors 6..9
+template <typename T>
+CgResult pcg(hhg_ctx* c, int l, bool mg, const T* f, T* x, double rtol, int max_iter) {
+  ensure_work<T>(c, l);
+  LevelHost& L = c->lv(l);
+  DevMem* W = work<T>(L);
+  T* r = W[6].as<T>();
+  T* z = W[7].as<T>();
+  T* p = W[8].as<T>();
+  T* q = W[9].as<T>();
+  const int64_t n = 3 * L.entries;
+  CgResult res;
+  const double r0 = residual_op<T>(c, l, f, x, r, true);
+  res.r0 = std::sqrt(r0);
+  if (!std::isfinite(r0)) THROW(HHG_ERR_NUMERIC, "non-finite initial residual");
+  if (r0 == 0.0) {
+    res.converged = true;
+    return res;
+  }
+  precondition<T>(c, l, mg, r, z);
+  CK(cudaMemcpyAsync(p, z, n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+  double rz = dot<T>(c, l, r, z);
+  double rr = r0;
+  for (int it = 1; it <= max_iter; ++it) {
+    apply_op<T>(c, l, p, q);
+    const double pq = dot<T>(c, l, p, q);
+    if (!(pq > 0.0) || !std::isfinite(pq)) THROW(HHG_ERR_NUMERIC, "CG breakdown (p.Ap = %g)", pq);
+    const double alpha = rz / pq;
+    CK(launch_axpby<T>(n, (T)alpha, p, (T)1, x, c->stream));
+    CK(launch_axpby<T>(n, (T)(-alpha), q, (T)1, r, c->stream));
+    rr = dot<T>(c, l, r, r);
+    res.iterations = it;
+    if (!std::isfinite(rr)) THROW(HHG_ERR_NUMERIC, "non-finite residual");
+    if (std::sqrt(rr / r0) <= rtol) {
+      res.converged = true;
+      break;
+    }
+    precondition<T>(c, l, mg, r, z);
+    const double rzn = dot<T>(c, l, r, z);
+    const double beta = rzn / rz;
+    rz = rzn;
+    CK(launch_axpby<T>(n, (T)1, z, (T)beta, p, c->stream));
+  }
+  res.rel = std::sqrt(rr / r0);
+  return res;
+}
+
+void mg_check(hhg_ctx* c) {
+  need_ready(c, true);
+  if (!c->mg_ready) THROW(HHG_ERR_STATE, "call hhg_mg_setup after setting the coefficient");
+}
+
+template <typename F>
+hhg_status dispatch(hhg_ctx* c, hhg_dtype dt, F&& f) {
+  return guard(c, [&] {
+    if (dt == HHG_F64)
+      f((double*)nullptr);
+    else if (dt == HHG_F32)
+      f((float*)nullptr);
+    else
+      THROW(HHG_ERR_ARG, "dtype");
+  });
+}
+
+}  // namespace
+
+extern "C" {
+
+hhg_status hhg_set_mg_params(hhg_ctx* c, const hhg_mg_params* p) {
+  return guard(c, [&] {
+    if (!p) THROW(HHG_ERR_ARG, "null params");
+    if (p->smoother != HHG_SMOOTH_JACOBI && p->smoother != HHG_SMOOTH_CHEBYSHEV) THROW(HHG_ERR_ARG, "smoother");
+    if (p->pre < 0 || p->post < 0 || p->pre + p->post == 0) THROW(HHG_ERR_ARG, "smoothing steps");
+    if (!(p->omega > 0.0 && p->omega < 2.0)) THROW(HHG_ERR_ARG, "omega");
+    if (!(p->cheby_lo > 0.0 && p->cheby_hi > p->cheby_lo)) THROW(HHG_ERR_ARG, "Chebyshev interval");
+    if (p->power_iters < 1) THROW(HHG_ERR_ARG, "power_iters");
+    c->mg = *p;
+  });
+}
+
+hhg_status hhg_mg_setup(hhg_ctx* c) {
+  return guard(c, [&] {
+    need_ready(c, true);
+    for (int l = c->level_min; l <= c->level_max; ++l) {
+      compute_diag<double>(c, l);
+      compute_diag<float>(c, l);
+      LevelHost& L = c->lv(l);
+      if (!L.lambda_set) {
+        L.lambda_max = power_lambda(c, l, c->mg.power_iters);
+        L.lambda_set = true;
+      }
+    }
+    coarse_setup(c);
+    wait_stream(c);
+    c->mg_ready = true;
+  });
+}
+
+hhg_status hhg_get_lambda_max(hhg_ctx* c, int level, double* lambda) {
+  return guard(c, [&] {
+    LevelHost& L = c->lv(level);
+    if (!lambda) THROW(HHG_ERR_ARG, "null output");
+    if (!L.lambda_set) THROW(HHG_ERR_STATE, "lambda_max not computed");
+    *lambda = L.lambda_max;
+  });
+}
+
+hhg_status hhg_set_lambda_max(hhg_ctx* c, int level, double lambda) {
+  return guard(c, [&] {
+    LevelHost& L = c->lv(level);
+    if (!(lambda > 0.0)) THROW(HHG_ERR_ARG, "lambda must be positive");
+    L.lambda_max = lambda;
+    L.lambda_set = true;
+  });
+}
+
+hhg_status hhg_diagonal(hhg_ctx* c, int level, hhg_dtype dt, void* d) {
+  return dispatch(c, dt, [&](auto* tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    need_ready(c, true);
+    if (!d) THROW(HHG_ERR_ARG, "null output");
+    ensure_work<T>(c, level);
+    LevelHost& L = c->lv(level);
+    SweepArgs<T> a{};
+    a.x = work<T>(L)[1].template as<T>();
+    a.out = (T*)d;
+    sweep<T>(c, level, OP_DIAG, a, nullptr);
+  });
+}
+
+hhg_status hhg_smooth(hhg_ctx* c, int level, hhg_dtype dt, int steps, const void* f, void* x) {
+  return dispatch(c, dt, [&](auto* tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    mg_check(c);
+    if (!f || !x || steps < 0) THROW(HHG_ERR_ARG, "bad arguments");
+    smooth<T>(c, level, steps, (const T*)f, (T*)x);
+  });
+}
+
+hhg_status hhg_prolongate_add(hhg_ctx* c, int fine, hhg_dtype dt, const void* xc, void* xf) {
+  return dispatch(c, dt, [&](auto* tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    need_ready(c, false);
+    if (fine <= c->level_min) THROW(HHG_ERR_ARG, "fine level must be above the coarsest level");
+    if (!xc || !xf) THROW(HHG_ERR_ARG, "null buffer");
+    CK(launch_prolong_add<T>(c->lv(fine).dev, c->lv(fine - 1).dev, (const T*)xc, (T*)xf, c->stream));
+  });
+}
+
+hhg_status hhg_restrict(hhg_ctx* c, int fine, hhg_dtype dt, const void* rf, void* rc) {
+  return dispatch(c, dt, [&](auto* tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    need_ready(c, false);
+    if (fine <= c->level_min) THROW(HHG_ERR_ARG, "fine level must be above the coarsest level");
+    if (!rf || !rc) THROW(HHG_ERR_ARG, "null buffer");
+    restrict_op<T>(c, fine, (const T*)rf, (T*)rc);
+  });
+}
+
+hhg_status hhg_vcycle(hhg_ctx* c, int level, hhg_dtype dt, const void* f, void* x) {
+  return dispatch(c, dt, [&](auto* tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    mg_check(c);
+    if (!f || !x) THROW(HHG_ERR_ARG, "null buffer");
+    c->lv(level);
+    vcycle<T>(c, level, (const T*)f, (T*)x);
+  });
+}
+
+hhg_status hhg_solve(hhg_ctx* c, const hhg_solve_opts* o, const void* f, void* x, hhg_solve_report* rep) {
+  bool not_converged = false;
+  hhg_status st = guard(c, [&] {
+    if (!o || !f || !x) THROW(HHG_ERR_ARG, "null argument");
+    need_ready(c, true);
+    const int l = o->level;
+    c->lv(l);
+    if (!(o->rtol > 0.0) || o->max_iter < 1) THROW(HHG_ERR_ARG, "rtol / max_iter");
+    if (o->method != HHG_SOLVE_PCG_JACOBI) mg_check(c);
+    const auto t0 = std::chrono::steady_clock::now();
+    hhg_solve_report R{};
+    if (o->method == HHG_SOLVE_PCG_JACOBI || o->method == HHG_SOLVE_MG_CG) {
+      const bool mg = o->method == HHG_SOLVE_MG_CG;
+      if (o->dt == HHG_F64) {
+        if (!mg && !c->lv(l).dinv64.p) compute_diag<double>(c, l);
+        CgResult cr = pcg<double>(c, l, mg, (const double*)f, (double*)x, o->rtol, o->max_iter);
+        R.iterations = cr.iterations;
+        R.residual0 = cr.r0;
+        R.rel_residual = cr.rel;
+        R.converged = cr.converged;
+      } else if (o->dt == HHG_F32) {
+        if (!mg && !c->lv(l).dinv32.p) compute_diag<float>(c, l);
+        CgResult cr = pcg<float>(c, l, mg, (const float*)f, (float*)x, o->rtol, o->max_iter);
+        R.iterations = cr.iterations;
+        R.residual0 = cr.r0;
+        R.rel_residual = cr.rel;
+        R.converged = cr.converged;
+      } else {
+        THROW(HHG_ERR_ARG, "dtype");
+      }
+    } else if (o->method == HHG_SOLVE_MG) {
+      auto run = [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        ensure_work<T>(c, l);
+        T* r = work<T>(c->lv(l))[6].template as<T>();
+        const double r0 = residual_op<T>(c, l, (const T*)f, (const T*)x, r, true);
+        R.residual0 = std::sqrt(r0);
+        double rr = r0;
+        for (int it = 1; it <= o->max_iter && r0 > 0.0; ++it) {
+          vcycle<T>(c, l, (const T*)f, (T*)x);
+          rr = residual_op<T>(c, l, (const T*)f, (const T*)x, r, true);
+          R.iterations = it;
+          if (!std::isfinite(rr)) THROW(HHG_ERR_NUMERIC, "non-finite residual");
+          if (std::sqrt(rr / r0) <= o->rtol) break;
+        }
+        R.rel_residual = r0 > 0.0 ? std::sqrt(rr / r0) : 0.0;
+        R.converged = R.rel_residual <= o->rtol;
+      };
+      if (o->dt == HHG_F64)
+        run((double*)nullptr);
+      else if (o->dt == HHG_F32)
+        run((float*)nullptr);
+      else
+        THROW(HHG_ERR_ARG, "dtype");
+    } else if (o->method == HHG_SOLVE_IR_MG_CG) {
+      if (o->dt != HHG_F64) THROW(HHG_ERR_ARG, "iterative refinement needs FP64 f and x");
+      if (!(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || o->inner_max_iter < 1) THROW(HHG_ERR_ARG, "inner tol");
+      ensure_work<double>(c, l);
+      ensure_work<float>(c, l);
+      LevelHost& L = c->lv(l);
+      const int64_t n = 3 * L.entries;
+      double* r64 = work<double>(L)[10].as<double>();
+      float* r32 = work<float>(L)[10].as<float>();
+      float* e32 = work<float>(L)[11].as<float>();
+      const double r0 = residual_op<double>(c, l, (const double*)f, (const double*)x, r64, true);
+      R.residual0 = std::sqrt(r0);
+      double rr = r0;
+      for (int it = 1; it <= o->max_iter && r0 > 0.0 && std::sqrt(rr / r0) > o->rtol; ++it) {
+        CK(launch_convert<double, float>(n, r64, r32, c->stream));
+        CK(cudaMemsetAsync(e32, 0, n * sizeof(float), c->stream));
+        CgResult cr = pcg<float>(c, l, true, r32, e32, o->inner_rtol, o->inner_max_iter);
+        R.inner_iterations += cr.iterations;
+        CK(launch_add_f32_to_f64(n, e32, (double*)x, c->stream));
+        rr = residual_op<double>(c, l, (const double*)f, (const double*)x, r64, true);
+        R.iterations = it;
+        if (!std::isfinite(rr)) THROW(HHG_ERR_NUMERIC, "non-finite residual");
+      }
+      R.rel_residual = r0 > 0.0 ? std::sqrt(rr / r0) : 0.0;
+      R.converged = R.rel_residual <= o->rtol;
+    } else {
+      THROW(HHG_ERR_ARG, "method");
+    }
+    wait_stream(c);
+    R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rep) *rep = R;
+    not_converged = !R.converged;
+  });
+  if (st == HHG_OK && not_converged) {
+    c->err = "maximum number of iterations reached";
+    return HHG_ERR_NOT_CONVERGED;
+  }
+  return st;
+}
+
+}  // extern "C"

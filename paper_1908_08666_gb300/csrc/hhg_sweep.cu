@@ -51,6 +51,10 @@ __device__ __forceinline__ void epilogue(const SweepArgs<T>& a, int64_t e, int64
     a.out[e] = ax;
     a.out[e + E] = ay;
     a.out[e + 2 * E] = az;
+  } else if (OP == OP_DIAG) {
+    a.out[e] = dgx;
+    a.out[e + E] = dgy;
+    a.out[e + 2 * E] = dgz;
   } else {
     const T rx = a.f[e] - ax, ry = a.f[e + E] - ay, rz = a.f[e + 2 * E] - az;
     if (OP == OP_RESID) {
@@ -63,11 +67,11 @@ __device__ __forceinline__ void epilogue(const SweepArgs<T>& a, int64_t e, int64
       a.out[e] = x0 + om * rx / dgx;
       a.out[e + E] = y0 + om * ry / dgy;
       a.out[e + 2 * E] = z0 + om * rz / dgz;
-    } else {  // OP_CHEBY
+    } else if (OP == OP_CHEBY) {
       const T r1 = (T)a.rho1, r2c = (T)a.rho2;
-      const T ux = r1 * a.d[e] + r2c * rx / dgx;
-      const T uy = r1 * a.d[e + E] + r2c * ry / dgy;
-      const T uz = r1 * a.d[e + 2 * E] + r2c * rz / dgz;
+      const T ux = (a.d ? r1 * a.d[e] : (T)0) + r2c * rx / dgx;
+      const T uy = (a.d ? r1 * a.d[e + E] : (T)0) + r2c * ry / dgy;
+      const T uz = (a.d ? r1 * a.d[e + 2 * E] : (T)0) + r2c * rz / dgz;
       a.dout[e] = ux;
       a.dout[e + E] = uy;
       a.dout[e + 2 * E] = uz;
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(TILE_I* TILE_J) k_interior(const LevelDev L, c
         ay += wpz * dx[d] - wpx * dz[d] + wmz * dx[e] - wmx * dz[e];
         az += wpx * dy[d] - wpy * dx[d] + wmx * dy[e] - wmy * dx[e];
       }
-      if (OP == OP_JACOBI || OP == OP_CHEBY) {
+      if (OP == OP_JACOBI || OP == OP_CHEBY || OP == OP_DIAG) {
         const T ks = khp + khm;
         dgx -= ks * S[0];
         dgy -= ks * S[1];
@@ -462,6 +466,10 @@ __global__ void __launch_bounds__(128) k_dirichlet(const LevelDev L, const Sweep
       a.out[e] = 0;
       a.out[e + E] = 0;
       a.out[e + 2 * E] = 0;
+    } else if (OP == OP_DIAG) {
+      a.out[e] = 1;
+      a.out[e + E] = 1;
+      a.out[e + 2 * E] = 1;
     } else {
       a.out[e] = x0;
       a.out[e + E] = y0;
@@ -551,6 +559,7 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
       case OP_RESID: k_interior<T, OP_RESID><<<L.ntiles_int, blk, 0, s>>>(L, st_host[m], m, fl, am); break;
       case OP_JACOBI: k_interior<T, OP_JACOBI><<<L.ntiles_int, blk, 0, s>>>(L, st_host[m], m, fl, am); break;
       case OP_CHEBY: k_interior<T, OP_CHEBY><<<L.ntiles_int, blk, 0, s>>>(L, st_host[m], m, fl, am); break;
+      case OP_DIAG: k_interior<T, OP_DIAG><<<L.ntiles_int, blk, 0, s>>>(L, st_host[m], m, fl, am); break;
     }
     used += L.ntiles_int;
   }
@@ -568,6 +577,7 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
         case OP_RESID: k_face_finalize<T, OP_RESID><<<nb, 128, 0, s>>>(L, am); break;
         case OP_JACOBI: k_face_finalize<T, OP_JACOBI><<<nb, 128, 0, s>>>(L, am); break;
         case OP_CHEBY: k_face_finalize<T, OP_CHEBY><<<nb, 128, 0, s>>>(L, am); break;
+        case OP_DIAG: k_face_finalize<T, OP_DIAG><<<nb, 128, 0, s>>>(L, am); break;
       }
       used += nb;
     }
@@ -580,6 +590,7 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
         case OP_RESID: k_skeleton_ev<T, OP_RESID><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
         case OP_JACOBI: k_skeleton_ev<T, OP_JACOBI><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
         case OP_CHEBY: k_skeleton_ev<T, OP_CHEBY><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
+        case OP_DIAG: k_skeleton_ev<T, OP_DIAG><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
       }
       used += nb;
     }
@@ -590,6 +601,7 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
         case OP_RESID: k_dirichlet<T, OP_RESID><<<nb, 128, 0, s>>>(L, a); break;
         case OP_JACOBI: k_dirichlet<T, OP_JACOBI><<<nb, 128, 0, s>>>(L, a); break;
         case OP_CHEBY: k_dirichlet<T, OP_CHEBY><<<nb, 128, 0, s>>>(L, a); break;
+        case OP_DIAG: k_dirichlet<T, OP_DIAG><<<nb, 128, 0, s>>>(L, a); break;
       }
     }
   }

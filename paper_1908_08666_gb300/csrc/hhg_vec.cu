@@ -162,6 +162,49 @@ __global__ void k_fill(int64_t n, T v, T* __restrict__ d) {
     d[e] = v;
 }
 
+template <typename T>
+__global__ void k_mul(int64_t n, const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = a[e] * b[e];
+}
+
+template <typename T>
+__global__ void k_recip(int64_t n, const T* __restrict__ a, T* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (T)1 / a[e];
+}
+
+__global__ void k_add_f32_to_f64(int64_t n, const float* __restrict__ e32, double* __restrict__ x) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    x[e] += (double)e32[e];
+}
+
+// splitmix64 of (node, component): a deterministic start vector that depends on the
+// unique node only, so every copy of a skeleton node gets the same value
+template <typename T>
+__global__ void k_hash_unique(int64_t U, int comps, const int8_t* __restrict__ udir, T* __restrict__ u) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < U; q += (int64_t)gridDim.x * blockDim.x) {
+    for (int c = 0; c < comps; ++c) {
+      uint64_t z = (uint64_t)(q * comps + c) + 0x9E3779B97F4A7C15ull;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z = z ^ (z >> 31);
+      const double v = (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+      u[c * U + q] = udir[q] ? (T)0 : (T)v;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_dense_matvec(int N, const T* __restrict__ A, const int64_t* __restrict__ idx,
+                               const T* __restrict__ src, T* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  T acc = 0;
+  for (int j = 0; j < N; ++j) acc += A[(int64_t)i * N + j] * src[idx[j]];
+  dst[idx[i]] = acc;
+}
+
 inline int grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
   if (g > 152 * 16) g = 152 * 16;
@@ -237,6 +280,35 @@ int launch_fill(int64_t n, T v, T* dst, void* stream) {
   return (int)cudaGetLastError();
 }
 
+template <typename T>
+int launch_mul(int64_t n, const T* a, const T* b, T* out, void* stream) {
+  k_mul<T><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(n, a, b, out);
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_recip(int64_t n, const T* a, T* out, void* stream) {
+  k_recip<T><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(n, a, out);
+  return (int)cudaGetLastError();
+}
+
+int launch_add_f32_to_f64(int64_t n, const float* e, double* x, void* stream) {
+  k_add_f32_to_f64<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(n, e, x);
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_hash_unique(int64_t U, int comps, const int8_t* udir, T* u, void* stream) {
+  k_hash_unique<T><<<grid_for(U, 256), 256, 0, (cudaStream_t)stream>>>(U, comps, udir, u);
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_dense_matvec(int N, const T* A, const int64_t* idx, const T* src_u, T* dst_u, void* stream) {
+  k_dense_matvec<T><<<(N + 127) / 128, 128, 0, (cudaStream_t)stream>>>(N, A, idx, src_u, dst_u);
+  return (int)cudaGetLastError();
+}
+
 #define HHG_INST(T)                                                                                              \
   template int launch_dot<T>(const LevelDev&, int, const T*, const T*, double*, int64_t*, void*);               \
   template int launch_prolong_add<T>(const LevelDev&, const LevelDev&, const T*, T*, void*);                     \
@@ -245,7 +317,11 @@ int launch_fill(int64_t n, T v, T* dst, void* stream) {
   template int launch_inject<T>(const LevelDev&, const LevelDev&, const T*, T*, void*);                          \
   template int launch_axpby<T>(int64_t, T, const T*, T, T*, void*);                                              \
   template int launch_gather<T>(int64_t, int, int64_t, int64_t, const int64_t*, const T*, T*, void*);            \
-  template int launch_fill<T>(int64_t, T, T*, void*);
+  template int launch_fill<T>(int64_t, T, T*, void*);                                                           \
+  template int launch_mul<T>(int64_t, const T*, const T*, T*, void*);                                           \
+  template int launch_recip<T>(int64_t, const T*, T*, void*);                                                    \
+  template int launch_hash_unique<T>(int64_t, int, const int8_t*, T*, void*);                                    \
+  template int launch_dense_matvec<T>(int, const T*, const int64_t*, const T*, T*, void*);
 HHG_INST(float)
 HHG_INST(double)
 template int launch_convert<double, float>(int64_t, const double*, float*, void*);

@@ -32,6 +32,32 @@ class Ctx:
         first[self.e2u[::-1]] = np.arange(self.E)[::-1]
         self.coords_u = self.coords_e[first]
 
+    def maps(self, level):
+        """(coords_u, e2u, udir, E, U) of any level."""
+        E, U, _ = B.hhg_num_nodes(self.h, level)
+        ce = B.hhg_entry_coords(self.h, level)
+        e2u, udir = B.hhg_entry_to_unique(self.h, level)
+        first = np.full(U, -1, dtype=np.int64)
+        first[e2u[::-1]] = np.arange(E)[::-1]
+        return ce[first], e2u, udir, E, U
+
+    def to_lib_level(self, level, unique_vals, dtype, comps=3):
+        t = self.torch
+        E, U, _ = B.hhg_num_nodes(self.h, level)
+        u = np.asarray(unique_vals, dtype=np.float64).reshape(U, comps).T.copy()
+        src = self.dev(u.reshape(-1), dtype)
+        dst = t.empty(comps * E, dtype=dtype, device="cuda")
+        B.hhg_scatter_unique(self.h, level, B.F64 if dtype == t.float64 else B.F32, comps, src, dst)
+        return dst
+
+    def from_lib_level(self, level, field, comps=3):
+        t = self.torch
+        E, U, _ = B.hhg_num_nodes(self.h, level)
+        dst = t.empty(comps * U, dtype=field.dtype, device="cuda")
+        B.hhg_gather_unique(self.h, level, B.F64 if field.dtype == t.float64 else B.F32, comps, field, dst)
+        t.cuda.synchronize()
+        return dst.double().cpu().numpy().reshape(comps, U).T.copy()
+
     def close(self):
         if self.h:
             B.hhg_destroy(self.h)
