@@ -90,7 +90,7 @@ struct KeyHash {
 struct LevelHost {
   int level = 0, n = 0;
   int64_t nt = 0, entries = 0;
-  std::vector<int32_t> tiles_int, tiles_all;
+  std::vector<int32_t> tiles_int, tiles_all, tiles_lin;
   std::vector<int32_t> skel_ptr;
   std::vector<SkelInc> skel_inc;
   std::vector<int8_t> skel_dir;
@@ -108,7 +108,7 @@ struct LevelHost {
   std::vector<int64_t> rent;
   std::vector<double> rw;
   // device
-  DevMem d_tiles_int, d_tiles_all, d_skel_ptr, d_skel_inc, d_skel_dir, d_mask, d_first, d_e2u;
+  DevMem d_tiles_int, d_tiles_all, d_tiles_lin, d_skel_ptr, d_skel_inc, d_skel_dir, d_mask, d_first, d_e2u;
   DevMem d_face_items, d_face_nodes, d_ev_nodes, d_dir_nodes, d_acc32, d_acc64;
   DevMem d_rptr, d_rent, d_rw64, d_rw32;
   DevMem d_mc64, d_mc32;
@@ -198,7 +198,7 @@ inline int64_t max_partials(hhg_ctx* c) {
   int64_t mx = 1024;
   for (int l = c->level_min; l <= c->level_max; ++l) {
     const LevelHost& L = *c->levels[l];
-    mx = std::max<int64_t>(mx, (int64_t)L.tiles_int.size() * (int64_t)c->tets.size() + (L.face_nodes.size() + 127) / 128 +
+    mx = std::max<int64_t>(mx, (int64_t)L.tiles_lin.size() * (int64_t)c->tets.size() + (L.face_nodes.size() + 127) / 128 +
                                    L.ev_nodes.size() + 8);
   }
   return mx;

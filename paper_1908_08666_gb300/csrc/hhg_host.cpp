@@ -249,6 +249,13 @@ void build_level(hhg_ctx* c, int level) {
   for (int k = 0; k <= n; ++k)
     for (int j0 = 0; j0 <= n - k; j0 += TILE_J)
       for (int i0 = 0; i0 <= n - k - j0; i0 += TILE_I) L->tiles_all.push_back((k << 20) | (j0 << 10) | i0);
+  // interior points of slice k, enumerated row by row (j = 1..M-1, i = 1..M-j, M = n-1-k),
+  // in chunks of INTERIOR_BLOCK
+  for (int k = 1; k <= n - 3; ++k) {
+    const int M = n - 1 - k;
+    const int count = (M - 1) * M / 2;
+    for (int start = 0; start < count; start += INTERIOR_BLOCK) L->tiles_lin.push_back((k << 20) | start);
+  }
   // skeleton nodes
   std::unordered_map<std::array<int64_t, 3>, int32_t, KeyHash> skel_id;
   std::vector<std::vector<SkelInc>> incs;
@@ -361,6 +368,15 @@ void build_level(hhg_ctx* c, int level) {
       L->ev_nodes.push_back((int32_t)s);
     }
   }
+  // group the face items by macro and face type so that the lanes of a warp share the
+  // candidate set (the unrolled candidate loop then does not diverge)
+  std::stable_sort(L->face_items.begin(), L->face_items.end(), [](const FaceItem& a, const FaceItem& b) {
+    if (a.macro != b.macro) return a.macro < b.macro;
+    if (a.f != b.f) return a.f < b.f;
+    if (a.k != b.k) return a.k < b.k;
+    if (a.j != b.j) return a.j < b.j;
+    return a.i < b.i;
+  });
   // candidate elements around a face-interior point that lie inside the macro (per face
   // type); checked against every face item of this level
   auto cand_inside = [](int nn, int i, int j, int k, int bit) {
@@ -429,6 +445,7 @@ void build_restriction(hhg_ctx* c, int lc) {
 void upload_level(hhg_ctx* c, LevelHost& L) {
   upload(L.d_tiles_int, L.tiles_int);
   upload(L.d_tiles_all, L.tiles_all);
+  upload(L.d_tiles_lin, L.tiles_lin);
   upload(L.d_skel_ptr, L.skel_ptr);
   upload(L.d_skel_inc, L.skel_inc);
   upload(L.d_skel_dir, L.skel_dir);
@@ -461,6 +478,8 @@ void upload_level(hhg_ctx* c, LevelHost& L) {
   D.ntiles_all = (int32_t)L.tiles_all.size();
   D.tiles_int = L.d_tiles_int.as<int32_t>();
   D.tiles_all = L.d_tiles_all.as<int32_t>();
+  D.ntiles_lin = (int32_t)L.tiles_lin.size();
+  D.tiles_lin = L.d_tiles_lin.as<int32_t>();
   D.nskel = (int32_t)L.skel_dir.size();
   D.skel_ptr = L.d_skel_ptr.as<int32_t>();
   D.skel_inc = L.d_skel_inc.as<SkelInc>();

@@ -128,6 +128,8 @@ struct LevelDev {
   int64_t entries;     // nmacro * nt
   int32_t ntiles_int;  // interior tiles
   int32_t ntiles_all;  // tiles over all lattice points
+  int32_t ntiles_lin;  // 128-node chunks of the interior points of each slice: (k << 20) | start
+  const int32_t* tiles_lin;
   const int32_t* tiles_int;  // packed (k << 20) | (j0 << 10) | i0
   const int32_t* tiles_all;
   int32_t nskel;
@@ -147,6 +149,7 @@ struct LevelDev {
   double* acc64;
 };
 
+constexpr int INTERIOR_BLOCK = 128;
 constexpr int TILE_I = 32;
 constexpr int TILE_J = 4;
 

@@ -33,7 +33,7 @@ struct SweepArgs {
 };
 
 // parts: 1 = macro-interior kernels (one launch per macro), 2 = skeleton kernel, 3 = both.
-// partial_offset: first partial slot used (the interior launches take ntiles_int slots per
+// partial_offset: first partial slot used (the interior launches take ntiles_lin slots per
 // macro, then the skeleton kernel one per block); *partial_count returns the slots used.
 template <typename T>
 int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev, OpKind op,

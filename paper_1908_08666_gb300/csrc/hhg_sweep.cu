@@ -82,26 +82,41 @@ __device__ __forceinline__ void epilogue(const SweepArgs<T>& a, int64_t e, int64
   }
 }
 
-template <typename T, int OP>
-__global__ void __launch_bounds__(TILE_I* TILE_J) k_interior(const LevelDev L, const MacroStencil<T> st,
+// (j, i) of the t-th interior point of a slice with M = n-1-k: rows j = 1..M-1 hold
+// M-j points; C(j) = (j-1)(2M-j)/2 points precede row j.
+__device__ __forceinline__ void slice_decode(int M, int t, int& j, int& i) {
+  const float b = (float)(2 * M - 1);
+  int u = (int)floorf(0.5f * (b - sqrtf(fmaxf(b * b - 8.0f * (float)t, 0.0f))));
+  u = max(0, min(u, M - 2));
+  // exact correction: C(u+1) <= t < C(u+2)
+  if (((u + 1) * (2 * M - u - 2)) / 2 <= t) ++u;
+  if ((u * (2 * M - u - 1)) / 2 > t) --u;
+  j = u + 1;
+  i = t - (u * (2 * M - u - 1)) / 2 + 1;
+}
+
+// GEN = 0: physical scaling with the patch mean (the default operator, flags folded
+// at compile time); GEN = 1: variant and khat rule from the run-time flags.
+template <typename T, int OP, int GEN>
+__global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, const MacroStencil<T> st,
                                                               const int macro, const OpFlags fl,
                                                               const SweepArgs<T> a) {
-  const int32_t tile = L.tiles_int[blockIdx.x];
+  const int32_t tile = L.tiles_lin[blockIdx.x];
   const int n = L.n;
   const int k = tile >> 20;
-  const int j = ((tile >> 10) & 1023) + threadIdx.y;
-  const int i = (tile & 1023) + threadIdx.x;
+  const int M = n - 1 - k;
+  const int t = (tile & 0xFFFFF) + threadIdx.x;
   double r2 = 0.0;
-  if (i + j + k <= n - 1) {  // i, j, k >= 1 by construction of the interior tiles
+  const bool physical = GEN ? fl.physical != 0 : true;
+  const bool khat_edge = GEN ? fl.khat_edge != 0 : false;
+  if (t < (M - 1) * M / 2) {
+    int j, i;
+    slice_decode(M, t, j, i);
     const int64_t E = L.entries;
     const int64_t base = (int64_t)macro * L.nt;
-    const T* __restrict__ px = a.x + base;
-    const T* __restrict__ py = px + E;
-    const T* __restrict__ pz = py + E;
-    const T* __restrict__ pk = a.k + base;
-    // row starts of the seven lattice rows the stencil touches
+    // starts of the seven lattice rows the stencil touches (plus i)
     const int m = n - k;
-    const int r00 = (int)(tetnum(n + 1) - tetnum(n + 1 - k)) + j * (2 * m + 3 - j) / 2;
+    const int r00 = (int)(tetnum(n + 1) - tetnum(n + 1 - k)) + j * (2 * m + 3 - j) / 2 + i;
     const int r10 = r00 + (m + 1 - j);
     const int rm0 = r00 - (m + 2 - j);
     const int sz = (m + 1) * (m + 2) / 2;
@@ -110,32 +125,43 @@ __global__ void __launch_bounds__(TILE_I* TILE_J) k_interior(const LevelDev L, c
     const int r0m = r00 - szm + j;
     const int rm1 = rm0 + sz - j + 1;
     const int r1m = r10 - szm + j + 1;
-    int nb[NDIR];
-    nb[0] = r00 + i + 1;
-    nb[1] = r10 + i - 1;
-    nb[2] = rm1 + i;
-    nb[3] = r10 + i;
-    nb[4] = r01 + i - 1;
-    nb[5] = rm1 + i + 1;
-    nb[6] = r01 + i;
-    nb[7] = r00 + i - 1;
-    nb[8] = rm0 + i + 1;
-    nb[9] = r1m + i;
-    nb[10] = rm0 + i;
-    nb[11] = r0m + i + 1;
-    nb[12] = r1m + i - 1;
-    nb[13] = r0m + i;
-    const int c0 = r00 + i;
-    const T x0 = px[c0], y0 = py[c0], z0 = pz[c0], k0 = pk[c0];
+    // neighbour d lies in row rowof[d] at column offset -1, 0 or +1: load through one
+    // pointer per (row, array) with immediate offsets
     T kk[NDIR], dx[NDIR], dy[NDIR], dz[NDIR];
+    T x0, y0, z0, k0;
+    {
+      const T* __restrict__ X = a.x + base;
+      const T* __restrict__ K = a.k + base;
+#define HHG_ROW(R, ...)                                                                                   \
+  {                                                                                                      \
+    const T* px_ = X + (R);                                                                              \
+    const T* py_ = px_ + E;                                                                              \
+    const T* pz_ = py_ + E;                                                                              \
+    const T* pk_ = K + (R);                                                                              \
+    __VA_ARGS__                                                                                          \
+  }
+#define HHG_NB(D, OFF)                                                                                    \
+  kk[D] = pk_[OFF];                                                                                      \
+  dx[D] = px_[OFF];                                                                                      \
+      dy[D] = py_[OFF];                                                                                  \
+      dz[D] = pz_[OFF];
+      HHG_ROW(r00, x0 = px_[0]; y0 = py_[0]; z0 = pz_[0]; k0 = pk_[0]; HHG_NB(0, 1) HHG_NB(7, -1))
+      HHG_ROW(r10, HHG_NB(1, -1) HHG_NB(3, 0))
+      HHG_ROW(rm1, HHG_NB(2, 0) HHG_NB(5, 1))
+      HHG_ROW(r01, HHG_NB(4, -1) HHG_NB(6, 0))
+      HHG_ROW(rm0, HHG_NB(8, 1) HHG_NB(10, 0))
+      HHG_ROW(r1m, HHG_NB(9, 0) HHG_NB(12, -1))
+      HHG_ROW(r0m, HHG_NB(11, 1) HHG_NB(13, 0))
+#undef HHG_NB
+#undef HHG_ROW
+    }
 #pragma unroll
     for (int d = 0; d < NDIR; ++d) {
-      const int o = nb[d];
-      kk[d] = pk[o];
-      dx[d] = px[o] - x0;
-      dy[d] = py[o] - y0;
-      dz[d] = pz[o] - z0;
+      dx[d] -= x0;
+      dy[d] -= y0;
+      dz[d] -= z0;
     }
+    const T k0q = (T)0.25 * k0;
     T ax = 0, ay = 0, az = 0, dgx = 0, dgy = 0, dgz = 0;
 #pragma unroll
     for (int d = 0; d < 7; ++d) {
@@ -150,43 +176,61 @@ __global__ void __launch_bounds__(TILE_I* TILE_J) k_interior(const LevelDev L, c
           const T la = kk[ring_a(e, c)], lb = kk[ring_b(e, c)];
           rsp += ka + kb;
           rsm += la + lb;
-          const T dp = ka - kb, dm = la - lb;
-          wpx += dp * st.s[d][c][0];
-          wpy += dp * st.s[d][c][1];
-          wpz += dp * st.s[d][c][2];
-          wmx += dm * st.s[e][c][0];
-          wmy += dm * st.s[e][c][1];
-          wmz += dm * st.s[e][c][2];
+          if (physical) {
+            const T dp = ka - kb, dm = la - lb;
+            wpx = fma(dp, st.s[d][c][0], wpx);
+            wpy = fma(dp, st.s[d][c][1], wpy);
+            wpz = fma(dp, st.s[d][c][2], wpz);
+            wmx = fma(dm, st.s[e][c][0], wmx);
+            wmy = fma(dm, st.s[e][c][1], wmy);
+            wmz = fma(dm, st.s[e][c][2], wmz);
+          }
         }
       }
       T khp, khm;
-      if (fl.khat_edge) {
+      if (khat_edge) {
         khp = (T)0.5 * (k0 + kk[d]);
         khm = (T)0.5 * (k0 + kk[e]);
       } else {
-        khp = (T)0.25 * (k0 + kk[d]) + wr * rsp;
-        khm = (T)0.25 * (k0 + kk[e]) + wr * rsm;
+        khp = fma(wr, rsp, fma((T)0.25, kk[d], k0q));
+        khm = fma(wr, rsm, fma((T)0.25, kk[e], k0q));
       }
-      const T vx = khp * dx[d] + khm * dx[e];
-      const T vy = khp * dy[d] + khm * dy[e];
-      const T vz = khp * dz[d] + khm * dz[e];
+      const T vx = fma(khp, dx[d], khm * dx[e]);
+      const T vy = fma(khp, dy[d], khm * dy[e]);
+      const T vz = fma(khp, dz[d], khm * dz[e]);
       const T* S = st.S[d];
-      ax += S[0] * vx + S[3] * vy + S[4] * vz;
-      ay += S[3] * vx + S[1] * vy + S[5] * vz;
-      az += S[4] * vx + S[5] * vy + S[2] * vz;
-      if (fl.physical) {
-        ax += wpy * dz[d] - wpz * dy[d] + wmy * dz[e] - wmz * dy[e];
-        ay += wpz * dx[d] - wpx * dz[d] + wmz * dx[e] - wmx * dz[e];
-        az += wpx * dy[d] - wpy * dx[d] + wmx * dy[e] - wmy * dx[e];
+      ax = fma(S[0], vx, ax);
+      ax = fma(S[3], vy, ax);
+      ax = fma(S[4], vz, ax);
+      ay = fma(S[3], vx, ay);
+      ay = fma(S[1], vy, ay);
+      ay = fma(S[5], vz, ay);
+      az = fma(S[4], vx, az);
+      az = fma(S[5], vy, az);
+      az = fma(S[2], vz, az);
+      if (physical) {
+        // w x delta for both directions
+        ax = fma(wpy, dz[d], ax);
+        ax = fma(-wpz, dy[d], ax);
+        ax = fma(wmy, dz[e], ax);
+        ax = fma(-wmz, dy[e], ax);
+        ay = fma(wpz, dx[d], ay);
+        ay = fma(-wpx, dz[d], ay);
+        ay = fma(wmz, dx[e], ay);
+        ay = fma(-wmx, dz[e], ay);
+        az = fma(wpx, dy[d], az);
+        az = fma(-wpy, dx[d], az);
+        az = fma(wmx, dy[e], az);
+        az = fma(-wmy, dx[e], az);
       }
       if (OP == OP_JACOBI || OP == OP_CHEBY || OP == OP_DIAG) {
         const T ks = khp + khm;
-        dgx -= ks * S[0];
-        dgy -= ks * S[1];
-        dgz -= ks * S[2];
+        dgx = fma(-ks, S[0], dgx);
+        dgy = fma(-ks, S[1], dgy);
+        dgz = fma(-ks, S[2], dgz);
       }
     }
-    epilogue<T, OP>(a, base + c0, E, ax, ay, az, dgx, dgy, dgz, x0, y0, z0, r2);
+    epilogue<T, OP>(a, base + r00, E, ax, ay, az, dgx, dgy, dgz, x0, y0, z0, r2);
   }
   if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
 }
@@ -550,18 +594,19 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
   cudaStream_t s = (cudaStream_t)stream;
   const dim3 blk(TILE_I, TILE_J);
   int64_t used = partial_offset;
+  const bool gen = !(fl.physical == 1 && fl.khat_edge == 0);
   for (int m = 0; m < L.nmacro && (parts & 1); ++m) {
-    if (L.ntiles_int == 0) break;
+    if (L.ntiles_lin == 0) break;
     SweepArgs<T> am = a;
     if (a.partial) am.partial = a.partial + used;
     switch (op) {
-      case OP_APPLY: k_interior<T, OP_APPLY><<<L.ntiles_int, blk, 0, s>>>(L, st_host[m], m, fl, am); break;
-      case OP_RESID: k_interior<T, OP_RESID><<<L.ntiles_int, blk, 0, s>>>(L, st_host[m], m, fl, am); break;
-      case OP_JACOBI: k_interior<T, OP_JACOBI><<<L.ntiles_int, blk, 0, s>>>(L, st_host[m], m, fl, am); break;
-      case OP_CHEBY: k_interior<T, OP_CHEBY><<<L.ntiles_int, blk, 0, s>>>(L, st_host[m], m, fl, am); break;
-      case OP_DIAG: k_interior<T, OP_DIAG><<<L.ntiles_int, blk, 0, s>>>(L, st_host[m], m, fl, am); break;
+      case OP_APPLY: (gen ? k_interior<T, OP_APPLY, 1> : k_interior<T, OP_APPLY, 0>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st_host[m], m, fl, am); break;
+      case OP_RESID: (gen ? k_interior<T, OP_RESID, 1> : k_interior<T, OP_RESID, 0>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st_host[m], m, fl, am); break;
+      case OP_JACOBI: (gen ? k_interior<T, OP_JACOBI, 1> : k_interior<T, OP_JACOBI, 0>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st_host[m], m, fl, am); break;
+      case OP_CHEBY: (gen ? k_interior<T, OP_CHEBY, 1> : k_interior<T, OP_CHEBY, 0>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st_host[m], m, fl, am); break;
+      case OP_DIAG: (gen ? k_interior<T, OP_DIAG, 1> : k_interior<T, OP_DIAG, 0>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st_host[m], m, fl, am); break;
     }
-    used += L.ntiles_int;
+    used += L.ntiles_lin;
   }
   if (parts & 2) {
     if (L.nface_items > 0) {
@@ -639,20 +684,20 @@ int noalloc_scratch_address(int device, double** ptr) {
 }
 
 int64_t noalloc_partials_needed(const LevelDev& L) {
-  return (int64_t)L.nmacro * L.ntiles_int + L.nface_nodes + L.nev;
+  return (int64_t)L.nmacro * L.ntiles_lin + L.nface_nodes + L.nev;
 }
 
 template <typename T>
 int launch_residual_noalloc(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev,
                             const OpFlags& fl, SweepArgs<T> a, double* scratch, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  const dim3 blk(TILE_I, TILE_J);
   int64_t used = 0;
-  for (int m = 0; m < L.nmacro && L.ntiles_int > 0; ++m) {
+  const bool gen = !(fl.physical == 1 && fl.khat_edge == 0);
+  for (int m = 0; m < L.nmacro && L.ntiles_lin > 0; ++m) {
     SweepArgs<T> am = a;
     am.partial = scratch + used;
-    k_interior<T, OP_RESID><<<L.ntiles_int, blk, 0, s>>>(L, st_host[m], m, fl, am);
-    used += L.ntiles_int;
+    (gen ? k_interior<T, OP_RESID, 1> : k_interior<T, OP_RESID, 0>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st_host[m], m, fl, am);
+    used += L.ntiles_lin;
   }
   if (L.nface_nodes > 0) {
     LevelDev Lf = L;  // face-interior nodes through the warp-per-node path
