@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--level", type=int, default=LEVEL)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-stokes", action="store_true")
     return ap.parse_args()
 
 
@@ -219,6 +220,60 @@ def solve_times(B, torch, h, level, coords_u):
     return out
 
 
+def stokes_bench(B, torch, level, dev, stream, steps=20):
+    """Stokes with variable viscosity (Sec. 5.2) on the same cube and level: mu = 1 inside a
+    sphere of radius 0.25 around the centre and 1e3 outside (tanh blend of width 0.02), body
+    force i.i.d. uniform[-1, 1] (seed 4).  FP32 saddle-operator apply throughput (4 DoFs per
+    node, L2 flushed before each apply) and the time to an FP64 relative residual of 1e-8
+    with FP64 iterative refinement around FP32 block-preconditioned MINRES."""
+    import hhg_inputs as hi
+
+    xyz, tets = hi.kuhn_cube(1)
+    h = B.hhg_create(dev, stream.cuda_stream)
+    try:
+        B.hhg_set_macro_mesh(h, xyz, tets)
+        B.hhg_refine(h, level)
+        B.hhg_set_problem(h, kind=B.STOKES)
+        E, U, _ = B.hhg_num_nodes(h, level)
+        ce = B.hhg_entry_coords(h, level)
+        e2u, udir = B.hhg_entry_to_unique(h, level)
+        first = np.full(U, -1, dtype=np.int64)
+        first[e2u[::-1]] = np.arange(E)[::-1]
+        cu = ce[first]
+        mu = hi.viscosity_sphere(cu)
+        mul = torch.empty(E, dtype=torch.float64, device="cuda")
+        B.hhg_scatter_unique(h, level, B.F64, 1, torch.as_tensor(mu, device="cuda"), mul)
+        B.hhg_set_coefficient(h, mul, B.F64)
+        fu = hi.sample_grid(hi.uniform_grid(1 << level, seed=4), cu)
+        fu[udir] = 0.0
+        src = np.zeros((4, U))
+        src[:3] = fu.T
+        f = torch.empty(4 * E, dtype=torch.float64, device="cuda")
+        B.hhg_scatter_unique(h, level, B.F64, 4, torch.as_tensor(src.reshape(-1), device="cuda"), f)
+        x32 = f.float()
+        y32 = torch.empty_like(x32)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            B.hhg_stokes_apply(h, level, B.F32, x32, y32)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.fill_(1.0)
+            a.record(stream)
+            B.hhg_stokes_apply(h, level, B.F32, x32, y32)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        B.hhg_mg_setup(h)
+        x = torch.zeros_like(f)
+        rep = B.hhg_solve(h, f, x, method=B.SOLVE_STOKES_IR_MINRES, level=level, dt=B.F64, rtol=1e-8, max_iter=30,
+                          inner_rtol=1e-3, inner_max_iter=400, allow_not_converged=True)
+        return {"workload": "Stokes, 6-macro cube, level %d, viscosity sphere 1 / 1e3, f ~ U[-1,1] (seed 4)" % level,
+                "apply_ms": round(ms, 5), "apply_gdofs": round(4 * U / (ms * 1e-3) / 1e9, 3),
+                "ir_minres": {k: (float("%.4g" % v) if isinstance(v, float) else v) for k, v in rep.items()}}
+    finally:
+        B.hhg_destroy(h)
+
+
 # ---------------------------------------------------------------------------- our arm
 
 
@@ -311,6 +366,7 @@ def run_ours(args):
     assert torch.isfinite(y).all()
     solve = None if args.no_solve else solve_times(B, torch, h, level, coords_e[first])
     B.hhg_destroy(h)
+    stokes = None if args.no_stokes else stokes_bench(B, torch, level, dev, stream)
 
     ms_per_step = total_ms / args.steps
     value = world * dofs / (ms_per_step * 1e-3) / 1e9
@@ -364,6 +420,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4)},
         "gpu_launches": int(prof_launches[0] + prof_launches[1]),
         "solve": solve,
+        "stokes": stokes,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

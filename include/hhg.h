@@ -195,7 +195,12 @@ typedef enum {
   HHG_SOLVE_PCG_JACOBI = 0, /* point-Jacobi preconditioned CG */
   HHG_SOLVE_MG_CG = 1,      /* CG preconditioned by one V-cycle */
   HHG_SOLVE_IR_MG_CG = 2,   /* FP64 iterative refinement around FP32 MG-CG (f, x in FP64) */
-  HHG_SOLVE_MG = 3          /* stationary V-cycles */
+  HHG_SOLVE_MG = 3,         /* stationary V-cycles */
+  /* Stokes (problem kind HHG_STOKES; f, x hold (u, v, w, p), 4*E values): MINRES
+   * preconditioned by blockdiag(one velocity V-cycle, mu_i / m_i) with m the lumped
+   * pressure mass; the pressure is shifted to zero mean (sum m_i p_i = 0) at the end. */
+  HHG_SOLVE_STOKES_MINRES = 4,
+  HHG_SOLVE_STOKES_IR_MINRES = 5  /* FP64 iterative refinement around FP32 MINRES */
 } hhg_solve_method;
 
 typedef struct {
@@ -222,6 +227,16 @@ typedef struct {
  * max_iter is reached, HHG_ERR_NUMERIC on a non-finite residual. */
 hhg_status hhg_solve(hhg_ctx* ctx, const hhg_solve_opts* opts, const void* f_dev, void* x_dev,
                      hhg_solve_report* report);
+
+/* Stokes saddle operator (problem kind HHG_STOKES, Sec. 5.2): on (u, v, w, p)
+ * vectors of 4*E values (component-major),
+ *     K = [[A(mu), B^T], [B, C]],  A(mu) = scaled-stencil operator of (2 mu eps(u), eps(v)),
+ *     B = -(div u, q),  C = -(h^2/12) (grad p, grad q),  h = (6 |T|)^{1/3} / n per macro,
+ * mu = the coefficient.  Velocity-Dirichlet rows are identity rows (residual 0);
+ * every pressure row is free. */
+hhg_status hhg_stokes_apply(hhg_ctx* ctx, int level, hhg_dtype dt, const void* x_dev, void* y_dev);
+hhg_status hhg_stokes_residual(hhg_ctx* ctx, int level, hhg_dtype dt, const void* f_dev, const void* x_dev,
+                               void* r_dev, double* norm2_host);
 
 /* Residual with norm that allocates nothing.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory at

@@ -31,7 +31,7 @@ class HhgError(RuntimeError):
 
 
 SMOOTH_JACOBI, SMOOTH_CHEBYSHEV = 0, 1
-SOLVE_PCG_JACOBI, SOLVE_MG_CG, SOLVE_IR_MG_CG, SOLVE_MG = 0, 1, 2, 3
+SOLVE_PCG_JACOBI, SOLVE_MG_CG, SOLVE_IR_MG_CG, SOLVE_MG, SOLVE_STOKES_MINRES, SOLVE_STOKES_IR_MINRES = 0, 1, 2, 3, 4, 5
 
 
 class hhg_mg_params(C.Structure):
@@ -85,6 +85,8 @@ _SIGS = {
     "hhg_prolongate_add": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
     "hhg_restrict": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
     "hhg_vcycle": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+    "hhg_stokes_apply": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+    "hhg_stokes_residual": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)],
     "hhg_solve": [C.c_void_p, C.POINTER(hhg_solve_opts), C.c_void_p, C.c_void_p, C.POINTER(hhg_solve_report)],
     "hhg_profile": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "hhg_residual_noalloc": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -289,3 +291,14 @@ def hhg_solve(ctx, f, x, method=SOLVE_MG_CG, level=None, dt=F64, rtol=1e-8, max_
         return rep.as_dict()
     _check(ctx, st)
     return rep.as_dict()
+
+
+def hhg_stokes_apply(ctx, level, dt, x, y):
+    _check(ctx, load().hhg_stokes_apply(ctx, level, dt, _ptr(x), _ptr(y)))
+
+
+def hhg_stokes_residual(ctx, level, dt, f, x, r, want_norm=False):
+    nrm = C.c_double()
+    _check(ctx, load().hhg_stokes_residual(ctx, level, dt, _ptr(f), _ptr(x), _ptr(r),
+                                           C.byref(nrm) if want_norm else None))
+    return nrm.value if want_norm else None

@@ -98,8 +98,11 @@ struct LevelHost {
   std::vector<std::array<int64_t, 3>> skel_key;
   std::vector<FaceItem> face_items;
   std::vector<int32_t> face_nodes, ev_nodes, dir_nodes;
+  std::vector<FaceItem> face_items_all;
+  std::vector<int32_t> face_nodes_all, ev_all;
   uint32_t face_mask[4] = {0, 0, 0, 0};
-  std::vector<uint8_t> mask;
+  std::vector<uint8_t> mask, mask_own;  // owned copy of a free node / of any node
+  std::vector<double> lumped;           // lumped P1 mass of every entry's node
   std::vector<int64_t> entry_to_unique, unique_first;
   std::vector<int8_t> unique_dir;
   int64_t nunique = 0, nfree = 0;
@@ -110,6 +113,10 @@ struct LevelHost {
   // device
   DevMem d_tiles_int, d_tiles_all, d_tiles_lin, d_skel_ptr, d_skel_inc, d_skel_dir, d_mask, d_first, d_e2u;
   DevMem d_face_items, d_face_nodes, d_ev_nodes, d_dir_nodes, d_acc32, d_acc64;
+  DevMem d_face_items_all, d_face_nodes_all, d_ev_all;
+  DevMem d_mask_own, d_invm64, d_invm32;  // owned-node mask; inverse lumped mass
+  DevMem d_mass64, d_mass32;              // lumped mass
+  DevMem sw64[10], sw32[10];               // Stokes work vectors (4*E)
   DevMem d_rptr, d_rent, d_rw64, d_rw32;
   DevMem d_mc64, d_mc32;
   DevMem d_k64, d_k32;
@@ -198,8 +205,8 @@ inline int64_t max_partials(hhg_ctx* c) {
   int64_t mx = 1024;
   for (int l = c->level_min; l <= c->level_max; ++l) {
     const LevelHost& L = *c->levels[l];
-    mx = std::max<int64_t>(mx, (int64_t)L.tiles_lin.size() * (int64_t)c->tets.size() + (L.face_nodes.size() + 127) / 128 +
-                                   L.ev_nodes.size() + 8);
+    mx = std::max<int64_t>(mx, (int64_t)L.tiles_lin.size() * (int64_t)c->tets.size() +
+                                   (L.face_nodes_all.size() + 127) / 128 + L.ev_all.size() + 8);
   }
   return mx;
 }

@@ -99,8 +99,46 @@ int dir_from_kuhn(const int v[3]) {
 
 // Per-macro constants at intervals n: element stiffness of the 6 Kuhn element
 // types and the interior stencil (Shat and the correction axial vectors).
+// P1 gradients and volume of one element
+void element_gradients(const Vec3d v[4], double g[4][3], double& vol) {
+  double K[4][4][9];
+  element_stiffness(v, 1.0, 0.0, K);  // validates the element
+  double J[3][3];
+  const Vec3d* w[3] = {&v[1], &v[2], &v[3]};
+  for (int r = 0; r < 3; ++r) {
+    J[r][0] = w[r]->x - v[0].x;
+    J[r][1] = w[r]->y - v[0].y;
+    J[r][2] = w[r]->z - v[0].z;
+  }
+  const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                     J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  // columns of J^{-1} = gradients of barycentrics 1..3 (cofactor formula)
+  const double c00 = (J[1][1] * J[2][2] - J[1][2] * J[2][1]), c01 = (J[0][2] * J[2][1] - J[0][1] * J[2][2]),
+               c02 = (J[0][1] * J[1][2] - J[0][2] * J[1][1]);
+  const double c10 = (J[1][2] * J[2][0] - J[1][0] * J[2][2]), c11 = (J[0][0] * J[2][2] - J[0][2] * J[2][0]),
+               c12 = (J[0][2] * J[1][0] - J[0][0] * J[1][2]);
+  const double c20 = (J[1][0] * J[2][1] - J[1][1] * J[2][0]), c21 = (J[0][1] * J[2][0] - J[0][0] * J[2][1]),
+               c22 = (J[0][0] * J[1][1] - J[0][1] * J[1][0]);
+  const double inv[3][3] = {{c00 / det, c01 / det, c02 / det}, {c10 / det, c11 / det, c12 / det},
+                            {c20 / det, c21 / det, c22 / det}};
+  for (int a = 1; a < 4; ++a)
+    for (int c = 0; c < 3; ++c) g[a][c] = inv[c][a - 1];
+  for (int c = 0; c < 3; ++c) g[0][c] = -(g[1][c] + g[2][c] + g[3][c]);
+  vol = std::fabs(det) / 6.0;
+}
+
 void macro_constants(const MacroGeom& G, int n, double c_eps, double c_div, MacroConsts<double>& out) {
   double KE[6][4][4][9];
+  double BD[6][4][4][3], LC[6][4][4];
+  // stabilisation length of the macro's refined mesh: h = (6 |T|)^{1/3} / n (the lattice
+  // spacing 1/n on the Kuhn cube)
+  double hT;
+  {
+    Vec3d v[4] = {G.v[0], G.v[1], G.v[2], G.v[3]};
+    double g[4][3], volT;
+    element_gradients(v, g, volT);
+    hT = std::cbrt(6.0 * volT) / n;
+  }
   for (int p = 0; p < 6; ++p) {
     int P[4][3];
     kuhn_vertices(p, P);
@@ -110,6 +148,15 @@ void macro_constants(const MacroGeom& G, int n, double c_eps, double c_div, Macr
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b)
         for (int q = 0; q < 9; ++q) out.ke[p][a][b][q] = KE[p][a][b][q];
+    double g[4][3], vol;
+    element_gradients(v, g, vol);
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        for (int l = 0; l < 3; ++l) BD[p][a][b][l] = -0.25 * vol * g[b][l];
+        LC[p][a][b] = -(hT * hT / 12.0) * vol * (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2]);
+        for (int l = 0; l < 3; ++l) out.bd[p][a][b][l] = BD[p][a][b][l];
+        out.lc[p][a][b] = LC[p][a][b];
+      }
   }
   // patches of the 14 directions
   for (int d = 0; d < NDIR; ++d) {
@@ -149,6 +196,18 @@ void macro_constants(const MacroGeom& G, int n, double c_eps, double c_div, Macr
       if (off[0] == 0 && off[1] == 0 && off[2] == 0) return NDIR;
       return dir_from_kuhn(off);
     };
+    for (int l = 0; l < 3; ++l) {
+      out.st.B[d][l] = 0;
+      out.st.G[d][l] = 0;
+    }
+    out.st.C[d] = 0;
+    for (const PatchEl& e : patch) {
+      for (int l = 0; l < 3; ++l) {
+        out.st.B[d][l] += BD[e.p][e.a][e.b][l];
+        out.st.G[d][l] += BD[e.p][e.b][e.a][l];
+      }
+      out.st.C[d] += LC[e.p][e.a][e.b];
+    }
     for (const PatchEl& e : patch) {
       const double* K = KE[e.p][e.a][e.b];
       for (int m = 0; m < 3; ++m)
@@ -220,6 +279,29 @@ void macro_constants(const MacroGeom& G, int n, double c_eps, double c_div, Macr
           THROW(HHG_ERR_STATE, "Shat(-d) != Shat(d) for direction %d", d);
     }
   }
+}
+
+// the centre terms of B, B^T and C at a macro-interior node, from the 24 elements around it
+void check_stokes_row_sums(const MacroConsts<double>& mc) {
+  double b0[3] = {0, 0, 0}, c0 = 0, scale = 0;
+  for (int p = 0; p < 6; ++p)
+    for (int a = 0; a < 4; ++a) {
+      for (int l = 0; l < 3; ++l) b0[l] += mc.bd[p][a][a][l];
+      c0 += mc.lc[p][a][a];
+    }
+  double sb[3] = {b0[0], b0[1], b0[2]}, sg[3] = {b0[0], b0[1], b0[2]}, sc = c0;
+  for (int d = 0; d < NDIR; ++d) {
+    for (int l = 0; l < 3; ++l) {
+      sb[l] += mc.st.B[d][l];
+      sg[l] += mc.st.G[d][l];
+      scale = std::max(scale, std::fabs(mc.st.B[d][l]));
+    }
+    sc += mc.st.C[d];
+  }
+  for (int l = 0; l < 3; ++l)
+    if (std::fabs(sb[l]) > 1e-12 * scale || std::fabs(sg[l]) > 1e-12 * scale || std::fabs(b0[l]) > 1e-12 * scale)
+      THROW(HHG_ERR_STATE, "Stokes divergence stencil has a non-zero row sum");
+  if (std::fabs(sc) > 1e-12 * (std::fabs(c0) + 1e-300)) THROW(HHG_ERR_STATE, "stabilisation row sum");
 }
 
 template <typename T>
@@ -338,45 +420,99 @@ void build_level(hhg_ctx* c, int level) {
   }
   L->nfree = L->nunique;
   for (int64_t s = 0; s < nskel; ++s) L->nfree -= L->skel_dir[s];
-  // skeleton split for the kernels
-  for (int64_t s = 0; s < nskel; ++s) {
-    if (L->skel_dir[s]) {
-      L->dir_nodes.push_back((int32_t)s);
-    } else if (L->skel_support[s] == 3) {
-      const int32_t fid = (int32_t)L->face_nodes.size();
-      L->face_nodes.push_back((int32_t)s);
+  L->mask_own.assign(L->entries, 0);
+  for (int64_t u = 0; u < L->nunique; ++u) L->mask_own[L->unique_first[u]] = 1;
+  // lumped mass (sum over the elements around a node of |t|/4); all elements of a macro
+  // have the volume |T| / n^3
+  {
+    std::vector<double> volt(M);
+    for (int m = 0; m < M; ++m) {
+      Vec3d v[4];
+      for (int q = 0; q < 4; ++q) v[q] = c->xyz[c->tets[m][q]];
+      double g[4][3], vol;
+      element_gradients(v, g, vol);
+      volt[m] = vol / ((double)n * n * n);
+    }
+    auto elements_inside = [&](int i, int j, int k) {
+      int cnt = 0;
+      const int X = i + j + k, Y = j + k, Z = k;
+      for (int p = 0; p < 6; ++p) {
+        int P[4][3];
+        kuhn_vertices(p, P);
+        for (int av = 0; av < 4; ++av) {
+          bool ok = true;
+          for (int v = 0; v < 4 && ok; ++v) {
+            const int VX = X - P[av][0] + P[v][0], VY = Y - P[av][1] + P[v][1], VZ = Z - P[av][2] + P[v][2];
+            ok = 0 <= VZ && VZ <= VY && VY <= VX && VX <= n;
+          }
+          cnt += ok;
+        }
+      }
+      return cnt;
+    };
+    std::vector<double> mu(L->nunique, 0.0);
+    for (int m = 0; m < M; ++m)
+      for (int64_t q = 0; q < L->nt; ++q) {
+        const int64_t e = (int64_t)m * L->nt + q;
+        const int64_t u = L->entry_to_unique[e];
+        if (u < nint) mu[u] = 6.0 * volt[m];
+      }
+    for (int64_t s = 0; s < nskel; ++s)
       for (int q = L->skel_ptr[s]; q < L->skel_ptr[s + 1]; ++q) {
         const SkelInc& I = L->skel_inc[q];
-        const int w[4] = {n - I.i - I.j - I.k, I.i, I.j, I.k};
-        int f = -1, zeros = 0;
-        for (int c = 0; c < 4; ++c)
-          if (w[c] == 0) {
-            f = c;
-            ++zeros;
-          }
-        if (zeros != 1) THROW(HHG_ERR_STATE, "face node with %d zero barycentric weights", zeros);
-        FaceItem it;
-        it.macro = I.macro;
-        it.node = fid;
-        it.i = I.i;
-        it.j = I.j;
-        it.k = I.k;
-        it.f = (int16_t)f;
-        L->face_items.push_back(it);
+        mu[nint + s] += 0.25 * volt[I.macro] * elements_inside(I.i, I.j, I.k);
       }
-    } else {
-      L->ev_nodes.push_back((int32_t)s);
+    L->lumped.resize(L->entries);
+    for (int64_t e = 0; e < L->entries; ++e) L->lumped[e] = mu[L->entry_to_unique[e]];
+  }
+  // skeleton split for the kernels: free face-interior nodes, free edge/vertex nodes and
+  // Dirichlet nodes; and the same face/edge-vertex split including Dirichlet nodes
+  auto add_face = [&](int64_t s, std::vector<int32_t>& nodes, std::vector<FaceItem>& items) {
+    const int32_t fid = (int32_t)nodes.size();
+    nodes.push_back((int32_t)s);
+    for (int q = L->skel_ptr[s]; q < L->skel_ptr[s + 1]; ++q) {
+      const SkelInc& I = L->skel_inc[q];
+      const int w[4] = {n - I.i - I.j - I.k, I.i, I.j, I.k};
+      int f = -1, zeros = 0;
+      for (int cc = 0; cc < 4; ++cc)
+        if (w[cc] == 0) {
+          f = cc;
+          ++zeros;
+        }
+      if (zeros != 1) THROW(HHG_ERR_STATE, "face node with %d zero barycentric weights", zeros);
+      FaceItem it;
+      it.macro = I.macro;
+      it.node = fid;
+      it.i = I.i;
+      it.j = I.j;
+      it.k = I.k;
+      it.f = (int16_t)f;
+      items.push_back(it);
     }
+  };
+  for (int64_t s = 0; s < nskel; ++s) {
+    if (L->skel_dir[s])
+      L->dir_nodes.push_back((int32_t)s);
+    else if (L->skel_support[s] == 3)
+      add_face(s, L->face_nodes, L->face_items);
+    else
+      L->ev_nodes.push_back((int32_t)s);
+    if (L->skel_support[s] == 3)
+      add_face(s, L->face_nodes_all, L->face_items_all);
+    else
+      L->ev_all.push_back((int32_t)s);
   }
   // group the face items by macro and face type so that the lanes of a warp share the
   // candidate set (the unrolled candidate loop then does not diverge)
-  std::stable_sort(L->face_items.begin(), L->face_items.end(), [](const FaceItem& a, const FaceItem& b) {
+  auto item_order = [](const FaceItem& a, const FaceItem& b) {
     if (a.macro != b.macro) return a.macro < b.macro;
     if (a.f != b.f) return a.f < b.f;
     if (a.k != b.k) return a.k < b.k;
     if (a.j != b.j) return a.j < b.j;
     return a.i < b.i;
-  });
+  };
+  std::stable_sort(L->face_items.begin(), L->face_items.end(), item_order);
+  std::stable_sort(L->face_items_all.begin(), L->face_items_all.end(), item_order);
   // candidate elements around a face-interior point that lie inside the macro (per face
   // type); checked against every face item of this level
   auto cand_inside = [](int nn, int i, int j, int k, int bit) {
@@ -398,7 +534,7 @@ void build_level(hhg_ctx* c, int level) {
       for (int bit = 0; bit < 24; ++bit)
         if (cand_inside(nn, rep[f][0], rep[f][1], rep[f][2], bit)) L->face_mask[f] |= 1u << bit;
     }
-    for (const FaceItem& it : L->face_items)
+    for (const FaceItem& it : L->face_items_all)
       for (int bit = 0; bit < 24; ++bit)
         if (cand_inside(n, it.i, it.j, it.k, bit) != (((L->face_mask[it.f] >> bit) & 1u) != 0))
           THROW(HHG_ERR_STATE, "face candidate mask mismatch");
@@ -450,12 +586,29 @@ void upload_level(hhg_ctx* c, LevelHost& L) {
   upload(L.d_skel_inc, L.skel_inc);
   upload(L.d_skel_dir, L.skel_dir);
   upload(L.d_mask, L.mask);
+  upload(L.d_mask_own, L.mask_own);
+  {
+    std::vector<double> im(L.entries);
+    std::vector<float> im32(L.entries);
+    for (int64_t e = 0; e < L.entries; ++e) {
+      im[e] = 1.0 / L.lumped[e];
+      im32[e] = (float)im[e];
+    }
+    upload(L.d_invm64, im);
+    upload(L.d_invm32, im32);
+    std::vector<float> m32(L.lumped.begin(), L.lumped.end());
+    upload(L.d_mass64, L.lumped);
+    upload(L.d_mass32, m32);
+  }
   upload(L.d_face_items, L.face_items);
+  upload(L.d_face_items_all, L.face_items_all);
+  upload(L.d_face_nodes_all, L.face_nodes_all);
+  upload(L.d_ev_all, L.ev_all);
   upload(L.d_face_nodes, L.face_nodes);
   upload(L.d_ev_nodes, L.ev_nodes);
   upload(L.d_dir_nodes, L.dir_nodes);
-  CK(L.d_acc32.alloc(std::max<size_t>(1, L.face_nodes.size()) * 6 * sizeof(float)));
-  CK(L.d_acc64.alloc(std::max<size_t>(1, L.face_nodes.size()) * 6 * sizeof(double)));
+  CK(L.d_acc32.alloc(std::max<size_t>(1, L.face_nodes_all.size()) * 8 * sizeof(float)));
+  CK(L.d_acc64.alloc(std::max<size_t>(1, L.face_nodes_all.size()) * 8 * sizeof(double)));
   CK(cudaMemset(L.d_acc32.p, 0, L.d_acc32.bytes));
   CK(cudaMemset(L.d_acc64.p, 0, L.d_acc64.bytes));
   upload(L.d_first, L.unique_first);
@@ -494,6 +647,12 @@ void upload_level(hhg_ctx* c, LevelHost& L) {
   D.ev_nodes = L.d_ev_nodes.as<int32_t>();
   D.dir_nodes = L.d_dir_nodes.as<int32_t>();
   for (int f = 0; f < 4; ++f) D.face_mask[f] = L.face_mask[f];
+  D.nface_items_all = (int32_t)L.face_items_all.size();
+  D.nface_nodes_all = (int32_t)L.face_nodes_all.size();
+  D.nev_all = (int32_t)L.ev_all.size();
+  D.face_items_all = L.d_face_items_all.as<FaceItem>();
+  D.face_nodes_all = L.d_face_nodes_all.as<int32_t>();
+  D.ev_all = L.d_ev_all.as<int32_t>();
   D.acc32 = L.d_acc32.as<float>();
   D.acc64 = L.d_acc64.as<double>();
 }
@@ -648,6 +807,7 @@ hhg_status hhg_set_problem(hhg_ctx* c, const hhg_problem* p) {
         MacroGeom G;
         for (int q = 0; q < 4; ++q) G.v[q] = c->xyz[c->tets[m][q]];
         macro_constants(G, L.n, ce, cd, mc64[m]);
+        check_stokes_row_sums(mc64[m]);
         mc32[m] = cast_consts<float>(mc64[m]);
         L.st64[m] = mc64[m].st;
         L.st32[m] = mc32[m].st;

@@ -89,19 +89,33 @@ HHG_HD void kuhn_perm(int p, int& a0, int& a1, int& a2) {
 // directions (Shat_{-d} = Shat_d), symmetric 3x3 stored xx yy zz xy xz yz; axial
 // vectors of the correction matrices (eq. correctionterm3D): the antisymmetric
 // matrix of ring pair c of direction d is [s[d][c]]_x, acting as s x v.
+//
+// Stokes blocks (Sec. 5.2, stabilised P1-P1; coefficient-free): divergence B,
+// gradient B^T and stabilisation C = -(h^2/12)(grad p, grad q) in difference form
+// over the 14 directions (their row sums vanish at macro-interior nodes):
+//   (B u)_i = sum_d B[d] . (u_{i+d} - u_i),  (B^T p)_i = sum_d G[d] (p_{i+d} - p_i),
+//   (C p)_i = sum_d C[d] (p_{i+d} - p_i).
 template <typename T>
 struct MacroStencil {
   T S[7][6];
   T s[NDIR][3][3];
+  T B[NDIR][3];
+  T G[NDIR][3];
+  T C[NDIR];
 };
 
 // Constants of one macro for the skeleton kernel (global memory): the interior
 // stencil plus the 6 element stiffness matrices K[type][a][b][m][l] (test
 // vertex a, trial vertex b) of the Kuhn element types.
+// Element matrices for the Stokes blocks: bd[type][a][b][l] = -int phi_a d_l phi_b
+// (pressure test vertex a, velocity trial vertex b), lc[type][a][b] = -(h^2/12) int
+// grad phi_a . grad phi_b.
 template <typename T>
 struct MacroConsts {
   MacroStencil<T> st;
   T ke[6][4][4][9];
+  T bd[6][4][4][3];
+  T lc[6][4][4];
 };
 
 // one incidence of a skeleton node in a macro
@@ -145,8 +159,14 @@ struct LevelDev {
   const int32_t* ev_nodes;    // skeleton ids
   const int32_t* dir_nodes;   // skeleton ids
   uint32_t face_mask[4];      // candidate elements (bit 4p+av) inside the macro, per face type
-  float* acc32;               // [nface_nodes * 6] accumulators, zero between sweeps
+  float* acc32;               // [nface_nodes_all * 8] accumulators, zero between sweeps
   double* acc64;
+  // the same split including Dirichlet skeleton nodes (the Stokes pressure rows of
+  // velocity-Dirichlet nodes are free)
+  int32_t nface_items_all, nface_nodes_all, nev_all;
+  const FaceItem* face_items_all;
+  const int32_t* face_nodes_all;
+  const int32_t* ev_all;
 };
 
 constexpr int INTERIOR_BLOCK = 128;

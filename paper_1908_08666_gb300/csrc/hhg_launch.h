@@ -53,6 +53,11 @@ int launch_residual_noalloc(const LevelDev& L, const MacroStencil<T>* st_host, c
 // constant-memory direction tables of the skeleton kernels (once per device)
 int upload_direction_tables();
 
+// Stokes saddle operator on (u, v, w, p) vectors (4 components): apply or residual
+template <typename T>
+int launch_stokes_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev, OpKind op,
+                        const OpFlags& fl, const SweepArgs<T>& a, void* stream, int64_t* partial_count);
+
 // sum of partials[0..count) into out[0] (single block), deterministic
 int launch_reduce(const double* partials, int64_t count, double* out, void* stream);
 
@@ -60,6 +65,15 @@ int launch_reduce(const double* partials, int64_t count, double* out, void* stre
 template <typename T>
 int launch_dot(const LevelDev& L, int comps, const T* a, const T* b, double* partials, int64_t* partial_count,
                void* stream);
+
+// dot over entries with mask[e] != 0 (comps components of stride E)
+template <typename T>
+int launch_dot_masked(const uint8_t* mask, int64_t E, int comps, const T* a, const T* b, double* partials,
+                      int64_t* partial_count, void* stream);
+template <typename T>
+int launch_mul3(int64_t n, const T* a, const T* b, const T* c, T* out, void* stream);  // out = a * b * c
+template <typename T>
+int launch_add_const(int64_t n, T v, T* dst, void* stream);                           // dst += v
 
 // multigrid transfers and coefficient injection (all on the fine level's lattice)
 template <typename T>

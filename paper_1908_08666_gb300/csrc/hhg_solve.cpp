@@ -386,6 +386,197 @@ CgResult pcg(hhg_ctx* c, int l, bool mg, const T* f, T* x, double rtol, int max_
   return res;
 }
 
+// ------------------------------------------------------------------- Stokes (Sec. 5.2)
+
+template <typename T>
+DevMem* swork(LevelHost& L);
+template <>
+DevMem* swork<double>(LevelHost& L) {
+  return L.sw64;
+}
+template <>
+DevMem* swork<float>(LevelHost& L) {
+  return L.sw32;
+}
+template <typename T>
+const T* invm(LevelHost& L);
+template <>
+const double* invm<double>(LevelHost& L) {
+  return L.d_invm64.as<double>();
+}
+template <>
+const float* invm<float>(LevelHost& L) {
+  return L.d_invm32.as<float>();
+}
+template <typename T>
+const T* mass(LevelHost& L);
+template <>
+const double* mass<double>(LevelHost& L) {
+  return L.d_mass64.as<double>();
+}
+template <>
+const float* mass<float>(LevelHost& L) {
+  return L.d_mass32.as<float>();
+}
+
+constexpr int NSWORK = 10;
+
+template <typename T>
+void ensure_swork(hhg_ctx* c, int l) {
+  LevelHost& L = c->lv(l);
+  DevMem* W = swork<T>(L);
+  if (W[0].p) return;
+  for (int q = 0; q < NSWORK; ++q) {
+    CK(W[q].alloc(4 * (size_t)L.entries * sizeof(T)));
+    CK(cudaMemsetAsync(W[q].p, 0, W[q].bytes, c->stream));
+  }
+}
+
+void need_stokes(hhg_ctx* c) {
+  need_ready(c, true);
+  if (c->prob.kind != HHG_STOKES) THROW(HHG_ERR_STATE, "problem kind is not Stokes");
+}
+
+template <typename T>
+double stokes_sweep(hhg_ctx* c, int l, OpKind op, const T* f, const T* x, T* out, bool norm) {
+  LevelHost& L = c->lv(l);
+  SweepArgs<T> a{};
+  a.x = x;
+  a.f = f;
+  a.out = out;
+  a.k = kptr<T>(L);
+  if (norm) a.partial = c->scratch.as<double>();
+  int64_t np = 0;
+  CK(launch_stokes_sweep<T>(L.dev, stencils<T>(L), consts_dev<T>(L), op, c->flags, a, c->stream, &np));
+  if (!norm) return 0.0;
+  CK(launch_reduce(c->scratch.as<double>(), np, c->scalar.as<double>(), c->stream));
+  CK(cudaMemcpyAsync(c->pinned, c->scalar.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  wait_stream(c);
+  return c->pinned[0];
+}
+
+// Euclidean inner product over the unique DoFs: free velocity components and all pressures
+template <typename T>
+double sdot(hhg_ctx* c, int l, const T* a, const T* b) {
+  LevelHost& L = c->lv(l);
+  int64_t n1 = 0, n2 = 0;
+  double* part = c->scratch.as<double>();
+  CK(launch_dot_masked<T>(L.d_mask.as<uint8_t>(), L.entries, 3, a, b, part, &n1, c->stream));
+  CK(launch_dot_masked<T>(L.d_mask_own.as<uint8_t>(), L.entries, 1, a + 3 * L.entries, b + 3 * L.entries, part + n1,
+                          &n2, c->stream));
+  CK(launch_reduce(part, n1 + n2, c->scalar.as<double>(), c->stream));
+  CK(cudaMemcpyAsync(c->pinned, c->scalar.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  wait_stream(c);
+  return c->pinned[0];
+}
+
+// z = blockdiag(V-cycle of A(mu), diag(mu / m)) r
+template <typename T>
+void stokes_precond(hhg_ctx* c, int l, const T* r, T* z) {
+  LevelHost& L = c->lv(l);
+  CK(cudaMemsetAsync(z, 0, 3 * L.entries * sizeof(T), c->stream));
+  vcycle<T>(c, l, r, z);
+  CK(launch_mul3<T>(L.entries, r + 3 * L.entries, kptr<T>(L), invm<T>(L), z + 3 * L.entries, c->stream));
+}
+
+// shift the pressure to zero mean: sum_i m_i p_i = 0 over unique nodes
+template <typename T>
+void project_pressure(hhg_ctx* c, int l, T* x) {
+  LevelHost& L = c->lv(l);
+  int64_t n1 = 0;
+  double* part = c->scratch.as<double>();
+  T* p = x + 3 * L.entries;
+  CK(launch_dot_masked<T>(L.d_mask_own.as<uint8_t>(), L.entries, 1, mass<T>(L), p, part, &n1, c->stream));
+  CK(launch_reduce(part, n1, c->scalar.as<double>(), c->stream));
+  CK(cudaMemcpyAsync(c->pinned, c->scalar.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  wait_stream(c);
+  double msum = 0.0;
+  for (int64_t u = 0; u < L.nunique; ++u) msum += L.lumped[L.unique_first[u]];
+  CK(launch_add_const<T>(L.entries, (T)(-c->pinned[0] / msum), p, c->stream));
+}
+
+struct MinresResult {
+  int iterations = 0;
+  double r0 = 0.0, rel = 0.0;
+  bool converged = false;
+};
+
+// Preconditioned MINRES (Lanczos with Givens rotations; Elman, Silvester and Wathen,
+// Finite Elements and Fast Iterative Solvers, Alg. 4.1) on K x = f; stops when the
+// preconditioned residual estimate |eta| <= rtol |eta_0|; returns the true relative residual.
+template <typename T>
+MinresResult minres(hhg_ctx* c, int l, const T* f, T* x, double rtol, int max_iter) {
+  ensure_swork<T>(c, l);
+  ensure_work<T>(c, l);
+  LevelHost& L = c->lv(l);
+  DevMem* W = swork<T>(L);
+  const int64_t n = 4 * L.entries;
+  T* v_prev = W[0].as<T>();
+  T* v = W[1].as<T>();
+  T* q = W[2].as<T>();
+  T* z = W[3].as<T>();
+  T* w_prev = W[4].as<T>();
+  T* w = W[5].as<T>();
+  MinresResult R;
+  const double r0 = stokes_sweep<T>(c, l, OP_RESID, f, x, v, true);
+  R.r0 = std::sqrt(r0);
+  if (!std::isfinite(r0)) THROW(HHG_ERR_NUMERIC, "non-finite initial residual");
+  if (r0 == 0.0) {
+    R.converged = true;
+    return R;
+  }
+  CK(cudaMemsetAsync(v_prev, 0, n * sizeof(T), c->stream));
+  CK(cudaMemsetAsync(w_prev, 0, n * sizeof(T), c->stream));
+  CK(cudaMemsetAsync(w, 0, n * sizeof(T), c->stream));
+  stokes_precond<T>(c, l, v, z);
+  double gamma = std::sqrt(sdot<T>(c, l, z, v));
+  if (!(gamma > 0.0) || !std::isfinite(gamma)) THROW(HHG_ERR_NUMERIC, "preconditioner is not positive definite");
+  const double eta0 = gamma;
+  double eta = gamma, gamma_prev = 1.0;
+  double c_prev = 1.0, c_cur = 1.0, s_prev = 0.0, s_cur = 0.0;
+  for (int it = 1; it <= max_iter; ++it) {
+    CK(launch_axpby<T>(n, (T)0, z, (T)(1.0 / gamma), z, c->stream));  // z /= gamma
+    stokes_sweep<T>(c, l, OP_APPLY, nullptr, z, q, false);
+    const double delta = sdot<T>(c, l, q, z);
+    CK(launch_axpby<T>(n, (T)(-delta / gamma), v, (T)1, q, c->stream));
+    CK(launch_axpby<T>(n, (T)(-gamma / gamma_prev), v_prev, (T)1, q, c->stream));  // q = v_next
+    std::swap(v_prev, v);
+    std::swap(v, q);  // v = v_next, q = old v_prev (free)
+    // z_next into q (z is still needed for w)
+    stokes_precond<T>(c, l, v, q);
+    const double gn2 = sdot<T>(c, l, q, v);
+    if (!(gn2 >= 0.0) || !std::isfinite(gn2)) THROW(HHG_ERR_NUMERIC, "MINRES breakdown");
+    const double gamma_next = std::sqrt(gn2);
+    const double a0 = c_cur * delta - c_prev * s_cur * gamma;
+    const double a1 = std::sqrt(a0 * a0 + gamma_next * gamma_next);
+    const double a2 = s_cur * delta + c_prev * c_cur * gamma;
+    const double a3 = s_prev * gamma;
+    const double c_next = a0 / a1, s_next = gamma_next / a1;
+    // w_next = (z - a3 w_prev - a2 w) / a1, stored in w_prev
+    CK(launch_axpby<T>(n, (T)(1.0 / a1), z, (T)(-a3 / a1), w_prev, c->stream));
+    CK(launch_axpby<T>(n, (T)(-a2 / a1), w, (T)1, w_prev, c->stream));
+    std::swap(w_prev, w);  // w = w_next, w_prev = old w
+    CK(launch_axpby<T>(n, (T)(c_next * eta), w, (T)1, x, c->stream));
+    eta = -s_next * eta;
+    std::swap(z, q);  // z = z_next
+    gamma_prev = gamma;
+    gamma = gamma_next;
+    c_prev = c_cur;
+    c_cur = c_next;
+    s_prev = s_cur;
+    s_cur = s_next;
+    R.iterations = it;
+    if (std::fabs(eta) <= rtol * eta0 || gamma == 0.0) {
+      R.converged = true;
+      break;
+    }
+  }
+  T* r = W[6].as<T>();
+  const double rr = stokes_sweep<T>(c, l, OP_RESID, f, x, r, true);
+  R.rel = std::sqrt(rr / r0);
+  return R;
+}
+
 void mg_check(hhg_ctx* c) {
   need_ready(c, true);
   if (!c->mg_ready) THROW(HHG_ERR_STATE, "call hhg_mg_setup after setting the coefficient");
@@ -508,6 +699,28 @@ hhg_status hhg_vcycle(hhg_ctx* c, int level, hhg_dtype dt, const void* f, void* 
   });
 }
 
+hhg_status hhg_stokes_apply(hhg_ctx* c, int level, hhg_dtype dt, const void* x, void* y) {
+  return dispatch(c, dt, [&](auto* tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    need_stokes(c);
+    if (!x || !y || x == y) THROW(HHG_ERR_ARG, "x and y must be distinct device buffers");
+    c->lv(level);
+    stokes_sweep<T>(c, level, OP_APPLY, nullptr, (const T*)x, (T*)y, false);
+  });
+}
+
+hhg_status hhg_stokes_residual(hhg_ctx* c, int level, hhg_dtype dt, const void* f, const void* x, void* r,
+                               double* norm2) {
+  return dispatch(c, dt, [&](auto* tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    need_stokes(c);
+    if (!f || !x || !r || x == r || f == r) THROW(HHG_ERR_ARG, "bad buffers");
+    c->lv(level);
+    const double n2 = stokes_sweep<T>(c, level, OP_RESID, (const T*)f, (const T*)x, (T*)r, norm2 != nullptr);
+    if (norm2) *norm2 = n2;
+  });
+}
+
 hhg_status hhg_solve(hhg_ctx* c, const hhg_solve_opts* o, const void* f, void* x, hhg_solve_report* rep) {
   bool not_converged = false;
   hhg_status st = guard(c, [&] {
@@ -585,6 +798,50 @@ hhg_status hhg_solve(hhg_ctx* c, const hhg_solve_opts* o, const void* f, void* x
         R.iterations = it;
         if (!std::isfinite(rr)) THROW(HHG_ERR_NUMERIC, "non-finite residual");
       }
+      R.rel_residual = r0 > 0.0 ? std::sqrt(rr / r0) : 0.0;
+      R.converged = R.rel_residual <= o->rtol;
+    } else if (o->method == HHG_SOLVE_STOKES_MINRES) {
+      need_stokes(c);
+      auto run = [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        MinresResult mr = minres<T>(c, l, (const T*)f, (T*)x, o->rtol, o->max_iter);
+        project_pressure<T>(c, l, (T*)x);
+        R.iterations = mr.iterations;
+        R.residual0 = mr.r0;
+        R.rel_residual = mr.rel;
+        R.converged = mr.converged && mr.rel <= 10.0 * o->rtol;
+      };
+      if (o->dt == HHG_F64)
+        run((double*)nullptr);
+      else if (o->dt == HHG_F32)
+        run((float*)nullptr);
+      else
+        THROW(HHG_ERR_ARG, "dtype");
+    } else if (o->method == HHG_SOLVE_STOKES_IR_MINRES) {
+      need_stokes(c);
+      if (o->dt != HHG_F64) THROW(HHG_ERR_ARG, "iterative refinement needs FP64 f and x");
+      if (!(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || o->inner_max_iter < 1) THROW(HHG_ERR_ARG, "inner tol");
+      ensure_swork<double>(c, l);
+      ensure_swork<float>(c, l);
+      LevelHost& L = c->lv(l);
+      const int64_t n = 4 * L.entries;
+      double* r64 = swork<double>(L)[8].as<double>();
+      float* r32 = swork<float>(L)[8].as<float>();
+      float* e32 = swork<float>(L)[9].as<float>();
+      const double r0 = stokes_sweep<double>(c, l, OP_RESID, (const double*)f, (const double*)x, r64, true);
+      R.residual0 = std::sqrt(r0);
+      double rr = r0;
+      for (int it = 1; it <= o->max_iter && r0 > 0.0 && std::sqrt(rr / r0) > o->rtol; ++it) {
+        CK(launch_convert<double, float>(n, r64, r32, c->stream));
+        CK(cudaMemsetAsync(e32, 0, n * sizeof(float), c->stream));
+        MinresResult mr = minres<float>(c, l, r32, e32, o->inner_rtol, o->inner_max_iter);
+        R.inner_iterations += mr.iterations;
+        CK(launch_add_f32_to_f64(n, e32, (double*)x, c->stream));
+        rr = stokes_sweep<double>(c, l, OP_RESID, (const double*)f, (const double*)x, r64, true);
+        R.iterations = it;
+        if (!std::isfinite(rr)) THROW(HHG_ERR_NUMERIC, "non-finite residual");
+      }
+      project_pressure<double>(c, l, (double*)x);
       R.rel_residual = r0 > 0.0 ? std::sqrt(rr / r0) : 0.0;
       R.converged = R.rel_residual <= o->rtol;
     } else {

@@ -97,7 +97,30 @@ __device__ __forceinline__ void slice_decode(int M, int t, int& j, int& i) {
 
 // GEN = 0: physical scaling with the patch mean (the default operator, flags folded
 // at compile time); GEN = 1: variant and khat rule from the run-time flags.
-template <typename T, int OP, int GEN>
+// Stokes epilogue (apply / residual) for one copy: velocity rows (identity on
+// velocity-Dirichlet nodes) and the pressure row.
+template <typename T, int OP>
+__device__ __forceinline__ void stokes_epilogue(const SweepArgs<T>& a, int64_t e, int64_t E, T ax, T ay, T az, T yp,
+                                                T x0, T y0, T z0, bool vdir, double& r2) {
+  if (OP == OP_APPLY) {
+    a.out[e] = vdir ? x0 : ax;
+    a.out[e + E] = vdir ? y0 : ay;
+    a.out[e + 2 * E] = vdir ? z0 : az;
+    a.out[e + 3 * E] = yp;
+  } else {
+    const T rx = vdir ? (T)0 : a.f[e] - ax, ry = vdir ? (T)0 : a.f[e + E] - ay, rz = vdir ? (T)0 : a.f[e + 2 * E] - az;
+    const T rp = a.f[e + 3 * E] - yp;
+    a.out[e] = rx;
+    a.out[e + E] = ry;
+    a.out[e + 2 * E] = rz;
+    a.out[e + 3 * E] = rp;
+    r2 += (double)rx * rx + (double)ry * ry + (double)rz * rz + (double)rp * rp;
+  }
+}
+
+// STK = 1: the Stokes saddle operator [[A(mu), B^T], [B, C]] on (u, v, w, p) (Sec. 5.2),
+// the velocity block being the scaled-stencil operator of the 2 mu eps(u) form.
+template <typename T, int OP, int GEN, int STK = 0>
 __global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, const MacroStencil<T> st,
                                                               const int macro, const OpFlags fl,
                                                               const SweepArgs<T> a) {
@@ -129,6 +152,26 @@ __global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, c
     // pointer per (row, array) with immediate offsets
     T kk[NDIR], dx[NDIR], dy[NDIR], dz[NDIR];
     T x0, y0, z0, k0;
+    T dp[STK ? NDIR : 1];
+    T p0 = 0;
+    if constexpr (STK) {
+      const T* __restrict__ P = a.x + base + 3 * E;
+      p0 = P[r00];
+      dp[0] = P[r00 + 1] - p0;
+      dp[7] = P[r00 - 1] - p0;
+      dp[1] = P[r10 - 1] - p0;
+      dp[3] = P[r10] - p0;
+      dp[2] = P[rm1] - p0;
+      dp[5] = P[rm1 + 1] - p0;
+      dp[4] = P[r01 - 1] - p0;
+      dp[6] = P[r01] - p0;
+      dp[8] = P[rm0 + 1] - p0;
+      dp[10] = P[rm0] - p0;
+      dp[9] = P[r1m] - p0;
+      dp[12] = P[r1m - 1] - p0;
+      dp[11] = P[r0m + 1] - p0;
+      dp[13] = P[r0m] - p0;
+    }
     {
       const T* __restrict__ X = a.x + base;
       const T* __restrict__ K = a.k + base;
@@ -230,7 +273,22 @@ __global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, c
         dgz = fma(-ks, S[2], dgz);
       }
     }
-    epilogue<T, OP>(a, base + r00, E, ax, ay, az, dgx, dgy, dgz, x0, y0, z0, r2);
+    if constexpr (STK) {
+      T yp = 0;
+#pragma unroll
+      for (int d = 0; d < NDIR; ++d) {
+        ax = fma(st.G[d][0], dp[d], ax);
+        ay = fma(st.G[d][1], dp[d], ay);
+        az = fma(st.G[d][2], dp[d], az);
+        yp = fma(st.B[d][0], dx[d], yp);
+        yp = fma(st.B[d][1], dy[d], yp);
+        yp = fma(st.B[d][2], dz[d], yp);
+        yp = fma(st.C[d], dp[d], yp);
+      }
+      stokes_epilogue<T, OP>(a, base + r00, E, ax, ay, az, yp, x0, y0, z0, false, r2);
+    } else {
+      epilogue<T, OP>(a, base + r00, E, ax, ay, az, dgx, dgy, dgz, x0, y0, z0, r2);
+    }
   }
   if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
 }
@@ -453,7 +511,7 @@ __global__ void __launch_bounds__(128) k_face_items(const LevelDev L, const Macr
   T ax = 0, ay = 0, az = 0, dgx = 0, dgy = 0, dgz = 0;
   incidence_row<T>(mc[it.macro], px, pk, E, n, it.i, it.j, it.k, L.face_mask[it.f], (1u << NDIR) - 1u, x0, y0, z0,
                    fl, ax, ay, az, dgx, dgy, dgz);
-  T* acc = acc_of<T>(L) + 6 * (int64_t)it.node;
+  T* acc = acc_of<T>(L) + 8 * (int64_t)it.node;
   atomicAdd(acc + 0, ax);
   atomicAdd(acc + 1, ay);
   atomicAdd(acc + 2, az);
@@ -471,7 +529,7 @@ __global__ void __launch_bounds__(128) k_face_finalize(const LevelDev L, const S
   if (t < L.nface_nodes) {
     const int n = L.n;
     const int64_t E = L.entries;
-    T* acc = acc_of<T>(L) + 6 * (int64_t)t;
+    T* acc = acc_of<T>(L) + 8 * (int64_t)t;
     const T ax = acc[0], ay = acc[1], az = acc[2], dgx = acc[3], dgy = acc[4], dgz = acc[5];
 #pragma unroll
     for (int c = 0; c < 6; ++c) acc[c] = 0;
@@ -580,6 +638,164 @@ __global__ void __launch_bounds__(128) k_skeleton_ev(const LevelDev L, const Mac
     const int64_t e = (int64_t)I.macro * L.nt + lattice_index32(n, I.i, I.j, I.k);
     double tmp = 0.0;
     epilogue<T, OP>(a, e, E, ax, ay, az, dgx, dgy, dgz, x0, y0, z0, tmp);
+    if (q == b0) r2 = tmp;
+  }
+  if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
+}
+
+// Stokes element terms of one candidate element (permutation p, node at vertex av)
+// of one incident macro for the skeleton node at Kuhn coordinates (X, Y, Z): full
+// element sums of B u, C p (pressure row) and B^T p (velocity rows) -- no interface
+// rule applies to these coefficient-free blocks.
+template <typename T>
+__device__ __forceinline__ void stokes_candidate(const MacroConsts<T>& C, const T* __restrict__ px, int64_t E, int n,
+                                                 int X, int Y, int Z, int p, int av, T& ax, T& ay, T& az, T& yp) {
+  const int a0 = p >> 1;
+  const int lo = a0 == 0 ? 1 : 0, hi = a0 == 2 ? 1 : 2;
+  const int a1 = (p & 1) ? hi : lo, a2 = (p & 1) ? lo : hi;
+  const int oX = (av >= 1 && a0 == 0) + (av >= 2 && a1 == 0) + (av >= 3 && a2 == 0);
+  const int oY = (av >= 1 && a0 == 1) + (av >= 2 && a1 == 1) + (av >= 3 && a2 == 1);
+  const int oZ = (av >= 1 && a0 == 2) + (av >= 2 && a1 == 2) + (av >= 3 && a2 == 2);
+  bool ok = true;
+  int idx[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int VX = X - oX + (v >= 1 && a0 == 0) + (v >= 2 && a1 == 0) + (v >= 3 && a2 == 0);
+    const int VY = Y - oY + (v >= 1 && a0 == 1) + (v >= 2 && a1 == 1) + (v >= 3 && a2 == 1);
+    const int VZ = Z - oZ + (v >= 1 && a0 == 2) + (v >= 2 && a1 == 2) + (v >= 3 && a2 == 2);
+    ok = ok && kuhn_inside(n, VX, VY, VZ);
+    idx[v] = ok ? lattice_index32(n, VX - VY, VY - VZ, VZ) : 0;
+  }
+  if (!ok) return;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const T ux = px[idx[v]], uy = px[idx[v] + E], uz = px[idx[v] + 2 * E], pv = px[idx[v] + 3 * E];
+    const T* b = C.bd[p][av][v];
+    yp = fma(b[0], ux, yp);
+    yp = fma(b[1], uy, yp);
+    yp = fma(b[2], uz, yp);
+    yp = fma(C.lc[p][av][v], pv, yp);
+    const T* g = C.bd[p][v][av];
+    ax = fma(g[0], pv, ax);
+    ay = fma(g[1], pv, ay);
+    az = fma(g[2], pv, az);
+  }
+}
+
+// Stokes: face-interior skeleton nodes (Dirichlet ones included), one thread per
+// (node, incident macro); velocity part as in k_face_items unless the node is
+// velocity-Dirichlet, plus the element terms of B, B^T and C.
+template <typename T>
+__global__ void __launch_bounds__(128) k_face_items_stk(const LevelDev L, const MacroConsts<T>* __restrict__ mc,
+                                                         const OpFlags fl, const T* __restrict__ x,
+                                                         const T* __restrict__ kc) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L.nface_items_all) return;
+  const FaceItem it = L.face_items_all[t];
+  const int n = L.n;
+  const int64_t E = L.entries;
+  const int64_t base = (int64_t)it.macro * L.nt;
+  const T* px = x + base;
+  const T* pk = kc + base;
+  const int c0 = lattice_index32(n, it.i, it.j, it.k);
+  const T x0 = px[c0], y0 = px[c0 + E], z0 = px[c0 + 2 * E];
+  T ax = 0, ay = 0, az = 0, dgx = 0, dgy = 0, dgz = 0, yp = 0;
+  const bool vdir = L.skel_dir[L.face_nodes_all[it.node]] != 0;
+  const MacroConsts<T>& C = mc[it.macro];
+  if (!vdir)
+    incidence_row<T>(C, px, pk, E, n, it.i, it.j, it.k, L.face_mask[it.f], (1u << NDIR) - 1u, x0, y0, z0, fl, ax, ay,
+                     az, dgx, dgy, dgz);
+  const uint32_t cand = L.face_mask[it.f];
+  const int X = it.i + it.j + it.k, Y = it.j + it.k, Z = it.k;
+#pragma unroll
+  for (int bit = 0; bit < 24; ++bit)
+    if ((cand >> bit) & 1u) stokes_candidate<T>(C, px, E, n, X, Y, Z, bit >> 2, bit & 3, ax, ay, az, yp);
+  T* acc = acc_of<T>(L) + 8 * (int64_t)it.node;
+  atomicAdd(acc + 0, ax);
+  atomicAdd(acc + 1, ay);
+  atomicAdd(acc + 2, az);
+  atomicAdd(acc + 6, yp);
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(128) k_face_finalize_stk(const LevelDev L, const SweepArgs<T> a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double r2 = 0.0;
+  if (t < L.nface_nodes_all) {
+    const int n = L.n;
+    const int64_t E = L.entries;
+    T* acc = acc_of<T>(L) + 8 * (int64_t)t;
+    const T ax = acc[0], ay = acc[1], az = acc[2], yp = acc[6];
+    acc[0] = 0;
+    acc[1] = 0;
+    acc[2] = 0;
+    acc[6] = 0;
+    const int s = L.face_nodes_all[t];
+    const bool vdir = L.skel_dir[s] != 0;
+    const int b0 = L.skel_ptr[s], b1 = L.skel_ptr[s + 1];
+    const SkelInc I0 = L.skel_inc[b0];
+    const int64_t e0 = (int64_t)I0.macro * L.nt + lattice_index32(n, I0.i, I0.j, I0.k);
+    const T x0 = a.x[e0], y0 = a.x[e0 + E], z0 = a.x[e0 + 2 * E];
+    for (int q = b0; q < b1; ++q) {
+      const SkelInc I = L.skel_inc[q];
+      const int64_t e = (int64_t)I.macro * L.nt + lattice_index32(n, I.i, I.j, I.k);
+      double tmp = 0.0;
+      stokes_epilogue<T, OP>(a, e, E, ax, ay, az, yp, x0, y0, z0, vdir, tmp);
+      if (q == b0) r2 = tmp;
+    }
+  }
+  if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
+}
+
+// Stokes: macro edge/vertex skeleton nodes (Dirichlet ones included), one block per node.
+template <typename T, int OP>
+__global__ void __launch_bounds__(128) k_skeleton_ev_stk(const LevelDev L, const MacroConsts<T>* __restrict__ mc,
+                                                          const OpFlags fl, const SweepArgs<T> a) {
+  __shared__ T part[4][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double r2 = 0.0;
+  const int s = L.ev_all[blockIdx.x];
+  const bool vdir = L.skel_dir[s] != 0;
+  const int n = L.n;
+  const int64_t E = L.entries;
+  const int b0 = L.skel_ptr[s], b1 = L.skel_ptr[s + 1];
+  const SkelInc I0 = L.skel_inc[b0];
+  const int64_t e0 = (int64_t)I0.macro * L.nt + lattice_index32(n, I0.i, I0.j, I0.k);
+  const T x0 = a.x[e0], y0 = a.x[e0 + E], z0 = a.x[e0 + 2 * E];
+  T ax = 0, ay = 0, az = 0, dgx = 0, dgy = 0, dgz = 0, yp = 0;
+  for (int q = b0 + warp; q < b1; q += 4) {
+    const SkelInc I = L.skel_inc[q];
+    const int64_t base = (int64_t)I.macro * L.nt;
+    if (!vdir)
+      incidence_lane<T>(mc[I.macro], a.x + base, a.k + base, E, n, I.i, I.j, I.k, lane, x0, y0, z0, fl, ax, ay, az,
+                        dgx, dgy, dgz);
+    if (lane < 24)
+      stokes_candidate<T>(mc[I.macro], a.x + base, E, n, I.i + I.j + I.k, I.j + I.k, I.k, lane >> 2, lane & 3, ax, ay,
+                          az, yp);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    az += __shfl_xor_sync(0xffffffffu, az, o);
+    yp += __shfl_xor_sync(0xffffffffu, yp, o);
+  }
+  if (lane == 0) {
+    part[warp][0] = ax;
+    part[warp][1] = ay;
+    part[warp][2] = az;
+    part[warp][3] = yp;
+  }
+  __syncthreads();
+  ax = (part[0][0] + part[1][0]) + (part[2][0] + part[3][0]);
+  ay = (part[0][1] + part[1][1]) + (part[2][1] + part[3][1]);
+  az = (part[0][2] + part[1][2]) + (part[2][2] + part[3][2]);
+  yp = (part[0][3] + part[1][3]) + (part[2][3] + part[3][3]);
+  for (int q = b0 + threadIdx.x; q < b1; q += blockDim.x) {
+    const SkelInc I = L.skel_inc[q];
+    const int64_t e = (int64_t)I.macro * L.nt + lattice_index32(n, I.i, I.j, I.k);
+    double tmp = 0.0;
+    stokes_epilogue<T, OP>(a, e, E, ax, ay, az, yp, x0, y0, z0, vdir, tmp);
     if (q == b0) r2 = tmp;
   }
   if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
@@ -727,6 +943,53 @@ template int launch_residual_noalloc<float>(const LevelDev&, const MacroStencil<
 template int launch_residual_noalloc<double>(const LevelDev&, const MacroStencil<double>*,
                                              const MacroConsts<double>*, const OpFlags&, SweepArgs<double>, double*,
                                              void*);
+
+template <typename T>
+int launch_stokes_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev, OpKind op,
+                        const OpFlags& fl, const SweepArgs<T>& a, void* stream, int64_t* partial_count) {
+  if (op != OP_APPLY && op != OP_RESID) return (int)cudaErrorInvalidValue;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t used = 0;
+  const bool gen = !(fl.physical == 1 && fl.khat_edge == 0);
+  for (int m = 0; m < L.nmacro && L.ntiles_lin > 0; ++m) {
+    SweepArgs<T> am = a;
+    if (a.partial) am.partial = a.partial + used;
+    if (op == OP_APPLY)
+      (gen ? k_interior<T, OP_APPLY, 1, 1> : k_interior<T, OP_APPLY, 0, 1>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(
+          L, st_host[m], m, fl, am);
+    else
+      (gen ? k_interior<T, OP_RESID, 1, 1> : k_interior<T, OP_RESID, 0, 1>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(
+          L, st_host[m], m, fl, am);
+    used += L.ntiles_lin;
+  }
+  if (L.nface_items_all > 0) k_face_items_stk<T><<<(L.nface_items_all + 127) / 128, 128, 0, s>>>(L, mc_dev, fl, a.x, a.k);
+  if (L.nface_nodes_all > 0) {
+    const int nb = (L.nface_nodes_all + 127) / 128;
+    SweepArgs<T> am = a;
+    if (a.partial) am.partial = a.partial + used;
+    if (op == OP_APPLY)
+      k_face_finalize_stk<T, OP_APPLY><<<nb, 128, 0, s>>>(L, am);
+    else
+      k_face_finalize_stk<T, OP_RESID><<<nb, 128, 0, s>>>(L, am);
+    used += nb;
+  }
+  if (L.nev_all > 0) {
+    SweepArgs<T> am = a;
+    if (a.partial) am.partial = a.partial + used;
+    if (op == OP_APPLY)
+      k_skeleton_ev_stk<T, OP_APPLY><<<L.nev_all, 128, 0, s>>>(L, mc_dev, fl, am);
+    else
+      k_skeleton_ev_stk<T, OP_RESID><<<L.nev_all, 128, 0, s>>>(L, mc_dev, fl, am);
+    used += L.nev_all;
+  }
+  if (partial_count) *partial_count = used;
+  return (int)cudaGetLastError();
+}
+
+template int launch_stokes_sweep<float>(const LevelDev&, const MacroStencil<float>*, const MacroConsts<float>*, OpKind,
+                                        const OpFlags&, const SweepArgs<float>&, void*, int64_t*);
+template int launch_stokes_sweep<double>(const LevelDev&, const MacroStencil<double>*, const MacroConsts<double>*,
+                                         OpKind, const OpFlags&, const SweepArgs<double>&, void*, int64_t*);
 
 // fills the direction / ring tables used with run-time indices
 int upload_direction_tables() {

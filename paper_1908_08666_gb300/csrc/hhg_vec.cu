@@ -205,6 +205,19 @@ __global__ void k_dense_matvec(int N, const T* __restrict__ A, const int64_t* __
   dst[idx[i]] = acc;
 }
 
+template <typename T>
+__global__ void k_mul3(int64_t n, const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ c,
+                       T* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = a[e] * b[e] * c[e];
+}
+
+template <typename T>
+__global__ void k_add_const(int64_t n, T v, T* __restrict__ d) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] += v;
+}
+
 inline int grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
   if (g > 152 * 16) g = 152 * 16;
@@ -226,6 +239,26 @@ int launch_dot(const LevelDev& L, int comps, const T* a, const T* b, double* par
                void* stream) {
   k_dot<T><<<DOT_BLOCKS, 256, 0, (cudaStream_t)stream>>>(L.mask, L.entries, comps, a, b, partials);
   *partial_count = DOT_BLOCKS;
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_dot_masked(const uint8_t* mask, int64_t E, int comps, const T* a, const T* b, double* partials,
+                      int64_t* partial_count, void* stream) {
+  k_dot<T><<<DOT_BLOCKS, 256, 0, (cudaStream_t)stream>>>(mask, E, comps, a, b, partials);
+  *partial_count = DOT_BLOCKS;
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_mul3(int64_t n, const T* a, const T* b, const T* c, T* out, void* stream) {
+  k_mul3<T><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(n, a, b, c, out);
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_add_const(int64_t n, T v, T* dst, void* stream) {
+  k_add_const<T><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(n, v, dst);
   return (int)cudaGetLastError();
 }
 
@@ -318,6 +351,9 @@ int launch_dense_matvec(int N, const T* A, const int64_t* idx, const T* src_u, T
   template int launch_axpby<T>(int64_t, T, const T*, T, T*, void*);                                              \
   template int launch_gather<T>(int64_t, int, int64_t, int64_t, const int64_t*, const T*, T*, void*);            \
   template int launch_fill<T>(int64_t, T, T*, void*);                                                           \
+  template int launch_dot_masked<T>(const uint8_t*, int64_t, int, const T*, const T*, double*, int64_t*, void*);  \
+  template int launch_mul3<T>(int64_t, const T*, const T*, const T*, T*, void*);                                  \
+  template int launch_add_const<T>(int64_t, T, T*, void*);                                                        \
   template int launch_mul<T>(int64_t, const T*, const T*, T*, void*);                                           \
   template int launch_recip<T>(int64_t, const T*, T*, void*);                                                    \
   template int launch_hash_unique<T>(int64_t, int, const int8_t*, T*, void*);                                    \
