@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-stokes", action="store_true")
+    ap.add_argument("--no-carreau", action="store_true")
+    ap.add_argument("--carreau-level", type=int, default=7)
     return ap.parse_args()
 
 
@@ -274,6 +276,42 @@ def stokes_bench(B, torch, level, dev, stream, steps=20):
         B.hhg_destroy(h)
 
 
+def carreau_bench(B, torch, level, dev, stream):
+    """Generalised Newtonian Stokes (Sec. 5.2.2): Carreau law with n = 0.5, eta0 = 1,
+    eta_inf = 1e-3, lambda = 1 (kappa = lambda^2, r = (n-1)/2), lid-driven cavity on the
+    6-macro cube; Picard iterations (Alg. 1) with the FP64 viscosity update."""
+    import hhg_inputs as hi
+
+    xyz, tets = hi.kuhn_cube(1)
+    h = B.hhg_create(dev, stream.cuda_stream)
+    try:
+        B.hhg_set_macro_mesh(h, xyz, tets)
+        B.hhg_refine(h, level)
+        B.hhg_set_problem(h, kind=B.STOKES)
+        E, U, _ = B.hhg_num_nodes(h, level)
+        ce = B.hhg_entry_coords(h, level)
+        e2u, _ = B.hhg_entry_to_unique(h, level)
+        first = np.full(U, -1, dtype=np.int64)
+        first[e2u[::-1]] = np.arange(E)[::-1]
+        cu = ce[first]
+        one = torch.ones(E, dtype=torch.float64, device="cuda")
+        B.hhg_set_coefficient(h, one, B.F64)
+        x0 = np.zeros((4, U))
+        x0[:3] = hi.lid_velocity(cu).T
+        x = torch.empty(4 * E, dtype=torch.float64, device="cuda")
+        B.hhg_scatter_unique(h, level, B.F64, 4, torch.as_tensor(x0.reshape(-1), device="cuda"), x)
+        f = torch.zeros_like(x)
+        torch.cuda.synchronize()
+        rep = B.hhg_picard(h, f, x, level, eta0=1.0, eta_inf=1e-3, kappa=1.0, r=-0.25, picard_tol=1e-3,
+                           max_picard=40, step_rtol=1e-2, step_max_iter=100, final_rtol=1e-3,
+                           allow_not_converged=True)
+        return {"workload": "Carreau Stokes (n=0.5, eta0=1, eta_inf=1e-3, lambda=1), lid-driven 6-macro cube, "
+                            "level %d (%d nodes)" % (level, U),
+                "picard": {k: (float("%.4g" % v) if isinstance(v, float) else v) for k, v in rep.items()}}
+    finally:
+        B.hhg_destroy(h)
+
+
 # ---------------------------------------------------------------------------- our arm
 
 
@@ -367,6 +405,7 @@ def run_ours(args):
     solve = None if args.no_solve else solve_times(B, torch, h, level, coords_e[first])
     B.hhg_destroy(h)
     stokes = None if args.no_stokes else stokes_bench(B, torch, level, dev, stream)
+    carreau = None if args.no_carreau else carreau_bench(B, torch, args.carreau_level, dev, stream)
 
     ms_per_step = total_ms / args.steps
     value = world * dofs / (ms_per_step * 1e-3) / 1e9
@@ -421,6 +460,7 @@ def run_ours(args):
         "gpu_launches": int(prof_launches[0] + prof_launches[1]),
         "solve": solve,
         "stokes": stokes,
+        "carreau": carreau,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -238,6 +238,51 @@ hhg_status hhg_stokes_apply(hhg_ctx* ctx, int level, hhg_dtype dt, const void* x
 hhg_status hhg_stokes_residual(hhg_ctx* ctx, int level, hhg_dtype dt, const void* f_dev, const void* x_dev,
                                void* r_dev, double* norm2_host);
 
+/* ---------------------------------------------------------------------------
+ * Generalised Newtonian (Carreau) Stokes, Sec. 5.2.2 and Sec. 3.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  double eta0, eta_inf, kappa, r; /* mu = eta_inf + (eta0 - eta_inf) (1 + kappa |eps(u)|^2)^r (eq. carreau) */
+} hhg_carreau;
+
+/* Nodal viscosity from a velocity field (Sec. 3): at every node the affine
+ * least-squares fit of each velocity component over the node and its mesh
+ * neighbours (eq. minimization_problem, m = 1; on macro interiors the patch is
+ * point-symmetric and the fit reduces to a fixed slope operator) gives grad u,
+ * |eps(u)|^2 = eps : eps, and mu by the Carreau law.  u_dev: FP64, components
+ * at u_dev[c*E + e] (c = 0..2; a Stokes vector can be passed directly);
+ * mu_dev: FP64[E], every copy written. */
+hhg_status hhg_carreau_viscosity(hhg_ctx* ctx, int level, const hhg_carreau* params, const void* u_dev,
+                                 void* mu_dev);
+
+typedef struct {
+  hhg_carreau carreau;
+  int level;
+  double picard_tol;     /* stop when max_i |u_i - u_i_prev| < picard_tol * max_i |u_i| (Alg. 1) */
+  int max_picard;
+  double step_rtol;      /* relative tolerance of the inexact solve of each fixed-point step */
+  int step_max_iter;     /* MINRES iterations per step */
+  double final_rtol;     /* final solve to this relative residual (Alg. 1: 1e-3) */
+} hhg_picard_opts;
+
+typedef struct {
+  int picard_iterations;
+  int minres_iterations; /* total */
+  double final_rel_residual;
+  double last_change;    /* max |u - u_prev| / max |u| of the last fixed-point step */
+  double mu_min, mu_max;
+  double seconds;
+  int converged;
+} hhg_picard_report;
+
+/* Alg. 1: fixed-point (Picard) iterations for Carreau Stokes on opts->level with FP64
+ * f and x (4*E; x holds the initial guess and the Dirichlet velocity).  Each step sets
+ * mu = mu(u) (FP64), refreshes the multigrid hierarchy, and solves the linearised saddle
+ * system inexactly (FP64 refinement around FP32 MINRES); the final solve reaches
+ * final_rtol and the viscosity is updated once more (left as the coefficient). */
+hhg_status hhg_picard(hhg_ctx* ctx, const hhg_picard_opts* opts, const void* f_dev, void* x_dev,
+                      hhg_picard_report* report);
+
 /* Residual with norm that allocates nothing.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory at
  * the time they need a residual norm -- a process whose device memory is owned

@@ -52,6 +52,24 @@ class hhg_solve_report(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class hhg_carreau(C.Structure):
+    _fields_ = [("eta0", C.c_double), ("eta_inf", C.c_double), ("kappa", C.c_double), ("r", C.c_double)]
+
+
+class hhg_picard_opts(C.Structure):
+    _fields_ = [("carreau", hhg_carreau), ("level", C.c_int), ("picard_tol", C.c_double), ("max_picard", C.c_int),
+                ("step_rtol", C.c_double), ("step_max_iter", C.c_int), ("final_rtol", C.c_double)]
+
+
+class hhg_picard_report(C.Structure):
+    _fields_ = [("picard_iterations", C.c_int), ("minres_iterations", C.c_int), ("final_rel_residual", C.c_double),
+                ("last_change", C.c_double), ("mu_min", C.c_double), ("mu_max", C.c_double),
+                ("seconds", C.c_double), ("converged", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class hhg_problem(C.Structure):
     _fields_ = [("kind", C.c_int), ("nu", C.c_double), ("variant", C.c_int), ("khat", C.c_int), ("iface", C.c_int)]
 
@@ -87,6 +105,8 @@ _SIGS = {
     "hhg_vcycle": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
     "hhg_stokes_apply": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
     "hhg_stokes_residual": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)],
+    "hhg_carreau_viscosity": [C.c_void_p, C.c_int, C.POINTER(hhg_carreau), C.c_void_p, C.c_void_p],
+    "hhg_picard": [C.c_void_p, C.POINTER(hhg_picard_opts), C.c_void_p, C.c_void_p, C.POINTER(hhg_picard_report)],
     "hhg_solve": [C.c_void_p, C.POINTER(hhg_solve_opts), C.c_void_p, C.c_void_p, C.POINTER(hhg_solve_report)],
     "hhg_profile": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "hhg_residual_noalloc": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -302,3 +322,20 @@ def hhg_stokes_residual(ctx, level, dt, f, x, r, want_norm=False):
     _check(ctx, load().hhg_stokes_residual(ctx, level, dt, _ptr(f), _ptr(x), _ptr(r),
                                            C.byref(nrm) if want_norm else None))
     return nrm.value if want_norm else None
+
+
+def hhg_carreau_viscosity(ctx, level, u, mu, eta0=1.0, eta_inf=1e-3, kappa=1.0, r=-0.25):
+    p = hhg_carreau(eta0, eta_inf, kappa, r)
+    _check(ctx, load().hhg_carreau_viscosity(ctx, level, C.byref(p), _ptr(u), _ptr(mu)))
+
+
+def hhg_picard(ctx, f, x, level, eta0=1.0, eta_inf=1e-3, kappa=1.0, r=-0.25, picard_tol=1e-3, max_picard=30,
+               step_rtol=1e-2, step_max_iter=50, final_rtol=1e-3, allow_not_converged=False):
+    o = hhg_picard_opts(hhg_carreau(eta0, eta_inf, kappa, r), level, picard_tol, max_picard, step_rtol,
+                        step_max_iter, final_rtol)
+    rep = hhg_picard_report()
+    st = load().hhg_picard(ctx, C.byref(o), _ptr(f), _ptr(x), C.byref(rep))
+    if st == 5 and allow_not_converged:
+        return rep.as_dict()
+    _check(ctx, st)
+    return rep.as_dict()

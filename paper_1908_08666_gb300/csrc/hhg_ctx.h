@@ -117,6 +117,12 @@ struct LevelHost {
   DevMem d_mask_own, d_invm64, d_invm32;  // owned-node mask; inverse lumped mass
   DevMem d_mass64, d_mass32;              // lumped mass
   DevMem sw64[10], sw32[10];               // Stokes work vectors (4*E)
+  // Carreau viscosity: per-macro slope operators and skeleton patch lists (built on first use)
+  std::vector<SlopeOp> slope;
+  DevMem d_pnode, d_pptr, d_pent, d_pdx;
+  PatchLists plist{};
+  bool carreau_ready = false;
+  DevMem d_mu64;  // viscosity of the Picard iteration
   DevMem d_rptr, d_rent, d_rw64, d_rw32;
   DevMem d_mc64, d_mc32;
   DevMem d_k64, d_k32;

@@ -58,6 +58,29 @@ template <typename T>
 int launch_stokes_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev, OpKind op,
                         const OpFlags& fl, const SweepArgs<T>& a, void* stream, int64_t* partial_count);
 
+// Carreau viscosity from the nodal least-squares strain rate (Sec. 3, eq. carreau):
+// interior nodes with the per-macro slope operator Q (grad u_c = sum_d Q[d] (u_c(i+d) - u_c(i))),
+// skeleton nodes from their precomputed patch lists (general affine least squares).
+struct CarreauParams {
+  double eta0, eta_inf, kappa, r;
+};
+struct SlopeOp {
+  double Q[NDIR][3];
+};
+struct PatchLists {
+  int32_t nnodes;
+  const int32_t* node;   // skeleton id
+  const int32_t* ptr;    // [nnodes+1]
+  const int64_t* ent;    // entry of each patch point (the node itself included)
+  const double* dx;      // 3 per patch point: x_point - x_node
+};
+int launch_carreau(const LevelDev& L, const SlopeOp* q_host, const PatchLists& P, const CarreauParams& cp,
+                   const double* u, double* mu, void* stream);
+
+// out[0] = max over masked entries of |a - b|_2 over comps components (b nullable)
+int launch_node_maxnorm(const uint8_t* mask, int64_t E, int comps, const double* a, const double* b,
+                        double* partials, double* out, void* stream);
+
 // sum of partials[0..count) into out[0] (single block), deterministic
 int launch_reduce(const double* partials, int64_t count, double* out, void* stream);
 

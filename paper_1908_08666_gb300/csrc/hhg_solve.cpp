@@ -577,6 +577,104 @@ MinresResult minres(hhg_ctx* c, int l, const T* f, T* x, double rtol, int max_it
   return R;
 }
 
+// ------------------------------------------------------------------- Carreau (Sec. 3, 5.2.2)
+
+// per-macro slope operators and skeleton patch lists of the level (host, once)
+void carreau_setup(hhg_ctx* c, int l) {
+  LevelHost& L = c->lv(l);
+  if (L.carreau_ready) return;
+  const int n = L.n;
+  const int M = (int)c->tets.size();
+  auto phys = [&](int m, double i, double j, double k, double out[3]) {
+    const Vec3d& v0 = c->xyz[c->tets[m][0]];
+    const Vec3d& v1 = c->xyz[c->tets[m][1]];
+    const Vec3d& v2 = c->xyz[c->tets[m][2]];
+    const Vec3d& v3 = c->xyz[c->tets[m][3]];
+    out[0] = v0.x + (i * (v1.x - v0.x) + j * (v2.x - v0.x) + k * (v3.x - v0.x)) / n;
+    out[1] = v0.y + (i * (v1.y - v0.y) + j * (v2.y - v0.y) + k * (v3.y - v0.y)) / n;
+    out[2] = v0.z + (i * (v1.z - v0.z) + j * (v2.z - v0.z) + k * (v3.z - v0.z)) / n;
+  };
+  L.slope.resize(M);
+  for (int m = 0; m < M; ++m) {
+    double dx[NDIR][3], G[3][3] = {{0}};
+    double o[3];
+    phys(m, 0, 0, 0, o);
+    for (int d = 0; d < NDIR; ++d) {
+      double q[3];
+      phys(m, dir_di(d), dir_dj(d), dir_dk(d), q);
+      for (int a = 0; a < 3; ++a) dx[d][a] = q[a] - o[a];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) G[a][b] += dx[d][a] * dx[d][b];
+    }
+    // G^{-1} by cofactors
+    const double det = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) -
+                       G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
+                       G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+    double Gi[3][3];
+    Gi[0][0] = (G[1][1] * G[2][2] - G[1][2] * G[2][1]) / det;
+    Gi[0][1] = (G[0][2] * G[2][1] - G[0][1] * G[2][2]) / det;
+    Gi[0][2] = (G[0][1] * G[1][2] - G[0][2] * G[1][1]) / det;
+    Gi[1][0] = (G[1][2] * G[2][0] - G[1][0] * G[2][2]) / det;
+    Gi[1][1] = (G[0][0] * G[2][2] - G[0][2] * G[2][0]) / det;
+    Gi[1][2] = (G[0][2] * G[1][0] - G[0][0] * G[1][2]) / det;
+    Gi[2][0] = (G[1][0] * G[2][1] - G[1][1] * G[2][0]) / det;
+    Gi[2][1] = (G[0][1] * G[2][0] - G[0][0] * G[2][1]) / det;
+    Gi[2][2] = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) / det;
+    for (int d = 0; d < NDIR; ++d)
+      for (int a = 0; a < 3; ++a)
+        L.slope[m].Q[d][a] = Gi[a][0] * dx[d][0] + Gi[a][1] * dx[d][1] + Gi[a][2] * dx[d][2];
+  }
+  // skeleton patches: the node and its lattice neighbours in every incident macro (unique)
+  std::vector<int32_t> node, ptr(1, 0);
+  std::vector<int64_t> ent;
+  std::vector<double> dxs;
+  const int64_t nskel = (int64_t)L.skel_dir.size();
+  for (int64_t s = 0; s < nskel; ++s) {
+    node.push_back((int32_t)s);
+    std::map<int64_t, std::array<double, 4>> pts;  // unique node -> (entry, dx)
+    for (int q = L.skel_ptr[s]; q < L.skel_ptr[s + 1]; ++q) {
+      const SkelInc& I = L.skel_inc[q];
+      double o[3];
+      phys(I.macro, I.i, I.j, I.k, o);
+      for (int d = -1; d < NDIR; ++d) {
+        const int qi = I.i + (d < 0 ? 0 : dir_di(d)), qj = I.j + (d < 0 ? 0 : dir_dj(d)),
+                  qk = I.k + (d < 0 ? 0 : dir_dk(d));
+        if (!lattice_inside(n, qi, qj, qk)) continue;
+        const int64_t e = (int64_t)I.macro * L.nt + lattice_index(n, qi, qj, qk);
+        const int64_t u = L.entry_to_unique[e];
+        if (pts.count(u)) continue;
+        double x[3];
+        phys(I.macro, qi, qj, qk, x);
+        pts[u] = {(double)e, x[0] - o[0], x[1] - o[1], x[2] - o[2]};
+      }
+    }
+    for (auto& kv : pts) {
+      ent.push_back((int64_t)kv.second[0]);
+      dxs.push_back(kv.second[1]);
+      dxs.push_back(kv.second[2]);
+      dxs.push_back(kv.second[3]);
+    }
+    ptr.push_back((int32_t)ent.size());
+  }
+  upload(L.d_pnode, node);
+  upload(L.d_pptr, ptr);
+  upload(L.d_pent, ent);
+  upload(L.d_pdx, dxs);
+  L.plist.nnodes = (int32_t)node.size();
+  L.plist.node = L.d_pnode.as<int32_t>();
+  L.plist.ptr = L.d_pptr.as<int32_t>();
+  L.plist.ent = L.d_pent.as<int64_t>();
+  L.plist.dx = L.d_pdx.as<double>();
+  L.carreau_ready = true;
+}
+
+void carreau_viscosity(hhg_ctx* c, int l, const hhg_carreau& p, const double* u, double* mu) {
+  carreau_setup(c, l);
+  LevelHost& L = c->lv(l);
+  CarreauParams cp{p.eta0, p.eta_inf, p.kappa, p.r};
+  CK(launch_carreau(L.dev, L.slope.data(), L.plist, cp, u, mu, c->stream));
+}
+
 void mg_check(hhg_ctx* c) {
   need_ready(c, true);
   if (!c->mg_ready) THROW(HHG_ERR_STATE, "call hhg_mg_setup after setting the coefficient");
@@ -719,6 +817,104 @@ hhg_status hhg_stokes_residual(hhg_ctx* c, int level, hhg_dtype dt, const void* 
     const double n2 = stokes_sweep<T>(c, level, OP_RESID, (const T*)f, (const T*)x, (T*)r, norm2 != nullptr);
     if (norm2) *norm2 = n2;
   });
+}
+
+hhg_status hhg_carreau_viscosity(hhg_ctx* c, int level, const hhg_carreau* p, const void* u, void* mu) {
+  return guard(c, [&] {
+    need_ready(c, false);
+    if (!p || !u || !mu) THROW(HHG_ERR_ARG, "null argument");
+    if (!(p->eta0 > 0.0 && p->eta_inf >= 0.0 && p->kappa >= 0.0)) THROW(HHG_ERR_ARG, "Carreau parameters");
+    carreau_viscosity(c, level, *p, (const double*)u, (double*)mu);
+  });
+}
+
+double node_maxnorm(hhg_ctx* c, int l, int comps, const double* a, const double* b) {
+  LevelHost& L = c->lv(l);
+  CK(launch_node_maxnorm(L.d_mask_own.as<uint8_t>(), L.entries, comps, a, b, c->scratch.as<double>(),
+                         c->scalar.as<double>(), c->stream));
+  CK(cudaMemcpyAsync(c->pinned, c->scalar.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  wait_stream(c);
+  return c->pinned[0];
+}
+
+hhg_status hhg_picard(hhg_ctx* c, const hhg_picard_opts* o, const void* f, void* x, hhg_picard_report* rep) {
+  bool not_converged = false;
+  hhg_status st = guard(c, [&] {
+    if (!o || !f || !x) THROW(HHG_ERR_ARG, "null argument");
+    need_stokes(c);
+    const int l = o->level;
+    if (l != c->level_max) THROW(HHG_ERR_ARG, "the Picard iteration runs on the finest level");
+    LevelHost& L = c->lv(l);
+    if (o->max_picard < 1 || !(o->picard_tol > 0.0) || !(o->final_rtol > 0.0) || !(o->step_rtol > 0.0) ||
+        o->step_max_iter < 1)
+      THROW(HHG_ERR_ARG, "Picard options");
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!L.d_mu64.p || L.d_mu64.bytes < L.entries * sizeof(double)) CK(L.d_mu64.alloc(L.entries * sizeof(double)));
+    ensure_swork<double>(c, l);
+    double* mu = L.d_mu64.as<double>();
+    double* xprev = swork<double>(L)[7].as<double>();
+    const int64_t n4 = 4 * L.entries;
+    auto check = [&](hhg_status s) {
+      if (s != HHG_OK && s != HHG_ERR_NOT_CONVERGED) THROW(s, "%s", c->err.c_str());
+    };
+    auto update_mu = [&]() {
+      carreau_viscosity(c, l, o->carreau, (const double*)x, mu);
+      check(hhg_set_coefficient(c, mu, HHG_F64));
+      check(hhg_mg_setup(c));
+    };
+    hhg_picard_report R{};
+    update_mu();  // mu^0 = mu(u^0)
+    hhg_solve_opts so{};
+    so.method = HHG_SOLVE_STOKES_IR_MINRES;
+    so.level = l;
+    so.dt = HHG_F64;
+    so.rtol = o->step_rtol;
+    so.max_iter = 1;
+    so.inner_rtol = std::max(o->step_rtol, 1e-6);
+    so.inner_max_iter = o->step_max_iter;
+    double change = 1.0;
+    for (int it = 1; it <= o->max_picard; ++it) {
+      CK(cudaMemcpyAsync(xprev, x, n4 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      hhg_solve_report sr{};
+      check(hhg_solve(c, &so, f, x, &sr));
+      R.minres_iterations += sr.inner_iterations;
+      const double du = node_maxnorm(c, l, 3, (const double*)x, xprev);
+      const double um = node_maxnorm(c, l, 3, (const double*)x, nullptr);
+      change = um > 0.0 ? du / um : 0.0;
+      R.picard_iterations = it;
+      update_mu();  // mu^{n+1} = mu(u^{n+1})
+      if (!std::isfinite(change)) THROW(HHG_ERR_NUMERIC, "non-finite velocity");
+      if (change < o->picard_tol) break;
+    }
+    R.last_change = change;
+    // final solve to final_rtol and the last viscosity update (Alg. 1)
+    hhg_solve_opts fo = so;
+    fo.rtol = o->final_rtol;
+    fo.max_iter = 50;
+    fo.inner_rtol = std::min(1e-2, std::max(o->final_rtol, 1e-6));
+    hhg_solve_report fr{};
+    check(hhg_solve(c, &fo, f, x, &fr));
+    R.minres_iterations += fr.inner_iterations;
+    R.final_rel_residual = fr.rel_residual;
+    carreau_viscosity(c, l, o->carreau, (const double*)x, mu);
+    check(hhg_set_coefficient(c, mu, HHG_F64));
+    R.mu_max = node_maxnorm(c, l, 1, mu, nullptr);
+    {
+      std::vector<double> h(L.entries);
+      CK(cudaMemcpyAsync(h.data(), mu, L.entries * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      wait_stream(c);
+      R.mu_min = *std::min_element(h.begin(), h.end());
+    }
+    R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    R.converged = change < o->picard_tol && fr.converged;
+    if (rep) *rep = R;
+    not_converged = !R.converged;
+  });
+  if (st == HHG_OK && not_converged) {
+    c->err = "Picard iteration did not converge";
+    return HHG_ERR_NOT_CONVERGED;
+  }
+  return st;
 }
 
 hhg_status hhg_solve(hhg_ctx* c, const hhg_solve_opts* o, const void* f, void* x, hhg_solve_report* rep) {

@@ -218,6 +218,147 @@ __global__ void k_add_const(int64_t n, T v, T* __restrict__ d) {
     d[e] += v;
 }
 
+__device__ __forceinline__ double carreau_mu(const CarreauParams& cp, const double g[3][3]) {
+  // |eps(u)|^2 = eps : eps with eps = (grad u + grad u^T) / 2
+  double e2 = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double e = 0.5 * (g[c][j] + g[j][c]);
+      e2 += e * e;
+    }
+  return cp.eta_inf + (cp.eta0 - cp.eta_inf) * pow(1.0 + cp.kappa * e2, cp.r);
+}
+
+// macro-interior nodes: the patch is point-symmetric, so the affine least-squares slope is
+// G^{-1} sum_d dx_d (u(i+d) - u(i)) with G = sum_d dx_d dx_d^T (precomputed as Q)
+__global__ void k_carreau_interior(const LevelDev L, const SlopeOp q, int macro, CarreauParams cp,
+                                   const double* __restrict__ u, double* __restrict__ mu) {
+  const int32_t tile = L.tiles_lin[blockIdx.x];
+  const int n = L.n;
+  const int k = tile >> 20;
+  const int M = n - 1 - k;
+  const int t = (tile & 0xFFFFF) + threadIdx.x;
+  if (t >= (M - 1) * M / 2) return;
+  // (j, i) of the t-th interior point of the slice
+  const float b = (float)(2 * M - 1);
+  int uu = (int)floorf(0.5f * (b - sqrtf(fmaxf(b * b - 8.0f * (float)t, 0.0f))));
+  uu = max(0, min(uu, M - 2));
+  if (((uu + 1) * (2 * M - uu - 2)) / 2 <= t) ++uu;
+  if ((uu * (2 * M - uu - 1)) / 2 > t) --uu;
+  const int j = uu + 1;
+  const int i = t - (uu * (2 * M - uu - 1)) / 2 + 1;
+  const int64_t E = L.entries;
+  const int64_t base = (int64_t)macro * L.nt;
+  const int64_t c0 = base + lattice_index(n, i, j, k);
+  double g[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+  for (int d = 0; d < NDIR; ++d) {
+    const int64_t e = base + lattice_index(n, i + dir_di(d), j + dir_dj(d), k + dir_dk(d));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double du = u[e + c * E] - u[c0 + c * E];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) g[c][a] = fma(q.Q[d][a], du, g[c][a]);
+    }
+  }
+  mu[c0] = carreau_mu(cp, g);
+}
+
+// skeleton nodes: general affine least squares min sum (c + b.dx - u)^2 over the patch
+// (normal equations, 4x4, Gaussian elimination with partial pivoting); every copy written
+__global__ void k_carreau_skeleton(const LevelDev L, const PatchLists P, CarreauParams cp,
+                                   const double* __restrict__ u, double* __restrict__ mu) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P.nnodes) return;
+  const int64_t E = L.entries;
+  double A[4][4] = {{0}}, R[4][3] = {{0}};
+  for (int q = P.ptr[t]; q < P.ptr[t + 1]; ++q) {
+    const double w[4] = {1.0, P.dx[3 * q], P.dx[3 * q + 1], P.dx[3 * q + 2]};
+    const int64_t e = P.ent[q];
+    const double uv[3] = {u[e], u[e + E], u[e + 2 * E]};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int b = 0; b < 4; ++b) A[a][b] += w[a] * w[b];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) R[a][c] += w[a] * uv[c];
+    }
+  }
+  for (int col = 0; col < 4; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < 4; ++r)
+      if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+    if (piv != col) {
+      for (int q = 0; q < 4; ++q) {
+        const double tmp = A[piv][q];
+        A[piv][q] = A[col][q];
+        A[col][q] = tmp;
+      }
+      for (int c = 0; c < 3; ++c) {
+        const double tmp = R[piv][c];
+        R[piv][c] = R[col][c];
+        R[col][c] = tmp;
+      }
+    }
+    const double inv = 1.0 / A[col][col];
+    for (int r = 0; r < 4; ++r) {
+      if (r == col) continue;
+      const double f = A[r][col] * inv;
+      for (int q = col; q < 4; ++q) A[r][q] -= f * A[col][q];
+      for (int c = 0; c < 3; ++c) R[r][c] -= f * R[col][c];
+    }
+  }
+  double g[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) g[c][a] = R[a + 1][c] / A[a + 1][a + 1];
+  const double m = carreau_mu(cp, g);
+  const int s = P.node[t];
+  for (int q = L.skel_ptr[s]; q < L.skel_ptr[s + 1]; ++q) {
+    const SkelInc I = L.skel_inc[q];
+    mu[(int64_t)I.macro * L.nt + lattice_index(L.n, I.i, I.j, I.k)] = m;
+  }
+}
+
+// max over masked entries of the 2-norm of (a - b) over `comps` components (b nullable)
+__global__ void k_node_maxnorm(const uint8_t* __restrict__ mask, int64_t E, int comps, const double* __restrict__ a,
+                               const double* __restrict__ b, double* partials) {
+  double v = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    if (!mask[e]) continue;
+    double s = 0.0;
+    for (int c = 0; c < comps; ++c) {
+      const double d = a[e + c * E] - (b ? b[e + c * E] : 0.0);
+      s += d * d;
+    }
+    v = fmax(v, sqrt(s));
+  }
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double m = threadIdx.x < (blockDim.x + 31) / 32 ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) partials[blockIdx.x] = m;
+  }
+}
+
+__global__ void k_reduce_max(const double* __restrict__ p, int64_t count, double* out) {
+  double v = 0.0;
+  for (int64_t q = threadIdx.x; q < count; q += blockDim.x) v = fmax(v, p[q]);
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double m = threadIdx.x < (blockDim.x + 31) / 32 ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) *out = m;
+  }
+}
+
 inline int grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
   if (g > 152 * 16) g = 152 * 16;
@@ -247,6 +388,22 @@ int launch_dot_masked(const uint8_t* mask, int64_t E, int comps, const T* a, con
                       int64_t* partial_count, void* stream) {
   k_dot<T><<<DOT_BLOCKS, 256, 0, (cudaStream_t)stream>>>(mask, E, comps, a, b, partials);
   *partial_count = DOT_BLOCKS;
+  return (int)cudaGetLastError();
+}
+
+int launch_node_maxnorm(const uint8_t* mask, int64_t E, int comps, const double* a, const double* b,
+                        double* partials, double* out, void* stream) {
+  k_node_maxnorm<<<DOT_BLOCKS, 256, 0, (cudaStream_t)stream>>>(mask, E, comps, a, b, partials);
+  k_reduce_max<<<1, 1024, 0, (cudaStream_t)stream>>>(partials, DOT_BLOCKS, out);
+  return (int)cudaGetLastError();
+}
+
+int launch_carreau(const LevelDev& L, const SlopeOp* q_host, const PatchLists& P, const CarreauParams& cp,
+                   const double* u, double* mu, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int m = 0; m < L.nmacro && L.ntiles_lin > 0; ++m)
+    k_carreau_interior<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, q_host[m], m, cp, u, mu);
+  if (P.nnodes > 0) k_carreau_skeleton<<<(P.nnodes + 127) / 128, 128, 0, s>>>(L, P, cp, u, mu);
   return (int)cudaGetLastError();
 }
 
