@@ -1,0 +1,121 @@
+"""Oracle for the learned preconditioner's convolutional network (plain numpy, FP64 with
+BF16 rounding where the GPU stores BF16).
+
+Test infrastructure only (see the package docstring).  The network is not part of the
+paper; this module defines what the GPU kernels compute so that their forward pass and
+gradients can be checked.
+
+Network: 4 layers of 3x3x3 convolutions on a channels-last grid (z, y, x, c) with zero
+padding, 16 hidden channels, ReLU after the first three layers:
+
+    a_0 = bf16(input)   (4 channels, padded with zeros to 16)
+    z_l = conv(a_{l-1}, W_l) + b_l,   a_l = bf16(relu(z_l))  (l = 1..3),   out = z_4[..., :3]
+
+conv(a, W)[v, o] = sum_{t, i} a[v + off(t), i] W[t, i, o], tap t = (dz+1)*9 + (dy+1)*3 + (dx+1),
+offsets dz, dy, dx in {-1, 0, 1}.  Weights are BF16 values (W[t, i, o], 27 x 16 x 16),
+biases FP32.  Loss: mean over the batch, voxels and the 3 output channels of
+(out - target)^2.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+C = 16
+NLAYERS = 4
+CIN, COUT = 4, 3
+
+
+def bf16(a):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    a = np.asarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    rounding = ((u >> 16) & 1) + 0x7FFF
+    u = ((u + rounding) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def offsets():
+    return [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+
+
+def conv(a, W):
+    """a: (B, D, H, X, Cin), W: (27, Cin, Cout) -> (B, D, H, X, Cout), zero padding."""
+    B, D, H, X, _ = a.shape
+    p = np.pad(a, ((0, 0), (1, 1), (1, 1), (1, 1), (0, 0)))
+    out = np.zeros((B, D, H, X, W.shape[2]))
+    for t, (dz, dy, dx) in enumerate(offsets()):
+        sl = p[:, 1 + dz:1 + dz + D, 1 + dy:1 + dy + H, 1 + dx:1 + dx + X, :]
+        out += sl @ W[t]
+    return out
+
+
+def conv_transpose_input(g, W):
+    """Gradient of conv w.r.t. its input: sum over taps of g shifted back times W^T."""
+    B, D, H, X, _ = g.shape
+    p = np.pad(g, ((0, 0), (1, 1), (1, 1), (1, 1), (0, 0)))
+    out = np.zeros((B, D, H, X, W.shape[1]))
+    for t, (dz, dy, dx) in enumerate(offsets()):
+        sl = p[:, 1 - dz:1 - dz + D, 1 - dy:1 - dy + H, 1 - dx:1 - dx + X, :]
+        out += sl @ W[t].T
+    return out
+
+
+def conv_weight_grad(a, g):
+    """dL/dW[t, i, o] = sum_v a[v + off(t), i] g[v, o]."""
+    B, D, H, X, Cin = a.shape
+    p = np.pad(a, ((0, 0), (1, 1), (1, 1), (1, 1), (0, 0)))
+    dW = np.zeros((27, Cin, g.shape[-1]))
+    for t, (dz, dy, dx) in enumerate(offsets()):
+        sl = p[:, 1 + dz:1 + dz + D, 1 + dy:1 + dy + H, 1 + dx:1 + dx + X, :]
+        dW[t] = np.einsum("bzyxi,bzyxo->io", sl, g)
+    return dW
+
+
+def init_params(seed):
+    """He-style initialisation (BF16-rounded weights, zero biases)."""
+    rng = np.random.default_rng(seed)
+    Ws, bs = [], []
+    for l in range(NLAYERS):
+        cin = CIN if l == 0 else C
+        W = np.zeros((27, C, C))
+        W[:, :cin, :] = rng.normal(size=(27, cin, C)) * np.sqrt(2.0 / (27 * cin))
+        if l == NLAYERS - 1:
+            W[:, :, COUT:] = 0.0
+            W *= 0.1
+        Ws.append(bf16(W))
+        bs.append(np.zeros(C))
+    return Ws, bs
+
+
+def forward(x, Ws, bs, round_bf16=True):
+    """x: (B, D, H, X, 4) -> (out (B, D, H, X, 3), activations)."""
+    rnd = bf16 if round_bf16 else (lambda v: np.asarray(v, dtype=np.float64))
+    a = np.zeros(x.shape[:4] + (C,))
+    a[..., :CIN] = rnd(x)
+    acts = [a]
+    for l in range(NLAYERS):
+        z = conv(acts[-1], Ws[l]) + bs[l]
+        if l < NLAYERS - 1:
+            acts.append(rnd(np.maximum(z, 0.0)))
+        else:
+            out = z
+    return out[..., :COUT], acts
+
+
+def loss_and_grads(x, target, Ws, bs, round_bf16=True):
+    """MSE loss and its gradients w.r.t. all weights and biases (the BF16 rounding of the
+    activations is treated as identity in the backward pass, as on the GPU)."""
+    out, acts = forward(x, Ws, bs, round_bf16)
+    n = out.size
+    diff = out - target
+    loss = float((diff**2).sum() / n)
+    g = np.zeros(out.shape[:4] + (C,))
+    g[..., :COUT] = 2.0 * diff / n
+    dWs, dbs = [None] * NLAYERS, [None] * NLAYERS
+    for l in reversed(range(NLAYERS)):
+        dWs[l] = conv_weight_grad(acts[l], g)
+        dbs[l] = g.sum(axis=(0, 1, 2, 3))
+        if l > 0:
+            g = conv_transpose_input(g, Ws[l]) * (acts[l] > 0)
+    return loss, dWs, dbs
