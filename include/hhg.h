@@ -200,7 +200,13 @@ typedef enum {
    * preconditioned by blockdiag(one velocity V-cycle, mu_i / m_i) with m the lumped
    * pressure mass; the pressure is shifted to zero mean (sum m_i p_i = 0) at the end. */
   HHG_SOLVE_STOKES_MINRES = 4,
-  HHG_SOLVE_STOKES_IR_MINRES = 5  /* FP64 iterative refinement around FP32 MINRES */
+  HHG_SOLVE_STOKES_IR_MINRES = 5, /* FP64 iterative refinement around FP32 MINRES */
+  /* Elasticity on a mesh whose nodes lie on an axis-aligned uniform lattice: FP64
+   * iterative refinement around FP32 flexible CG preconditioned by one V-cycle plus the
+   * learned correction (hhg_learn_*; parameters must be set), or by the V-cycle alone
+   * (IR_FCG, the same solver without the network). */
+  HHG_SOLVE_IR_FCG_LEARNED = 6,
+  HHG_SOLVE_IR_FCG = 7
 } hhg_solve_method;
 
 typedef struct {
@@ -307,6 +313,90 @@ hhg_status hhg_picard(hhg_ctx* ctx, const hhg_picard_opts* opts, const void* f_d
  * (bounded wait). */
 hhg_status hhg_residual_noalloc(hhg_ctx* ctx, int level, hhg_dtype dt, const void* f_dev, const void* x_dev,
                                 void* r_dev, double* norm2_host);
+
+/* ------------------------------------------------------------------------------------
+ * Learned preconditioner.  Not part of the paper: a small convolutional network that
+ * maps what a V-cycle leaves behind to a further correction, used inside flexible CG.
+ *
+ * Grid.  The network runs on the node grid of a level: the mesh's nodes must lie on an
+ * axis-aligned uniform lattice (Kuhn-split cubes, axis-aligned corner tetrahedra);
+ * voxel (z, y, x) at index (z*H + y)*W + x holds that lattice point's node (empty voxels
+ * are zero).  Other meshes get HHG_ERR_UNSUPPORTED.
+ *
+ * Network.  4 layers of 3x3x3 convolutions, 16 channels, zero padding, ReLU after the
+ * first three; BF16 activations and weights, FP32 accumulation (tensor cores), FP32
+ * biases and master weights.  hhg_learn_num_params() = 4*(27*16*16 + 16) parameters,
+ * layer l at offset l*6928: W_l[t][i][o] at (t*16 + i)*16 + o (tap t = (dz+1)*9 +
+ * (dy+1)*3 + (dx+1), input channel i, output channel o), then b_l[16].
+ *
+ * Input features per voxel (7 channels): r1/s (3), D z0/s (3), log k - mean log k (1),
+ * where for a residual r: z0 = V-cycle(r), r1 = r - A z0, D = point diagonal of A,
+ * s = RMS of D z0 over the free nodes.  Output (3 channels): D c / s.  The correction
+ * is z = z0 + alpha c with alpha = (c, r1)/(c, A c), the minimiser of the energy norm of
+ * the error over that line (alpha = 0, i.e. the plain V-cycle, when it is not finite).
+ *
+ * Training pairs.  From a random error e0 on the grid: e1 = e0 - V-cycle(A e0),
+ * r1 = A e1; the pair is (features(r1, z0), target D e1 / s); `cycles` steps per e0.
+ * Loss: mean squared error over voxels and the 3 output channels; Adam (0.9, 0.999,
+ * 1e-8) with a cosine learning-rate decay to 5% of lr. */
+int64_t hhg_learn_num_params(void);
+/* He-normal initialisation (std sqrt(2/(27*fan_in)), last layer x0.1; BF16 values,
+ * zero biases) from a seeded generator; resets the optimiser state. */
+hhg_status hhg_learn_init(hhg_ctx* ctx, uint64_t seed);
+/* Copy the n = hhg_learn_num_params() FP32 parameters out of / into the context
+ * (set: all must be finite; resets the optimiser state; weights are used in BF16). */
+hhg_status hhg_learn_get_params(hhg_ctx* ctx, float* params_host, int64_t n);
+hhg_status hhg_learn_set_params(hhg_ctx* ctx, const float* params_host, int64_t n);
+/* Node-grid dimensions (D, H, W) of a level and its number of voxels with a free node. */
+hhg_status hhg_learn_grid(hhg_ctx* ctx, int level, int* dhw_host, int64_t* free_voxels);
+/* Network forward pass on B grids of D x H x W voxels: x_dev FP32 [B][D][H][W][cin]
+ * (cin <= 16, rounded to BF16), out_dev FP32 [B][D][H][W][3]. */
+hhg_status hhg_learn_forward(hhg_ctx* ctx, const float* x_dev, int cin, int B, int D, int H, int W, float* out_dev);
+/* Loss against target_dev (FP32 [B][D][H][W][3]) and its gradient with respect to all
+ * parameters (grad_host: hhg_learn_num_params() floats, nullable), for checking the
+ * backward pass.  Waits for the stream. */
+hhg_status hhg_learn_loss_grad(hhg_ctx* ctx, const float* x_dev, int cin, const float* target_dev, int B, int D, int H,
+                               int W, double* loss_host, float* grad_host);
+/* Allocate storage for `capacity` training pairs of `level` (drops stored pairs). */
+hhg_status hhg_learn_reserve_pairs(hhg_ctx* ctx, int level, int64_t capacity);
+/* Append `cycles` pairs from the error e0_grid_dev (FP32 [D][H][W][3] on the node grid
+ * of `level`; Dirichlet nodes are ignored).  Needs hhg_mg_setup.  count_host: pairs stored. */
+hhg_status hhg_learn_collect(hhg_ctx* ctx, int level, const float* e0_grid_dev, int cycles, int64_t* count_host);
+/* Copy stored pair `index` to the host: in_host FP32 [D][H][W][7] (the BF16 inputs),
+ * target_host FP32 [D][H][W][3] (either nullable).  Waits. */
+hhg_status hhg_learn_get_pair(hhg_ctx* ctx, int64_t index, float* in_host, float* target_host);
+
+typedef struct {
+  int steps;      /* optimiser steps */
+  int batch;      /* crops per step */
+  int crop;       /* crop edge in voxels (<= every pair-grid dimension) */
+  double lr;      /* peak learning rate */
+  uint64_t seed;  /* of the crop choices */
+} hhg_learn_train_opts;
+
+typedef struct {
+  double loss_first;  /* mean loss of the first 10% of steps */
+  double loss_last;   /* mean loss of the last 10% of steps */
+  int64_t pairs;
+  double seconds;     /* host wall time */
+} hhg_learn_train_report;
+
+/* Train on the stored pairs: each step takes `batch` random crops (pair and origin from
+ * the seed), runs the forward and backward passes and one Adam step.  Waits. */
+hhg_status hhg_learn_train(hhg_ctx* ctx, const hhg_learn_train_opts* opts, hhg_learn_train_report* report);
+/* One preconditioner application z = z0 + alpha c for the FP32 residual r_dev (3*E),
+ * (use_net = 0: z = z0, the V-cycle alone); alpha_host receives alpha.  Waits. */
+hhg_status hhg_learn_precondition(hhg_ctx* ctx, int level, int use_net, const void* r_dev, void* z_dev,
+                                  double* alpha_host);
+
+typedef struct {
+  int64_t applications;  /* preconditioner applications with the network */
+  int64_t fallbacks;     /* of which fell back to the V-cycle (alpha = 0) */
+  double alpha_mean, alpha_min, alpha_max;
+} hhg_learn_stats_report;
+
+/* Statistics since the last reset (reset != 0 clears them after reading). */
+hhg_status hhg_learn_stats(hhg_ctx* ctx, hhg_learn_stats_report* report, int reset);
 
 /* End-to-end apply with host buffers: copies x_host (3*E values of type dt,
  * library layout; pinned memory gives full copy bandwidth) to a library-owned

@@ -1,20 +1,27 @@
-"""Oracle for the learned preconditioner's convolutional network (plain numpy, FP64 with
-BF16 rounding where the GPU stores BF16).
+"""Oracle for the learned preconditioner: its convolutional network (plain numpy, FP64 with
+BF16 rounding where the GPU stores BF16) and the preconditioner application around it.
 
 Test infrastructure only (see the package docstring).  The network is not part of the
-paper; this module defines what the GPU kernels compute so that their forward pass and
-gradients can be checked.
+paper; this module defines what the GPU kernels compute so that their forward pass,
+gradients, training pairs and preconditioner application can be checked.
 
 Network: 4 layers of 3x3x3 convolutions on a channels-last grid (z, y, x, c) with zero
 padding, 16 hidden channels, ReLU after the first three layers:
 
-    a_0 = bf16(input)   (4 channels, padded with zeros to 16)
+    a_0 = bf16(input)   (CIN = 7 channels, padded with zeros to 16)
     z_l = conv(a_{l-1}, W_l) + b_l,   a_l = bf16(relu(z_l))  (l = 1..3),   out = z_4[..., :3]
 
 conv(a, W)[v, o] = sum_{t, i} a[v + off(t), i] W[t, i, o], tap t = (dz+1)*9 + (dy+1)*3 + (dx+1),
 offsets dz, dy, dx in {-1, 0, 1}.  Weights are BF16 values (W[t, i, o], 27 x 16 x 16),
 biases FP32.  Loss: mean over the batch, voxels and the 3 output channels of
 (out - target)^2.
+
+Preconditioner application for a residual r (vectors node-major (N, 3), FP64):
+z0 = V-cycle(r), r1 = r - A z0, D = point diagonal, s = RMS of D z0 over the free DoFs;
+input features per grid voxel of a free node: r1/s, D z0/s, log k - mean log k (the
+last also at Dirichlet nodes); correction c = s out / D on free nodes;
+z = z0 + alpha c with alpha = (c, r1) / (c, A c).  Training pair from an error e:
+z0 = V-cycle(A e), e1 = e - z0, r1 = A e1, target D e1 / s.
 """
 
 from __future__ import annotations
@@ -23,7 +30,7 @@ import numpy as np
 
 C = 16
 NLAYERS = 4
-CIN, COUT = 4, 3
+CIN, COUT = 7, 3
 
 
 def bf16(a):
@@ -72,12 +79,12 @@ def conv_weight_grad(a, g):
     return dW
 
 
-def init_params(seed):
+def init_params(seed, cin0=CIN):
     """He-style initialisation (BF16-rounded weights, zero biases)."""
     rng = np.random.default_rng(seed)
     Ws, bs = [], []
     for l in range(NLAYERS):
-        cin = CIN if l == 0 else C
+        cin = cin0 if l == 0 else C
         W = np.zeros((27, C, C))
         W[:, :cin, :] = rng.normal(size=(27, cin, C)) * np.sqrt(2.0 / (27 * cin))
         if l == NLAYERS - 1:
@@ -89,10 +96,10 @@ def init_params(seed):
 
 
 def forward(x, Ws, bs, round_bf16=True):
-    """x: (B, D, H, X, 4) -> (out (B, D, H, X, 3), activations)."""
+    """x: (B, D, H, X, cin <= 16) -> (out (B, D, H, X, 3), activations)."""
     rnd = bf16 if round_bf16 else (lambda v: np.asarray(v, dtype=np.float64))
     a = np.zeros(x.shape[:4] + (C,))
-    a[..., :CIN] = rnd(x)
+    a[..., :x.shape[-1]] = rnd(x)
     acts = [a]
     for l in range(NLAYERS):
         z = conv(acts[-1], Ws[l]) + bs[l]
@@ -119,3 +126,68 @@ def loss_and_grads(x, target, Ws, bs, round_bf16=True):
         if l > 0:
             g = conv_transpose_input(g, Ws[l]) * (acts[l] > 0)
     return loss, dWs, dbs
+
+
+def grid_index(coords, h):
+    """(z, y, x) voxel of every node of an axis-aligned lattice with spacing h and dims."""
+    lo = coords.min(axis=0)
+    ijk = np.rint((coords - lo) / h).astype(np.int64)
+    assert np.allclose(lo + ijk * h, coords, atol=1e-9)
+    dims = tuple(int(v) for v in ijk.max(axis=0)[::-1] + 1)  # (D, H, W) = (nz, ny, nx)
+    return ijk[:, ::-1], dims
+
+
+def _dot_free(a, b, dirichlet):
+    fr = ~np.asarray(dirichlet)
+    return float((a[fr] * b[fr]).sum())
+
+
+def features(vox, dims, dirichlet, k, r1, z0, D):
+    """Input grid (1, D, H, W, CIN) and the scale s (see the module docstring)."""
+    fr = ~np.asarray(dirichlet)
+    s2 = ((D[fr] * z0[fr]) ** 2).sum() / (3.0 * max(fr.sum(), 1))
+    s = np.sqrt(s2) if s2 > 0 else 1.0
+    X = np.zeros((1,) + dims + (CIN,))
+    lk = np.log(k)
+    lk = lk - lk.mean()
+    X[0, vox[:, 0], vox[:, 1], vox[:, 2], 6] = lk
+    f = np.zeros((len(k), 6))
+    f[:, :3] = r1 / s
+    f[:, 3:] = D * z0 / s
+    f[~fr] = 0.0
+    X[0, vox[fr, 0], vox[fr, 1], vox[fr, 2], :6] = f[fr]
+    return X, s
+
+
+def correction(A, dirichlet, vox, dims, k, r, z0, Ws, bs):
+    """(z, alpha, c): the learned preconditioner's output for residual r given z0 = V-cycle(r)."""
+    fr = ~np.asarray(dirichlet)
+    Dg = A.diagonal().reshape(-1, 3).copy()
+    Dg[~fr] = 1.0
+    r1 = r - (A @ z0.reshape(-1)).reshape(-1, 3)
+    r1[~fr] = 0.0
+    X, s = features(vox, dims, dirichlet, k, r1, z0, Dg)
+    out, _ = forward(X, Ws, bs)
+    c = s * out[0, vox[:, 0], vox[:, 1], vox[:, 2], :] / Dg
+    c[~fr] = 0.0
+    Ac = (A @ c.reshape(-1)).reshape(-1, 3)
+    d2 = _dot_free(c, Ac, dirichlet)
+    alpha = _dot_free(c, r1, dirichlet) / d2 if d2 > 0 else 0.0
+    return z0 + alpha * c, alpha, c
+
+
+def training_pair(A, dirichlet, vox, dims, k, e, vcycle):
+    """(inputs (1, D, H, W, CIN), target (1, D, H, W, 3), e1) of one multigrid step from error e."""
+    fr = ~np.asarray(dirichlet)
+    Dg = A.diagonal().reshape(-1, 3).copy()
+    Dg[~fr] = 1.0
+    r = (A @ e.reshape(-1)).reshape(-1, 3)
+    r[~fr] = 0.0
+    z0 = vcycle(r)
+    e1 = e - z0
+    r1 = (A @ e1.reshape(-1)).reshape(-1, 3)
+    r1[~fr] = 0.0
+    X, s = features(vox, dims, dirichlet, k, r1, z0, Dg)
+    T = np.zeros((1,) + dims + (COUT,))
+    T[0, vox[fr, 0], vox[fr, 1], vox[fr, 2], :] = (Dg * e1 / s)[fr]
+    return X, T, e1

@@ -32,6 +32,7 @@ class HhgError(RuntimeError):
 
 SMOOTH_JACOBI, SMOOTH_CHEBYSHEV = 0, 1
 SOLVE_PCG_JACOBI, SOLVE_MG_CG, SOLVE_IR_MG_CG, SOLVE_MG, SOLVE_STOKES_MINRES, SOLVE_STOKES_IR_MINRES = 0, 1, 2, 3, 4, 5
+SOLVE_IR_FCG_LEARNED, SOLVE_IR_FCG = 6, 7
 
 
 class hhg_mg_params(C.Structure):
@@ -65,6 +66,25 @@ class hhg_picard_report(C.Structure):
     _fields_ = [("picard_iterations", C.c_int), ("minres_iterations", C.c_int), ("final_rel_residual", C.c_double),
                 ("last_change", C.c_double), ("mu_min", C.c_double), ("mu_max", C.c_double),
                 ("seconds", C.c_double), ("converged", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class hhg_learn_train_opts(C.Structure):
+    _fields_ = [("steps", C.c_int), ("batch", C.c_int), ("crop", C.c_int), ("lr", C.c_double), ("seed", C.c_uint64)]
+
+
+class hhg_learn_train_report(C.Structure):
+    _fields_ = [("loss_first", C.c_double), ("loss_last", C.c_double), ("pairs", C.c_int64), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class hhg_learn_stats_report(C.Structure):
+    _fields_ = [("applications", C.c_int64), ("fallbacks", C.c_int64), ("alpha_mean", C.c_double),
+                ("alpha_min", C.c_double), ("alpha_max", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -111,8 +131,22 @@ _SIGS = {
     "hhg_profile": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "hhg_residual_noalloc": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.POINTER(C.c_double)],
+    "hhg_learn_num_params": [],
+    "hhg_learn_init": [C.c_void_p, C.c_uint64],
+    "hhg_learn_get_params": [C.c_void_p, C.c_void_p, C.c_int64],
+    "hhg_learn_set_params": [C.c_void_p, C.c_void_p, C.c_int64],
+    "hhg_learn_grid": [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int64)],
+    "hhg_learn_forward": [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p],
+    "hhg_learn_loss_grad": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                            C.POINTER(C.c_double), C.c_void_p],
+    "hhg_learn_reserve_pairs": [C.c_void_p, C.c_int, C.c_int64],
+    "hhg_learn_collect": [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int64)],
+    "hhg_learn_get_pair": [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p],
+    "hhg_learn_train": [C.c_void_p, C.POINTER(hhg_learn_train_opts), C.POINTER(hhg_learn_train_report)],
+    "hhg_learn_precondition": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)],
+    "hhg_learn_stats": [C.c_void_p, C.POINTER(hhg_learn_stats_report), C.c_int],
 }
-_RESTYPE = {"hhg_last_error": C.c_char_p}
+_RESTYPE = {"hhg_last_error": C.c_char_p, "hhg_learn_num_params": C.c_int64}
 
 
 def declared_symbols():
@@ -338,4 +372,83 @@ def hhg_picard(ctx, f, x, level, eta0=1.0, eta_inf=1e-3, kappa=1.0, r=-0.25, pic
     if st == 5 and allow_not_converged:
         return rep.as_dict()
     _check(ctx, st)
+    return rep.as_dict()
+
+
+def hhg_learn_num_params():
+    return int(load().hhg_learn_num_params())
+
+
+def hhg_learn_init(ctx, seed=0):
+    _check(ctx, load().hhg_learn_init(ctx, int(seed)))
+
+
+def hhg_learn_get_params(ctx):
+    n = hhg_learn_num_params()
+    out = np.empty(n, dtype=np.float32)
+    _check(ctx, load().hhg_learn_get_params(ctx, out.ctypes.data, n))
+    return out
+
+
+def hhg_learn_set_params(ctx, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(ctx, load().hhg_learn_set_params(ctx, p.ctypes.data, p.size))
+
+
+def hhg_learn_grid(ctx, level):
+    """((D, H, W), number of voxels holding a free node) of the level's node grid."""
+    dhw = np.zeros(3, dtype=np.int32)
+    nf = C.c_int64()
+    _check(ctx, load().hhg_learn_grid(ctx, level, dhw.ctypes.data, C.byref(nf)))
+    return tuple(int(v) for v in dhw), nf.value
+
+
+def hhg_learn_forward(ctx, x, cin, B, D, H, W, out):
+    _check(ctx, load().hhg_learn_forward(ctx, _ptr(x), cin, B, D, H, W, _ptr(out)))
+
+
+def hhg_learn_loss_grad(ctx, x, cin, target, B, D, H, W):
+    """(loss, gradient as FP32 numpy array in the parameter layout)."""
+    loss = C.c_double()
+    g = np.empty(hhg_learn_num_params(), dtype=np.float32)
+    _check(ctx, load().hhg_learn_loss_grad(ctx, _ptr(x), cin, _ptr(target), B, D, H, W, C.byref(loss), g.ctypes.data))
+    return loss.value, g
+
+
+def hhg_learn_reserve_pairs(ctx, level, capacity):
+    _check(ctx, load().hhg_learn_reserve_pairs(ctx, level, int(capacity)))
+
+
+def hhg_learn_collect(ctx, level, e0_grid, cycles):
+    n = C.c_int64()
+    _check(ctx, load().hhg_learn_collect(ctx, level, _ptr(e0_grid), cycles, C.byref(n)))
+    return n.value
+
+
+def hhg_learn_get_pair(ctx, index, dhw):
+    """(inputs FP32 (D, H, W, 7), targets FP32 (D, H, W, 3)) of stored pair `index`."""
+    D, H, W = dhw
+    x = np.empty((D, H, W, 7), dtype=np.float32)
+    y = np.empty((D, H, W, 3), dtype=np.float32)
+    _check(ctx, load().hhg_learn_get_pair(ctx, int(index), x.ctypes.data, y.ctypes.data))
+    return x, y
+
+
+def hhg_learn_train(ctx, steps, batch, crop, lr=2e-3, seed=0):
+    o = hhg_learn_train_opts(steps, batch, crop, lr, seed)
+    rep = hhg_learn_train_report()
+    _check(ctx, load().hhg_learn_train(ctx, C.byref(o), C.byref(rep)))
+    return rep.as_dict()
+
+
+def hhg_learn_precondition(ctx, level, use_net, r, z):
+    """z = V-cycle(r) + alpha * correction (FP32 library-layout vectors); returns alpha."""
+    a = C.c_double()
+    _check(ctx, load().hhg_learn_precondition(ctx, level, int(use_net), _ptr(r), _ptr(z), C.byref(a)))
+    return a.value
+
+
+def hhg_learn_stats(ctx, reset=False):
+    rep = hhg_learn_stats_report()
+    _check(ctx, load().hhg_learn_stats(ctx, C.byref(rep), int(reset)))
     return rep.as_dict()

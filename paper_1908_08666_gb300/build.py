@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhhgs.so")
 
-SOURCES = ["hhg_host.cpp", "hhg_solve.cpp", "hhg_sweep.cu", "hhg_vec.cu"]
+SOURCES = ["hhg_host.cpp", "hhg_solve.cpp", "hhg_learn.cpp", "hhg_sweep.cu", "hhg_vec.cu", "hhg_learn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-O2",
          "-I" + os.path.join(os.path.dirname(HERE), "include")]
@@ -27,7 +27,7 @@ def nvcc():
 
 
 def _compile(src, extra):
-    obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
+    obj = os.path.join(OUT, src + ".o")
     cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -140,6 +140,35 @@ struct LevelHost {
   DevMem d_cdof, d_cinv64, d_cinv32;  // and the inverse of the coarse matrix restricted to them
 };
 
+// Node grid of a level whose nodes lie on an axis-aligned uniform lattice (learned
+// preconditioner): voxel g = (z * H + y) * W + x.
+struct LearnGrid {
+  int D = 0, H = 0, W = 0;
+  int64_t V = 0, nfree = 0;
+  int64_t coeff_version = -1;  // of the log-coefficient feature
+  DevMem gent, gfree, e2g, efree, logk;
+  DevMem lw[10];  // FP32 work vectors (3*E) of the learned preconditioner and its FCG
+};
+
+// Learned preconditioner: network parameters, optimiser state, training pairs, buffers.
+struct LearnState {
+  bool have_params = false;
+  int adam_step = 0;
+  DevMem params, grad, m, v, fwd, bwd;  // LN_NPARAM floats; packed fragments LN_LAYERS * LN_PACK words
+  std::map<int, std::unique_ptr<LearnGrid>> grids;
+  // training pairs of one level: inputs (LN_PAIR_IN BF16 per voxel) and targets (3 FP32)
+  int pair_level = -1;
+  int64_t pair_cap = 0, pair_count = 0;
+  DevMem pin, ptg;
+  // activation buffers (16-channel BF16), outputs, gradients, partial sums
+  int64_t act_voxels = 0;
+  DevMem act[4], gb[2], out, tgt;
+  DevMem wpart, bpart, dpart, dscal;
+  // statistics of the preconditioner applications
+  int64_t applications = 0, fallbacks = 0;
+  double alpha_sum = 0.0, alpha_min = 0.0, alpha_max = 0.0;
+};
+
 
 }  // namespace host
 }  // namespace hhg
@@ -164,6 +193,8 @@ struct hhg_ctx {
   hhg_problem prob{};
   bool have_problem = false;
   bool have_coeff = false;
+  int64_t coeff_version = 0;  // incremented by hhg_set_coefficient
+  std::unique_ptr<LearnState> learn;
   OpFlags flags{1, 0, 0};
   DevMem scratch;   // reduction partials
   DevMem scalar;    // device scalars

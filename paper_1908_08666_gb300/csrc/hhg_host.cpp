@@ -914,6 +914,7 @@ hhg_status hhg_set_coefficient(hhg_ctx* c, const void* k, hhg_dtype dt) {
       CK(launch_convert<double, float>(L.entries, L.d_k64.as<double>(), L.d_k32.as<float>(), c->stream));
     }
     c->have_coeff = true;
+    ++c->coeff_version;
     // the multigrid data (diagonals, lambda_max, coarse inverse) depend on the coefficient
     c->mg_ready = false;
     for (int l = c->level_min; l <= c->level_max; ++l) c->levels[l]->lambda_set = false;

@@ -1,0 +1,680 @@
+// Learned preconditioner of libhhgs (not part of the paper): a 4-layer 3x3x3 conv net
+// with 16 channels on the node grid, trained on the GPU on residual/error pairs that the
+// multigrid solver itself produces, and used inside flexible CG as a correction after
+// the V-cycle.  Kernels in hhg_learn.cu; conventions in hhg_learn.h.
+//
+// Preconditioner application for a residual r (FP32):
+//   z0 = V-cycle(r) (zero initial guess),  r1 = r - A z0   (the residual the V-cycle leaves),
+//   c  = s * D^-1 N(features(r1, z0, log k))               (network correction),
+//   z  = z0 + alpha c,  alpha = (c, r1) / (c, A c)
+// alpha minimises the energy norm of the error A^-1 r - z over the line z0 + alpha c, so
+// an application never leaves a larger error (in that norm) than the V-cycle alone; when
+// alpha is not finite (e.g. c = 0) the application falls back to z = z0.
+//
+// Training pairs: for a random error e (given on the grid by the caller), one multigrid
+// step gives z0 = V-cycle(A e), the remaining error e1 = e - z0 and residual r1 = A e1;
+// the pair is (features(r1, z0), D e1 / s).  Further steps continue from e1.
+#include <cmath>
+#include <cstring>
+
+#include "hhg_ctx.h"
+#include "hhg_learn.h"
+#include "hhg_solver.h"
+
+namespace {
+
+using namespace hhg;
+using namespace hhg::host;
+
+// work vectors of LearnGrid::lw
+enum { LW_Z0 = 0, LW_AZ0, LW_R1, LW_C, LW_AC, LW_R, LW_Z, LW_AZ, LW_P, LW_Q };
+
+LearnState& state(hhg_ctx* c) {
+  if (!c->learn) c->learn.reset(new LearnState());
+  return *c->learn;
+}
+
+uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+double uniform01(uint64_t& s) { return ((splitmix64(s) >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+
+// standard normal by the Box-Muller transform
+double normal(uint64_t& s) {
+  const double u1 = uniform01(s), u2 = uniform01(s);
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+// nearest BF16 value (ties to even) of a float
+float round_bf16(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u = ((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16) << 16;
+  float y;
+  std::memcpy(&y, &u, 4);
+  return y;
+}
+
+void need_elasticity(hhg_ctx* c) {
+  need_ready(c, true);
+  if (c->prob.kind != HHG_ELASTICITY) THROW(HHG_ERR_UNSUPPORTED, "the learned preconditioner needs an elasticity problem");
+}
+
+void need_params(LearnState& S) {
+  if (!S.have_params) THROW(HHG_ERR_STATE, "network parameters not set (hhg_learn_init or hhg_learn_set_params)");
+}
+
+void repack(hhg_ctx* c, LearnState& S) {
+  CK(launch_pack(S.params.as<float>(), S.fwd.as<uint32_t>(), S.bwd.as<uint32_t>(), c->stream));
+}
+
+void alloc_params(hhg_ctx* c, LearnState& S) {
+  if (S.params.p) return;
+  const size_t nb = LN_NPARAM * sizeof(float);
+  CK(S.params.alloc(nb));
+  CK(S.grad.alloc(nb));
+  CK(S.m.alloc(nb));
+  CK(S.v.alloc(nb));
+  CK(S.fwd.alloc(LN_LAYERS * LN_PACK * sizeof(uint32_t)));
+  CK(S.bwd.alloc(LN_LAYERS * LN_PACK * sizeof(uint32_t)));
+  CK(S.dscal.alloc(8 * sizeof(double)));
+}
+
+void reset_adam(hhg_ctx* c, LearnState& S) {
+  CK(cudaMemsetAsync(S.m.p, 0, S.m.bytes, c->stream));
+  CK(cudaMemsetAsync(S.v.p, 0, S.v.bytes, c->stream));
+  S.adam_step = 0;
+}
+
+void upload_params(hhg_ctx* c, LearnState& S, const std::vector<float>& h) {
+  alloc_params(c, S);
+  CK(cudaMemcpyAsync(S.params.p, h.data(), LN_NPARAM * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  wait_stream(c);  // h is the caller's or a temporary buffer
+  repack(c, S);
+  reset_adam(c, S);
+  S.have_params = true;
+}
+
+// activation buffers for V voxels
+void ensure_acts(hhg_ctx* c, LearnState& S, int64_t V) {
+  if (S.act_voxels >= V) return;
+  const size_t b16 = (size_t)V * LN_C * 2;
+  for (auto& a : S.act) CK(a.alloc(b16));
+  for (auto& g : S.gb) CK(g.alloc(b16));
+  CK(S.out.alloc((size_t)V * LN_COUT * sizeof(float)));
+  CK(S.tgt.alloc((size_t)V * LN_COUT * sizeof(float)));
+  CK(S.dpart.alloc((size_t)std::max<int64_t>(mse_partials(V), 1) * sizeof(double)));
+  S.act_voxels = V;
+}
+
+void ensure_grad_scratch(hhg_ctx* c, LearnState& S, GridShape s) {
+  const size_t wp = (size_t)wgrad_partials(s) * LN_WSIZE * sizeof(float);
+  if (S.wpart.bytes < wp) CK(S.wpart.alloc(wp));
+  const size_t bp = (size_t)bgrad_partials(s.voxels()) * 16 * sizeof(float);
+  if (S.bpart.bytes < bp) CK(S.bpart.alloc(bp));
+}
+
+const float* layer_bias(LearnState& S, int l) { return S.params.as<float>() + (int64_t)l * LN_LSIZE + LN_WSIZE; }
+const uint32_t* layer_fwd(LearnState& S, int l) { return S.fwd.as<uint32_t>() + (int64_t)l * LN_PACK; }
+const uint32_t* layer_bwd(LearnState& S, int l) { return S.bwd.as<uint32_t>() + (int64_t)l * LN_PACK; }
+
+// forward pass from act[0]: act[1..3] = hidden activations, out = FP32 output channels
+void forward(hhg_ctx* c, LearnState& S, GridShape s, float* out) {
+  for (int l = 0; l < LN_LAYERS; ++l) {
+    const bool last = l == LN_LAYERS - 1;
+    CK(launch_conv(S.act[l].p, layer_fwd(S, l), layer_bias(S, l), last ? nullptr : S.act[l + 1].p,
+                   last ? out : nullptr, LN_COUT, nullptr, s, last ? 0 : 1, c->stream));
+  }
+}
+
+// inference with two activation buffers (act[0] holds the input; act[0] and act[1] alternate)
+void forward_inference(hhg_ctx* c, LearnState& S, GridShape s, float* out) {
+  for (int l = 0; l < LN_LAYERS; ++l) {
+    const bool last = l == LN_LAYERS - 1;
+    CK(launch_conv(S.act[l & 1].p, layer_fwd(S, l), layer_bias(S, l), last ? nullptr : S.act[(l + 1) & 1].p,
+                   last ? out : nullptr, LN_COUT, nullptr, s, last ? 0 : 1, c->stream));
+  }
+}
+
+// backward pass after forward(): MSE against tgt into *loss (device), gradients into S.grad
+void backward(hhg_ctx* c, LearnState& S, GridShape s, const float* out, const float* tgt, double* loss) {
+  const int64_t V = s.voxels();
+  ensure_grad_scratch(c, S, s);
+  CK(launch_mse(out, tgt, V, S.gb[0].p, S.dpart.as<double>(), loss, c->stream));
+  int cur = 0;
+  for (int l = LN_LAYERS - 1; l >= 0; --l) {
+    float* gW = S.grad.as<float>() + (int64_t)l * LN_LSIZE;
+    CK(launch_wgrad(S.act[l].p, S.gb[cur].p, S.wpart.as<float>(), gW, s, c->stream));
+    CK(launch_bgrad(S.gb[cur].p, V, S.bpart.as<float>(), gW + LN_WSIZE, c->stream));
+    if (l > 0) {
+      CK(launch_conv(S.gb[cur].p, layer_bwd(S, l), nullptr, S.gb[cur ^ 1].p, nullptr, 0, S.act[l].p, s, 0,
+                     c->stream));
+      cur ^= 1;
+    }
+  }
+}
+
+// Node grid of level l: every entry's lattice point must sit on an axis-aligned uniform
+// lattice (spacing = the smallest nonzero coordinate step of the macros' lattice vectors).
+LearnGrid& grid(hhg_ctx* c, int l) {
+  LearnState& S = state(c);
+  LevelHost& L = c->lv(l);
+  auto it = S.grids.find(l);
+  LearnGrid* G = it == S.grids.end() ? nullptr : it->second.get();
+  if (!G) {
+    const int n = L.n;
+    const int M = (int)c->tets.size();
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, h[3] = {1e300, 1e300, 1e300};
+    for (int m = 0; m < M; ++m)
+      for (int q = 0; q < 4; ++q) {
+        const Vec3d& v = c->xyz[c->tets[m][q]];
+        const double p[3] = {v.x, v.y, v.z};
+        for (int a = 0; a < 3; ++a) {
+          lo[a] = std::min(lo[a], p[a]);
+          hi[a] = std::max(hi[a], p[a]);
+        }
+        if (q == 0) continue;
+        const Vec3d& v0 = c->xyz[c->tets[m][0]];
+        const double d[3] = {(v.x - v0.x) / n, (v.y - v0.y) / n, (v.z - v0.z) / n};
+        for (int a = 0; a < 3; ++a)
+          if (std::fabs(d[a]) > 1e-12 * (1.0 + std::fabs(hi[a] - lo[a]))) h[a] = std::min(h[a], std::fabs(d[a]));
+      }
+    int dims[3];
+    auto steps = [&](double x, int a) {
+      const double s = x / h[a];
+      const double r = std::round(s);
+      if (std::fabs(s - r) > 1e-6) THROW(HHG_ERR_UNSUPPORTED, "mesh nodes do not lie on an axis-aligned uniform lattice");
+      return (int64_t)r;
+    };
+    for (int a = 0; a < 3; ++a) {
+      if (!(h[a] < 1e299)) THROW(HHG_ERR_UNSUPPORTED, "degenerate macro mesh for the node grid");
+      dims[a] = (int)steps(hi[a] - lo[a], a) + 1;
+    }
+    const int64_t V = (int64_t)dims[0] * dims[1] * dims[2];
+    if (V > 8 * L.nunique + 64) THROW(HHG_ERR_UNSUPPORTED, "node grid too sparse (%lld voxels for %lld nodes)",
+                                      (long long)V, (long long)L.nunique);
+    std::unique_ptr<LearnGrid> ng(new LearnGrid());
+    G = ng.get();
+    G->W = dims[0];
+    G->H = dims[1];
+    G->D = dims[2];
+    G->V = V;
+    std::vector<int64_t> gent(V, -1), e2g(L.entries, -1);
+    std::vector<uint8_t> gfree(V, 0), efree(L.entries, 0);
+    for (int m = 0; m < M; ++m) {
+      int64_t o[3], s1[3], s2[3], s3[3];
+      const Vec3d& v0 = c->xyz[c->tets[m][0]];
+      const double p0[3] = {v0.x, v0.y, v0.z};
+      const Vec3d* vv[3] = {&c->xyz[c->tets[m][1]], &c->xyz[c->tets[m][2]], &c->xyz[c->tets[m][3]]};
+      int64_t* sv[3] = {s1, s2, s3};
+      for (int a = 0; a < 3; ++a) o[a] = steps(p0[a] - lo[a], a);
+      for (int q = 0; q < 3; ++q) {
+        const double p[3] = {vv[q]->x, vv[q]->y, vv[q]->z};
+        for (int a = 0; a < 3; ++a) sv[q][a] = steps((p[a] - p0[a]) / n, a);
+      }
+      for (int k = 0; k <= n; ++k)
+        for (int j = 0; j <= n - k; ++j)
+          for (int i = 0; i <= n - k - j; ++i) {
+            const int64_t e = (int64_t)m * L.nt + lattice_index(n, i, j, k);
+            int64_t ix[3];
+            for (int a = 0; a < 3; ++a) ix[a] = o[a] + i * s1[a] + j * s2[a] + k * s3[a];
+            const int64_t g = (ix[2] * dims[1] + ix[1]) * dims[0] + ix[0];
+            if (g < 0 || g >= V) THROW(HHG_ERR_UNSUPPORTED, "node outside the node grid");
+            const int64_t u = L.entry_to_unique[e];
+            e2g[e] = g;
+            efree[e] = L.unique_dir[u] ? 0 : 1;
+            if (gent[g] < 0) {
+              gent[g] = e;
+              gfree[g] = efree[e];
+            } else if (L.entry_to_unique[gent[g]] != u) {
+              THROW(HHG_ERR_UNSUPPORTED, "two nodes share a grid point");
+            }
+          }
+    }
+    for (int64_t g = 0; g < V; ++g) G->nfree += gfree[g];
+    upload(G->gent, gent);
+    upload(G->gfree, gfree);
+    upload(G->e2g, e2g);
+    upload(G->efree, efree);
+    CK(G->logk.alloc(V * sizeof(float)));
+    S.grids[l] = std::move(ng);
+  }
+  if (G->coeff_version != c->coeff_version) {
+    // log-coefficient feature: log k at the voxel's node minus its mean over the nodes
+    std::vector<double> k(L.entries);
+    CK(cudaMemcpyAsync(k.data(), L.d_k64.p, L.entries * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    wait_stream(c);
+    std::vector<int64_t> gent(G->V);
+    CK(cudaMemcpy(gent.data(), G->gent.p, G->V * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    std::vector<float> lk(G->V, 0.f);
+    double sum = 0.0;
+    int64_t cnt = 0;
+    for (int64_t g = 0; g < G->V; ++g)
+      if (gent[g] >= 0) {
+        const double kv = k[gent[g]];
+        if (!(kv > 0.0)) THROW(HHG_ERR_NUMERIC, "coefficient must be positive for the learned preconditioner");
+        sum += std::log(kv);
+        ++cnt;
+      }
+    const double mean = cnt ? sum / cnt : 0.0;
+    for (int64_t g = 0; g < G->V; ++g)
+      if (gent[g] >= 0) lk[g] = (float)(std::log(k[gent[g]]) - mean);
+    CK(cudaMemcpy(G->logk.p, lk.data(), G->V * sizeof(float), cudaMemcpyHostToDevice));
+    G->coeff_version = c->coeff_version;
+  }
+  return *G;
+}
+
+float* lwork(hhg_ctx* c, LearnGrid& G, int l, int q) {
+  if (!G.lw[q].p) {
+    const size_t b = 3 * (size_t)c->lv(l).entries * sizeof(float);
+    CK(G.lw[q].alloc(b));
+    CK(cudaMemsetAsync(G.lw[q].p, 0, b, c->stream));
+  }
+  return G.lw[q].as<float>();
+}
+
+void copy32(hhg_ctx* c, int l, const float* src, float* dst) {
+  CK(cudaMemcpyAsync(dst, src, 3 * (size_t)c->lv(l).entries * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+}
+
+// z = z0 + alpha c and az = A z (see the file comment); use_net = false: z = z0
+double precondition(hhg_ctx* c, int l, const float* r, float* z, float* az, bool use_net) {
+  LearnState& S = state(c);
+  LearnGrid& G = grid(c, l);
+  const int64_t E = c->lv(l).entries, n = 3 * E;
+  float* z0 = lwork(c, G, l, LW_Z0);
+  float* az0 = lwork(c, G, l, LW_AZ0);
+  CK(cudaMemsetAsync(z0, 0, n * sizeof(float), c->stream));
+  vcycle32(c, l, r, z0);
+  apply32(c, l, z0, az0);
+  double alpha = 0.0;
+  if (use_net) {
+    need_params(S);
+    float* r1 = lwork(c, G, l, LW_R1);
+    float* cc = lwork(c, G, l, LW_C);
+    float* acc = lwork(c, G, l, LW_AC);
+    const float* dinv = dinv32(c, l);
+    ensure_acts(c, S, G.V);
+    copy32(c, l, r, r1);
+    CK(launch_axpby<float>(n, -1.f, az0, 1.f, r1, c->stream));
+    double* ssum = S.dscal.as<double>();
+    CK(launch_feature_norm(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), z0, dinv, S.dpart.as<double>(), ssum,
+                           c->stream));
+    const double cnt = 3.0 * (double)std::max<int64_t>(G.nfree, 1);
+    CK(launch_features(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), G.logk.as<float>(), r1, z0, nullptr, dinv,
+                       ssum, cnt, S.act[0].p, nullptr, nullptr, c->stream));
+    forward_inference(c, S, GridShape{1, G.D, G.H, G.W}, S.out.as<float>());
+    CK(launch_grid_to_lib(E, G.e2g.as<int64_t>(), G.efree.as<uint8_t>(), S.out.as<float>(), dinv, ssum, cnt, cc,
+                          c->stream));
+    apply32(c, l, cc, acc);
+    const double d1 = dot32(c, l, cc, r1);
+    const double d2 = dot32(c, l, cc, acc);
+    alpha = (d2 > 0.0 && std::isfinite(d1) && std::isfinite(d2)) ? d1 / d2 : 0.0;
+    if (!std::isfinite(alpha)) alpha = 0.0;
+    S.applications++;
+    if (alpha == 0.0) S.fallbacks++;
+    S.alpha_sum += alpha;
+    S.alpha_min = S.applications == 1 ? alpha : std::min(S.alpha_min, alpha);
+    S.alpha_max = S.applications == 1 ? alpha : std::max(S.alpha_max, alpha);
+    copy32(c, l, z0, z);
+    copy32(c, l, az0, az);
+    if (alpha != 0.0) {
+      CK(launch_axpby<float>(n, (float)alpha, cc, 1.f, z, c->stream));
+      CK(launch_axpby<float>(n, (float)alpha, acc, 1.f, az, c->stream));
+    }
+  } else {
+    copy32(c, l, z0, z);
+    copy32(c, l, az0, az);
+  }
+  return alpha;
+}
+
+// Flexible CG (one-term A-orthogonalisation: p_k = z_k - (z_k, A p_{k-1}) / (p_{k-1}, A p_{k-1}) p_{k-1})
+// on A x = f in FP32; A p follows from the preconditioner's A z by the same recurrence.
+SolverResult fcg(hhg_ctx* c, int l, const float* f, float* x, double rtol, int max_iter, bool use_net) {
+  LearnGrid& G = grid(c, l);
+  const int64_t n = 3 * c->lv(l).entries;
+  float* r = lwork(c, G, l, LW_R);
+  float* z = lwork(c, G, l, LW_Z);
+  float* az = lwork(c, G, l, LW_AZ);
+  float* p = lwork(c, G, l, LW_P);
+  float* q = lwork(c, G, l, LW_Q);
+  SolverResult res;
+  const double r0 = residual32(c, l, f, x, r);
+  res.r0 = std::sqrt(r0);
+  if (!std::isfinite(r0)) THROW(HHG_ERR_NUMERIC, "non-finite initial residual");
+  if (r0 == 0.0) {
+    res.converged = true;
+    return res;
+  }
+  precondition(c, l, r, z, az, use_net);
+  copy32(c, l, z, p);
+  copy32(c, l, az, q);
+  double rp = dot32(c, l, r, p);
+  double rr = r0;
+  for (int it = 1; it <= max_iter; ++it) {
+    const double pq = dot32(c, l, p, q);
+    if (!(pq > 0.0) || !std::isfinite(pq)) THROW(HHG_ERR_NUMERIC, "FCG breakdown (p.Ap = %g)", pq);
+    const double alpha = rp / pq;
+    CK(launch_axpby<float>(n, (float)alpha, p, 1.f, x, c->stream));
+    CK(launch_axpby<float>(n, (float)(-alpha), q, 1.f, r, c->stream));
+    rr = dot32(c, l, r, r);
+    res.iterations = it;
+    if (!std::isfinite(rr)) THROW(HHG_ERR_NUMERIC, "non-finite residual");
+    if (std::sqrt(rr / r0) <= rtol) {
+      res.converged = true;
+      break;
+    }
+    precondition(c, l, r, z, az, use_net);
+    const double beta = -dot32(c, l, z, q) / pq;
+    CK(launch_axpby<float>(n, 1.f, z, (float)beta, p, c->stream));
+    CK(launch_axpby<float>(n, 1.f, az, (float)beta, q, c->stream));
+    rp = dot32(c, l, r, p);
+  }
+  res.rel = std::sqrt(rr / r0);
+  return res;
+}
+
+}  // namespace
+
+namespace hhg {
+namespace host {
+
+// FP64 iterative refinement around FP32 flexible CG with the learned preconditioner
+// (use_net = false: the same solver with the plain V-cycle)
+void learned_ir(hhg_ctx* c, const hhg_solve_opts* o, const double* f, double* x, bool use_net, hhg_solve_report& R) {
+  need_elasticity(c);
+  mg_ready_check(c);
+  const int l = o->level;
+  if (use_net) need_params(state(c));
+  if (!(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || o->inner_max_iter < 1) THROW(HHG_ERR_ARG, "inner tol");
+  ensure_work64(c, l);
+  const int64_t n = 3 * c->lv(l).entries;
+  double* r64 = work64(c, l, 10);
+  float* r32 = work32(c, l, 10);
+  float* e32 = work32(c, l, 11);
+  const double r0 = residual64(c, l, f, x, r64);
+  R.residual0 = std::sqrt(r0);
+  double rr = r0;
+  for (int it = 1; it <= o->max_iter && r0 > 0.0 && std::sqrt(rr / r0) > o->rtol; ++it) {
+    CK(launch_convert<double, float>(n, r64, r32, c->stream));
+    CK(cudaMemsetAsync(e32, 0, n * sizeof(float), c->stream));
+    SolverResult cr = fcg(c, l, r32, e32, o->inner_rtol, o->inner_max_iter, use_net);
+    R.inner_iterations += cr.iterations;
+    CK(launch_add_f32_to_f64(n, e32, x, c->stream));
+    rr = residual64(c, l, f, x, r64);
+    R.iterations = it;
+    if (!std::isfinite(rr)) THROW(HHG_ERR_NUMERIC, "non-finite residual");
+  }
+  R.rel_residual = r0 > 0.0 ? std::sqrt(rr / r0) : 0.0;
+  R.converged = R.rel_residual <= o->rtol;
+}
+
+}  // namespace host
+}  // namespace hhg
+
+extern "C" {
+
+int64_t hhg_learn_num_params(void) { return LN_NPARAM; }
+
+hhg_status hhg_learn_init(hhg_ctx* c, uint64_t seed) {
+  return guard(c, [&] {
+    LearnState& S = state(c);
+    std::vector<float> h(LN_NPARAM, 0.f);
+    uint64_t s = seed ^ 0x6C6561726E6564ull;
+    for (int l = 0; l < LN_LAYERS; ++l) {
+      const int cin = l == 0 ? LN_CIN : LN_C;
+      const int cout = l == LN_LAYERS - 1 ? LN_COUT : LN_C;
+      const double sd = std::sqrt(2.0 / (LN_TAPS * cin)) * (l == LN_LAYERS - 1 ? 0.1 : 1.0);
+      float* W = h.data() + (int64_t)l * LN_LSIZE;
+      for (int t = 0; t < LN_TAPS; ++t)
+        for (int i = 0; i < cin; ++i)
+          for (int o = 0; o < cout; ++o) W[(t * LN_C + i) * LN_C + o] = round_bf16((float)(sd * normal(s)));
+    }
+    upload_params(c, S, h);
+  });
+}
+
+hhg_status hhg_learn_get_params(hhg_ctx* c, float* params_host, int64_t n) {
+  return guard(c, [&] {
+    LearnState& S = state(c);
+    need_params(S);
+    if (!params_host || n != LN_NPARAM) THROW(HHG_ERR_ARG, "need %d parameters", LN_NPARAM);
+    CK(cudaMemcpyAsync(params_host, S.params.p, LN_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    wait_stream(c);
+  });
+}
+
+hhg_status hhg_learn_set_params(hhg_ctx* c, const float* params_host, int64_t n) {
+  return guard(c, [&] {
+    if (!params_host || n != LN_NPARAM) THROW(HHG_ERR_ARG, "need %d parameters", LN_NPARAM);
+    for (int64_t q = 0; q < n; ++q)
+      if (!std::isfinite(params_host[q])) THROW(HHG_ERR_ARG, "non-finite parameter %lld", (long long)q);
+    std::vector<float> h(params_host, params_host + n);
+    upload_params(c, state(c), h);
+  });
+}
+
+hhg_status hhg_learn_grid(hhg_ctx* c, int level, int* dhw, int64_t* free_voxels) {
+  return guard(c, [&] {
+    need_ready(c, true);
+    LearnGrid& G = grid(c, level);
+    if (dhw) {
+      dhw[0] = G.D;
+      dhw[1] = G.H;
+      dhw[2] = G.W;
+    }
+    if (free_voxels) *free_voxels = G.nfree;
+  });
+}
+
+hhg_status hhg_learn_forward(hhg_ctx* c, const float* x, int cin, int B, int D, int H, int W, float* out) {
+  return guard(c, [&] {
+    LearnState& S = state(c);
+    need_params(S);
+    if (!x || !out || cin < 1 || cin > LN_C || B < 1 || D < 1 || H < 1 || W < 1) THROW(HHG_ERR_ARG, "bad arguments");
+    const GridShape s{B, D, H, W};
+    ensure_acts(c, S, s.voxels());
+    CK(launch_to_bf16(s.voxels(), cin, x, S.act[0].p, c->stream));
+    forward_inference(c, S, s, out);
+  });
+}
+
+hhg_status hhg_learn_loss_grad(hhg_ctx* c, const float* x, int cin, const float* target, int B, int D, int H, int W,
+                               double* loss_host, float* grad_host) {
+  return guard(c, [&] {
+    LearnState& S = state(c);
+    need_params(S);
+    if (!x || !target || cin < 1 || cin > LN_C || B < 1 || D < 1 || H < 1 || W < 1) THROW(HHG_ERR_ARG, "bad arguments");
+    const GridShape s{B, D, H, W};
+    ensure_acts(c, S, s.voxels());
+    CK(launch_to_bf16(s.voxels(), cin, x, S.act[0].p, c->stream));
+    forward(c, S, s, S.out.as<float>());
+    double* loss = S.dscal.as<double>() + 1;
+    backward(c, S, s, S.out.as<float>(), target, loss);
+    CK(cudaMemcpyAsync(c->pinned, loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (grad_host)
+      CK(cudaMemcpyAsync(grad_host, S.grad.p, LN_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    wait_stream(c);
+    if (loss_host) *loss_host = c->pinned[0];
+  });
+}
+
+hhg_status hhg_learn_reserve_pairs(hhg_ctx* c, int level, int64_t capacity) {
+  return guard(c, [&] {
+    need_elasticity(c);
+    if (capacity < 1) THROW(HHG_ERR_ARG, "capacity");
+    LearnState& S = state(c);
+    LearnGrid& G = grid(c, level);
+    CK(S.pin.alloc((size_t)capacity * G.V * LN_PAIR_IN * 2));
+    CK(S.ptg.alloc((size_t)capacity * G.V * 3 * sizeof(float)));
+    S.pair_level = level;
+    S.pair_cap = capacity;
+    S.pair_count = 0;
+  });
+}
+
+hhg_status hhg_learn_collect(hhg_ctx* c, int level, const float* e0_grid, int cycles, int64_t* count) {
+  return guard(c, [&] {
+    need_elasticity(c);
+    mg_ready_check(c);
+    LearnState& S = state(c);
+    if (!e0_grid || cycles < 1) THROW(HHG_ERR_ARG, "bad arguments");
+    if (S.pair_level != level) THROW(HHG_ERR_STATE, "reserve pair storage for level %d first", level);
+    if (S.pair_count + cycles > S.pair_cap) THROW(HHG_ERR_ARG, "pair storage full (%lld)", (long long)S.pair_cap);
+    LearnGrid& G = grid(c, level);
+    const int64_t E = c->lv(level).entries, n = 3 * E;
+    float* e = lwork(c, G, level, LW_R);
+    float* r = lwork(c, G, level, LW_Z);
+    float* z0 = lwork(c, G, level, LW_Z0);
+    float* az0 = lwork(c, G, level, LW_AZ0);
+    float* r1 = lwork(c, G, level, LW_R1);
+    const float* dinv = dinv32(c, level);
+    if (S.dpart.bytes < (size_t)mse_partials(G.V) * sizeof(double))
+      CK(S.dpart.alloc((size_t)mse_partials(G.V) * sizeof(double)));
+    CK(launch_grid_to_lib(E, G.e2g.as<int64_t>(), G.efree.as<uint8_t>(), e0_grid, nullptr, nullptr, 1.0, e,
+                          c->stream));
+    const double cnt = 3.0 * (double)std::max<int64_t>(G.nfree, 1);
+    double* ssum = S.dscal.p ? S.dscal.as<double>() : nullptr;
+    if (!ssum) {
+      CK(S.dscal.alloc(8 * sizeof(double)));
+      ssum = S.dscal.as<double>();
+    }
+    for (int j = 0; j < cycles; ++j) {
+      apply32(c, level, e, r);
+      CK(cudaMemsetAsync(z0, 0, n * sizeof(float), c->stream));
+      vcycle32(c, level, r, z0);
+      apply32(c, level, z0, az0);
+      copy32(c, level, r, r1);
+      CK(launch_axpby<float>(n, -1.f, az0, 1.f, r1, c->stream));
+      CK(launch_axpby<float>(n, -1.f, z0, 1.f, e, c->stream));  // e <- e1 = e - z0
+      CK(launch_feature_norm(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), z0, dinv, S.dpart.as<double>(),
+                             ssum, c->stream));
+      const int64_t p = S.pair_count++;
+      CK(launch_features(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), G.logk.as<float>(), r1, z0, e, dinv,
+                         ssum, cnt, nullptr, (char*)S.pin.p + (size_t)p * G.V * LN_PAIR_IN * 2,
+                         S.ptg.as<float>() + (size_t)p * G.V * 3, c->stream));
+    }
+    wait_stream(c);
+    if (count) *count = S.pair_count;
+  });
+}
+
+hhg_status hhg_learn_get_pair(hhg_ctx* c, int64_t index, float* in_host, float* target_host) {
+  return guard(c, [&] {
+    LearnState& S = state(c);
+    if (index < 0 || index >= S.pair_count) THROW(HHG_ERR_ARG, "pair %lld not stored", (long long)index);
+    LearnGrid& G = grid(c, S.pair_level);
+    if (in_host) {
+      std::vector<uint16_t> h((size_t)G.V * LN_PAIR_IN);
+      CK(cudaMemcpyAsync(h.data(), (const char*)S.pin.p + (size_t)index * G.V * LN_PAIR_IN * 2, h.size() * 2,
+                         cudaMemcpyDeviceToHost, c->stream));
+      wait_stream(c);
+      for (int64_t g = 0; g < G.V; ++g)
+        for (int q = 0; q < LN_CIN; ++q) {
+          const uint32_t u = (uint32_t)h[(size_t)g * LN_PAIR_IN + q] << 16;
+          std::memcpy(&in_host[(size_t)g * LN_CIN + q], &u, 4);
+        }
+    }
+    if (target_host) {
+      CK(cudaMemcpyAsync(target_host, S.ptg.as<float>() + (size_t)index * G.V * 3, (size_t)G.V * 3 * sizeof(float),
+                         cudaMemcpyDeviceToHost, c->stream));
+      wait_stream(c);
+    }
+  });
+}
+
+hhg_status hhg_learn_train(hhg_ctx* c, const hhg_learn_train_opts* o, hhg_learn_train_report* rep) {
+  return guard(c, [&] {
+    LearnState& S = state(c);
+    need_params(S);
+    if (!o || o->steps < 1 || o->batch < 1 || o->crop < 1 || !(o->lr > 0.0)) THROW(HHG_ERR_ARG, "bad options");
+    if (S.pair_count < 1) THROW(HHG_ERR_STATE, "no training pairs (hhg_learn_collect)");
+    LearnGrid& G = grid(c, S.pair_level);
+    const int Sc = o->crop;
+    if (Sc > G.D || Sc > G.H || Sc > G.W) THROW(HHG_ERR_ARG, "crop %d larger than the pair grid", Sc);
+    const auto t0 = std::chrono::steady_clock::now();
+    const GridShape s{o->batch, Sc, Sc, Sc};
+    const int64_t V = s.voxels();
+    ensure_acts(c, S, V);
+    ensure_grad_scratch(c, S, s);
+    // crop choices for every step
+    std::vector<int32_t> idx((size_t)o->steps * o->batch), org((size_t)o->steps * o->batch * 3);
+    uint64_t rs = o->seed ^ 0x747261696E696E67ull;
+    for (size_t q = 0; q < idx.size(); ++q) {
+      idx[q] = (int32_t)(splitmix64(rs) % (uint64_t)S.pair_count);
+      org[3 * q] = (int32_t)(splitmix64(rs) % (uint64_t)(G.D - Sc + 1));
+      org[3 * q + 1] = (int32_t)(splitmix64(rs) % (uint64_t)(G.H - Sc + 1));
+      org[3 * q + 2] = (int32_t)(splitmix64(rs) % (uint64_t)(G.W - Sc + 1));
+    }
+    DevMem didx, dorg, dloss;
+    upload(didx, idx);
+    upload(dorg, org);
+    CK(dloss.alloc((size_t)o->steps * sizeof(double)));
+    for (int st = 0; st < o->steps; ++st) {
+      CK(launch_crop(S.pin.p, S.ptg.as<float>(), G.D, G.H, G.W, didx.as<int32_t>() + (size_t)st * o->batch,
+                     dorg.as<int32_t>() + (size_t)st * o->batch * 3, o->batch, Sc, S.act[0].p, S.tgt.as<float>(),
+                     c->stream));
+      forward(c, S, s, S.out.as<float>());
+      backward(c, S, s, S.out.as<float>(), S.tgt.as<float>(), dloss.as<double>() + st);
+      const double lr = o->lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(3.141592653589793 * st / o->steps)));
+      CK(launch_adam(S.params.as<float>(), S.grad.as<float>(), S.m.as<float>(), S.v.as<float>(), LN_NPARAM, (float)lr,
+                     ++S.adam_step, c->stream));
+      repack(c, S);
+    }
+    std::vector<double> hl(o->steps);
+    CK(cudaMemcpyAsync(hl.data(), dloss.p, o->steps * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    wait_stream(c);
+    for (double v : hl)
+      if (!std::isfinite(v)) THROW(HHG_ERR_NUMERIC, "training diverged");
+    if (rep) {
+      const int tail = std::max(1, o->steps / 10);
+      double a = 0.0, b = 0.0;
+      for (int q = 0; q < tail; ++q) {
+        a += hl[q];
+        b += hl[o->steps - tail + q];
+      }
+      rep->loss_first = a / tail;
+      rep->loss_last = b / tail;
+      rep->pairs = S.pair_count;
+      rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+  });
+}
+
+hhg_status hhg_learn_precondition(hhg_ctx* c, int level, int use_net, const void* r, void* z, double* alpha) {
+  return guard(c, [&] {
+    need_elasticity(c);
+    mg_ready_check(c);
+    if (!r || !z) THROW(HHG_ERR_ARG, "null vector");
+    LearnGrid& G = grid(c, level);
+    float* az = lwork(c, G, level, LW_AZ);
+    const double a = precondition(c, level, (const float*)r, (float*)z, az, use_net != 0);
+    wait_stream(c);
+    if (alpha) *alpha = a;
+  });
+}
+
+hhg_status hhg_learn_stats(hhg_ctx* c, hhg_learn_stats_report* rep, int reset) {
+  return guard(c, [&] {
+    LearnState& S = state(c);
+    if (rep) {
+      rep->applications = S.applications;
+      rep->fallbacks = S.fallbacks;
+      rep->alpha_mean = S.applications ? S.alpha_sum / S.applications : 0.0;
+      rep->alpha_min = S.alpha_min;
+      rep->alpha_max = S.alpha_max;
+    }
+    if (reset) {
+      S.applications = S.fallbacks = 0;
+      S.alpha_sum = S.alpha_min = S.alpha_max = 0.0;
+    }
+  });
+}
+
+}  // extern "C"

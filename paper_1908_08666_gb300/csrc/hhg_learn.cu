@@ -1,0 +1,536 @@
+// Kernels of the learned preconditioner (not part of the paper): the 3x3x3 convolution
+// of the 16-channel network on BF16 tensor cores with FP32 accumulation (warp-level
+// mma.sync m16n8k16), its weight and bias gradients, the MSE loss, Adam, weight
+// packing, and the transfers between the library's vector layout and the node grid.
+// Layouts and conventions are those of hhg_learn.h.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "hhg_learn.h"
+
+namespace hhg {
+
+namespace {
+
+constexpr int WARPS = 4;          // warps per block of the convolution kernels
+constexpr int WG_ROWS = 32;       // 16-voxel row segments per warp in the weight gradient
+constexpr int RED_BLOCK = 256;
+constexpr int RED_MAX_BLOCKS = 1024;
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat16 a = __float2bfloat16_rn(lo), b = __float2bfloat16_rn(hi);
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+__device__ __forceinline__ uint32_t pack_raw(unsigned short lo, unsigned short hi) {
+  return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+// D += A * B, A 16x16 (row), B 16x8 (col), BF16 inputs, FP32 accumulators
+__device__ __forceinline__ void mma_bf16(float d[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// a BF16 value packed in the low (hi = 0) or high half of w is > 0
+__device__ __forceinline__ bool bf16_positive(uint32_t w, int hi) {
+  const uint32_t h = hi ? (w >> 16) : (w & 0xFFFFu);
+  return (h & 0x8000u) == 0 && (h & 0x7FFFu) != 0;
+}
+
+// Convolution.  A task is one row segment of 16 voxels along x; a warp computes all 16
+// output channels of it: per tap one A fragment (16 voxels x 16 input channels, the
+// rows shifted by the tap offset) against two B fragments (16 inputs x 8 outputs).
+// Fragment layouts of m16n8k16 (lane = 4 * gid + tig):
+//   A: a0 (row gid, cols 2 tig, +1), a1 (row gid + 8), a2 (cols + 8), a3 (row + 8, cols + 8)
+//   B: b0 (rows 2 tig, +1; col gid), b1 (rows + 8)
+//   D: d0, d1 (row gid, cols 2 tig, +1), d2, d3 (row gid + 8)
+// Voxels are rows, channels columns; a voxel's 16 channels are 8 32-bit words.
+__global__ void __launch_bounds__(WARPS * 32) k_conv(const uint32_t* __restrict__ X, const uint32_t* __restrict__ Wp,
+                                                     const float* __restrict__ bias, uint32_t* __restrict__ Y,
+                                                     float* __restrict__ Yf, int nf,
+                                                     const uint32_t* __restrict__ mask, int B, int D, int H, int W,
+                                                     int relu) {
+  __shared__ uint32_t ws[LN_PACK];
+  for (int q = threadIdx.x; q < LN_PACK; q += blockDim.x) ws[q] = Wp[q];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, tg = lane & 3;
+  float bv[2][2];
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt) {
+    bv[nt][0] = bias ? bias[nt * 8 + 2 * tg] : 0.f;
+    bv[nt][1] = bias ? bias[nt * 8 + 2 * tg + 1] : 0.f;
+  }
+  const int nxs = (W + 15) / 16;
+  const int64_t ntask = (int64_t)B * D * H * nxs;
+  for (int64_t task = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5); task < ntask;
+       task += (int64_t)gridDim.x * WARPS) {
+    const int xs = (int)(task % nxs);
+    int64_t rest = task / nxs;
+    const int y = (int)(rest % H);
+    rest /= H;
+    const int z = (int)(rest % D);
+    const int b = (int)(rest / D);
+    const int x0 = xs * 16;
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = z + dz;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = y + dy;
+        const bool rin = zz >= 0 && zz < D && yy >= 0 && yy < H;  // warp-uniform
+        const int64_t row = (((int64_t)b * D + zz) * H + yy) * W;
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int t = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+          uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+          if (rin) {
+            const int xa = x0 + g + dx, xb = x0 + g + 8 + dx;
+            if (xa >= 0 && xa < W) {
+              a0 = X[(row + xa) * 8 + tg];
+              a2 = X[(row + xa) * 8 + tg + 4];
+            }
+            if (xb >= 0 && xb < W) {
+              a1 = X[(row + xb) * 8 + tg];
+              a3 = X[(row + xb) * 8 + tg + 4];
+            }
+          }
+          const uint32_t* wb = ws + (t * 2) * 64 + lane * 2;
+          mma_bf16(acc[0], a0, a1, a2, a3, wb[0], wb[1]);
+          mma_bf16(acc[1], a0, a1, a2, a3, wb[64], wb[65]);
+        }
+      }
+    }
+    const int64_t rowo = (((int64_t)b * D + z) * H + y) * W;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int x = x0 + g + 8 * half;
+      if (x >= W) continue;
+      const int64_t v = rowo + x;
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int co = nt * 8 + 2 * tg;
+        float v0 = acc[nt][2 * half] + bv[nt][0];
+        float v1 = acc[nt][2 * half + 1] + bv[nt][1];
+        if (relu) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        }
+        if (mask) {
+          const uint32_t m = mask[v * 8 + (co >> 1)];
+          if (!bf16_positive(m, 0)) v0 = 0.f;
+          if (!bf16_positive(m, 1)) v1 = 0.f;
+        }
+        if (Y) Y[v * 8 + (co >> 1)] = pack_bf16x2(v0, v1);
+        if (Yf) {
+          if (co < nf) Yf[v * nf + co] = v0;
+          if (co + 1 < nf) Yf[v * nf + co + 1] = v1;
+        }
+      }
+    }
+  }
+}
+
+// Weight gradient of tap t = blockIdx.y: dW[t][i][o] = sum_v A[v + off(t)][i] G[v][o] as a
+// tensor-core product with the voxels as the k dimension (A fragment: input channels x
+// 16 voxels, B fragment: 16 voxels x 8 output channels).  Each warp covers WG_ROWS row
+// segments, the block sums its warps in a fixed order and writes one partial tile.
+__global__ void __launch_bounds__(WARPS * 32) k_wgrad(const unsigned short* __restrict__ A,
+                                                      const unsigned short* __restrict__ G, float* __restrict__ partial,
+                                                      int B, int D, int H, int W) {
+  __shared__ float red[WARPS][256];
+  const int t = blockIdx.y;
+  const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, tg = lane & 3;
+  const int nxs = (W + 15) / 16;
+  const int64_t nseg = (int64_t)B * D * H * nxs;
+  const int64_t seg0 = ((int64_t)blockIdx.x * WARPS + warp) * WG_ROWS;
+  float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  for (int r = 0; r < WG_ROWS; ++r) {
+    const int64_t seg = seg0 + r;
+    if (seg >= nseg) break;  // warp-uniform
+    const int xs = (int)(seg % nxs);
+    int64_t rest = seg / nxs;
+    const int y = (int)(rest % H);
+    rest /= H;
+    const int z = (int)(rest % D);
+    const int b = (int)(rest / D);
+    const int x0 = xs * 16;
+    const int64_t rowo = (((int64_t)b * D + z) * H + y) * W;
+    const int zz = z + dz, yy = y + dy;
+    const bool rin = zz >= 0 && zz < D && yy >= 0 && yy < H;
+    const int64_t rowi = (((int64_t)b * D + zz) * H + yy) * W;
+    // k index (voxel of the segment) of the four values this lane holds: 2tg, 2tg+1, 2tg+8, 2tg+9
+    unsigned short av[4][2], gv[4][2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int x = x0 + 2 * tg + (q & 1) + 8 * (q >> 1);
+      const bool vin = x < W;
+      const int xi = x + dx;
+      const bool ain = vin && rin && xi >= 0 && xi < W;
+      av[q][0] = ain ? A[(rowi + xi) * 16 + g] : (unsigned short)0;
+      av[q][1] = ain ? A[(rowi + xi) * 16 + g + 8] : (unsigned short)0;
+      gv[q][0] = vin ? G[(rowo + x) * 16 + g] : (unsigned short)0;
+      gv[q][1] = vin ? G[(rowo + x) * 16 + g + 8] : (unsigned short)0;
+    }
+    const uint32_t a0 = pack_raw(av[0][0], av[1][0]);  // row (input channel) g, k = 2tg, 2tg+1
+    const uint32_t a1 = pack_raw(av[0][1], av[1][1]);  // row g + 8
+    const uint32_t a2 = pack_raw(av[2][0], av[3][0]);  // row g, k = 2tg+8, 2tg+9
+    const uint32_t a3 = pack_raw(av[2][1], av[3][1]);  // row g + 8
+    mma_bf16(acc[0], a0, a1, a2, a3, pack_raw(gv[0][0], gv[1][0]), pack_raw(gv[2][0], gv[3][0]));
+    mma_bf16(acc[1], a0, a1, a2, a3, pack_raw(gv[0][1], gv[1][1]), pack_raw(gv[2][1], gv[3][1]));
+  }
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt) {
+    const int o = nt * 8 + 2 * tg;
+    red[warp][g * 16 + o] = acc[nt][0];
+    red[warp][g * 16 + o + 1] = acc[nt][1];
+    red[warp][(g + 8) * 16 + o] = acc[nt][2];
+    red[warp][(g + 8) * 16 + o + 1] = acc[nt][3];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) {
+    float s = 0.f;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) s += red[w][e];
+    partial[(int64_t)blockIdx.x * LN_WSIZE + t * 256 + e] = s;
+  }
+}
+
+// out[c] = sum over rows r (in order) of partial[r * ncol + c]
+__global__ void k_colsum(const float* __restrict__ partial, int64_t rows, int ncol, float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncol) return;
+  float s = 0.f;
+  for (int64_t r = 0; r < rows; ++r) s += partial[r * ncol + c];
+  out[c] = s;
+}
+
+__global__ void __launch_bounds__(RED_BLOCK) k_bgrad(const uint32_t* __restrict__ G, int64_t V,
+                                                     float* __restrict__ partial) {
+  __shared__ float s[16][RED_BLOCK / 32];
+  float acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+    const uint4* p = reinterpret_cast<const uint4*>(G + v * 8);
+    const uint4 w0 = p[0], w1 = p[1];
+    const uint32_t w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      acc[2 * q] += __uint_as_float(w[q] << 16);
+      acc[2 * q + 1] += __uint_as_float(w[q] & 0xFFFF0000u);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    float x = acc[c];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) s[c][threadIdx.x >> 5] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    float x = 0.f;
+    for (int w = 0; w < RED_BLOCK / 32; ++w) x += s[threadIdx.x][w];
+    partial[blockIdx.x * 16 + threadIdx.x] = x;
+  }
+}
+
+__global__ void __launch_bounds__(RED_BLOCK) k_mse(const float* __restrict__ out, const float* __restrict__ target,
+                                                   int64_t V, double inv_n, uint32_t* __restrict__ G,
+                                                   double* __restrict__ partial) {
+  __shared__ double s[RED_BLOCK / 32];
+  double acc = 0.0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+    float gr[LN_COUT];
+#pragma unroll
+    for (int c = 0; c < LN_COUT; ++c) {
+      const double d = (double)out[v * LN_COUT + c] - (double)target[v * LN_COUT + c];
+      acc += d * d;
+      gr[c] = (float)(2.0 * d * inv_n);
+    }
+    uint4* p = reinterpret_cast<uint4*>(G + v * 8);
+    p[0] = make_uint4(pack_bf16x2(gr[0], gr[1]), pack_bf16x2(gr[2], 0.f), 0u, 0u);
+    p[1] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0;
+    for (int w = 0; w < RED_BLOCK / 32; ++w) x += s[w];
+    partial[blockIdx.x] = x * inv_n;
+  }
+}
+
+// *out = sum of partial[0..n) (one block, fixed order)
+__global__ void __launch_bounds__(RED_BLOCK) k_sum_into(const double* __restrict__ partial, int n,
+                                                        double* __restrict__ out) {
+  __shared__ double s[RED_BLOCK];
+  double x = 0.0;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) x += partial[q];
+  s[threadIdx.x] = x;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m,
+                       float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const float g = gr[q];
+  const float mm = b1 * m[q] + (1.f - b1) * g;
+  const float vv = b2 * v[q] + (1.f - b2) * g * g;
+  m[q] = mm;
+  v[q] = vv;
+  p[q] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+}
+
+// one thread per (layer, tap, n-tile, lane): the lane's b0, b1 words of the forward
+// fragments (B[k][n] = W[t][k][n]) and of the input-gradient fragments (B[k][n] = W[26-t][n][k])
+__global__ void k_pack(const float* __restrict__ params, uint32_t* __restrict__ fwd, uint32_t* __restrict__ bwd) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= LN_LAYERS * LN_TAPS * 64) return;
+  const int l = q / (LN_TAPS * 64);
+  const int r = q % (LN_TAPS * 64);
+  const int lane = r & 31, nt = (r >> 5) & 1, t = r >> 6;
+  const int g = lane >> 2, tg = lane & 3;
+  const int n = nt * 8 + g;
+  const float* Wl = params + (int64_t)l * LN_LSIZE;
+  auto wf = [&](int k) { return Wl[t * 256 + k * 16 + n]; };
+  auto wb = [&](int k) { return Wl[(26 - t) * 256 + n * 16 + k]; };
+  uint32_t* F = fwd + (int64_t)l * LN_PACK + r * 2;
+  uint32_t* Bk = bwd + (int64_t)l * LN_PACK + r * 2;
+  F[0] = pack_bf16x2(wf(2 * tg), wf(2 * tg + 1));
+  F[1] = pack_bf16x2(wf(2 * tg + 8), wf(2 * tg + 9));
+  Bk[0] = pack_bf16x2(wb(2 * tg), wb(2 * tg + 1));
+  Bk[1] = pack_bf16x2(wb(2 * tg + 8), wb(2 * tg + 9));
+}
+
+__global__ void k_to_bf16(int64_t V, int cin, const float* __restrict__ src, uint32_t* __restrict__ X) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+    float f[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) f[c] = c < cin ? src[v * cin + c] : 0.f;
+    uint4* p = reinterpret_cast<uint4*>(X + v * 8);
+    p[0] = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
+                      pack_bf16x2(f[6], f[7]));
+    p[1] = make_uint4(pack_bf16x2(f[8], f[9]), pack_bf16x2(f[10], f[11]), pack_bf16x2(f[12], f[13]),
+                      pack_bf16x2(f[14], f[15]));
+  }
+}
+
+__device__ __forceinline__ double feature_scale(const double* sumsq, double count) {
+  if (!sumsq) return 1.0;
+  const double s2 = *sumsq / count;
+  return (s2 > 0.0 && s2 < 1e300) ? sqrt(s2) : 1.0;
+}
+
+__global__ void __launch_bounds__(RED_BLOCK) k_feature_norm(int64_t V, int64_t E, const int64_t* __restrict__ gent,
+                                                            const uint8_t* __restrict__ gfree,
+                                                            const float* __restrict__ z0,
+                                                            const float* __restrict__ dinv,
+                                                            double* __restrict__ partial) {
+  __shared__ double s[RED_BLOCK / 32];
+  double acc = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < V; g += (int64_t)gridDim.x * blockDim.x) {
+    if (!gfree[g]) continue;
+    const int64_t e = gent[g];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double w = (double)z0[e + c * E] / (double)dinv[e + c * E];
+      acc += w * w;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0;
+    for (int w = 0; w < RED_BLOCK / 32; ++w) x += s[w];
+    partial[blockIdx.x] = x;
+  }
+}
+
+__global__ void k_features(int64_t V, int64_t E, const int64_t* __restrict__ gent, const uint8_t* __restrict__ gfree,
+                           const float* __restrict__ logk, const float* __restrict__ r1,
+                           const float* __restrict__ z0, const float* __restrict__ e1,
+                           const float* __restrict__ dinv, const double* __restrict__ sumsq, double count,
+                           uint32_t* __restrict__ X, uint32_t* __restrict__ pin, float* __restrict__ target) {
+  const float inv = (float)(1.0 / feature_scale(sumsq, count));
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < V; g += (int64_t)gridDim.x * blockDim.x) {
+    float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float tg[3] = {0.f, 0.f, 0.f};
+    f[6] = logk[g];
+    if (gfree[g]) {
+      const int64_t e = gent[g];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float d = 1.f / dinv[e + c * E];
+        f[c] = r1[e + c * E] * inv;
+        f[3 + c] = z0[e + c * E] * d * inv;
+        if (e1) tg[c] = e1[e + c * E] * d * inv;
+      }
+    }
+    const uint4 w0 = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
+                                pack_bf16x2(f[6], f[7]));
+    if (X) {
+      uint4* p = reinterpret_cast<uint4*>(X + g * 8);
+      p[0] = w0;
+      p[1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (pin) reinterpret_cast<uint4*>(pin)[g] = w0;
+    if (target) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) target[g * 3 + c] = tg[c];
+    }
+  }
+}
+
+__global__ void k_grid_to_lib(int64_t E, const int64_t* __restrict__ e2g, const uint8_t* __restrict__ efree,
+                              const float* __restrict__ out, const float* __restrict__ dinv,
+                              const double* __restrict__ sumsq, double count, float* __restrict__ z) {
+  const float s = (float)feature_scale(sumsq, count);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const bool f = efree[e] != 0;
+    const int64_t g = e2g[e];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) z[e + c * E] = f ? s * out[g * 3 + c] * (dinv ? dinv[e + c * E] : 1.f) : 0.f;
+  }
+}
+
+__global__ void k_crop(const uint4* __restrict__ pin, const float* __restrict__ ptg, int PD, int PH, int PW,
+                       const int32_t* __restrict__ idx, const int32_t* __restrict__ org, int B, int S,
+                       uint4* __restrict__ X, float* __restrict__ target) {
+  const int64_t V = (int64_t)B * S * S * S;
+  const int64_t N3 = (int64_t)PD * PH * PW;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(v % S);
+    const int y = (int)((v / S) % S);
+    const int z = (int)((v / ((int64_t)S * S)) % S);
+    const int b = (int)(v / ((int64_t)S * S * S));
+    const int64_t src = (int64_t)idx[b] * N3 + ((int64_t)(org[3 * b] + z) * PH + (org[3 * b + 1] + y)) * PW +
+                        (org[3 * b + 2] + x);
+    X[2 * v] = pin[src];
+    X[2 * v + 1] = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) target[v * 3 + c] = ptg[src * 3 + c];
+  }
+}
+
+inline unsigned blocks_for(int64_t n, int block, int64_t cap) {
+  int64_t g = (n + block - 1) / block;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+inline int64_t red_blocks(int64_t V) { return blocks_for(V, RED_BLOCK, RED_MAX_BLOCKS); }
+
+}  // namespace
+
+int launch_conv(const void* X, const uint32_t* Wp, const float* bias, void* Y, float* Yf, int nf, const void* mask,
+                GridShape s, int relu, void* stream) {
+  const int64_t ntask = (int64_t)s.B * s.D * s.H * ((s.W + 15) / 16);
+  if (ntask == 0) return 0;
+  k_conv<<<blocks_for(ntask, WARPS, 152 * 12), WARPS * 32, 0, (cudaStream_t)stream>>>(
+      (const uint32_t*)X, Wp, bias, (uint32_t*)Y, Yf, nf, (const uint32_t*)mask, s.B, s.D, s.H, s.W, relu);
+  return (int)cudaGetLastError();
+}
+
+int64_t wgrad_partials(GridShape s) {
+  const int64_t nseg = (int64_t)s.B * s.D * s.H * ((s.W + 15) / 16);
+  const int64_t nb = (nseg + WARPS * WG_ROWS - 1) / (WARPS * WG_ROWS);
+  return nb < 1 ? 1 : nb;
+}
+
+int launch_wgrad(const void* A, const void* G, float* partial, float* dW, GridShape s, void* stream) {
+  const int64_t nb = wgrad_partials(s);
+  dim3 grid((unsigned)nb, LN_TAPS);
+  k_wgrad<<<grid, WARPS * 32, 0, (cudaStream_t)stream>>>((const unsigned short*)A, (const unsigned short*)G, partial,
+                                                         s.B, s.D, s.H, s.W);
+  k_colsum<<<(LN_WSIZE + 255) / 256, 256, 0, (cudaStream_t)stream>>>(partial, nb, LN_WSIZE, dW);
+  return (int)cudaGetLastError();
+}
+
+int64_t bgrad_partials(int64_t V) { return red_blocks(V); }
+
+int launch_bgrad(const void* G, int64_t V, float* partial, float* db, void* stream) {
+  const int64_t nb = red_blocks(V);
+  k_bgrad<<<(unsigned)nb, RED_BLOCK, 0, (cudaStream_t)stream>>>((const uint32_t*)G, V, partial);
+  k_colsum<<<1, 32, 0, (cudaStream_t)stream>>>(partial, nb, 16, db);
+  return (int)cudaGetLastError();
+}
+
+int64_t mse_partials(int64_t V) { return red_blocks(V); }
+
+int launch_mse(const float* out, const float* target, int64_t V, void* G, double* partial, double* loss,
+               void* stream) {
+  const int64_t nb = red_blocks(V);
+  k_mse<<<(unsigned)nb, RED_BLOCK, 0, (cudaStream_t)stream>>>(out, target, V, 1.0 / ((double)V * LN_COUT),
+                                                               (uint32_t*)G, partial);
+  k_sum_into<<<1, RED_BLOCK, 0, (cudaStream_t)stream>>>(partial, (int)nb, loss);
+  return (int)cudaGetLastError();
+}
+
+int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, int step, void* stream) {
+  const double b1 = 0.9, b2 = 0.999;
+  const float c1 = (float)(1.0 - std::pow(b1, step)), c2 = (float)(1.0 - std::pow(b2, step));
+  k_adam<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(p, g, m, v, n, lr, (float)b1, (float)b2, 1e-8f, c1, c2);
+  return (int)cudaGetLastError();
+}
+
+int launch_pack(const float* params, uint32_t* fwd, uint32_t* bwd, void* stream) {
+  const int n = LN_LAYERS * LN_TAPS * 64;
+  k_pack<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(params, fwd, bwd);
+  return (int)cudaGetLastError();
+}
+
+int launch_to_bf16(int64_t V, int cin, const float* src, void* X, void* stream) {
+  k_to_bf16<<<blocks_for(V, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(V, cin, src, (uint32_t*)X);
+  return (int)cudaGetLastError();
+}
+
+int launch_feature_norm(int64_t V, int64_t E, const int64_t* gent, const uint8_t* gfree, const float* z0,
+                        const float* dinv, double* partial, double* out, void* stream) {
+  const int64_t nb = red_blocks(V);
+  k_feature_norm<<<(unsigned)nb, RED_BLOCK, 0, (cudaStream_t)stream>>>(V, E, gent, gfree, z0, dinv, partial);
+  k_sum_into<<<1, RED_BLOCK, 0, (cudaStream_t)stream>>>(partial, (int)nb, out);
+  return (int)cudaGetLastError();
+}
+
+int launch_features(int64_t V, int64_t E, const int64_t* gent, const uint8_t* gfree, const float* logk,
+                    const float* r1, const float* z0, const float* e1, const float* dinv, const double* sumsq,
+                    double count, void* X, void* pin, float* target, void* stream) {
+  k_features<<<blocks_for(V, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(
+      V, E, gent, gfree, logk, r1, z0, e1, dinv, sumsq, count, (uint32_t*)X, (uint32_t*)pin, target);
+  return (int)cudaGetLastError();
+}
+
+int launch_grid_to_lib(int64_t E, const int64_t* e2g, const uint8_t* efree, const float* out, const float* dinv,
+                       const double* sumsq, double count, float* z, void* stream) {
+  k_grid_to_lib<<<blocks_for(E, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(E, e2g, efree, out, dinv, sumsq,
+                                                                                 count, z);
+  return (int)cudaGetLastError();
+}
+
+int launch_crop(const void* pin, const float* ptg, int PD, int PH, int PW, const int32_t* idx, const int32_t* org,
+                int B, int S, void* X, float* target, void* stream) {
+  const int64_t V = (int64_t)B * S * S * S;
+  k_crop<<<blocks_for(V, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>((const uint4*)pin, ptg, PD, PH, PW, idx, org,
+                                                                          B, S, (uint4*)X, target);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace hhg

@@ -11,6 +11,7 @@
 // iterations), and the coarsest level (level 2) is solved exactly with a dense
 // inverse of its matrix restricted to the free degrees of freedom.
 #include "hhg_ctx.h"
+#include "hhg_solver.h"
 
 namespace {
 
@@ -694,6 +695,37 @@ hhg_status dispatch(hhg_ctx* c, hhg_dtype dt, F&& f) {
 
 }  // namespace
 
+namespace hhg {
+namespace host {
+
+void mg_ready_check(hhg_ctx* c) { mg_check(c); }
+void apply32(hhg_ctx* c, int l, const float* x, float* y) { apply_op<float>(c, l, x, y); }
+double dot32(hhg_ctx* c, int l, const float* a, const float* b) { return dot<float>(c, l, a, b); }
+void vcycle32(hhg_ctx* c, int l, const float* f, float* x) {
+  ensure_work<float>(c, l);
+  vcycle<float>(c, l, f, x);
+}
+const float* dinv32(hhg_ctx* c, int l) {
+  LevelHost& L = c->lv(l);
+  if (!L.dinv32.p) compute_diag<float>(c, l);
+  return L.dinv32.as<float>();
+}
+double residual32(hhg_ctx* c, int l, const float* f, const float* x, float* r) {
+  return residual_op<float>(c, l, f, x, r, true);
+}
+double residual64(hhg_ctx* c, int l, const double* f, const double* x, double* r) {
+  return residual_op<double>(c, l, f, x, r, true);
+}
+void ensure_work64(hhg_ctx* c, int l) {
+  ensure_work<double>(c, l);
+  ensure_work<float>(c, l);
+}
+double* work64(hhg_ctx* c, int l, int q) { return work<double>(c->lv(l))[q].as<double>(); }
+float* work32(hhg_ctx* c, int l, int q) { return work<float>(c->lv(l))[q].as<float>(); }
+
+}  // namespace host
+}  // namespace hhg
+
 extern "C" {
 
 hhg_status hhg_set_mg_params(hhg_ctx* c, const hhg_mg_params* p) {
@@ -1040,6 +1072,9 @@ hhg_status hhg_solve(hhg_ctx* c, const hhg_solve_opts* o, const void* f, void* x
       project_pressure<double>(c, l, (double*)x);
       R.rel_residual = r0 > 0.0 ? std::sqrt(rr / r0) : 0.0;
       R.converged = R.rel_residual <= o->rtol;
+    } else if (o->method == HHG_SOLVE_IR_FCG_LEARNED || o->method == HHG_SOLVE_IR_FCG) {
+      if (o->dt != HHG_F64) THROW(HHG_ERR_ARG, "iterative refinement needs FP64 f and x");
+      learned_ir(c, o, (const double*)f, (double*)x, o->method == HHG_SOLVE_IR_FCG_LEARNED, R);
     } else {
       THROW(HHG_ERR_ARG, "method");
     }

@@ -1,0 +1,30 @@
+// Solver building blocks of hhg_solve.cpp used by other translation units (internal).
+#pragma once
+#include "hhg_ctx.h"
+
+namespace hhg {
+namespace host {
+
+struct SolverResult {
+  int iterations = 0;
+  double r0 = 0.0, rel = 0.0;
+  bool converged = false;
+};
+
+void mg_ready_check(hhg_ctx* c);                                           // coefficient set and hhg_mg_setup done
+void apply32(hhg_ctx* c, int l, const float* x, float* y);                // y = A x (FP32)
+double dot32(hhg_ctx* c, int l, const float* a, const float* b);          // over unique free DoFs (waits)
+void vcycle32(hhg_ctx* c, int l, const float* f, float* x);               // one V-cycle, x updated
+const float* dinv32(hhg_ctx* c, int l);                                   // inverse point diagonal (3*E)
+double residual32(hhg_ctx* c, int l, const float* f, const float* x, float* r);   // returns |r|^2
+double residual64(hhg_ctx* c, int l, const double* f, const double* x, double* r);  // returns |r|^2
+void ensure_work64(hhg_ctx* c, int l);
+double* work64(hhg_ctx* c, int l, int q);  // FP64 work vector q (3*E); 10 and 11 are free for drivers
+float* work32(hhg_ctx* c, int l, int q);   // FP32 work vector q (3*E); 10 and 11 are free for drivers
+
+// FP64 iterative refinement around FP32 flexible CG whose preconditioner is the V-cycle
+// plus the learned correction (use_net) or the V-cycle alone (hhg_learn.cpp)
+void learned_ir(hhg_ctx* c, const hhg_solve_opts* o, const double* f, double* x, bool use_net, hhg_solve_report& R);
+
+}  // namespace host
+}  // namespace hhg

@@ -13,54 +13,9 @@ import hhg_inputs as hi
 from oracle import fem, mesh, operators as op, solvers as S
 from paper_1908_08666_gb300 import binding as B
 
-from hhg_gpu import Ctx
+from hhg_gpu import NU, Pair, kfun_smooth as _kfun  # noqa: F401
 
 pytestmark = pytest.mark.gpu
-
-NU = 0.3
-
-
-def _kfun(c):
-    return 1.0 + 0.5 * np.sin(3.0 * c[:, 0]) * np.cos(2.0 * c[:, 1]) + 0.3 * c[:, 2]
-
-
-def _oracle_hier(builder, levels, kfun):
-    xyz, tets = builder()
-    mm = mesh.MacroMesh.build(xyz, tets)
-    ce, cd = fem.elasticity_coefficients(NU)
-
-    def A_of(lv):
-        K = fem.element_stiffness(lv.coords[lv.elems], ce, cd)
-        return op.with_dirichlet_rows(op.scaled_operator(lv, K, kfun(lv.coords)), lv.dirichlet)
-
-    return S.Hierarchy(mm, levels, A_of)
-
-
-class Pair:
-    """GPU context and oracle hierarchy on the same mesh, with node permutations."""
-
-    def __init__(self, builder, level, kfun=_kfun):
-        self.xyz, self.tets = builder()
-        self.level = level
-        self.H = _oracle_hier(builder, list(range(2, level + 1)), kfun)
-        self.ctx = Ctx(self.xyz, self.tets, level, dict(nu=NU))
-        self.ctx.set_k(kfun(self.ctx.coords_u))
-        self.perm, self.dirs = {}, {}
-        for l in range(2, level + 1):
-            cu, _, udir, _, _ = self.ctx.maps(l)
-            self.perm[l] = mesh.match_nodes(self.H.lv[l].coords, cu)
-            self.dirs[l] = udir
-
-    def to_lib(self, l, x_or, dtype):
-        u = np.empty_like(x_or)
-        u[self.perm[l]] = x_or
-        return self.ctx.to_lib_level(l, u, dtype)
-
-    def from_lib(self, l, field):
-        return self.ctx.from_lib_level(l, field)[self.perm[l]]
-
-    def close(self):
-        self.ctx.close()
 
 
 @pytest.fixture(scope="module")

@@ -32,7 +32,7 @@ def test_transpose_is_adjoint():
 
 def test_gradients_match_finite_differences():
     rng = np.random.default_rng(2)
-    x = rng.normal(size=(2, 4, 4, 5, 4))
+    x = rng.normal(size=(2, 4, 4, 5, LN.CIN))
     tgt = rng.normal(size=(2, 4, 4, 5, 3))
     Ws, bs = LN.init_params(3)
     Ws = [W + 0.05 * rng.normal(size=W.shape) for W in Ws]
@@ -64,3 +64,81 @@ def test_bf16_rounding():
     r = LN.bf16(v)
     assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0078125
     assert abs(r[3] + 3.140625) < 1e-12
+
+
+def _cube_problem(level):
+    import hhg_inputs as hi
+    from oracle import fem, mesh, operators as op, solvers as S
+
+    xyz, tets = hi.kuhn_cube()
+    mm = mesh.MacroMesh.build(xyz, tets)
+    ce, cd = fem.elasticity_coefficients(0.3)
+    kf = lambda c: hi.young_sine(c)
+
+    def A_of(lv):
+        K = fem.element_stiffness(lv.coords[lv.elems], ce, cd)
+        return op.with_dirichlet_rows(op.scaled_operator(lv, K, kf(lv.coords)), lv.dirichlet)
+
+    H = S.Hierarchy(mm, list(range(2, level + 1)), A_of)
+    lam = {l: S.lambda_max_DinvA(H.A[l], H.lv[l].dirichlet) for l in range(3, level + 1)}
+    lv = H.lv[level]
+    vox, dims = LN.grid_index(lv.coords, 1.0 / 2**level)
+    vc = lambda r: H.vcycle(level, r, np.zeros_like(r), "chebyshev", 2, 2, lam)
+    return H, lv, vox, dims, kf(lv.coords), vc
+
+
+def test_grid_index_is_a_bijection_onto_the_cube_lattice():
+    H, lv, vox, dims, k, vc = _cube_problem(3)
+    assert dims == (9, 9, 9)
+    flat = (vox[:, 0] * 9 + vox[:, 1]) * 9 + vox[:, 2]
+    assert np.array_equal(np.sort(flat), np.arange(729))
+
+
+def test_line_search_never_loses_to_the_vcycle():
+    """alpha minimises the energy norm of the error on z0 + alpha c: any other step on that
+    line (alpha = 0 is the plain V-cycle) leaves a larger error."""
+    import hhg_inputs as hi
+
+    H, lv, vox, dims, k, vc = _cube_problem(3)
+    A = H.A[3]
+    fr = ~lv.dirichlet
+    e = hi.node_noise(lv.coords, seed=5)
+    e[~fr] = 0.0
+    r = (A @ e.reshape(-1)).reshape(-1, 3)
+    r[~fr] = 0.0
+    z0 = vc(r)
+    Ws, bs = LN.init_params(7)
+    z, alpha, c = LN.correction(A, lv.dirichlet, vox, dims, k, r, z0, Ws, bs)
+    assert np.abs(c).max() > 0
+
+    def energy(zz):
+        d = (e - zz).reshape(-1)
+        return float(d @ (A @ d))
+
+    best = energy(z)
+    for da in (-0.5, -0.1, 0.1, 0.5):
+        assert energy(z0 + (alpha + da * (abs(alpha) + 1e-3)) * c) > best
+    assert best <= energy(z0)
+
+
+def test_features_are_scale_invariant_and_pairs_consistent():
+    import hhg_inputs as hi
+
+    H, lv, vox, dims, k, vc = _cube_problem(3)
+    A = H.A[3]
+    fr = ~lv.dirichlet
+    e = hi.node_noise(lv.coords, seed=6)
+    e[~fr] = 0.0
+    X, T, e1 = LN.training_pair(A, lv.dirichlet, vox, dims, k, e, vc)
+    X2, T2, _ = LN.training_pair(A, lv.dirichlet, vox, dims, k, 3.0 * e, vc)
+    assert np.allclose(X, X2, rtol=1e-12, atol=1e-14) and np.allclose(T, T2, rtol=1e-12, atol=1e-14)
+    # the target is D e1 / s and the residual channels are A e1 / s with the same s
+    Dg = A.diagonal().reshape(-1, 3)
+    t = T[0, vox[:, 0], vox[:, 1], vox[:, 2]]
+    r1 = X[0, vox[:, 0], vox[:, 1], vox[:, 2], :3]
+    s = (Dg[fr] * e1[fr])[0, 0] / t[fr][0, 0]
+    Ae1 = (A @ e1.reshape(-1)).reshape(-1, 3)
+    assert np.allclose(r1[fr] * s, Ae1[fr], rtol=1e-10, atol=1e-12 * np.abs(Ae1).max())
+    # s is the RMS of D z0 over the free DoFs: the z0 channels have unit mean square
+    z0c = X[0, vox[fr, 0], vox[fr, 1], vox[fr, 2], 3:6]
+    assert abs((z0c**2).mean() - 1.0) < 1e-12
