@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--no-stokes", action="store_true")
     ap.add_argument("--no-carreau", action="store_true")
     ap.add_argument("--carreau-level", type=int, default=7)
+    ap.add_argument("--no-learn", action="store_true")
+    ap.add_argument("--learn-train-level", type=int, default=6)
+    ap.add_argument("--learn-level", type=int, default=8)
+    ap.add_argument("--learn-seeds", type=int, default=24)
+    ap.add_argument("--learn-steps", type=int, default=4000)
     return ap.parse_args()
 
 
@@ -315,6 +320,128 @@ def carreau_bench(B, torch, level, dev, stream):
 # ---------------------------------------------------------------------------- our arm
 
 
+def learned_bench(B, torch, dev, stream, train_level, eval_level, nseed, nrhs, iters, steps):
+    """Learned preconditioner: training pairs from the errors of MG-preconditioned CG
+    solves at train_level (lognormal E with seeds 100.., f ~ U[-1, 1]), GPU training of the
+    conv net (Adam, batches of 8 random 32^3 crops), then the time to an FP64 relative
+    residual of 1e-8 at eval_level on the bench field (seed 2, f seed 3): FP64 refinement
+    around FP32 flexible CG with the V-cycle plus the learned correction, against the same
+    solver with the V-cycle alone and plain FP64 MG-CG.  Also the conv-net forward
+    throughput on the eval grid (tensor-core roofline of the dominant learned kernel)."""
+    import hhg_inputs as hi
+
+    xyz, tets = hi.kuhn_cube(1)
+
+    def make(level):
+        h = B.hhg_create(dev, stream.cuda_stream)
+        B.hhg_set_macro_mesh(h, xyz, tets)
+        B.hhg_refine(h, level)
+        B.hhg_set_problem(h, nu=NU)
+        E, U, _ = B.hhg_num_nodes(h, level)
+        ce = B.hhg_entry_coords(h, level)
+        e2u, udir = B.hhg_entry_to_unique(h, level)
+        first = np.full(U, -1, dtype=np.int64)
+        first[e2u[::-1]] = np.arange(E)[::-1]
+        return h, E, U, ce[first], udir
+
+    def scatter(h, level, u, comps, dt):
+        tdt = torch.float64 if dt == B.F64 else torch.float32
+        src = torch.as_tensor(np.ascontiguousarray(np.asarray(u).reshape(-1, comps).T).reshape(-1), dtype=tdt,
+                              device="cuda")
+        E = B.hhg_num_nodes(h, level)[0]
+        dst = torch.empty(comps * E, dtype=tdt, device="cuda")
+        B.hhg_scatter_unique(h, level, dt, comps, src, dst)
+        return dst
+
+    # training pairs and training
+    h, E, U, cu, udir = make(train_level)
+    Nt = 1 << train_level
+    B.hhg_learn_reserve_pairs(h, train_level, nseed * nrhs * iters)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(nseed):
+        B.hhg_set_coefficient(h, scatter(h, train_level, hi.sample_grid(hi.lognormal_grid(Nt, 100 + s), cu), 1,
+                                         B.F64), B.F64)
+        B.hhg_mg_setup(h)
+        for q in range(nrhs):
+            f = np.random.default_rng(1000 * s + q).uniform(-1, 1, size=(U, 3))
+            f[udir] = 0.0
+            B.hhg_learn_collect_cg(h, train_level, scatter(h, train_level, f, 3, B.F32), iters)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    B.hhg_learn_init(h, 1)
+    tr = B.hhg_learn_train(h, steps=steps, batch=8, crop=32, lr=2e-3, seed=2)
+    params = B.hhg_learn_get_params(h)
+    B.hhg_destroy(h)
+
+    # evaluation
+    h, E, U, cu, udir = make(eval_level)
+    N = 1 << eval_level
+    B.hhg_set_coefficient(h, scatter(h, eval_level, hi.sample_grid(hi.lognormal_grid(N, 2), cu), 1, B.F64), B.F64)
+    B.hhg_mg_setup(h)
+    B.hhg_learn_set_params(h, params)
+    f = scatter(h, eval_level, hi.sample_grid(hi.uniform_grid(N, seed=3), cu), 3, B.F64)
+    out = {"train": {"level": train_level, "coefficient_seeds": "%d..%d" % (100, 100 + nseed - 1),
+                     "pairs": int(tr["pairs"]), "pair_source": "errors of %d MG-CG iterations x %d RHS per field"
+                     % (iters, nrhs), "pair_generation_s": round(gen_s, 3), "steps": steps, "batch": "8 x 32^3",
+                     "loss_first": tr["loss_first"], "loss_last": tr["loss_last"],
+                     "train_s": round(tr["seconds"], 3)},
+           "eval_level": eval_level, "rtol": 1e-8}
+    for name, method, kw in (("ir_fcg_learned", B.SOLVE_IR_FCG_LEARNED, dict(inner_rtol=1e-3, inner_max_iter=100)),
+                             ("ir_fcg_vcycle", B.SOLVE_IR_FCG, dict(inner_rtol=1e-3, inner_max_iter=100)),
+                             ("fp64_mgcg", B.SOLVE_MG_CG, {})):
+        best = None
+        for _ in range(2):
+            x = torch.zeros_like(f)
+            B.hhg_learn_stats(h, reset=True)
+            torch.cuda.synchronize()
+            rep = B.hhg_solve(h, f, x, method=method, level=eval_level, dt=B.F64, rtol=1e-8, max_iter=100, **kw)
+            st = B.hhg_learn_stats(h)
+            if best is None or rep["seconds"] < best[0]["seconds"]:
+                best = (rep, st)
+        rep, st = best
+        r = torch.empty_like(f)
+        r2 = B.hhg_residual(h, eval_level, B.F64, f, x, r, want_norm=True)
+        out[name] = {"seconds": round(rep["seconds"], 5), "iterations": rep["iterations"],
+                     "inner_iterations": rep["inner_iterations"],
+                     "rel_residual_fp64": float(np.sqrt(r2)) / rep["residual0"], "converged": bool(rep["converged"])}
+        if method == B.SOLVE_IR_FCG_LEARNED:
+            out[name].update({"net_applications": st["applications"], "fallbacks": st["fallbacks"],
+                              "mean_weight_b_over_a": round(st["alpha_mean"], 4),
+                              "mean_extra_energy_reduction": round(st["gain_mean"], 5)})
+    out["iterations_saved_vs_vcycle"] = out["ir_fcg_vcycle"]["inner_iterations"] - out["ir_fcg_learned"]["inner_iterations"]
+    out["speedup_learned_vs_fp64_mgcg"] = round(out["fp64_mgcg"]["seconds"] / out["ir_fcg_learned"]["seconds"], 3)
+    # conv-net forward throughput on the eval grid (4 layers, 27 taps, 16 x 16 channels)
+    (D, H, W), _ = B.hhg_learn_grid(h, eval_level)
+    V = D * H * W
+    xin = torch.randn(V * 7, device="cuda")
+    yo = torch.empty(V * 3, device="cuda")
+    for _ in range(3):
+        B.hhg_learn_forward(h, xin, 7, 1, D, H, W, yo)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    reps = 10
+    for _ in range(reps):
+        B.hhg_learn_forward(h, xin, 7, 1, D, H, W, yo)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    flops = V * 4 * 27 * 16 * 16 * 2
+    peak = None
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peak = float(json.load(open(pp))["bf16_tflops"])
+        src = "measured (cuBLAS bf16 burst)"
+    else:
+        peak, src = 1900.0, "fallback"
+    tf = flops / (ms * 1e-3) / 1e12
+    out["conv_forward"] = {"grid": [D, H, W], "ms": round(ms, 4), "tflops": round(tf, 2), "peak_tflops": peak,
+                           "frac": round(tf / peak, 4), "peak_source": src,
+                           "kernel": "k_conv (mma.sync m16n8k16 BF16, FP32 accumulate), 4 launches"}
+    B.hhg_destroy(h)
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -406,6 +533,8 @@ def run_ours(args):
     B.hhg_destroy(h)
     stokes = None if args.no_stokes else stokes_bench(B, torch, level, dev, stream)
     carreau = None if args.no_carreau else carreau_bench(B, torch, args.carreau_level, dev, stream)
+    learned = None if args.no_learn else learned_bench(B, torch, dev, stream, args.learn_train_level,
+                                                       args.learn_level, args.learn_seeds, 2, 6, args.learn_steps)
 
     ms_per_step = total_ms / args.steps
     value = world * dofs / (ms_per_step * 1e-3) / 1e9
@@ -461,6 +590,7 @@ def run_ours(args):
         "solve": solve,
         "stokes": stokes,
         "carreau": carreau,
+        "learned": learned,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -330,13 +330,18 @@ hhg_status hhg_residual_noalloc(hhg_ctx* ctx, int level, hhg_dtype dt, const voi
  * (dy+1)*3 + (dx+1), input channel i, output channel o), then b_l[16].
  *
  * Input features per voxel (7 channels): r1/s (3), D z0/s (3), log k - mean log k (1),
- * where for a residual r: z0 = V-cycle(r), r1 = r - A z0, D = point diagonal of A,
- * s = RMS of D z0 over the free nodes.  Output (3 channels): D c / s.  The correction
- * is z = z0 + alpha c with alpha = (c, r1)/(c, A c), the minimiser of the energy norm of
- * the error over that line (alpha = 0, i.e. the plain V-cycle, when it is not finite).
+ * where for a residual r: z0 = a0 V-cycle(r) with the energy-optimal step length
+ * a0 = (v, r)/(v, A v), v = V-cycle(r); r1 = r - A z0; D = point diagonal of A;
+ * s = RMS of D z0 over the free nodes.  Output (3 channels): D c / s.  The
+ * preconditioned vector is z = a z0 + b c with (a, b) minimising the energy norm of
+ * the error A^-1 r - z over span{z0, c} (2x2 normal equations); when that system is
+ * singular or not finite, z = z0 (the plain V-cycle direction).  An application never
+ * leaves a larger error in that norm than the V-cycle alone.
  *
- * Training pairs.  From a random error e0 on the grid: e1 = e0 - V-cycle(A e0),
- * r1 = A e1; the pair is (features(r1, z0), target D e1 / s); `cycles` steps per e0.
+ * Training pairs.  From an error e: z0 as above for r = A e, e1 = e - z0, r1 = A e1;
+ * the pair is (features(r1, z0), target D e1 / s).  hhg_learn_collect takes random
+ * errors (`cycles` steps per e0, each continuing from e1); hhg_learn_collect_cg the
+ * errors of the plain multigrid-preconditioned CG iterates.
  * Loss: mean squared error over voxels and the 3 output channels; Adam (0.9, 0.999,
  * 1e-8) with a cosine learning-rate decay to 5% of lr. */
 int64_t hhg_learn_num_params(void);
@@ -362,6 +367,12 @@ hhg_status hhg_learn_reserve_pairs(hhg_ctx* ctx, int level, int64_t capacity);
 /* Append `cycles` pairs from the error e0_grid_dev (FP32 [D][H][W][3] on the node grid
  * of `level`; Dirichlet nodes are ignored).  Needs hhg_mg_setup.  count_host: pairs stored. */
 hhg_status hhg_learn_collect(hhg_ctx* ctx, int level, const float* e0_grid_dev, int cycles, int64_t* count_host);
+/* Append up to `iters` pairs from the errors of flexible CG with the plain V-cycle on
+ * A x = f from x = 0 (f_dev FP32, 3*E, consistent copies; Dirichlet values zero): the
+ * library first solves for x* (FP64 refinement to 1e-10), then stores the pair of the
+ * error x* - x_k before each preconditioner application k = 0, 1, ...  These are the
+ * errors the preconditioner meets inside the solver.  count_host: pairs stored. */
+hhg_status hhg_learn_collect_cg(hhg_ctx* ctx, int level, const float* f_dev, int iters, int64_t* count_host);
 /* Copy stored pair `index` to the host: in_host FP32 [D][H][W][7] (the BF16 inputs),
  * target_host FP32 [D][H][W][3] (either nullable).  Waits. */
 hhg_status hhg_learn_get_pair(hhg_ctx* ctx, int64_t index, float* in_host, float* target_host);
@@ -384,15 +395,16 @@ typedef struct {
 /* Train on the stored pairs: each step takes `batch` random crops (pair and origin from
  * the seed), runs the forward and backward passes and one Adam step.  Waits. */
 hhg_status hhg_learn_train(hhg_ctx* ctx, const hhg_learn_train_opts* opts, hhg_learn_train_report* report);
-/* One preconditioner application z = z0 + alpha c for the FP32 residual r_dev (3*E),
- * (use_net = 0: z = z0, the V-cycle alone); alpha_host receives alpha.  Waits. */
+/* One preconditioner application z = a z0 + b c for the FP32 residual r_dev (3*E)
+ * (use_net = 0: z = V-cycle(r), unscaled); alpha_host receives b / a.  Waits. */
 hhg_status hhg_learn_precondition(hhg_ctx* ctx, int level, int use_net, const void* r_dev, void* z_dev,
                                   double* alpha_host);
 
 typedef struct {
   int64_t applications;  /* preconditioner applications with the network */
-  int64_t fallbacks;     /* of which fell back to the V-cycle (alpha = 0) */
-  double alpha_mean, alpha_min, alpha_max;
+  int64_t fallbacks;     /* of which fell back to the V-cycle (b = 0) */
+  double alpha_mean, alpha_min, alpha_max;  /* of the weight b / a */
+  double gain_mean;      /* energy reduction added by c, relative to the scaled V-cycle step's */
 } hhg_learn_stats_report;
 
 /* Statistics since the last reset (reset != 0 clears them after reading). */

@@ -17,11 +17,13 @@ biases FP32.  Loss: mean over the batch, voxels and the 3 output channels of
 (out - target)^2.
 
 Preconditioner application for a residual r (vectors node-major (N, 3), FP64):
-z0 = V-cycle(r), r1 = r - A z0, D = point diagonal, s = RMS of D z0 over the free DoFs;
-input features per grid voxel of a free node: r1/s, D z0/s, log k - mean log k (the
-last also at Dirichlet nodes); correction c = s out / D on free nodes;
-z = z0 + alpha c with alpha = (c, r1) / (c, A c).  Training pair from an error e:
-z0 = V-cycle(A e), e1 = e - z0, r1 = A e1, target D e1 / s.
+v = V-cycle(r), z0 = a0 v with a0 = (v, r) / (v, A v), r1 = r - A z0, D = point
+diagonal, s = RMS of D z0 over the free DoFs; input features per grid voxel of a free
+node: r1/s, D z0/s, log k - mean log k (the last also at Dirichlet nodes); correction
+c = s out / D on free nodes; z = a z0 + b c with (a, b) minimising the energy norm
+(e - z, A (e - z)) of the error e = A^-1 r (the 2x2 normal equations need only r).
+Training pair from an error e: z0 as above for r = A e, e1 = e - z0, r1 = A e1,
+target D e1 / s.
 """
 
 from __future__ import annotations
@@ -159,21 +161,34 @@ def features(vox, dims, dirichlet, k, r1, z0, D):
     return X, s
 
 
-def correction(A, dirichlet, vox, dims, k, r, z0, Ws, bs):
-    """(z, alpha, c): the learned preconditioner's output for residual r given z0 = V-cycle(r)."""
+def _scaled_step(A, dirichlet, r, v):
+    """Energy-optimal multiple a0 v of the V-cycle output v for the residual r, and A a0 v."""
+    Av = (A @ v.reshape(-1)).reshape(-1, 3)
+    den = _dot_free(v, Av, dirichlet)
+    a0 = _dot_free(v, r, dirichlet) / den if den > 0 else 1.0
+    return a0 * v, a0 * Av
+
+
+def correction(A, dirichlet, vox, dims, k, r, v, Ws, bs):
+    """(z, b/a, c): the learned preconditioner's output for residual r given v = V-cycle(r):
+    z0 = a0 v, c from the network, z = a z0 + b c minimising the energy norm of the error
+    over span{z0, c}."""
     fr = ~np.asarray(dirichlet)
     Dg = A.diagonal().reshape(-1, 3).copy()
     Dg[~fr] = 1.0
-    r1 = r - (A @ z0.reshape(-1)).reshape(-1, 3)
+    z0, Az0 = _scaled_step(A, dirichlet, r, v)
+    r1 = r - Az0
     r1[~fr] = 0.0
     X, s = features(vox, dims, dirichlet, k, r1, z0, Dg)
     out, _ = forward(X, Ws, bs)
     c = s * out[0, vox[:, 0], vox[:, 1], vox[:, 2], :] / Dg
     c[~fr] = 0.0
     Ac = (A @ c.reshape(-1)).reshape(-1, 3)
-    d2 = _dot_free(c, Ac, dirichlet)
-    alpha = _dot_free(c, r1, dirichlet) / d2 if d2 > 0 else 0.0
-    return z0 + alpha * c, alpha, c
+    M = np.array([[_dot_free(z0, Az0, dirichlet), _dot_free(c, Az0, dirichlet)],
+                  [_dot_free(c, Az0, dirichlet), _dot_free(c, Ac, dirichlet)]])
+    rhs = np.array([_dot_free(z0, r, dirichlet), _dot_free(c, r, dirichlet)])
+    a, b = np.linalg.solve(M, rhs)
+    return a * z0 + b * c, b / a, c
 
 
 def training_pair(A, dirichlet, vox, dims, k, e, vcycle):
@@ -183,7 +198,7 @@ def training_pair(A, dirichlet, vox, dims, k, e, vcycle):
     Dg[~fr] = 1.0
     r = (A @ e.reshape(-1)).reshape(-1, 3)
     r[~fr] = 0.0
-    z0 = vcycle(r)
+    z0, _ = _scaled_step(A, dirichlet, r, vcycle(r))
     e1 = e - z0
     r1 = (A @ e1.reshape(-1)).reshape(-1, 3)
     r1[~fr] = 0.0

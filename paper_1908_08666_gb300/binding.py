@@ -84,7 +84,7 @@ class hhg_learn_train_report(C.Structure):
 
 class hhg_learn_stats_report(C.Structure):
     _fields_ = [("applications", C.c_int64), ("fallbacks", C.c_int64), ("alpha_mean", C.c_double),
-                ("alpha_min", C.c_double), ("alpha_max", C.c_double)]
+                ("alpha_min", C.c_double), ("alpha_max", C.c_double), ("gain_mean", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -141,6 +141,7 @@ _SIGS = {
                             C.POINTER(C.c_double), C.c_void_p],
     "hhg_learn_reserve_pairs": [C.c_void_p, C.c_int, C.c_int64],
     "hhg_learn_collect": [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int64)],
+    "hhg_learn_collect_cg": [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int64)],
     "hhg_learn_get_pair": [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p],
     "hhg_learn_train": [C.c_void_p, C.POINTER(hhg_learn_train_opts), C.POINTER(hhg_learn_train_report)],
     "hhg_learn_precondition": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)],
@@ -425,6 +426,12 @@ def hhg_learn_collect(ctx, level, e0_grid, cycles):
     return n.value
 
 
+def hhg_learn_collect_cg(ctx, level, f, iters):
+    n = C.c_int64()
+    _check(ctx, load().hhg_learn_collect_cg(ctx, level, _ptr(f), iters, C.byref(n)))
+    return n.value
+
+
 def hhg_learn_get_pair(ctx, index, dhw):
     """(inputs FP32 (D, H, W, 7), targets FP32 (D, H, W, 3)) of stored pair `index`."""
     D, H, W = dhw
@@ -442,7 +449,7 @@ def hhg_learn_train(ctx, steps, batch, crop, lr=2e-3, seed=0):
 
 
 def hhg_learn_precondition(ctx, level, use_net, r, z):
-    """z = V-cycle(r) + alpha * correction (FP32 library-layout vectors); returns alpha."""
+    """z = a V-cycle step + b correction (FP32 library-layout vectors); returns b / a."""
     a = C.c_double()
     _check(ctx, load().hhg_learn_precondition(ctx, level, int(use_net), _ptr(r), _ptr(z), C.byref(a)))
     return a.value

@@ -147,7 +147,8 @@ struct LearnGrid {
   int64_t V = 0, nfree = 0;
   int64_t coeff_version = -1;  // of the log-coefficient feature
   DevMem gent, gfree, e2g, efree, logk;
-  DevMem lw[10];  // FP32 work vectors (3*E) of the learned preconditioner and its FCG
+  DevMem lw[13];  // FP32 work vectors (3*E) of the learned preconditioner and its FCG
+  DevMem lw64[2]; // FP64 work vectors (3*E) of the pair collection
 };
 
 // Learned preconditioner: network parameters, optimiser state, training pairs, buffers.
@@ -166,7 +167,7 @@ struct LearnState {
   DevMem wpart, bpart, dpart, dscal;
   // statistics of the preconditioner applications
   int64_t applications = 0, fallbacks = 0;
-  double alpha_sum = 0.0, alpha_min = 0.0, alpha_max = 0.0;
+  double alpha_sum = 0.0, alpha_min = 0.0, alpha_max = 0.0, gain_sum = 0.0;
 };
 
 

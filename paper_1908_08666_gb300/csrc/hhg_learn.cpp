@@ -4,18 +4,23 @@
 // the V-cycle.  Kernels in hhg_learn.cu; conventions in hhg_learn.h.
 //
 // Preconditioner application for a residual r (FP32):
-//   z0 = V-cycle(r) (zero initial guess),  r1 = r - A z0   (the residual the V-cycle leaves),
-//   c  = s * D^-1 N(features(r1, z0, log k))               (network correction),
-//   z  = z0 + alpha c,  alpha = (c, r1) / (c, A c)
-// alpha minimises the energy norm of the error A^-1 r - z over the line z0 + alpha c, so
-// an application never leaves a larger error (in that norm) than the V-cycle alone; when
-// alpha is not finite (e.g. c = 0) the application falls back to z = z0.
+//   z0 = a0 V-cycle(r), a0 = energy-optimal step length (z0, r) / (z0, A z0) of the V-cycle,
+//   r1 = r - A z0       (the residual the scaled V-cycle step leaves; (z0, r1) = 0),
+//   c  = s D^-1 N(features(r1, z0, log k))   (network correction),
+//   z  = a z0 + b c,  (a, b) minimising the energy norm of the error A^-1 r - z over
+//        span{z0, c}  (2x2 normal equations).
+// Hence an application never leaves a larger error (in that norm) than the V-cycle alone,
+// and the network is not rewarded for what a rescaling of z0 would do (CG is invariant
+// to that); when the 2x2 system is singular or not finite the application falls back to
+// z = z0.
 //
-// Training pairs: for a random error e (given on the grid by the caller), one multigrid
-// step gives z0 = V-cycle(A e), the remaining error e1 = e - z0 and residual r1 = A e1;
-// the pair is (features(r1, z0), D e1 / s).  Further steps continue from e1.
+// Training pairs: for an error e, one multigrid step gives z0 = a0 V-cycle(A e), the
+// remaining error e1 = e - z0 and residual r1 = A e1; the pair is (features(r1, z0),
+// D e1 / s).  The errors are either random (further steps continue from e1) or the
+// errors of the plain multigrid-preconditioned CG iterates (hhg_learn_collect_cg).
 #include <cmath>
 #include <cstring>
+#include <functional>
 
 #include "hhg_ctx.h"
 #include "hhg_learn.h"
@@ -27,7 +32,7 @@ using namespace hhg;
 using namespace hhg::host;
 
 // work vectors of LearnGrid::lw
-enum { LW_Z0 = 0, LW_AZ0, LW_R1, LW_C, LW_AC, LW_R, LW_Z, LW_AZ, LW_P, LW_Q };
+enum { LW_Z0 = 0, LW_AZ0, LW_R1, LW_C, LW_AC, LW_R, LW_Z, LW_AZ, LW_P, LW_Q, LW_X, LW_XS, LW_E };
 
 LearnState& state(hhg_ctx* c) {
   if (!c->learn) c->learn.reset(new LearnState());
@@ -243,7 +248,7 @@ LearnGrid& grid(hhg_ctx* c, int l) {
     CK(G->logk.alloc(V * sizeof(float)));
     S.grids[l] = std::move(ng);
   }
-  if (G->coeff_version != c->coeff_version) {
+  if (c->have_coeff && G->coeff_version != c->coeff_version) {
     // log-coefficient feature: log k at the voxel's node minus its mean over the nodes
     std::vector<double> k(L.entries);
     CK(cudaMemcpyAsync(k.data(), L.d_k64.p, L.entries * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -282,7 +287,20 @@ void copy32(hhg_ctx* c, int l, const float* src, float* dst) {
   CK(cudaMemcpyAsync(dst, src, 3 * (size_t)c->lv(l).entries * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
 }
 
-// z = z0 + alpha c and az = A z (see the file comment); use_net = false: z = z0
+// Scale the V-cycle correction z0 (and A z0) to its energy-optimal length for the residual
+// r: z0 <- a0 z0 with a0 = (z0, r) / (z0, A z0) (unchanged when that is not finite).
+// Returns (z0, r) after scaling.
+double scale_vcycle_step(hhg_ctx* c, int l, const float* r, float* z0, float* az0) {
+  const int64_t n = 3 * c->lv(l).entries;
+  const double zr = dot32(c, l, z0, r), zaz = dot32(c, l, z0, az0);
+  const double a0 = (zaz > 0.0 && std::isfinite(zr / zaz)) ? zr / zaz : 1.0;
+  CK(launch_axpby<float>(n, (float)a0, z0, 0.f, z0, c->stream));
+  CK(launch_axpby<float>(n, (float)a0, az0, 0.f, az0, c->stream));
+  return a0 * zr;
+}
+
+// z and az = A z of one preconditioner application (see the file comment); use_net = false:
+// z = z0.  Returns the weight b / a of the correction in z = a z0 + b c.
 double precondition(hhg_ctx* c, int l, const float* r, float* z, float* az, bool use_net) {
   LearnState& S = state(c);
   LearnGrid& G = grid(c, l);
@@ -292,51 +310,64 @@ double precondition(hhg_ctx* c, int l, const float* r, float* z, float* az, bool
   CK(cudaMemsetAsync(z0, 0, n * sizeof(float), c->stream));
   vcycle32(c, l, r, z0);
   apply32(c, l, z0, az0);
-  double alpha = 0.0;
-  if (use_net) {
-    need_params(S);
-    float* r1 = lwork(c, G, l, LW_R1);
-    float* cc = lwork(c, G, l, LW_C);
-    float* acc = lwork(c, G, l, LW_AC);
-    const float* dinv = dinv32(c, l);
-    ensure_acts(c, S, G.V);
-    copy32(c, l, r, r1);
-    CK(launch_axpby<float>(n, -1.f, az0, 1.f, r1, c->stream));
-    double* ssum = S.dscal.as<double>();
-    CK(launch_feature_norm(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), z0, dinv, S.dpart.as<double>(), ssum,
-                           c->stream));
-    const double cnt = 3.0 * (double)std::max<int64_t>(G.nfree, 1);
-    CK(launch_features(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), G.logk.as<float>(), r1, z0, nullptr, dinv,
-                       ssum, cnt, S.act[0].p, nullptr, nullptr, c->stream));
-    forward_inference(c, S, GridShape{1, G.D, G.H, G.W}, S.out.as<float>());
-    CK(launch_grid_to_lib(E, G.e2g.as<int64_t>(), G.efree.as<uint8_t>(), S.out.as<float>(), dinv, ssum, cnt, cc,
-                          c->stream));
-    apply32(c, l, cc, acc);
-    const double d1 = dot32(c, l, cc, r1);
-    const double d2 = dot32(c, l, cc, acc);
-    alpha = (d2 > 0.0 && std::isfinite(d1) && std::isfinite(d2)) ? d1 / d2 : 0.0;
-    if (!std::isfinite(alpha)) alpha = 0.0;
-    S.applications++;
-    if (alpha == 0.0) S.fallbacks++;
-    S.alpha_sum += alpha;
-    S.alpha_min = S.applications == 1 ? alpha : std::min(S.alpha_min, alpha);
-    S.alpha_max = S.applications == 1 ? alpha : std::max(S.alpha_max, alpha);
+  if (!use_net) {
     copy32(c, l, z0, z);
     copy32(c, l, az0, az);
-    if (alpha != 0.0) {
-      CK(launch_axpby<float>(n, (float)alpha, cc, 1.f, z, c->stream));
-      CK(launch_axpby<float>(n, (float)alpha, acc, 1.f, az, c->stream));
-    }
-  } else {
-    copy32(c, l, z0, z);
-    copy32(c, l, az0, az);
+    return 0.0;
   }
-  return alpha;
+  need_params(S);
+  float* r1 = lwork(c, G, l, LW_R1);
+  float* cc = lwork(c, G, l, LW_C);
+  float* acc = lwork(c, G, l, LW_AC);
+  const float* dinv = dinv32(c, l);
+  ensure_acts(c, S, G.V);
+  const double rv = scale_vcycle_step(c, l, r, z0, az0);  // (z0, r) = (z0, A z0) after scaling
+  copy32(c, l, r, r1);
+  CK(launch_axpby<float>(n, -1.f, az0, 1.f, r1, c->stream));
+  double* ssum = S.dscal.as<double>();
+  CK(launch_feature_norm(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), z0, dinv, S.dpart.as<double>(), ssum,
+                         c->stream));
+  const double cnt = 3.0 * (double)std::max<int64_t>(G.nfree, 1);
+  CK(launch_features(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), G.logk.as<float>(), r1, z0, nullptr, dinv,
+                     ssum, cnt, S.act[0].p, nullptr, nullptr, c->stream));
+  forward_inference(c, S, GridShape{1, G.D, G.H, G.W}, S.out.as<float>());
+  CK(launch_grid_to_lib(E, G.e2g.as<int64_t>(), G.efree.as<uint8_t>(), S.out.as<float>(), dinv, ssum, cnt, cc,
+                        c->stream));
+  apply32(c, l, cc, acc);
+  // energy-optimal a, b: [m11 m12; m12 m22] (a, b) = ((z0, r), (c, r))
+  const double m11 = rv, m12 = dot32(c, l, cc, az0), m22 = dot32(c, l, cc, acc), rc = dot32(c, l, cc, r);
+  const double det = m11 * m22 - m12 * m12;
+  double a = 1.0, b = 0.0;
+  if (m11 > 0.0 && m22 > 0.0 && det > 1e-6 * m11 * m22 && std::isfinite(det) && std::isfinite(rc)) {
+    a = (rv * m22 - m12 * rc) / det;
+    b = (m11 * rc - m12 * rv) / det;
+    if (!(std::isfinite(a) && std::isfinite(b)) || a <= 0.0) {
+      a = 1.0;
+      b = 0.0;
+    }
+  }
+  const double w = b / a;
+  S.applications++;
+  if (b == 0.0) S.fallbacks++;
+  S.alpha_sum += w;
+  S.alpha_min = S.applications == 1 ? w : std::min(S.alpha_min, w);
+  S.alpha_max = S.applications == 1 ? w : std::max(S.alpha_max, w);
+  // extra energy reduction over the scaled V-cycle step, relative to that step's own
+  if (m11 > 0.0) S.gain_sum += (a * rv + b * rc - m11) / m11;
+  copy32(c, l, z0, z);
+  copy32(c, l, az0, az);
+  if (b != 0.0) {
+    CK(launch_axpby<float>(n, (float)b, cc, (float)a, z, c->stream));
+    CK(launch_axpby<float>(n, (float)b, acc, (float)a, az, c->stream));
+  }
+  return w;
 }
 
 // Flexible CG (one-term A-orthogonalisation: p_k = z_k - (z_k, A p_{k-1}) / (p_{k-1}, A p_{k-1}) p_{k-1})
 // on A x = f in FP32; A p follows from the preconditioner's A z by the same recurrence.
-SolverResult fcg(hhg_ctx* c, int l, const float* f, float* x, double rtol, int max_iter, bool use_net) {
+// hook (nullable) is called with the iterate before every preconditioner application.
+SolverResult fcg(hhg_ctx* c, int l, const float* f, float* x, double rtol, int max_iter, bool use_net,
+                 const std::function<void(const float*)>& hook = nullptr) {
   LearnGrid& G = grid(c, l);
   const int64_t n = 3 * c->lv(l).entries;
   float* r = lwork(c, G, l, LW_R);
@@ -352,6 +383,7 @@ SolverResult fcg(hhg_ctx* c, int l, const float* f, float* x, double rtol, int m
     res.converged = true;
     return res;
   }
+  if (hook) hook(x);
   precondition(c, l, r, z, az, use_net);
   copy32(c, l, z, p);
   copy32(c, l, az, q);
@@ -370,6 +402,7 @@ SolverResult fcg(hhg_ctx* c, int l, const float* f, float* x, double rtol, int m
       res.converged = true;
       break;
     }
+    if (hook) hook(x);
     precondition(c, l, r, z, az, use_net);
     const double beta = -dot32(c, l, z, q) / pq;
     CK(launch_axpby<float>(n, 1.f, z, (float)beta, p, c->stream));
@@ -378,6 +411,44 @@ SolverResult fcg(hhg_ctx* c, int l, const float* f, float* x, double rtol, int m
   }
   res.rel = std::sqrt(rr / r0);
   return res;
+}
+
+// One training pair from the error e (library layout): r = A e, z0 = a0 V-cycle(r) with
+// the energy-optimal a0, e1 = e - z0, r1 = r - A z0; stores (features(r1, z0), D e1 / s).
+// e1_out (nullable) receives e1.  Uses the work vectors Z0, AZ0, R1, C, AC.
+void store_pair(hhg_ctx* c, int l, const float* e, float* e1_out) {
+  LearnState& S = state(c);
+  LearnGrid& G = grid(c, l);
+  if (S.pair_level != l) THROW(HHG_ERR_STATE, "reserve pair storage for level %d first", l);
+  if (S.pair_count >= S.pair_cap) THROW(HHG_ERR_ARG, "pair storage full (%lld)", (long long)S.pair_cap);
+  const int64_t E = c->lv(l).entries, n = 3 * E;
+  float* z0 = lwork(c, G, l, LW_Z0);
+  float* az0 = lwork(c, G, l, LW_AZ0);
+  float* r1 = lwork(c, G, l, LW_R1);
+  float* r = lwork(c, G, l, LW_C);
+  float* e1 = lwork(c, G, l, LW_AC);
+  const float* dinv = dinv32(c, l);
+  if (S.dpart.bytes < (size_t)mse_partials(G.V) * sizeof(double))
+    CK(S.dpart.alloc((size_t)mse_partials(G.V) * sizeof(double)));
+  if (!S.dscal.p) CK(S.dscal.alloc(8 * sizeof(double)));
+  double* ssum = S.dscal.as<double>();
+  const double cnt = 3.0 * (double)std::max<int64_t>(G.nfree, 1);
+  apply32(c, l, e, r);
+  CK(cudaMemsetAsync(z0, 0, n * sizeof(float), c->stream));
+  vcycle32(c, l, r, z0);
+  apply32(c, l, z0, az0);
+  scale_vcycle_step(c, l, r, z0, az0);
+  copy32(c, l, r, r1);
+  CK(launch_axpby<float>(n, -1.f, az0, 1.f, r1, c->stream));
+  copy32(c, l, e, e1);
+  CK(launch_axpby<float>(n, -1.f, z0, 1.f, e1, c->stream));
+  CK(launch_feature_norm(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), z0, dinv, S.dpart.as<double>(), ssum,
+                         c->stream));
+  const int64_t p = S.pair_count++;
+  CK(launch_features(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), G.logk.as<float>(), r1, z0, e1, dinv, ssum,
+                     cnt, nullptr, (char*)S.pin.p + (size_t)p * G.V * LN_PAIR_IN * 2,
+                     S.ptg.as<float>() + (size_t)p * G.V * 3, c->stream));
+  if (e1_out) copy32(c, l, e1, e1_out);
 }
 
 }  // namespace
@@ -462,7 +533,7 @@ hhg_status hhg_learn_set_params(hhg_ctx* c, const float* params_host, int64_t n)
 
 hhg_status hhg_learn_grid(hhg_ctx* c, int level, int* dhw, int64_t* free_voxels) {
   return guard(c, [&] {
-    need_ready(c, true);
+    need_ready(c, false);
     LearnGrid& G = grid(c, level);
     if (dhw) {
       dhw[0] = G.D;
@@ -507,7 +578,8 @@ hhg_status hhg_learn_loss_grad(hhg_ctx* c, const float* x, int cin, const float*
 
 hhg_status hhg_learn_reserve_pairs(hhg_ctx* c, int level, int64_t capacity) {
   return guard(c, [&] {
-    need_elasticity(c);
+    need_ready(c, false);
+    if (c->prob.kind != HHG_ELASTICITY) THROW(HHG_ERR_UNSUPPORTED, "the learned preconditioner needs an elasticity problem");
     if (capacity < 1) THROW(HHG_ERR_ARG, "capacity");
     LearnState& S = state(c);
     LearnGrid& G = grid(c, level);
@@ -528,38 +600,57 @@ hhg_status hhg_learn_collect(hhg_ctx* c, int level, const float* e0_grid, int cy
     if (S.pair_level != level) THROW(HHG_ERR_STATE, "reserve pair storage for level %d first", level);
     if (S.pair_count + cycles > S.pair_cap) THROW(HHG_ERR_ARG, "pair storage full (%lld)", (long long)S.pair_cap);
     LearnGrid& G = grid(c, level);
-    const int64_t E = c->lv(level).entries, n = 3 * E;
-    float* e = lwork(c, G, level, LW_R);
-    float* r = lwork(c, G, level, LW_Z);
-    float* z0 = lwork(c, G, level, LW_Z0);
-    float* az0 = lwork(c, G, level, LW_AZ0);
-    float* r1 = lwork(c, G, level, LW_R1);
-    const float* dinv = dinv32(c, level);
-    if (S.dpart.bytes < (size_t)mse_partials(G.V) * sizeof(double))
-      CK(S.dpart.alloc((size_t)mse_partials(G.V) * sizeof(double)));
-    CK(launch_grid_to_lib(E, G.e2g.as<int64_t>(), G.efree.as<uint8_t>(), e0_grid, nullptr, nullptr, 1.0, e,
-                          c->stream));
-    const double cnt = 3.0 * (double)std::max<int64_t>(G.nfree, 1);
-    double* ssum = S.dscal.p ? S.dscal.as<double>() : nullptr;
-    if (!ssum) {
-      CK(S.dscal.alloc(8 * sizeof(double)));
-      ssum = S.dscal.as<double>();
-    }
-    for (int j = 0; j < cycles; ++j) {
-      apply32(c, level, e, r);
-      CK(cudaMemsetAsync(z0, 0, n * sizeof(float), c->stream));
-      vcycle32(c, level, r, z0);
-      apply32(c, level, z0, az0);
-      copy32(c, level, r, r1);
-      CK(launch_axpby<float>(n, -1.f, az0, 1.f, r1, c->stream));
-      CK(launch_axpby<float>(n, -1.f, z0, 1.f, e, c->stream));  // e <- e1 = e - z0
-      CK(launch_feature_norm(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), z0, dinv, S.dpart.as<double>(),
-                             ssum, c->stream));
-      const int64_t p = S.pair_count++;
-      CK(launch_features(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), G.logk.as<float>(), r1, z0, e, dinv,
-                         ssum, cnt, nullptr, (char*)S.pin.p + (size_t)p * G.V * LN_PAIR_IN * 2,
-                         S.ptg.as<float>() + (size_t)p * G.V * 3, c->stream));
-    }
+    float* e = lwork(c, G, level, LW_E);
+    CK(launch_grid_to_lib(c->lv(level).entries, G.e2g.as<int64_t>(), G.efree.as<uint8_t>(), e0_grid, nullptr, nullptr,
+                          1.0, e, c->stream));
+    for (int j = 0; j < cycles; ++j) store_pair(c, level, e, e);
+    wait_stream(c);
+    if (count) *count = S.pair_count;
+  });
+}
+
+hhg_status hhg_learn_collect_cg(hhg_ctx* c, int level, const float* f, int iters, int64_t* count) {
+  return guard(c, [&] {
+    need_elasticity(c);
+    mg_ready_check(c);
+    LearnState& S = state(c);
+    if (!f || iters < 1) THROW(HHG_ERR_ARG, "bad arguments");
+    if (S.pair_level != level) THROW(HHG_ERR_STATE, "reserve pair storage for level %d first", level);
+    if (S.pair_count + iters > S.pair_cap) THROW(HHG_ERR_ARG, "pair storage full (%lld)", (long long)S.pair_cap);
+    LearnGrid& G = grid(c, level);
+    const int64_t n = 3 * c->lv(level).entries;
+    // reference solution x* (FP64 refinement to 1e-10)
+    for (auto& v : G.lw64)
+      if (!v.p) CK(v.alloc(n * sizeof(double)));
+    double* f64 = G.lw64[0].as<double>();
+    double* x64 = G.lw64[1].as<double>();
+    CK(launch_convert<float, double>(n, f, f64, c->stream));
+    CK(cudaMemsetAsync(x64, 0, n * sizeof(double), c->stream));
+    hhg_solve_opts o{};
+    o.method = HHG_SOLVE_IR_FCG;
+    o.level = level;
+    o.dt = HHG_F64;
+    o.rtol = 1e-10;
+    o.max_iter = 30;
+    o.inner_rtol = 1e-3;
+    o.inner_max_iter = 100;
+    hhg_solve_report R{};
+    learned_ir(c, &o, f64, x64, false, R);
+    if (!R.converged) THROW(HHG_ERR_NOT_CONVERGED, "reference solve did not converge");
+    float* xs = lwork(c, G, level, LW_XS);
+    float* x = lwork(c, G, level, LW_X);
+    float* e = lwork(c, G, level, LW_E);
+    CK(launch_convert<double, float>(n, x64, xs, c->stream));
+    CK(cudaMemsetAsync(x, 0, n * sizeof(float), c->stream));
+    int stored = 0;
+    auto hook = [&](const float* xk) {
+      if (stored >= iters) return;
+      copy32(c, level, xs, e);
+      CK(launch_axpby<float>(n, -1.f, xk, 1.f, e, c->stream));  // e_k = x* - x_k
+      store_pair(c, level, e, nullptr);
+      ++stored;
+    };
+    fcg(c, level, f, x, 1e-7, iters, false, hook);
     wait_stream(c);
     if (count) *count = S.pair_count;
   });
@@ -669,10 +760,11 @@ hhg_status hhg_learn_stats(hhg_ctx* c, hhg_learn_stats_report* rep, int reset) {
       rep->alpha_mean = S.applications ? S.alpha_sum / S.applications : 0.0;
       rep->alpha_min = S.alpha_min;
       rep->alpha_max = S.alpha_max;
+      rep->gain_mean = S.applications ? S.gain_sum / S.applications : 0.0;
     }
     if (reset) {
       S.applications = S.fallbacks = 0;
-      S.alpha_sum = S.alpha_min = S.alpha_max = 0.0;
+      S.alpha_sum = S.alpha_min = S.alpha_max = S.gain_sum = 0.0;
     }
   });
 }

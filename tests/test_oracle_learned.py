@@ -94,9 +94,9 @@ def test_grid_index_is_a_bijection_onto_the_cube_lattice():
     assert np.array_equal(np.sort(flat), np.arange(729))
 
 
-def test_line_search_never_loses_to_the_vcycle():
-    """alpha minimises the energy norm of the error on z0 + alpha c: any other step on that
-    line (alpha = 0 is the plain V-cycle) leaves a larger error."""
+def test_combination_never_loses_to_the_vcycle():
+    """(a, b) minimise the energy norm of the error over span{z0, c}: any other point of
+    that plane -- the V-cycle step alone (b = 0) included -- leaves a larger error."""
     import hhg_inputs as hi
 
     H, lv, vox, dims, k, vc = _cube_problem(3)
@@ -106,19 +106,22 @@ def test_line_search_never_loses_to_the_vcycle():
     e[~fr] = 0.0
     r = (A @ e.reshape(-1)).reshape(-1, 3)
     r[~fr] = 0.0
-    z0 = vc(r)
+    v = vc(r)
     Ws, bs = LN.init_params(7)
-    z, alpha, c = LN.correction(A, lv.dirichlet, vox, dims, k, r, z0, Ws, bs)
-    assert np.abs(c).max() > 0
+    z, w, c = LN.correction(A, lv.dirichlet, vox, dims, k, r, v, Ws, bs)
+    assert np.abs(c).max() > 0 and w != 0
 
     def energy(zz):
         d = (e - zz).reshape(-1)
         return float(d @ (A @ d))
 
     best = energy(z)
-    for da in (-0.5, -0.1, 0.1, 0.5):
-        assert energy(z0 + (alpha + da * (abs(alpha) + 1e-3)) * c) > best
-    assert best <= energy(z0)
+    z0, _ = LN._scaled_step(A, lv.dirichlet, r, v)
+    rng = np.random.default_rng(0)
+    for _ in range(6):
+        da, db = rng.normal(size=2) * 0.05
+        assert energy(z + da * z0 + db * c * np.abs(z0).max() / np.abs(c).max()) > best
+    assert best <= energy(z0) <= energy(v) * (1 + 1e-12)
 
 
 def test_features_are_scale_invariant_and_pairs_consistent():
