@@ -44,88 +44,125 @@ __device__ __forceinline__ bool bf16_positive(uint32_t w, int hi) {
   return (h & 0x8000u) == 0 && (h & 0x7FFFu) != 0;
 }
 
-// Convolution.  A task is one row segment of 16 voxels along x; a warp computes all 16
-// output channels of it: per tap one A fragment (16 voxels x 16 input channels, the
-// rows shifted by the tap offset) against two B fragments (16 inputs x 8 outputs).
+// Convolution as an implicit GEMM on a shared-memory tile.  A block computes an output
+// tile of CT_Z x CT_Y x CT_X voxels (all 16 output channels): it stages the layer's packed
+// B fragments and the input tile with its one-voxel halo (zero outside the grid) in
+// shared memory with cp.async, then every warp takes two x-rows of 32 voxels (four m16
+// tiles) and, per tap, loads the four A fragments with ldmatrix (rows = 16 voxels shifted
+// by the tap, columns = 16 input channels) and the two B fragments (16 inputs x 8
+// outputs) once for all four tiles: 8 mma.sync m16n8k16 per 4 ldmatrix.x4 + 2 LDS.64.
+// A voxel's 16 channels are 32 bytes; its two 16-byte halves are stored swapped when bit
+// 2 of the tile-voxel index is set, so the 8 rows of every ldmatrix phase (8 consecutive
+// voxels) fall into distinct banks.
 // Fragment layouts of m16n8k16 (lane = 4 * gid + tig):
 //   A: a0 (row gid, cols 2 tig, +1), a1 (row gid + 8), a2 (cols + 8), a3 (row + 8, cols + 8)
 //   B: b0 (rows 2 tig, +1; col gid), b1 (rows + 8)
 //   D: d0, d1 (row gid, cols 2 tig, +1), d2, d3 (row gid + 8)
-// Voxels are rows, channels columns; a voxel's 16 channels are 8 32-bit words.
-__global__ void __launch_bounds__(WARPS * 32) k_conv(const uint32_t* __restrict__ X, const uint32_t* __restrict__ Wp,
-                                                     const float* __restrict__ bias, uint32_t* __restrict__ Y,
-                                                     float* __restrict__ Yf, int nf,
-                                                     const uint32_t* __restrict__ mask, int B, int D, int H, int W,
-                                                     int relu) {
-  __shared__ uint32_t ws[LN_PACK];
-  for (int q = threadIdx.x; q < LN_PACK; q += blockDim.x) ws[q] = Wp[q];
+// ldmatrix.x4: lane l addresses row (l & 15) of the 16-row block, channel half (l >> 4),
+// so that the four matrices are exactly a0..a3.
+constexpr int CT_X = 32, CT_Y = 4, CT_Z = 4;
+constexpr int CI_X = CT_X + 2, CI_Y = CT_Y + 2, CI_Z = CT_Z + 2;
+constexpr int CI_VOX = CI_X * CI_Y * CI_Z;
+constexpr int CONV_WARPS = 8;  // = CT_Y * CT_Z / 2 rows per warp
+constexpr int CONV_SMEM = LN_PACK * 4 + CI_VOX * 32;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0));
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+__global__ void __launch_bounds__(CONV_WARPS * 32) k_conv(const uint4* __restrict__ X, const uint4* __restrict__ Wp,
+                                                          const float* __restrict__ bias, uint32_t* __restrict__ Y,
+                                                          float* __restrict__ Yf, int nf,
+                                                          const uint32_t* __restrict__ mask, int D, int H, int W,
+                                                          int ntz, int relu) {
+  extern __shared__ uint4 smem[];
+  uint4* ws = smem;                  // LN_PACK / 4 chunks
+  uint4* xs = smem + LN_PACK / 4;    // CI_VOX * 2 chunks
+  const int b = blockIdx.z / ntz;
+  const int x0 = blockIdx.x * CT_X, y0 = blockIdx.y * CT_Y, z0 = (blockIdx.z % ntz) * CT_Z;
+  for (int q = threadIdx.x; q < LN_PACK / 4; q += blockDim.x) cp_async16(smem_u32(ws + q), Wp + q, true);
+  for (int q = threadIdx.x; q < CI_VOX * 2; q += blockDim.x) {
+    const int v = q >> 1, h = q & 1;
+    const int ix = v % CI_X, iy = (v / CI_X) % CI_Y, iz = v / (CI_X * CI_Y);
+    const int gx = x0 - 1 + ix, gy = y0 - 1 + iy, gz = z0 - 1 + iz;
+    const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D;
+    const uint4* src = in ? X + ((((int64_t)b * D + gz) * H + gy) * W + gx) * 2 + h : X;
+    cp_async16(smem_u32(xs + v * 2 + (h ^ ((v >> 2) & 1))), src, in);
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, tg = lane & 3;
+  const int lrow = lane & 15, lhalf = lane >> 4;
+  const uint32_t xs_base = smem_u32(xs);
+  const uint2* wsl = reinterpret_cast<const uint2*>(ws) + lane;
+  // rows of this warp: r = 2 warp + s (s = 0, 1); r -> (oz, oy) = (r / CT_Y, r % CT_Y)
+  float acc[4][2][4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[m][nt][q] = 0.f;
+#pragma unroll 1
+  for (int dz = 0; dz < 3; ++dz)
+#pragma unroll 1
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        const int t = dz * 9 + dy * 3 + dx;
+        const uint2 b0 = wsl[(t * 2) * 32], b1 = wsl[(t * 2 + 1) * 32];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int r = 2 * warp + (m >> 1);
+          const int oz = r / CT_Y, oy = r % CT_Y;
+          const int v = ((oz + dz) * CI_Y + (oy + dy)) * CI_X + (m & 1) * 16 + dx + lrow;
+          uint32_t a0, a1, a2, a3;
+          ldmatrix_x4(xs_base + (uint32_t)(v * 2 + (lhalf ^ ((v >> 2) & 1))) * 16u, a0, a1, a2, a3);
+          mma_bf16(acc[m][0], a0, a1, a2, a3, b0.x, b0.y);
+          mma_bf16(acc[m][1], a0, a1, a2, a3, b1.x, b1.y);
+        }
+      }
   float bv[2][2];
 #pragma unroll
   for (int nt = 0; nt < 2; ++nt) {
     bv[nt][0] = bias ? bias[nt * 8 + 2 * tg] : 0.f;
     bv[nt][1] = bias ? bias[nt * 8 + 2 * tg + 1] : 0.f;
   }
-  const int nxs = (W + 15) / 16;
-  const int64_t ntask = (int64_t)B * D * H * nxs;
-  for (int64_t task = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5); task < ntask;
-       task += (int64_t)gridDim.x * WARPS) {
-    const int xs = (int)(task % nxs);
-    int64_t rest = task / nxs;
-    const int y = (int)(rest % H);
-    rest /= H;
-    const int z = (int)(rest % D);
-    const int b = (int)(rest / D);
-    const int x0 = xs * 16;
-    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int zz = z + dz;
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int yy = y + dy;
-        const bool rin = zz >= 0 && zz < D && yy >= 0 && yy < H;  // warp-uniform
-        const int64_t row = (((int64_t)b * D + zz) * H + yy) * W;
 #pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int t = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
-          uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-          if (rin) {
-            const int xa = x0 + g + dx, xb = x0 + g + 8 + dx;
-            if (xa >= 0 && xa < W) {
-              a0 = X[(row + xa) * 8 + tg];
-              a2 = X[(row + xa) * 8 + tg + 4];
-            }
-            if (xb >= 0 && xb < W) {
-              a1 = X[(row + xb) * 8 + tg];
-              a3 = X[(row + xb) * 8 + tg + 4];
-            }
-          }
-          const uint32_t* wb = ws + (t * 2) * 64 + lane * 2;
-          mma_bf16(acc[0], a0, a1, a2, a3, wb[0], wb[1]);
-          mma_bf16(acc[1], a0, a1, a2, a3, wb[64], wb[65]);
-        }
-      }
-    }
+  for (int m = 0; m < 4; ++m) {
+    const int r = 2 * warp + (m >> 1);
+    const int z = z0 + r / CT_Y, y = y0 + r % CT_Y;
+    if (z >= D || y >= H) continue;
     const int64_t rowo = (((int64_t)b * D + z) * H + y) * W;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
-      const int x = x0 + g + 8 * half;
+      const int x = x0 + (m & 1) * 16 + g + 8 * half;
       if (x >= W) continue;
       const int64_t v = rowo + x;
 #pragma unroll
       for (int nt = 0; nt < 2; ++nt) {
         const int co = nt * 8 + 2 * tg;
-        float v0 = acc[nt][2 * half] + bv[nt][0];
-        float v1 = acc[nt][2 * half + 1] + bv[nt][1];
+        float v0 = acc[m][nt][2 * half] + bv[nt][0];
+        float v1 = acc[m][nt][2 * half + 1] + bv[nt][1];
         if (relu) {
           v0 = fmaxf(v0, 0.f);
           v1 = fmaxf(v1, 0.f);
         }
         if (mask) {
-          const uint32_t m = mask[v * 8 + (co >> 1)];
-          if (!bf16_positive(m, 0)) v0 = 0.f;
-          if (!bf16_positive(m, 1)) v1 = 0.f;
+          const uint32_t mw = mask[v * 8 + (co >> 1)];
+          if (!bf16_positive(mw, 0)) v0 = 0.f;
+          if (!bf16_positive(mw, 1)) v1 = 0.f;
         }
         if (Y) Y[v * 8 + (co >> 1)] = pack_bf16x2(v0, v1);
         if (Yf) {
@@ -442,10 +479,22 @@ inline int64_t red_blocks(int64_t V) { return blocks_for(V, RED_BLOCK, RED_MAX_B
 
 int launch_conv(const void* X, const uint32_t* Wp, const float* bias, void* Y, float* Yf, int nf, const void* mask,
                 GridShape s, int relu, void* stream) {
-  const int64_t ntask = (int64_t)s.B * s.D * s.H * ((s.W + 15) / 16);
-  if (ntask == 0) return 0;
-  k_conv<<<blocks_for(ntask, WARPS, 152 * 12), WARPS * 32, 0, (cudaStream_t)stream>>>(
-      (const uint32_t*)X, Wp, bias, (uint32_t*)Y, Yf, nf, (const uint32_t*)mask, s.B, s.D, s.H, s.W, relu);
+  if (s.voxels() == 0) return 0;
+  static bool attr[64] = {};  // per device: dynamic shared memory above 48 KB
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+  if (!attr[dev]) {
+    e = cudaFuncSetAttribute(k_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM);
+    if (e != cudaSuccess) return (int)e;
+    attr[dev] = true;
+  }
+  const int ntz = (s.D + CT_Z - 1) / CT_Z;
+  dim3 grid((unsigned)((s.W + CT_X - 1) / CT_X), (unsigned)((s.H + CT_Y - 1) / CT_Y), (unsigned)(ntz * s.B));
+  k_conv<<<grid, CONV_WARPS * 32, CONV_SMEM, (cudaStream_t)stream>>>((const uint4*)X, (const uint4*)Wp, bias,
+                                                                     (uint32_t*)Y, Yf, nf, (const uint32_t*)mask, s.D,
+                                                                     s.H, s.W, ntz, relu);
   return (int)cudaGetLastError();
 }
 
