@@ -165,6 +165,9 @@ hhg_status hhg_residual(hhg_ctx* ctx, int level, hhg_dtype dt, const void* f_dev
  * iterations) and an exact dense solve on the coarsest level (level 2).
  * ------------------------------------------------------------------------- */
 typedef enum { HHG_SMOOTH_JACOBI = 0, HHG_SMOOTH_CHEBYSHEV = 1 } hhg_smoother;
+/* Coarse-level coefficient: injection (the reading of Sec. 5's rediscretisation),
+ * or a local arithmetic / harmonic mean of the finer level's (for large jumps). */
+typedef enum { HHG_COARSE_INJECT = 0, HHG_COARSE_MEAN = 1, HHG_COARSE_HARMONIC = 2 } hhg_coarse_coeff;
 
 typedef struct {
   hhg_smoother smoother;
@@ -172,11 +175,17 @@ typedef struct {
   double omega;           /* Jacobi damping */
   double cheby_lo, cheby_hi; /* Chebyshev interval as fractions of lambda_max (default 1/8, 1.1) */
   int power_iters;        /* power iterations for lambda_max */
+  hhg_coarse_coeff coarse_coeff; /* coefficient of the coarse levels (default injection) */
 } hhg_mg_params;
 
 hhg_status hhg_set_mg_params(hhg_ctx* ctx, const hhg_mg_params* params);
 /* Diagonals, lambda_max of every level (unless set) and the dense coarse inverse
- * (at most 3000 coarse DoFs).  Call after hhg_set_coefficient; waits for the stream. */
+ * (at most 3000 coarse DoFs).  With coarse_coeff = MEAN or HARMONIC it first replaces
+ * the coarse levels' coefficient (level by level from the finest): at a coarse
+ * macro-interior node, the weighted mean of the fine coefficient (or of its inverse)
+ * over the node and its 14 fine neighbours with weights 1 and 1/2 (the restriction's
+ * weights, normalised); skeleton nodes keep the injected value.  Call after
+ * hhg_set_coefficient; waits for the stream. */
 hhg_status hhg_mg_setup(hhg_ctx* ctx);
 hhg_status hhg_get_lambda_max(hhg_ctx* ctx, int level, double* lambda);
 hhg_status hhg_set_lambda_max(hhg_ctx* ctx, int level, double lambda);

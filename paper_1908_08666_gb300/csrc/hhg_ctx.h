@@ -203,7 +203,7 @@ struct hhg_ctx {
   // host-buffer apply (hhg_apply_host)
   DevMem hx, hy;
   // kernel timing (hhg_profile): event pairs per part (0 interior, 1 skeleton)
-  hhg_mg_params mg{HHG_SMOOTH_CHEBYSHEV, 2, 2, 2.0 / 3.0, 1.0 / 8.0, 1.1, 15};
+  hhg_mg_params mg{HHG_SMOOTH_CHEBYSHEV, 2, 2, 2.0 / 3.0, 1.0 / 8.0, 1.1, 15, HHG_COARSE_INJECT};
   bool mg_ready = false;
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;

@@ -106,6 +106,10 @@ int launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const int32_t* rptr,
                     const T* rf, T* rc, void* stream);
 template <typename T>
 int launch_inject(const LevelDev& Lf, const LevelDev& Lc, const T* kf, T* kc, void* stream);
+// coarse macro-interior nodes: kc = weighted mean (harmonic = 1: of 1/k, inverted) of kf over the
+// coincident fine node (weight 1) and its 14 fine neighbours (weight 1/2); other nodes untouched
+int launch_average_coeff(const LevelDev& Lf, const LevelDev& Lc, const double* kf, double* kc, int harmonic,
+                         void* stream);
 
 // vector kernels over n elements
 template <typename T>

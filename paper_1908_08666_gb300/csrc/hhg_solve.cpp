@@ -736,6 +736,7 @@ hhg_status hhg_set_mg_params(hhg_ctx* c, const hhg_mg_params* p) {
     if (!(p->omega > 0.0 && p->omega < 2.0)) THROW(HHG_ERR_ARG, "omega");
     if (!(p->cheby_lo > 0.0 && p->cheby_hi > p->cheby_lo)) THROW(HHG_ERR_ARG, "Chebyshev interval");
     if (p->power_iters < 1) THROW(HHG_ERR_ARG, "power_iters");
+    if (p->coarse_coeff < HHG_COARSE_INJECT || p->coarse_coeff > HHG_COARSE_HARMONIC) THROW(HHG_ERR_ARG, "coarse_coeff");
     c->mg = *p;
   });
 }
@@ -743,6 +744,17 @@ hhg_status hhg_set_mg_params(hhg_ctx* c, const hhg_mg_params* p) {
 hhg_status hhg_mg_setup(hhg_ctx* c) {
   return guard(c, [&] {
     need_ready(c, true);
+    if (c->mg.coarse_coeff != HHG_COARSE_INJECT) {
+      for (int l = c->level_max; l > c->level_min; --l) {
+        LevelHost& Lf = c->lv(l);
+        LevelHost& Lc = c->lv(l - 1);
+        CK(launch_inject<double>(Lf.dev, Lc.dev, Lf.d_k64.as<double>(), Lc.d_k64.as<double>(), c->stream));
+        CK(launch_average_coeff(Lf.dev, Lc.dev, Lf.d_k64.as<double>(), Lc.d_k64.as<double>(),
+                                c->mg.coarse_coeff == HHG_COARSE_HARMONIC, c->stream));
+        CK(launch_convert<double, float>(Lc.entries, Lc.d_k64.as<double>(), Lc.d_k32.as<float>(), c->stream));
+        Lc.lambda_set = false;
+      }
+    }
     for (int l = c->level_min; l <= c->level_max; ++l) {
       compute_diag<double>(c, l);
       compute_diag<float>(c, l);

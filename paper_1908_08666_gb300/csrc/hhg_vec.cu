@@ -122,6 +122,26 @@ __global__ void k_restrict_skeleton(const LevelDev Lc, const int32_t* __restrict
   }
 }
 
+// coarse macro-interior nodes: local weighted mean of the fine coefficient (or of its inverse)
+__global__ void k_average_coeff(const LevelDev Lf, const LevelDev Lc, const double* __restrict__ kf,
+                                double* __restrict__ kc, int harmonic) {
+  const int m = blockIdx.y;
+  const int32_t tile = Lc.tiles_int[blockIdx.x];
+  const int k = tile >> 20;
+  const int j = ((tile >> 10) & 1023) + threadIdx.y;
+  const int i = (tile & 1023) + threadIdx.x;
+  const int n = Lf.n, nc = Lc.n;
+  if (i + j + k > nc - 1) return;
+  const int64_t fb = (int64_t)m * Lf.nt;
+  auto val = [&](int64_t e) { return harmonic ? 1.0 / kf[e] : kf[e]; };
+  double s = val(fb + lattice_index(n, 2 * i, 2 * j, 2 * k));
+#pragma unroll
+  for (int d = 0; d < NDIR; ++d)
+    s += 0.5 * val(fb + lattice_index(n, 2 * i + dir_di(d), 2 * j + dir_dj(d), 2 * k + dir_dk(d)));
+  s /= 1.0 + 0.5 * NDIR;
+  kc[(int64_t)m * Lc.nt + lattice_index(nc, i, j, k)] = harmonic ? 1.0 / s : s;
+}
+
 // coefficient injection: coarse points are fine points
 template <typename T>
 __global__ void k_inject(const LevelDev Lf, const LevelDev Lc, const T* __restrict__ kf, T* __restrict__ kc) {
@@ -435,6 +455,14 @@ int launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const int32_t* rptr,
     k_restrict_interior<T><<<grid, dim3(TILE_I, TILE_J), 0, s>>>(Lf, Lc, rf, rc);
   }
   if (Lc.nskel > 0) k_restrict_skeleton<T><<<(Lc.nskel + 127) / 128, 128, 0, s>>>(Lc, rptr, rent, rw, Lf.entries, rf, rc);
+  return (int)cudaGetLastError();
+}
+
+int launch_average_coeff(const LevelDev& Lf, const LevelDev& Lc, const double* kf, double* kc, int harmonic,
+                         void* stream) {
+  if (Lc.ntiles_int == 0) return 0;
+  dim3 grid(Lc.ntiles_int, Lc.nmacro);
+  k_average_coeff<<<grid, dim3(TILE_I, TILE_J), 0, (cudaStream_t)stream>>>(Lf, Lc, kf, kc, harmonic);
   return (int)cudaGetLastError();
 }
 
