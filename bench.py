@@ -529,6 +529,30 @@ def run_ours(args):
     time.sleep(0.2)
     clk = clocks.stop()
     assert torch.isfinite(y).all()
+    # BF16 coefficient option: the same apply with k rounded to BF16 (the macro-interior
+    # kernels read it as 2 bytes per node); error against the FP32-coefficient apply above
+    kb = kl.to(torch.bfloat16)
+    B.hhg_set_coefficient(h, kb.view(torch.int16), B.BF16)
+    yb = torch.empty_like(y)
+    for _ in range(3):
+        B.hhg_apply(h, level, B.F32, x, yb)
+    torch.cuda.synchronize()
+    B.hhg_profile(h, 1)
+    evb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for s, (a0, a1) in enumerate(evb):
+        flush.fill_(float(s))
+        a0.record(stream)
+        B.hhg_apply(h, level, B.F32, x, yb)
+        a1.record(stream)
+    torch.cuda.synchronize()
+    pb_ms, pb_l = B.hhg_profile(h, 0, read=True)
+    bms = sum(a0.elapsed_time(a1) for a0, a1 in evb) / args.steps
+    bf16 = {"ms_per_step": round(bms, 5), "value": round(dofs / (bms * 1e-3) / 1e9, 3), "unit": "GDoF/s",
+            "interior_launch_ms": round(pb_ms[0] / max(1, pb_l[0]), 5),
+            "bytes_per_interior_node": BYTES_PER_NODE_F32 - 2,
+            "rel_error_vs_fp32_coefficient": float((yb.double() - y.double()).norm() / y.double().norm()),
+            "max_abs_error_over_max_abs": float((yb - y).abs().max() / y.abs().max())}
+    B.hhg_set_coefficient(h, kl, B.F64)
     solve = None if args.no_solve else solve_times(B, torch, h, level, coords_e[first])
     B.hhg_destroy(h)
     stokes = None if args.no_stokes else stokes_bench(B, torch, level, dev, stream)
@@ -590,6 +614,7 @@ def run_ours(args):
         "solve": solve,
         "stokes": stokes,
         "carreau": carreau,
+        "bf16_coefficient": bf16,
         "learned": learned,
         "clocks": clk,
     }

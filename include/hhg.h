@@ -142,8 +142,14 @@ hhg_status hhg_gather_unique(hhg_ctx* ctx, int level, hhg_dtype dt, int comps, c
 hhg_status hhg_scatter_unique(hhg_ctx* ctx, int level, hhg_dtype dt, int comps, const void* src_dev, void* dst_dev);
 
 /* Nodal coefficient k (E for elasticity, mu for Stokes; Sec. 2, eq. nodalquad)
- * on the finest level, k_dev[E] in the library layout (dtype F64 or F32).
- * Coarser levels receive the injection (coarse nodes are fine nodes). */
+ * on the finest level, k_dev[E] in the library layout (dtype F64, F32 or BF16; BF16
+ * values are IEEE bfloat16 bit patterns, uint16).  Coarser levels receive the
+ * injection (coarse nodes are fine nodes).  With BF16 the operator is the one of the
+ * BF16 coefficient on every path; FP32 sweeps then read the coefficient of macro-interior
+ * nodes as BF16 (2 instead of 4 bytes per node), the other kernels read the same values
+ * widened.  The error against the FP32/FP64 coefficient is that of rounding each nodal
+ * k to BF16 (relative error at most 2^-8): each scaled block changes by at most 2^-8
+ * times the sum of the magnitudes of its terms. */
 hhg_status hhg_set_coefficient(hhg_ctx* ctx, const void* k_dev, hhg_dtype dt);
 
 /* y = A x on `level` (eq. residuallinalg without f): x_dev, y_dev are 3*E
@@ -425,10 +431,14 @@ hhg_status hhg_learn_stats(hhg_ctx* ctx, hhg_learn_stats_report* report, int res
  * waits for the stream (bounded wait). */
 hhg_status hhg_apply_host(hhg_ctx* ctx, int level, hhg_dtype dt, const void* x_host, void* y_host);
 
-/* Kernel timing.  enable != 0 starts (and resets) recording CUDA events around
- * the macro-interior launches and the skeleton launch of every sweep; ms_host[2]
- * and launches_host[2] (nullable) receive the accumulated device time and launch
- * counts of [interior, skeleton] since the last call (this waits for the stream). */
+/* Kernel timing.  enable != 0 starts (and resets) recording CUDA events around the
+ * parts of every operator sweep: the macro-interior launches (one per macro; they
+ * alternate between the context stream and a side stream, so consecutive launches
+ * overlap) and the skeleton kernels (on a second side stream, concurrent with the
+ * interior).  ms_host[2] and launches_host[2] (nullable) receive the accumulated span
+ * of each part (first start to last end, device time) and its launch count since the
+ * last call; span / launches is the interior launches' effective duration.  Waits for
+ * the stream. */
 hhg_status hhg_profile(hhg_ctx* ctx, int enable, double* ms_host, int64_t* launches_host);
 
 #ifdef __cplusplus

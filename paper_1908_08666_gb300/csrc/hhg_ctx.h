@@ -14,6 +14,7 @@
 #include <set>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -126,6 +127,7 @@ struct LevelHost {
   DevMem d_rptr, d_rent, d_rw64, d_rw32;
   DevMem d_mc64, d_mc32;
   DevMem d_k64, d_k32;
+  DevMem d_k16;  // BF16 bits of the coefficient (BF16 coefficient mode)
   std::vector<MacroStencil<double>> st64;
   std::vector<MacroStencil<float>> st32;
   LevelDev dev{};
@@ -195,6 +197,7 @@ struct hhg_ctx {
   bool have_problem = false;
   bool have_coeff = false;
   int64_t coeff_version = 0;  // incremented by hhg_set_coefficient
+  bool coeff_bf16 = false;     // the coefficient was given in BF16 (k16 holds it on every level)
   std::unique_ptr<LearnState> learn;
   OpFlags flags{1, 0, 0};
   DevMem scratch;   // reduction partials
@@ -206,11 +209,20 @@ struct hhg_ctx {
   hhg_mg_params mg{HHG_SMOOTH_CHEBYSHEV, 2, 2, 2.0 / 3.0, 1.0 / 8.0, 1.1, 15, HHG_COARSE_INJECT};
   bool mg_ready = false;
   bool prof = false;
+  // side streams of a sweep: aux[0] runs the skeleton kernels, aux[1] every second macro's
+  // interior launch, both forked from and joined back into `stream` by events
+  cudaStream_t aux[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::array<cudaEvent_t, 2>> prof_ev[2];
   int64_t prof_launches[2] = {0, 0};
   ~hhg_ctx() {
     if (pinned) cudaFreeHost(pinned);
+    for (auto st : aux)
+      if (st) cudaStreamDestroy(st);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    for (auto e : ev_join)
+      if (e) cudaEventDestroy(e);
     for (auto e : ev_pool) cudaEventDestroy(e);
     for (int q = 0; q < 2; ++q)
       for (auto& pr : prof_ev[q]) {
@@ -346,31 +358,58 @@ inline const MacroConsts<float>* consts_dev<float>(LevelHost& L) {
   return L.d_mc32.as<MacroConsts<float>>();
 }
 
+// One operator sweep on a level.  The macro-interior launches (one per macro) alternate
+// between `stream` and aux[1] so that the tail of one overlaps the next, and the skeleton
+// kernels run concurrently on aux[0] (they write disjoint entries and their own partial-sum
+// slots); both side streams are joined back into `stream`.  With profiling on, the
+// interior span (fork to join of the interior launches) and the skeleton span are timed.
 template <typename T>
 void sweep(hhg_ctx* c, int level, OpKind op, SweepArgs<T> a, double* norm2) {
   LevelHost& L = c->lv(level);
   a.k = kptr<T>(L);
-  int64_t np = 0;
+  if (std::is_same<T, float>::value && c->coeff_bf16) a.k16 = L.d_k16.as<uint16_t>();
   if (norm2) a.partial = c->scratch.as<double>();
-  if (!c->prof) {
-    CK(launch_sweep<T>(L.dev, stencils<T>(L), consts_dev<T>(L), op, c->flags, a, c->stream, 3, 0, &np));
-  } else {
-    int64_t off = 0;
-    for (int part = 0; part < 2; ++part) {
-      std::array<cudaEvent_t, 2> pr = {c->take_event(), c->take_event()};
-      CK(cudaEventRecord(pr[0], c->stream));
-      int64_t used = 0;
-      CK(launch_sweep<T>(L.dev, stencils<T>(L), consts_dev<T>(L), op, c->flags, a, c->stream, part + 1, off,
-                         &used));
-      CK(cudaEventRecord(pr[1], c->stream));
-      off += used;
-      c->prof_ev[part].push_back(pr);
-      c->prof_launches[part] += part == 0 ? (L.dev.ntiles_int > 0 ? L.dev.nmacro : 0)
-                                          : (L.dev.nface_items > 0) + (L.dev.nface_nodes > 0) + (L.dev.nev > 0) +
-                                                (L.dev.ndir > 0);
-    }
-    np = off;
+  if (!c->aux[0]) {
+    for (auto& st : c->aux) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    for (auto& e : c->ev_join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
+  std::array<cudaEvent_t, 2> pi{}, ps{};
+  if (c->prof) {
+    pi = {c->take_event(), c->take_event()};
+    ps = {c->take_event(), c->take_event()};
+    CK(cudaEventRecord(pi[0], c->stream));
+  }
+  CK(cudaEventRecord(c->ev_fork, c->stream));
+  CK(cudaStreamWaitEvent(c->aux[0], c->ev_fork, 0));
+  CK(cudaStreamWaitEvent(c->aux[1], c->ev_fork, 0));
+  // interior: macro m on stream (m even) or aux[1] (m odd); partial slots in macro order
+  int64_t used = 0;
+  for (int m = 0; m < L.dev.nmacro; ++m) {
+    int64_t cnt = 0;
+    CK(launch_sweep_macro<T>(L.dev, stencils<T>(L), m, op, c->flags, a, m % 2 ? c->aux[1] : c->stream, used, &cnt));
+    used += cnt;
+  }
+  if (c->prof) {
+    CK(cudaEventRecord(c->ev_join[1], c->aux[1]));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join[1], 0));
+    CK(cudaEventRecord(pi[1], c->stream));
+    CK(cudaEventRecord(ps[0], c->aux[0]));
+  }
+  int64_t used_sk = 0;
+  CK(launch_sweep<T>(L.dev, stencils<T>(L), consts_dev<T>(L), op, c->flags, a, c->aux[0], 2, used, &used_sk));
+  if (c->prof) {
+    CK(cudaEventRecord(ps[1], c->aux[0]));
+    c->prof_ev[0].push_back(pi);
+    c->prof_ev[1].push_back(ps);
+    c->prof_launches[0] += L.dev.ntiles_lin > 0 ? L.dev.nmacro : 0;
+    c->prof_launches[1] += (L.dev.nface_items > 0) + (L.dev.nface_nodes > 0) + (L.dev.nev > 0) + (L.dev.ndir > 0);
+  }
+  for (int q = 0; q < 2; ++q) {
+    CK(cudaEventRecord(c->ev_join[q], c->aux[q]));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join[q], 0));
+  }
+  const int64_t np = used + used_sk;
   if (norm2) {
     CK(launch_reduce(c->scratch.as<double>(), np, c->scalar.as<double>(), c->stream));
     CK(cudaMemcpyAsync(c->pinned, c->scalar.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));

@@ -901,9 +901,12 @@ hhg_status hhg_set_coefficient(hhg_ctx* c, const void* k, hhg_dtype dt) {
       CK(cudaMemcpyAsync(F.d_k64.p, k, F.entries * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     } else if (dt == HHG_F32) {
       CK(launch_convert<float, double>(F.entries, (const float*)k, F.d_k64.as<double>(), c->stream));
+    } else if (dt == HHG_BF16) {
+      CK(launch_bf16_to_f64(F.entries, (const uint16_t*)k, F.d_k64.as<double>(), c->stream));
     } else {
       THROW(HHG_ERR_ARG, "coefficient dtype");
     }
+    c->coeff_bf16 = dt == HHG_BF16;
     for (int l = c->level_max; l > c->level_min; --l) {
       LevelHost& Lf = *c->levels[l];
       LevelHost& Lc = *c->levels[l - 1];
@@ -911,7 +914,13 @@ hhg_status hhg_set_coefficient(hhg_ctx* c, const void* k, hhg_dtype dt) {
     }
     for (int l = c->level_min; l <= c->level_max; ++l) {
       LevelHost& L = *c->levels[l];
-      CK(launch_convert<double, float>(L.entries, L.d_k64.as<double>(), L.d_k32.as<float>(), c->stream));
+      if (c->coeff_bf16) {  // values are BF16 already: the rounding below is exact
+        if (!L.d_k16.p) CK(L.d_k16.alloc(L.entries * sizeof(uint16_t)));
+        CK(launch_round_bf16(L.entries, L.d_k64.as<double>(), L.d_k32.as<float>(), L.d_k16.as<uint16_t>(),
+                             c->stream));
+      } else {
+        CK(launch_convert<double, float>(L.entries, L.d_k64.as<double>(), L.d_k32.as<float>(), c->stream));
+      }
     }
     c->have_coeff = true;
     ++c->coeff_version;

@@ -30,6 +30,9 @@ struct SweepArgs {
   T* dout;  // CHEBY only
   double* partial;  // RESID: per-block partial sums of |r|^2 (nullable)
   double omega, rho1, rho2;
+  // BF16 bits of the coefficient (FP32 sweeps only; nullable): the macro-interior kernels
+  // read k from here (2 B per node); k holds the same values widened, for the others
+  const uint16_t* k16 = nullptr;
 };
 
 // parts: 1 = macro-interior kernels (one launch per macro), 2 = skeleton kernel, 3 = both.
@@ -39,6 +42,12 @@ template <typename T>
 int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev, OpKind op,
                  const OpFlags& fl, const SweepArgs<T>& a, void* stream, int parts, int64_t partial_offset,
                  int64_t* partial_count);
+
+// The macro-interior launch of macro m alone (partial slots from partial_offset; *partial_count
+// returns the slots used).
+template <typename T>
+int launch_sweep_macro(const LevelDev& L, const MacroStencil<T>* st_host, int m, OpKind op, const OpFlags& fl,
+                       const SweepArgs<T>& a, void* stream, int64_t partial_offset, int64_t* partial_count);
 
 // No-alloc residual (see hhg_residual_noalloc): static device scratch of
 // NOALLOC_SLOTS partial sums plus the result slot at index NOALLOC_SLOTS.
@@ -106,6 +115,10 @@ int launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const int32_t* rptr,
                     const T* rf, T* rc, void* stream);
 template <typename T>
 int launch_inject(const LevelDev& Lf, const LevelDev& Lc, const T* kf, T* kc, void* stream);
+// coefficient copies: k64[e] <- FP64 widening of BF16 bits (bf16_to_f64); or round k64 to the
+// nearest BF16 and write the value to k64, k32 and its bits to k16 (round_bf16)
+int launch_bf16_to_f64(int64_t n, const uint16_t* src, double* dst, void* stream);
+int launch_round_bf16(int64_t n, double* k64, float* k32, uint16_t* k16, void* stream);
 // coarse macro-interior nodes: kc = weighted mean (harmonic = 1: of 1/k, inverted) of kf over the
 // coincident fine node (weight 1) and its 14 fine neighbours (weight 1/2); other nodes untouched
 int launch_average_coeff(const LevelDev& Lf, const LevelDev& Lc, const double* kf, double* kc, int harmonic,

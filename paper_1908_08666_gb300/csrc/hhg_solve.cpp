@@ -751,7 +751,11 @@ hhg_status hhg_mg_setup(hhg_ctx* c) {
         CK(launch_inject<double>(Lf.dev, Lc.dev, Lf.d_k64.as<double>(), Lc.d_k64.as<double>(), c->stream));
         CK(launch_average_coeff(Lf.dev, Lc.dev, Lf.d_k64.as<double>(), Lc.d_k64.as<double>(),
                                 c->mg.coarse_coeff == HHG_COARSE_HARMONIC, c->stream));
-        CK(launch_convert<double, float>(Lc.entries, Lc.d_k64.as<double>(), Lc.d_k32.as<float>(), c->stream));
+        if (c->coeff_bf16)  // keep every copy of the coarse coefficient a BF16 value
+          CK(launch_round_bf16(Lc.entries, Lc.d_k64.as<double>(), Lc.d_k32.as<float>(), Lc.d_k16.as<uint16_t>(),
+                               c->stream));
+        else
+          CK(launch_convert<double, float>(Lc.entries, Lc.d_k64.as<double>(), Lc.d_k32.as<float>(), c->stream));
         Lc.lambda_set = false;
       }
     }

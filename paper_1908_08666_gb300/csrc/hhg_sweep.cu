@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "hhg_internal.h"
 #include "hhg_launch.h"
@@ -120,7 +121,8 @@ __device__ __forceinline__ void stokes_epilogue(const SweepArgs<T>& a, int64_t e
 
 // STK = 1: the Stokes saddle operator [[A(mu), B^T], [B, C]] on (u, v, w, p) (Sec. 5.2),
 // the velocity block being the scaled-stencil operator of the 2 mu eps(u) form.
-template <typename T, int OP, int GEN, int STK = 0>
+// KB = 1 (FP32, default operator only): the coefficient is read as BF16 bits from a.k16.
+template <typename T, int OP, int GEN, int STK = 0, int KB = 0>
 __global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, const MacroStencil<T> st,
                                                               const int macro, const OpFlags fl,
                                                               const SweepArgs<T> a) {
@@ -175,20 +177,23 @@ __global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, c
     {
       const T* __restrict__ X = a.x + base;
       const T* __restrict__ K = a.k + base;
+      const uint16_t* __restrict__ K16 = KB ? a.k16 + base : nullptr;
 #define HHG_ROW(R, ...)                                                                                   \
   {                                                                                                      \
     const T* px_ = X + (R);                                                                              \
     const T* py_ = px_ + E;                                                                              \
     const T* pz_ = py_ + E;                                                                              \
     const T* pk_ = K + (R);                                                                              \
+    const uint16_t* pk16_ = KB ? K16 + (R) : nullptr;                                                    \
     __VA_ARGS__                                                                                          \
   }
+#define HHG_K(OFF) (KB ? (T)__uint_as_float((uint32_t)pk16_[OFF] << 16) : pk_[OFF])
 #define HHG_NB(D, OFF)                                                                                    \
-  kk[D] = pk_[OFF];                                                                                      \
+  kk[D] = HHG_K(OFF);                                                                                    \
   dx[D] = px_[OFF];                                                                                      \
       dy[D] = py_[OFF];                                                                                  \
       dz[D] = pz_[OFF];
-      HHG_ROW(r00, x0 = px_[0]; y0 = py_[0]; z0 = pz_[0]; k0 = pk_[0]; HHG_NB(0, 1) HHG_NB(7, -1))
+      HHG_ROW(r00, x0 = px_[0]; y0 = py_[0]; z0 = pz_[0]; k0 = HHG_K(0); HHG_NB(0, 1) HHG_NB(7, -1))
       HHG_ROW(r10, HHG_NB(1, -1) HHG_NB(3, 0))
       HHG_ROW(rm1, HHG_NB(2, 0) HHG_NB(5, 1))
       HHG_ROW(r01, HHG_NB(4, -1) HHG_NB(6, 0))
@@ -196,6 +201,7 @@ __global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, c
       HHG_ROW(r1m, HHG_NB(9, 0) HHG_NB(12, -1))
       HHG_ROW(r0m, HHG_NB(11, 1) HHG_NB(13, 0))
 #undef HHG_NB
+#undef HHG_K
 #undef HHG_ROW
     }
 #pragma unroll
@@ -803,6 +809,43 @@ __global__ void __launch_bounds__(128) k_skeleton_ev_stk(const LevelDev L, const
 
 }  // namespace
 
+// one macro's interior launch: the BF16-coefficient kernel for FP32 sweeps of the default
+// operator when a.k16 is set, else the FP32/FP64 coefficient kernel
+template <typename T, int OP>
+void launch_interior(bool gen, const LevelDev& L, const MacroStencil<T>& st, int m, const OpFlags& fl,
+                     const SweepArgs<T>& am, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (am.k16 && !gen) {
+      k_interior<T, OP, 0, 0, 1><<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st, m, fl, am);
+      return;
+    }
+  }
+  if (gen)
+    k_interior<T, OP, 1><<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st, m, fl, am);
+  else
+    k_interior<T, OP, 0><<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st, m, fl, am);
+}
+
+template <typename T>
+int launch_sweep_macro(const LevelDev& L, const MacroStencil<T>* st_host, int m, OpKind op, const OpFlags& fl,
+                       const SweepArgs<T>& a, void* stream, int64_t partial_offset, int64_t* partial_count) {
+  if (partial_count) *partial_count = 0;
+  if (L.ntiles_lin == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool gen = !(fl.physical == 1 && fl.khat_edge == 0);
+  SweepArgs<T> am = a;
+  if (a.partial) am.partial = a.partial + partial_offset;
+  switch (op) {
+    case OP_APPLY: launch_interior<T, OP_APPLY>(gen, L, st_host[m], m, fl, am, s); break;
+    case OP_RESID: launch_interior<T, OP_RESID>(gen, L, st_host[m], m, fl, am, s); break;
+    case OP_JACOBI: launch_interior<T, OP_JACOBI>(gen, L, st_host[m], m, fl, am, s); break;
+    case OP_CHEBY: launch_interior<T, OP_CHEBY>(gen, L, st_host[m], m, fl, am, s); break;
+    case OP_DIAG: launch_interior<T, OP_DIAG>(gen, L, st_host[m], m, fl, am, s); break;
+  }
+  if (partial_count) *partial_count = L.ntiles_lin;
+  return (int)cudaGetLastError();
+}
+
 template <typename T>
 int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev, OpKind op,
                  const OpFlags& fl, const SweepArgs<T>& a, void* stream, int parts, int64_t partial_offset,
@@ -816,11 +859,11 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
     SweepArgs<T> am = a;
     if (a.partial) am.partial = a.partial + used;
     switch (op) {
-      case OP_APPLY: (gen ? k_interior<T, OP_APPLY, 1> : k_interior<T, OP_APPLY, 0>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st_host[m], m, fl, am); break;
-      case OP_RESID: (gen ? k_interior<T, OP_RESID, 1> : k_interior<T, OP_RESID, 0>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st_host[m], m, fl, am); break;
-      case OP_JACOBI: (gen ? k_interior<T, OP_JACOBI, 1> : k_interior<T, OP_JACOBI, 0>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st_host[m], m, fl, am); break;
-      case OP_CHEBY: (gen ? k_interior<T, OP_CHEBY, 1> : k_interior<T, OP_CHEBY, 0>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st_host[m], m, fl, am); break;
-      case OP_DIAG: (gen ? k_interior<T, OP_DIAG, 1> : k_interior<T, OP_DIAG, 0>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st_host[m], m, fl, am); break;
+      case OP_APPLY: launch_interior<T, OP_APPLY>(gen, L, st_host[m], m, fl, am, s); break;
+      case OP_RESID: launch_interior<T, OP_RESID>(gen, L, st_host[m], m, fl, am, s); break;
+      case OP_JACOBI: launch_interior<T, OP_JACOBI>(gen, L, st_host[m], m, fl, am, s); break;
+      case OP_CHEBY: launch_interior<T, OP_CHEBY>(gen, L, st_host[m], m, fl, am, s); break;
+      case OP_DIAG: launch_interior<T, OP_DIAG>(gen, L, st_host[m], m, fl, am, s); break;
     }
     used += L.ntiles_lin;
   }
@@ -1010,6 +1053,10 @@ int upload_direction_tables() {
   return (int)e;
 }
 
+template int launch_sweep_macro<float>(const LevelDev&, const MacroStencil<float>*, int, OpKind, const OpFlags&,
+                                       const SweepArgs<float>&, void*, int64_t, int64_t*);
+template int launch_sweep_macro<double>(const LevelDev&, const MacroStencil<double>*, int, OpKind, const OpFlags&,
+                                        const SweepArgs<double>&, void*, int64_t, int64_t*);
 template int launch_sweep<float>(const LevelDev&, const MacroStencil<float>*, const MacroConsts<float>*, OpKind,
                                  const OpFlags&, const SweepArgs<float>&, void*, int, int64_t, int64_t*);
 template int launch_sweep<double>(const LevelDev&, const MacroStencil<double>*, const MacroConsts<double>*, OpKind,

@@ -6,7 +6,10 @@
 // direction whose Kuhn coordinates are the parities (X mod 2, Y mod 2, Z mod 2)
 // of q.  Prolongation takes 1 resp. 1/2 of the parents; restriction is the
 // exact transpose: coarse point p collects r(2p) + 1/2 sum_d r(2p + d).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "hhg_internal.h"
 #include "hhg_launch.h"
@@ -119,6 +122,21 @@ __global__ void k_restrict_skeleton(const LevelDev Lc, const int32_t* __restrict
     const SkelInc I = Lc.skel_inc[q];
     const int64_t e = (int64_t)I.macro * Lc.nt + lattice_index(Lc.n, I.i, I.j, I.k);
     for (int c = 0; c < 3; ++c) rc[e + c * Lc.entries] = acc[c];
+  }
+}
+
+__global__ void k_bf16_to_f64(int64_t n, const uint16_t* __restrict__ src, double* __restrict__ dst) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (double)__uint_as_float((uint32_t)src[e] << 16);
+}
+
+__global__ void k_round_bf16(int64_t n, double* __restrict__ k64, float* __restrict__ k32, uint16_t* __restrict__ k16) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const __nv_bfloat16 b = __double2bfloat16(k64[e]);
+    const float f = __bfloat162float(b);
+    k16[e] = __bfloat16_as_ushort(b);
+    k32[e] = f;
+    k64[e] = (double)f;
   }
 }
 
@@ -455,6 +473,17 @@ int launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const int32_t* rptr,
     k_restrict_interior<T><<<grid, dim3(TILE_I, TILE_J), 0, s>>>(Lf, Lc, rf, rc);
   }
   if (Lc.nskel > 0) k_restrict_skeleton<T><<<(Lc.nskel + 127) / 128, 128, 0, s>>>(Lc, rptr, rent, rw, Lf.entries, rf, rc);
+  return (int)cudaGetLastError();
+}
+
+int launch_bf16_to_f64(int64_t n, const uint16_t* src, double* dst, void* stream) {
+  k_bf16_to_f64<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, (cudaStream_t)stream>>>(n, src, dst);
+  return (int)cudaGetLastError();
+}
+
+int launch_round_bf16(int64_t n, double* k64, float* k32, uint16_t* k16, void* stream) {
+  k_round_bf16<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, (cudaStream_t)stream>>>(n, k64, k32,
+                                                                                                     k16);
   return (int)cudaGetLastError();
 }
 

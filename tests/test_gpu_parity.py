@@ -171,3 +171,49 @@ def _decode(n, loc):
                 loc -= L
         loc -= sz
     raise ValueError
+
+
+def test_bf16_coefficient_parity_and_error():
+    """BF16 coefficient: the GPU operator equals the oracle's operator built with the
+    BF16-rounded nodal values (FP64 to 1e-12, FP32 to the FP32 bound; the FP32 apply reads
+    the BF16 bits), and differs from the operator of the unrounded coefficient by the
+    stated rounding error (each block by at most 2^-8 of its terms)."""
+    from oracle.learned import bf16
+
+    xyz, tets = hi.kuhn_cube()
+    level = 4
+    mm, lv, A = _oracle(xyz, tets, level, _kfun)
+    _, _, Ab = _oracle(xyz, tets, level, lambda c: bf16(_kfun(c)))
+    Ab_bc = op.with_dirichlet_rows(Ab, lv.dirichlet)
+    A_bc = op.with_dirichlet_rows(A, lv.dirichlet)
+    ctx = Ctx(xyz, tets, level, dict(nu=0.3))
+    try:
+        t = ctx.torch
+        perm = mesh.match_nodes(lv.coords, ctx.coords_u)
+        kb = np.empty(lv.num_nodes)
+        kb[perm] = bf16(_kfun(lv.coords))
+        kl = ctx.to_lib(kb, t.float32, 1).to(t.bfloat16)
+        assert np.array_equal(kl.float().cpu().numpy(), ctx.to_lib(kb, t.float32, 1).cpu().numpy())
+        B.hhg_set_coefficient(ctx.h, kl.view(t.int16), B.BF16)
+        x_or = hi.node_noise(lv.coords, seed=7)
+        x_u = np.empty_like(x_or)
+        x_u[perm] = x_or
+        y_b = op.apply(Ab_bc, x_or)
+        y_k = op.apply(A_bc, x_or)
+        scale = _fp32_scale(Ab, x_or, lv)
+        free = ~lv.dirichlet
+        for dt, tdt in ((B.F64, t.float64), (B.F32, t.float32)):
+            x = ctx.to_lib(x_u, tdt, 3)
+            y = t.empty_like(x)
+            B.hhg_apply(ctx.h, level, dt, x, y)
+            yg = ctx.from_lib(y, 3)[perm]
+            if dt == B.F64:
+                assert np.abs(yg - y_b).max() <= 1e-12 * np.abs(y_b).max()
+            else:
+                assert np.all(np.abs(yg - y_b)[free] <= FP32_C * scale[free] + 1e-30)
+        # the stated error of the BF16 coefficient against the exact one (2^-8 per term; the
+        # row scale below sums |A_ij| rather than the terms' magnitudes, hence a factor 2)
+        assert np.all(np.abs(y_b - y_k)[free] <= 2.0**-7 * _fp32_scale(A, x_or, lv)[free] + 1e-30)
+        assert np.linalg.norm(y_b - y_k) > 0
+    finally:
+        ctx.close()

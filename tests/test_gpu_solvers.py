@@ -13,7 +13,7 @@ import hhg_inputs as hi
 from oracle import fem, mesh, operators as op, solvers as S
 from paper_1908_08666_gb300 import binding as B
 
-from hhg_gpu import NU, Pair, kfun_smooth as _kfun  # noqa: F401
+from hhg_gpu import NU, Ctx, Pair, kfun_smooth as _kfun  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
