@@ -209,10 +209,11 @@ struct hhg_ctx {
   hhg_mg_params mg{HHG_SMOOTH_CHEBYSHEV, 2, 2, 2.0 / 3.0, 1.0 / 8.0, 1.1, 15, HHG_COARSE_INJECT};
   bool mg_ready = false;
   bool prof = false;
-  // side streams of a sweep: aux[0] runs the skeleton kernels, aux[1] every second macro's
-  // interior launch, both forked from and joined back into `stream` by events
-  cudaStream_t aux[2] = {nullptr, nullptr};
-  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+  // side streams of a sweep: aux[0] runs the face-node skeleton kernels, aux[1] every
+  // second macro's interior launch, aux[2] the edge/vertex kernel, aux[3] the Dirichlet
+  // rows; all forked from and joined back into `stream` by events
+  cudaStream_t aux[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::array<cudaEvent_t, 2>> prof_ev[2];
   int64_t prof_launches[2] = {0, 0};
@@ -381,8 +382,7 @@ void sweep(hhg_ctx* c, int level, OpKind op, SweepArgs<T> a, double* norm2) {
     CK(cudaEventRecord(pi[0], c->stream));
   }
   CK(cudaEventRecord(c->ev_fork, c->stream));
-  CK(cudaStreamWaitEvent(c->aux[0], c->ev_fork, 0));
-  CK(cudaStreamWaitEvent(c->aux[1], c->ev_fork, 0));
+  for (auto st : c->aux) CK(cudaStreamWaitEvent(st, c->ev_fork, 0));
   // interior: macro m on stream (m even) or aux[1] (m odd); partial slots in macro order
   int64_t used = 0;
   for (int m = 0; m < L.dev.nmacro; ++m) {
@@ -397,15 +397,20 @@ void sweep(hhg_ctx* c, int level, OpKind op, SweepArgs<T> a, double* norm2) {
     CK(cudaEventRecord(ps[0], c->aux[0]));
   }
   int64_t used_sk = 0;
-  CK(launch_sweep<T>(L.dev, stencils<T>(L), consts_dev<T>(L), op, c->flags, a, c->aux[0], 2, used, &used_sk));
+  CK(launch_sweep<T>(L.dev, stencils<T>(L), consts_dev<T>(L), op, c->flags, a, c->aux[0], 2, used, &used_sk,
+                     c->aux[2], c->aux[3]));
   if (c->prof) {
+    for (int q = 2; q < 4; ++q) {  // the skeleton span ends when all three skeleton streams have
+      CK(cudaEventRecord(c->ev_join[q], c->aux[q]));
+      CK(cudaStreamWaitEvent(c->aux[0], c->ev_join[q], 0));
+    }
     CK(cudaEventRecord(ps[1], c->aux[0]));
     c->prof_ev[0].push_back(pi);
     c->prof_ev[1].push_back(ps);
     c->prof_launches[0] += L.dev.ntiles_lin > 0 ? L.dev.nmacro : 0;
     c->prof_launches[1] += (L.dev.nface_items > 0) + (L.dev.nface_nodes > 0) + (L.dev.nev > 0) + (L.dev.ndir > 0);
   }
-  for (int q = 0; q < 2; ++q) {
+  for (int q = 0; q < 4; ++q) {
     CK(cudaEventRecord(c->ev_join[q], c->aux[q]));
     CK(cudaStreamWaitEvent(c->stream, c->ev_join[q], 0));
   }

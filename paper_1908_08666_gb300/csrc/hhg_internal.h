@@ -55,6 +55,15 @@ HHG_HD int ring_b(int d, int c) {
   return d < 7 ? t[d][c] : dir_neg(t[d - 7][c]);
 }
 
+// direction index of the corner offset (di, dj, dk), -1 if it is not a stencil direction
+HHG_HD int dir_of_offset(int di, int dj, int dk) {
+  int r = -1;
+#pragma unroll
+  for (int d = 0; d < NDIR; ++d)
+    if (dir_di(d) == di && dir_dj(d) == dj && dir_dk(d) == dk) r = d;
+  return r;
+}
+
 HHG_HD int64_t tetnum(int64_t a) { return a * (a + 1) * (a + 2) / 6; }
 HHG_HD int64_t lattice_size(int n) { return tetnum(n + 1); }
 // compact index of (i, j, k) inside one macro
@@ -67,6 +76,35 @@ HHG_HD int lattice_index32(int n, int i, int j, int k) {
   const int m = n - k;
   const int a = n + 1, b = n + 1 - k;
   return a * (a + 1) * (a + 2) / 6 - b * (b + 1) * (b + 2) / 6 + ((j * (2 * m + 3 - j)) >> 1) + i;
+}
+// compact indices of the 14 neighbours of (i, j, k) (32-bit, n <= 1000), from the
+// starts of the seven lattice rows they lie in; an entry is meaningful only where that
+// neighbour is a lattice point
+HHG_HD void lattice_neighbours(int n, int i, int j, int k, int nb[NDIR]) {
+  const int m = n - k;
+  const int r00 = lattice_index32(n, i, j, k);
+  const int r10 = r00 + (m + 1 - j);
+  const int rm0 = r00 - (m + 2 - j);
+  const int sz = (m + 1) * (m + 2) / 2;
+  const int szm = (m + 2) * (m + 3) / 2;
+  const int r01 = r00 + sz - j;
+  const int r0m = r00 - szm + j;
+  const int rm1 = rm0 + sz - j + 1;
+  const int r1m = r10 - szm + j + 1;
+  nb[0] = r00 + 1;
+  nb[7] = r00 - 1;
+  nb[1] = r10 - 1;
+  nb[3] = r10;
+  nb[2] = rm1;
+  nb[5] = rm1 + 1;
+  nb[4] = r01 - 1;
+  nb[6] = r01;
+  nb[8] = rm0 + 1;
+  nb[10] = rm0;
+  nb[9] = r1m;
+  nb[12] = r1m - 1;
+  nb[11] = r0m + 1;
+  nb[13] = r0m;
 }
 HHG_HD bool lattice_inside(int n, int i, int j, int k) { return i >= 0 && j >= 0 && k >= 0 && i + j + k <= n; }
 HHG_HD bool lattice_interior(int n, int i, int j, int k) {

@@ -38,10 +38,12 @@ struct SweepArgs {
 // parts: 1 = macro-interior kernels (one launch per macro), 2 = skeleton kernel, 3 = both.
 // partial_offset: first partial slot used (the interior launches take ntiles_lin slots per
 // macro, then the skeleton kernel one per block); *partial_count returns the slots used.
+// stream_ev / stream_dir (nullable: `stream`): streams of the edge/vertex and Dirichlet
+// skeleton kernels, which write disjoint entries and may run concurrently.
 template <typename T>
 int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev, OpKind op,
                  const OpFlags& fl, const SweepArgs<T>& a, void* stream, int parts, int64_t partial_offset,
-                 int64_t* partial_count);
+                 int64_t* partial_count, void* stream_ev = nullptr, void* stream_dir = nullptr);
 
 // The macro-interior launch of macro m alone (partial slots from partial_offset; *partial_count
 // returns the slots used).

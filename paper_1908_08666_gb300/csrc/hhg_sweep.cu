@@ -312,16 +312,20 @@ __device__ __forceinline__ bool kuhn_interior(int n, int X, int Y, int Z) {
 // 4p+av: Kuhn permutation p, node at vertex av) for partner vertices on the
 // skeleton (every partner with the practical rule), and the scaled blocks of
 // the directions that end at a macro-interior node (symmetric rule).
-template <typename T>
+// Candidates bit in [B0, B1) and directions in [D0, D1) only (a part of the row).
+template <typename T, int B0 = 0, int B1 = 24, int D0 = 0, int D1 = NDIR>
 __device__ __forceinline__ void incidence_row(const MacroConsts<T>& C, const T* __restrict__ px,
                                               const T* __restrict__ pk, int64_t E, int n, int i, int j, int k,
                                               uint32_t cand, uint32_t dirs, T x0, T y0, T z0, const OpFlags& fl,
                                               T& ax, T& ay, T& az, T& dgx, T& dgy, T& dgz) {
   const int X = i + j + k, Y = j + k, Z = k;
-  // fully unrolled over the 24 candidates so that permutation, vertex offsets and
-  // stiffness offsets are compile-time constants
+  int nb[NDIR];
+  lattice_neighbours(n, i, j, k, nb);
+  const int c0 = lattice_index32(n, i, j, k);
+  // fully unrolled over the 24 candidates so that permutation, vertex offsets, the
+  // neighbour direction of every vertex and stiffness offsets are compile-time constants
 #pragma unroll
-  for (int bit = 0; bit < 24; ++bit) {
+  for (int bit = B0; bit < B1; ++bit) {
     if (!((cand >> bit) & 1u)) continue;
     const int p = bit >> 2, av = bit & 3;
     int a0, a1, a2;
@@ -341,7 +345,9 @@ __device__ __forceinline__ void incidence_row(const MacroConsts<T>& C, const T* 
     for (int v = 0; v < 4; ++v) {
       const int VX = cX + PX[v], VY = cY + PY[v], VZ = cZ + PZ[v];
       ok = ok && kuhn_inside(n, VX, VY, VZ);
-      idx[v] = ok ? lattice_index32(n, VX - VY, VY - VZ, VZ) : 0;
+      // Kuhn offset of vertex v from the node, as a corner offset -> stencil direction
+      const int oX = PX[v] - PX[av], oY = PY[v] - PY[av], oZ = PZ[v] - PZ[av];
+      idx[v] = v == av ? c0 : nb[dir_of_offset(oX - oY, oY - oZ, oZ)];
       inner[v] = kuhn_interior(n, VX, VY, VZ);
     }
     if (!ok) continue;
@@ -361,20 +367,19 @@ __device__ __forceinline__ void incidence_row(const MacroConsts<T>& C, const T* 
     }
   }
   if (fl.practical || !dirs) return;
-  const T k0 = pk[lattice_index32(n, i, j, k)];
+  const T k0 = pk[c0];
 #pragma unroll
-  for (int d = 0; d < NDIR; ++d) {
+  for (int d = D0; d < D1; ++d) {
     if (!((dirs >> d) & 1u)) continue;
     const int qi = i + dir_di(d), qj = j + dir_dj(d), qk = k + dir_dk(d);
     if (!lattice_interior(n, qi, qj, qk)) continue;
-    const int qe = lattice_index32(n, qi, qj, qk);
+    const int qe = nb[d];
     T rs = 0, wx = 0, wy = 0, wz = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       if (c >= ring_count(d)) continue;
-      const int ra = ring_a(d, c), rb = ring_b(d, c);
-      const T ka = pk[lattice_index32(n, i + dir_di(ra), j + dir_dj(ra), k + dir_dk(ra))];
-      const T kb = pk[lattice_index32(n, i + dir_di(rb), j + dir_dj(rb), k + dir_dk(rb))];
+      const T ka = pk[nb[ring_a(d, c)]];
+      const T kb = pk[nb[ring_b(d, c)]];
       rs += ka + kb;
       const T dk = ka - kb;
       wx += dk * C.st.s[d][c][0];
@@ -497,33 +502,56 @@ __device__ __forceinline__ double* acc_of<double>(const LevelDev& L) {
   return L.acc64;
 }
 
-// Free face-interior skeleton nodes, one thread per (node, incident macro):
-// the macro's part of the row is added to the node's accumulator.  A face node
-// has at most two incidences, so 0 + a + b is the same in either order.
+// Free face-interior skeleton nodes, four warps per 32 (node, incident macro) items: warp
+// q of the block evaluates, for the item of its lane, candidate elements [6q, 6q+6) and
+// the directions [0,4), [4,8), [8,11) or [11,14) of the macro's part of the row (the part
+// is uniform per warp, so the unrolled bodies do not diverge); the block adds the four
+// partial sums in a fixed order, (p0 + p1) + (p2 + p3), into the node's accumulator.  A
+// face node has at most two incidences, so 0 + a + b is the same in either order.
+constexpr int FACE_PARTS = 4;
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_face_items(const LevelDev L, const MacroConsts<T>* __restrict__ mc,
-                                                     const OpFlags fl, const T* __restrict__ x,
-                                                     const T* __restrict__ kc) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= L.nface_items) return;
-  const FaceItem it = L.face_items[t];
-  const int n = L.n;
-  const int64_t E = L.entries;
-  const int64_t base = (int64_t)it.macro * L.nt;
-  const T* px = x + base;
-  const T* pk = kc + base;
-  const int c0 = lattice_index32(n, it.i, it.j, it.k);
-  const T x0 = px[c0], y0 = px[c0 + E], z0 = px[c0 + 2 * E];
+__global__ void __launch_bounds__(32 * FACE_PARTS) k_face_items(const LevelDev L, const MacroConsts<T>* __restrict__ mc,
+                                                                const OpFlags fl, const T* __restrict__ x,
+                                                                const T* __restrict__ kc) {
+  __shared__ T red[FACE_PARTS][6][32];
+  const int lane = threadIdx.x & 31, part = threadIdx.x >> 5;
+  const int64_t item = (int64_t)blockIdx.x * 32 + lane;
   T ax = 0, ay = 0, az = 0, dgx = 0, dgy = 0, dgz = 0;
-  incidence_row<T>(mc[it.macro], px, pk, E, n, it.i, it.j, it.k, L.face_mask[it.f], (1u << NDIR) - 1u, x0, y0, z0,
-                   fl, ax, ay, az, dgx, dgy, dgz);
-  T* acc = acc_of<T>(L) + 8 * (int64_t)it.node;
-  atomicAdd(acc + 0, ax);
-  atomicAdd(acc + 1, ay);
-  atomicAdd(acc + 2, az);
-  atomicAdd(acc + 3, dgx);
-  atomicAdd(acc + 4, dgy);
-  atomicAdd(acc + 5, dgz);
+  const bool valid = item < L.nface_items;
+  FaceItem it{};
+  if (valid) {
+    it = L.face_items[item];
+    const int n = L.n;
+    const int64_t E = L.entries;
+    const int64_t base = (int64_t)it.macro * L.nt;
+    const T* px = x + base;
+    const T* pk = kc + base;
+    const int c0 = lattice_index32(n, it.i, it.j, it.k);
+    const T x0 = px[c0], y0 = px[c0 + E], z0 = px[c0 + 2 * E];
+    const uint32_t cand = L.face_mask[it.f];
+    const uint32_t dirs = (1u << NDIR) - 1u;
+    const MacroConsts<T>& C = mc[it.macro];
+    switch (part) {
+      case 0: incidence_row<T, 0, 6, 0, 4>(C, px, pk, E, n, it.i, it.j, it.k, cand, dirs, x0, y0, z0, fl, ax, ay, az, dgx, dgy, dgz); break;
+      case 1: incidence_row<T, 6, 12, 4, 8>(C, px, pk, E, n, it.i, it.j, it.k, cand, dirs, x0, y0, z0, fl, ax, ay, az, dgx, dgy, dgz); break;
+      case 2: incidence_row<T, 12, 18, 8, 11>(C, px, pk, E, n, it.i, it.j, it.k, cand, dirs, x0, y0, z0, fl, ax, ay, az, dgx, dgy, dgz); break;
+      default: incidence_row<T, 18, 24, 11, 14>(C, px, pk, E, n, it.i, it.j, it.k, cand, dirs, x0, y0, z0, fl, ax, ay, az, dgx, dgy, dgz); break;
+    }
+  }
+  red[part][0][lane] = ax;
+  red[part][1][lane] = ay;
+  red[part][2][lane] = az;
+  red[part][3][lane] = dgx;
+  red[part][4][lane] = dgy;
+  red[part][5][lane] = dgz;
+  __syncthreads();
+  if (part == 0 && valid) {
+    T* acc = acc_of<T>(L) + 8 * (int64_t)it.node;
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      atomicAdd(acc + q, (red[0][q][lane] + red[1][q][lane]) + (red[2][q][lane] + red[3][q][lane]));
+  }
 }
 
 // Face nodes: finish the row from the accumulator (which is reset to zero) and
@@ -849,8 +877,10 @@ int launch_sweep_macro(const LevelDev& L, const MacroStencil<T>* st_host, int m,
 template <typename T>
 int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev, OpKind op,
                  const OpFlags& fl, const SweepArgs<T>& a, void* stream, int parts, int64_t partial_offset,
-                 int64_t* partial_count) {
+                 int64_t* partial_count, void* stream_ev, void* stream_dir) {
   cudaStream_t s = (cudaStream_t)stream;
+  cudaStream_t s_ev = stream_ev ? (cudaStream_t)stream_ev : s;
+  cudaStream_t s_dir = stream_dir ? (cudaStream_t)stream_dir : s;
   const dim3 blk(TILE_I, TILE_J);
   int64_t used = partial_offset;
   const bool gen = !(fl.physical == 1 && fl.khat_edge == 0);
@@ -869,8 +899,8 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
   }
   if (parts & 2) {
     if (L.nface_items > 0) {
-      const int nb = (L.nface_items + 127) / 128;
-      k_face_items<T><<<nb, 128, 0, s>>>(L, mc_dev, fl, a.x, a.k);
+      const int nb = (L.nface_items + 31) / 32;
+      k_face_items<T><<<nb, 32 * FACE_PARTS, 0, s>>>(L, mc_dev, fl, a.x, a.k);
     }
     if (L.nface_nodes > 0) {
       const int nb = (L.nface_nodes + 127) / 128;
@@ -890,22 +920,22 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
       SweepArgs<T> am = a;
       if (a.partial) am.partial = a.partial + used;
       switch (op) {
-        case OP_APPLY: k_skeleton_ev<T, OP_APPLY><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
-        case OP_RESID: k_skeleton_ev<T, OP_RESID><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
-        case OP_JACOBI: k_skeleton_ev<T, OP_JACOBI><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
-        case OP_CHEBY: k_skeleton_ev<T, OP_CHEBY><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
-        case OP_DIAG: k_skeleton_ev<T, OP_DIAG><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
+        case OP_APPLY: k_skeleton_ev<T, OP_APPLY><<<nb, 128, 0, s_ev>>>(L, mc_dev, fl, am); break;
+        case OP_RESID: k_skeleton_ev<T, OP_RESID><<<nb, 128, 0, s_ev>>>(L, mc_dev, fl, am); break;
+        case OP_JACOBI: k_skeleton_ev<T, OP_JACOBI><<<nb, 128, 0, s_ev>>>(L, mc_dev, fl, am); break;
+        case OP_CHEBY: k_skeleton_ev<T, OP_CHEBY><<<nb, 128, 0, s_ev>>>(L, mc_dev, fl, am); break;
+        case OP_DIAG: k_skeleton_ev<T, OP_DIAG><<<nb, 128, 0, s_ev>>>(L, mc_dev, fl, am); break;
       }
       used += nb;
     }
     if (L.ndir > 0) {
       const int nb = (L.ndir + 127) / 128;
       switch (op) {
-        case OP_APPLY: k_dirichlet<T, OP_APPLY><<<nb, 128, 0, s>>>(L, a); break;
-        case OP_RESID: k_dirichlet<T, OP_RESID><<<nb, 128, 0, s>>>(L, a); break;
-        case OP_JACOBI: k_dirichlet<T, OP_JACOBI><<<nb, 128, 0, s>>>(L, a); break;
-        case OP_CHEBY: k_dirichlet<T, OP_CHEBY><<<nb, 128, 0, s>>>(L, a); break;
-        case OP_DIAG: k_dirichlet<T, OP_DIAG><<<nb, 128, 0, s>>>(L, a); break;
+        case OP_APPLY: k_dirichlet<T, OP_APPLY><<<nb, 128, 0, s_dir>>>(L, a); break;
+        case OP_RESID: k_dirichlet<T, OP_RESID><<<nb, 128, 0, s_dir>>>(L, a); break;
+        case OP_JACOBI: k_dirichlet<T, OP_JACOBI><<<nb, 128, 0, s_dir>>>(L, a); break;
+        case OP_CHEBY: k_dirichlet<T, OP_CHEBY><<<nb, 128, 0, s_dir>>>(L, a); break;
+        case OP_DIAG: k_dirichlet<T, OP_DIAG><<<nb, 128, 0, s_dir>>>(L, a); break;
       }
     }
   }
@@ -1058,8 +1088,8 @@ template int launch_sweep_macro<float>(const LevelDev&, const MacroStencil<float
 template int launch_sweep_macro<double>(const LevelDev&, const MacroStencil<double>*, int, OpKind, const OpFlags&,
                                         const SweepArgs<double>&, void*, int64_t, int64_t*);
 template int launch_sweep<float>(const LevelDev&, const MacroStencil<float>*, const MacroConsts<float>*, OpKind,
-                                 const OpFlags&, const SweepArgs<float>&, void*, int, int64_t, int64_t*);
+                                 const OpFlags&, const SweepArgs<float>&, void*, int, int64_t, int64_t*, void*, void*);
 template int launch_sweep<double>(const LevelDev&, const MacroStencil<double>*, const MacroConsts<double>*, OpKind,
-                                  const OpFlags&, const SweepArgs<double>&, void*, int, int64_t, int64_t*);
+                                  const OpFlags&, const SweepArgs<double>&, void*, int, int64_t, int64_t*, void*, void*);
 
 }  // namespace hhg
