@@ -271,12 +271,15 @@ def stokes_bench(B, torch, level, dev, stream, steps=20):
         torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev) / steps
         B.hhg_mg_setup(h)
-        x = torch.zeros_like(f)
-        rep = B.hhg_solve(h, f, x, method=B.SOLVE_STOKES_IR_MINRES, level=level, dt=B.F64, rtol=1e-8, max_iter=30,
-                          inner_rtol=1e-3, inner_max_iter=400, allow_not_converged=True)
-        return {"workload": "Stokes, 6-macro cube, level %d, viscosity sphere 1 / 1e3, f ~ U[-1,1] (seed 4)" % level,
-                "apply_ms": round(ms, 5), "apply_gdofs": round(4 * U / (ms * 1e-3) / 1e9, 3),
-                "ir_minres": {k: (float("%.4g" % v) if isinstance(v, float) else v) for k, v in rep.items()}}
+        out = {"workload": "Stokes, 6-macro cube, level %d, viscosity sphere 1 / 1e3, f ~ U[-1,1] (seed 4)" % level,
+               "apply_ms": round(ms, 5), "apply_gdofs": round(4 * U / (ms * 1e-3) / 1e9, 3)}
+        for name, method, inner in (("ir_minres", B.SOLVE_STOKES_IR_MINRES, 400),
+                                    ("ir_uzawa_mg", B.SOLVE_STOKES_IR_UZAWA, 40)):
+            x = torch.zeros_like(f)
+            rep = B.hhg_solve(h, f, x, method=method, level=level, dt=B.F64, rtol=1e-8, max_iter=30,
+                              inner_rtol=1e-3, inner_max_iter=inner, allow_not_converged=True)
+            out[name] = {k: (float("%.4g" % v) if isinstance(v, float) else v) for k, v in rep.items()}
+        return out
     finally:
         B.hhg_destroy(h)
 

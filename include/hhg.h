@@ -182,6 +182,12 @@ typedef struct {
   double cheby_lo, cheby_hi; /* Chebyshev interval as fractions of lambda_max (default 1/8, 1.1) */
   int power_iters;        /* power iterations for lambda_max */
   hhg_coarse_coeff coarse_coeff; /* coefficient of the coarse levels (default injection) */
+  /* Stokes inexact-Uzawa multigrid (HHG_SOLVE_STOKES_UZAWA*): V(uzawa_pre, uzawa_post)
+   * with uzawa_extra more steps on every coarser level (variable V-cycle, default 3, 3, 2);
+   * each Uzawa step smooths the velocity with uzawa_vsteps steps of the smoother above
+   * (default 2) and then relaxes the pressure with weight uzawa_omega (default 0.5). */
+  int uzawa_pre, uzawa_post, uzawa_extra, uzawa_vsteps;
+  double uzawa_omega;
 } hhg_mg_params;
 
 hhg_status hhg_set_mg_params(hhg_ctx* ctx, const hhg_mg_params* params);
@@ -212,8 +218,9 @@ typedef enum {
   HHG_SOLVE_IR_MG_CG = 2,   /* FP64 iterative refinement around FP32 MG-CG (f, x in FP64) */
   HHG_SOLVE_MG = 3,         /* stationary V-cycles */
   /* Stokes (problem kind HHG_STOKES; f, x hold (u, v, w, p), 4*E values): MINRES
-   * preconditioned by blockdiag(one velocity V-cycle, mu_i / m_i) with m the lumped
-   * pressure mass; the pressure is shifted to zero mean (sum m_i p_i = 0) at the end. */
+   * preconditioned by blockdiag(one velocity V-cycle, S^-1) with the diagonal Schur
+   * surrogate S_ii = m_i / mu_i + (-C)_ii (m the lumped pressure mass, C the pressure
+   * stabilisation); the pressure is shifted to zero mean (sum m_i p_i = 0) at the end. */
   HHG_SOLVE_STOKES_MINRES = 4,
   HHG_SOLVE_STOKES_IR_MINRES = 5, /* FP64 iterative refinement around FP32 MINRES */
   /* Elasticity on a mesh whose nodes lie on an axis-aligned uniform lattice: FP64
@@ -221,7 +228,16 @@ typedef enum {
    * learned correction (hhg_learn_*; parameters must be set), or by the V-cycle alone
    * (IR_FCG, the same solver without the network). */
   HHG_SOLVE_IR_FCG_LEARNED = 6,
-  HHG_SOLVE_IR_FCG = 7
+  HHG_SOLVE_IR_FCG = 7,
+  /* Stokes: the inexact Uzawa multigrid of Sec. 5.2 -- all-at-once V-cycles on the saddle
+   * system (velocity and pressure restricted and prolongated together, coarsest level
+   * solved exactly), each smoothing step a velocity smoothing with the pressure fixed
+   * followed by the pressure update p -= omega S^-1 (g - B u - C p) with S as for MINRES.  UZAWA
+   * iterates V-cycles in the type of f and x; IR_UZAWA refines in FP64 around FP32
+   * V-cycles, each inner solve to inner_rtol (at most inner_max_iter cycles).  The
+   * pressure is shifted to zero mean at the end. */
+  HHG_SOLVE_STOKES_UZAWA = 8,
+  HHG_SOLVE_STOKES_IR_UZAWA = 9
 } hhg_solve_method;
 
 typedef struct {

@@ -34,12 +34,14 @@ SMOOTH_JACOBI, SMOOTH_CHEBYSHEV = 0, 1
 COARSE_INJECT, COARSE_MEAN, COARSE_HARMONIC = 0, 1, 2
 SOLVE_PCG_JACOBI, SOLVE_MG_CG, SOLVE_IR_MG_CG, SOLVE_MG, SOLVE_STOKES_MINRES, SOLVE_STOKES_IR_MINRES = 0, 1, 2, 3, 4, 5
 SOLVE_IR_FCG_LEARNED, SOLVE_IR_FCG = 6, 7
+SOLVE_STOKES_UZAWA, SOLVE_STOKES_IR_UZAWA = 8, 9
 
 
 class hhg_mg_params(C.Structure):
     _fields_ = [("smoother", C.c_int), ("pre", C.c_int), ("post", C.c_int), ("omega", C.c_double),
                 ("cheby_lo", C.c_double), ("cheby_hi", C.c_double), ("power_iters", C.c_int),
-                ("coarse_coeff", C.c_int)]
+                ("coarse_coeff", C.c_int), ("uzawa_pre", C.c_int), ("uzawa_post", C.c_int),
+                ("uzawa_extra", C.c_int), ("uzawa_vsteps", C.c_int), ("uzawa_omega", C.c_double)]
 
 
 class hhg_solve_opts(C.Structure):
@@ -299,8 +301,10 @@ def hhg_residual_noalloc(ctx, level, dt, f, x, r):
 
 
 def hhg_set_mg_params(ctx, smoother=SMOOTH_CHEBYSHEV, pre=2, post=2, omega=2.0 / 3.0, cheby_lo=1.0 / 8.0,
-                      cheby_hi=1.1, power_iters=15, coarse_coeff=0):
-    p = hhg_mg_params(smoother, pre, post, omega, cheby_lo, cheby_hi, power_iters, coarse_coeff)
+                      cheby_hi=1.1, power_iters=15, coarse_coeff=0, uzawa_pre=3, uzawa_post=3, uzawa_extra=2,
+                      uzawa_vsteps=2, uzawa_omega=0.5):
+    p = hhg_mg_params(smoother, pre, post, omega, cheby_lo, cheby_hi, power_iters, coarse_coeff, uzawa_pre,
+                      uzawa_post, uzawa_extra, uzawa_vsteps, uzawa_omega)
     _check(ctx, load().hhg_set_mg_params(ctx, C.byref(p)))
 
 

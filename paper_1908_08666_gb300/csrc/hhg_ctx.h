@@ -117,7 +117,15 @@ struct LevelHost {
   DevMem d_face_items_all, d_face_nodes_all, d_ev_all;
   DevMem d_mask_own, d_invm64, d_invm32;  // owned-node mask; inverse lumped mass
   DevMem d_mass64, d_mass32;              // lumped mass
+  DevMem d_sdiag64, d_sdiag32;            // Stokes: diagonal of -C (pressure stabilisation)
   DevMem sw64[10], sw32[10];               // Stokes work vectors (4*E)
+  // Stokes all-at-once multigrid: pressure restriction lists over all fine nodes (this
+  // level as the coarse one), Uzawa work vectors (4*E), dense coarse saddle inverse
+  bool rlist_p = false;
+  DevMem d_rptr_p, d_rent_p, d_rw64_p, d_rw32_p;
+  DevMem uz64[4], uz32[4];
+  int nscdof = 0;
+  DevMem d_scdof, d_scinv64, d_scinv32, su64, su32;
   // Carreau viscosity: per-macro slope operators and skeleton patch lists (built on first use)
   std::vector<SlopeOp> slope;
   DevMem d_pnode, d_pptr, d_pent, d_pdx;
@@ -206,7 +214,7 @@ struct hhg_ctx {
   // host-buffer apply (hhg_apply_host)
   DevMem hx, hy;
   // kernel timing (hhg_profile): event pairs per part (0 interior, 1 skeleton)
-  hhg_mg_params mg{HHG_SMOOTH_CHEBYSHEV, 2, 2, 2.0 / 3.0, 1.0 / 8.0, 1.1, 15, HHG_COARSE_INJECT};
+  hhg_mg_params mg{HHG_SMOOTH_CHEBYSHEV, 2, 2, 2.0 / 3.0, 1.0 / 8.0, 1.1, 15, HHG_COARSE_INJECT, 3, 3, 2, 2, 0.5};
   bool mg_ready = false;
   bool prof = false;
   // side streams of a sweep: aux[0] runs the face-node skeleton kernels, aux[1] every

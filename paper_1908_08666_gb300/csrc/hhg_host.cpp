@@ -814,6 +814,44 @@ hhg_status hhg_set_problem(hhg_ctx* c, const hhg_problem* p) {
       }
       upload(L.d_mc64, mc64);
       upload(L.d_mc32, mc32);
+      if (p->kind == HHG_STOKES) {
+        // diagonal of -C (pressure stabilisation) at every node: sum over the elements
+        // around it, in every incident macro, of the element matrix's diagonal entry
+        const int n = L.n;
+        auto inside = [&](int i, int j, int k, int pp, int av) {
+          const int X = i + j + k, Y = j + k, Z = k;
+          int P[4][3];
+          kuhn_vertices(pp, P);
+          for (int v = 0; v < 4; ++v) {
+            const int VX = X - P[av][0] + P[v][0], VY = Y - P[av][1] + P[v][1], VZ = Z - P[av][2] + P[v][2];
+            if (!(0 <= VZ && VZ <= VY && VY <= VX && VX <= n)) return false;
+          }
+          return true;
+        };
+        std::vector<double> du(L.nunique, 0.0);
+        const int64_t nint = L.nunique - (int64_t)L.skel_dir.size();
+        std::vector<double> dint(M, 0.0);
+        for (int m = 0; m < M; ++m)
+          for (int pp = 0; pp < 6; ++pp)
+            for (int av = 0; av < 4; ++av) dint[m] -= mc64[m].lc[pp][av][av];
+        for (int m = 0; m < M; ++m)
+          for (int64_t q = 0; q < L.nt; ++q) {
+            const int64_t u = L.entry_to_unique[(int64_t)m * L.nt + q];
+            if (u < nint) du[u] = dint[m];
+          }
+        for (int64_t sk = 0; sk < (int64_t)L.skel_dir.size(); ++sk)
+          for (int q = L.skel_ptr[sk]; q < L.skel_ptr[sk + 1]; ++q) {
+            const SkelInc& I = L.skel_inc[q];
+            for (int pp = 0; pp < 6; ++pp)
+              for (int av = 0; av < 4; ++av)
+                if (inside(I.i, I.j, I.k, pp, av)) du[nint + sk] -= mc64[I.macro].lc[pp][av][av];
+          }
+        std::vector<double> d64(L.entries);
+        for (int64_t e = 0; e < L.entries; ++e) d64[e] = du[L.entry_to_unique[e]];
+        std::vector<float> d32(d64.begin(), d64.end());
+        upload(L.d_sdiag64, d64);
+        upload(L.d_sdiag32, d32);
+      }
     }
     c->prob = *p;
     c->flags.physical = p->variant == HHG_PHYSICAL ? 1 : 0;

@@ -108,13 +108,18 @@ template <typename T>
 int launch_mul3(int64_t n, const T* a, const T* b, const T* c, T* out, void* stream);  // out = a * b * c
 template <typename T>
 int launch_add_const(int64_t n, T v, T* dst, void* stream);                           // dst += v
+// out = r / (m / mu + s): the pressure Schur-complement diagonal of the Stokes solvers
+template <typename T>
+int launch_schur_diag(int64_t n, const T* r, const T* mu, const T* m, const T* s, T* out, void* stream);
 
 // multigrid transfers and coefficient injection (all on the fine level's lattice)
+// comps: components of the fields (3 velocity, 1 pressure); use_dir = 0: the coarse skeleton
+// rows of Dirichlet nodes are restricted too (pressure, with lists over all fine nodes)
 template <typename T>
-int launch_prolong_add(const LevelDev& Lf, const LevelDev& Lc, const T* ec, T* ef, void* stream);
+int launch_prolong_add(const LevelDev& Lf, const LevelDev& Lc, const T* ec, T* ef, void* stream, int comps = 3);
 template <typename T>
 int launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const int32_t* rptr, const int64_t* rent, const T* rw,
-                    const T* rf, T* rc, void* stream);
+                    const T* rf, T* rc, void* stream, int comps = 3, int use_dir = 1);
 template <typename T>
 int launch_inject(const LevelDev& Lf, const LevelDev& Lc, const T* kf, T* kc, void* stream);
 // coefficient copies: k64[e] <- FP64 widening of BF16 bits (bf16_to_f64); or round k64 to the

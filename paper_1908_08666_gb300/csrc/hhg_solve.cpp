@@ -471,13 +471,33 @@ double sdot(hhg_ctx* c, int l, const T* a, const T* b) {
   return c->pinned[0];
 }
 
-// z = blockdiag(V-cycle of A(mu), diag(mu / m)) r
+template <typename T>
+const T* sdiag(LevelHost& L);
+template <>
+const double* sdiag<double>(LevelHost& L) {
+  return L.d_sdiag64.as<double>();
+}
+template <>
+const float* sdiag<float>(LevelHost& L) {
+  return L.d_sdiag32.as<float>();
+}
+
+// Pressure Schur-complement surrogate: S = C - B A^-1 B^T is approximated by
+// -diag(m_i / mu_i + (-C)_ii) (lumped mass over the viscosity, plus the stabilisation,
+// which carries no 1/mu and dominates where mu is large); out = r / (m / mu + (-C)_ii).
+template <typename T>
+void schur_apply(hhg_ctx* c, int l, const T* r, T* out) {
+  LevelHost& L = c->lv(l);
+  CK(launch_schur_diag<T>(L.entries, r, kptr<T>(L), mass<T>(L), sdiag<T>(L), out, c->stream));
+}
+
+// z = blockdiag(V-cycle of A(mu), Schur surrogate^-1) r
 template <typename T>
 void stokes_precond(hhg_ctx* c, int l, const T* r, T* z) {
   LevelHost& L = c->lv(l);
   CK(cudaMemsetAsync(z, 0, 3 * L.entries * sizeof(T), c->stream));
   vcycle<T>(c, l, r, z);
-  CK(launch_mul3<T>(L.entries, r + 3 * L.entries, kptr<T>(L), invm<T>(L), z + 3 * L.entries, c->stream));
+  schur_apply<T>(c, l, r + 3 * L.entries, z + 3 * L.entries);
 }
 
 // shift the pressure to zero mean: sum_i m_i p_i = 0 over unique nodes
@@ -576,6 +596,244 @@ MinresResult minres(hhg_ctx* c, int l, const T* f, T* x, double rtol, int max_it
   const double rr = stokes_sweep<T>(c, l, OP_RESID, f, x, r, true);
   R.rel = std::sqrt(rr / r0);
   return R;
+}
+
+// ------------------------------------------------ Stokes inexact Uzawa multigrid (Sec. 5.2)
+
+template <typename T>
+DevMem* uzwork(LevelHost& L);
+template <>
+DevMem* uzwork<double>(LevelHost& L) {
+  return L.uz64;
+}
+template <>
+DevMem* uzwork<float>(LevelHost& L) {
+  return L.uz32;
+}
+
+template <typename T>
+void ensure_uzwork(hhg_ctx* c, int l) {
+  LevelHost& L = c->lv(l);
+  DevMem* W = uzwork<T>(L);
+  if (W[0].p) return;
+  for (int q = 0; q < 4; ++q) {
+    CK(W[q].alloc(4 * (size_t)L.entries * sizeof(T)));
+    CK(cudaMemsetAsync(W[q].p, 0, W[q].bytes, c->stream));
+  }
+}
+
+// restriction lists of the pressure: the coarse skeleton node lc gathers every unique fine
+// node of its restriction stencil (weights 1 and 1/2), Dirichlet or not
+void build_pressure_restriction(hhg_ctx* c, int lc) {
+  LevelHost& C = c->lv(lc);
+  if (C.rlist_p) return;
+  LevelHost& F = c->lv(lc + 1);
+  const int nf = F.n;
+  const int64_t nskel = (int64_t)C.skel_dir.size();
+  std::vector<int32_t> ptr(nskel + 1, 0);
+  std::vector<int64_t> ent;
+  std::vector<double> w;
+  for (int64_t s = 0; s < nskel; ++s) {
+    std::map<int64_t, std::pair<int64_t, double>> fine;
+    for (int q = C.skel_ptr[s]; q < C.skel_ptr[s + 1]; ++q) {
+      const SkelInc& I = C.skel_inc[q];
+      const int fi = 2 * I.i, fj = 2 * I.j, fk = 2 * I.k;
+      for (int d = -1; d < NDIR; ++d) {
+        const int qi = fi + (d < 0 ? 0 : dir_di(d)), qj = fj + (d < 0 ? 0 : dir_dj(d)), qk = fk + (d < 0 ? 0 : dir_dk(d));
+        if (!lattice_inside(nf, qi, qj, qk)) continue;
+        const int64_t e = (int64_t)I.macro * F.nt + lattice_index(nf, qi, qj, qk);
+        fine.emplace(F.entry_to_unique[e], std::make_pair(e, d < 0 ? 1.0 : 0.5));
+      }
+    }
+    for (auto& kv : fine) {
+      ent.push_back(kv.second.first);
+      w.push_back(kv.second.second);
+    }
+    ptr[s + 1] = (int32_t)ent.size();
+  }
+  std::vector<float> w32(w.begin(), w.end());
+  upload(C.d_rptr_p, ptr);
+  upload(C.d_rent_p, ent);
+  upload(C.d_rw64_p, w);
+  upload(C.d_rw32_p, w32);
+  C.rlist_p = true;
+}
+
+template <typename T>
+const T* rw_p(LevelHost& L);
+template <>
+const double* rw_p<double>(LevelHost& L) {
+  return L.d_rw64_p.as<double>();
+}
+template <>
+const float* rw_p<float>(LevelHost& L) {
+  return L.d_rw32_p.as<float>();
+}
+
+// (velocity, pressure) restriction of a saddle residual from level lf to lf - 1
+template <typename T>
+void stokes_restrict(hhg_ctx* c, int lf, const T* rf, T* rc) {
+  LevelHost& F = c->lv(lf);
+  LevelHost& C = c->lv(lf - 1);
+  restrict_op<T>(c, lf, rf, rc);
+  CK(launch_restrict<T>(F.dev, C.dev, C.d_rptr_p.as<int32_t>(), C.d_rent_p.as<int64_t>(), rw_p<T>(C),
+                        rf + 3 * F.entries, rc + 3 * C.entries, c->stream, 1, 0));
+}
+
+template <typename T>
+DevMem& scinv(LevelHost& L);
+template <>
+DevMem& scinv<double>(LevelHost& L) {
+  return L.d_scinv64;
+}
+template <>
+DevMem& scinv<float>(LevelHost& L) {
+  return L.d_scinv32;
+}
+template <typename T>
+DevMem& suvec(LevelHost& L);
+template <>
+DevMem& suvec<double>(LevelHost& L) {
+  return L.su64;
+}
+template <>
+DevMem& suvec<float>(LevelHost& L) {
+  return L.su32;
+}
+
+// Dense inverse of the coarsest saddle matrix on its free velocity DoFs and all pressure
+// DoFs, with beta u u^T added to the pressure block (u = normalised constant pressure,
+// the kernel of the matrix): for a right-hand side orthogonal to that kernel the
+// shifted system has the zero-mean solution of the singular one.
+void stokes_coarse_setup(hhg_ctx* c) {
+  const int l = c->level_min;
+  LevelHost& L = c->lv(l);
+  ensure_swork<double>(c, l);
+  const int64_t U = L.nunique;
+  std::vector<int64_t> dof;
+  for (int64_t u = 0; u < U; ++u)
+    if (!L.unique_dir[u])
+      for (int q = 0; q < 3; ++q) dof.push_back(q * U + u);
+  const int nvel = (int)dof.size();
+  for (int64_t u = 0; u < U; ++u) dof.push_back(3 * U + u);
+  const int N = (int)dof.size();
+  if (N > MAX_COARSE_DOFS) THROW(HHG_ERR_UNSUPPORTED, "coarse saddle system too large (%d DoFs)", N);
+  for (DevMem* d : {&L.su64, &L.su32})
+    if (!d->p) CK(d->alloc(2 * 4 * (size_t)U * (d == &L.su64 ? sizeof(double) : sizeof(float))));
+  double* u = L.su64.as<double>();
+  DevMem* W = swork<double>(L);
+  std::vector<double> A((size_t)N * N), col(4 * U);
+  const double one = 1.0;
+  for (int j = 0; j < N; ++j) {
+    CK(cudaMemsetAsync(u, 0, 4 * U * sizeof(double), c->stream));
+    CK(cudaMemcpyAsync(u + dof[j], &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(launch_gather<double>(L.entries, 4, U, L.entries, L.d_e2u.as<int64_t>(), u, W[0].as<double>(), c->stream));
+    stokes_sweep<double>(c, l, OP_APPLY, nullptr, W[0].as<double>(), W[1].as<double>(), false);
+    CK(launch_gather<double>(U, 4, L.entries, U, L.d_first.as<int64_t>(), W[1].as<double>(), u, c->stream));
+    CK(cudaMemcpyAsync(col.data(), u, col.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    wait_stream(c);
+    for (int i = 0; i < N; ++i) A[(size_t)i * N + j] = col[dof[i]];
+  }
+  double beta = 0.0;
+  for (double v : A) beta = std::max(beta, std::fabs(v));
+  const int np = N - nvel;
+  for (int i = nvel; i < N; ++i)
+    for (int j = nvel; j < N; ++j) A[(size_t)i * N + j] += beta / np;
+  invert_dense(A, N);
+  std::vector<float> A32(A.begin(), A.end());
+  upload(L.d_scdof, dof);
+  upload(L.d_scinv64, A);
+  upload(L.d_scinv32, A32);
+  L.nscdof = N;
+  CK(cudaMemsetAsync(W[0].p, 0, W[0].bytes, c->stream));
+  CK(cudaMemsetAsync(W[1].p, 0, W[1].bytes, c->stream));
+}
+
+template <typename T>
+void stokes_coarse_solve(hhg_ctx* c, int l, const T* f, T* x) {
+  LevelHost& L = c->lv(l);
+  if (L.nscdof <= 0) THROW(HHG_ERR_STATE, "coarse saddle inverse missing (call hhg_mg_setup)");
+  const int64_t U = L.nunique;
+  T* us = suvec<T>(L).template as<T>();
+  T* ud = us + 4 * U;
+  CK(launch_gather<T>(U, 4, L.entries, U, L.d_first.as<int64_t>(), f, us, c->stream));
+  CK(cudaMemsetAsync(ud, 0, 4 * U * sizeof(T), c->stream));
+  CK(launch_dense_matvec<T>(L.nscdof, scinv<T>(L).template as<T>(), L.d_scdof.as<int64_t>(), us, ud, c->stream));
+  CK(launch_gather<T>(L.entries, 4, U, L.entries, L.d_e2u.as<int64_t>(), ud, x, c->stream));
+}
+
+// One inexact Uzawa step on K (u, p) = (f, g): velocity smoothing of A du = f - A u - B^T p
+// (pressure fixed), u += du, then p -= omega S^-1 (g - B u - C p) with the diagonal Schur
+// surrogate S = m / mu + (-C)_ii.
+template <typename T>
+void uzawa_step(hhg_ctx* c, int l, const T* f, T* x) {
+  LevelHost& L = c->lv(l);
+  const int64_t E = L.entries;
+  DevMem* Z = uzwork<T>(L);
+  T* r = Z[0].as<T>();
+  T* du = Z[1].as<T>();
+  stokes_sweep<T>(c, l, OP_RESID, f, x, r, false);
+  CK(cudaMemsetAsync(du, 0, 3 * E * sizeof(T), c->stream));
+  smooth<T>(c, l, c->mg.uzawa_vsteps, r, du);
+  CK(launch_axpby<T>(3 * E, (T)1, du, (T)1, x, c->stream));
+  stokes_sweep<T>(c, l, OP_RESID, f, x, r, false);
+  T* dp = du + 3 * E;
+  schur_apply<T>(c, l, r + 3 * E, dp);
+  CK(launch_axpby<T>(E, (T)(-c->mg.uzawa_omega), dp, (T)1, x + 3 * E, c->stream));
+}
+
+// Variable V-cycle: uzawa_pre / uzawa_post steps on the finest level, uzawa_extra more on
+// every coarser one; exact solve on the coarsest.  Work vectors of a level: [0], [1]
+// scratch of its Uzawa steps, [2] and [3] its right-hand side and iterate when it is the
+// coarse level of the cycle.
+template <typename T>
+void uzawa_vcycle(hhg_ctx* c, int l, const T* f, T* x) {
+  if (l == c->level_min) {
+    stokes_coarse_solve<T>(c, l, f, x);
+    return;
+  }
+  ensure_uzwork<T>(c, l);
+  ensure_uzwork<T>(c, l - 1);
+  ensure_work<T>(c, l);
+  build_pressure_restriction(c, l - 1);
+  LevelHost& L = c->lv(l);
+  LevelHost& C = c->lv(l - 1);
+  DevMem* Z = uzwork<T>(L);
+  DevMem* Zc = uzwork<T>(C);
+  const int extra = c->mg.uzawa_extra * (c->level_max - l);
+  for (int s = 0; s < c->mg.uzawa_pre + extra; ++s) uzawa_step<T>(c, l, f, x);
+  T* r = Z[0].as<T>();
+  T* fc = Zc[2].as<T>();
+  T* xc = Zc[3].as<T>();
+  stokes_sweep<T>(c, l, OP_RESID, f, x, r, false);
+  stokes_restrict<T>(c, l, r, fc);
+  CK(cudaMemsetAsync(xc, 0, 4 * C.entries * sizeof(T), c->stream));
+  uzawa_vcycle<T>(c, l - 1, fc, xc);
+  CK(launch_prolong_add<T>(L.dev, C.dev, xc, x, c->stream, 3));
+  CK(launch_prolong_add<T>(L.dev, C.dev, xc + 3 * C.entries, x + 3 * L.entries, c->stream, 1));
+  for (int s = 0; s < c->mg.uzawa_post + extra; ++s) uzawa_step<T>(c, l, f, x);
+}
+
+// Stationary Uzawa V-cycles on K x = f until |f - K x| <= rtol |f - K x0|.
+template <typename T>
+MinresResult uzawa_solve(hhg_ctx* c, int l, const T* f, T* x, double rtol, int max_iter) {
+  ensure_uzwork<T>(c, l);
+  T* r = uzwork<T>(c->lv(l))[0].template as<T>();  // free between cycles
+  MinresResult res;
+  const double r0 = stokes_sweep<T>(c, l, OP_RESID, f, x, r, true);
+  res.r0 = std::sqrt(r0);
+  if (!std::isfinite(r0)) THROW(HHG_ERR_NUMERIC, "non-finite initial residual");
+  double rr = r0;
+  for (int it = 1; it <= max_iter && r0 > 0.0; ++it) {
+    uzawa_vcycle<T>(c, l, f, x);
+    rr = stokes_sweep<T>(c, l, OP_RESID, f, x, r, true);
+    res.iterations = it;
+    if (!std::isfinite(rr)) THROW(HHG_ERR_NUMERIC, "non-finite residual");
+    if (std::sqrt(rr / r0) <= rtol) break;
+  }
+  res.rel = r0 > 0.0 ? std::sqrt(rr / r0) : 0.0;
+  res.converged = res.rel <= rtol;
+  return res;
 }
 
 // ------------------------------------------------------------------- Carreau (Sec. 3, 5.2.2)
@@ -737,6 +995,9 @@ hhg_status hhg_set_mg_params(hhg_ctx* c, const hhg_mg_params* p) {
     if (!(p->cheby_lo > 0.0 && p->cheby_hi > p->cheby_lo)) THROW(HHG_ERR_ARG, "Chebyshev interval");
     if (p->power_iters < 1) THROW(HHG_ERR_ARG, "power_iters");
     if (p->coarse_coeff < HHG_COARSE_INJECT || p->coarse_coeff > HHG_COARSE_HARMONIC) THROW(HHG_ERR_ARG, "coarse_coeff");
+    if (p->uzawa_pre < 0 || p->uzawa_post < 0 || p->uzawa_pre + p->uzawa_post == 0 || p->uzawa_extra < 0 ||
+        p->uzawa_vsteps < 1 || !(p->uzawa_omega > 0.0 && p->uzawa_omega < 2.0))
+      THROW(HHG_ERR_ARG, "Uzawa parameters");
     c->mg = *p;
   });
 }
@@ -769,6 +1030,7 @@ hhg_status hhg_mg_setup(hhg_ctx* c) {
       }
     }
     coarse_setup(c);
+    if (c->prob.kind == HHG_STOKES) stokes_coarse_setup(c);
     wait_stream(c);
     c->mg_ready = true;
   });
@@ -1079,6 +1341,50 @@ hhg_status hhg_solve(hhg_ctx* c, const hhg_solve_opts* o, const void* f, void* x
         CK(launch_convert<double, float>(n, r64, r32, c->stream));
         CK(cudaMemsetAsync(e32, 0, n * sizeof(float), c->stream));
         MinresResult mr = minres<float>(c, l, r32, e32, o->inner_rtol, o->inner_max_iter);
+        R.inner_iterations += mr.iterations;
+        CK(launch_add_f32_to_f64(n, e32, (double*)x, c->stream));
+        rr = stokes_sweep<double>(c, l, OP_RESID, (const double*)f, (const double*)x, r64, true);
+        R.iterations = it;
+        if (!std::isfinite(rr)) THROW(HHG_ERR_NUMERIC, "non-finite residual");
+      }
+      project_pressure<double>(c, l, (double*)x);
+      R.rel_residual = r0 > 0.0 ? std::sqrt(rr / r0) : 0.0;
+      R.converged = R.rel_residual <= o->rtol;
+    } else if (o->method == HHG_SOLVE_STOKES_UZAWA) {
+      need_stokes(c);
+      auto run = [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        MinresResult mr = uzawa_solve<T>(c, l, (const T*)f, (T*)x, o->rtol, o->max_iter);
+        project_pressure<T>(c, l, (T*)x);
+        R.iterations = mr.iterations;
+        R.residual0 = mr.r0;
+        R.rel_residual = mr.rel;
+        R.converged = mr.converged;
+      };
+      if (o->dt == HHG_F64)
+        run((double*)nullptr);
+      else if (o->dt == HHG_F32)
+        run((float*)nullptr);
+      else
+        THROW(HHG_ERR_ARG, "dtype");
+    } else if (o->method == HHG_SOLVE_STOKES_IR_UZAWA) {
+      need_stokes(c);
+      if (o->dt != HHG_F64) THROW(HHG_ERR_ARG, "iterative refinement needs FP64 f and x");
+      if (!(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || o->inner_max_iter < 1) THROW(HHG_ERR_ARG, "inner tol");
+      ensure_swork<double>(c, l);
+      ensure_swork<float>(c, l);
+      LevelHost& L = c->lv(l);
+      const int64_t n = 4 * L.entries;
+      double* r64 = swork<double>(L)[8].as<double>();
+      float* r32 = swork<float>(L)[8].as<float>();
+      float* e32 = swork<float>(L)[9].as<float>();
+      const double r0 = stokes_sweep<double>(c, l, OP_RESID, (const double*)f, (const double*)x, r64, true);
+      R.residual0 = std::sqrt(r0);
+      double rr = r0;
+      for (int it = 1; it <= o->max_iter && r0 > 0.0 && std::sqrt(rr / r0) > o->rtol; ++it) {
+        CK(launch_convert<double, float>(n, r64, r32, c->stream));
+        CK(cudaMemsetAsync(e32, 0, n * sizeof(float), c->stream));
+        MinresResult mr = uzawa_solve<float>(c, l, r32, e32, o->inner_rtol, o->inner_max_iter);
         R.inner_iterations += mr.iterations;
         CK(launch_add_f32_to_f64(n, e32, (double*)x, c->stream));
         rr = stokes_sweep<double>(c, l, OP_RESID, (const double*)f, (const double*)x, r64, true);

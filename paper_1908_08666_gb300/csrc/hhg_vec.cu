@@ -56,7 +56,8 @@ __global__ void k_dot(const uint8_t* __restrict__ mask, int64_t E, int comps, co
 
 // fine point (i, j, k) of macro `m` of the fine level; adds P e_c
 template <typename T>
-__global__ void k_prolong_add(const LevelDev Lf, const LevelDev Lc, const T* __restrict__ ec, T* __restrict__ ef) {
+__global__ void k_prolong_add(const LevelDev Lf, const LevelDev Lc, const T* __restrict__ ec, T* __restrict__ ef,
+                              int comps) {
   const int m = blockIdx.y;
   const int32_t tile = Lf.tiles_all[blockIdx.x];
   const int k = tile >> 20;
@@ -70,12 +71,12 @@ __global__ void k_prolong_add(const LevelDev Lf, const LevelDev Lc, const T* __r
   const int64_t cb = (int64_t)m * Lc.nt;
   if (!(pX | pY | pZ)) {
     const int64_t c = cb + lattice_index(nc, i >> 1, j >> 1, k >> 1);
-    for (int q = 0; q < 3; ++q) ef[ef0 + q * Lf.entries] += ec[c + q * Lc.entries];
+    for (int q = 0; q < comps; ++q) ef[ef0 + q * Lf.entries] += ec[c + q * Lc.entries];
   } else {
     const int di = pX - pY, dj = pY - pZ, dk = pZ;
     const int64_t ca = cb + lattice_index(nc, (i - di) >> 1, (j - dj) >> 1, (k - dk) >> 1);
     const int64_t cc = cb + lattice_index(nc, (i + di) >> 1, (j + dj) >> 1, (k + dk) >> 1);
-    for (int q = 0; q < 3; ++q)
+    for (int q = 0; q < comps; ++q)
       ef[ef0 + q * Lf.entries] += (T)0.5 * (ec[ca + q * Lc.entries] + ec[cc + q * Lc.entries]);
   }
 }
@@ -83,7 +84,7 @@ __global__ void k_prolong_add(const LevelDev Lf, const LevelDev Lc, const T* __r
 // coarse macro-interior points: rc(p) = rf(2p) + 1/2 sum_d rf(2p + d)
 template <typename T>
 __global__ void k_restrict_interior(const LevelDev Lf, const LevelDev Lc, const T* __restrict__ rf,
-                                    T* __restrict__ rc) {
+                                    T* __restrict__ rc, int comps) {
   const int m = blockIdx.y;
   const int32_t tile = Lc.tiles_int[blockIdx.x];
   const int k = tile >> 20;
@@ -94,7 +95,7 @@ __global__ void k_restrict_interior(const LevelDev Lf, const LevelDev Lc, const 
   const int64_t fb = (int64_t)m * Lf.nt;
   const int64_t c = (int64_t)m * Lc.nt + lattice_index(nc, i, j, k);
   const int64_t f0 = fb + lattice_index(n, 2 * i, 2 * j, 2 * k);
-  for (int q = 0; q < 3; ++q) {
+  for (int q = 0; q < comps; ++q) {
     const T* r = rf + q * Lf.entries;
     T s = 0;
 #pragma unroll
@@ -107,21 +108,21 @@ __global__ void k_restrict_interior(const LevelDev Lf, const LevelDev Lc, const 
 template <typename T>
 __global__ void k_restrict_skeleton(const LevelDev Lc, const int32_t* __restrict__ rptr,
                                     const int64_t* __restrict__ rent, const T* __restrict__ rw, int64_t Ef,
-                                    const T* __restrict__ rf, T* __restrict__ rc) {
+                                    const T* __restrict__ rf, T* __restrict__ rc, int comps, int use_dir) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= Lc.nskel) return;
   T acc[3] = {0, 0, 0};
-  if (!Lc.skel_dir[s]) {
+  if (!(use_dir && Lc.skel_dir[s])) {
     for (int q = rptr[s]; q < rptr[s + 1]; ++q) {
       const int64_t e = rent[q];
       const T w = rw[q];
-      for (int c = 0; c < 3; ++c) acc[c] += w * rf[e + c * Ef];
+      for (int c = 0; c < comps; ++c) acc[c] += w * rf[e + c * Ef];
     }
   }
   for (int q = Lc.skel_ptr[s]; q < Lc.skel_ptr[s + 1]; ++q) {
     const SkelInc I = Lc.skel_inc[q];
     const int64_t e = (int64_t)I.macro * Lc.nt + lattice_index(Lc.n, I.i, I.j, I.k);
-    for (int c = 0; c < 3; ++c) rc[e + c * Lc.entries] = acc[c];
+    for (int c = 0; c < comps; ++c) rc[e + c * Lc.entries] = acc[c];
   }
 }
 
@@ -171,6 +172,13 @@ __global__ void k_inject(const LevelDev Lf, const LevelDev Lc, const T* __restri
   if (i + j + k > Lc.n) return;
   kc[(int64_t)m * Lc.nt + lattice_index(Lc.n, i, j, k)] =
       kf[(int64_t)m * Lf.nt + lattice_index(Lf.n, 2 * i, 2 * j, 2 * k)];
+}
+
+template <typename T>
+__global__ void k_schur_diag(int64_t n, const T* __restrict__ r, const T* __restrict__ mu, const T* __restrict__ m,
+                             const T* __restrict__ sd, T* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = r[e] / (m[e] / mu[e] + sd[e]);
 }
 
 template <typename T>
@@ -458,23 +466,35 @@ int launch_add_const(int64_t n, T v, T* dst, void* stream) {
 }
 
 template <typename T>
-int launch_prolong_add(const LevelDev& Lf, const LevelDev& Lc, const T* ec, T* ef, void* stream) {
+int launch_prolong_add(const LevelDev& Lf, const LevelDev& Lc, const T* ec, T* ef, void* stream, int comps) {
   dim3 grid(Lf.ntiles_all, Lf.nmacro);
-  k_prolong_add<T><<<grid, dim3(TILE_I, TILE_J), 0, (cudaStream_t)stream>>>(Lf, Lc, ec, ef);
+  k_prolong_add<T><<<grid, dim3(TILE_I, TILE_J), 0, (cudaStream_t)stream>>>(Lf, Lc, ec, ef, comps);
   return (int)cudaGetLastError();
 }
 
 template <typename T>
 int launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const int32_t* rptr, const int64_t* rent, const T* rw,
-                    const T* rf, T* rc, void* stream) {
+                    const T* rf, T* rc, void* stream, int comps, int use_dir) {
   cudaStream_t s = (cudaStream_t)stream;
   if (Lc.ntiles_int > 0) {
     dim3 grid(Lc.ntiles_int, Lc.nmacro);
-    k_restrict_interior<T><<<grid, dim3(TILE_I, TILE_J), 0, s>>>(Lf, Lc, rf, rc);
+    k_restrict_interior<T><<<grid, dim3(TILE_I, TILE_J), 0, s>>>(Lf, Lc, rf, rc, comps);
   }
-  if (Lc.nskel > 0) k_restrict_skeleton<T><<<(Lc.nskel + 127) / 128, 128, 0, s>>>(Lc, rptr, rent, rw, Lf.entries, rf, rc);
+  if (Lc.nskel > 0)
+    k_restrict_skeleton<T><<<(Lc.nskel + 127) / 128, 128, 0, s>>>(Lc, rptr, rent, rw, Lf.entries, rf, rc, comps,
+                                                                  use_dir);
   return (int)cudaGetLastError();
 }
+
+template <typename T>
+int launch_schur_diag(int64_t n, const T* r, const T* mu, const T* m, const T* sd, T* out, void* stream) {
+  k_schur_diag<T><<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, (cudaStream_t)stream>>>(n, r, mu, m,
+                                                                                                        sd, out);
+  return (int)cudaGetLastError();
+}
+template int launch_schur_diag<float>(int64_t, const float*, const float*, const float*, const float*, float*, void*);
+template int launch_schur_diag<double>(int64_t, const double*, const double*, const double*, const double*, double*,
+                                       void*);
 
 int launch_bf16_to_f64(int64_t n, const uint16_t* src, double* dst, void* stream) {
   k_bf16_to_f64<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, (cudaStream_t)stream>>>(n, src, dst);
@@ -558,9 +578,9 @@ int launch_dense_matvec(int N, const T* A, const int64_t* idx, const T* src_u, T
 
 #define HHG_INST(T)                                                                                              \
   template int launch_dot<T>(const LevelDev&, int, const T*, const T*, double*, int64_t*, void*);               \
-  template int launch_prolong_add<T>(const LevelDev&, const LevelDev&, const T*, T*, void*);                     \
+  template int launch_prolong_add<T>(const LevelDev&, const LevelDev&, const T*, T*, void*, int);                     \
   template int launch_restrict<T>(const LevelDev&, const LevelDev&, const int32_t*, const int64_t*, const T*,   \
-                                  const T*, T*, void*);                                                          \
+                                  const T*, T*, void*, int, int);                                                \
   template int launch_inject<T>(const LevelDev&, const LevelDev&, const T*, T*, void*);                          \
   template int launch_axpby<T>(int64_t, T, const T*, T, T*, void*);                                              \
   template int launch_gather<T>(int64_t, int, int64_t, int64_t, const int64_t*, const T*, T*, void*);            \

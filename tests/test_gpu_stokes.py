@@ -83,7 +83,8 @@ def _direct(mm, lv, Kbc, f):
     return sol[:-1]
 
 
-@pytest.mark.parametrize("method", [B.SOLVE_STOKES_MINRES, B.SOLVE_STOKES_IR_MINRES])
+@pytest.mark.parametrize("method", [B.SOLVE_STOKES_MINRES, B.SOLVE_STOKES_IR_MINRES, B.SOLVE_STOKES_UZAWA,
+                                    B.SOLVE_STOKES_IR_UZAWA])
 def test_stokes_minres_solve(method):
     level = 4
     mm, lv, Kbc, K, ctx, perm = _setup(hi.kuhn_cube, level)
