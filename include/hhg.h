@@ -79,7 +79,10 @@ typedef enum { HHG_ELASTICITY = 0, HHG_STOKES = 1 } hhg_problem_kind;
 
 /* Sec. 2: physical scaling (Lemma 2.1), unphysical scaling (eq.
  * stencilscalingwithoutcorr, R = 0), or nodal integration everywhere
- * (eq. nodalintegration). */
+ * (eq. nodalintegration; elasticity only): the paper's comparison method, whose
+ * macro-interior rows sum kbar^t times the element stiffness over the 24 elements
+ * around each node on the fly (skeleton rows are a_h rows in every variant's
+ * practical interface rule; hhg_residual_noalloc rejects this variant). */
 typedef enum { HHG_PHYSICAL = 0, HHG_UNPHYSICAL = 1, HHG_NODAL = 2 } hhg_variant;
 
 /* khat: patch mean (eq. patchmean) or edge mean (k_i + k_j)/2 (Remark after Sec. 2.2). */

@@ -138,6 +138,8 @@ struct LevelHost {
   DevMem d_k16;  // BF16 bits of the coefficient (BF16 coefficient mode)
   std::vector<MacroStencil<double>> st64;
   std::vector<MacroStencil<float>> st32;
+  std::vector<NodalConsts<double>> nc64;  // element stiffness per macro (NODAL variant)
+  std::vector<NodalConsts<float>> nc32;
   LevelDev dev{};
   // multigrid / solver state (hhg_mg_setup and the solvers)
   DevMem d_udir;                    // int8 Dirichlet flag per unique node
@@ -357,6 +359,16 @@ inline const MacroStencil<float>* stencils<float>(LevelHost& L) {
   return L.st32.data();
 }
 template <typename T>
+const NodalConsts<T>* nodal_consts(LevelHost& L);
+template <>
+inline const NodalConsts<double>* nodal_consts<double>(LevelHost& L) {
+  return L.nc64.data();
+}
+template <>
+inline const NodalConsts<float>* nodal_consts<float>(LevelHost& L) {
+  return L.nc32.data();
+}
+template <typename T>
 const MacroConsts<T>* consts_dev(LevelHost& L);
 template <>
 inline const MacroConsts<double>* consts_dev<double>(LevelHost& L) {
@@ -395,7 +407,8 @@ void sweep(hhg_ctx* c, int level, OpKind op, SweepArgs<T> a, double* norm2) {
   int64_t used = 0;
   for (int m = 0; m < L.dev.nmacro; ++m) {
     int64_t cnt = 0;
-    CK(launch_sweep_macro<T>(L.dev, stencils<T>(L), m, op, c->flags, a, m % 2 ? c->aux[1] : c->stream, used, &cnt));
+    CK(launch_sweep_macro<T>(L.dev, stencils<T>(L), nodal_consts<T>(L), m, op, c->flags, a,
+                             m % 2 ? c->aux[1] : c->stream, used, &cnt));
     used += cnt;
   }
   if (c->prof) {

@@ -792,8 +792,10 @@ hhg_status hhg_set_problem(hhg_ctx* c, const hhg_problem* p) {
     } else {
       THROW(HHG_ERR_ARG, "unknown problem kind");
     }
-    if (p->variant == HHG_NODAL) THROW(HHG_ERR_UNSUPPORTED, "nodal-integration interior kernel not built");
-    if (p->variant != HHG_PHYSICAL && p->variant != HHG_UNPHYSICAL) THROW(HHG_ERR_ARG, "bad variant");
+    if (p->variant != HHG_PHYSICAL && p->variant != HHG_UNPHYSICAL && p->variant != HHG_NODAL)
+      THROW(HHG_ERR_ARG, "bad variant");
+    if (p->variant == HHG_NODAL && p->kind != HHG_ELASTICITY)
+      THROW(HHG_ERR_UNSUPPORTED, "the nodal-integration variant is built for elasticity");
     if (p->khat != HHG_KHAT_PATCH && p->khat != HHG_KHAT_EDGE) THROW(HHG_ERR_ARG, "bad khat");
     if (p->iface != HHG_IFACE_SYMMETRIC && p->iface != HHG_IFACE_PRACTICAL) THROW(HHG_ERR_ARG, "bad iface");
     for (int l = c->level_min; l <= c->level_max; ++l) {
@@ -803,6 +805,8 @@ hhg_status hhg_set_problem(hhg_ctx* c, const hhg_problem* p) {
       std::vector<MacroConsts<float>> mc32(M);
       L.st64.resize(M);
       L.st32.resize(M);
+      L.nc64.resize(M);
+      L.nc32.resize(M);
       for (int m = 0; m < M; ++m) {
         MacroGeom G;
         for (int q = 0; q < 4; ++q) G.v[q] = c->xyz[c->tets[m][q]];
@@ -811,6 +815,8 @@ hhg_status hhg_set_problem(hhg_ctx* c, const hhg_problem* p) {
         mc32[m] = cast_consts<float>(mc64[m]);
         L.st64[m] = mc64[m].st;
         L.st32[m] = mc32[m].st;
+        std::memcpy(L.nc64[m].ke, mc64[m].ke, sizeof(L.nc64[m].ke));
+        std::memcpy(L.nc32[m].ke, mc32[m].ke, sizeof(L.nc32[m].ke));
       }
       upload(L.d_mc64, mc64);
       upload(L.d_mc32, mc32);
@@ -856,7 +862,9 @@ hhg_status hhg_set_problem(hhg_ctx* c, const hhg_problem* p) {
     c->prob = *p;
     c->flags.physical = p->variant == HHG_PHYSICAL ? 1 : 0;
     c->flags.khat_edge = p->khat == HHG_KHAT_EDGE ? 1 : 0;
-    c->flags.practical = p->iface == HHG_IFACE_PRACTICAL ? 1 : 0;
+    // the nodal variant is a_h on every row: skeleton rows by the a_h (practical) rule
+    c->flags.practical = (p->iface == HHG_IFACE_PRACTICAL || p->variant == HHG_NODAL) ? 1 : 0;
+    c->flags.nodal = p->variant == HHG_NODAL ? 1 : 0;
     c->have_problem = true;
   });
 }
@@ -1047,6 +1055,7 @@ hhg_status hhg_residual_noalloc(hhg_ctx* c, int level, hhg_dtype dt, const void*
     need_ready(c, true);
     if (!x || !r || !f || !norm2_host || x == r || f == r) THROW(HHG_ERR_ARG, "bad buffers");
     LevelHost& L = c->lv(level);
+    if (c->flags.nodal) THROW(HHG_ERR_UNSUPPORTED, "the no-alloc residual is built for the scaled-stencil variants");
     const int64_t need = noalloc_partials_needed(L.dev);
     if (need > NOALLOC_SLOTS)
       THROW(HHG_ERR_ARG, "level %d needs %lld partial sums; the no-alloc scratch holds %lld (use hhg_residual)", level,

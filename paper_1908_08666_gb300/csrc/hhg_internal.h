@@ -148,6 +148,13 @@ struct MacroStencil {
 // Element matrices for the Stokes blocks: bd[type][a][b][l] = -int phi_a d_l phi_b
 // (pressure test vertex a, velocity trial vertex b), lc[type][a][b] = -(h^2/12) int
 // grad phi_a . grad phi_b.
+// Element stiffness of one macro's 6 Kuhn element types for the nodal-integration
+// interior kernel (kernel parameter, 864 values): ke[type][a][b][3 m + l].
+template <typename T>
+struct NodalConsts {
+  T ke[6][4][4][9];
+};
+
 template <typename T>
 struct MacroConsts {
   MacroStencil<T> st;

@@ -13,6 +13,7 @@ struct OpFlags {
   int physical;   // 1: add the correction R (physical scaling); 0: unphysical
   int khat_edge;  // 1: khat = (k_i + k_j)/2; 0: patch mean
   int practical;  // 1: skeleton rows are the a_h rows; 0: symmetric interface rows
+  int nodal = 0;  // 1: macro-interior rows by nodal integration a_h (the NODAL variant)
 };
 
 // Arguments of one stencil sweep.  Vectors are component-major over the level
@@ -47,9 +48,11 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
 
 // The macro-interior launch of macro m alone (partial slots from partial_offset; *partial_count
 // returns the slots used).
+// nc_host: per-macro element stiffness, used when fl.nodal is set.
 template <typename T>
-int launch_sweep_macro(const LevelDev& L, const MacroStencil<T>* st_host, int m, OpKind op, const OpFlags& fl,
-                       const SweepArgs<T>& a, void* stream, int64_t partial_offset, int64_t* partial_count);
+int launch_sweep_macro(const LevelDev& L, const MacroStencil<T>* st_host, const NodalConsts<T>* nc_host, int m,
+                       OpKind op, const OpFlags& fl, const SweepArgs<T>& a, void* stream, int64_t partial_offset,
+                       int64_t* partial_count);
 
 // No-alloc residual (see hhg_residual_noalloc): static device scratch of
 // NOALLOC_SLOTS partial sums plus the result slot at index NOALLOC_SLOTS.

@@ -299,6 +299,85 @@ __global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, c
   if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
 }
 
+// Macro-interior rows by nodal integration (the NODAL variant, eq. nodalintegration):
+// (A x)_i = sum over the 24 elements t around i of kbar^t sum_{b != a} K^t_ab (x_b - x_i),
+// kbar^t the mean of the element's 4 nodal coefficients, K^t the element stiffness of the
+// element's Kuhn type (kernel parameter).  Each element vertex b is a stencil neighbour of
+// i; the unrolled loops make all element/vertex/direction indices compile-time constants.
+template <typename T, int OP>
+__global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior_nodal(const LevelDev L, const NodalConsts<T> nc,
+                                                                    const int macro, const SweepArgs<T> a) {
+  const int32_t tile = L.tiles_lin[blockIdx.x];
+  const int n = L.n;
+  const int k = tile >> 20;
+  const int M = n - 1 - k;
+  const int t = (tile & 0xFFFFF) + threadIdx.x;
+  double r2 = 0.0;
+  if (t < (M - 1) * M / 2) {
+    int j, i;
+    slice_decode(M, t, j, i);
+    const int64_t E = L.entries;
+    const int64_t base = (int64_t)macro * L.nt;
+    int nb[NDIR];
+    lattice_neighbours(n, i, j, k, nb);
+    const int c0 = lattice_index32(n, i, j, k);
+    const T* __restrict__ X = a.x + base;
+    const T* __restrict__ K = a.k + base;
+    const T x0 = X[c0], y0 = X[c0 + E], z0 = X[c0 + 2 * E], k0 = K[c0];
+    T kk[NDIR], dx[NDIR], dy[NDIR], dz[NDIR];
+#pragma unroll
+    for (int d = 0; d < NDIR; ++d) {
+      kk[d] = K[nb[d]];
+      dx[d] = X[nb[d]] - x0;
+      dy[d] = X[nb[d] + E] - y0;
+      dz[d] = X[nb[d] + 2 * E] - z0;
+    }
+    T ax = 0, ay = 0, az = 0, dgx = 0, dgy = 0, dgz = 0;
+#pragma unroll
+    for (int bit = 0; bit < 24; ++bit) {
+      const int p = bit >> 2, av = bit & 3;
+      int a0, a1, a2;
+      kuhn_perm(p, a0, a1, a2);
+      int PX[4], PY[4], PZ[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        PX[v] = (v >= 1 && a0 == 0) + (v >= 2 && a1 == 0) + (v >= 3 && a2 == 0);
+        PY[v] = (v >= 1 && a0 == 1) + (v >= 2 && a1 == 1) + (v >= 3 && a2 == 1);
+        PZ[v] = (v >= 1 && a0 == 2) + (v >= 2 && a1 == 2) + (v >= 3 && a2 == 2);
+      }
+      int dv[4];
+      T ks = k0;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int oX = PX[v] - PX[av], oY = PY[v] - PY[av], oZ = PZ[v] - PZ[av];
+        dv[v] = v == av ? -1 : dir_of_offset(oX - oY, oY - oZ, oZ);
+        if (v != av) ks += kk[dv[v]];
+      }
+      const T kb = (T)0.25 * ks;
+      T ex = 0, ey = 0, ez = 0;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        if (v == av) continue;
+        const T* Kt = nc.ke[p][av][v];
+        const int d = dv[v];
+        ex = fma(Kt[0], dx[d], fma(Kt[1], dy[d], fma(Kt[2], dz[d], ex)));
+        ey = fma(Kt[3], dx[d], fma(Kt[4], dy[d], fma(Kt[5], dz[d], ey)));
+        ez = fma(Kt[6], dx[d], fma(Kt[7], dy[d], fma(Kt[8], dz[d], ez)));
+        if (OP == OP_JACOBI || OP == OP_CHEBY || OP == OP_DIAG) {
+          dgx = fma(-kb, Kt[0], dgx);
+          dgy = fma(-kb, Kt[4], dgy);
+          dgz = fma(-kb, Kt[8], dgz);
+        }
+      }
+      ax = fma(kb, ex, ax);
+      ay = fma(kb, ey, ay);
+      az = fma(kb, ez, az);
+    }
+    epilogue<T, OP>(a, base + c0, E, ax, ay, az, dgx, dgy, dgz, x0, y0, z0, r2);
+  }
+  if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
+}
+
 // Kuhn coordinates of corner (i, j, k): X = i+j+k, Y = j+k, Z = k.
 __device__ __forceinline__ bool kuhn_inside(int n, int X, int Y, int Z) {
   return 0 <= Z && Z <= Y && Y <= X && X <= n;
@@ -855,14 +934,27 @@ void launch_interior(bool gen, const LevelDev& L, const MacroStencil<T>& st, int
 }
 
 template <typename T>
-int launch_sweep_macro(const LevelDev& L, const MacroStencil<T>* st_host, int m, OpKind op, const OpFlags& fl,
-                       const SweepArgs<T>& a, void* stream, int64_t partial_offset, int64_t* partial_count) {
+int launch_sweep_macro(const LevelDev& L, const MacroStencil<T>* st_host, const NodalConsts<T>* nc_host, int m,
+                       OpKind op, const OpFlags& fl, const SweepArgs<T>& a, void* stream, int64_t partial_offset,
+                       int64_t* partial_count) {
   if (partial_count) *partial_count = 0;
   if (L.ntiles_lin == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
   const bool gen = !(fl.physical == 1 && fl.khat_edge == 0);
   SweepArgs<T> am = a;
   if (a.partial) am.partial = a.partial + partial_offset;
+  if (fl.nodal) {
+    const dim3 g(L.ntiles_lin);
+    switch (op) {
+      case OP_APPLY: k_interior_nodal<T, OP_APPLY><<<g, INTERIOR_BLOCK, 0, s>>>(L, nc_host[m], m, am); break;
+      case OP_RESID: k_interior_nodal<T, OP_RESID><<<g, INTERIOR_BLOCK, 0, s>>>(L, nc_host[m], m, am); break;
+      case OP_JACOBI: k_interior_nodal<T, OP_JACOBI><<<g, INTERIOR_BLOCK, 0, s>>>(L, nc_host[m], m, am); break;
+      case OP_CHEBY: k_interior_nodal<T, OP_CHEBY><<<g, INTERIOR_BLOCK, 0, s>>>(L, nc_host[m], m, am); break;
+      case OP_DIAG: k_interior_nodal<T, OP_DIAG><<<g, INTERIOR_BLOCK, 0, s>>>(L, nc_host[m], m, am); break;
+    }
+    if (partial_count) *partial_count = L.ntiles_lin;
+    return (int)cudaGetLastError();
+  }
   switch (op) {
     case OP_APPLY: launch_interior<T, OP_APPLY>(gen, L, st_host[m], m, fl, am, s); break;
     case OP_RESID: launch_interior<T, OP_RESID>(gen, L, st_host[m], m, fl, am, s); break;
@@ -1083,10 +1175,11 @@ int upload_direction_tables() {
   return (int)e;
 }
 
-template int launch_sweep_macro<float>(const LevelDev&, const MacroStencil<float>*, int, OpKind, const OpFlags&,
-                                       const SweepArgs<float>&, void*, int64_t, int64_t*);
-template int launch_sweep_macro<double>(const LevelDev&, const MacroStencil<double>*, int, OpKind, const OpFlags&,
-                                        const SweepArgs<double>&, void*, int64_t, int64_t*);
+template int launch_sweep_macro<float>(const LevelDev&, const MacroStencil<float>*, const NodalConsts<float>*, int,
+                                       OpKind, const OpFlags&, const SweepArgs<float>&, void*, int64_t, int64_t*);
+template int launch_sweep_macro<double>(const LevelDev&, const MacroStencil<double>*, const NodalConsts<double>*,
+                                        int, OpKind, const OpFlags&, const SweepArgs<double>&, void*, int64_t,
+                                        int64_t*);
 template int launch_sweep<float>(const LevelDev&, const MacroStencil<float>*, const MacroConsts<float>*, OpKind,
                                  const OpFlags&, const SweepArgs<float>&, void*, int, int64_t, int64_t*, void*, void*);
 template int launch_sweep<double>(const LevelDev&, const MacroStencil<double>*, const MacroConsts<double>*, OpKind,

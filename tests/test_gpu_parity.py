@@ -53,11 +53,13 @@ CASES = [
     ("cube_l4_unphysical", hi.kuhn_cube, 4, {"variant": "unphysical"}),
     ("cube_l4_khat_edge", hi.kuhn_cube, 4, {"khat": "edge"}),
     ("cube_l4_practical", hi.kuhn_cube, 4, {"iface": "practical"}),
+    ("cube_l4_nodal", hi.kuhn_cube, 4, {"variant": "nodal"}),
+    ("skewed_l4_nodal", hi.skewed_pair, 4, {"variant": "nodal"}),
     ("skewed_l4", hi.skewed_pair, 4, {}),
     ("cube2_l3", lambda: hi.kuhn_cube(2), 3, {}),
 ]
 
-_VAR = {"physical": B.PHYSICAL, "unphysical": B.UNPHYSICAL}
+_VAR = {"physical": B.PHYSICAL, "unphysical": B.UNPHYSICAL, "nodal": B.NODAL}
 _KH = {"patch": B.KHAT_PATCH, "edge": B.KHAT_EDGE}
 _IF = {"symmetric": B.IFACE_SYMMETRIC, "practical": B.IFACE_PRACTICAL}
 
