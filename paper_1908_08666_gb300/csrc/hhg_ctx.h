@@ -14,6 +14,7 @@
 #include <set>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <type_traits>
 #include <unordered_map>
 #include <vector>
@@ -224,10 +225,21 @@ struct hhg_ctx {
   // rows; all forked from and joined back into `stream` by events
   cudaStream_t aux[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join[4] = {nullptr, nullptr, nullptr, nullptr};
+  // CUDA graphs of "x = 0; one V-cycle for f" per (precision, level, f, x), replayed by
+  // the solvers; dropped whenever the multigrid data change (hhg_mg_setup and friends)
+  std::map<std::tuple<int, int, const void*, void*>, cudaGraphExec_t> vc_graphs;
+  cudaStream_t cap_stream = nullptr;  // capture stream (the caller's may be the legacy one)
+  bool graphs_ok = true;              // false after a failed capture: launch directly
+  void drop_graphs() {
+    for (auto& kv : vc_graphs) cudaGraphExecDestroy(kv.second);
+    vc_graphs.clear();
+  }
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::array<cudaEvent_t, 2>> prof_ev[2];
   int64_t prof_launches[2] = {0, 0};
   ~hhg_ctx() {
+    drop_graphs();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     if (pinned) cudaFreeHost(pinned);
     for (auto st : aux)
       if (st) cudaStreamDestroy(st);
@@ -288,13 +300,17 @@ inline void wait_stream(hhg_ctx* c) {
       cudaEventDestroy(ev);
       CK(e);
     }
-    const auto ms =
-        std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
-    if (ms > c->timeout_ms) {
+    const auto us =
+        std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+    if (us > 1000 * c->timeout_ms) {
       cudaEventDestroy(ev);
       THROW(HHG_ERR_TIMEOUT, "stream did not finish within %lld ms", (long long)c->timeout_ms);
     }
-    std::this_thread::sleep_for(std::chrono::microseconds(50));
+    // poll without sleeping for the first 2 ms (short solver waits), then every 50 us
+    if (us < 2000)
+      std::this_thread::yield();
+    else
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
   cudaEventDestroy(ev);
 }

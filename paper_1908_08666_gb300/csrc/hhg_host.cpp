@@ -779,6 +779,7 @@ hhg_status hhg_refine(hhg_ctx* c, int level_max) {
 
 hhg_status hhg_set_problem(hhg_ctx* c, const hhg_problem* p) {
   return guard(c, [&] {
+    c->drop_graphs();
     if (!p) THROW(HHG_ERR_ARG, "null problem");
     if (!c->have_mesh || c->level_max < 0) THROW(HHG_ERR_STATE, "refine first");
     double ce, cd;
@@ -940,6 +941,7 @@ hhg_status hhg_scatter_unique(hhg_ctx* c, int level, hhg_dtype dt, int comps, co
 
 hhg_status hhg_set_coefficient(hhg_ctx* c, const void* k, hhg_dtype dt) {
   return guard(c, [&] {
+    c->drop_graphs();
     if (!c->have_mesh || c->level_max < 0) THROW(HHG_ERR_STATE, "refine first");
     if (!k) THROW(HHG_ERR_ARG, "null coefficient");
     LevelHost& F = *c->levels[c->level_max];

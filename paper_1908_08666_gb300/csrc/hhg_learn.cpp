@@ -307,8 +307,7 @@ double precondition(hhg_ctx* c, int l, const float* r, float* z, float* az, bool
   const int64_t E = c->lv(l).entries, n = 3 * E;
   float* z0 = lwork(c, G, l, LW_Z0);
   float* az0 = lwork(c, G, l, LW_AZ0);
-  CK(cudaMemsetAsync(z0, 0, n * sizeof(float), c->stream));
-  vcycle32(c, l, r, z0);
+  vcycle_zero32(c, l, r, z0);
   apply32(c, l, z0, az0);
   if (!use_net) {
     copy32(c, l, z0, z);

@@ -323,12 +323,76 @@ void vcycle(hhg_ctx* c, int l, const T* f, T* x) {
   smooth<T>(c, l, c->mg.post, f, x);
 }
 
+// x = 0 followed by one V-cycle for f on level l.  The first call for a (precision,
+// level, f, x) runs the cycle directly (allocating its work vectors), the second captures
+// it as a CUDA graph on the context's capture stream, later calls replay the graph on the
+// context stream.  A failed capture disables graphs for the context (direct launches).
+template <typename T>
+void vcycle_zero(hhg_ctx* c, int l, const T* f, T* x) {
+  LevelHost& L = c->lv(l);
+  auto direct = [&] {
+    CK(cudaMemsetAsync(x, 0, 3 * L.entries * sizeof(T), c->stream));
+    vcycle<T>(c, l, f, x);
+  };
+  if (!c->graphs_ok || c->prof) {
+    direct();
+    return;
+  }
+  const auto key = std::make_tuple((int)sizeof(T), l, (const void*)f, (void*)x);
+  auto it = c->vc_graphs.find(key);
+  if (it != c->vc_graphs.end() && it->second) {
+    CK(cudaGraphLaunch(it->second, c->stream));
+    return;
+  }
+  if (it == c->vc_graphs.end()) {  // first use: run directly, so every work vector exists
+    c->vc_graphs[key] = nullptr;
+    direct();
+    return;
+  }
+  if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  // the capture stream starts after everything issued so far on the context stream
+  cudaEvent_t ev = c->take_event();
+  CK(cudaEventRecord(ev, c->stream));
+  CK(cudaStreamWaitEvent(c->cap_stream, ev, 0));
+  c->ev_pool.push_back(ev);
+  cudaStream_t user = c->stream;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    c->stream = c->cap_stream;
+    try {
+      CK(cudaMemsetAsync(x, 0, 3 * L.entries * sizeof(T), c->stream));
+      vcycle<T>(c, l, f, x);
+    } catch (...) {
+      c->stream = user;
+      cudaStreamEndCapture(c->cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      c->graphs_ok = false;
+      cudaGetLastError();
+      direct();
+      return;
+    }
+    c->stream = user;
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->graphs_ok = false;
+    direct();
+    return;
+  }
+  c->vc_graphs[key] = ge;
+  CK(cudaGraphLaunch(ge, c->stream));
+}
+
 template <typename T>
 void precondition(hhg_ctx* c, int l, bool mg, const T* r, T* z) {
   LevelHost& L = c->lv(l);
   if (mg) {
-    CK(cudaMemsetAsync(z, 0, 3 * L.entries * sizeof(T), c->stream));
-    vcycle<T>(c, l, r, z);
+    vcycle_zero<T>(c, l, r, z);
   } else {
     CK(launch_mul<T>(3 * L.entries, dinv<T>(L).template as<T>(), r, z, c->stream));
   }
@@ -495,8 +559,7 @@ void schur_apply(hhg_ctx* c, int l, const T* r, T* out) {
 template <typename T>
 void stokes_precond(hhg_ctx* c, int l, const T* r, T* z) {
   LevelHost& L = c->lv(l);
-  CK(cudaMemsetAsync(z, 0, 3 * L.entries * sizeof(T), c->stream));
-  vcycle<T>(c, l, r, z);
+  vcycle_zero<T>(c, l, r, z);
   schur_apply<T>(c, l, r + 3 * L.entries, z + 3 * L.entries);
 }
 
@@ -963,6 +1026,10 @@ void vcycle32(hhg_ctx* c, int l, const float* f, float* x) {
   ensure_work<float>(c, l);
   vcycle<float>(c, l, f, x);
 }
+void vcycle_zero32(hhg_ctx* c, int l, const float* f, float* x) {
+  ensure_work<float>(c, l);
+  vcycle_zero<float>(c, l, f, x);
+}
 const float* dinv32(hhg_ctx* c, int l) {
   LevelHost& L = c->lv(l);
   if (!L.dinv32.p) compute_diag<float>(c, l);
@@ -988,6 +1055,7 @@ extern "C" {
 
 hhg_status hhg_set_mg_params(hhg_ctx* c, const hhg_mg_params* p) {
   return guard(c, [&] {
+    c->drop_graphs();
     if (!p) THROW(HHG_ERR_ARG, "null params");
     if (p->smoother != HHG_SMOOTH_JACOBI && p->smoother != HHG_SMOOTH_CHEBYSHEV) THROW(HHG_ERR_ARG, "smoother");
     if (p->pre < 0 || p->post < 0 || p->pre + p->post == 0) THROW(HHG_ERR_ARG, "smoothing steps");
@@ -1004,6 +1072,7 @@ hhg_status hhg_set_mg_params(hhg_ctx* c, const hhg_mg_params* p) {
 
 hhg_status hhg_mg_setup(hhg_ctx* c) {
   return guard(c, [&] {
+    c->drop_graphs();
     need_ready(c, true);
     if (c->mg.coarse_coeff != HHG_COARSE_INJECT) {
       for (int l = c->level_max; l > c->level_min; --l) {
@@ -1047,6 +1116,7 @@ hhg_status hhg_get_lambda_max(hhg_ctx* c, int level, double* lambda) {
 
 hhg_status hhg_set_lambda_max(hhg_ctx* c, int level, double lambda) {
   return guard(c, [&] {
+    c->drop_graphs();
     LevelHost& L = c->lv(level);
     if (!(lambda > 0.0)) THROW(HHG_ERR_ARG, "lambda must be positive");
     L.lambda_max = lambda;

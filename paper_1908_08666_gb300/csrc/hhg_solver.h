@@ -15,6 +15,7 @@ void mg_ready_check(hhg_ctx* c);                                           // co
 void apply32(hhg_ctx* c, int l, const float* x, float* y);                // y = A x (FP32)
 double dot32(hhg_ctx* c, int l, const float* a, const float* b);          // over unique free DoFs (waits)
 void vcycle32(hhg_ctx* c, int l, const float* f, float* x);               // one V-cycle, x updated
+void vcycle_zero32(hhg_ctx* c, int l, const float* f, float* x);          // x = 0, one V-cycle (graph replay)
 const float* dinv32(hhg_ctx* c, int l);                                   // inverse point diagonal (3*E)
 double residual32(hhg_ctx* c, int l, const float* f, const float* x, float* r);   // returns |r|^2
 double residual64(hhg_ctx* c, int l, const double* f, const double* x, double* r);  // returns |r|^2
