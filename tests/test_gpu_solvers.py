@@ -109,6 +109,14 @@ def test_smoothers_and_vcycle(name, request):
         B.hhg_set_mg_params(h)
 
 
+@pytest.fixture(scope="module")
+def cube5():
+    p = Pair(hi.kuhn_cube, 5)
+    B.hhg_mg_setup(p.ctx.h)
+    yield p
+    p.close()
+
+
 @pytest.mark.parametrize("method,dt,rtol", [
     (B.SOLVE_PCG_JACOBI, B.F64, 1e-10),
     (B.SOLVE_MG_CG, B.F64, 1e-8),
@@ -116,34 +124,30 @@ def test_smoothers_and_vcycle(name, request):
     (B.SOLVE_MG, B.F64, 1e-8),
     (B.SOLVE_MG_CG, B.F32, 1e-5),
 ])
-def test_solvers_cube_level5(method, dt, rtol):
-    p = Pair(hi.kuhn_cube, 5)
-    try:
-        t = p.ctx.torch
-        h = p.ctx.h
-        B.hhg_mg_setup(h)
-        l = 5
-        lv, A = p.H.lv[l], p.H.A[l]
-        f = hi.node_noise(lv.coords, seed=31)
-        g = np.zeros_like(f)
-        g[lv.dirichlet] = hi.node_noise(lv.coords, seed=32)[lv.dirichlet] * 0.1  # non-zero Dirichlet data
-        tdt = t.float64 if dt == B.F64 else t.float32
-        x = p.to_lib(l, g, tdt)
-        rep = B.hhg_solve(h, p.to_lib(l, f, tdt), x, method=method, level=l, dt=dt, rtol=rtol, max_iter=500)
-        assert rep["converged"]
-        xs = p.from_lib(l, x)
-        assert np.array_equal(xs[lv.dirichlet], p.from_lib(l, p.to_lib(l, g, tdt))[lv.dirichlet])
-        r0 = np.linalg.norm(S.residual(A, lv.dirichlet, f, g))
-        r = np.linalg.norm(S.residual(A, lv.dirichlet, f, xs))
-        slack = 1.01 if dt == B.F64 else 20.0
-        assert r <= slack * rtol * r0, (r / r0, rep)
-        if method == B.SOLVE_IR_MG_CG:
-            assert rep["inner_iterations"] >= rep["iterations"] >= 1
-        if method == B.SOLVE_PCG_JACOBI:
-            xd = S.direct_solve(A, lv.dirichlet, f, g)
-            assert np.abs(xs - xd).max() <= 1e-6 * np.abs(xd).max()
-    finally:
-        p.close()
+def test_solvers_cube_level5(cube5, method, dt, rtol):
+    """Checked by the oracle's residual of the returned solution (the comparison with a
+    direct solve is the unit-tetrahedron test's: a sparse LU of the level-5 cube takes
+    minutes)."""
+    p = cube5
+    t = p.ctx.torch
+    h = p.ctx.h
+    l = 5
+    lv, A = p.H.lv[l], p.H.A[l]
+    f = hi.node_noise(lv.coords, seed=31)
+    g = np.zeros_like(f)
+    g[lv.dirichlet] = hi.node_noise(lv.coords, seed=32)[lv.dirichlet] * 0.1  # non-zero Dirichlet data
+    tdt = t.float64 if dt == B.F64 else t.float32
+    x = p.to_lib(l, g, tdt)
+    rep = B.hhg_solve(h, p.to_lib(l, f, tdt), x, method=method, level=l, dt=dt, rtol=rtol, max_iter=500)
+    assert rep["converged"]
+    xs = p.from_lib(l, x)
+    assert np.array_equal(xs[lv.dirichlet], p.from_lib(l, p.to_lib(l, g, tdt))[lv.dirichlet])
+    r0 = np.linalg.norm(S.residual(A, lv.dirichlet, f, g))
+    r = np.linalg.norm(S.residual(A, lv.dirichlet, f, xs))
+    slack = 1.01 if dt == B.F64 else 20.0
+    assert r <= slack * rtol * r0, (r / r0, rep)
+    if method == B.SOLVE_IR_MG_CG:
+        assert rep["inner_iterations"] >= rep["iterations"] >= 1
 
 
 def test_jacobi_pcg_unit_tet_level5():

@@ -83,28 +83,37 @@ def _direct(mm, lv, Kbc, f):
     return sol[:-1]
 
 
-@pytest.mark.parametrize("method", [B.SOLVE_STOKES_MINRES, B.SOLVE_STOKES_IR_MINRES, B.SOLVE_STOKES_UZAWA,
-                                    B.SOLVE_STOKES_IR_UZAWA])
-def test_stokes_minres_solve(method):
+@pytest.fixture(scope="module")
+def cube4_solve():
+    """Stokes level-4 cube: GPU context, oracle operator, right-hand side and the direct
+    solution (computed once for all solver methods)."""
     level = 4
     mm, lv, Kbc, K, ctx, perm = _setup(hi.kuhn_cube, level)
-    try:
-        t = ctx.torch
-        N = lv.num_nodes
-        fu = hi.node_noise(lv.coords, 9)
-        fu[lv.dirichlet] = 0.0
-        f_or = ST.pack(fu, np.zeros(N))
-        B.hhg_mg_setup(ctx.h)
-        f = ctx.to_lib(_to_u(perm, fu, np.zeros(N)), t.float64, 4)
-        x = t.zeros_like(f)
-        rep = B.hhg_solve(ctx.h, f, x, method=method, level=level, dt=B.F64, rtol=1e-8, max_iter=400,
-                          inner_rtol=1e-3, inner_max_iter=200)
-        xg = ctx.from_lib(x, 4)[perm]
-        x_g = ST.pack(xg[:, :3], xg[:, 3])
-        r = ST.residual(Kbc, lv.dirichlet, f_or, x_g)
-        assert np.linalg.norm(r) <= 2e-8 * np.linalg.norm(f_or), rep
-        xd = _direct(mm, lv, Kbc, f_or)
-        assert np.abs(x_g - xd).max() <= 1e-5 * np.abs(xd).max(), rep
-        assert abs((ST.lumped_mass(lv) * x_g[3 * N:]).sum()) <= 1e-10 * np.abs(x_g[3 * N:]).sum()
-    finally:
-        ctx.close()
+    N = lv.num_nodes
+    fu = hi.node_noise(lv.coords, 9)
+    fu[lv.dirichlet] = 0.0
+    f_or = ST.pack(fu, np.zeros(N))
+    B.hhg_mg_setup(ctx.h)
+    xd = _direct(mm, lv, Kbc, f_or)
+    yield dict(level=level, lv=lv, Kbc=Kbc, ctx=ctx, perm=perm, fu=fu, f_or=f_or, xd=xd)
+    ctx.close()
+
+
+@pytest.mark.parametrize("method", [B.SOLVE_STOKES_MINRES, B.SOLVE_STOKES_IR_MINRES, B.SOLVE_STOKES_UZAWA,
+                                    B.SOLVE_STOKES_IR_UZAWA])
+def test_stokes_minres_solve(cube4_solve, method):
+    d = cube4_solve
+    ctx, lv, perm, level = d["ctx"], d["lv"], d["perm"], d["level"]
+    t = ctx.torch
+    N = lv.num_nodes
+    f = ctx.to_lib(_to_u(perm, d["fu"], np.zeros(N)), t.float64, 4)
+    x = t.zeros_like(f)
+    rep = B.hhg_solve(ctx.h, f, x, method=method, level=level, dt=B.F64, rtol=1e-8, max_iter=400,
+                      inner_rtol=1e-3, inner_max_iter=200)
+    xg = ctx.from_lib(x, 4)[perm]
+    x_g = ST.pack(xg[:, :3], xg[:, 3])
+    r = ST.residual(d["Kbc"], lv.dirichlet, d["f_or"], x_g)
+    assert np.linalg.norm(r) <= 2e-8 * np.linalg.norm(d["f_or"]), rep
+    xd = d["xd"]
+    assert np.abs(x_g - xd).max() <= 1e-5 * np.abs(xd).max(), rep
+    assert abs((ST.lumped_mass(lv) * x_g[3 * N:]).sum()) <= 1e-10 * np.abs(x_g[3 * N:]).sum()
