@@ -395,6 +395,25 @@ inline const MacroConsts<float>* consts_dev<float>(LevelHost& L) {
   return L.d_mc32.as<MacroConsts<float>>();
 }
 
+// Fork the side streams from `stream` (they start after everything issued so far).
+inline void fork_side_streams(hhg_ctx* c) {
+  if (!c->aux[0]) {
+    for (auto& st : c->aux) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    for (auto& e : c->ev_join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  CK(cudaEventRecord(c->ev_fork, c->stream));
+  for (auto st : c->aux) CK(cudaStreamWaitEvent(st, c->ev_fork, 0));
+}
+
+// Join the side streams back into `stream`.
+inline void join_side_streams(hhg_ctx* c) {
+  for (int q = 0; q < 4; ++q) {
+    CK(cudaEventRecord(c->ev_join[q], c->aux[q]));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join[q], 0));
+  }
+}
+
 // One operator sweep on a level.  The macro-interior launches (one per macro) alternate
 // between `stream` and aux[1] so that the tail of one overlaps the next, and the skeleton
 // kernels run concurrently on aux[0] (they write disjoint entries and their own partial-sum

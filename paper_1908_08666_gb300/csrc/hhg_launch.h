@@ -68,9 +68,12 @@ int launch_residual_noalloc(const LevelDev& L, const MacroStencil<T>* st_host, c
 int upload_direction_tables();
 
 // Stokes saddle operator on (u, v, w, p) vectors (4 components): apply or residual
+// side (nullable): three side streams for the face-node chain, every second macro's
+// interior launch and the edge/vertex nodes (they write disjoint entries).
 template <typename T>
 int launch_stokes_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev, OpKind op,
-                        const OpFlags& fl, const SweepArgs<T>& a, void* stream, int64_t* partial_count);
+                        const OpFlags& fl, const SweepArgs<T>& a, void* stream, int64_t* partial_count,
+                        void* const* side = nullptr);
 
 // Carreau viscosity from the nodal least-squares strain rate (Sec. 3, eq. carreau):
 // interior nodes with the per-macro slope operator Q (grad u_c = sum_d Q[d] (u_c(i+d) - u_c(i))),

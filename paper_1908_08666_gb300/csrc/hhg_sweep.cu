@@ -1111,40 +1111,47 @@ template int launch_residual_noalloc<double>(const LevelDev&, const MacroStencil
 
 template <typename T>
 int launch_stokes_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev, OpKind op,
-                        const OpFlags& fl, const SweepArgs<T>& a, void* stream, int64_t* partial_count) {
+                        const OpFlags& fl, const SweepArgs<T>& a, void* stream, int64_t* partial_count,
+                        void* const* side) {
   if (op != OP_APPLY && op != OP_RESID) return (int)cudaErrorInvalidValue;
   cudaStream_t s = (cudaStream_t)stream;
+  // side streams (nullable): [0] face chain, [1] every second macro, [2] edge/vertex nodes
+  cudaStream_t s_face = side ? (cudaStream_t)side[0] : s;
+  cudaStream_t s_odd = side ? (cudaStream_t)side[1] : s;
+  cudaStream_t s_ev = side ? (cudaStream_t)side[2] : s;
   int64_t used = 0;
   const bool gen = !(fl.physical == 1 && fl.khat_edge == 0);
   for (int m = 0; m < L.nmacro && L.ntiles_lin > 0; ++m) {
     SweepArgs<T> am = a;
     if (a.partial) am.partial = a.partial + used;
+    cudaStream_t sm = m % 2 ? s_odd : s;
     if (op == OP_APPLY)
-      (gen ? k_interior<T, OP_APPLY, 1, 1> : k_interior<T, OP_APPLY, 0, 1>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(
+      (gen ? k_interior<T, OP_APPLY, 1, 1> : k_interior<T, OP_APPLY, 0, 1>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, sm>>>(
           L, st_host[m], m, fl, am);
     else
-      (gen ? k_interior<T, OP_RESID, 1, 1> : k_interior<T, OP_RESID, 0, 1>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(
+      (gen ? k_interior<T, OP_RESID, 1, 1> : k_interior<T, OP_RESID, 0, 1>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, sm>>>(
           L, st_host[m], m, fl, am);
     used += L.ntiles_lin;
   }
-  if (L.nface_items_all > 0) k_face_items_stk<T><<<(L.nface_items_all + 127) / 128, 128, 0, s>>>(L, mc_dev, fl, a.x, a.k);
+  if (L.nface_items_all > 0)
+    k_face_items_stk<T><<<(L.nface_items_all + 127) / 128, 128, 0, s_face>>>(L, mc_dev, fl, a.x, a.k);
   if (L.nface_nodes_all > 0) {
     const int nb = (L.nface_nodes_all + 127) / 128;
     SweepArgs<T> am = a;
     if (a.partial) am.partial = a.partial + used;
     if (op == OP_APPLY)
-      k_face_finalize_stk<T, OP_APPLY><<<nb, 128, 0, s>>>(L, am);
+      k_face_finalize_stk<T, OP_APPLY><<<nb, 128, 0, s_face>>>(L, am);
     else
-      k_face_finalize_stk<T, OP_RESID><<<nb, 128, 0, s>>>(L, am);
+      k_face_finalize_stk<T, OP_RESID><<<nb, 128, 0, s_face>>>(L, am);
     used += nb;
   }
   if (L.nev_all > 0) {
     SweepArgs<T> am = a;
     if (a.partial) am.partial = a.partial + used;
     if (op == OP_APPLY)
-      k_skeleton_ev_stk<T, OP_APPLY><<<L.nev_all, 128, 0, s>>>(L, mc_dev, fl, am);
+      k_skeleton_ev_stk<T, OP_APPLY><<<L.nev_all, 128, 0, s_ev>>>(L, mc_dev, fl, am);
     else
-      k_skeleton_ev_stk<T, OP_RESID><<<L.nev_all, 128, 0, s>>>(L, mc_dev, fl, am);
+      k_skeleton_ev_stk<T, OP_RESID><<<L.nev_all, 128, 0, s_ev>>>(L, mc_dev, fl, am);
     used += L.nev_all;
   }
   if (partial_count) *partial_count = used;
@@ -1152,9 +1159,10 @@ int launch_stokes_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const
 }
 
 template int launch_stokes_sweep<float>(const LevelDev&, const MacroStencil<float>*, const MacroConsts<float>*, OpKind,
-                                        const OpFlags&, const SweepArgs<float>&, void*, int64_t*);
+                                        const OpFlags&, const SweepArgs<float>&, void*, int64_t*, void* const*);
 template int launch_stokes_sweep<double>(const LevelDev&, const MacroStencil<double>*, const MacroConsts<double>*,
-                                         OpKind, const OpFlags&, const SweepArgs<double>&, void*, int64_t*);
+                                         OpKind, const OpFlags&, const SweepArgs<double>&, void*, int64_t*,
+                                         void* const*);
 
 // fills the direction / ring tables used with run-time indices
 int upload_direction_tables() {
