@@ -137,6 +137,7 @@ _SIGS = {
                              C.POINTER(C.c_double)],
     "hhg_learn_num_params": [],
     "hhg_learn_init": [C.c_void_p, C.c_uint64],
+    "hhg_learn_set_conv_kernel": [C.c_void_p, C.c_int],
     "hhg_learn_get_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "hhg_learn_set_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "hhg_learn_grid": [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int64)],
@@ -384,6 +385,11 @@ def hhg_picard(ctx, f, x, level, eta0=1.0, eta_inf=1e-3, kappa=1.0, r=-0.25, pic
 
 def hhg_learn_num_params():
     return int(load().hhg_learn_num_params())
+
+
+def hhg_learn_set_conv_kernel(ctx, kernel):
+    """0: warp-level MMA convolution (default), 1: tcgen05 tensor-memory convolution."""
+    _check(ctx, load().hhg_learn_set_conv_kernel(ctx, int(kernel)))
 
 
 def hhg_learn_init(ctx, seed=0):

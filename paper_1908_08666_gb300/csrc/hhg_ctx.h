@@ -169,6 +169,8 @@ struct LearnState {
   bool have_params = false;
   int adam_step = 0;
   DevMem params, grad, m, v, fwd, bwd;  // LN_NPARAM floats; packed fragments LN_LAYERS * LN_PACK words
+  DevMem fwd_u, bwd_u;                   // tcgen05 operands, LN_LAYERS * LN_UMMA bytes
+  bool umma = false;                     // tensor-memory (tcgen05) convolution instead of the warp-MMA one
   std::map<int, std::unique_ptr<LearnGrid>> grids;
   // training pairs of one level: inputs (LN_PAIR_IN BF16 per voxel) and targets (3 FP32)
   int pair_level = -1;

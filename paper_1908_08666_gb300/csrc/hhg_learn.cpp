@@ -75,6 +75,18 @@ void need_params(LearnState& S) {
 
 void repack(hhg_ctx* c, LearnState& S) {
   CK(launch_pack(S.params.as<float>(), S.fwd.as<uint32_t>(), S.bwd.as<uint32_t>(), c->stream));
+  CK(launch_pack_umma(S.params.as<float>(), S.fwd_u.p, S.bwd_u.p, c->stream));
+}
+
+// after a wait on the stream: a tensor-core convolution whose bounded wait ran out disables
+// that kernel for the context (the warp-MMA convolution takes over) and fails the call
+void check_conv(LearnState& S) {
+  int flag = 0;
+  CK(conv_take_error(&flag));
+  if (flag) {
+    S.umma = false;
+    THROW(HHG_ERR_TIMEOUT, "tensor-core convolution timed out (switched to the warp-MMA kernel)");
+  }
 }
 
 void alloc_params(hhg_ctx* c, LearnState& S) {
@@ -86,6 +98,8 @@ void alloc_params(hhg_ctx* c, LearnState& S) {
   CK(S.v.alloc(nb));
   CK(S.fwd.alloc(LN_LAYERS * LN_PACK * sizeof(uint32_t)));
   CK(S.bwd.alloc(LN_LAYERS * LN_PACK * sizeof(uint32_t)));
+  CK(S.fwd_u.alloc((size_t)LN_LAYERS * LN_UMMA));
+  CK(S.bwd_u.alloc((size_t)LN_LAYERS * LN_UMMA));
   CK(S.dscal.alloc(8 * sizeof(double)));
 }
 
@@ -126,12 +140,18 @@ void ensure_grad_scratch(hhg_ctx* c, LearnState& S, GridShape s) {
 const float* layer_bias(LearnState& S, int l) { return S.params.as<float>() + (int64_t)l * LN_LSIZE + LN_WSIZE; }
 const uint32_t* layer_fwd(LearnState& S, int l) { return S.fwd.as<uint32_t>() + (int64_t)l * LN_PACK; }
 const uint32_t* layer_bwd(LearnState& S, int l) { return S.bwd.as<uint32_t>() + (int64_t)l * LN_PACK; }
+const void* layer_fwd_u(LearnState& S, int l) {
+  return S.umma ? (const void*)((const char*)S.fwd_u.p + (size_t)l * LN_UMMA) : nullptr;
+}
+const void* layer_bwd_u(LearnState& S, int l) {
+  return S.umma ? (const void*)((const char*)S.bwd_u.p + (size_t)l * LN_UMMA) : nullptr;
+}
 
 // forward pass from act[0]: act[1..3] = hidden activations, out = FP32 output channels
 void forward(hhg_ctx* c, LearnState& S, GridShape s, float* out) {
   for (int l = 0; l < LN_LAYERS; ++l) {
     const bool last = l == LN_LAYERS - 1;
-    CK(launch_conv(S.act[l].p, layer_fwd(S, l), layer_bias(S, l), last ? nullptr : S.act[l + 1].p,
+    CK(launch_conv(S.act[l].p, layer_fwd(S, l), layer_fwd_u(S, l), layer_bias(S, l), last ? nullptr : S.act[l + 1].p,
                    last ? out : nullptr, LN_COUT, nullptr, s, last ? 0 : 1, c->stream));
   }
 }
@@ -140,8 +160,9 @@ void forward(hhg_ctx* c, LearnState& S, GridShape s, float* out) {
 void forward_inference(hhg_ctx* c, LearnState& S, GridShape s, float* out) {
   for (int l = 0; l < LN_LAYERS; ++l) {
     const bool last = l == LN_LAYERS - 1;
-    CK(launch_conv(S.act[l & 1].p, layer_fwd(S, l), layer_bias(S, l), last ? nullptr : S.act[(l + 1) & 1].p,
-                   last ? out : nullptr, LN_COUT, nullptr, s, last ? 0 : 1, c->stream));
+    CK(launch_conv(S.act[l & 1].p, layer_fwd(S, l), layer_fwd_u(S, l), layer_bias(S, l),
+                   last ? nullptr : S.act[(l + 1) & 1].p, last ? out : nullptr, LN_COUT, nullptr, s, last ? 0 : 1,
+                   c->stream));
   }
 }
 
@@ -156,8 +177,8 @@ void backward(hhg_ctx* c, LearnState& S, GridShape s, const float* out, const fl
     CK(launch_wgrad(S.act[l].p, S.gb[cur].p, S.wpart.as<float>(), gW, s, c->stream));
     CK(launch_bgrad(S.gb[cur].p, V, S.bpart.as<float>(), gW + LN_WSIZE, c->stream));
     if (l > 0) {
-      CK(launch_conv(S.gb[cur].p, layer_bwd(S, l), nullptr, S.gb[cur ^ 1].p, nullptr, 0, S.act[l].p, s, 0,
-                     c->stream));
+      CK(launch_conv(S.gb[cur].p, layer_bwd(S, l), layer_bwd_u(S, l), nullptr, S.gb[cur ^ 1].p, nullptr, 0,
+                     S.act[l].p, s, 0, c->stream));
       cur ^= 1;
     }
   }
@@ -483,6 +504,7 @@ void learned_ir(hhg_ctx* c, const hhg_solve_opts* o, const double* f, double* x,
   }
   R.rel_residual = r0 > 0.0 ? std::sqrt(rr / r0) : 0.0;
   R.converged = R.rel_residual <= o->rtol;
+  if (use_net) check_conv(state(c));
 }
 
 }  // namespace host
@@ -507,6 +529,13 @@ hhg_status hhg_learn_init(hhg_ctx* c, uint64_t seed) {
           for (int o = 0; o < cout; ++o) W[(t * LN_C + i) * LN_C + o] = round_bf16((float)(sd * normal(s)));
     }
     upload_params(c, S, h);
+  });
+}
+
+hhg_status hhg_learn_set_conv_kernel(hhg_ctx* c, int kernel) {
+  return guard(c, [&] {
+    if (kernel != 0 && kernel != 1) THROW(HHG_ERR_ARG, "conv kernel 0 (warp MMA) or 1 (tcgen05)");
+    state(c).umma = kernel == 1;
   });
 }
 
@@ -552,6 +581,8 @@ hhg_status hhg_learn_forward(hhg_ctx* c, const float* x, int cin, int B, int D, 
     ensure_acts(c, S, s.voxels());
     CK(launch_to_bf16(s.voxels(), cin, x, S.act[0].p, c->stream));
     forward_inference(c, S, s, out);
+    wait_stream(c);
+    check_conv(S);
   });
 }
 
@@ -571,6 +602,7 @@ hhg_status hhg_learn_loss_grad(hhg_ctx* c, const float* x, int cin, const float*
     if (grad_host)
       CK(cudaMemcpyAsync(grad_host, S.grad.p, LN_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     wait_stream(c);
+    check_conv(S);
     if (loss_host) *loss_host = c->pinned[0];
   });
 }
@@ -720,6 +752,7 @@ hhg_status hhg_learn_train(hhg_ctx* c, const hhg_learn_train_opts* o, hhg_learn_
     std::vector<double> hl(o->steps);
     CK(cudaMemcpyAsync(hl.data(), dloss.p, o->steps * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     wait_stream(c);
+    check_conv(S);
     for (double v : hl)
       if (!std::isfinite(v)) THROW(HHG_ERR_NUMERIC, "training diverged");
     if (rep) {
@@ -746,6 +779,7 @@ hhg_status hhg_learn_precondition(hhg_ctx* c, int level, int use_net, const void
     float* az = lwork(c, G, level, LW_AZ);
     const double a = precondition(c, level, (const float*)r, (float*)z, az, use_net != 0);
     wait_stream(c);
+    check_conv(state(c));
     if (alpha) *alpha = a;
   });
 }

@@ -174,6 +174,171 @@ __global__ void __launch_bounds__(CONV_WARPS * 32) k_conv(const uint4* __restric
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Convolution on the 5th-generation tensor cores (tcgen05, accumulators in tensor memory).
+// A block owns an output tile of UX x UY x UZ voxels and stages the input tile with its
+// one-voxel halo (UPX x UPY x UPZ voxels, zero outside the grid) in shared memory as two
+// planes of 16-byte rows (channels 0-7 and 8-15 of every voxel), the K-major no-swizzle
+// layout: 8 consecutive voxels form one 128-byte core matrix.  The implicit GEMM takes
+// M = 128 consecutive padded positions starting at the first interior one, N = 16 output
+// channels and K = 16 input channels per tap; tap (dz, dy, dx) shifts the A operand by
+// ((dz UPY + dy) UPX + dx) rows, i.e. its descriptor start address by 16 bytes per row.
+// Six such M tiles cover every interior position of the tile (rows at halo positions are
+// computed and discarded).  One thread issues the 6 x 27 MMAs into six 16-column TMEM
+// accumulators and commits them to an mbarrier; after a bounded wait every warp reads its
+// 32 TMEM lanes (one output row per thread, 16 channels) and runs the epilogue.
+constexpr int UX = 32, UY = 4, UZ = 4;
+constexpr int UPX = UX + 2, UPY = UY + 2, UPZ = UZ + 2;
+constexpr int U_VOX = UPX * UPY * UPZ;                  // staged voxels (1224)
+constexpr int U_P0 = (UPY + 1) * UPX + 1;               // first interior padded position
+constexpr int U_MT = 6;                                 // M tiles of 128 rows
+constexpr int U_PLANE_VOX = 1280;                       // >= U_P0 + 128 U_MT + U_P0: rows any tap reads
+constexpr int U_PLANE = U_PLANE_VOX * 16;               // bytes per channel-half plane
+constexpr int U_WBYTES = LN_TAPS * 512;                 // B operands: [tap][k half][n 16][8 bf16]
+constexpr int U_BAR = 2 * U_PLANE + U_WBYTES;           // mbarrier and TMEM-address slot
+constexpr int U_SMEM = U_BAR + 64;
+constexpr int U_TMEM_COLS = 128;                        // 6 accumulators x 16 columns, rounded up
+constexpr uint32_t U_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr long long U_SPIN_LIMIT = 1ll << 24;           // bound of the mbarrier wait (polls, 100 ns apart)
+
+static_assert(U_P0 + 128 * U_MT - 1 + U_P0 < U_PLANE_VOX, "plane too small for the shifted rows");
+static_assert((UZ * UPY + UY) * UPX + UX <= U_P0 + 128 * U_MT - 1, "M tiles do not cover the tile");
+
+__device__ int g_conv_error = 0;  // set when a tensor-core convolution's wait ran out
+
+// shared-memory matrix descriptor: start address, leading (K) and stride (M/N) byte
+// offsets of the core matrices, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+
+__global__ void __launch_bounds__(128) k_conv_umma(const uint4* __restrict__ X, const uint4* __restrict__ Wu,
+                                                   const float* __restrict__ bias, uint4* __restrict__ Y,
+                                                   float* __restrict__ Yf, int nf, const uint4* __restrict__ mask,
+                                                   int D, int H, int W, int ntz, int relu) {
+  extern __shared__ __align__(1024) unsigned char usm[];
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(usm);
+  const uint32_t bar = sbase + U_BAR;
+  const uint32_t slot = sbase + U_BAR + 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.z / ntz;
+  const int x0 = blockIdx.x * UX, y0 = blockIdx.y * UY, z0 = (blockIdx.z % ntz) * UZ;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(U_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // B operands of the layer, then the input tile (two channel-half planes)
+  for (int q = threadIdx.x; q < U_WBYTES / 16; q += blockDim.x) cp_async16(sbase + 2 * U_PLANE + 16 * q, Wu + q, true);
+  for (int q = threadIdx.x; q < U_VOX * 2; q += blockDim.x) {
+    const int v = q >> 1, h = q & 1;
+    const int ix = v % UPX, iy = (v / UPX) % UPY, iz = v / (UPX * UPY);
+    const int gx = x0 - 1 + ix, gy = y0 - 1 + iy, gz = z0 - 1 + iz;
+    const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D;
+    const uint4* src = in ? X + ((((int64_t)b * D + gz) * H + gy) * W + gx) * 2 + h : X;
+    cp_async16(sbase + h * U_PLANE + 16 * v, src, in);
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  uint32_t tmem;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(slot));
+  if (threadIdx.x == 0) {
+    for (int mt = 0; mt < U_MT; ++mt) {
+      for (int t = 0; t < LN_TAPS; ++t) {
+        const int off = ((t / 9 - 1) * UPY + ((t / 3) % 3 - 1)) * UPX + (t % 3 - 1);
+        const uint64_t ad = umma_desc(sbase + 16u * (uint32_t)(U_P0 + 128 * mt + off), U_PLANE, 128);
+        const uint64_t bd = umma_desc(sbase + 2 * U_PLANE + 512u * t, 256, 128);
+        const uint32_t acc = t > 0;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem + 16u * mt),
+            "l"(ad), "l"(bd), "r"(U_IDESC), "r"(acc));
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+  }
+  // bounded wait for the MMAs; a short sleep between polls leaves the issue slots to the
+  // other blocks on the SM (their staging and epilogues)
+  uint32_t done = 0;
+  for (long long it = 0; it < U_SPIN_LIMIT && !done; ++it) {
+    asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+                 : "=r"(done)
+                 : "r"(bar), "r"(0)
+                 : "memory");
+    if (!done) __nanosleep(100);
+  }
+  done = __all_sync(0xffffffffu, done);
+  if (!done && lane == 0) atomicExch(&g_conv_error, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  float bv[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) bv[c] = bias ? bias[c] : 0.f;
+  for (int mt = 0; mt < U_MT && done; ++mt) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(tmem + ((uint32_t)(32 * warp) << 16) + 16u * mt));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int p = U_P0 + 128 * mt + 32 * warp + lane;
+    const int iz = p / (UPX * UPY), rem = p % (UPX * UPY), iy = rem / UPX, ix = rem % UPX;
+    const int gx = x0 + ix - 1, gy = y0 + iy - 1, gz = z0 + iz - 1;
+    if (ix < 1 || ix > UX || iy < 1 || iy > UY || iz < 1 || iz > UZ || gx >= W || gy >= H || gz >= D) continue;
+    const int64_t v = (((int64_t)b * D + gz) * H + gy) * W + gx;
+    float o[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      o[c] = __uint_as_float(r[c]) + bv[c];
+      if (relu) o[c] = fmaxf(o[c], 0.f);
+    }
+    if (mask) {
+      const uint4 m0 = mask[2 * v], m1 = mask[2 * v + 1];
+      const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (!bf16_positive(mw[q], 0)) o[2 * q] = 0.f;
+        if (!bf16_positive(mw[q], 1)) o[2 * q + 1] = 0.f;
+      }
+    }
+    if (Y) {
+      Y[2 * v] = make_uint4(pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]), pack_bf16x2(o[4], o[5]),
+                            pack_bf16x2(o[6], o[7]));
+      Y[2 * v + 1] = make_uint4(pack_bf16x2(o[8], o[9]), pack_bf16x2(o[10], o[11]), pack_bf16x2(o[12], o[13]),
+                                pack_bf16x2(o[14], o[15]));
+    }
+    if (Yf) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < nf) Yf[v * nf + c] = o[c];
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(U_TMEM_COLS));
+}
+
+// tcgen05 B operands of every layer: fwd[t][h][n][j] = W[t][8h+j][n] (forward),
+// bwd[t][h][n][j] = W[26-t][n][8h+j] (input gradient), BF16, LN_TAPS * 256 values per layer
+__global__ void k_pack_umma(const float* __restrict__ params, __nv_bfloat16* __restrict__ fwd,
+                            __nv_bfloat16* __restrict__ bwd) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= LN_LAYERS * LN_TAPS * 256) return;
+  const int l = q / (LN_TAPS * 256), r = q % (LN_TAPS * 256);
+  const int t = r / 256, h = (r / 128) % 2, n = (r / 8) % 16, j = r % 8;
+  const int k = 8 * h + j;
+  const float* Wl = params + (int64_t)l * LN_LSIZE;
+  fwd[q] = __float2bfloat16_rn(Wl[t * 256 + k * 16 + n]);
+  bwd[q] = __float2bfloat16_rn(Wl[(26 - t) * 256 + n * 16 + k]);
+}
+
 // Weight gradient of tap t = blockIdx.y: dW[t][i][o] = sum_v A[v + off(t)][i] G[v][o] as a
 // tensor-core product with the voxels as the k dimension (A fragment: input channels x
 // 16 voxels, B fragment: 16 voxels x 8 output channels).  Each warp covers WG_ROWS row
@@ -477,9 +642,26 @@ inline int64_t red_blocks(int64_t V) { return blocks_for(V, RED_BLOCK, RED_MAX_B
 
 }  // namespace
 
-int launch_conv(const void* X, const uint32_t* Wp, const float* bias, void* Y, float* Yf, int nf, const void* mask,
-                GridShape s, int relu, void* stream) {
+int launch_conv(const void* X, const uint32_t* Wp, const void* Wu, const float* bias, void* Y, float* Yf, int nf,
+                const void* mask, GridShape s, int relu, void* stream) {
   if (s.voxels() == 0) return 0;
+  if (Wu) {
+    static bool uattr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return (int)e;
+    if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+    if (!uattr[dev]) {
+      e = cudaFuncSetAttribute(k_conv_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM);
+      if (e != cudaSuccess) return (int)e;
+      uattr[dev] = true;
+    }
+    const int ntz = (s.D + UZ - 1) / UZ;
+    dim3 grid((unsigned)((s.W + UX - 1) / UX), (unsigned)((s.H + UY - 1) / UY), (unsigned)(ntz * s.B));
+    k_conv_umma<<<grid, 128, U_SMEM, (cudaStream_t)stream>>>((const uint4*)X, (const uint4*)Wu, bias, (uint4*)Y, Yf,
+                                                             nf, (const uint4*)mask, s.D, s.H, s.W, ntz, relu);
+    return (int)cudaGetLastError();
+  }
   static bool attr[64] = {};  // per device: dynamic shared memory above 48 KB
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -538,6 +720,24 @@ int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, i
   const float c1 = (float)(1.0 - std::pow(b1, step)), c2 = (float)(1.0 - std::pow(b2, step));
   k_adam<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(p, g, m, v, n, lr, (float)b1, (float)b2, 1e-8f, c1, c2);
   return (int)cudaGetLastError();
+}
+
+int launch_pack_umma(const float* params, void* fwd, void* bwd, void* stream) {
+  const int n = LN_LAYERS * LN_TAPS * 256;
+  k_pack_umma<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(params, (__nv_bfloat16*)fwd, (__nv_bfloat16*)bwd);
+  return (int)cudaGetLastError();
+}
+
+int conv_take_error(int* flag) {
+  int v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_conv_error, sizeof(int));
+  if (e != cudaSuccess) return (int)e;
+  if (v) {
+    const int zero = 0;
+    e = cudaMemcpyToSymbol(g_conv_error, &zero, sizeof(int));
+  }
+  *flag = v;
+  return (int)e;
 }
 
 int launch_pack(const float* params, uint32_t* fwd, uint32_t* bwd, void* stream) {

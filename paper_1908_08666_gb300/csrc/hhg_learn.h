@@ -38,8 +38,15 @@ struct GridShape {
 // (launch_pack).  Y (BF16, 16 channels) and Yf (FP32, the first nf channels) are optional.
 // mask (BF16, 16 channels, optional): outputs where mask <= 0 are set to 0 (the ReLU
 // derivative in the backward pass).  relu: apply max(., 0) before the mask.
-int launch_conv(const void* X, const uint32_t* Wp, const float* bias, void* Y, float* Yf, int nf, const void* mask,
-                GridShape s, int relu, void* stream);
+// Wu (nullable): the layer's tcgen05 operands (launch_pack_umma); when given, the
+// tensor-memory kernel runs instead of the warp-MMA one.
+int launch_conv(const void* X, const uint32_t* Wp, const void* Wu, const float* bias, void* Y, float* Yf, int nf,
+                const void* mask, GridShape s, int relu, void* stream);
+// tcgen05 operands of every layer (LN_UMMA bytes each, forward and input-gradient weights)
+constexpr int LN_UMMA = LN_TAPS * 256 * 2;
+int launch_pack_umma(const float* params, void* fwd, void* bwd, void* stream);
+// *flag = whether a tensor-core convolution's bounded wait ran out since the last call (resets it)
+int conv_take_error(int* flag);
 
 // dW[t][i][o] = sum_v A[v + off(t)][i] G[v][o] for all taps: per-block partial sums into
 // partial (wgrad_partials() blocks x LN_WSIZE floats), then their ordered sum into dW.

@@ -66,9 +66,11 @@ def test_param_layout_roundtrip(ctx):
     assert abs(Wq[1].std() - np.sqrt(2.0 / (27 * 16))) < 0.1 * np.sqrt(2.0 / (27 * 16))
 
 
-@pytest.mark.parametrize("shape", [(2, 5, 6, 19), (1, 3, 4, 16), (1, 1, 1, 1)])
-def test_forward_matches_oracle(ctx, shape):
+@pytest.mark.parametrize("kernel", [0, 1], ids=["mma_sync", "tcgen05"])
+@pytest.mark.parametrize("shape", [(2, 5, 6, 19), (1, 3, 4, 16), (1, 1, 1, 1), (1, 9, 7, 40)])
+def test_forward_matches_oracle(ctx, shape, kernel):
     t = ctx.torch
+    B.hhg_learn_set_conv_kernel(ctx.h, kernel)
     Bn, D, H, W = shape
     rng = np.random.default_rng(sum(shape))
     Ws, bs = _params(2)
@@ -84,9 +86,11 @@ def test_forward_matches_oracle(ctx, shape):
     assert np.linalg.norm(got - want) <= 3e-3 * np.linalg.norm(want)
 
 
+@pytest.mark.parametrize("kernel", [0, 1], ids=["mma_sync", "tcgen05"])
 @pytest.mark.parametrize("shape", [(2, 6, 5, 21), (1, 4, 4, 16)])
-def test_gradients_match_oracle(ctx, shape):
+def test_gradients_match_oracle(ctx, shape, kernel):
     t = ctx.torch
+    B.hhg_learn_set_conv_kernel(ctx.h, kernel)
     Bn, D, H, W = shape
     rng = np.random.default_rng(10 + sum(shape))
     Ws, bs = _params(3)
@@ -119,6 +123,7 @@ def cube4():
 
 
 def test_grid_of_the_cube(cube4):
+    B.hhg_learn_set_conv_kernel(cube4.ctx.h, 0)
     dims, nfree = B.hhg_learn_grid(cube4.ctx.h, 4)
     assert dims == (17, 17, 17) and nfree == 15**3
 
