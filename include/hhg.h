@@ -381,8 +381,11 @@ hhg_status hhg_residual_noalloc(hhg_ctx* ctx, int level, hhg_dtype dt, const voi
 int64_t hhg_learn_num_params(void);
 /* Convolution kernel of the network: 0 = warp-level BF16 MMA (mma.sync m16n8k16) on a
  * shared-memory tile (default), 1 = 5th-generation tensor cores (tcgen05.mma with
- * accumulators in tensor memory, 6 x 27 MMAs of 128 x 16 x 16 per 32 x 4 x 4 output tile).
- * Both give the same results up to FP32 summation order. */
+ * accumulators in tensor memory, 6 x 27 MMAs of 128 x 16 x 16 per 32 x 4 x 4 output tile,
+ * one tile per block), 2 = the same MMAs in a persistent pipeline (tensor-memory-
+ * accelerator loads into two shared stages, two tensor-memory accumulator sets, an
+ * epilogue warpgroup draining one while the next tile's MMAs run).  All give the same
+ * results up to FP32 summation order. */
 hhg_status hhg_learn_set_conv_kernel(hhg_ctx* ctx, int kernel);
 /* He-normal initialisation (std sqrt(2/(27*fan_in)), last layer x0.1; BF16 values,
  * zero biases) from a seeded generator; resets the optimiser state. */

@@ -388,7 +388,7 @@ def hhg_learn_num_params():
 
 
 def hhg_learn_set_conv_kernel(ctx, kernel):
-    """0: warp-level MMA convolution (default), 1: tcgen05 tensor-memory convolution."""
+    """0: warp-level MMA convolution (default), 1: tcgen05 per tile, 2: TMA + tcgen05 pipeline."""
     _check(ctx, load().hhg_learn_set_conv_kernel(ctx, int(kernel)))
 
 

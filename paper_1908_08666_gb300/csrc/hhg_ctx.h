@@ -170,7 +170,7 @@ struct LearnState {
   int adam_step = 0;
   DevMem params, grad, m, v, fwd, bwd;  // LN_NPARAM floats; packed fragments LN_LAYERS * LN_PACK words
   DevMem fwd_u, bwd_u;                   // tcgen05 operands, LN_LAYERS * LN_UMMA bytes
-  bool umma = false;                     // tensor-memory (tcgen05) convolution instead of the warp-MMA one
+  int conv_kernel = 0;                   // 0 warp MMA, 1 tcgen05 per tile, 2 TMA + tcgen05 pipeline
   std::map<int, std::unique_ptr<LearnGrid>> grids;
   // training pairs of one level: inputs (LN_PAIR_IN BF16 per voxel) and targets (3 FP32)
   int pair_level = -1;

@@ -84,7 +84,7 @@ void check_conv(LearnState& S) {
   int flag = 0;
   CK(conv_take_error(&flag));
   if (flag) {
-    S.umma = false;
+    S.conv_kernel = 0;
     THROW(HHG_ERR_TIMEOUT, "tensor-core convolution timed out (switched to the warp-MMA kernel)");
   }
 }
@@ -140,19 +140,26 @@ void ensure_grad_scratch(hhg_ctx* c, LearnState& S, GridShape s) {
 const float* layer_bias(LearnState& S, int l) { return S.params.as<float>() + (int64_t)l * LN_LSIZE + LN_WSIZE; }
 const uint32_t* layer_fwd(LearnState& S, int l) { return S.fwd.as<uint32_t>() + (int64_t)l * LN_PACK; }
 const uint32_t* layer_bwd(LearnState& S, int l) { return S.bwd.as<uint32_t>() + (int64_t)l * LN_PACK; }
-const void* layer_fwd_u(LearnState& S, int l) {
-  return S.umma ? (const void*)((const char*)S.fwd_u.p + (size_t)l * LN_UMMA) : nullptr;
-}
-const void* layer_bwd_u(LearnState& S, int l) {
-  return S.umma ? (const void*)((const char*)S.bwd_u.p + (size_t)l * LN_UMMA) : nullptr;
+const void* layer_fwd_u(LearnState& S, int l) { return (const char*)S.fwd_u.p + (size_t)l * LN_UMMA; }
+const void* layer_bwd_u(LearnState& S, int l) { return (const char*)S.bwd_u.p + (size_t)l * LN_UMMA; }
+
+// one convolution with the context's kernel choice (bwd: input-gradient weights)
+void conv(hhg_ctx* c, LearnState& S, int l, bool bwd, const void* X, const float* bias, void* Y, float* Yf, int nf,
+          const void* mask, GridShape s, int relu) {
+  const uint32_t* wp = bwd ? layer_bwd(S, l) : layer_fwd(S, l);
+  const void* wu = bwd ? layer_bwd_u(S, l) : layer_fwd_u(S, l);
+  if (S.conv_kernel == 2)
+    CK(launch_conv_tma(X, wu, bias, Y, Yf, nf, mask, s, relu, c->stream));
+  else
+    CK(launch_conv(X, wp, S.conv_kernel == 1 ? wu : nullptr, bias, Y, Yf, nf, mask, s, relu, c->stream));
 }
 
 // forward pass from act[0]: act[1..3] = hidden activations, out = FP32 output channels
 void forward(hhg_ctx* c, LearnState& S, GridShape s, float* out) {
   for (int l = 0; l < LN_LAYERS; ++l) {
     const bool last = l == LN_LAYERS - 1;
-    CK(launch_conv(S.act[l].p, layer_fwd(S, l), layer_fwd_u(S, l), layer_bias(S, l), last ? nullptr : S.act[l + 1].p,
-                   last ? out : nullptr, LN_COUT, nullptr, s, last ? 0 : 1, c->stream));
+    conv(c, S, l, false, S.act[l].p, layer_bias(S, l), last ? nullptr : S.act[l + 1].p, last ? out : nullptr, LN_COUT,
+         nullptr, s, last ? 0 : 1);
   }
 }
 
@@ -160,9 +167,8 @@ void forward(hhg_ctx* c, LearnState& S, GridShape s, float* out) {
 void forward_inference(hhg_ctx* c, LearnState& S, GridShape s, float* out) {
   for (int l = 0; l < LN_LAYERS; ++l) {
     const bool last = l == LN_LAYERS - 1;
-    CK(launch_conv(S.act[l & 1].p, layer_fwd(S, l), layer_fwd_u(S, l), layer_bias(S, l),
-                   last ? nullptr : S.act[(l + 1) & 1].p, last ? out : nullptr, LN_COUT, nullptr, s, last ? 0 : 1,
-                   c->stream));
+    conv(c, S, l, false, S.act[l & 1].p, layer_bias(S, l), last ? nullptr : S.act[(l + 1) & 1].p,
+         last ? out : nullptr, LN_COUT, nullptr, s, last ? 0 : 1);
   }
 }
 
@@ -177,8 +183,7 @@ void backward(hhg_ctx* c, LearnState& S, GridShape s, const float* out, const fl
     CK(launch_wgrad(S.act[l].p, S.gb[cur].p, S.wpart.as<float>(), gW, s, c->stream));
     CK(launch_bgrad(S.gb[cur].p, V, S.bpart.as<float>(), gW + LN_WSIZE, c->stream));
     if (l > 0) {
-      CK(launch_conv(S.gb[cur].p, layer_bwd(S, l), layer_bwd_u(S, l), nullptr, S.gb[cur ^ 1].p, nullptr, 0,
-                     S.act[l].p, s, 0, c->stream));
+      conv(c, S, l, true, S.gb[cur].p, nullptr, S.gb[cur ^ 1].p, nullptr, 0, S.act[l].p, s, 0);
       cur ^= 1;
     }
   }
@@ -534,8 +539,8 @@ hhg_status hhg_learn_init(hhg_ctx* c, uint64_t seed) {
 
 hhg_status hhg_learn_set_conv_kernel(hhg_ctx* c, int kernel) {
   return guard(c, [&] {
-    if (kernel != 0 && kernel != 1) THROW(HHG_ERR_ARG, "conv kernel 0 (warp MMA) or 1 (tcgen05)");
-    state(c).umma = kernel == 1;
+    if (kernel < 0 || kernel > 2) THROW(HHG_ERR_ARG, "conv kernel 0 (warp MMA), 1 (tcgen05) or 2 (TMA + tcgen05)");
+    state(c).conv_kernel = kernel;
   });
 }
 

@@ -3,6 +3,7 @@
 // mma.sync m16n8k16), its weight and bias gradients, the MSE loss, Adam, weight
 // packing, and the transfers between the library's vector layout and the node grid.
 // Layouts and conventions are those of hhg_learn.h.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -250,16 +251,17 @@ __global__ void __launch_bounds__(128) k_conv_umma(const uint4* __restrict__ X, 
   uint32_t tmem;
   asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(slot));
   if (threadIdx.x == 0) {
+    const uint64_t a0 = umma_desc(sbase + 16u * U_P0, U_PLANE, 128);
+    const uint64_t b0 = umma_desc(sbase + 2 * U_PLANE, 256, 128);
     for (int mt = 0; mt < U_MT; ++mt) {
+      const uint64_t am = a0 + (uint64_t)(128 * mt);
+#pragma unroll
       for (int t = 0; t < LN_TAPS; ++t) {
         const int off = ((t / 9 - 1) * UPY + ((t / 3) % 3 - 1)) * UPX + (t % 3 - 1);
-        const uint64_t ad = umma_desc(sbase + 16u * (uint32_t)(U_P0 + 128 * mt + off), U_PLANE, 128);
-        const uint64_t bd = umma_desc(sbase + 2 * U_PLANE + 512u * t, 256, 128);
-        const uint32_t acc = t > 0;
         asm volatile(
             "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
                 tmem + 16u * mt),
-            "l"(ad), "l"(bd), "r"(U_IDESC), "r"(acc));
+            "l"(am + (uint64_t)(int64_t)off), "l"(b0 + (uint64_t)(32 * t)), "r"(U_IDESC), "r"((uint32_t)(t > 0)));
       }
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -323,6 +325,236 @@ __global__ void __launch_bounds__(128) k_conv_umma(const uint4* __restrict__ X, 
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(U_TMEM_COLS));
+}
+
+// ---------------------------------------------------------------------------------------
+// The same convolution as a persistent, warp-specialised pipeline: warp 0 loads input
+// tiles with the tensor memory accelerator (one 5-D tiled copy per channel half straight
+// into the plane layout; the halo outside the grid is zero-filled by the copy) into two
+// shared-memory stages, warp 1 issues the tile's 6 x 27 MMAs into one of two TMEM
+// accumulator sets, and warps 2-5 drain the other set through the epilogue, so loading,
+// tensor-core work and stores of consecutive tiles overlap.  Stage and accumulator hand-off
+// use mbarriers (full / empty per stage, tmem-full / tmem-empty per accumulator set); every
+// wait is bounded and, once one runs out, all roles leave their loops (error flag set).
+constexpr int P_STAGES = 2;
+constexpr int P_THREADS = 192;
+constexpr int P_WOFF = P_STAGES * 2 * U_PLANE;
+constexpr int P_BAR = P_WOFF + U_WBYTES;
+constexpr int P_FULL = P_BAR, P_EMPTY = P_BAR + 16, P_TFULL = P_BAR + 32, P_TEMPTY = P_BAR + 48;
+constexpr int P_WBAR = P_BAR + 64, P_SLOT = P_BAR + 72, P_ABORT = P_BAR + 76;
+constexpr int P_SMEM = P_BAR + 128;
+constexpr int P_TMEM_COLS = 256;
+constexpr uint32_t P_TX = 2u * U_VOX * 16u;  // bytes of one stage (two halves of 8 channels)
+
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  for (long long it = 0; it < U_SPIN_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    if (ok) return true;
+    if (*abort) return false;
+    __nanosleep(64);
+  }
+  *abort = 1;
+  atomicExch(&g_conv_error, 1);
+  return false;
+}
+
+// bounded wait that ignores the abort flag: used to drain a block's own copies and MMAs
+__device__ __forceinline__ void bar_drain(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < U_SPIN_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    if (ok) return;
+    __nanosleep(64);
+  }
+  atomicExch(&g_conv_error, 1);
+}
+
+__device__ __forceinline__ void bar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(P_THREADS, 1) k_conv_tma(const __grid_constant__ CUtensorMap tmap,
+                                                           const uint4* __restrict__ Wu,
+                                                           const float* __restrict__ bias, uint4* __restrict__ Y,
+                                                           float* __restrict__ Yf, int nf,
+                                                           const uint4* __restrict__ mask, int D, int H, int W,
+                                                           int ntx, int nty, int ntz, int ntiles, int relu) {
+  extern __shared__ __align__(1024) unsigned char psm[];
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(psm);
+  volatile int* abort = (volatile int*)(psm + P_ABORT);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    *abort = 0;
+    for (int q = 0; q < P_STAGES; ++q) {
+      bar_init(sbase + P_FULL + 8 * q, 1);
+      bar_init(sbase + P_EMPTY + 8 * q, 1);
+      bar_init(sbase + P_TFULL + 8 * q, 1);
+      bar_init(sbase + P_TEMPTY + 8 * q, 4);
+    }
+    bar_init(sbase + P_WBAR, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sbase + P_SLOT),
+                 "r"(P_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  uint32_t tmem;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(sbase + P_SLOT));
+  const int ntile_mine = blockIdx.x < (unsigned)ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      bar_expect_tx(sbase + P_WBAR, U_WBYTES);
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       sbase + P_WOFF),
+                   "l"(Wu), "r"(U_WBYTES), "r"(sbase + P_WBAR)
+                   : "memory");
+      int last[P_STAGES] = {-1, -1};
+      for (int k = 0; k < ntile_mine; ++k) {
+        const int st = k & 1;
+        if (k >= 2 && !bar_wait(sbase + P_EMPTY + 8 * st, ((k >> 1) - 1) & 1, abort)) break;
+        last[st] = k;
+        const int tile = (int)blockIdx.x + k * (int)gridDim.x;
+        const int tx = tile % ntx, ty = (tile / ntx) % nty, tzb = tile / (ntx * nty);
+        const int b = tzb / ntz, tz = tzb % ntz;
+        const int cx = tx * UX - 1, cy = ty * UY - 1, cz = tz * UZ - 1;
+        const uint32_t full = sbase + P_FULL + 8 * st;
+        bar_expect_tx(full, P_TX);
+        for (int h = 0; h < 2; ++h)
+          asm volatile(
+              "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+              "%5, %6}], [%7];" ::"r"(sbase + (2 * st + h) * U_PLANE),
+              "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(8 * h), "r"(cx), "r"(cy), "r"(cz), "r"(b), "r"(full)
+              : "memory");
+      }
+      // no tensor copy of this block may still be writing shared memory when it exits
+      if (*abort)
+        for (int st = 0; st < P_STAGES; ++st)
+          if (last[st] >= 0) bar_drain(sbase + P_FULL + 8 * st, (last[st] >> 1) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && bar_wait(sbase + P_WBAR, 0, abort)) {
+      int last[P_STAGES] = {-1, -1};
+      for (int k = 0; k < ntile_mine; ++k) {
+        const int st = k & 1;
+        if (!bar_wait(sbase + P_FULL + 8 * st, (k >> 1) & 1, abort)) break;
+        if (k >= 2 && !bar_wait(sbase + P_TEMPTY + 8 * st, ((k >> 1) - 1) & 1, abort)) break;
+        last[st] = k;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // descriptors as base + offset in 16-byte units (the start-address field): an M tile
+        // is 128 rows further, a tap shifts by its row offset, a B operand is 512 bytes further
+        const uint64_t a0 = umma_desc(sbase + 2 * st * U_PLANE + 16u * U_P0, U_PLANE, 128);
+        const uint64_t b0 = umma_desc(sbase + P_WOFF, 256, 128);
+        for (int mt = 0; mt < U_MT; ++mt) {
+          const uint64_t am = a0 + (uint64_t)(128 * mt);
+          const uint32_t d = tmem + 128u * st + 16u * mt;
+#pragma unroll
+          for (int t = 0; t < LN_TAPS; ++t) {
+            const int off = ((t / 9 - 1) * UPY + ((t / 3) % 3 - 1)) * UPX + (t % 3 - 1);
+            const uint64_t ad = am + (uint64_t)(int64_t)off;
+            const uint64_t bd = b0 + (uint64_t)(32 * t);
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::
+                    "r"(d),
+                "l"(ad), "l"(bd), "r"(U_IDESC), "r"((uint32_t)(t > 0)));
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         sbase + P_EMPTY + 8 * st)
+                     : "memory");
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         sbase + P_TFULL + 8 * st)
+                     : "memory");
+      }
+      // no MMA of this block may still be running when its tensor memory is freed
+      if (*abort)
+        for (int st = 0; st < P_STAGES; ++st)
+          if (last[st] >= 0) bar_drain(sbase + P_EMPTY + 8 * st, (last[st] >> 1) & 1);
+    }
+    __syncwarp();
+  } else {
+    const int quarter = warp & 3;  // TMEM lanes 32 quarter .. of this warp
+    float bv[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) bv[c] = bias ? bias[c] : 0.f;
+    for (int k = 0; k < ntile_mine; ++k) {
+      const int st = k & 1;
+      const bool ok = __all_sync(0xffffffffu, bar_wait(sbase + P_TFULL + 8 * st, (k >> 1) & 1, abort));
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int tile = (int)blockIdx.x + k * (int)gridDim.x;
+      const int tx = tile % ntx, ty = (tile / ntx) % nty, tzb = tile / (ntx * nty);
+      const int b = tzb / ntz, tz = tzb % ntz;
+      const int x0 = tx * UX, y0 = ty * UY, z0 = tz * UZ;
+      for (int mt = 0; mt < U_MT; ++mt) {
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(tmem + ((uint32_t)(32 * quarter) << 16) + 128u * st + 16u * mt));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int p = U_P0 + 128 * mt + 32 * quarter + lane;
+        const int iz = p / (UPX * UPY), rem = p % (UPX * UPY), iy = rem / UPX, ix = rem % UPX;
+        const int gx = x0 + ix - 1, gy = y0 + iy - 1, gz = z0 + iz - 1;
+        if (ix < 1 || ix > UX || iy < 1 || iy > UY || iz < 1 || iz > UZ || gx >= W || gy >= H || gz >= D) continue;
+        const int64_t v = (((int64_t)b * D + gz) * H + gy) * W + gx;
+        float o[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          o[c] = __uint_as_float(r[c]) + bv[c];
+          if (relu) o[c] = fmaxf(o[c], 0.f);
+        }
+        if (mask) {
+          const uint4 m0 = mask[2 * v], m1 = mask[2 * v + 1];
+          const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (!bf16_positive(mw[q], 0)) o[2 * q] = 0.f;
+            if (!bf16_positive(mw[q], 1)) o[2 * q + 1] = 0.f;
+          }
+        }
+        if (Y) {
+          Y[2 * v] = make_uint4(pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]), pack_bf16x2(o[4], o[5]),
+                                pack_bf16x2(o[6], o[7]));
+          Y[2 * v + 1] = make_uint4(pack_bf16x2(o[8], o[9]), pack_bf16x2(o[10], o[11]), pack_bf16x2(o[12], o[13]),
+                                    pack_bf16x2(o[14], o[15]));
+        }
+        if (Yf) {
+#pragma unroll
+          for (int c = 0; c < 16; ++c)
+            if (c < nf) Yf[v * nf + c] = o[c];
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) bar_arrive(sbase + P_TEMPTY + 8 * st);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P_TMEM_COLS));
+  }
 }
 
 // tcgen05 B operands of every layer: fwd[t][h][n][j] = W[t][8h+j][n] (forward),
@@ -719,6 +951,56 @@ int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, i
   const double b1 = 0.9, b2 = 0.999;
   const float c1 = (float)(1.0 - std::pow(b1, step)), c2 = (float)(1.0 - std::pow(b2, step));
   k_adam<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(p, g, m, v, n, lr, (float)b1, (float)b2, 1e-8f, c1, c2);
+  return (int)cudaGetLastError();
+}
+
+// 5-D tensor map of a [B][D][H][W][16] BF16 activation tensor with a box of 8 channels x the
+// padded tile (encoded through the driver entry point; no link to the driver library)
+static int encode_act_map(CUtensorMap* map, const void* X, GridShape s) {
+  typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return (int)e;
+    if (q != cudaDriverEntryPointSuccess || !p) return (int)cudaErrorNotSupported;
+    fn = (EncodeFn)p;
+  }
+  const cuuint64_t dims[5] = {16, (cuuint64_t)s.W, (cuuint64_t)s.H, (cuuint64_t)s.D, (cuuint64_t)s.B};
+  const cuuint64_t strides[4] = {32, 32ull * s.W, 32ull * s.W * s.H, 32ull * s.W * s.H * s.D};
+  const cuuint32_t box[5] = {8, UPX, UPY, UPZ, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(X), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : (int)cudaErrorInvalidValue;
+}
+
+int launch_conv_tma(const void* X, const void* Wu, const float* bias, void* Y, float* Yf, int nf, const void* mask,
+                    GridShape s, int relu, void* stream) {
+  if (s.voxels() == 0) return 0;
+  static bool pattr[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+  if (!pattr[dev]) {
+    e = cudaFuncSetAttribute(k_conv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM);
+    if (e != cudaSuccess) return (int)e;
+    pattr[dev] = true;
+  }
+  CUtensorMap map;
+  const int er = encode_act_map(&map, X, s);
+  if (er) return er;
+  const int ntx = (s.W + UX - 1) / UX, nty = (s.H + UY - 1) / UY, ntz = (s.D + UZ - 1) / UZ;
+  const int ntiles = ntx * nty * ntz * s.B;
+  const int grid = ntiles < 2 * 152 ? ntiles : 2 * 152;
+  k_conv_tma<<<grid, P_THREADS, P_SMEM, (cudaStream_t)stream>>>(map, (const uint4*)Wu, bias, (uint4*)Y, Yf, nf,
+                                                                 (const uint4*)mask, s.D, s.H, s.W, ntx, nty, ntz,
+                                                                 ntiles, relu);
   return (int)cudaGetLastError();
 }
 

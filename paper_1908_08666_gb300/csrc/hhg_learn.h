@@ -42,6 +42,9 @@ struct GridShape {
 // tensor-memory kernel runs instead of the warp-MMA one.
 int launch_conv(const void* X, const uint32_t* Wp, const void* Wu, const float* bias, void* Y, float* Yf, int nf,
                 const void* mask, GridShape s, int relu, void* stream);
+// The same convolution as a persistent TMA + tcgen05 pipeline (Wu required)
+int launch_conv_tma(const void* X, const void* Wu, const float* bias, void* Y, float* Yf, int nf, const void* mask,
+                    GridShape s, int relu, void* stream);
 // tcgen05 operands of every layer (LN_UMMA bytes each, forward and input-gradient weights)
 constexpr int LN_UMMA = LN_TAPS * 256 * 2;
 int launch_pack_umma(const float* params, void* fwd, void* bwd, void* stream);

@@ -66,7 +66,7 @@ def test_param_layout_roundtrip(ctx):
     assert abs(Wq[1].std() - np.sqrt(2.0 / (27 * 16))) < 0.1 * np.sqrt(2.0 / (27 * 16))
 
 
-@pytest.mark.parametrize("kernel", [0, 1], ids=["mma_sync", "tcgen05"])
+@pytest.mark.parametrize("kernel", [0, 1, 2], ids=["mma_sync", "tcgen05", "tma_tcgen05"])
 @pytest.mark.parametrize("shape", [(2, 5, 6, 19), (1, 3, 4, 16), (1, 1, 1, 1), (1, 9, 7, 40)])
 def test_forward_matches_oracle(ctx, shape, kernel):
     t = ctx.torch
@@ -86,7 +86,7 @@ def test_forward_matches_oracle(ctx, shape, kernel):
     assert np.linalg.norm(got - want) <= 3e-3 * np.linalg.norm(want)
 
 
-@pytest.mark.parametrize("kernel", [0, 1], ids=["mma_sync", "tcgen05"])
+@pytest.mark.parametrize("kernel", [0, 1, 2], ids=["mma_sync", "tcgen05", "tma_tcgen05"])
 @pytest.mark.parametrize("shape", [(2, 6, 5, 21), (1, 4, 4, 16)])
 def test_gradients_match_oracle(ctx, shape, kernel):
     t = ctx.torch
