@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--learn-level", type=int, default=8)
     ap.add_argument("--learn-seeds", type=int, default=24)
     ap.add_argument("--learn-steps", type=int, default=4000)
+    ap.add_argument("--no-learn-stokes", action="store_true")
+    ap.add_argument("--learn-stokes-fields", type=int, default=8)
+    ap.add_argument("--learn-stokes-steps", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -274,7 +277,8 @@ def stokes_bench(B, torch, level, dev, stream, steps=20):
         out = {"workload": "Stokes, 6-macro cube, level %d, viscosity sphere 1 / 1e3, f ~ U[-1,1] (seed 4)" % level,
                "apply_ms": round(ms, 5), "apply_gdofs": round(4 * U / (ms * 1e-3) / 1e9, 3)}
         for name, method, inner in (("ir_minres", B.SOLVE_STOKES_IR_MINRES, 400),
-                                    ("ir_uzawa_mg", B.SOLVE_STOKES_IR_UZAWA, 40)):
+                                    ("ir_uzawa_mg", B.SOLVE_STOKES_IR_UZAWA, 40),
+                                    ("ir_fgcr_uzawa_mg", B.SOLVE_STOKES_IR_FGCR, 60)):
             x = torch.zeros_like(f)
             rep = B.hhg_solve(h, f, x, method=method, level=level, dt=B.F64, rtol=1e-8, max_iter=30,
                               inner_rtol=1e-3, inner_max_iter=inner, allow_not_converged=True)
@@ -471,6 +475,103 @@ def learned_bench(B, torch, dev, stream, train_level, eval_level, nseed, nrhs, i
     return out
 
 
+def learned_stokes_bench(B, torch, dev, stream, train_level, eval_level, nfield, nrhs, iters, steps):
+    """Learned preconditioner for Stokes: training pairs from the errors of flexible GCR
+    with the inexact Uzawa V-cycle at train_level (viscosity 1 inside / 1e3 outside a sphere
+    of seeded centre in [0.35, 0.65]^3 and radius in [0.15, 0.3], tanh width 0.02; body
+    force U[-1, 1] per seed), GPU training (4 output channels: velocity and pressure),
+    then the time to an FP64 relative residual of 1e-8 at eval_level on the Stokes bench
+    workload (sphere at the centre, radius 0.25; f seed 4): FP64 refinement around FP32
+    flexible GCR with the Uzawa V-cycle plus the learned correction, against the same
+    solver with the V-cycle alone."""
+    import hhg_inputs as hi
+
+    xyz, tets = hi.kuhn_cube(1)
+
+    def make(level):
+        h = B.hhg_create(dev, stream.cuda_stream)
+        B.hhg_set_macro_mesh(h, xyz, tets)
+        B.hhg_refine(h, level)
+        B.hhg_set_problem(h, kind=B.STOKES)
+        E, U, _ = B.hhg_num_nodes(h, level)
+        ce = B.hhg_entry_coords(h, level)
+        e2u, udir = B.hhg_entry_to_unique(h, level)
+        first = np.full(U, -1, dtype=np.int64)
+        first[e2u[::-1]] = np.arange(E)[::-1]
+        return h, E, U, ce[first], udir
+
+    def scatter(h, level, u, comps, dt):
+        tdt = torch.float64 if dt == B.F64 else torch.float32
+        src = torch.as_tensor(np.ascontiguousarray(np.asarray(u).reshape(-1, comps).T).reshape(-1), dtype=tdt,
+                              device="cuda")
+        E = B.hhg_num_nodes(h, level)[0]
+        dst = torch.empty(comps * E, dtype=tdt, device="cuda")
+        B.hhg_scatter_unique(h, level, dt, comps, src, dst)
+        return dst
+
+    h, E, U, cu, udir = make(train_level)
+    B.hhg_learn_reserve_pairs(h, train_level, nfield * nrhs * iters)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(nfield):
+        rng = np.random.default_rng(500 + s)
+        ctr = rng.uniform(0.35, 0.65, size=3)
+        rad = rng.uniform(0.15, 0.3)
+        mu = hi.viscosity_sphere(cu - (ctr - 0.5), radius=rad)
+        B.hhg_set_coefficient(h, scatter(h, train_level, mu, 1, B.F64), B.F64)
+        B.hhg_mg_setup(h)
+        for q in range(nrhs):
+            f = np.zeros((U, 4))
+            f[:, :3] = rng.uniform(-1, 1, size=(U, 3))
+            f[udir, :3] = 0.0
+            B.hhg_learn_collect_cg(h, train_level, scatter(h, train_level, f, 4, B.F32), iters)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    B.hhg_learn_init(h, 1)
+    tr = B.hhg_learn_train(h, steps=steps, batch=8, crop=32, lr=2e-3, seed=2)
+    params = B.hhg_learn_get_params(h)
+    B.hhg_destroy(h)
+
+    h, E, U, cu, udir = make(eval_level)
+    try:
+        B.hhg_set_coefficient(h, scatter(h, eval_level, hi.viscosity_sphere(cu), 1, B.F64), B.F64)
+        B.hhg_mg_setup(h)
+        B.hhg_learn_set_params(h, params)
+        fu = hi.sample_grid(hi.uniform_grid(1 << eval_level, seed=4), cu)
+        fu[udir] = 0.0
+        f4 = np.zeros((U, 4))
+        f4[:, :3] = fu
+        f = scatter(h, eval_level, f4, 4, B.F64)
+        out = {"train": {"level": train_level, "fields": nfield, "pairs": int(tr["pairs"]),
+                         "pair_source": "errors of %d FGCR iterations x %d RHS per field" % (iters, nrhs),
+                         "pair_generation_s": round(gen_s, 3), "steps": steps, "batch": "8 x 32^3",
+                         "loss_first": tr["loss_first"], "loss_last": tr["loss_last"],
+                         "train_s": round(tr["seconds"], 3)},
+               "eval_level": eval_level, "rtol": 1e-8,
+               "workload": "Stokes, 6-macro cube, level %d, viscosity sphere 1 / 1e3, f ~ U[-1,1] (seed 4)"
+                           % eval_level}
+        for name, method in (("ir_fgcr_learned", B.SOLVE_STOKES_IR_FGCR_LEARNED),
+                             ("ir_fgcr_uzawa", B.SOLVE_STOKES_IR_FGCR)):
+            x = torch.zeros_like(f)
+            B.hhg_learn_stats(h, reset=True)
+            torch.cuda.synchronize()
+            rep = B.hhg_solve(h, f, x, method=method, level=eval_level, dt=B.F64, rtol=1e-8, max_iter=30,
+                              inner_rtol=1e-3, inner_max_iter=60, allow_not_converged=True)
+            st = B.hhg_learn_stats(h)
+            out[name] = {"seconds": round(rep["seconds"], 5), "iterations": rep["iterations"],
+                         "inner_iterations": rep["inner_iterations"],
+                         "rel_residual": float("%.4g" % rep["rel_residual"]), "converged": bool(rep["converged"])}
+            if method == B.SOLVE_STOKES_IR_FGCR_LEARNED:
+                out[name].update({"net_applications": st["applications"], "fallbacks": st["fallbacks"],
+                                  "mean_weight_b_over_a": round(st["alpha_mean"], 4),
+                                  "mean_extra_residual_reduction": round(st["gain_mean"], 5)})
+        out["iterations_saved_vs_vcycle"] = (out["ir_fgcr_uzawa"]["inner_iterations"] -
+                                             out["ir_fgcr_learned"]["inner_iterations"])
+        return out
+    finally:
+        B.hhg_destroy(h)
+
+
 def run_ours(args):
     import torch
 
@@ -605,6 +706,9 @@ def run_ours(args):
     carreau = None if args.no_carreau else carreau_bench(B, torch, args.carreau_level, dev, stream)
     learned = None if args.no_learn else learned_bench(B, torch, dev, stream, args.learn_train_level,
                                                        args.learn_level, args.learn_seeds, 2, 6, args.learn_steps)
+    learned_stokes = None if args.no_learn_stokes else learned_stokes_bench(
+        B, torch, dev, stream, args.learn_train_level, level, args.learn_stokes_fields, 2, 6,
+        args.learn_stokes_steps)
 
     ms_per_step = total_ms / args.steps
     value = world * dofs / (ms_per_step * 1e-3) / 1e9
@@ -663,6 +767,7 @@ def run_ours(args):
         "bf16_coefficient": bf16,
         "nodal_integration": nodal,
         "learned": learned,
+        "learned_stokes": learned_stokes,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -240,7 +240,17 @@ typedef enum {
    * V-cycles, each inner solve to inner_rtol (at most inner_max_iter cycles).  The
    * pressure is shifted to zero mean at the end. */
   HHG_SOLVE_STOKES_UZAWA = 8,
-  HHG_SOLVE_STOKES_IR_UZAWA = 9
+  HHG_SOLVE_STOKES_IR_UZAWA = 9,
+  /* Stokes on a mesh whose nodes lie on an axis-aligned uniform lattice: FP64 iterative
+   * refinement around FP32 flexible GCR (generalised conjugate residual with a variable
+   * preconditioner: each new direction is made K^T K-orthogonal to the stored ones and the
+   * step minimises |r|_2; equal to flexible GMRES in exact arithmetic; restarted after 30
+   * directions), preconditioned by one inexact Uzawa V-cycle from zero (as
+   * HHG_SOLVE_STOKES_UZAWA) plus the learned correction (hhg_learn_*; parameters must be
+   * set), or by the V-cycle alone (IR_FGCR).  Each inner solve runs to inner_rtol (at most
+   * inner_max_iter applications); the pressure is shifted to zero mean at the end. */
+  HHG_SOLVE_STOKES_IR_FGCR_LEARNED = 10,
+  HHG_SOLVE_STOKES_IR_FGCR = 11
 } hhg_solve_method;
 
 typedef struct {
@@ -350,7 +360,11 @@ hhg_status hhg_residual_noalloc(hhg_ctx* ctx, int level, hhg_dtype dt, const voi
 
 /* ------------------------------------------------------------------------------------
  * Learned preconditioner.  Not part of the paper: a small convolutional network that
- * maps what a V-cycle leaves behind to a further correction, used inside flexible CG.
+ * maps what a multigrid cycle leaves behind to a further correction, used inside flexible
+ * CG (elasticity, nc = 3 unknowns per node) or flexible GCR (Stokes, nc = 4: velocity and
+ * pressure).  Below, K is the system operator (A for elasticity, the saddle operator for
+ * Stokes), MG(r) one V-cycle from zero for K e = r (the elasticity V-cycle, or the
+ * inexact Uzawa V-cycle), and vectors have nc*E values.
  *
  * Grid.  The network runs on the node grid of a level: the mesh's nodes must lie on an
  * axis-aligned uniform lattice (Kuhn-split cubes, axis-aligned corner tetrahedra);
@@ -363,20 +377,24 @@ hhg_status hhg_residual_noalloc(hhg_ctx* ctx, int level, hhg_dtype dt, const voi
  * layer l at offset l*6928: W_l[t][i][o] at (t*16 + i)*16 + o (tap t = (dz+1)*9 +
  * (dy+1)*3 + (dx+1), input channel i, output channel o), then b_l[16].
  *
- * Input features per voxel (7 channels): r1/s (3), D z0/s (3), log k - mean log k (1),
- * where for a residual r: z0 = a0 V-cycle(r) with the energy-optimal step length
- * a0 = (v, r)/(v, A v), v = V-cycle(r); r1 = r - A z0; D = point diagonal of A;
- * s = RMS of D z0 over the free nodes.  Output (3 channels): D c / s.  The
- * preconditioned vector is z = a z0 + b c with (a, b) minimising the energy norm of
- * the error A^-1 r - z over span{z0, c} (2x2 normal equations); when that system is
- * singular or not finite, z = z0 (the plain V-cycle direction).  An application never
- * leaves a larger error in that norm than the V-cycle alone.
+ * Input features per voxel (cin = 2 nc + 1 channels: 7 elasticity, 9 Stokes): r1/s (nc),
+ * D z0/s (nc), log k - mean log k (1), where for a residual r: z0 = a0 v, v = MG(r),
+ * with the optimal step length a0 (elasticity: energy norm, a0 = (v, r)/(v, A v);
+ * Stokes: residual norm, a0 = (K v, r)/(K v, K v)); r1 = r - K z0; D = point diagonal
+ * of A (velocity) and, for the pressure, the diagonal Schur surrogate m_i/mu_i + (-C)_ii;
+ * s = RMS of D z0 over the free DoFs (velocity at free nodes, pressure everywhere).
+ * Output (nc channels): D c / s.  The preconditioned vector is z = a z0 + b c with
+ * (a, b) minimising over span{z0, c} the energy norm of the error K^-1 r - z
+ * (elasticity) or the residual norm |r - K z|_2 (Stokes), by 2x2 normal equations; when
+ * that system is singular or not finite, z = z0.  An application never does worse in
+ * that norm than the scaled multigrid step alone.
  *
- * Training pairs.  From an error e: z0 as above for r = A e, e1 = e - z0, r1 = A e1;
- * the pair is (features(r1, z0), target D e1 / s).  hhg_learn_collect takes random
- * errors (`cycles` steps per e0, each continuing from e1); hhg_learn_collect_cg the
- * errors of the plain multigrid-preconditioned CG iterates.
- * Loss: mean squared error over voxels and the 3 output channels; Adam (0.9, 0.999,
+ * Training pairs.  From an error e: z0 as above for r = K e, e1 = e - z0 (Stokes: its
+ * pressure shifted to zero mass-weighted mean), r1 = r - K z0; the pair is
+ * (features(r1, z0), target D e1 / s).  hhg_learn_collect takes random errors (`cycles`
+ * steps per e0, each continuing from e1); hhg_learn_collect_cg the errors of the plain
+ * multigrid-preconditioned Krylov iterates.  Pairs take nc from the problem kind.
+ * Loss: mean squared error over voxels and the nc output channels; Adam (0.9, 0.999,
  * 1e-8) with a cosine learning-rate decay to 5% of lr. */
 int64_t hhg_learn_num_params(void);
 /* Convolution kernel of the network: 0 = warp-level BF16 MMA (mma.sync m16n8k16) on a
@@ -388,7 +406,8 @@ int64_t hhg_learn_num_params(void);
  * results up to FP32 summation order. */
 hhg_status hhg_learn_set_conv_kernel(hhg_ctx* ctx, int kernel);
 /* He-normal initialisation (std sqrt(2/(27*fan_in)), last layer x0.1; BF16 values,
- * zero biases) from a seeded generator; resets the optimiser state. */
+ * zero biases) from a seeded generator, with the input and output channels of the
+ * context's problem kind (7 / 3 elasticity, 9 / 4 Stokes); resets the optimiser state. */
 hhg_status hhg_learn_init(hhg_ctx* ctx, uint64_t seed);
 /* Copy the n = hhg_learn_num_params() FP32 parameters out of / into the context
  * (set: all must be finite; resets the optimiser state; weights are used in BF16). */
@@ -396,27 +415,34 @@ hhg_status hhg_learn_get_params(hhg_ctx* ctx, float* params_host, int64_t n);
 hhg_status hhg_learn_set_params(hhg_ctx* ctx, const float* params_host, int64_t n);
 /* Node-grid dimensions (D, H, W) of a level and its number of voxels with a free node. */
 hhg_status hhg_learn_grid(hhg_ctx* ctx, int level, int* dhw_host, int64_t* free_voxels);
+/* Input and output channels (cin, cout) of the context's problem kind. */
+hhg_status hhg_learn_channels(hhg_ctx* ctx, int* cin_host, int* cout_host);
 /* Network forward pass on B grids of D x H x W voxels: x_dev FP32 [B][D][H][W][cin]
- * (cin <= 16, rounded to BF16), out_dev FP32 [B][D][H][W][3]. */
-hhg_status hhg_learn_forward(hhg_ctx* ctx, const float* x_dev, int cin, int B, int D, int H, int W, float* out_dev);
-/* Loss against target_dev (FP32 [B][D][H][W][3]) and its gradient with respect to all
- * parameters (grad_host: hhg_learn_num_params() floats, nullable), for checking the
- * backward pass.  Waits for the stream. */
-hhg_status hhg_learn_loss_grad(hhg_ctx* ctx, const float* x_dev, int cin, const float* target_dev, int B, int D, int H,
-                               int W, double* loss_host, float* grad_host);
+ * (cin <= 16, rounded to BF16), out_dev FP32 [B][D][H][W][cout] (cout 3 or 4: the first
+ * cout output channels). */
+hhg_status hhg_learn_forward(hhg_ctx* ctx, const float* x_dev, int cin, int cout, int B, int D, int H, int W,
+                             float* out_dev);
+/* Loss against target_dev (FP32 [B][D][H][W][cout], cout 3 or 4) and its gradient with
+ * respect to all parameters (grad_host: hhg_learn_num_params() floats, nullable), for
+ * checking the backward pass.  Waits for the stream. */
+hhg_status hhg_learn_loss_grad(hhg_ctx* ctx, const float* x_dev, int cin, const float* target_dev, int cout, int B,
+                               int D, int H, int W, double* loss_host, float* grad_host);
 /* Allocate storage for `capacity` training pairs of `level` (drops stored pairs). */
 hhg_status hhg_learn_reserve_pairs(hhg_ctx* ctx, int level, int64_t capacity);
-/* Append `cycles` pairs from the error e0_grid_dev (FP32 [D][H][W][3] on the node grid
- * of `level`; Dirichlet nodes are ignored).  Needs hhg_mg_setup.  count_host: pairs stored. */
+/* Append `cycles` pairs from the error e0_grid_dev (FP32 [D][H][W][nc] on the node grid
+ * of `level`; velocity at Dirichlet nodes is ignored).  Needs hhg_mg_setup.  count_host:
+ * pairs stored. */
 hhg_status hhg_learn_collect(hhg_ctx* ctx, int level, const float* e0_grid_dev, int cycles, int64_t* count_host);
-/* Append up to `iters` pairs from the errors of flexible CG with the plain V-cycle on
- * A x = f from x = 0 (f_dev FP32, 3*E, consistent copies; Dirichlet values zero): the
- * library first solves for x* (FP64 refinement to 1e-10), then stores the pair of the
- * error x* - x_k before each preconditioner application k = 0, 1, ...  These are the
- * errors the preconditioner meets inside the solver.  count_host: pairs stored. */
+/* Append up to `iters` pairs from the errors of the flexible Krylov solver (CG,
+ * Stokes: GCR) with the plain V-cycle on K x = f from x = 0 (f_dev FP32, nc*E, consistent
+ * copies; Dirichlet values zero): the library first solves for x* (FP64 refinement to
+ * 1e-10; Stokes: pressure of zero mean), then stores the pair of the error x* - x_k
+ * before each preconditioner application k = 0, 1, ...  These are the errors the
+ * preconditioner meets inside the solver.  count_host: pairs stored. */
 hhg_status hhg_learn_collect_cg(hhg_ctx* ctx, int level, const float* f_dev, int iters, int64_t* count_host);
-/* Copy stored pair `index` to the host: in_host FP32 [D][H][W][7] (the BF16 inputs),
- * target_host FP32 [D][H][W][3] (either nullable).  Waits. */
+/* Copy stored pair `index` to the host: in_host FP32 [D][H][W][2 nc + 1] (the BF16
+ * inputs), target_host FP32 [D][H][W][nc] (either nullable), nc of the stored pairs.
+ * Waits. */
 hhg_status hhg_learn_get_pair(hhg_ctx* ctx, int64_t index, float* in_host, float* target_host);
 
 typedef struct {
@@ -437,8 +463,8 @@ typedef struct {
 /* Train on the stored pairs: each step takes `batch` random crops (pair and origin from
  * the seed), runs the forward and backward passes and one Adam step.  Waits. */
 hhg_status hhg_learn_train(hhg_ctx* ctx, const hhg_learn_train_opts* opts, hhg_learn_train_report* report);
-/* One preconditioner application z = a z0 + b c for the FP32 residual r_dev (3*E)
- * (use_net = 0: z = V-cycle(r), unscaled); alpha_host receives b / a.  Waits. */
+/* One preconditioner application z = a z0 + b c for the FP32 residual r_dev (nc*E)
+ * (use_net = 0: z = MG(r), unscaled); alpha_host receives b / a.  Waits. */
 hhg_status hhg_learn_precondition(hhg_ctx* ctx, int level, int use_net, const void* r_dev, void* z_dev,
                                   double* alpha_host);
 
@@ -446,7 +472,8 @@ typedef struct {
   int64_t applications;  /* preconditioner applications with the network */
   int64_t fallbacks;     /* of which fell back to the V-cycle (b = 0) */
   double alpha_mean, alpha_min, alpha_max;  /* of the weight b / a */
-  double gain_mean;      /* energy reduction added by c, relative to the scaled V-cycle step's */
+  double gain_mean;      /* reduction (energy norm^2; Stokes: residual norm^2) added by c,
+                            relative to the scaled multigrid step's own */
 } hhg_learn_stats_report;
 
 /* Statistics since the last reset (reset != 0 clears them after reading). */

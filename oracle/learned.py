@@ -24,6 +24,15 @@ c = s out / D on free nodes; z = a z0 + b c with (a, b) minimising the energy no
 (e - z, A (e - z)) of the error e = A^-1 r (the 2x2 normal equations need only r).
 Training pair from an error e: z0 as above for r = A e, e1 = e - z0, r1 = A e1,
 target D e1 / s.
+
+Stokes (``stokes_*``; vectors (N, 4): velocity, then pressure; K the saddle operator with
+velocity-Dirichlet identity rows, v = one inexact Uzawa V-cycle of the residual): the
+same with 4 components, CIN = 9 input channels (r1/s, D z0/s, log mu) and 4 outputs,
+where D is the velocity point diagonal and, for the pressure, the Schur surrogate
+m_i / mu_i + (-C)_ii; s is the RMS of D z0 over the free velocity DoFs and all
+pressures; and, K being indefinite, the residual norm replaces the energy norm: z0 = a0 v
+with a0 = (K v, r) / (K v, K v), and (a, b) minimise |r - K (a z0 + b c)|_2.  The
+training error e1 = e - z0 has its pressure shifted to zero mass-weighted mean.
 """
 
 from __future__ import annotations
@@ -81,7 +90,7 @@ def conv_weight_grad(a, g):
     return dW
 
 
-def init_params(seed, cin0=CIN):
+def init_params(seed, cin0=CIN, cout=COUT):
     """He-style initialisation (BF16-rounded weights, zero biases)."""
     rng = np.random.default_rng(seed)
     Ws, bs = [], []
@@ -90,15 +99,15 @@ def init_params(seed, cin0=CIN):
         W = np.zeros((27, C, C))
         W[:, :cin, :] = rng.normal(size=(27, cin, C)) * np.sqrt(2.0 / (27 * cin))
         if l == NLAYERS - 1:
-            W[:, :, COUT:] = 0.0
+            W[:, :, cout:] = 0.0
             W *= 0.1
         Ws.append(bf16(W))
         bs.append(np.zeros(C))
     return Ws, bs
 
 
-def forward(x, Ws, bs, round_bf16=True):
-    """x: (B, D, H, X, cin <= 16) -> (out (B, D, H, X, 3), activations)."""
+def forward(x, Ws, bs, round_bf16=True, cout=COUT):
+    """x: (B, D, H, X, cin <= 16) -> (out (B, D, H, X, cout), activations)."""
     rnd = bf16 if round_bf16 else (lambda v: np.asarray(v, dtype=np.float64))
     a = np.zeros(x.shape[:4] + (C,))
     a[..., :x.shape[-1]] = rnd(x)
@@ -109,18 +118,18 @@ def forward(x, Ws, bs, round_bf16=True):
             acts.append(rnd(np.maximum(z, 0.0)))
         else:
             out = z
-    return out[..., :COUT], acts
+    return out[..., :cout], acts
 
 
-def loss_and_grads(x, target, Ws, bs, round_bf16=True):
+def loss_and_grads(x, target, Ws, bs, round_bf16=True, cout=COUT):
     """MSE loss and its gradients w.r.t. all weights and biases (the BF16 rounding of the
     activations is treated as identity in the backward pass, as on the GPU)."""
-    out, acts = forward(x, Ws, bs, round_bf16)
+    out, acts = forward(x, Ws, bs, round_bf16, cout)
     n = out.size
     diff = out - target
     loss = float((diff**2).sum() / n)
     g = np.zeros(out.shape[:4] + (C,))
-    g[..., :COUT] = 2.0 * diff / n
+    g[..., :cout] = 2.0 * diff / n
     dWs, dbs = [None] * NLAYERS, [None] * NLAYERS
     for l in reversed(range(NLAYERS)):
         dWs[l] = conv_weight_grad(acts[l], g)
@@ -205,4 +214,81 @@ def training_pair(A, dirichlet, vox, dims, k, e, vcycle):
     X, s = features(vox, dims, dirichlet, k, r1, z0, Dg)
     T = np.zeros((1,) + dims + (COUT,))
     T[0, vox[fr, 0], vox[fr, 1], vox[fr, 2], :] = (Dg * e1 / s)[fr]
+    return X, T, e1
+
+
+# ------------------------------------------------------------------------------ Stokes
+
+STOKES_CIN, STOKES_COUT = 9, 4
+
+
+def stokes_diag(H, l):
+    """(N, 4) diagonal D of the features: velocity point diagonal of A (1 on Dirichlet
+    rows), then the Schur surrogate."""
+    N = H.lv[l].num_nodes
+    D = np.empty((N, 4))
+    D[:, :3] = H.A[l].diagonal().reshape(N, 3)
+    D[H.lv[l].dirichlet, :3] = 1.0
+    D[:, 3] = H.s[l]
+    return D
+
+
+def stokes_features(vox, dims, dirichlet, k, r1, z0, D):
+    """Input grid (1, D, H, W, 9) and the scale s for (N, 4) fields r1, z0, D."""
+    on = np.ones(z0.shape, dtype=bool)
+    on[np.asarray(dirichlet), :3] = False
+    w = (D * z0)[on]
+    s2 = (w**2).sum() / max(on.sum(), 1)
+    s = np.sqrt(s2) if s2 > 0 else 1.0
+    X = np.zeros((1,) + dims + (STOKES_CIN,))
+    lk = np.log(k)
+    X[0, vox[:, 0], vox[:, 1], vox[:, 2], 8] = lk - lk.mean()
+    f = np.zeros((len(k), 8))
+    f[:, :4] = np.where(on, r1 / s, 0.0)
+    f[:, 4:] = np.where(on, D * z0 / s, 0.0)
+    X[0, vox[:, 0], vox[:, 1], vox[:, 2], :8] = f
+    return X, s
+
+
+def _stokes_scaled_step(H, l, r, v):
+    """Residual-optimal multiple a0 v of the cycle output v for the residual r, and K a0 v."""
+    Kv = H.apply(l, v)
+    den = H.dot(l, Kv, Kv)
+    a0 = H.dot(l, Kv, r) / den if den > 0 else 1.0
+    return a0 * v, a0 * Kv
+
+
+def stokes_correction(H, l, vox, dims, k, r, v, Ws, bs):
+    """(z, b/a, c) of the Stokes learned preconditioner for residual r given v = MG(r):
+    z0 = a0 v, c from the network, z = a z0 + b c minimising |r - K z|_2."""
+    d = H.lv[l].dirichlet
+    D = stokes_diag(H, l)
+    z0, Kz0 = _stokes_scaled_step(H, l, r, v)
+    r1 = r - Kz0
+    r1[d, :3] = 0.0
+    X, s = stokes_features(vox, dims, d, k, r1, z0, D)
+    out, _ = forward(X, Ws, bs, cout=STOKES_COUT)
+    c = s * out[0, vox[:, 0], vox[:, 1], vox[:, 2], :] / D
+    c[d, :3] = 0.0
+    Kc = H.apply(l, c)
+    M = np.array([[H.dot(l, Kz0, Kz0), H.dot(l, Kc, Kz0)], [H.dot(l, Kc, Kz0), H.dot(l, Kc, Kc)]])
+    rhs = np.array([H.dot(l, Kz0, r), H.dot(l, Kc, r)])
+    a, b = np.linalg.solve(M, rhs)
+    return a * z0 + b * c, b / a, c
+
+
+def stokes_training_pair(H, l, vox, dims, k, e, mg):
+    """(inputs (1, D, H, W, 9), target (1, D, H, W, 4), e1) of one multigrid step from the
+    error e ((N, 4), zero velocity on Dirichlet nodes); mg(r) = one V-cycle from zero."""
+    d = H.lv[l].dirichlet
+    D = stokes_diag(H, l)
+    r = H.residual(l, np.zeros_like(e), -e)  # K e with zero velocity-Dirichlet rows
+    z0, _ = _stokes_scaled_step(H, l, r, mg(r))
+    e1 = H.project_pressure(l, e - z0)
+    r1 = H.residual(l, np.zeros_like(e1), -e1)
+    X, s = stokes_features(vox, dims, d, k, r1, z0, D)
+    on = np.ones(e.shape, dtype=bool)
+    on[d, :3] = False
+    T = np.zeros((1,) + dims + (STOKES_COUT,))
+    T[0, vox[:, 0], vox[:, 1], vox[:, 2], :] = np.where(on, D * e1 / s, 0.0)
     return X, T, e1

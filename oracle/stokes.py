@@ -88,3 +88,138 @@ def residual(Kbc, dirichlet, f, x):
     ru = r[:3 * N].reshape(N, 3)
     ru[np.asarray(dirichlet)] = 0.0
     return r
+
+
+# ------------------------------------------------------- inexact Uzawa multigrid (Sec. 5.2)
+#
+# The paper solves its Stokes systems with an all-at-once multigrid whose smoother is an
+# inexact Uzawa iteration: a velocity smoothing with the pressure fixed, then a damped
+# pressure update with an approximation of the Schur complement S = C - B A^-1 B^T;
+# V-cycles with more smoothing steps on coarser levels.  The library's choices, restated
+# here one step at a time (vectors (N, 4): velocity node-major, then the pressure):
+#   * velocity smoothing: `vsteps` Chebyshev steps on D^-1 A (A the velocity block with
+#     Dirichlet identity rows, interval [lo, hi] * lambda_max) for A du = r_u from du = 0;
+#   * pressure update: p -= omega (g - B u - C p) / s,  s_i = m_i / mu_i + (-C)_ii
+#     (m the lumped mass, a diagonal surrogate of -S);
+#   * V-cycle on level l: pre + extra (lmax - l) steps, restriction of the saddle residual
+#     (velocity: P^T with Dirichlet rows zeroed; pressure: P^T), recursion from zero,
+#     prolongation x += P x_c (both fields), post + extra (lmax - l) steps;
+#   * coarsest level: exact solve on the free velocity and all pressure DoFs with
+#     beta / N_p added to every pressure-pressure entry (beta = the largest absolute entry),
+#     which removes the constant-pressure kernel.
+
+
+def pack4(x4):
+    """(N, 4) node-major (u, v, w, p) -> the packed ordering of stokes_operator."""
+    x4 = np.asarray(x4, dtype=np.float64)
+    return np.concatenate([x4[:, :3].reshape(-1), x4[:, 3]])
+
+
+def unpack4(x, N):
+    out = np.empty((N, 4))
+    out[:, :3] = x[:3 * N].reshape(N, 3)
+    out[:, 3] = x[3 * N:]
+    return out
+
+
+def schur_surrogate(mm: MacroMesh, lv: Level, mu):
+    """s_i = m_i / mu_i + (-C)_ii."""
+    C = stabilisation_matrix(mm, lv)
+    return lumped_mass(lv) / np.asarray(mu) - C.diagonal()
+
+
+class UzawaHierarchy:
+    """Levels of one macro mesh with the saddle operator K (velocity-Dirichlet identity
+    rows), its velocity block A, the Schur surrogate s, the lumped mass and the linear
+    interpolation P between consecutive levels; the viscosity at every level is mu_fun at
+    that level's nodes (injection, the nodes of a coarse level being fine nodes)."""
+
+    def __init__(self, mm: MacroMesh, levels, mu_fun):
+        from .mesh import build_level, prolongation_parents
+        from .solvers import prolongation
+
+        self.mm = mm
+        self.levels = sorted(levels)
+        self.lv, self.K, self.A, self.s, self.m = {}, {}, {}, {}, {}
+        for l in self.levels:
+            lv = build_level(mm, l)
+            mu = mu_fun(lv.coords)
+            Kbc, _ = stokes_operator(mm, lv, mu)
+            N = lv.num_nodes
+            self.lv[l] = lv
+            self.K[l] = Kbc
+            self.A[l] = Kbc[:3 * N, :3 * N].tocsr()
+            self.s[l] = schur_surrogate(mm, lv, mu)
+            self.m[l] = lumped_mass(lv)
+        self.P = {}
+        for l in self.levels[1:]:
+            par = prolongation_parents(mm, self.lv[l - 1], self.lv[l])
+            self.P[l] = prolongation(self.lv[l - 1], self.lv[l], par)
+
+    def apply(self, l, x4):
+        return unpack4(self.K[l] @ pack4(x4), self.lv[l].num_nodes)
+
+    def residual(self, l, f4, x4):
+        r = np.asarray(f4, dtype=np.float64) - self.apply(l, x4)
+        r[self.lv[l].dirichlet, :3] = 0.0
+        return r
+
+    def dot(self, l, a, b):
+        """Inner product over the free velocity DoFs and all pressures."""
+        fr = ~self.lv[l].dirichlet
+        return float((a[fr, :3] * b[fr, :3]).sum() + (a[:, 3] * b[:, 3]).sum())
+
+    def project_pressure(self, l, x4):
+        """Shift the pressure to zero mass-weighted mean."""
+        x4 = np.array(x4, dtype=np.float64)
+        m = self.m[l]
+        x4[:, 3] -= (m * x4[:, 3]).sum() / m.sum()
+        return x4
+
+    def coarse_solve(self, f4):
+        l = self.levels[0]
+        lv = self.lv[l]
+        N = lv.num_nodes
+        vel = np.repeat(~lv.dirichlet, 3)
+        keep = np.concatenate([vel, np.ones(N, dtype=bool)])
+        Kd = self.K[l].toarray()[np.ix_(keep, keep)]
+        beta = np.abs(Kd).max()
+        nv = int(vel.sum())
+        Kd[nv:, nv:] += beta / N
+        x = np.zeros(4 * N)
+        x[keep] = np.linalg.solve(Kd, pack4(f4)[keep])
+        return unpack4(x, N)
+
+    def uzawa_step(self, l, f4, x4, lam, vsteps=2, omega=0.5, lo=1 / 8, hi=1.1):
+        from .solvers import chebyshev
+
+        d = self.lv[l].dirichlet
+        x4 = np.array(x4, dtype=np.float64)
+        r = self.residual(l, f4, x4)
+        du = chebyshev(self.A[l], d, r[:, :3], np.zeros((len(d), 3)), lam[l], lo, hi, vsteps)
+        x4[:, :3] += du
+        r = self.residual(l, f4, x4)
+        x4[:, 3] -= omega * r[:, 3] / self.s[l]
+        return x4
+
+    def vcycle(self, l, f4, x4, lam, lmax, pre=3, post=3, extra=2, vsteps=2, omega=0.5, lo=1 / 8, hi=1.1):
+        """One variable V-cycle on level l (lmax: the finest level, for the extra steps)."""
+        from .solvers import restrict
+
+        if l == self.levels[0]:
+            return self.coarse_solve(f4)
+        x4 = np.array(x4, dtype=np.float64)
+        ex = extra * (lmax - l)
+        for _ in range(pre + ex):
+            x4 = self.uzawa_step(l, f4, x4, lam, vsteps, omega, lo, hi)
+        r = self.residual(l, f4, x4)
+        Nc = self.lv[l - 1].num_nodes
+        rc = np.zeros((Nc, 4))
+        rc[:, :3] = restrict(self.P[l], r[:, :3], self.lv[l].dirichlet, self.lv[l - 1].dirichlet)
+        rc[:, 3] = self.P[l].T @ r[:, 3]
+        ec = self.vcycle(l - 1, rc, np.zeros((Nc, 4)), lam, lmax, pre, post, extra, vsteps, omega, lo, hi)
+        x4[:, :3] += self.P[l] @ ec[:, :3]
+        x4[:, 3] += self.P[l] @ ec[:, 3]
+        for _ in range(post + ex):
+            x4 = self.uzawa_step(l, f4, x4, lam, vsteps, omega, lo, hi)
+        return x4

@@ -35,6 +35,7 @@ COARSE_INJECT, COARSE_MEAN, COARSE_HARMONIC = 0, 1, 2
 SOLVE_PCG_JACOBI, SOLVE_MG_CG, SOLVE_IR_MG_CG, SOLVE_MG, SOLVE_STOKES_MINRES, SOLVE_STOKES_IR_MINRES = 0, 1, 2, 3, 4, 5
 SOLVE_IR_FCG_LEARNED, SOLVE_IR_FCG = 6, 7
 SOLVE_STOKES_UZAWA, SOLVE_STOKES_IR_UZAWA = 8, 9
+SOLVE_STOKES_IR_FGCR_LEARNED, SOLVE_STOKES_IR_FGCR = 10, 11
 
 
 class hhg_mg_params(C.Structure):
@@ -141,8 +142,9 @@ _SIGS = {
     "hhg_learn_get_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "hhg_learn_set_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "hhg_learn_grid": [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int64)],
-    "hhg_learn_forward": [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p],
-    "hhg_learn_loss_grad": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+    "hhg_learn_channels": [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "hhg_learn_forward": [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p],
+    "hhg_learn_loss_grad": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                             C.POINTER(C.c_double), C.c_void_p],
     "hhg_learn_reserve_pairs": [C.c_void_p, C.c_int, C.c_int64],
     "hhg_learn_collect": [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int64)],
@@ -416,15 +418,23 @@ def hhg_learn_grid(ctx, level):
     return tuple(int(v) for v in dhw), nf.value
 
 
-def hhg_learn_forward(ctx, x, cin, B, D, H, W, out):
-    _check(ctx, load().hhg_learn_forward(ctx, _ptr(x), cin, B, D, H, W, _ptr(out)))
+def hhg_learn_channels(ctx):
+    """(input, output) channels of the network for the context's problem kind."""
+    ci, co = C.c_int(), C.c_int()
+    _check(ctx, load().hhg_learn_channels(ctx, C.byref(ci), C.byref(co)))
+    return ci.value, co.value
 
 
-def hhg_learn_loss_grad(ctx, x, cin, target, B, D, H, W):
+def hhg_learn_forward(ctx, x, cin, B, D, H, W, out, cout=3):
+    _check(ctx, load().hhg_learn_forward(ctx, _ptr(x), cin, cout, B, D, H, W, _ptr(out)))
+
+
+def hhg_learn_loss_grad(ctx, x, cin, target, B, D, H, W, cout=3):
     """(loss, gradient as FP32 numpy array in the parameter layout)."""
     loss = C.c_double()
     g = np.empty(hhg_learn_num_params(), dtype=np.float32)
-    _check(ctx, load().hhg_learn_loss_grad(ctx, _ptr(x), cin, _ptr(target), B, D, H, W, C.byref(loss), g.ctypes.data))
+    _check(ctx, load().hhg_learn_loss_grad(ctx, _ptr(x), cin, _ptr(target), cout, B, D, H, W, C.byref(loss),
+                                           g.ctypes.data))
     return loss.value, g
 
 
@@ -444,11 +454,12 @@ def hhg_learn_collect_cg(ctx, level, f, iters):
     return n.value
 
 
-def hhg_learn_get_pair(ctx, index, dhw):
-    """(inputs FP32 (D, H, W, 7), targets FP32 (D, H, W, 3)) of stored pair `index`."""
+def hhg_learn_get_pair(ctx, index, dhw, nc=3):
+    """(inputs FP32 (D, H, W, 2 nc + 1), targets FP32 (D, H, W, nc)) of stored pair `index`
+    (nc = 3 elasticity, 4 Stokes)."""
     D, H, W = dhw
-    x = np.empty((D, H, W, 7), dtype=np.float32)
-    y = np.empty((D, H, W, 3), dtype=np.float32)
+    x = np.empty((D, H, W, 2 * nc + 1), dtype=np.float32)
+    y = np.empty((D, H, W, nc), dtype=np.float32)
     _check(ctx, load().hhg_learn_get_pair(ctx, int(index), x.ctypes.data, y.ctypes.data))
     return x, y
 
@@ -461,7 +472,7 @@ def hhg_learn_train(ctx, steps, batch, crop, lr=2e-3, seed=0):
 
 
 def hhg_learn_precondition(ctx, level, use_net, r, z):
-    """z = a V-cycle step + b correction (FP32 library-layout vectors); returns b / a."""
+    """z = a multigrid step + b correction (FP32 library-layout vectors); returns b / a."""
     a = C.c_double()
     _check(ctx, load().hhg_learn_precondition(ctx, level, int(use_net), _ptr(r), _ptr(z), C.byref(a)))
     return a.value

@@ -157,11 +157,19 @@ struct LevelHost {
 // preconditioner): voxel g = (z * H + y) * W + x.
 struct LearnGrid {
   int D = 0, H = 0, W = 0;
-  int64_t V = 0, nfree = 0;
+  int64_t V = 0, nfree = 0, nnode = 0;  // voxels; with a free node; with a node
   int64_t coeff_version = -1;  // of the log-coefficient feature
   DevMem gent, gfree, e2g, efree, logk;
-  DevMem lw[13];  // FP32 work vectors (3*E) of the learned preconditioner and its FCG
-  DevMem lw64[2]; // FP64 work vectors (3*E) of the pair collection
+  DevMem lw[13];  // FP32 work vectors (4*E) of the learned preconditioner and its Krylov solvers
+  DevMem lw64[2]; // FP64 work vectors (4*E) of the pair collection
+  // Stokes: inverse diagonal of the features (velocity point diagonal, pressure Schur
+  // surrogate; 4*E) and the coefficient version it was computed for
+  DevMem dinv4;
+  int64_t dinv4_version = -1;
+  // flexible GCR search directions p_j and K p_j (4*E each; the solver restarts after
+  // GCR_DIRS directions)
+  static constexpr int GCR_DIRS = 30;
+  DevMem gcr_p[GCR_DIRS], gcr_q[GCR_DIRS];
 };
 
 // Learned preconditioner: network parameters, optimiser state, training pairs, buffers.
@@ -172,8 +180,9 @@ struct LearnState {
   DevMem fwd_u, bwd_u;                   // tcgen05 operands, LN_LAYERS * LN_UMMA bytes
   int conv_kernel = 0;                   // 0 warp MMA, 1 tcgen05 per tile, 2 TMA + tcgen05 pipeline
   std::map<int, std::unique_ptr<LearnGrid>> grids;
-  // training pairs of one level: inputs (LN_PAIR_IN BF16 per voxel) and targets (3 FP32)
-  int pair_level = -1;
+  // training pairs of one level: inputs (ln_pair_in(pair_nc) BF16 per voxel) and targets
+  // (pair_nc FP32), pair_nc = components of the problem they came from
+  int pair_level = -1, pair_nc = 3;
   int64_t pair_cap = 0, pair_count = 0;
   DevMem pin, ptg;
   // activation buffers (16-channel BF16), outputs, gradients, partial sums

@@ -1,23 +1,28 @@
 // Learned preconditioner of libhhgs (not part of the paper): a 4-layer 3x3x3 conv net
 // with 16 channels on the node grid, trained on the GPU on residual/error pairs that the
-// multigrid solver itself produces, and used inside flexible CG as a correction after
-// the V-cycle.  Kernels in hhg_learn.cu; conventions in hhg_learn.h.
+// multigrid solver itself produces, and used inside a flexible Krylov solver as a
+// correction after the multigrid cycle: flexible CG after the V-cycle for elasticity
+// (nc = 3 unknowns per node), flexible GCR after the inexact Uzawa V-cycle for Stokes
+// (nc = 4: velocity and pressure).  Kernels in hhg_learn.cu; conventions in hhg_learn.h.
 //
-// Preconditioner application for a residual r (FP32):
-//   z0 = a0 V-cycle(r), a0 = energy-optimal step length (z0, r) / (z0, A z0) of the V-cycle,
-//   r1 = r - A z0       (the residual the scaled V-cycle step leaves; (z0, r1) = 0),
+// Preconditioner application for a residual r (FP32), K the system operator, MG one cycle:
+//   z0 = a0 MG(r), a0 = optimal step length of the cycle's output: in the energy norm
+//        (elasticity, a0 = (z0, r) / (z0, K z0)) or the residual norm (Stokes, whose
+//        operator is indefinite: a0 = (K z0, r) / (K z0, K z0)),
+//   r1 = r - K z0       (the residual the scaled step leaves),
 //   c  = s D^-1 N(features(r1, z0, log k))   (network correction),
-//   z  = a z0 + b c,  (a, b) minimising the energy norm of the error A^-1 r - z over
-//        span{z0, c}  (2x2 normal equations).
-// Hence an application never leaves a larger error (in that norm) than the V-cycle alone,
-// and the network is not rewarded for what a rescaling of z0 would do (CG is invariant
-// to that); when the 2x2 system is singular or not finite the application falls back to
-// z = z0.
+//   z  = a z0 + b c,  (a, b) minimising the same norm (of the error K^-1 r - z, resp. of
+//        the residual r - K z) over span{z0, c}  (2x2 normal equations).
+// Hence an application never does worse (in that norm) than the scaled cycle alone, and
+// the network is not rewarded for what a rescaling of z0 would do (the Krylov solvers are
+// invariant to that); when the 2x2 system is singular or not finite the application falls
+// back to z = z0.
 //
-// Training pairs: for an error e, one multigrid step gives z0 = a0 V-cycle(A e), the
-// remaining error e1 = e - z0 and residual r1 = A e1; the pair is (features(r1, z0),
-// D e1 / s).  The errors are either random (further steps continue from e1) or the
-// errors of the plain multigrid-preconditioned CG iterates (hhg_learn_collect_cg).
+// Training pairs: for an error e, one multigrid step gives z0 = a0 MG(K e), the
+// remaining error e1 = e - z0 (Stokes: pressure shifted to zero mean, the constant being
+// invisible to K) and residual r1 = K e1; the pair is (features(r1, z0), D e1 / s).  The
+// errors are either random (further steps continue from e1) or the errors of the plain
+// multigrid-preconditioned Krylov iterates (hhg_learn_collect_cg).
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -66,7 +71,31 @@ float round_bf16(float x) {
 
 void need_elasticity(hhg_ctx* c) {
   need_ready(c, true);
-  if (c->prob.kind != HHG_ELASTICITY) THROW(HHG_ERR_UNSUPPORTED, "the learned preconditioner needs an elasticity problem");
+  if (c->prob.kind != HHG_ELASTICITY) THROW(HHG_ERR_UNSUPPORTED, "flexible CG needs an elasticity problem");
+}
+
+bool is_stokes(hhg_ctx* c) { return c->prob.kind == HHG_STOKES; }
+int ncomp(hhg_ctx* c) { return is_stokes(c) ? 4 : 3; }
+
+// the system operator K of the problem kind, its inner product over the unique free DoFs,
+// its residual (returns |r|^2) and one multigrid cycle from zero, all FP32
+void sys_apply(hhg_ctx* c, int l, const float* x, float* y) {
+  if (is_stokes(c))
+    stokes_apply32(c, l, x, y);
+  else
+    apply32(c, l, x, y);
+}
+double sys_dot(hhg_ctx* c, int l, const float* a, const float* b) {
+  return is_stokes(c) ? stokes_dot32(c, l, a, b) : dot32(c, l, a, b);
+}
+double sys_residual(hhg_ctx* c, int l, const float* f, const float* x, float* r) {
+  return is_stokes(c) ? stokes_residual32(c, l, f, x, r) : residual32(c, l, f, x, r);
+}
+void sys_mg(hhg_ctx* c, int l, const float* r, float* z) {
+  if (is_stokes(c))
+    uzawa_zero32(c, l, r, z);
+  else
+    vcycle_zero32(c, l, r, z);
 }
 
 void need_params(LearnState& S) {
@@ -118,14 +147,14 @@ void upload_params(hhg_ctx* c, LearnState& S, const std::vector<float>& h) {
   S.have_params = true;
 }
 
-// activation buffers for V voxels
+// activation buffers for V voxels (outputs and targets of up to 4 channels)
 void ensure_acts(hhg_ctx* c, LearnState& S, int64_t V) {
   if (S.act_voxels >= V) return;
   const size_t b16 = (size_t)V * LN_C * 2;
   for (auto& a : S.act) CK(a.alloc(b16));
   for (auto& g : S.gb) CK(g.alloc(b16));
-  CK(S.out.alloc((size_t)V * LN_COUT * sizeof(float)));
-  CK(S.tgt.alloc((size_t)V * LN_COUT * sizeof(float)));
+  CK(S.out.alloc((size_t)V * 4 * sizeof(float)));
+  CK(S.tgt.alloc((size_t)V * 4 * sizeof(float)));
   CK(S.dpart.alloc((size_t)std::max<int64_t>(mse_partials(V), 1) * sizeof(double)));
   S.act_voxels = V;
 }
@@ -154,29 +183,31 @@ void conv(hhg_ctx* c, LearnState& S, int l, bool bwd, const void* X, const float
     CK(launch_conv(X, wp, S.conv_kernel == 1 ? wu : nullptr, bias, Y, Yf, nf, mask, s, relu, c->stream));
 }
 
-// forward pass from act[0]: act[1..3] = hidden activations, out = FP32 output channels
-void forward(hhg_ctx* c, LearnState& S, GridShape s, float* out) {
+// forward pass from act[0]: act[1..3] = hidden activations, out = the first nout FP32
+// output channels
+void forward(hhg_ctx* c, LearnState& S, GridShape s, float* out, int nout) {
   for (int l = 0; l < LN_LAYERS; ++l) {
     const bool last = l == LN_LAYERS - 1;
-    conv(c, S, l, false, S.act[l].p, layer_bias(S, l), last ? nullptr : S.act[l + 1].p, last ? out : nullptr, LN_COUT,
+    conv(c, S, l, false, S.act[l].p, layer_bias(S, l), last ? nullptr : S.act[l + 1].p, last ? out : nullptr, nout,
          nullptr, s, last ? 0 : 1);
   }
 }
 
 // inference with two activation buffers (act[0] holds the input; act[0] and act[1] alternate)
-void forward_inference(hhg_ctx* c, LearnState& S, GridShape s, float* out) {
+void forward_inference(hhg_ctx* c, LearnState& S, GridShape s, float* out, int nout) {
   for (int l = 0; l < LN_LAYERS; ++l) {
     const bool last = l == LN_LAYERS - 1;
     conv(c, S, l, false, S.act[l & 1].p, layer_bias(S, l), last ? nullptr : S.act[(l + 1) & 1].p,
-         last ? out : nullptr, LN_COUT, nullptr, s, last ? 0 : 1);
+         last ? out : nullptr, nout, nullptr, s, last ? 0 : 1);
   }
 }
 
-// backward pass after forward(): MSE against tgt into *loss (device), gradients into S.grad
-void backward(hhg_ctx* c, LearnState& S, GridShape s, const float* out, const float* tgt, double* loss) {
+// backward pass after forward(): MSE over nout channels against tgt into *loss (device),
+// gradients into S.grad
+void backward(hhg_ctx* c, LearnState& S, GridShape s, const float* out, const float* tgt, int nout, double* loss) {
   const int64_t V = s.voxels();
   ensure_grad_scratch(c, S, s);
-  CK(launch_mse(out, tgt, V, S.gb[0].p, S.dpart.as<double>(), loss, c->stream));
+  CK(launch_mse(out, tgt, V, nout, S.gb[0].p, S.dpart.as<double>(), loss, c->stream));
   int cur = 0;
   for (int l = LN_LAYERS - 1; l >= 0; --l) {
     float* gW = S.grad.as<float>() + (int64_t)l * LN_LSIZE;
@@ -266,7 +297,10 @@ LearnGrid& grid(hhg_ctx* c, int l) {
             }
           }
     }
-    for (int64_t g = 0; g < V; ++g) G->nfree += gfree[g];
+    for (int64_t g = 0; g < V; ++g) {
+      G->nfree += gfree[g];
+      G->nnode += gent[g] >= 0;
+    }
     upload(G->gent, gent);
     upload(G->gfree, gfree);
     upload(G->e2g, e2g);
@@ -300,41 +334,73 @@ LearnGrid& grid(hhg_ctx* c, int l) {
   return *G;
 }
 
+// work vector q of the grid's level (4*E floats: room for either problem kind)
 float* lwork(hhg_ctx* c, LearnGrid& G, int l, int q) {
   if (!G.lw[q].p) {
-    const size_t b = 3 * (size_t)c->lv(l).entries * sizeof(float);
+    const size_t b = 4 * (size_t)c->lv(l).entries * sizeof(float);
     CK(G.lw[q].alloc(b));
     CK(cudaMemsetAsync(G.lw[q].p, 0, b, c->stream));
   }
   return G.lw[q].as<float>();
 }
 
+int64_t sys_n(hhg_ctx* c, int l) { return ncomp(c) * c->lv(l).entries; }
+
 void copy32(hhg_ctx* c, int l, const float* src, float* dst) {
-  CK(cudaMemcpyAsync(dst, src, 3 * (size_t)c->lv(l).entries * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(dst, src, sys_n(c, l) * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
 }
 
-// Scale the V-cycle correction z0 (and A z0) to its energy-optimal length for the residual
-// r: z0 <- a0 z0 with a0 = (z0, r) / (z0, A z0) (unchanged when that is not finite).
-// Returns (z0, r) after scaling.
-double scale_vcycle_step(hhg_ctx* c, int l, const float* r, float* z0, float* az0) {
-  const int64_t n = 3 * c->lv(l).entries;
-  const double zr = dot32(c, l, z0, r), zaz = dot32(c, l, z0, az0);
-  const double a0 = (zaz > 0.0 && std::isfinite(zr / zaz)) ? zr / zaz : 1.0;
+// Inverse diagonal D^-1 of the features (nc*E): elasticity the point diagonal of A; Stokes
+// that of the velocity block, then 1 / (m_i / mu_i + (-C)_ii) for the pressure (recomputed
+// when the coefficient changes).
+const float* sys_dinv(hhg_ctx* c, int l, LearnGrid& G) {
+  if (!is_stokes(c)) return dinv32(c, l);
+  if (!G.dinv4.p || G.dinv4_version != c->coeff_version) {
+    const int64_t E = c->lv(l).entries;
+    if (!G.dinv4.p) CK(G.dinv4.alloc(4 * (size_t)E * sizeof(float)));
+    float* d = G.dinv4.as<float>();
+    CK(cudaMemcpyAsync(d, dinv32(c, l), 3 * (size_t)E * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemsetAsync(d + 3 * E, 0, (size_t)E * sizeof(float), c->stream));
+    CK(launch_add_const<float>(E, 1.f, d + 3 * E, c->stream));
+    schur_inv32(c, l, d + 3 * E, d + 3 * E);
+    G.dinv4_version = c->coeff_version;
+  }
+  return G.dinv4.as<float>();
+}
+
+// number of free DoFs on the grid (the feature scale s is an RMS over them)
+double feature_count(hhg_ctx* c, const LearnGrid& G) {
+  return std::max(1.0, 3.0 * (double)G.nfree + (is_stokes(c) ? (double)G.nnode : 0.0));
+}
+
+// Scale the multigrid correction z0 (and K z0) to its optimal length for the residual r:
+// z0 <- a0 z0 with a0 = (z0, r) / (z0, K z0) (energy norm; elasticity) or
+// a0 = (K z0, r) / (K z0, K z0) (residual norm; Stokes), unchanged when that is not
+// finite.  Returns the reduction of the squared norm by the scaled step, (z0, r) resp.
+// (K z0, r) after scaling.
+double scale_mg_step(hhg_ctx* c, int l, const float* r, float* z0, float* az0) {
+  const int64_t n = sys_n(c, l);
+  const bool st = is_stokes(c);
+  const double num = st ? sys_dot(c, l, az0, r) : sys_dot(c, l, z0, r);
+  const double den = st ? sys_dot(c, l, az0, az0) : sys_dot(c, l, z0, az0);
+  const double a0 = (den > 0.0 && std::isfinite(num / den)) ? num / den : 1.0;
   CK(launch_axpby<float>(n, (float)a0, z0, 0.f, z0, c->stream));
   CK(launch_axpby<float>(n, (float)a0, az0, 0.f, az0, c->stream));
-  return a0 * zr;
+  return a0 * num;
 }
 
-// z and az = A z of one preconditioner application (see the file comment); use_net = false:
-// z = z0.  Returns the weight b / a of the correction in z = a z0 + b c.
+// z and az = K z of one preconditioner application (see the file comment); use_net =
+// false: z = z0 = MG(r), unscaled.  Returns the weight b / a of the correction in z = a z0 + b c.
 double precondition(hhg_ctx* c, int l, const float* r, float* z, float* az, bool use_net) {
   LearnState& S = state(c);
   LearnGrid& G = grid(c, l);
-  const int64_t E = c->lv(l).entries, n = 3 * E;
+  const bool st = is_stokes(c);
+  const int nc = ncomp(c);
+  const int64_t E = c->lv(l).entries, n = nc * E;
   float* z0 = lwork(c, G, l, LW_Z0);
   float* az0 = lwork(c, G, l, LW_AZ0);
-  vcycle_zero32(c, l, r, z0);
-  apply32(c, l, z0, az0);
+  sys_mg(c, l, r, z0);
+  sys_apply(c, l, z0, az0);
   if (!use_net) {
     copy32(c, l, z0, z);
     copy32(c, l, az0, az);
@@ -344,23 +410,28 @@ double precondition(hhg_ctx* c, int l, const float* r, float* z, float* az, bool
   float* r1 = lwork(c, G, l, LW_R1);
   float* cc = lwork(c, G, l, LW_C);
   float* acc = lwork(c, G, l, LW_AC);
-  const float* dinv = dinv32(c, l);
+  const float* dinv = sys_dinv(c, l, G);
   ensure_acts(c, S, G.V);
-  const double rv = scale_vcycle_step(c, l, r, z0, az0);  // (z0, r) = (z0, A z0) after scaling
+  // after scaling, the first normal-equation entry and right-hand side are both rv
+  const double rv = scale_mg_step(c, l, r, z0, az0);
   copy32(c, l, r, r1);
   CK(launch_axpby<float>(n, -1.f, az0, 1.f, r1, c->stream));
   double* ssum = S.dscal.as<double>();
-  CK(launch_feature_norm(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), z0, dinv, S.dpart.as<double>(), ssum,
-                         c->stream));
-  const double cnt = 3.0 * (double)std::max<int64_t>(G.nfree, 1);
-  CK(launch_features(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), G.logk.as<float>(), r1, z0, nullptr, dinv,
-                     ssum, cnt, S.act[0].p, nullptr, nullptr, c->stream));
-  forward_inference(c, S, GridShape{1, G.D, G.H, G.W}, S.out.as<float>());
-  CK(launch_grid_to_lib(E, G.e2g.as<int64_t>(), G.efree.as<uint8_t>(), S.out.as<float>(), dinv, ssum, cnt, cc,
+  CK(launch_feature_norm(G.V, E, nc, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), z0, dinv, S.dpart.as<double>(),
+                         ssum, c->stream));
+  const double cnt = feature_count(c, G);
+  CK(launch_features(G.V, E, nc, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), G.logk.as<float>(), r1, z0, nullptr,
+                     dinv, ssum, cnt, S.act[0].p, nullptr, nullptr, c->stream));
+  forward_inference(c, S, GridShape{1, G.D, G.H, G.W}, S.out.as<float>(), nc);
+  CK(launch_grid_to_lib(E, nc, G.e2g.as<int64_t>(), G.efree.as<uint8_t>(), S.out.as<float>(), dinv, ssum, cnt, cc,
                         c->stream));
-  apply32(c, l, cc, acc);
-  // energy-optimal a, b: [m11 m12; m12 m22] (a, b) = ((z0, r), (c, r))
-  const double m11 = rv, m12 = dot32(c, l, cc, az0), m22 = dot32(c, l, cc, acc), rc = dot32(c, l, cc, r);
+  sys_apply(c, l, cc, acc);
+  // optimal a, b: [m11 m12; m12 m22] (a, b) = (rv, rc) with the energy inner product
+  // (u, K v) (elasticity) or the residual one (K u, K v) (Stokes)
+  const double m11 = rv;
+  const double m12 = st ? sys_dot(c, l, acc, az0) : sys_dot(c, l, cc, az0);
+  const double m22 = st ? sys_dot(c, l, acc, acc) : sys_dot(c, l, cc, acc);
+  const double rc = st ? sys_dot(c, l, acc, r) : sys_dot(c, l, cc, r);
   const double det = m11 * m22 - m12 * m12;
   double a = 1.0, b = 0.0;
   if (m11 > 0.0 && m22 > 0.0 && det > 1e-6 * m11 * m22 && std::isfinite(det) && std::isfinite(rc)) {
@@ -377,7 +448,8 @@ double precondition(hhg_ctx* c, int l, const float* r, float* z, float* az, bool
   S.alpha_sum += w;
   S.alpha_min = S.applications == 1 ? w : std::min(S.alpha_min, w);
   S.alpha_max = S.applications == 1 ? w : std::max(S.alpha_max, w);
-  // extra energy reduction over the scaled V-cycle step, relative to that step's own
+  // extra reduction of the squared norm over the scaled multigrid step, relative to that
+  // step's own
   if (m11 > 0.0) S.gain_sum += (a * rv + b * rc - m11) / m11;
   copy32(c, l, z0, z);
   copy32(c, l, az0, az);
@@ -438,41 +510,104 @@ SolverResult fcg(hhg_ctx* c, int l, const float* f, float* x, double rtol, int m
   return res;
 }
 
-// One training pair from the error e (library layout): r = A e, z0 = a0 V-cycle(r) with
-// the energy-optimal a0, e1 = e - z0, r1 = r - A z0; stores (features(r1, z0), D e1 / s).
-// e1_out (nullable) receives e1.  Uses the work vectors Z0, AZ0, R1, C, AC.
+constexpr int GCR_RESTART = LearnGrid::GCR_DIRS;
+
+// Flexible GCR (generalised conjugate residual with a variable preconditioner; Eisenstat,
+// Elman and Schultz, SIAM J. Numer. Anal. 20 (1983), in its flexible form) on the Stokes
+// system K x = f in FP32: each preconditioned direction p = z (with q = K p from the
+// preconditioner) is made (q, q_j) = 0 against the stored directions by modified
+// Gram-Schmidt, and the step x += alpha p, alpha = (r, q) / (q, q), minimises |r|_2 along
+// it; after GCR_RESTART directions the stored ones are dropped.  hook (nullable) is
+// called with the iterate before every preconditioner application.
+SolverResult fgcr(hhg_ctx* c, int l, const float* f, float* x, double rtol, int max_iter, bool use_net,
+                  const std::function<void(const float*)>& hook = nullptr) {
+  LearnGrid& G = grid(c, l);
+  const int64_t n = sys_n(c, l);
+  float* r = lwork(c, G, l, LW_R);
+  float* z = lwork(c, G, l, LW_Z);
+  float* az = lwork(c, G, l, LW_AZ);
+  std::vector<double> qq(GCR_RESTART, 0.0);
+  SolverResult res;
+  const double r0 = sys_residual(c, l, f, x, r);
+  res.r0 = std::sqrt(r0);
+  if (!std::isfinite(r0)) THROW(HHG_ERR_NUMERIC, "non-finite initial residual");
+  if (r0 == 0.0) {
+    res.converged = true;
+    return res;
+  }
+  double rr = r0;
+  int m = 0;
+  for (int it = 1; it <= max_iter; ++it) {
+    if (hook) hook(x);
+    precondition(c, l, r, z, az, use_net);
+    if (m == GCR_RESTART) m = 0;
+    for (DevMem* d : {&G.gcr_p[m], &G.gcr_q[m]})
+      if (!d->p) CK(d->alloc(4 * (size_t)c->lv(l).entries * sizeof(float)));
+    float* p = G.gcr_p[m].as<float>();
+    float* q = G.gcr_q[m].as<float>();
+    copy32(c, l, z, p);
+    copy32(c, l, az, q);
+    for (int j = 0; j < m; ++j) {
+      const double beta = sys_dot(c, l, q, G.gcr_q[j].as<float>()) / qq[j];
+      CK(launch_axpby<float>(n, (float)(-beta), G.gcr_p[j].as<float>(), 1.f, p, c->stream));
+      CK(launch_axpby<float>(n, (float)(-beta), G.gcr_q[j].as<float>(), 1.f, q, c->stream));
+    }
+    const double qn = sys_dot(c, l, q, q);
+    if (!(qn > 0.0) || !std::isfinite(qn)) THROW(HHG_ERR_NUMERIC, "FGCR breakdown (|K p|^2 = %g)", qn);
+    const double alpha = sys_dot(c, l, r, q) / qn;
+    CK(launch_axpby<float>(n, (float)alpha, p, 1.f, x, c->stream));
+    CK(launch_axpby<float>(n, (float)(-alpha), q, 1.f, r, c->stream));
+    qq[m++] = qn;
+    rr = sys_dot(c, l, r, r);
+    res.iterations = it;
+    if (!std::isfinite(rr)) THROW(HHG_ERR_NUMERIC, "non-finite residual");
+    if (std::sqrt(rr / r0) <= rtol) {
+      res.converged = true;
+      break;
+    }
+  }
+  res.rel = std::sqrt(rr / r0);
+  return res;
+}
+
+// One training pair from the error e (library layout): r = K e, z0 = a0 MG(r) with the
+// optimal a0, e1 = e - z0 (Stokes: pressure shifted to zero mean), r1 = r - K z0; stores
+// (features(r1, z0), D e1 / s).  e1_out (nullable) receives e1.  Uses the work vectors
+// Z0, AZ0, R1, C, AC.
 void store_pair(hhg_ctx* c, int l, const float* e, float* e1_out) {
   LearnState& S = state(c);
   LearnGrid& G = grid(c, l);
+  const int nc = ncomp(c);
   if (S.pair_level != l) THROW(HHG_ERR_STATE, "reserve pair storage for level %d first", l);
+  if (S.pair_nc != nc) THROW(HHG_ERR_STATE, "pair storage was reserved for another problem kind");
   if (S.pair_count >= S.pair_cap) THROW(HHG_ERR_ARG, "pair storage full (%lld)", (long long)S.pair_cap);
-  const int64_t E = c->lv(l).entries, n = 3 * E;
+  const int64_t E = c->lv(l).entries, n = nc * E;
   float* z0 = lwork(c, G, l, LW_Z0);
   float* az0 = lwork(c, G, l, LW_AZ0);
   float* r1 = lwork(c, G, l, LW_R1);
   float* r = lwork(c, G, l, LW_C);
   float* e1 = lwork(c, G, l, LW_AC);
-  const float* dinv = dinv32(c, l);
+  const float* dinv = sys_dinv(c, l, G);
   if (S.dpart.bytes < (size_t)mse_partials(G.V) * sizeof(double))
     CK(S.dpart.alloc((size_t)mse_partials(G.V) * sizeof(double)));
   if (!S.dscal.p) CK(S.dscal.alloc(8 * sizeof(double)));
   double* ssum = S.dscal.as<double>();
-  const double cnt = 3.0 * (double)std::max<int64_t>(G.nfree, 1);
-  apply32(c, l, e, r);
-  CK(cudaMemsetAsync(z0, 0, n * sizeof(float), c->stream));
-  vcycle32(c, l, r, z0);
-  apply32(c, l, z0, az0);
-  scale_vcycle_step(c, l, r, z0, az0);
+  const double cnt = feature_count(c, G);
+  sys_apply(c, l, e, r);
+  sys_mg(c, l, r, z0);
+  sys_apply(c, l, z0, az0);
+  scale_mg_step(c, l, r, z0, az0);
   copy32(c, l, r, r1);
   CK(launch_axpby<float>(n, -1.f, az0, 1.f, r1, c->stream));
   copy32(c, l, e, e1);
   CK(launch_axpby<float>(n, -1.f, z0, 1.f, e1, c->stream));
-  CK(launch_feature_norm(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), z0, dinv, S.dpart.as<double>(), ssum,
-                         c->stream));
+  if (nc == 4) project_pressure32(c, l, e1);
+  CK(launch_feature_norm(G.V, E, nc, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), z0, dinv, S.dpart.as<double>(),
+                         ssum, c->stream));
   const int64_t p = S.pair_count++;
-  CK(launch_features(G.V, E, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), G.logk.as<float>(), r1, z0, e1, dinv, ssum,
-                     cnt, nullptr, (char*)S.pin.p + (size_t)p * G.V * LN_PAIR_IN * 2,
-                     S.ptg.as<float>() + (size_t)p * G.V * 3, c->stream));
+  CK(launch_features(G.V, E, nc, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), G.logk.as<float>(), r1, z0, e1, dinv,
+                     ssum, cnt, nullptr, (char*)S.pin.p + (size_t)p * G.V * ln_pair_in(nc) * 2,
+                     S.ptg.as<float>() + (size_t)p * G.V * nc, c->stream));
   if (e1_out) copy32(c, l, e1, e1_out);
 }
 
@@ -481,32 +616,50 @@ void store_pair(hhg_ctx* c, int l, const float* e, float* e1_out) {
 namespace hhg {
 namespace host {
 
-// FP64 iterative refinement around FP32 flexible CG with the learned preconditioner
-// (use_net = false: the same solver with the plain V-cycle)
+// FP64 iterative refinement around the FP32 flexible Krylov solver with the learned
+// preconditioner (use_net = false: the same solver with the plain multigrid cycle):
+// flexible CG for the elasticity methods, flexible GCR for the Stokes ones (pressure
+// shifted to zero mean at the end)
 void learned_ir(hhg_ctx* c, const hhg_solve_opts* o, const double* f, double* x, bool use_net, hhg_solve_report& R) {
-  need_elasticity(c);
+  const bool st = o->method == HHG_SOLVE_STOKES_IR_FGCR || o->method == HHG_SOLVE_STOKES_IR_FGCR_LEARNED;
+  if (st)
+    need_stokes_problem(c);
+  else
+    need_elasticity(c);
   mg_ready_check(c);
   const int l = o->level;
   if (use_net) need_params(state(c));
   if (!(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || o->inner_max_iter < 1) THROW(HHG_ERR_ARG, "inner tol");
-  ensure_work64(c, l);
-  const int64_t n = 3 * c->lv(l).entries;
-  double* r64 = work64(c, l, 10);
-  float* r32 = work32(c, l, 10);
-  float* e32 = work32(c, l, 11);
-  const double r0 = residual64(c, l, f, x, r64);
+  const int64_t n = sys_n(c, l);
+  double* r64;
+  float *r32, *e32;
+  if (st) {
+    ensure_stokes_work(c, l);
+    r64 = stokes_work64(c, l, 8);
+    r32 = stokes_work32(c, l, 8);
+    e32 = stokes_work32(c, l, 9);
+  } else {
+    ensure_work64(c, l);
+    r64 = work64(c, l, 10);
+    r32 = work32(c, l, 10);
+    e32 = work32(c, l, 11);
+  }
+  auto residual = [&] { return st ? stokes_residual64(c, l, f, x, r64) : residual64(c, l, f, x, r64); };
+  const double r0 = residual();
   R.residual0 = std::sqrt(r0);
   double rr = r0;
   for (int it = 1; it <= o->max_iter && r0 > 0.0 && std::sqrt(rr / r0) > o->rtol; ++it) {
     CK(launch_convert<double, float>(n, r64, r32, c->stream));
     CK(cudaMemsetAsync(e32, 0, n * sizeof(float), c->stream));
-    SolverResult cr = fcg(c, l, r32, e32, o->inner_rtol, o->inner_max_iter, use_net);
+    SolverResult cr = st ? fgcr(c, l, r32, e32, o->inner_rtol, o->inner_max_iter, use_net)
+                         : fcg(c, l, r32, e32, o->inner_rtol, o->inner_max_iter, use_net);
     R.inner_iterations += cr.iterations;
     CK(launch_add_f32_to_f64(n, e32, x, c->stream));
-    rr = residual64(c, l, f, x, r64);
+    rr = residual();
     R.iterations = it;
     if (!std::isfinite(rr)) THROW(HHG_ERR_NUMERIC, "non-finite residual");
   }
+  if (st) project_pressure64(c, l, x);
   R.rel_residual = r0 > 0.0 ? std::sqrt(rr / r0) : 0.0;
   R.converged = R.rel_residual <= o->rtol;
   if (use_net) check_conv(state(c));
@@ -524,9 +677,10 @@ hhg_status hhg_learn_init(hhg_ctx* c, uint64_t seed) {
     LearnState& S = state(c);
     std::vector<float> h(LN_NPARAM, 0.f);
     uint64_t s = seed ^ 0x6C6561726E6564ull;
+    const int nc = ncomp(c);
     for (int l = 0; l < LN_LAYERS; ++l) {
-      const int cin = l == 0 ? LN_CIN : LN_C;
-      const int cout = l == LN_LAYERS - 1 ? LN_COUT : LN_C;
+      const int cin = l == 0 ? ln_cin(nc) : LN_C;
+      const int cout = l == LN_LAYERS - 1 ? nc : LN_C;
       const double sd = std::sqrt(2.0 / (LN_TAPS * cin)) * (l == LN_LAYERS - 1 ? 0.1 : 1.0);
       float* W = h.data() + (int64_t)l * LN_LSIZE;
       for (int t = 0; t < LN_TAPS; ++t)
@@ -577,32 +731,41 @@ hhg_status hhg_learn_grid(hhg_ctx* c, int level, int* dhw, int64_t* free_voxels)
   });
 }
 
-hhg_status hhg_learn_forward(hhg_ctx* c, const float* x, int cin, int B, int D, int H, int W, float* out) {
+hhg_status hhg_learn_channels(hhg_ctx* c, int* cin, int* cout) {
+  return guard(c, [&] {
+    if (cin) *cin = ln_cin(ncomp(c));
+    if (cout) *cout = ncomp(c);
+  });
+}
+
+hhg_status hhg_learn_forward(hhg_ctx* c, const float* x, int cin, int cout, int B, int D, int H, int W, float* out) {
   return guard(c, [&] {
     LearnState& S = state(c);
     need_params(S);
-    if (!x || !out || cin < 1 || cin > LN_C || B < 1 || D < 1 || H < 1 || W < 1) THROW(HHG_ERR_ARG, "bad arguments");
+    if (!x || !out || cin < 1 || cin > LN_C || (cout != 3 && cout != 4) || B < 1 || D < 1 || H < 1 || W < 1)
+      THROW(HHG_ERR_ARG, "bad arguments");
     const GridShape s{B, D, H, W};
     ensure_acts(c, S, s.voxels());
     CK(launch_to_bf16(s.voxels(), cin, x, S.act[0].p, c->stream));
-    forward_inference(c, S, s, out);
+    forward_inference(c, S, s, out, cout);
     wait_stream(c);
     check_conv(S);
   });
 }
 
-hhg_status hhg_learn_loss_grad(hhg_ctx* c, const float* x, int cin, const float* target, int B, int D, int H, int W,
-                               double* loss_host, float* grad_host) {
+hhg_status hhg_learn_loss_grad(hhg_ctx* c, const float* x, int cin, const float* target, int cout, int B, int D,
+                               int H, int W, double* loss_host, float* grad_host) {
   return guard(c, [&] {
     LearnState& S = state(c);
     need_params(S);
-    if (!x || !target || cin < 1 || cin > LN_C || B < 1 || D < 1 || H < 1 || W < 1) THROW(HHG_ERR_ARG, "bad arguments");
+    if (!x || !target || cin < 1 || cin > LN_C || (cout != 3 && cout != 4) || B < 1 || D < 1 || H < 1 || W < 1)
+      THROW(HHG_ERR_ARG, "bad arguments");
     const GridShape s{B, D, H, W};
     ensure_acts(c, S, s.voxels());
     CK(launch_to_bf16(s.voxels(), cin, x, S.act[0].p, c->stream));
-    forward(c, S, s, S.out.as<float>());
+    forward(c, S, s, S.out.as<float>(), cout);
     double* loss = S.dscal.as<double>() + 1;
-    backward(c, S, s, S.out.as<float>(), target, loss);
+    backward(c, S, s, S.out.as<float>(), target, cout, loss);
     CK(cudaMemcpyAsync(c->pinned, loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (grad_host)
       CK(cudaMemcpyAsync(grad_host, S.grad.p, LN_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
@@ -615,12 +778,13 @@ hhg_status hhg_learn_loss_grad(hhg_ctx* c, const float* x, int cin, const float*
 hhg_status hhg_learn_reserve_pairs(hhg_ctx* c, int level, int64_t capacity) {
   return guard(c, [&] {
     need_ready(c, false);
-    if (c->prob.kind != HHG_ELASTICITY) THROW(HHG_ERR_UNSUPPORTED, "the learned preconditioner needs an elasticity problem");
     if (capacity < 1) THROW(HHG_ERR_ARG, "capacity");
     LearnState& S = state(c);
     LearnGrid& G = grid(c, level);
-    CK(S.pin.alloc((size_t)capacity * G.V * LN_PAIR_IN * 2));
-    CK(S.ptg.alloc((size_t)capacity * G.V * 3 * sizeof(float)));
+    const int nc = ncomp(c);
+    CK(S.pin.alloc((size_t)capacity * G.V * ln_pair_in(nc) * 2));
+    CK(S.ptg.alloc((size_t)capacity * G.V * nc * sizeof(float)));
+    S.pair_nc = nc;
     S.pair_level = level;
     S.pair_cap = capacity;
     S.pair_count = 0;
@@ -629,7 +793,7 @@ hhg_status hhg_learn_reserve_pairs(hhg_ctx* c, int level, int64_t capacity) {
 
 hhg_status hhg_learn_collect(hhg_ctx* c, int level, const float* e0_grid, int cycles, int64_t* count) {
   return guard(c, [&] {
-    need_elasticity(c);
+    need_ready(c, true);
     mg_ready_check(c);
     LearnState& S = state(c);
     if (!e0_grid || cycles < 1) THROW(HHG_ERR_ARG, "bad arguments");
@@ -637,8 +801,8 @@ hhg_status hhg_learn_collect(hhg_ctx* c, int level, const float* e0_grid, int cy
     if (S.pair_count + cycles > S.pair_cap) THROW(HHG_ERR_ARG, "pair storage full (%lld)", (long long)S.pair_cap);
     LearnGrid& G = grid(c, level);
     float* e = lwork(c, G, level, LW_E);
-    CK(launch_grid_to_lib(c->lv(level).entries, G.e2g.as<int64_t>(), G.efree.as<uint8_t>(), e0_grid, nullptr, nullptr,
-                          1.0, e, c->stream));
+    CK(launch_grid_to_lib(c->lv(level).entries, ncomp(c), G.e2g.as<int64_t>(), G.efree.as<uint8_t>(), e0_grid, nullptr,
+                          nullptr, 1.0, e, c->stream));
     for (int j = 0; j < cycles; ++j) store_pair(c, level, e, e);
     wait_stream(c);
     if (count) *count = S.pair_count;
@@ -647,23 +811,36 @@ hhg_status hhg_learn_collect(hhg_ctx* c, int level, const float* e0_grid, int cy
 
 hhg_status hhg_learn_collect_cg(hhg_ctx* c, int level, const float* f, int iters, int64_t* count) {
   return guard(c, [&] {
-    need_elasticity(c);
+    need_ready(c, true);
     mg_ready_check(c);
     LearnState& S = state(c);
     if (!f || iters < 1) THROW(HHG_ERR_ARG, "bad arguments");
     if (S.pair_level != level) THROW(HHG_ERR_STATE, "reserve pair storage for level %d first", level);
     if (S.pair_count + iters > S.pair_cap) THROW(HHG_ERR_ARG, "pair storage full (%lld)", (long long)S.pair_cap);
     LearnGrid& G = grid(c, level);
-    const int64_t n = 3 * c->lv(level).entries;
-    // reference solution x* (FP64 refinement to 1e-10)
+    const bool st = is_stokes(c);
+    const int64_t n = sys_n(c, level);
+    // reference solution x* (FP64 refinement to 1e-10; Stokes: zero-mean pressure)
     for (auto& v : G.lw64)
-      if (!v.p) CK(v.alloc(n * sizeof(double)));
+      if (!v.p) CK(v.alloc(4 * (size_t)c->lv(level).entries * sizeof(double)));
     double* f64 = G.lw64[0].as<double>();
     double* x64 = G.lw64[1].as<double>();
     CK(launch_convert<float, double>(n, f, f64, c->stream));
+    if (st) {
+      // K's range is orthogonal to the constant pressure: drop that component of f (FP32
+      // rounding alone leaves one of about 1e-8 relative, more than the 1e-10 asked for)
+      LevelHost& L = c->lv(level);
+      const int64_t E = L.entries;
+      std::vector<double> hp(E);
+      CK(cudaMemcpyAsync(hp.data(), f64 + 3 * E, E * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      wait_stream(c);
+      double sum = 0.0;
+      for (int64_t u = 0; u < L.nunique; ++u) sum += hp[L.unique_first[u]];
+      CK(launch_add_const<double>(E, -sum / (double)L.nunique, f64 + 3 * E, c->stream));
+    }
     CK(cudaMemsetAsync(x64, 0, n * sizeof(double), c->stream));
     hhg_solve_opts o{};
-    o.method = HHG_SOLVE_IR_FCG;
+    o.method = st ? HHG_SOLVE_STOKES_IR_FGCR : HHG_SOLVE_IR_FCG;
     o.level = level;
     o.dt = HHG_F64;
     o.rtol = 1e-10;
@@ -686,7 +863,10 @@ hhg_status hhg_learn_collect_cg(hhg_ctx* c, int level, const float* f, int iters
       store_pair(c, level, e, nullptr);
       ++stored;
     };
-    fcg(c, level, f, x, 1e-7, iters, false, hook);
+    if (st)
+      fgcr(c, level, f, x, 1e-7, iters, false, hook);
+    else
+      fcg(c, level, f, x, 1e-7, iters, false, hook);
     wait_stream(c);
     if (count) *count = S.pair_count;
   });
@@ -697,19 +877,20 @@ hhg_status hhg_learn_get_pair(hhg_ctx* c, int64_t index, float* in_host, float* 
     LearnState& S = state(c);
     if (index < 0 || index >= S.pair_count) THROW(HHG_ERR_ARG, "pair %lld not stored", (long long)index);
     LearnGrid& G = grid(c, S.pair_level);
+    const int nc = S.pair_nc, pin = ln_pair_in(nc), cin = ln_cin(nc);
     if (in_host) {
-      std::vector<uint16_t> h((size_t)G.V * LN_PAIR_IN);
-      CK(cudaMemcpyAsync(h.data(), (const char*)S.pin.p + (size_t)index * G.V * LN_PAIR_IN * 2, h.size() * 2,
+      std::vector<uint16_t> h((size_t)G.V * pin);
+      CK(cudaMemcpyAsync(h.data(), (const char*)S.pin.p + (size_t)index * G.V * pin * 2, h.size() * 2,
                          cudaMemcpyDeviceToHost, c->stream));
       wait_stream(c);
       for (int64_t g = 0; g < G.V; ++g)
-        for (int q = 0; q < LN_CIN; ++q) {
-          const uint32_t u = (uint32_t)h[(size_t)g * LN_PAIR_IN + q] << 16;
-          std::memcpy(&in_host[(size_t)g * LN_CIN + q], &u, 4);
+        for (int q = 0; q < cin; ++q) {
+          const uint32_t u = (uint32_t)h[(size_t)g * pin + q] << 16;
+          std::memcpy(&in_host[(size_t)g * cin + q], &u, 4);
         }
     }
     if (target_host) {
-      CK(cudaMemcpyAsync(target_host, S.ptg.as<float>() + (size_t)index * G.V * 3, (size_t)G.V * 3 * sizeof(float),
+      CK(cudaMemcpyAsync(target_host, S.ptg.as<float>() + (size_t)index * G.V * nc, (size_t)G.V * nc * sizeof(float),
                          cudaMemcpyDeviceToHost, c->stream));
       wait_stream(c);
     }
@@ -744,11 +925,11 @@ hhg_status hhg_learn_train(hhg_ctx* c, const hhg_learn_train_opts* o, hhg_learn_
     upload(dorg, org);
     CK(dloss.alloc((size_t)o->steps * sizeof(double)));
     for (int st = 0; st < o->steps; ++st) {
-      CK(launch_crop(S.pin.p, S.ptg.as<float>(), G.D, G.H, G.W, didx.as<int32_t>() + (size_t)st * o->batch,
+      CK(launch_crop(S.pair_nc, S.pin.p, S.ptg.as<float>(), G.D, G.H, G.W, didx.as<int32_t>() + (size_t)st * o->batch,
                      dorg.as<int32_t>() + (size_t)st * o->batch * 3, o->batch, Sc, S.act[0].p, S.tgt.as<float>(),
                      c->stream));
-      forward(c, S, s, S.out.as<float>());
-      backward(c, S, s, S.out.as<float>(), S.tgt.as<float>(), dloss.as<double>() + st);
+      forward(c, S, s, S.out.as<float>(), S.pair_nc);
+      backward(c, S, s, S.out.as<float>(), S.tgt.as<float>(), S.pair_nc, dloss.as<double>() + st);
       const double lr = o->lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(3.141592653589793 * st / o->steps)));
       CK(launch_adam(S.params.as<float>(), S.grad.as<float>(), S.m.as<float>(), S.v.as<float>(), LN_NPARAM, (float)lr,
                      ++S.adam_step, c->stream));
@@ -777,7 +958,7 @@ hhg_status hhg_learn_train(hhg_ctx* c, const hhg_learn_train_opts* o, hhg_learn_
 
 hhg_status hhg_learn_precondition(hhg_ctx* c, int level, int use_net, const void* r, void* z, double* alpha) {
   return guard(c, [&] {
-    need_elasticity(c);
+    need_ready(c, true);
     mg_ready_check(c);
     if (!r || !z) THROW(HHG_ERR_ARG, "null vector");
     LearnGrid& G = grid(c, level);

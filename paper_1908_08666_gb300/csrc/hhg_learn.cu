@@ -677,21 +677,23 @@ __global__ void __launch_bounds__(RED_BLOCK) k_bgrad(const uint32_t* __restrict_
   }
 }
 
+// NC = output channels of the network (3 elasticity, 4 Stokes)
+template <int NC>
 __global__ void __launch_bounds__(RED_BLOCK) k_mse(const float* __restrict__ out, const float* __restrict__ target,
                                                    int64_t V, double inv_n, uint32_t* __restrict__ G,
                                                    double* __restrict__ partial) {
   __shared__ double s[RED_BLOCK / 32];
   double acc = 0.0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
-    float gr[LN_COUT];
+    float gr[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int c = 0; c < LN_COUT; ++c) {
-      const double d = (double)out[v * LN_COUT + c] - (double)target[v * LN_COUT + c];
+    for (int c = 0; c < NC; ++c) {
+      const double d = (double)out[v * NC + c] - (double)target[v * NC + c];
       acc += d * d;
       gr[c] = (float)(2.0 * d * inv_n);
     }
     uint4* p = reinterpret_cast<uint4*>(G + v * 8);
-    p[0] = make_uint4(pack_bf16x2(gr[0], gr[1]), pack_bf16x2(gr[2], 0.f), 0u, 0u);
+    p[0] = make_uint4(pack_bf16x2(gr[0], gr[1]), pack_bf16x2(gr[2], gr[3]), 0u, 0u);
     p[1] = make_uint4(0u, 0u, 0u, 0u);
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -771,6 +773,10 @@ __device__ __forceinline__ double feature_scale(const double* sumsq, double coun
   return (s2 > 0.0 && s2 < 1e300) ? sqrt(s2) : 1.0;
 }
 
+// Feature kernels, NC = components of the system's unknowns: 3 (elasticity: velocity-like
+// displacement, zero on Dirichlet nodes) or 4 (Stokes: velocity, zero on velocity-Dirichlet
+// nodes, then the pressure, free at every node).  dinv holds NC * E values.
+template <int NC>
 __global__ void __launch_bounds__(RED_BLOCK) k_feature_norm(int64_t V, int64_t E, const int64_t* __restrict__ gent,
                                                             const uint8_t* __restrict__ gfree,
                                                             const float* __restrict__ z0,
@@ -779,10 +785,12 @@ __global__ void __launch_bounds__(RED_BLOCK) k_feature_norm(int64_t V, int64_t E
   __shared__ double s[RED_BLOCK / 32];
   double acc = 0.0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < V; g += (int64_t)gridDim.x * blockDim.x) {
-    if (!gfree[g]) continue;
     const int64_t e = gent[g];
+    if (e < 0) continue;
+    const bool fr = gfree[g] != 0;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < NC; ++c) {
+      if (c < 3 && !fr) continue;
       const double w = (double)z0[e + c * E] / (double)dinv[e + c * E];
       acc += w * w;
     }
@@ -797,41 +805,58 @@ __global__ void __launch_bounds__(RED_BLOCK) k_feature_norm(int64_t V, int64_t E
   }
 }
 
+// channels: r1 / s (NC), D z0 / s (NC), log k - mean (1); X holds 16 channels per voxel,
+// pin the first 8 * PW (PW = 1 for NC = 3, 2 for NC = 4)
+template <int NC>
 __global__ void k_features(int64_t V, int64_t E, const int64_t* __restrict__ gent, const uint8_t* __restrict__ gfree,
                            const float* __restrict__ logk, const float* __restrict__ r1,
                            const float* __restrict__ z0, const float* __restrict__ e1,
                            const float* __restrict__ dinv, const double* __restrict__ sumsq, double count,
                            uint32_t* __restrict__ X, uint32_t* __restrict__ pin, float* __restrict__ target) {
+  constexpr int PW = NC == 4 ? 2 : 1;
   const float inv = (float)(1.0 / feature_scale(sumsq, count));
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < V; g += (int64_t)gridDim.x * blockDim.x) {
-    float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float tg[3] = {0.f, 0.f, 0.f};
-    f[6] = logk[g];
-    if (gfree[g]) {
-      const int64_t e = gent[g];
+    float f[16];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
+    for (int q = 0; q < 16; ++q) f[q] = 0.f;
+    float tg[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) tg[c] = 0.f;
+    f[2 * NC] = logk[g];
+    const int64_t e = gent[g];
+    if (e >= 0) {
+      const bool fr = gfree[g] != 0;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (c < 3 && !fr) continue;
         const float d = 1.f / dinv[e + c * E];
         f[c] = r1[e + c * E] * inv;
-        f[3 + c] = z0[e + c * E] * d * inv;
+        f[NC + c] = z0[e + c * E] * d * inv;
         if (e1) tg[c] = e1[e + c * E] * d * inv;
       }
     }
     const uint4 w0 = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
                                 pack_bf16x2(f[6], f[7]));
+    const uint4 w1 = make_uint4(pack_bf16x2(f[8], f[9]), pack_bf16x2(f[10], f[11]), pack_bf16x2(f[12], f[13]),
+                                pack_bf16x2(f[14], f[15]));
     if (X) {
       uint4* p = reinterpret_cast<uint4*>(X + g * 8);
       p[0] = w0;
-      p[1] = make_uint4(0u, 0u, 0u, 0u);
+      p[1] = w1;
     }
-    if (pin) reinterpret_cast<uint4*>(pin)[g] = w0;
+    if (pin) {
+      uint4* p = reinterpret_cast<uint4*>(pin) + g * PW;
+      p[0] = w0;
+      if (PW == 2) p[1] = w1;
+    }
     if (target) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) target[g * 3 + c] = tg[c];
+      for (int c = 0; c < NC; ++c) target[g * NC + c] = tg[c];
     }
   }
 }
 
+template <int NC>
 __global__ void k_grid_to_lib(int64_t E, const int64_t* __restrict__ e2g, const uint8_t* __restrict__ efree,
                               const float* __restrict__ out, const float* __restrict__ dinv,
                               const double* __restrict__ sumsq, double count, float* __restrict__ z) {
@@ -840,26 +865,31 @@ __global__ void k_grid_to_lib(int64_t E, const int64_t* __restrict__ e2g, const 
     const bool f = efree[e] != 0;
     const int64_t g = e2g[e];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) z[e + c * E] = f ? s * out[g * 3 + c] * (dinv ? dinv[e + c * E] : 1.f) : 0.f;
+    for (int c = 0; c < NC; ++c) {
+      const bool on = c < 3 ? f : g >= 0;
+      z[e + c * E] = on ? s * out[g * NC + c] * (dinv ? dinv[e + c * E] : 1.f) : 0.f;
+    }
   }
 }
 
-__global__ void k_crop(const uint4* __restrict__ pin, const float* __restrict__ ptg, int PD, int PH, int PW,
+template <int NC>
+__global__ void k_crop(const uint4* __restrict__ pin, const float* __restrict__ ptg, int PD, int PH, int PW_,
                        const int32_t* __restrict__ idx, const int32_t* __restrict__ org, int B, int S,
                        uint4* __restrict__ X, float* __restrict__ target) {
+  constexpr int PW = NC == 4 ? 2 : 1;
   const int64_t V = (int64_t)B * S * S * S;
-  const int64_t N3 = (int64_t)PD * PH * PW;
+  const int64_t N3 = (int64_t)PD * PH * PW_;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(v % S);
     const int y = (int)((v / S) % S);
     const int z = (int)((v / ((int64_t)S * S)) % S);
     const int b = (int)(v / ((int64_t)S * S * S));
-    const int64_t src = (int64_t)idx[b] * N3 + ((int64_t)(org[3 * b] + z) * PH + (org[3 * b + 1] + y)) * PW +
+    const int64_t src = (int64_t)idx[b] * N3 + ((int64_t)(org[3 * b] + z) * PH + (org[3 * b + 1] + y)) * PW_ +
                         (org[3 * b + 2] + x);
-    X[2 * v] = pin[src];
-    X[2 * v + 1] = make_uint4(0u, 0u, 0u, 0u);
+    X[2 * v] = pin[src * PW];
+    X[2 * v + 1] = PW == 2 ? pin[src * PW + 1] : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) target[v * 3 + c] = ptg[src * 3 + c];
+    for (int c = 0; c < NC; ++c) target[v * NC + c] = ptg[src * NC + c];
   }
 }
 
@@ -938,11 +968,12 @@ int launch_bgrad(const void* G, int64_t V, float* partial, float* db, void* stre
 
 int64_t mse_partials(int64_t V) { return red_blocks(V); }
 
-int launch_mse(const float* out, const float* target, int64_t V, void* G, double* partial, double* loss,
+int launch_mse(const float* out, const float* target, int64_t V, int nc, void* G, double* partial, double* loss,
                void* stream) {
+  if (nc != 3 && nc != 4) return (int)cudaErrorInvalidValue;
   const int64_t nb = red_blocks(V);
-  k_mse<<<(unsigned)nb, RED_BLOCK, 0, (cudaStream_t)stream>>>(out, target, V, 1.0 / ((double)V * LN_COUT),
-                                                               (uint32_t*)G, partial);
+  (nc == 4 ? k_mse<4> : k_mse<3>)<<<(unsigned)nb, RED_BLOCK, 0, (cudaStream_t)stream>>>(
+      out, target, V, 1.0 / ((double)V * nc), (uint32_t*)G, partial);
   k_sum_into<<<1, RED_BLOCK, 0, (cudaStream_t)stream>>>(partial, (int)nb, loss);
   return (int)cudaGetLastError();
 }
@@ -1033,34 +1064,39 @@ int launch_to_bf16(int64_t V, int cin, const float* src, void* X, void* stream) 
   return (int)cudaGetLastError();
 }
 
-int launch_feature_norm(int64_t V, int64_t E, const int64_t* gent, const uint8_t* gfree, const float* z0,
+int launch_feature_norm(int64_t V, int64_t E, int nc, const int64_t* gent, const uint8_t* gfree, const float* z0,
                         const float* dinv, double* partial, double* out, void* stream) {
+  if (nc != 3 && nc != 4) return (int)cudaErrorInvalidValue;
   const int64_t nb = red_blocks(V);
-  k_feature_norm<<<(unsigned)nb, RED_BLOCK, 0, (cudaStream_t)stream>>>(V, E, gent, gfree, z0, dinv, partial);
+  (nc == 4 ? k_feature_norm<4> : k_feature_norm<3>)<<<(unsigned)nb, RED_BLOCK, 0, (cudaStream_t)stream>>>(
+      V, E, gent, gfree, z0, dinv, partial);
   k_sum_into<<<1, RED_BLOCK, 0, (cudaStream_t)stream>>>(partial, (int)nb, out);
   return (int)cudaGetLastError();
 }
 
-int launch_features(int64_t V, int64_t E, const int64_t* gent, const uint8_t* gfree, const float* logk,
+int launch_features(int64_t V, int64_t E, int nc, const int64_t* gent, const uint8_t* gfree, const float* logk,
                     const float* r1, const float* z0, const float* e1, const float* dinv, const double* sumsq,
                     double count, void* X, void* pin, float* target, void* stream) {
-  k_features<<<blocks_for(V, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(
+  if (nc != 3 && nc != 4) return (int)cudaErrorInvalidValue;
+  (nc == 4 ? k_features<4> : k_features<3>)<<<blocks_for(V, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(
       V, E, gent, gfree, logk, r1, z0, e1, dinv, sumsq, count, (uint32_t*)X, (uint32_t*)pin, target);
   return (int)cudaGetLastError();
 }
 
-int launch_grid_to_lib(int64_t E, const int64_t* e2g, const uint8_t* efree, const float* out, const float* dinv,
-                       const double* sumsq, double count, float* z, void* stream) {
-  k_grid_to_lib<<<blocks_for(E, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(E, e2g, efree, out, dinv, sumsq,
-                                                                                 count, z);
+int launch_grid_to_lib(int64_t E, int nc, const int64_t* e2g, const uint8_t* efree, const float* out,
+                       const float* dinv, const double* sumsq, double count, float* z, void* stream) {
+  if (nc != 3 && nc != 4) return (int)cudaErrorInvalidValue;
+  (nc == 4 ? k_grid_to_lib<4> : k_grid_to_lib<3>)<<<blocks_for(E, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(
+      E, e2g, efree, out, dinv, sumsq, count, z);
   return (int)cudaGetLastError();
 }
 
-int launch_crop(const void* pin, const float* ptg, int PD, int PH, int PW, const int32_t* idx, const int32_t* org,
-                int B, int S, void* X, float* target, void* stream) {
+int launch_crop(int nc, const void* pin, const float* ptg, int PD, int PH, int PW, const int32_t* idx,
+                const int32_t* org, int B, int S, void* X, float* target, void* stream) {
+  if (nc != 3 && nc != 4) return (int)cudaErrorInvalidValue;
   const int64_t V = (int64_t)B * S * S * S;
-  k_crop<<<blocks_for(V, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>((const uint4*)pin, ptg, PD, PH, PW, idx, org,
-                                                                          B, S, (uint4*)X, target);
+  (nc == 4 ? k_crop<4> : k_crop<3>)<<<blocks_for(V, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(
+      (const uint4*)pin, ptg, PD, PH, PW, idx, org, B, S, (uint4*)X, target);
   return (int)cudaGetLastError();
 }
 

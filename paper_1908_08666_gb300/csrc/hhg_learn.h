@@ -9,10 +9,12 @@
 // W_l[t][i][o] at l*LN_LSIZE + (t*16 + i)*16 + o, then b_l[o] at l*LN_LSIZE + LN_WSIZE + o,
 // tap t = (dz+1)*9 + (dy+1)*3 + (dx+1).
 //
-// Input features (LN_CIN channels, see k_features): r1/s (3), D z0/s (3), log k - mean (1),
-// with z0 the V-cycle correction of the residual r, r1 = r - A z0, D the point diagonal
-// and s the RMS of D z0 over the free nodes.  Output (LN_COUT channels): D c / s, c the
-// correction added to z0.
+// The system has nc = 3 unknowns per node (elasticity) or nc = 4 (Stokes: velocity and
+// pressure).  Input features (2 nc + 1 channels, see k_features): r1/s (nc), D z0/s (nc),
+// log k - mean (1), with z0 the multigrid correction of the residual r, r1 = r - K z0,
+// D the point diagonal of the velocity block (and, for the pressure, the diagonal Schur
+// surrogate m / mu + (-C)_ii) and s the RMS of D z0 over the free DoFs.  Output (nc
+// channels): D c / s, c the correction added to z0.
 #pragma once
 #include <cstdint>
 
@@ -20,14 +22,16 @@ namespace hhg {
 
 constexpr int LN_C = 16;
 constexpr int LN_LAYERS = 4;
-constexpr int LN_CIN = 7;
+constexpr int LN_CIN = 7;   // elasticity: 2 * 3 + 1
 constexpr int LN_COUT = 3;
+constexpr int ln_cin(int nc) { return 2 * nc + 1; }
 constexpr int LN_TAPS = 27;
 constexpr int LN_WSIZE = LN_TAPS * LN_C * LN_C;   // 6912
 constexpr int LN_LSIZE = LN_WSIZE + LN_C;         // 6928
 constexpr int LN_NPARAM = LN_LAYERS * LN_LSIZE;   // 27712
 constexpr int LN_PACK = LN_TAPS * 2 * 32 * 2;     // 32-bit words of one layer's packed B fragments
-constexpr int LN_PAIR_IN = 8;                     // BF16 input channels stored per pair voxel
+constexpr int LN_PAIR_IN = 8;                     // BF16 input channels stored per pair voxel (nc = 3)
+constexpr int ln_pair_in(int nc) { return nc == 4 ? 16 : LN_PAIR_IN; }
 
 struct GridShape {
   int B, D, H, W;
@@ -59,10 +63,11 @@ int launch_wgrad(const void* A, const void* G, float* partial, float* dW, GridSh
 int64_t bgrad_partials(int64_t V);
 int launch_bgrad(const void* G, int64_t V, float* partial, float* db, void* stream);
 
-// loss = mean over voxels and LN_COUT channels of (out - target)^2 (added into *loss via
-// partial sums); G = d loss / d out as BF16 16-channel tensor (channels >= LN_COUT zero)
+// loss = mean over voxels and nc (3 or 4) channels of (out - target)^2 (written to *loss via
+// partial sums); G = d loss / d out as BF16 16-channel tensor (channels >= nc zero)
 int64_t mse_partials(int64_t V);
-int launch_mse(const float* out, const float* target, int64_t V, void* G, double* partial, double* loss, void* stream);
+int launch_mse(const float* out, const float* target, int64_t V, int nc, void* G, double* partial, double* loss,
+               void* stream);
 
 // Adam (beta1 0.9, beta2 0.999, eps 1e-8) on n parameters, step >= 1
 int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, int step, void* stream);
@@ -74,26 +79,29 @@ int launch_pack(const float* params, uint32_t* fwd, uint32_t* bwd, void* stream)
 // FP32 [V][cin] -> BF16 [V][16] (zero padded)
 int launch_to_bf16(int64_t V, int cin, const float* src, void* X, void* stream);
 
-// sum over voxels with a free node of sum_c (z0[e + c E] / dinv[e + c E])^2, e = gent[g],
+// In the feature kernels, nc = 3 or 4 components per node (vectors of nc * E values, component
+// c of entry e at [e + c E]); velocity components count only at free nodes, the pressure
+// (component 3) at every node.
+// sum over voxels of sum_c (z0[e + c E] / dinv[e + c E])^2 (free components), e = gent[g],
 // written to *out (partial: mse_partials(V) doubles)
-int launch_feature_norm(int64_t V, int64_t E, const int64_t* gent, const uint8_t* gfree, const float* z0,
+int launch_feature_norm(int64_t V, int64_t E, int nc, const int64_t* gent, const uint8_t* gfree, const float* z0,
                         const float* dinv, double* partial, double* out, void* stream);
 
 // features of the library-layout vectors r1, z0 on the grid; s = sqrt(*sumsq / count)
-// (1 if zero).  X (16-channel BF16, inference) or pin (LN_PAIR_IN-channel BF16) and
-// target = D e1 / s (FP32, 3 channels; e1 nullable -> no target), whichever is non-null.
-int launch_features(int64_t V, int64_t E, const int64_t* gent, const uint8_t* gfree, const float* logk,
+// (1 if zero).  X (16-channel BF16, inference) or pin (ln_pair_in(nc)-channel BF16) and
+// target = D e1 / s (FP32, nc channels; e1 nullable -> no target), whichever is non-null.
+int launch_features(int64_t V, int64_t E, int nc, const int64_t* gent, const uint8_t* gfree, const float* logk,
                     const float* r1, const float* z0, const float* e1, const float* dinv, const double* sumsq,
                     double count, void* X, void* pin, float* target, void* stream);
 
-// library layout from a 3-channel FP32 grid field: z[e + c E] = free ? s * out[g][c] * dinv[e + c E] : 0
-// (dinv and sumsq nullable: factor 1)
-int launch_grid_to_lib(int64_t E, const int64_t* e2g, const uint8_t* efree, const float* out, const float* dinv,
-                       const double* sumsq, double count, float* z, void* stream);
+// library layout from an nc-channel FP32 grid field: z[e + c E] = (component free) ?
+// s * out[g][c] * dinv[e + c E] : 0 (dinv and sumsq nullable: factor 1)
+int launch_grid_to_lib(int64_t E, int nc, const int64_t* e2g, const uint8_t* efree, const float* out,
+                       const float* dinv, const double* sumsq, double count, float* z, void* stream);
 
 // training crops of S^3 voxels: sample b takes pair idx[b] at origin org[3b..3b+2] (z, y, x)
-// of the PD x PH x PW pair grids
-int launch_crop(const void* pin, const float* ptg, int PD, int PH, int PW, const int32_t* idx, const int32_t* org,
-                int B, int S, void* X, float* target, void* stream);
+// of the PD x PH x PW pair grids (ln_pair_in(nc) input and nc target channels per voxel)
+int launch_crop(int nc, const void* pin, const float* ptg, int PD, int PH, int PW, const int32_t* idx,
+                const int32_t* org, int B, int S, void* X, float* target, void* stream);
 
 }  // namespace hhg

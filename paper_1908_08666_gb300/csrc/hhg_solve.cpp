@@ -1051,6 +1051,31 @@ void ensure_work64(hhg_ctx* c, int l) {
 double* work64(hhg_ctx* c, int l, int q) { return work<double>(c->lv(l))[q].as<double>(); }
 float* work32(hhg_ctx* c, int l, int q) { return work<float>(c->lv(l))[q].as<float>(); }
 
+void need_stokes_problem(hhg_ctx* c) { need_stokes(c); }
+void stokes_apply32(hhg_ctx* c, int l, const float* x, float* y) {
+  stokes_sweep<float>(c, l, OP_APPLY, nullptr, x, y, false);
+}
+double stokes_dot32(hhg_ctx* c, int l, const float* a, const float* b) { return sdot<float>(c, l, a, b); }
+double stokes_residual32(hhg_ctx* c, int l, const float* f, const float* x, float* r) {
+  return stokes_sweep<float>(c, l, OP_RESID, f, x, r, true);
+}
+double stokes_residual64(hhg_ctx* c, int l, const double* f, const double* x, double* r) {
+  return stokes_sweep<double>(c, l, OP_RESID, f, x, r, true);
+}
+void uzawa_zero32(hhg_ctx* c, int l, const float* f, float* x) {
+  CK(cudaMemsetAsync(x, 0, 4 * (size_t)c->lv(l).entries * sizeof(float), c->stream));
+  uzawa_vcycle<float>(c, l, f, x);
+}
+void schur_inv32(hhg_ctx* c, int l, const float* r, float* out) { schur_apply<float>(c, l, r, out); }
+void project_pressure32(hhg_ctx* c, int l, float* x) { project_pressure<float>(c, l, x); }
+void project_pressure64(hhg_ctx* c, int l, double* x) { project_pressure<double>(c, l, x); }
+void ensure_stokes_work(hhg_ctx* c, int l) {
+  ensure_swork<double>(c, l);
+  ensure_swork<float>(c, l);
+}
+double* stokes_work64(hhg_ctx* c, int l, int q) { return swork<double>(c->lv(l))[q].as<double>(); }
+float* stokes_work32(hhg_ctx* c, int l, int q) { return swork<float>(c->lv(l))[q].as<float>(); }
+
 }  // namespace host
 }  // namespace hhg
 
@@ -1467,9 +1492,13 @@ hhg_status hhg_solve(hhg_ctx* c, const hhg_solve_opts* o, const void* f, void* x
       project_pressure<double>(c, l, (double*)x);
       R.rel_residual = r0 > 0.0 ? std::sqrt(rr / r0) : 0.0;
       R.converged = R.rel_residual <= o->rtol;
-    } else if (o->method == HHG_SOLVE_IR_FCG_LEARNED || o->method == HHG_SOLVE_IR_FCG) {
+    } else if (o->method == HHG_SOLVE_IR_FCG_LEARNED || o->method == HHG_SOLVE_IR_FCG ||
+               o->method == HHG_SOLVE_STOKES_IR_FGCR_LEARNED || o->method == HHG_SOLVE_STOKES_IR_FGCR) {
       if (o->dt != HHG_F64) THROW(HHG_ERR_ARG, "iterative refinement needs FP64 f and x");
-      learned_ir(c, o, (const double*)f, (double*)x, o->method == HHG_SOLVE_IR_FCG_LEARNED, R);
+      const bool st = o->method == HHG_SOLVE_STOKES_IR_FGCR_LEARNED || o->method == HHG_SOLVE_STOKES_IR_FGCR;
+      if (st) need_stokes(c);
+      learned_ir(c, o, (const double*)f, (double*)x,
+                 o->method == HHG_SOLVE_IR_FCG_LEARNED || o->method == HHG_SOLVE_STOKES_IR_FGCR_LEARNED, R);
     } else {
       THROW(HHG_ERR_ARG, "method");
     }

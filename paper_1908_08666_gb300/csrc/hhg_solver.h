@@ -23,8 +23,27 @@ void ensure_work64(hhg_ctx* c, int l);
 double* work64(hhg_ctx* c, int l, int q);  // FP64 work vector q (3*E); 10 and 11 are free for drivers
 float* work32(hhg_ctx* c, int l, int q);   // FP32 work vector q (3*E); 10 and 11 are free for drivers
 
-// FP64 iterative refinement around FP32 flexible CG whose preconditioner is the V-cycle
-// plus the learned correction (use_net) or the V-cycle alone (hhg_learn.cpp)
+// Stokes (4*E vectors): saddle apply, inner product over the unique DoFs (free velocity,
+// all pressures), residual (returns |r|^2), x = 0 and one inexact Uzawa V-cycle, the
+// diagonal Schur surrogate out = r / (m / mu + (-C)_ii) on E values, zero-mean pressure
+// shift, work vectors (indices 8 and 9 free for drivers)
+void need_stokes_problem(hhg_ctx* c);
+void stokes_apply32(hhg_ctx* c, int l, const float* x, float* y);
+double stokes_dot32(hhg_ctx* c, int l, const float* a, const float* b);
+double stokes_residual32(hhg_ctx* c, int l, const float* f, const float* x, float* r);
+double stokes_residual64(hhg_ctx* c, int l, const double* f, const double* x, double* r);
+void uzawa_zero32(hhg_ctx* c, int l, const float* f, float* x);
+void schur_inv32(hhg_ctx* c, int l, const float* r, float* out);
+void project_pressure32(hhg_ctx* c, int l, float* x);
+void project_pressure64(hhg_ctx* c, int l, double* x);
+void ensure_stokes_work(hhg_ctx* c, int l);
+double* stokes_work64(hhg_ctx* c, int l, int q);
+float* stokes_work32(hhg_ctx* c, int l, int q);
+
+// FP64 iterative refinement around an FP32 flexible Krylov solver whose preconditioner is
+// the multigrid cycle plus the learned correction (use_net) or the cycle alone: flexible
+// CG with the V-cycle for elasticity, flexible GCR with the inexact Uzawa V-cycle for
+// Stokes (hhg_learn.cpp)
 void learned_ir(hhg_ctx* c, const hhg_solve_opts* o, const double* f, double* x, bool use_net, hhg_solve_report& R);
 
 }  // namespace host

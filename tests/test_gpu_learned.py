@@ -21,14 +21,14 @@ from hhg_gpu import Ctx, Pair, torch_cuda
 pytestmark = pytest.mark.gpu
 
 
-def _params(seed):
+def _params(seed, cout=LN.COUT):
     """Oracle initialisation perturbed so that every layer (biases included) matters."""
     rng = np.random.default_rng(seed)
-    Ws, bs = LN.init_params(seed)
+    Ws, bs = LN.init_params(seed, 2 * cout + 1, cout)
     Ws = [LN.bf16(W + 0.02 * rng.normal(size=W.shape) * (W != 0)) for W in Ws]
-    Ws[-1][:, :, LN.COUT:] = 0.0
+    Ws[-1][:, :, cout:] = 0.0
     bs = [0.05 * rng.normal(size=b.shape) for b in bs]
-    bs[-1][LN.COUT:] = 0.0
+    bs[-1][cout:] = 0.0
     return Ws, bs
 
 
@@ -66,46 +66,50 @@ def test_param_layout_roundtrip(ctx):
     assert abs(Wq[1].std() - np.sqrt(2.0 / (27 * 16))) < 0.1 * np.sqrt(2.0 / (27 * 16))
 
 
+@pytest.mark.parametrize("cout", [3, 4], ids=["elasticity", "stokes"])
 @pytest.mark.parametrize("kernel", [0, 1, 2], ids=["mma_sync", "tcgen05", "tma_tcgen05"])
 @pytest.mark.parametrize("shape", [(2, 5, 6, 19), (1, 3, 4, 16), (1, 1, 1, 1), (1, 9, 7, 40)])
-def test_forward_matches_oracle(ctx, shape, kernel):
+def test_forward_matches_oracle(ctx, shape, kernel, cout):
     t = ctx.torch
     B.hhg_learn_set_conv_kernel(ctx.h, kernel)
     Bn, D, H, W = shape
+    cin = 2 * cout + 1
     rng = np.random.default_rng(sum(shape))
-    Ws, bs = _params(2)
+    Ws, bs = _params(2, cout)
     B.hhg_learn_set_params(ctx.h, _flat(Ws, bs))
-    x = rng.normal(size=(Bn, D, H, W, LN.CIN)).astype(np.float32)
-    out = t.empty((Bn, D, H, W, 3), dtype=t.float32, device="cuda")
-    B.hhg_learn_forward(ctx.h, ctx.dev(x, t.float32), LN.CIN, Bn, D, H, W, out)
+    x = rng.normal(size=(Bn, D, H, W, cin)).astype(np.float32)
+    out = t.empty((Bn, D, H, W, cout), dtype=t.float32, device="cuda")
+    B.hhg_learn_forward(ctx.h, ctx.dev(x, t.float32), cin, Bn, D, H, W, out, cout)
     t.cuda.synchronize()
-    want, _ = LN.forward(x.astype(np.float64), Ws, bs)
+    want, _ = LN.forward(x.astype(np.float64), Ws, bs, cout=cout)
     got = out.cpu().numpy().astype(np.float64)
     scale = np.abs(want).max()
     assert np.abs(got - want).max() <= 1e-2 * scale
     assert np.linalg.norm(got - want) <= 3e-3 * np.linalg.norm(want)
 
 
+@pytest.mark.parametrize("cout", [3, 4], ids=["elasticity", "stokes"])
 @pytest.mark.parametrize("kernel", [0, 1, 2], ids=["mma_sync", "tcgen05", "tma_tcgen05"])
 @pytest.mark.parametrize("shape", [(2, 6, 5, 21), (1, 4, 4, 16)])
-def test_gradients_match_oracle(ctx, shape, kernel):
+def test_gradients_match_oracle(ctx, shape, kernel, cout):
     t = ctx.torch
     B.hhg_learn_set_conv_kernel(ctx.h, kernel)
     Bn, D, H, W = shape
+    cin = 2 * cout + 1
     rng = np.random.default_rng(10 + sum(shape))
-    Ws, bs = _params(3)
+    Ws, bs = _params(3, cout)
     B.hhg_learn_set_params(ctx.h, _flat(Ws, bs))
-    x = rng.normal(size=(Bn, D, H, W, LN.CIN)).astype(np.float32)
-    tgt = rng.normal(size=(Bn, D, H, W, 3)).astype(np.float32)
-    loss, g = B.hhg_learn_loss_grad(ctx.h, ctx.dev(x, t.float32), LN.CIN, ctx.dev(tgt, t.float32), Bn, D, H, W)
-    wl, dWs, dbs = LN.loss_and_grads(x.astype(np.float64), tgt.astype(np.float64), Ws, bs)
+    x = rng.normal(size=(Bn, D, H, W, cin)).astype(np.float32)
+    tgt = rng.normal(size=(Bn, D, H, W, cout)).astype(np.float32)
+    loss, g = B.hhg_learn_loss_grad(ctx.h, ctx.dev(x, t.float32), cin, ctx.dev(tgt, t.float32), Bn, D, H, W, cout)
+    wl, dWs, dbs = LN.loss_and_grads(x.astype(np.float64), tgt.astype(np.float64), Ws, bs, cout=cout)
     assert abs(loss - wl) <= 1e-3 * wl
     gW, gb = _unflat(g.astype(np.float64))
     for l in range(4):
         assert np.linalg.norm(gW[l] - dWs[l]) <= 2e-2 * np.linalg.norm(dWs[l]), l
         assert np.linalg.norm(gb[l] - dbs[l]) <= 2e-2 * np.linalg.norm(dbs[l]) + 1e-12, l
     # structural zeros: unused input channels of layer 0, unused outputs of the last layer
-    assert not gW[0][:, LN.CIN:, :].any() and not gW[3][:, :, LN.COUT:].any() and not gb[3][LN.COUT:].any()
+    assert not gW[0][:, cin:, :].any() and not gW[3][:, :, cout:].any() and not gb[3][cout:].any()
 
 
 @pytest.fixture(scope="module")
