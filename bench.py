@@ -527,6 +527,13 @@ def learned_stokes_bench(B, torch, dev, stream, train_level, eval_level, nfield,
             B.hhg_learn_collect_cg(h, train_level, scatter(h, train_level, f, 4, B.F32), iters)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
+    # per-channel RMS of the inputs and targets over the stored pairs (every 6th pair)
+    dims, _ = B.hhg_learn_grid(h, train_level)
+    xs, ts = [], []
+    for j in range(0, nfield * nrhs * iters, 6):
+        xp, tp = B.hhg_learn_get_pair(h, j, dims, nc=4)
+        xs.append(np.sqrt((xp.reshape(-1, 9).astype(np.float64) ** 2).mean(axis=0)))
+        ts.append(np.sqrt((tp.reshape(-1, 4).astype(np.float64) ** 2).mean(axis=0)))
     B.hhg_learn_init(h, 1)
     tr = B.hhg_learn_train(h, steps=steps, batch=8, crop=32, lr=2e-3, seed=2)
     params = B.hhg_learn_get_params(h)
@@ -546,7 +553,9 @@ def learned_stokes_bench(B, torch, dev, stream, train_level, eval_level, nfield,
                          "pair_source": "errors of %d FGCR iterations x %d RHS per field" % (iters, nrhs),
                          "pair_generation_s": round(gen_s, 3), "steps": steps, "batch": "8 x 32^3",
                          "loss_first": tr["loss_first"], "loss_last": tr["loss_last"],
-                         "train_s": round(tr["seconds"], 3)},
+                         "train_s": round(tr["seconds"], 3),
+                         "input_rms_per_channel": [round(float(v), 4) for v in np.mean(xs, axis=0)],
+                         "target_rms_per_channel": [round(float(v), 4) for v in np.mean(ts, axis=0)]},
                "eval_level": eval_level, "rtol": 1e-8,
                "workload": "Stokes, 6-macro cube, level %d, viscosity sphere 1 / 1e3, f ~ U[-1,1] (seed 4)"
                            % eval_level}

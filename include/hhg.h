@@ -379,15 +379,15 @@ hhg_status hhg_residual_noalloc(hhg_ctx* ctx, int level, hhg_dtype dt, const voi
  *
  * Input features per voxel (cin = 2 nc + 1 channels: 7 elasticity, 9 Stokes): r1/s (nc),
  * D z0/s (nc), log k - mean log k (1), where for a residual r: z0 = a0 v, v = MG(r),
- * with the optimal step length a0 (elasticity: energy norm, a0 = (v, r)/(v, A v);
- * Stokes: residual norm, a0 = (K v, r)/(K v, K v)); r1 = r - K z0; D = point diagonal
+ * with the energy-optimal step length a0 = (v, r)/(v, A v) for elasticity and a0 = 1 for
+ * Stokes (the Uzawa cycle is a convergent iteration itself); r1 = r - K z0; D = point diagonal
  * of A (velocity) and, for the pressure, the diagonal Schur surrogate m_i/mu_i + (-C)_ii;
  * s = RMS of D z0 over the free DoFs (velocity at free nodes, pressure everywhere).
  * Output (nc channels): D c / s.  The preconditioned vector is z = a z0 + b c with
  * (a, b) minimising over span{z0, c} the energy norm of the error K^-1 r - z
  * (elasticity) or the residual norm |r - K z|_2 (Stokes), by 2x2 normal equations; when
  * that system is singular or not finite, z = z0.  An application never does worse in
- * that norm than the scaled multigrid step alone.
+ * that norm than the best multiple of the multigrid step alone.
  *
  * Training pairs.  From an error e: z0 as above for r = K e, e1 = e - z0 (Stokes: its
  * pressure shifted to zero mass-weighted mean), r1 = r - K z0; the pair is
@@ -473,7 +473,7 @@ typedef struct {
   int64_t fallbacks;     /* of which fell back to the V-cycle (b = 0) */
   double alpha_mean, alpha_min, alpha_max;  /* of the weight b / a */
   double gain_mean;      /* reduction (energy norm^2; Stokes: residual norm^2) added by c,
-                            relative to the scaled multigrid step's own */
+                            relative to that of the best multiple of the multigrid step */
 } hhg_learn_stats_report;
 
 /* Statistics since the last reset (reset != 0 clears them after reading). */

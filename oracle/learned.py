@@ -29,10 +29,12 @@ Stokes (``stokes_*``; vectors (N, 4): velocity, then pressure; K the saddle oper
 velocity-Dirichlet identity rows, v = one inexact Uzawa V-cycle of the residual): the
 same with 4 components, CIN = 9 input channels (r1/s, D z0/s, log mu) and 4 outputs,
 where D is the velocity point diagonal and, for the pressure, the Schur surrogate
-m_i / mu_i + (-C)_ii; s is the RMS of D z0 over the free velocity DoFs and all
-pressures; and, K being indefinite, the residual norm replaces the energy norm: z0 = a0 v
-with a0 = (K v, r) / (K v, K v), and (a, b) minimise |r - K (a z0 + b c)|_2.  The
-training error e1 = e - z0 has its pressure shifted to zero mass-weighted mean.
+m_i / mu_i + (-C)_ii; the velocity channels and targets are scaled by s, the RMS of
+D z0 over the free velocity DoFs, the pressure ones by s_p, the RMS of D z0 over the
+pressures (the two diagonals differ by orders of magnitude); z0 = v unscaled (the Uzawa cycle is a convergent iteration by itself); and, K
+being indefinite, the residual norm replaces the energy norm: (a, b) minimise
+|r - K (a z0 + b c)|_2.  The training error e1 = e - z0 has its pressure shifted to zero
+mass-weighted mean.
 """
 
 from __future__ import annotations
@@ -234,28 +236,33 @@ def stokes_diag(H, l):
 
 
 def stokes_features(vox, dims, dirichlet, k, r1, z0, D):
-    """Input grid (1, D, H, W, 9) and the scale s for (N, 4) fields r1, z0, D."""
+    """Input grid (1, D, H, W, 9) and the per-component scales (N, 4) (s on the velocity
+    components, s_p on the pressure) for (N, 4) fields r1, z0, D."""
+    d = np.asarray(dirichlet)
     on = np.ones(z0.shape, dtype=bool)
-    on[np.asarray(dirichlet), :3] = False
-    w = (D * z0)[on]
-    s2 = (w**2).sum() / max(on.sum(), 1)
-    s = np.sqrt(s2) if s2 > 0 else 1.0
+    on[d, :3] = False
+    w = D * z0
+
+    def rms(v):
+        s2 = (v**2).sum() / max(v.size, 1)
+        return np.sqrt(s2) if s2 > 0 else 1.0
+
+    sc = np.empty(z0.shape)
+    sc[:, :3] = rms(w[:, :3][on[:, :3]])
+    sc[:, 3] = rms(w[:, 3])
     X = np.zeros((1,) + dims + (STOKES_CIN,))
     lk = np.log(k)
     X[0, vox[:, 0], vox[:, 1], vox[:, 2], 8] = lk - lk.mean()
     f = np.zeros((len(k), 8))
-    f[:, :4] = np.where(on, r1 / s, 0.0)
-    f[:, 4:] = np.where(on, D * z0 / s, 0.0)
+    f[:, :4] = np.where(on, r1 / sc, 0.0)
+    f[:, 4:] = np.where(on, w / sc, 0.0)
     X[0, vox[:, 0], vox[:, 1], vox[:, 2], :8] = f
-    return X, s
+    return X, sc
 
 
-def _stokes_scaled_step(H, l, r, v):
-    """Residual-optimal multiple a0 v of the cycle output v for the residual r, and K a0 v."""
-    Kv = H.apply(l, v)
-    den = H.dot(l, Kv, Kv)
-    a0 = H.dot(l, Kv, r) / den if den > 0 else 1.0
-    return a0 * v, a0 * Kv
+def _stokes_step(H, l, r, v):
+    """The Stokes multigrid step z0 = v (unscaled) and K z0."""
+    return np.array(v, dtype=np.float64), H.apply(l, v)
 
 
 def stokes_correction(H, l, vox, dims, k, r, v, Ws, bs):
@@ -263,7 +270,7 @@ def stokes_correction(H, l, vox, dims, k, r, v, Ws, bs):
     z0 = a0 v, c from the network, z = a z0 + b c minimising |r - K z|_2."""
     d = H.lv[l].dirichlet
     D = stokes_diag(H, l)
-    z0, Kz0 = _stokes_scaled_step(H, l, r, v)
+    z0, Kz0 = _stokes_step(H, l, r, v)
     r1 = r - Kz0
     r1[d, :3] = 0.0
     X, s = stokes_features(vox, dims, d, k, r1, z0, D)
@@ -283,7 +290,7 @@ def stokes_training_pair(H, l, vox, dims, k, e, mg):
     d = H.lv[l].dirichlet
     D = stokes_diag(H, l)
     r = H.residual(l, np.zeros_like(e), -e)  # K e with zero velocity-Dirichlet rows
-    z0, _ = _stokes_scaled_step(H, l, r, mg(r))
+    z0, _ = _stokes_step(H, l, r, mg(r))
     e1 = H.project_pressure(l, e - z0)
     r1 = H.residual(l, np.zeros_like(e1), -e1)
     X, s = stokes_features(vox, dims, d, k, r1, z0, D)

@@ -183,6 +183,9 @@ struct LearnState {
   // training pairs of one level: inputs (ln_pair_in(pair_nc) BF16 per voxel) and targets
   // (pair_nc FP32), pair_nc = components of the problem they came from
   int pair_level = -1, pair_nc = 3;
+  // per-pair factor of the targets in training (Stokes: 1 / RMS of the pair's target, so
+  // that every pair weighs the same; elasticity: 1)
+  std::vector<float> pair_tscale;
   int64_t pair_cap = 0, pair_count = 0;
   DevMem pin, ptg;
   // activation buffers (16-channel BF16), outputs, gradients, partial sums

@@ -6,19 +6,21 @@
 // (nc = 4: velocity and pressure).  Kernels in hhg_learn.cu; conventions in hhg_learn.h.
 //
 // Preconditioner application for a residual r (FP32), K the system operator, MG one cycle:
-//   z0 = a0 MG(r), a0 = optimal step length of the cycle's output: in the energy norm
-//        (elasticity, a0 = (z0, r) / (z0, K z0)) or the residual norm (Stokes, whose
-//        operator is indefinite: a0 = (K z0, r) / (K z0, K z0)),
-//   r1 = r - K z0       (the residual the scaled step leaves),
+//   z0 = a0 MG(r), a0 = the energy-optimal step length (z0, r) / (z0, K z0) of the cycle's
+//        output for elasticity; a0 = 1 for Stokes (the Uzawa cycle is itself a convergent
+//        iteration, and K is indefinite),
+//   r1 = r - K z0       (the residual the step leaves),
 //   c  = s D^-1 N(features(r1, z0, log k))   (network correction),
-//   z  = a z0 + b c,  (a, b) minimising the same norm (of the error K^-1 r - z, resp. of
-//        the residual r - K z) over span{z0, c}  (2x2 normal equations).
-// Hence an application never does worse (in that norm) than the scaled cycle alone, and
+//   z  = a z0 + b c,  (a, b) minimising over span{z0, c} the energy norm of the error
+//        K^-1 r - z (elasticity) or the residual norm |r - K z|_2 (Stokes) (2x2 normal
+//        equations).
+// Hence an application never does worse (in that norm) than the best multiple of the
+// cycle's output alone, and
 // the network is not rewarded for what a rescaling of z0 would do (the Krylov solvers are
 // invariant to that); when the 2x2 system is singular or not finite the application falls
 // back to z = z0.
 //
-// Training pairs: for an error e, one multigrid step gives z0 = a0 MG(K e), the
+// Training pairs: for an error e, one multigrid step gives z0 = a0 MG(K e) (a0 as above), the
 // remaining error e1 = e - z0 (Stokes: pressure shifted to zero mean, the constant being
 // invisible to K) and residual r1 = K e1; the pair is (features(r1, z0), D e1 / s).  The
 // errors are either random (further steps continue from e1) or the errors of the plain
@@ -368,25 +370,45 @@ const float* sys_dinv(hhg_ctx* c, int l, LearnGrid& G) {
   return G.dinv4.as<float>();
 }
 
-// number of free DoFs on the grid (the feature scale s is an RMS over them)
-double feature_count(hhg_ctx* c, const LearnGrid& G) {
-  return std::max(1.0, 3.0 * (double)G.nfree + (is_stokes(c) ? (double)G.nnode : 0.0));
+// Scales of the features, as sums of squares and DoF counts: D z0 over the free
+// velocity-like DoFs (S.dscal[0]) and, for Stokes, over the pressure (S.dscal[2]; its
+// diagonal differs from the velocity's by orders of magnitude, so it gets its own scale)
+struct FeatureScale {
+  const double* su;
+  double cu;
+  const double* sp;
+  double cp;
+};
+
+FeatureScale feature_scales(hhg_ctx* c, int l, LearnState& S, LearnGrid& G, const float* z0, const float* dinv) {
+  const int nc = ncomp(c);
+  const int64_t E = c->lv(l).entries;
+  if (!S.dscal.p) CK(S.dscal.alloc(8 * sizeof(double)));
+  if (S.dpart.bytes < (size_t)mse_partials(G.V) * sizeof(double))
+    CK(S.dpart.alloc((size_t)mse_partials(G.V) * sizeof(double)));
+  double* ss = S.dscal.as<double>();
+  CK(launch_feature_norm(G.V, E, nc, 0, 3, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), z0, dinv,
+                         S.dpart.as<double>(), ss, c->stream));
+  FeatureScale f{ss, std::max(1.0, 3.0 * (double)G.nfree), nullptr, 1.0};
+  if (nc == 4) {
+    CK(launch_feature_norm(G.V, E, nc, 3, 4, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), z0, dinv,
+                           S.dpart.as<double>(), ss + 2, c->stream));
+    f.sp = ss + 2;
+    f.cp = std::max(1.0, (double)G.nnode);
+  }
+  return f;
 }
 
-// Scale the multigrid correction z0 (and K z0) to its optimal length for the residual r:
-// z0 <- a0 z0 with a0 = (z0, r) / (z0, K z0) (energy norm; elasticity) or
-// a0 = (K z0, r) / (K z0, K z0) (residual norm; Stokes), unchanged when that is not
-// finite.  Returns the reduction of the squared norm by the scaled step, (z0, r) resp.
-// (K z0, r) after scaling.
-double scale_mg_step(hhg_ctx* c, int l, const float* r, float* z0, float* az0) {
+// Elasticity: scale the V-cycle correction z0 (and K z0) to its energy-optimal length for
+// the residual r, z0 <- a0 z0 with a0 = (z0, r) / (z0, K z0) (unchanged when that is not
+// finite).  Stokes: no scaling.
+void scale_mg_step(hhg_ctx* c, int l, const float* r, float* z0, float* az0) {
+  if (is_stokes(c)) return;
   const int64_t n = sys_n(c, l);
-  const bool st = is_stokes(c);
-  const double num = st ? sys_dot(c, l, az0, r) : sys_dot(c, l, z0, r);
-  const double den = st ? sys_dot(c, l, az0, az0) : sys_dot(c, l, z0, az0);
+  const double num = sys_dot(c, l, z0, r), den = sys_dot(c, l, z0, az0);
   const double a0 = (den > 0.0 && std::isfinite(num / den)) ? num / den : 1.0;
   CK(launch_axpby<float>(n, (float)a0, z0, 0.f, z0, c->stream));
   CK(launch_axpby<float>(n, (float)a0, az0, 0.f, az0, c->stream));
-  return a0 * num;
 }
 
 // z and az = K z of one preconditioner application (see the file comment); use_net =
@@ -412,27 +434,26 @@ double precondition(hhg_ctx* c, int l, const float* r, float* z, float* az, bool
   float* acc = lwork(c, G, l, LW_AC);
   const float* dinv = sys_dinv(c, l, G);
   ensure_acts(c, S, G.V);
-  // after scaling, the first normal-equation entry and right-hand side are both rv
-  const double rv = scale_mg_step(c, l, r, z0, az0);
+  scale_mg_step(c, l, r, z0, az0);
   copy32(c, l, r, r1);
   CK(launch_axpby<float>(n, -1.f, az0, 1.f, r1, c->stream));
-  double* ssum = S.dscal.as<double>();
-  CK(launch_feature_norm(G.V, E, nc, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), z0, dinv, S.dpart.as<double>(),
-                         ssum, c->stream));
-  const double cnt = feature_count(c, G);
+  const FeatureScale fs = feature_scales(c, l, S, G, z0, dinv);
   CK(launch_features(G.V, E, nc, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), G.logk.as<float>(), r1, z0, nullptr,
-                     dinv, ssum, cnt, S.act[0].p, nullptr, nullptr, c->stream));
+                     dinv, fs.su, fs.cu, fs.sp, fs.cp, S.act[0].p, nullptr, nullptr, c->stream));
   forward_inference(c, S, GridShape{1, G.D, G.H, G.W}, S.out.as<float>(), nc);
-  CK(launch_grid_to_lib(E, nc, G.e2g.as<int64_t>(), G.efree.as<uint8_t>(), S.out.as<float>(), dinv, ssum, cnt, cc,
-                        c->stream));
+  CK(launch_grid_to_lib(E, nc, G.e2g.as<int64_t>(), G.efree.as<uint8_t>(), S.out.as<float>(), dinv, fs.su, fs.cu,
+                        fs.sp, fs.cp, cc, c->stream));
   sys_apply(c, l, cc, acc);
   // optimal a, b: [m11 m12; m12 m22] (a, b) = (rv, rc) with the energy inner product
   // (u, K v) (elasticity) or the residual one (K u, K v) (Stokes)
-  const double m11 = rv;
+  const double m11 = st ? sys_dot(c, l, az0, az0) : sys_dot(c, l, z0, az0);
+  const double rv = st ? sys_dot(c, l, az0, r) : sys_dot(c, l, z0, r);
   const double m12 = st ? sys_dot(c, l, acc, az0) : sys_dot(c, l, cc, az0);
   const double m22 = st ? sys_dot(c, l, acc, acc) : sys_dot(c, l, cc, acc);
   const double rc = st ? sys_dot(c, l, acc, r) : sys_dot(c, l, cc, r);
   const double det = m11 * m22 - m12 * m12;
+  // without c: the best multiple of z0, with a0 = rv / m11 (fallback a = 1 keeps z0 itself)
+  const double a_only = (m11 > 0.0 && std::isfinite(rv / m11)) ? rv / m11 : 1.0;
   double a = 1.0, b = 0.0;
   if (m11 > 0.0 && m22 > 0.0 && det > 1e-6 * m11 * m22 && std::isfinite(det) && std::isfinite(rc)) {
     a = (rv * m22 - m12 * rc) / det;
@@ -448,9 +469,9 @@ double precondition(hhg_ctx* c, int l, const float* r, float* z, float* az, bool
   S.alpha_sum += w;
   S.alpha_min = S.applications == 1 ? w : std::min(S.alpha_min, w);
   S.alpha_max = S.applications == 1 ? w : std::max(S.alpha_max, w);
-  // extra reduction of the squared norm over the scaled multigrid step, relative to that
-  // step's own
-  if (m11 > 0.0) S.gain_sum += (a * rv + b * rc - m11) / m11;
+  // extra reduction of the squared norm over the best multiple of z0, relative to that
+  // step's own (a_only rv)
+  if (m11 > 0.0 && a_only * rv > 0.0) S.gain_sum += (a * rv + b * rc - a_only * rv) / (a_only * rv);
   copy32(c, l, z0, z);
   copy32(c, l, az0, az);
   if (b != 0.0) {
@@ -570,8 +591,9 @@ SolverResult fgcr(hhg_ctx* c, int l, const float* f, float* x, double rtol, int 
   return res;
 }
 
-// One training pair from the error e (library layout): r = K e, z0 = a0 MG(r) with the
-// optimal a0, e1 = e - z0 (Stokes: pressure shifted to zero mean), r1 = r - K z0; stores
+// One training pair from the error e (library layout): r = K e, z0 = a0 MG(r) (elasticity:
+// the energy-optimal a0; Stokes: a0 = 1), e1 = e - z0 (Stokes: pressure shifted to zero
+// mean), r1 = r - K z0; stores
 // (features(r1, z0), D e1 / s).  e1_out (nullable) receives e1.  Uses the work vectors
 // Z0, AZ0, R1, C, AC.
 void store_pair(hhg_ctx* c, int l, const float* e, float* e1_out) {
@@ -588,11 +610,6 @@ void store_pair(hhg_ctx* c, int l, const float* e, float* e1_out) {
   float* r = lwork(c, G, l, LW_C);
   float* e1 = lwork(c, G, l, LW_AC);
   const float* dinv = sys_dinv(c, l, G);
-  if (S.dpart.bytes < (size_t)mse_partials(G.V) * sizeof(double))
-    CK(S.dpart.alloc((size_t)mse_partials(G.V) * sizeof(double)));
-  if (!S.dscal.p) CK(S.dscal.alloc(8 * sizeof(double)));
-  double* ssum = S.dscal.as<double>();
-  const double cnt = feature_count(c, G);
   sys_apply(c, l, e, r);
   sys_mg(c, l, r, z0);
   sys_apply(c, l, z0, az0);
@@ -602,12 +619,27 @@ void store_pair(hhg_ctx* c, int l, const float* e, float* e1_out) {
   copy32(c, l, e, e1);
   CK(launch_axpby<float>(n, -1.f, z0, 1.f, e1, c->stream));
   if (nc == 4) project_pressure32(c, l, e1);
-  CK(launch_feature_norm(G.V, E, nc, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), z0, dinv, S.dpart.as<double>(),
-                         ssum, c->stream));
+  const FeatureScale fs = feature_scales(c, l, S, G, z0, dinv);
   const int64_t p = S.pair_count++;
+  float* tg = S.ptg.as<float>() + (size_t)p * G.V * nc;
   CK(launch_features(G.V, E, nc, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), G.logk.as<float>(), r1, z0, e1, dinv,
-                     ssum, cnt, nullptr, (char*)S.pin.p + (size_t)p * G.V * ln_pair_in(nc) * 2,
-                     S.ptg.as<float>() + (size_t)p * G.V * nc, c->stream));
+                     fs.su, fs.cu, fs.sp, fs.cp, nullptr, (char*)S.pin.p + (size_t)p * G.V * ln_pair_in(nc) * 2, tg,
+                     c->stream));
+  float ts = 1.f;
+  if (nc == 4) {
+    // the 2x2 combination fixes the size of the correction, so only its direction matters:
+    // each Stokes pair's target is trained at unit RMS (the cycle's step is much smaller
+    // than the error for some pairs, whose raw targets would otherwise dominate the loss)
+    double* ss = S.dscal.as<double>() + 4;
+    if (S.dpart.bytes < (size_t)mse_partials((int64_t)G.V * nc) * sizeof(double))
+      CK(S.dpart.alloc((size_t)mse_partials((int64_t)G.V * nc) * sizeof(double)));
+    CK(launch_sumsq((int64_t)G.V * nc, tg, S.dpart.as<double>(), ss, c->stream));
+    CK(cudaMemcpyAsync(c->pinned, ss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    wait_stream(c);
+    const double ms = c->pinned[0] / ((double)G.V * nc);
+    ts = (ms > 0.0 && std::isfinite(ms)) ? (float)(1.0 / std::sqrt(ms)) : 1.f;
+  }
+  S.pair_tscale[p] = ts;
   if (e1_out) copy32(c, l, e1, e1_out);
 }
 
@@ -785,6 +817,7 @@ hhg_status hhg_learn_reserve_pairs(hhg_ctx* c, int level, int64_t capacity) {
     CK(S.pin.alloc((size_t)capacity * G.V * ln_pair_in(nc) * 2));
     CK(S.ptg.alloc((size_t)capacity * G.V * nc * sizeof(float)));
     S.pair_nc = nc;
+    S.pair_tscale.assign(capacity, 1.f);
     S.pair_level = level;
     S.pair_cap = capacity;
     S.pair_count = 0;
@@ -802,7 +835,7 @@ hhg_status hhg_learn_collect(hhg_ctx* c, int level, const float* e0_grid, int cy
     LearnGrid& G = grid(c, level);
     float* e = lwork(c, G, level, LW_E);
     CK(launch_grid_to_lib(c->lv(level).entries, ncomp(c), G.e2g.as<int64_t>(), G.efree.as<uint8_t>(), e0_grid, nullptr,
-                          nullptr, 1.0, e, c->stream));
+                          nullptr, 1.0, nullptr, 1.0, e, c->stream));
     for (int j = 0; j < cycles; ++j) store_pair(c, level, e, e);
     wait_stream(c);
     if (count) *count = S.pair_count;
@@ -920,12 +953,14 @@ hhg_status hhg_learn_train(hhg_ctx* c, const hhg_learn_train_opts* o, hhg_learn_
       org[3 * q + 1] = (int32_t)(splitmix64(rs) % (uint64_t)(G.H - Sc + 1));
       org[3 * q + 2] = (int32_t)(splitmix64(rs) % (uint64_t)(G.W - Sc + 1));
     }
-    DevMem didx, dorg, dloss;
+    DevMem didx, dorg, dloss, dts;
     upload(didx, idx);
     upload(dorg, org);
+    std::vector<float> ts(S.pair_tscale.begin(), S.pair_tscale.begin() + S.pair_count);
+    upload(dts, ts);
     CK(dloss.alloc((size_t)o->steps * sizeof(double)));
     for (int st = 0; st < o->steps; ++st) {
-      CK(launch_crop(S.pair_nc, S.pin.p, S.ptg.as<float>(), G.D, G.H, G.W, didx.as<int32_t>() + (size_t)st * o->batch,
+      CK(launch_crop(S.pair_nc, S.pin.p, S.ptg.as<float>(), dts.as<float>(), G.D, G.H, G.W, didx.as<int32_t>() + (size_t)st * o->batch,
                      dorg.as<int32_t>() + (size_t)st * o->batch * 3, o->batch, Sc, S.act[0].p, S.tgt.as<float>(),
                      c->stream));
       forward(c, S, s, S.out.as<float>(), S.pair_nc);

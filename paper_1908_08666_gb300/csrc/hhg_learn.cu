@@ -777,7 +777,8 @@ __device__ __forceinline__ double feature_scale(const double* sumsq, double coun
 // displacement, zero on Dirichlet nodes) or 4 (Stokes: velocity, zero on velocity-Dirichlet
 // nodes, then the pressure, free at every node).  dinv holds NC * E values.
 template <int NC>
-__global__ void __launch_bounds__(RED_BLOCK) k_feature_norm(int64_t V, int64_t E, const int64_t* __restrict__ gent,
+__global__ void __launch_bounds__(RED_BLOCK) k_feature_norm(int64_t V, int64_t E, int c0, int c1,
+                                                            const int64_t* __restrict__ gent,
                                                             const uint8_t* __restrict__ gfree,
                                                             const float* __restrict__ z0,
                                                             const float* __restrict__ dinv,
@@ -790,7 +791,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_feature_norm(int64_t V, int64_t E
     const bool fr = gfree[g] != 0;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      if (c < 3 && !fr) continue;
+      if (c < c0 || c >= c1 || (c < 3 && !fr)) continue;
       const double w = (double)z0[e + c * E] / (double)dinv[e + c * E];
       acc += w * w;
     }
@@ -806,15 +807,18 @@ __global__ void __launch_bounds__(RED_BLOCK) k_feature_norm(int64_t V, int64_t E
 }
 
 // channels: r1 / s (NC), D z0 / s (NC), log k - mean (1); X holds 16 channels per voxel,
-// pin the first 8 * PW (PW = 1 for NC = 3, 2 for NC = 4)
+// pin the first 8 * PW (PW = 1 for NC = 3, 2 for NC = 4).  The pressure (component 3) has
+// its own scale s_p = sqrt(*sumsq_p / count_p).
 template <int NC>
 __global__ void k_features(int64_t V, int64_t E, const int64_t* __restrict__ gent, const uint8_t* __restrict__ gfree,
                            const float* __restrict__ logk, const float* __restrict__ r1,
                            const float* __restrict__ z0, const float* __restrict__ e1,
                            const float* __restrict__ dinv, const double* __restrict__ sumsq, double count,
-                           uint32_t* __restrict__ X, uint32_t* __restrict__ pin, float* __restrict__ target) {
+                           const double* __restrict__ sumsq_p, double count_p, uint32_t* __restrict__ X,
+                           uint32_t* __restrict__ pin, float* __restrict__ target) {
   constexpr int PW = NC == 4 ? 2 : 1;
-  const float inv = (float)(1.0 / feature_scale(sumsq, count));
+  const float inv_u = (float)(1.0 / feature_scale(sumsq, count));
+  const float inv_p = NC == 4 ? (float)(1.0 / feature_scale(sumsq_p, count_p)) : inv_u;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < V; g += (int64_t)gridDim.x * blockDim.x) {
     float f[16];
 #pragma unroll
@@ -829,6 +833,7 @@ __global__ void k_features(int64_t V, int64_t E, const int64_t* __restrict__ gen
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         if (c < 3 && !fr) continue;
+        const float inv = c < 3 ? inv_u : inv_p;
         const float d = 1.f / dinv[e + c * E];
         f[c] = r1[e + c * E] * inv;
         f[NC + c] = z0[e + c * E] * d * inv;
@@ -859,23 +864,26 @@ __global__ void k_features(int64_t V, int64_t E, const int64_t* __restrict__ gen
 template <int NC>
 __global__ void k_grid_to_lib(int64_t E, const int64_t* __restrict__ e2g, const uint8_t* __restrict__ efree,
                               const float* __restrict__ out, const float* __restrict__ dinv,
-                              const double* __restrict__ sumsq, double count, float* __restrict__ z) {
-  const float s = (float)feature_scale(sumsq, count);
+                              const double* __restrict__ sumsq, double count, const double* __restrict__ sumsq_p,
+                              double count_p, float* __restrict__ z) {
+  const float s_u = (float)feature_scale(sumsq, count);
+  const float s_p = NC == 4 ? (float)feature_scale(sumsq_p, count_p) : s_u;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
     const bool f = efree[e] != 0;
     const int64_t g = e2g[e];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const bool on = c < 3 ? f : g >= 0;
+      const float s = c < 3 ? s_u : s_p;
       z[e + c * E] = on ? s * out[g * NC + c] * (dinv ? dinv[e + c * E] : 1.f) : 0.f;
     }
   }
 }
 
 template <int NC>
-__global__ void k_crop(const uint4* __restrict__ pin, const float* __restrict__ ptg, int PD, int PH, int PW_,
-                       const int32_t* __restrict__ idx, const int32_t* __restrict__ org, int B, int S,
-                       uint4* __restrict__ X, float* __restrict__ target) {
+__global__ void k_crop(const uint4* __restrict__ pin, const float* __restrict__ ptg, const float* __restrict__ tscale,
+                       int PD, int PH, int PW_, const int32_t* __restrict__ idx, const int32_t* __restrict__ org,
+                       int B, int S, uint4* __restrict__ X, float* __restrict__ target) {
   constexpr int PW = NC == 4 ? 2 : 1;
   const int64_t V = (int64_t)B * S * S * S;
   const int64_t N3 = (int64_t)PD * PH * PW_;
@@ -888,8 +896,28 @@ __global__ void k_crop(const uint4* __restrict__ pin, const float* __restrict__ 
                         (org[3 * b + 2] + x);
     X[2 * v] = pin[src * PW];
     X[2 * v + 1] = PW == 2 ? pin[src * PW + 1] : make_uint4(0u, 0u, 0u, 0u);
+    const float ts = tscale ? tscale[idx[b]] : 1.f;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) target[v * NC + c] = ptg[src * NC + c];
+    for (int c = 0; c < NC; ++c) target[v * NC + c] = ts * ptg[src * NC + c];
+  }
+}
+
+// partial[block] = sum of x[i]^2 over the block's grid-stride share
+__global__ void __launch_bounds__(RED_BLOCK) k_sumsq(const float* __restrict__ x, int64_t n,
+                                                     double* __restrict__ partial) {
+  __shared__ double s[RED_BLOCK / 32];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    acc += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < RED_BLOCK / 32; ++w) t += s[w];
+    partial[blockIdx.x] = t;
   }
 }
 
@@ -1064,39 +1092,49 @@ int launch_to_bf16(int64_t V, int cin, const float* src, void* X, void* stream) 
   return (int)cudaGetLastError();
 }
 
-int launch_feature_norm(int64_t V, int64_t E, int nc, const int64_t* gent, const uint8_t* gfree, const float* z0,
-                        const float* dinv, double* partial, double* out, void* stream) {
+int launch_feature_norm(int64_t V, int64_t E, int nc, int c0, int c1, const int64_t* gent, const uint8_t* gfree,
+                        const float* z0, const float* dinv, double* partial, double* out, void* stream) {
   if (nc != 3 && nc != 4) return (int)cudaErrorInvalidValue;
   const int64_t nb = red_blocks(V);
   (nc == 4 ? k_feature_norm<4> : k_feature_norm<3>)<<<(unsigned)nb, RED_BLOCK, 0, (cudaStream_t)stream>>>(
-      V, E, gent, gfree, z0, dinv, partial);
+      V, E, c0, c1, gent, gfree, z0, dinv, partial);
   k_sum_into<<<1, RED_BLOCK, 0, (cudaStream_t)stream>>>(partial, (int)nb, out);
   return (int)cudaGetLastError();
 }
 
 int launch_features(int64_t V, int64_t E, int nc, const int64_t* gent, const uint8_t* gfree, const float* logk,
                     const float* r1, const float* z0, const float* e1, const float* dinv, const double* sumsq,
-                    double count, void* X, void* pin, float* target, void* stream) {
+                    double count, const double* sumsq_p, double count_p, void* X, void* pin, float* target,
+                    void* stream) {
   if (nc != 3 && nc != 4) return (int)cudaErrorInvalidValue;
   (nc == 4 ? k_features<4> : k_features<3>)<<<blocks_for(V, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(
-      V, E, gent, gfree, logk, r1, z0, e1, dinv, sumsq, count, (uint32_t*)X, (uint32_t*)pin, target);
+      V, E, gent, gfree, logk, r1, z0, e1, dinv, sumsq, count, sumsq_p, count_p, (uint32_t*)X, (uint32_t*)pin,
+      target);
   return (int)cudaGetLastError();
 }
 
 int launch_grid_to_lib(int64_t E, int nc, const int64_t* e2g, const uint8_t* efree, const float* out,
-                       const float* dinv, const double* sumsq, double count, float* z, void* stream) {
+                       const float* dinv, const double* sumsq, double count, const double* sumsq_p, double count_p,
+                       float* z, void* stream) {
   if (nc != 3 && nc != 4) return (int)cudaErrorInvalidValue;
   (nc == 4 ? k_grid_to_lib<4> : k_grid_to_lib<3>)<<<blocks_for(E, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(
-      E, e2g, efree, out, dinv, sumsq, count, z);
+      E, e2g, efree, out, dinv, sumsq, count, sumsq_p, count_p, z);
   return (int)cudaGetLastError();
 }
 
-int launch_crop(int nc, const void* pin, const float* ptg, int PD, int PH, int PW, const int32_t* idx,
-                const int32_t* org, int B, int S, void* X, float* target, void* stream) {
+int launch_crop(int nc, const void* pin, const float* ptg, const float* tscale, int PD, int PH, int PW,
+                const int32_t* idx, const int32_t* org, int B, int S, void* X, float* target, void* stream) {
   if (nc != 3 && nc != 4) return (int)cudaErrorInvalidValue;
   const int64_t V = (int64_t)B * S * S * S;
   (nc == 4 ? k_crop<4> : k_crop<3>)<<<blocks_for(V, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(
-      (const uint4*)pin, ptg, PD, PH, PW, idx, org, B, S, (uint4*)X, target);
+      (const uint4*)pin, ptg, tscale, PD, PH, PW, idx, org, B, S, (uint4*)X, target);
+  return (int)cudaGetLastError();
+}
+
+int launch_sumsq(int64_t n, const float* x, double* partial, double* out, void* stream) {
+  const int64_t nb = red_blocks(n);
+  k_sumsq<<<(unsigned)nb, RED_BLOCK, 0, (cudaStream_t)stream>>>(x, n, partial);
+  k_sum_into<<<1, RED_BLOCK, 0, (cudaStream_t)stream>>>(partial, (int)nb, out);
   return (int)cudaGetLastError();
 }
 

@@ -82,26 +82,35 @@ int launch_to_bf16(int64_t V, int cin, const float* src, void* X, void* stream);
 // In the feature kernels, nc = 3 or 4 components per node (vectors of nc * E values, component
 // c of entry e at [e + c E]); velocity components count only at free nodes, the pressure
 // (component 3) at every node.
-// sum over voxels of sum_c (z0[e + c E] / dinv[e + c E])^2 (free components), e = gent[g],
-// written to *out (partial: mse_partials(V) doubles)
-int launch_feature_norm(int64_t V, int64_t E, int nc, const int64_t* gent, const uint8_t* gfree, const float* z0,
-                        const float* dinv, double* partial, double* out, void* stream);
+// sum over voxels of sum_c (z0[e + c E] / dinv[e + c E])^2 over the free components c in
+// [c0, c1), e = gent[g], written to *out (partial: mse_partials(V) doubles)
+int launch_feature_norm(int64_t V, int64_t E, int nc, int c0, int c1, const int64_t* gent, const uint8_t* gfree,
+                        const float* z0, const float* dinv, double* partial, double* out, void* stream);
 
-// features of the library-layout vectors r1, z0 on the grid; s = sqrt(*sumsq / count)
-// (1 if zero).  X (16-channel BF16, inference) or pin (ln_pair_in(nc)-channel BF16) and
-// target = D e1 / s (FP32, nc channels; e1 nullable -> no target), whichever is non-null.
+// features of the library-layout vectors r1, z0 on the grid with the scales
+// s = sqrt(*sumsq / count) for the velocity-like components and s_p = sqrt(*sumsq_p /
+// count_p) for the pressure (nc = 4; 1 if zero).  X (16-channel BF16, inference) or pin
+// (ln_pair_in(nc)-channel BF16) and target = D e1 / s (FP32, nc channels; e1 nullable ->
+// no target), whichever is non-null.
 int launch_features(int64_t V, int64_t E, int nc, const int64_t* gent, const uint8_t* gfree, const float* logk,
                     const float* r1, const float* z0, const float* e1, const float* dinv, const double* sumsq,
-                    double count, void* X, void* pin, float* target, void* stream);
+                    double count, const double* sumsq_p, double count_p, void* X, void* pin, float* target,
+                    void* stream);
 
 // library layout from an nc-channel FP32 grid field: z[e + c E] = (component free) ?
-// s * out[g][c] * dinv[e + c E] : 0 (dinv and sumsq nullable: factor 1)
+// s * out[g][c] * dinv[e + c E] : 0, with s (s_p for the pressure) as in launch_features
+// (dinv and sumsq nullable: factor 1)
 int launch_grid_to_lib(int64_t E, int nc, const int64_t* e2g, const uint8_t* efree, const float* out,
-                       const float* dinv, const double* sumsq, double count, float* z, void* stream);
+                       const float* dinv, const double* sumsq, double count, const double* sumsq_p, double count_p,
+                       float* z, void* stream);
 
 // training crops of S^3 voxels: sample b takes pair idx[b] at origin org[3b..3b+2] (z, y, x)
-// of the PD x PH x PW pair grids (ln_pair_in(nc) input and nc target channels per voxel)
-int launch_crop(int nc, const void* pin, const float* ptg, int PD, int PH, int PW, const int32_t* idx,
-                const int32_t* org, int B, int S, void* X, float* target, void* stream);
+// of the PD x PH x PW pair grids (ln_pair_in(nc) input and nc target channels per voxel),
+// its target multiplied by tscale[idx[b]] (tscale nullable: 1)
+int launch_crop(int nc, const void* pin, const float* ptg, const float* tscale, int PD, int PH, int PW,
+                const int32_t* idx, const int32_t* org, int B, int S, void* X, float* target, void* stream);
+
+// *out = sum of x[i]^2, i < n (partial: mse_partials(n) doubles)
+int launch_sumsq(int64_t n, const float* x, double* partial, double* out, void* stream);
 
 }  // namespace hhg

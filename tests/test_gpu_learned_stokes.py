@@ -129,7 +129,7 @@ def test_stokes_precondition_matches_oracle(sp4):
     z, w_or, c = LN.stokes_correction(p.H, p.level, p.vox, p.dims, p.k, r, v, Ws, bs)
     assert abs(alpha - w_or) <= 3e-2 * abs(w_or)
     zg = p.from_lib(zd)
-    z0, _ = LN._stokes_scaled_step(p.H, p.level, r, v)
+    z0, _ = LN._stokes_step(p.H, p.level, r, v)
     bc = z - z0 * (z * z0).sum() / (z0 * z0).sum()  # the part of z off the multigrid direction
     assert np.abs(zg - z).max() <= 3e-2 * np.abs(bc).max() + 1e-4 * np.abs(z).max()
     st = B.hhg_learn_stats(h, reset=True)

@@ -113,7 +113,7 @@ def test_stokes_combination_is_the_residual_least_squares_step(hier3):
     Ws, bs = _random_net(5)
     k = _mu(H.lv[l].coords)
     z, w, c = LN.stokes_correction(H, l, vox, dims, k, r, v, Ws, bs)
-    z0, Kz0 = LN._stokes_scaled_step(H, l, r, v)
+    z0, Kz0 = LN._stokes_step(H, l, r, v)
     on = np.ones(r.shape, dtype=bool)
     on[d, :3] = False
     Kc = H.apply(l, c)
@@ -139,13 +139,17 @@ def test_stokes_pair_is_consistent(hier3):
     on = np.ones(e.shape, dtype=bool)
     on[d, :3] = False
     Xv = X[0, vox[:, 0], vox[:, 1], vox[:, 2]]
-    # the D z0 / s channels have unit RMS over the free DoFs (definition of s)
-    assert abs(np.sqrt((Xv[:, 4:8][on] ** 2).mean()) - 1.0) < 1e-12
-    # the r1 channels are K e1 / s and the targets D e1 / s, with the same s
-    D = LN.stokes_diag(H, l)
-    scale = np.linalg.norm(Xv[:, :4][on]) / np.linalg.norm(H.residual(l, np.zeros_like(e1), -e1)[on])
     Tv = T[0, vox[:, 0], vox[:, 1], vox[:, 2]]
-    assert np.allclose(Tv[on] / scale, (D * e1)[on], rtol=1e-10, atol=1e-12 * np.abs(D * e1).max())
-    assert np.allclose(Xv[:, :4][on] / scale, H.residual(l, np.zeros_like(e1), -e1)[on], rtol=1e-10,
-                       atol=1e-12 * np.abs(Xv).max() / scale)
+    D = LN.stokes_diag(H, l)
+    r1 = H.residual(l, np.zeros_like(e1), -e1)
+    # the D z0 / s channels have unit RMS over the free velocity DoFs and over the pressures
+    # (definition of s and s_p); r1 / s and the targets D e1 / s share those scales
+    for comps in ([0, 1, 2], [3]):
+        m = on[:, comps]
+        assert abs(np.sqrt((Xv[:, [4 + c for c in comps]][m] ** 2).mean()) - 1.0) < 1e-12
+        scale = np.linalg.norm(Xv[:, comps][m]) / np.linalg.norm(r1[:, comps][m])
+        assert np.allclose(Tv[:, comps][m] / scale, (D * e1)[:, comps][m], rtol=1e-10,
+                           atol=1e-12 * np.abs(D * e1)[:, comps].max())
+        assert np.allclose(Xv[:, comps][m] / scale, r1[:, comps][m], rtol=1e-10,
+                           atol=1e-12 * np.abs(Xv[:, comps]).max() / scale)
     assert np.allclose(Xv[:, 8], np.log(k) - np.log(k).mean())
