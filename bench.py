@@ -66,6 +66,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(v, world, device="cuda"):
+    """The largest v over all ranks (the job takes as long as its slowest rank)."""
+    if world <= 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(dofs_per_rank, ms_per_step, world):
+    """Whole-job throughput in GDoF/s: every rank applies its own replica (weak scaling)."""
+    return world * dofs_per_rank / (ms_per_step * 1e-3) / 1e9
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -648,11 +665,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), world)
     # end-to-end: host buffers through the C ABI (H2D copy, apply, D2H copy, wait)
     xh = torch.empty(3 * E, dtype=torch.float32, pin_memory=True)
     xh.copy_(x.cpu())
@@ -720,7 +733,7 @@ def run_ours(args):
         args.learn_stokes_steps)
 
     ms_per_step = total_ms / args.steps
-    value = world * dofs / (ms_per_step * 1e-3) / 1e9
+    value = job_value(dofs, ms_per_step, world)
     hbm_peak, peak_kind = measured_peaks()
     launch_ms = prof_ms[0] / max(1, prof_launches[0])
     bytes_per_launch = interior_per_macro * BYTES_PER_NODE_F32
