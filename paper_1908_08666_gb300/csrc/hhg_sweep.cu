@@ -119,26 +119,11 @@ __device__ __forceinline__ void stokes_epilogue(const SweepArgs<T>& a, int64_t e
   }
 }
 
-// Resident blocks per SM the FP32 interior kernels are compiled for (ptxas registers per
-// thread and spills measured with -Xptxas -v): Jacobi / Chebyshev smoothing 8 (64
-// registers, no spill; unbounded they take 128), Stokes 5 (96 registers, no spill;
-// unbounded 141-168).  The apply and residual kernels take 64 registers by themselves (8
-// blocks); bounding them to 9 blocks spilled 16 bytes and measured no faster, since the
-// concurrent schedule already fills the tail of each launch.  FP64 and generic-flag
-// variants are left to the compiler.
-template <typename T, int OP, int GEN, int STK>
-constexpr int interior_min_blocks() {
-  return (sizeof(T) == 4 && !GEN && !STK && (OP == OP_JACOBI || OP == OP_CHEBY)) ? 8
-         : (sizeof(T) == 4 && !GEN && STK)                                       ? 5
-                                                                                    : 1;
-}
-
 // STK = 1: the Stokes saddle operator [[A(mu), B^T], [B, C]] on (u, v, w, p) (Sec. 5.2),
 // the velocity block being the scaled-stencil operator of the 2 mu eps(u) form.
 // KB = 1 (FP32, default operator only): the coefficient is read as BF16 bits from a.k16.
 template <typename T, int OP, int GEN, int STK = 0, int KB = 0>
-__global__ void __launch_bounds__(INTERIOR_BLOCK, interior_min_blocks<T, OP, GEN, STK>()) k_interior(const LevelDev L,
-                                                                                          const MacroStencil<T> st,
+__global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, const MacroStencil<T> st,
                                                               const int macro, const OpFlags fl,
                                                               const SweepArgs<T> a) {
   const int32_t tile = L.tiles_lin[blockIdx.x];
