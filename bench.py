@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-stokes", action="store_true")
     ap.add_argument("--no-carreau", action="store_true")
-    ap.add_argument("--carreau-level", type=int, default=7)
+    ap.add_argument("--carreau-level", type=int, default=8)
     ap.add_argument("--no-learn", action="store_true")
     ap.add_argument("--learn-train-level", type=int, default=6)
     ap.add_argument("--learn-level", type=int, default=8)
@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-learn-stokes", action="store_true")
     ap.add_argument("--learn-stokes-fields", type=int, default=8)
     ap.add_argument("--learn-stokes-steps", type=int, default=2000)
+    ap.add_argument("--learn-stokes-level", type=int, default=8)
     return ap.parse_args()
 
 
@@ -729,7 +730,7 @@ def run_ours(args):
     learned = None if args.no_learn else learned_bench(B, torch, dev, stream, args.learn_train_level,
                                                        args.learn_level, args.learn_seeds, 2, 6, args.learn_steps)
     learned_stokes = None if args.no_learn_stokes else learned_stokes_bench(
-        B, torch, dev, stream, args.learn_train_level, level, args.learn_stokes_fields, 2, 6,
+        B, torch, dev, stream, args.learn_train_level, args.learn_stokes_level, args.learn_stokes_fields, 2, 6,
         args.learn_stokes_steps)
 
     ms_per_step = total_ms / args.steps
