@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--learn-level", type=int, default=8)
     ap.add_argument("--learn-seeds", type=int, default=24)
     ap.add_argument("--learn-steps", type=int, default=4000)
+    ap.add_argument("--learn-coarsen", type=int, default=1)
+    ap.add_argument("--learn-coarse-train-level", type=int, default=6)
+    ap.add_argument("--learn-coarse-seeds", type=int, default=12)
     ap.add_argument("--no-learn-stokes", action="store_true")
     ap.add_argument("--learn-stokes-fields", type=int, default=8)
     ap.add_argument("--learn-stokes-steps", type=int, default=2000)
@@ -345,14 +348,17 @@ def carreau_bench(B, torch, level, dev, stream):
 # ---------------------------------------------------------------------------- our arm
 
 
-def learned_bench(B, torch, dev, stream, train_level, eval_level, nseed, nrhs, iters, steps):
+def learned_bench(B, torch, dev, stream, train_level, eval_level, nseed, nrhs, iters, steps, coarsen=0,
+                  coarse_train_level=7, coarse_seeds=12):
     """Learned preconditioner: training pairs from the errors of MG-preconditioned CG
     solves at train_level (lognormal E with seeds 100.., f ~ U[-1, 1]), GPU training of the
     conv net (Adam, batches of 8 random 32^3 crops), then the time to an FP64 relative
     residual of 1e-8 at eval_level on the bench field (seed 2, f seed 3): FP64 refinement
     around FP32 flexible CG with the V-cycle plus the learned correction, against the same
     solver with the V-cycle alone and plain FP64 MG-CG.  Also the conv-net forward
-    throughput on the eval grid (tensor-core roofline of the dominant learned kernel)."""
+    throughput on the eval grid (tensor-core roofline of the dominant learned kernel).
+    With coarsen = q > 0 also the coarse-grid mode: the network trained on pairs from
+    coarse_train_level stored q levels lower, and applied q levels below eval_level."""
     import hhg_inputs as hi
 
     xyz, tets = hi.kuhn_cube(1)
@@ -378,26 +384,33 @@ def learned_bench(B, torch, dev, stream, train_level, eval_level, nseed, nrhs, i
         B.hhg_scatter_unique(h, level, dt, comps, src, dst)
         return dst
 
+    def train(level, seeds, q, crop):
+        """Pairs from MG-CG errors on `seeds` lognormal fields at `level` (stored q levels
+        lower), GPU training; returns (parameters, report, pair-generation seconds)."""
+        h, E, U, cu, udir = make(level)
+        Nt = 1 << level
+        B.hhg_learn_set_coarsening(h, q)
+        B.hhg_learn_reserve_pairs(h, level, seeds * nrhs * iters)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(seeds):
+            B.hhg_set_coefficient(h, scatter(h, level, hi.sample_grid(hi.lognormal_grid(Nt, 100 + s), cu), 1, B.F64),
+                                  B.F64)
+            B.hhg_mg_setup(h)
+            for q2 in range(nrhs):
+                f = np.random.default_rng(1000 * s + q2).uniform(-1, 1, size=(U, 3))
+                f[udir] = 0.0
+                B.hhg_learn_collect_cg(h, level, scatter(h, level, f, 3, B.F32), iters)
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - t0
+        B.hhg_learn_init(h, 1)
+        tr = B.hhg_learn_train(h, steps=steps, batch=8, crop=crop, lr=2e-3, seed=2)
+        params = B.hhg_learn_get_params(h)
+        B.hhg_destroy(h)
+        return params, tr, gen_s
+
     # training pairs and training
-    h, E, U, cu, udir = make(train_level)
-    Nt = 1 << train_level
-    B.hhg_learn_reserve_pairs(h, train_level, nseed * nrhs * iters)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for s in range(nseed):
-        B.hhg_set_coefficient(h, scatter(h, train_level, hi.sample_grid(hi.lognormal_grid(Nt, 100 + s), cu), 1,
-                                         B.F64), B.F64)
-        B.hhg_mg_setup(h)
-        for q in range(nrhs):
-            f = np.random.default_rng(1000 * s + q).uniform(-1, 1, size=(U, 3))
-            f[udir] = 0.0
-            B.hhg_learn_collect_cg(h, train_level, scatter(h, train_level, f, 3, B.F32), iters)
-    torch.cuda.synchronize()
-    gen_s = time.perf_counter() - t0
-    B.hhg_learn_init(h, 1)
-    tr = B.hhg_learn_train(h, steps=steps, batch=8, crop=32, lr=2e-3, seed=2)
-    params = B.hhg_learn_get_params(h)
-    B.hhg_destroy(h)
+    params, tr, gen_s = train(train_level, nseed, 0, 32)
 
     # evaluation
     h, E, U, cu, udir = make(eval_level)
@@ -436,6 +449,34 @@ def learned_bench(B, torch, dev, stream, train_level, eval_level, nseed, nrhs, i
                               "mean_extra_energy_reduction": round(st["gain_mean"], 5)})
     out["iterations_saved_vs_vcycle"] = out["ir_fcg_vcycle"]["inner_iterations"] - out["ir_fcg_learned"]["inner_iterations"]
     out["speedup_learned_vs_fp64_mgcg"] = round(out["fp64_mgcg"]["seconds"] / out["ir_fcg_learned"]["seconds"], 3)
+    if coarsen > 0:
+        # coarse-grid mode: the network on the node grid `coarsen` levels below the solve's
+        cp, ctr, cgen = train(coarse_train_level, coarse_seeds, coarsen, 32)
+        B.hhg_learn_set_params(h, cp)
+        B.hhg_learn_set_coarsening(h, coarsen)
+        best = None
+        for _ in range(2):
+            x = torch.zeros_like(f)
+            B.hhg_learn_stats(h, reset=True)
+            torch.cuda.synchronize()
+            rep = B.hhg_solve(h, f, x, method=B.SOLVE_IR_FCG_LEARNED, level=eval_level, dt=B.F64, rtol=1e-8,
+                              max_iter=100, inner_rtol=1e-3, inner_max_iter=100)
+            st = B.hhg_learn_stats(h)
+            if best is None or rep["seconds"] < best[0]["seconds"]:
+                best = (rep, st)
+        rep, st = best
+        B.hhg_learn_set_coarsening(h, 0)
+        B.hhg_learn_set_params(h, params)
+        out["ir_fcg_learned_coarse"] = {
+            "coarsen": coarsen, "network_level": eval_level - coarsen,
+            "train": {"level": coarse_train_level, "pair_grid_level": coarse_train_level - coarsen,
+                      "pairs": int(ctr["pairs"]), "pair_generation_s": round(cgen, 3),
+                      "loss_first": ctr["loss_first"], "loss_last": ctr["loss_last"]},
+            "seconds": round(rep["seconds"], 5), "iterations": rep["iterations"],
+            "inner_iterations": rep["inner_iterations"], "converged": bool(rep["converged"]),
+            "net_applications": st["applications"], "fallbacks": st["fallbacks"],
+            "mean_extra_energy_reduction": round(st["gain_mean"], 5),
+            "iterations_saved_vs_vcycle": out["ir_fcg_vcycle"]["inner_iterations"] - rep["inner_iterations"]}
     # conv-net forward throughput on the eval grid (4 layers, 27 taps, 16 x 16 channels)
     (D, H, W), _ = B.hhg_learn_grid(h, eval_level)
     V = D * H * W
@@ -728,7 +769,9 @@ def run_ours(args):
     stokes = None if args.no_stokes else stokes_bench(B, torch, level, dev, stream)
     carreau = None if args.no_carreau else carreau_bench(B, torch, args.carreau_level, dev, stream)
     learned = None if args.no_learn else learned_bench(B, torch, dev, stream, args.learn_train_level,
-                                                       args.learn_level, args.learn_seeds, 2, 6, args.learn_steps)
+                                                       args.learn_level, args.learn_seeds, 2, 6, args.learn_steps,
+                                                       args.learn_coarsen, args.learn_coarse_train_level,
+                                                       args.learn_coarse_seeds)
     learned_stokes = None if args.no_learn_stokes else learned_stokes_bench(
         B, torch, dev, stream, args.learn_train_level, args.learn_stokes_level, args.learn_stokes_fields, 2, 6,
         args.learn_stokes_steps)

@@ -405,6 +405,14 @@ int64_t hhg_learn_num_params(void);
  * epilogue warpgroup draining one while the next tile's MMAs run).  All give the same
  * results up to FP32 summation order. */
 hhg_status hhg_learn_set_conv_kernel(hhg_ctx* ctx, int kernel);
+/* Coarse-grid mode (elasticity; levels = 0 default, 1..3): the network runs on the node
+ * grid `levels` levels below the solve's.  Its inputs there are r1 restricted (P^T, as in
+ * the V-cycle) and z0 injected (coarse nodes are fine nodes), D is that level's point
+ * diagonal, and its correction is prolongated back (P, linear interpolation) before the
+ * 2x2 combination; training pairs are stored on the coarse grid with the error injected
+ * there.  Pairs keep the coarsening they were reserved with; levels - coarsening must not
+ * go below the coarsest level. */
+hhg_status hhg_learn_set_coarsening(hhg_ctx* ctx, int levels);
 /* He-normal initialisation (std sqrt(2/(27*fan_in)), last layer x0.1; BF16 values,
  * zero biases) from a seeded generator, with the input and output channels of the
  * context's problem kind (7 / 3 elasticity, 9 / 4 Stokes); resets the optimiser state. */

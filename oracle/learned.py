@@ -25,6 +25,12 @@ c = s out / D on free nodes; z = a z0 + b c with (a, b) minimising the energy no
 Training pair from an error e: z0 as above for r = A e, e1 = e - z0, r1 = A e1,
 target D e1 / s.
 
+Coarse-grid mode (``coarse_*``, elasticity): the network runs q levels below the solve's
+level l.  Its inputs are r1 restricted q times (P^T with Dirichlet rows zeroed, as in the
+V-cycle) and z0 injected (coarse nodes are fine nodes), with that level's point diagonal
+and log k; its correction s out / D is prolongated q times (P) and then combined as
+above.  Its training target is D e1 / s with e1 injected to the coarse level.
+
 Stokes (``stokes_*``; vectors (N, 4): velocity, then pressure; K the saddle operator with
 velocity-Dirichlet identity rows, v = one inexact Uzawa V-cycle of the residual): the
 same with 4 components, CIN = 9 input channels (r1/s, D z0/s, log mu) and 4 outputs,
@@ -180,6 +186,16 @@ def _scaled_step(A, dirichlet, r, v):
     return a0 * v, a0 * Av
 
 
+def _combine(A, dirichlet, r, z0, Az0, c):
+    """z = a z0 + b c minimising the energy norm of the error A^-1 r - z, and b / a."""
+    Ac = (A @ c.reshape(-1)).reshape(-1, 3)
+    M = np.array([[_dot_free(z0, Az0, dirichlet), _dot_free(c, Az0, dirichlet)],
+                  [_dot_free(c, Az0, dirichlet), _dot_free(c, Ac, dirichlet)]])
+    rhs = np.array([_dot_free(z0, r, dirichlet), _dot_free(c, r, dirichlet)])
+    a, b = np.linalg.solve(M, rhs)
+    return a * z0 + b * c, b / a
+
+
 def correction(A, dirichlet, vox, dims, k, r, v, Ws, bs):
     """(z, b/a, c): the learned preconditioner's output for residual r given v = V-cycle(r):
     z0 = a0 v, c from the network, z = a z0 + b c minimising the energy norm of the error
@@ -194,12 +210,76 @@ def correction(A, dirichlet, vox, dims, k, r, v, Ws, bs):
     out, _ = forward(X, Ws, bs)
     c = s * out[0, vox[:, 0], vox[:, 1], vox[:, 2], :] / Dg
     c[~fr] = 0.0
-    Ac = (A @ c.reshape(-1)).reshape(-1, 3)
-    M = np.array([[_dot_free(z0, Az0, dirichlet), _dot_free(c, Az0, dirichlet)],
-                  [_dot_free(c, Az0, dirichlet), _dot_free(c, Ac, dirichlet)]])
-    rhs = np.array([_dot_free(z0, r, dirichlet), _dot_free(c, r, dirichlet)])
-    a, b = np.linalg.solve(M, rhs)
-    return a * z0 + b * c, b / a, c
+    z, w = _combine(A, dirichlet, r, z0, Az0, c)
+    return z, w, c
+
+
+def _inject_index(H, lev):
+    """Index in level lev of every node of level lev - 1 (coarse nodes are fine nodes)."""
+    key = lambda c: tuple(np.rint(np.asarray(c) * 2.0**(lev + 2)).astype(np.int64))
+    fine = {key(c): i for i, c in enumerate(H.lv[lev].coords)}
+    return np.array([fine[key(c)] for c in H.lv[lev - 1].coords], dtype=np.int64)
+
+
+def coarse_inputs(H, l, q, r1, z0, e1=None):
+    """r1 restricted and z0, e1 injected from level l to level l - q (H: a multigrid
+    hierarchy with levels, operators A and prolongations P)."""
+    from .solvers import restrict
+
+    for lev in range(l, l - q, -1):
+        idx = _inject_index(H, lev)
+        r1 = restrict(H.P[lev], r1, H.lv[lev].dirichlet, H.lv[lev - 1].dirichlet)
+        z0 = np.asarray(z0)[idx]
+        e1 = None if e1 is None else np.asarray(e1)[idx]
+    return r1, z0, e1
+
+
+def _point_diag(H, lev):
+    D = H.A[lev].diagonal().reshape(-1, 3).copy()
+    D[H.lv[lev].dirichlet] = 1.0
+    return D
+
+
+def coarse_correction(H, l, q, vox_c, dims_c, k_c, r, v, Ws, bs):
+    """(z, b/a, c) of the coarse-grid mode for residual r given v = V-cycle(r) at level l;
+    vox_c, dims_c, k_c: the node grid and coefficient of level l - q."""
+    A, d = H.A[l], H.lv[l].dirichlet
+    lc = l - q
+    dc = H.lv[lc].dirichlet
+    z0, Az0 = _scaled_step(A, d, r, v)
+    r1 = r - Az0
+    r1[d] = 0.0
+    r1c, z0c, _ = coarse_inputs(H, l, q, r1, z0)
+    Dc = _point_diag(H, lc)
+    X, s = features(vox_c, dims_c, dc, k_c, r1c, z0c, Dc)
+    out, _ = forward(X, Ws, bs)
+    c = s * out[0, vox_c[:, 0], vox_c[:, 1], vox_c[:, 2], :] / Dc
+    c[dc] = 0.0
+    for lev in range(lc + 1, l + 1):
+        c = H.P[lev] @ c
+    z, w = _combine(A, d, r, z0, Az0, c)
+    return z, w, c
+
+
+def coarse_training_pair(H, l, q, vox_c, dims_c, k_c, e, vcycle):
+    """(inputs, target, e1) of one multigrid step from the error e at level l, with the
+    pair on the node grid of level l - q."""
+    A, d = H.A[l], H.lv[l].dirichlet
+    lc = l - q
+    dc = H.lv[lc].dirichlet
+    r = (A @ e.reshape(-1)).reshape(-1, 3)
+    r[d] = 0.0
+    z0, _ = _scaled_step(A, d, r, vcycle(r))
+    e1 = e - z0
+    r1 = (A @ e1.reshape(-1)).reshape(-1, 3)
+    r1[d] = 0.0
+    r1c, z0c, e1c = coarse_inputs(H, l, q, r1, z0, e1)
+    Dc = _point_diag(H, lc)
+    X, s = features(vox_c, dims_c, dc, k_c, r1c, z0c, Dc)
+    T = np.zeros((1,) + dims_c + (COUT,))
+    fr = ~np.asarray(dc)
+    T[0, vox_c[fr, 0], vox_c[fr, 1], vox_c[fr, 2], :] = (Dc * e1c / s)[fr]
+    return X, T, e1
 
 
 def training_pair(A, dirichlet, vox, dims, k, e, vcycle):

@@ -139,6 +139,7 @@ _SIGS = {
     "hhg_learn_num_params": [],
     "hhg_learn_init": [C.c_void_p, C.c_uint64],
     "hhg_learn_set_conv_kernel": [C.c_void_p, C.c_int],
+    "hhg_learn_set_coarsening": [C.c_void_p, C.c_int],
     "hhg_learn_get_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "hhg_learn_set_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "hhg_learn_grid": [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int64)],
@@ -416,6 +417,10 @@ def hhg_learn_grid(ctx, level):
     nf = C.c_int64()
     _check(ctx, load().hhg_learn_grid(ctx, level, dhw.ctypes.data, C.byref(nf)))
     return tuple(int(v) for v in dhw), nf.value
+
+
+def hhg_learn_set_coarsening(ctx, levels):
+    _check(ctx, load().hhg_learn_set_coarsening(ctx, int(levels)))
 
 
 def hhg_learn_channels(ctx):

@@ -160,7 +160,7 @@ struct LearnGrid {
   int64_t V = 0, nfree = 0, nnode = 0;  // voxels; with a free node; with a node
   int64_t coeff_version = -1;  // of the log-coefficient feature
   DevMem gent, gfree, e2g, efree, logk;
-  DevMem lw[13];  // FP32 work vectors (4*E) of the learned preconditioner and its Krylov solvers
+  DevMem lw[16];  // FP32 work vectors (4*E) of the learned preconditioner and its Krylov solvers
   DevMem lw64[2]; // FP64 work vectors (4*E) of the pair collection
   // Stokes: inverse diagonal of the features (velocity point diagonal, pressure Schur
   // surrogate; 4*E) and the coefficient version it was computed for
@@ -183,6 +183,8 @@ struct LearnState {
   // training pairs of one level: inputs (ln_pair_in(pair_nc) BF16 per voxel) and targets
   // (pair_nc FP32), pair_nc = components of the problem they came from
   int pair_level = -1, pair_nc = 3;
+  int pair_coarsen = 0;  // the coarsening the pairs were stored with (their grid: pair_level - it)
+  int coarsen = 0;       // the network runs on the node grid this many levels below the solve's
   // per-pair factor of the targets in training (Stokes: 1 / RMS of the pair's target, so
   // that every pair weighs the same; elasticity: 1)
   std::vector<float> pair_tscale;

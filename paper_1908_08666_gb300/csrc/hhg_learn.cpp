@@ -39,7 +39,9 @@ using namespace hhg;
 using namespace hhg::host;
 
 // work vectors of LearnGrid::lw
-enum { LW_Z0 = 0, LW_AZ0, LW_R1, LW_C, LW_AC, LW_R, LW_Z, LW_AZ, LW_P, LW_Q, LW_X, LW_XS, LW_E };
+// (CR, CZ, CE, CC: restricted residual, injected correction and error, and the network's
+// correction, on the coarser levels of the coarse-grid mode)
+enum { LW_Z0 = 0, LW_AZ0, LW_R1, LW_C, LW_AC, LW_R, LW_Z, LW_AZ, LW_P, LW_Q, LW_X, LW_XS, LW_E, LW_CR, LW_CZ, LW_CE };
 
 LearnState& state(hhg_ctx* c) {
   if (!c->learn) c->learn.reset(new LearnState());
@@ -399,6 +401,37 @@ FeatureScale feature_scales(hhg_ctx* c, int l, LearnState& S, LearnGrid& G, cons
   return f;
 }
 
+// Coarse-grid mode (elasticity, S.coarsen = q > 0): the fields the network sees at level
+// l - q, r1 restricted (P^T, q times) and z0 (and e1) injected; returns the level-(l - q)
+// vectors (work vectors of the intermediate levels; e1 nullable).
+struct CoarseFields {
+  const float *r1, *z0, *e1;
+};
+
+CoarseFields to_coarse(hhg_ctx* c, int l, int q, const float* r1, const float* z0, const float* e1) {
+  CoarseFields f{r1, z0, e1};
+  for (int lev = l; lev > l - q; --lev) {
+    LearnGrid& Gn = grid(c, lev - 1);
+    float* rn = lwork(c, Gn, lev - 1, LW_CR);
+    float* zn = lwork(c, Gn, lev - 1, LW_CZ);
+    restrict32(c, lev, f.r1, rn);
+    inject32(c, lev, f.z0, zn);
+    f.r1 = rn;
+    f.z0 = zn;
+    if (f.e1) {
+      float* en = lwork(c, Gn, lev - 1, LW_CE);
+      inject32(c, lev, f.e1, en);
+      f.e1 = en;
+    }
+  }
+  return f;
+}
+
+void need_coarse_level(hhg_ctx* c, int l, int q) {
+  if (q > 0 && is_stokes(c)) THROW(HHG_ERR_UNSUPPORTED, "the coarse-grid mode is built for elasticity");
+  if (l - q < c->level_min) THROW(HHG_ERR_ARG, "coarsening %d below the coarsest level from level %d", q, l);
+}
+
 // Elasticity: scale the V-cycle correction z0 (and K z0) to its energy-optimal length for
 // the residual r, z0 <- a0 z0 with a0 = (z0, r) / (z0, K z0) (unchanged when that is not
 // finite).  Stokes: no scaling.
@@ -429,20 +462,36 @@ double precondition(hhg_ctx* c, int l, const float* r, float* z, float* az, bool
     return 0.0;
   }
   need_params(S);
+  const int q = S.coarsen;
+  need_coarse_level(c, l, q);
   float* r1 = lwork(c, G, l, LW_R1);
   float* cc = lwork(c, G, l, LW_C);
   float* acc = lwork(c, G, l, LW_AC);
-  const float* dinv = sys_dinv(c, l, G);
-  ensure_acts(c, S, G.V);
   scale_mg_step(c, l, r, z0, az0);
   copy32(c, l, r, r1);
   CK(launch_axpby<float>(n, -1.f, az0, 1.f, r1, c->stream));
-  const FeatureScale fs = feature_scales(c, l, S, G, z0, dinv);
-  CK(launch_features(G.V, E, nc, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), G.logk.as<float>(), r1, z0, nullptr,
-                     dinv, fs.su, fs.cu, fs.sp, fs.cp, S.act[0].p, nullptr, nullptr, c->stream));
-  forward_inference(c, S, GridShape{1, G.D, G.H, G.W}, S.out.as<float>(), nc);
-  CK(launch_grid_to_lib(E, nc, G.e2g.as<int64_t>(), G.efree.as<uint8_t>(), S.out.as<float>(), dinv, fs.su, fs.cu,
-                        fs.sp, fs.cp, cc, c->stream));
+  // the network's level (l itself unless coarse-grid mode) and its inputs there
+  const int lc = l - q;
+  LearnGrid& Gc = grid(c, lc);
+  const int64_t Ec = c->lv(lc).entries;
+  const CoarseFields cf = q ? to_coarse(c, l, q, r1, z0, nullptr) : CoarseFields{r1, z0, nullptr};
+  const float* dinv = sys_dinv(c, lc, Gc);
+  float* ccn = q ? lwork(c, Gc, lc, LW_C) : cc;
+  ensure_acts(c, S, Gc.V);
+  const FeatureScale fs = feature_scales(c, lc, S, Gc, cf.z0, dinv);
+  CK(launch_features(Gc.V, Ec, nc, Gc.gent.as<int64_t>(), Gc.gfree.as<uint8_t>(), Gc.logk.as<float>(), cf.r1, cf.z0,
+                     nullptr, dinv, fs.su, fs.cu, fs.sp, fs.cp, S.act[0].p, nullptr, nullptr, c->stream));
+  forward_inference(c, S, GridShape{1, Gc.D, Gc.H, Gc.W}, S.out.as<float>(), nc);
+  CK(launch_grid_to_lib(Ec, nc, Gc.e2g.as<int64_t>(), Gc.efree.as<uint8_t>(), S.out.as<float>(), dinv, fs.su, fs.cu,
+                        fs.sp, fs.cp, ccn, c->stream));
+  // coarse-grid mode: prolongate the correction back to level l
+  const float* cur = ccn;
+  for (int lev = lc + 1; lev <= l; ++lev) {
+    float* nx = lev == l ? cc : lwork(c, grid(c, lev), lev, LW_C);
+    CK(cudaMemsetAsync(nx, 0, 3 * (size_t)c->lv(lev).entries * sizeof(float), c->stream));
+    prolong_add32(c, lev, cur, nx);
+    cur = nx;
+  }
   sys_apply(c, l, cc, acc);
   // optimal a, b: [m11 m12; m12 m22] (a, b) = (rv, rc) with the energy inner product
   // (u, K v) (elasticity) or the residual one (K u, K v) (Stokes)
@@ -602,6 +651,7 @@ void store_pair(hhg_ctx* c, int l, const float* e, float* e1_out) {
   const int nc = ncomp(c);
   if (S.pair_level != l) THROW(HHG_ERR_STATE, "reserve pair storage for level %d first", l);
   if (S.pair_nc != nc) THROW(HHG_ERR_STATE, "pair storage was reserved for another problem kind");
+  if (S.pair_coarsen != S.coarsen) THROW(HHG_ERR_STATE, "pair storage was reserved with another coarsening");
   if (S.pair_count >= S.pair_cap) THROW(HHG_ERR_ARG, "pair storage full (%lld)", (long long)S.pair_cap);
   const int64_t E = c->lv(l).entries, n = nc * E;
   float* z0 = lwork(c, G, l, LW_Z0);
@@ -619,24 +669,30 @@ void store_pair(hhg_ctx* c, int l, const float* e, float* e1_out) {
   copy32(c, l, e, e1);
   CK(launch_axpby<float>(n, -1.f, z0, 1.f, e1, c->stream));
   if (nc == 4) project_pressure32(c, l, e1);
-  const FeatureScale fs = feature_scales(c, l, S, G, z0, dinv);
+  // the pair lives on the network's grid (level l - coarsening)
+  const int q = S.pair_coarsen;
+  const int lc = l - q;
+  LearnGrid& Gc = grid(c, lc);
+  const CoarseFields cf = q ? to_coarse(c, l, q, r1, z0, e1) : CoarseFields{r1, z0, e1};
+  const float* dinv_c = q ? sys_dinv(c, lc, Gc) : dinv;
+  const FeatureScale fs = feature_scales(c, lc, S, Gc, cf.z0, dinv_c);
   const int64_t p = S.pair_count++;
-  float* tg = S.ptg.as<float>() + (size_t)p * G.V * nc;
-  CK(launch_features(G.V, E, nc, G.gent.as<int64_t>(), G.gfree.as<uint8_t>(), G.logk.as<float>(), r1, z0, e1, dinv,
-                     fs.su, fs.cu, fs.sp, fs.cp, nullptr, (char*)S.pin.p + (size_t)p * G.V * ln_pair_in(nc) * 2, tg,
-                     c->stream));
+  float* tg = S.ptg.as<float>() + (size_t)p * Gc.V * nc;
+  CK(launch_features(Gc.V, c->lv(lc).entries, nc, Gc.gent.as<int64_t>(), Gc.gfree.as<uint8_t>(), Gc.logk.as<float>(),
+                     cf.r1, cf.z0, cf.e1, dinv_c, fs.su, fs.cu, fs.sp, fs.cp, nullptr,
+                     (char*)S.pin.p + (size_t)p * Gc.V * ln_pair_in(nc) * 2, tg, c->stream));
   float ts = 1.f;
   if (nc == 4) {
     // the 2x2 combination fixes the size of the correction, so only its direction matters:
     // each Stokes pair's target is trained at unit RMS (the cycle's step is much smaller
     // than the error for some pairs, whose raw targets would otherwise dominate the loss)
     double* ss = S.dscal.as<double>() + 4;
-    if (S.dpart.bytes < (size_t)mse_partials((int64_t)G.V * nc) * sizeof(double))
-      CK(S.dpart.alloc((size_t)mse_partials((int64_t)G.V * nc) * sizeof(double)));
-    CK(launch_sumsq((int64_t)G.V * nc, tg, S.dpart.as<double>(), ss, c->stream));
+    if (S.dpart.bytes < (size_t)mse_partials((int64_t)Gc.V * nc) * sizeof(double))
+      CK(S.dpart.alloc((size_t)mse_partials((int64_t)Gc.V * nc) * sizeof(double)));
+    CK(launch_sumsq((int64_t)Gc.V * nc, tg, S.dpart.as<double>(), ss, c->stream));
     CK(cudaMemcpyAsync(c->pinned, ss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     wait_stream(c);
-    const double ms = c->pinned[0] / ((double)G.V * nc);
+    const double ms = c->pinned[0] / ((double)Gc.V * nc);
     ts = (ms > 0.0 && std::isfinite(ms)) ? (float)(1.0 / std::sqrt(ms)) : 1.f;
   }
   S.pair_tscale[p] = ts;
@@ -730,6 +786,15 @@ hhg_status hhg_learn_set_conv_kernel(hhg_ctx* c, int kernel) {
   });
 }
 
+hhg_status hhg_learn_set_coarsening(hhg_ctx* c, int levels) {
+  return guard(c, [&] {
+    if (levels < 0 || levels > 3) THROW(HHG_ERR_ARG, "coarsening 0..3");
+    if (levels > 0 && c->prob.kind != HHG_ELASTICITY)
+      THROW(HHG_ERR_UNSUPPORTED, "the coarse-grid mode is built for elasticity");
+    state(c).coarsen = levels;
+  });
+}
+
 hhg_status hhg_learn_get_params(hhg_ctx* c, float* params_host, int64_t n) {
   return guard(c, [&] {
     LearnState& S = state(c);
@@ -812,11 +877,13 @@ hhg_status hhg_learn_reserve_pairs(hhg_ctx* c, int level, int64_t capacity) {
     need_ready(c, false);
     if (capacity < 1) THROW(HHG_ERR_ARG, "capacity");
     LearnState& S = state(c);
-    LearnGrid& G = grid(c, level);
+    need_coarse_level(c, level, S.coarsen);
+    LearnGrid& G = grid(c, level - S.coarsen);
     const int nc = ncomp(c);
     CK(S.pin.alloc((size_t)capacity * G.V * ln_pair_in(nc) * 2));
     CK(S.ptg.alloc((size_t)capacity * G.V * nc * sizeof(float)));
     S.pair_nc = nc;
+    S.pair_coarsen = S.coarsen;
     S.pair_tscale.assign(capacity, 1.f);
     S.pair_level = level;
     S.pair_cap = capacity;
@@ -909,7 +976,7 @@ hhg_status hhg_learn_get_pair(hhg_ctx* c, int64_t index, float* in_host, float* 
   return guard(c, [&] {
     LearnState& S = state(c);
     if (index < 0 || index >= S.pair_count) THROW(HHG_ERR_ARG, "pair %lld not stored", (long long)index);
-    LearnGrid& G = grid(c, S.pair_level);
+    LearnGrid& G = grid(c, S.pair_level - S.pair_coarsen);
     const int nc = S.pair_nc, pin = ln_pair_in(nc), cin = ln_cin(nc);
     if (in_host) {
       std::vector<uint16_t> h((size_t)G.V * pin);
@@ -936,7 +1003,7 @@ hhg_status hhg_learn_train(hhg_ctx* c, const hhg_learn_train_opts* o, hhg_learn_
     need_params(S);
     if (!o || o->steps < 1 || o->batch < 1 || o->crop < 1 || !(o->lr > 0.0)) THROW(HHG_ERR_ARG, "bad options");
     if (S.pair_count < 1) THROW(HHG_ERR_STATE, "no training pairs (hhg_learn_collect)");
-    LearnGrid& G = grid(c, S.pair_level);
+    LearnGrid& G = grid(c, S.pair_level - S.pair_coarsen);
     const int Sc = o->crop;
     if (Sc > G.D || Sc > G.H || Sc > G.W) THROW(HHG_ERR_ARG, "crop %d larger than the pair grid", Sc);
     const auto t0 = std::chrono::steady_clock::now();

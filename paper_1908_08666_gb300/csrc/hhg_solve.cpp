@@ -1051,6 +1051,17 @@ void ensure_work64(hhg_ctx* c, int l) {
 double* work64(hhg_ctx* c, int l, int q) { return work<double>(c->lv(l))[q].as<double>(); }
 float* work32(hhg_ctx* c, int l, int q) { return work<float>(c->lv(l))[q].as<float>(); }
 
+void restrict32(hhg_ctx* c, int lf, const float* rf, float* rc) { restrict_op<float>(c, lf, rf, rc); }
+void prolong_add32(hhg_ctx* c, int lf, const float* xc, float* xf) {
+  CK(launch_prolong_add<float>(c->lv(lf).dev, c->lv(lf - 1).dev, xc, xf, c->stream));
+}
+void inject32(hhg_ctx* c, int lf, const float* xf, float* xc) {
+  LevelHost& F = c->lv(lf);
+  LevelHost& C = c->lv(lf - 1);
+  for (int q = 0; q < 3; ++q)
+    CK(launch_inject<float>(F.dev, C.dev, xf + q * F.entries, xc + q * C.entries, c->stream));
+}
+
 void need_stokes_problem(hhg_ctx* c) { need_stokes(c); }
 void stokes_apply32(hhg_ctx* c, int l, const float* x, float* y) {
   stokes_sweep<float>(c, l, OP_APPLY, nullptr, x, y, false);

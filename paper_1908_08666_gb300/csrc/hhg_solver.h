@@ -23,6 +23,12 @@ void ensure_work64(hhg_ctx* c, int l);
 double* work64(hhg_ctx* c, int l, int q);  // FP64 work vector q (3*E); 10 and 11 are free for drivers
 float* work32(hhg_ctx* c, int l, int q);   // FP32 work vector q (3*E); 10 and 11 are free for drivers
 
+// Transfers of 3-component FP32 fields between level lf and lf - 1: rc = P^T rf (0 on
+// Dirichlet nodes), xf += P xc, and injection xc = xf at the coarse nodes
+void restrict32(hhg_ctx* c, int lf, const float* rf, float* rc);
+void prolong_add32(hhg_ctx* c, int lf, const float* xc, float* xf);
+void inject32(hhg_ctx* c, int lf, const float* xf, float* xc);
+
 // Stokes (4*E vectors): saddle apply, inner product over the unique DoFs (free velocity,
 // all pressures), residual (returns |r|^2), x = 0 and one inexact Uzawa V-cycle, the
 // diagonal Schur surrogate out = r / (m / mu + (-C)_ii) on E values, zero-mean pressure

@@ -180,6 +180,65 @@ def test_precondition_matches_oracle(cube4):
     assert st["applications"] == 1 and st["fallbacks"] == 0 and st["gain_mean"] >= -1e-6
 
 
+def _coarse_grid(p, lc):
+    vox_c, dims_c = LN.grid_index(p.H.lv[lc].coords, 1.0 / 2**lc)
+    return vox_c, dims_c, hi.young_sine(p.H.lv[lc].coords)
+
+
+def test_coarse_mode_pairs_match_oracle(cube4):
+    """Coarse-grid mode (network one level below the solve): the pairs live on the level-3
+    grid, restricted residual and injected z0 / error."""
+    p = cube4
+    t = p.ctx.torch
+    h = p.ctx.h
+    l = 4
+    lv, A = p.H.lv[l], p.H.A[l]
+    vox_c, dims_c, k_c = _coarse_grid(p, 3)
+    D, H, W = p.dims
+    e0 = np.random.default_rng(14).uniform(-1, 1, size=(D, H, W, 3)).astype(np.float32)
+    B.hhg_learn_set_coarsening(h, 1)
+    try:
+        B.hhg_learn_reserve_pairs(h, l, 4)
+        assert B.hhg_learn_collect(h, l, p.ctx.dev(e0, t.float32), 2) == 2
+        e = e0[p.vox[:, 0], p.vox[:, 1], p.vox[:, 2]].astype(np.float64)
+        e[lv.dirichlet] = 0.0
+        vc = lambda r: p.H.vcycle(l, r, np.zeros_like(r), "chebyshev", 2, 2, p.lam)
+        for j in range(2):
+            X, T, e = LN.coarse_training_pair(p.H, l, 1, vox_c, dims_c, k_c, e, vc)
+            xg, tg = B.hhg_learn_get_pair(h, j, dims_c)
+            assert np.allclose(xg, X[0], rtol=2.0**-7, atol=1e-4 * np.abs(X).max()), j
+            assert np.abs(tg - T[0]).max() <= 1e-4 * np.abs(T).max(), j
+    finally:
+        B.hhg_learn_set_coarsening(h, 0)
+
+
+def test_coarse_mode_precondition_matches_oracle(cube4):
+    p = cube4
+    t = p.ctx.torch
+    h = p.ctx.h
+    l = 4
+    lv, A = p.H.lv[l], p.H.A[l]
+    vox_c, dims_c, k_c = _coarse_grid(p, 3)
+    Ws, bs = _params(5)
+    B.hhg_learn_set_params(h, _flat(Ws, bs))
+    r = hi.node_noise(lv.coords, seed=43)
+    r[lv.dirichlet] = 0.0
+    rd = p.to_lib(l, r, t.float32)
+    zd = t.empty_like(rd)
+    B.hhg_learn_set_coarsening(h, 1)
+    try:
+        alpha = B.hhg_learn_precondition(h, l, 1, rd, zd)
+    finally:
+        B.hhg_learn_set_coarsening(h, 0)
+    v = p.H.vcycle(l, r, np.zeros_like(r), "chebyshev", 2, 2, p.lam)
+    z, w_or, c = LN.coarse_correction(p.H, l, 1, vox_c, dims_c, k_c, r, v, Ws, bs)
+    assert abs(alpha - w_or) <= 3e-2 * abs(w_or)
+    zg = p.from_lib(l, zd)
+    z0, _ = LN._scaled_step(A, lv.dirichlet, r, v)
+    bc = z - z0 * (z * z0).sum() / (z0 * z0).sum()
+    assert np.abs(zg - z).max() <= 3e-2 * np.abs(bc).max() + 1e-4 * np.abs(z).max()
+
+
 def test_precondition_never_worse_than_the_vcycle(cube4):
     """Energy norm of the error after one application, with and without the network
     (random weights: the line search must keep the step no worse)."""

@@ -145,3 +145,52 @@ def test_features_are_scale_invariant_and_pairs_consistent():
     # s is the RMS of D z0 over the free DoFs: the z0 channels have unit mean square
     z0c = X[0, vox[fr, 0], vox[fr, 1], vox[fr, 2], 3:6]
     assert abs((z0c**2).mean() - 1.0) < 1e-12
+
+
+def test_coarse_mode_without_coarsening_is_the_fine_mode():
+    import hhg_inputs as hi
+
+    H, lv, vox, dims, k, vc = _cube_problem(3)
+    A = H.A[3]
+    r = hi.node_noise(lv.coords, seed=8)
+    r[lv.dirichlet] = 0.0
+    v = vc(r)
+    Ws, bs = LN.init_params(3)
+    z, w, c = LN.correction(A, lv.dirichlet, vox, dims, k, r, v, Ws, bs)
+    zc, wc, cc = LN.coarse_correction(H, 3, 0, vox, dims, k, r, v, Ws, bs)
+    assert np.array_equal(z, zc) and w == wc and np.array_equal(c, cc)
+
+
+def test_coarse_mode_inputs_and_combination():
+    """Injection picks the coincident fine node; the coarse correction, prolongated, still
+    never loses to the V-cycle step in the energy norm."""
+    import hhg_inputs as hi
+
+    H, lv, vox, dims, k, vc = _cube_problem(3)
+    idx = LN._inject_index(H, 3)
+    assert np.array_equal(H.lv[3].coords[idx], H.lv[2].coords)
+    A = H.A[3]
+    e = hi.node_noise(lv.coords, seed=9)
+    e[lv.dirichlet] = 0.0
+    r = (A @ e.reshape(-1)).reshape(-1, 3)
+    r[lv.dirichlet] = 0.0
+    v = vc(r)
+    vox_c, dims_c = LN.grid_index(H.lv[2].coords, 1.0 / 4)
+    k_c = hi.young_sine(H.lv[2].coords)
+    Ws, bs = LN.init_params(4)
+    z, w, c = LN.coarse_correction(H, 3, 1, vox_c, dims_c, k_c, r, v, Ws, bs)
+    assert np.abs(c).max() > 0 and not c[lv.dirichlet].any()
+
+    def energy(zz):
+        d = (e - zz).reshape(-1)
+        return float(d @ (A @ d))
+
+    z0, _ = LN._scaled_step(A, lv.dirichlet, r, v)
+    assert energy(z) <= energy(z0) * (1 + 1e-12)
+    # the pair's target is D_c e1 / s at the injected nodes
+    X, T, e1 = LN.coarse_training_pair(H, 3, 1, vox_c, dims_c, k_c, e, vc)
+    Dc = LN._point_diag(H, 2)
+    t = T[0, vox_c[:, 0], vox_c[:, 1], vox_c[:, 2]]
+    fr = ~H.lv[2].dirichlet
+    ratio = (Dc * e1[idx])[fr] / t[fr]
+    assert np.allclose(ratio, ratio.flat[0], rtol=1e-10)
