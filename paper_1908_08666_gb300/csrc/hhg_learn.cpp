@@ -25,6 +25,11 @@
 // invisible to K) and residual r1 = K e1; the pair is (features(r1, z0), D e1 / s).  The
 // errors are either random (further steps continue from e1) or the errors of the plain
 // multigrid-preconditioned Krylov iterates (hhg_learn_collect_cg).
+//
+// Coarse-grid mode (elasticity, hhg_learn_set_coarsening(q)): the network sees r1
+// restricted q levels and z0 injected there, with that level's diagonal and log k; its
+// correction is prolongated back before the 2x2 combination, and pairs are stored on the
+// coarse grid with the error injected.
 #include <cmath>
 #include <cstring>
 #include <functional>
