@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-stokes", action="store_true")
+    ap.add_argument("--no-kernel-table", action="store_true")
     ap.add_argument("--no-carreau", action="store_true")
     ap.add_argument("--carreau-level", type=int, default=8)
     ap.add_argument("--no-learn", action="store_true")
@@ -248,6 +249,88 @@ def solve_times(B, torch, h, level, coords_u):
                      "inner_iterations": best["inner_iterations"], "rel_residual_fp64": float(np.sqrt(r2)) /
                      best["residual0"], "converged": bool(best["converged"])}
     out["speedup_ir_vs_fp64"] = round(out["fp64_mgcg"]["seconds"] / out["ir_fp64_over_fp32_mgcg"]["seconds"], 3)
+    return out
+
+
+# algorithmic bytes per node of each sweep (every array touched once): x (3 comps), k, y;
+# + f for the residual and a Jacobi step; x, f, k, d read and x, d written for a Chebyshev step
+SWEEP_BYTES = {("apply", 8): 56, ("residual", 8): 80, ("jacobi", 8): 80, ("chebyshev", 8): 128,
+               ("apply", 4): 28, ("residual", 4): 40, ("jacobi", 4): 40, ("chebyshev", 4): 64,
+               ("apply_bf16_k", 4): 26}
+
+
+def kernel_table(B, torch, dev, stream, levels=(7, 8), reps=10):
+    """Every sweep of the hot path on the C2 workload (lognormal E seed 2, x and f U[-1, 1]
+    seed 3) at each level: apply, residual, one Jacobi and one Chebyshev step in FP64 and FP32,
+    and the FP32 apply with the BF16 coefficient.  Device time of the whole sweep per call
+    (CUDA events; the L2 is flushed before each call), GDoF/s = 3 x unique nodes / t, the
+    algorithmic bytes per node and their rate against the measured copy bandwidth."""
+    import hhg_inputs as hi
+
+    hbm_peak, peak_kind = measured_peaks()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = {"workload": "C2: 6-macro cube, lognormal E (seed 2), x and f ~ U[-1,1] (seed 3)",
+           "hbm_peak_gbs": hbm_peak, "hbm_peak_source": peak_kind, "reps": reps, "rows": []}
+    xyz, tets = hi.kuhn_cube(1)
+    for level in levels:
+        h = B.hhg_create(dev, stream.cuda_stream)
+        try:
+            B.hhg_set_macro_mesh(h, xyz, tets)
+            B.hhg_refine(h, level)
+            B.hhg_set_problem(h, nu=NU)
+            E, U, _ = B.hhg_num_nodes(h, level)
+            ce = B.hhg_entry_coords(h, level)
+            e2u, udir = B.hhg_entry_to_unique(h, level)
+            first = np.full(U, -1, dtype=np.int64)
+            first[e2u[::-1]] = np.arange(E)[::-1]
+            k_u, x_u = workload_fields(ce[first], level)
+            x_u[udir] = 0.0
+            kl = torch.empty(E, dtype=torch.float64, device="cuda")
+            B.hhg_scatter_unique(h, level, B.F64, 1, torch.as_tensor(k_u, dtype=torch.float64, device="cuda"), kl)
+            B.hhg_set_coefficient(h, kl, B.F64)
+            B.hhg_mg_setup(h)
+            xs = torch.as_tensor(np.ascontiguousarray(x_u.T).reshape(-1), dtype=torch.float64, device="cuda")
+            x64 = torch.empty(3 * E, dtype=torch.float64, device="cuda")
+            B.hhg_scatter_unique(h, level, B.F64, 3, xs, x64)
+            f64 = 0.5 * x64
+            bufs = {B.F64: (x64, f64, torch.empty_like(x64)), B.F32: (x64.float(), f64.float(), None)}
+            bufs[B.F32] = bufs[B.F32][:2] + (torch.empty_like(bufs[B.F32][0]),)
+
+            def timed(call):
+                for _ in range(2):
+                    call()
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(reps)]
+                for q, (a, b) in enumerate(ev):
+                    flush.fill_(float(q))
+                    a.record(stream)
+                    call()
+                    b.record(stream)
+                torch.cuda.synchronize()
+                return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+            def row(kind, dt, ms):
+                w = 8 if dt == B.F64 else 4
+                byts = SWEEP_BYTES[(kind, w)]
+                gbs = byts * U / (ms * 1e-3) / 1e9
+                out["rows"].append({"level": level, "kernel": kind, "dtype": "f64" if w == 8 else "f32",
+                                    "ms": round(ms, 5), "gdofs": round(3 * U / (ms * 1e-3) / 1e9, 3),
+                                    "bytes_per_node": byts, "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4)})
+
+            for dt in (B.F64, B.F32):
+                x, f, y = bufs[dt]
+                row("apply", dt, timed(lambda: B.hhg_apply(h, level, dt, x, y)))
+                row("residual", dt, timed(lambda: B.hhg_residual(h, level, dt, f, x, y)))
+                for kind, sm in (("jacobi", B.SMOOTH_JACOBI), ("chebyshev", B.SMOOTH_CHEBYSHEV)):
+                    B.hhg_set_mg_params(h, smoother=sm)
+                    y.copy_(x)
+                    row(kind, dt, timed(lambda: B.hhg_smooth(h, level, dt, 1, f, y)))
+                B.hhg_set_mg_params(h)
+            x, f, y = bufs[B.F32]
+            B.hhg_set_coefficient(h, kl.to(torch.bfloat16).view(torch.int16), B.BF16)
+            row("apply_bf16_k", B.F32, timed(lambda: B.hhg_apply(h, level, B.F32, x, y)))
+        finally:
+            B.hhg_destroy(h)
     return out
 
 
@@ -767,6 +850,7 @@ def run_ours(args):
     solve = None if args.no_solve else solve_times(B, torch, h, level, coords_e[first])
     B.hhg_destroy(h)
     stokes = None if args.no_stokes else stokes_bench(B, torch, level, dev, stream)
+    ktable = None if args.no_kernel_table else kernel_table(B, torch, dev, stream, (level, level + 1))
     carreau = None if args.no_carreau else carreau_bench(B, torch, args.carreau_level, dev, stream)
     learned = None if args.no_learn else learned_bench(B, torch, dev, stream, args.learn_train_level,
                                                        args.learn_level, args.learn_seeds, 2, 6, args.learn_steps,
@@ -806,7 +890,9 @@ def run_ours(args):
                          "peak_source": peak_kind},
                  "alu": {"achieved_tflops": round(alu_achieved, 3), "peak_tflops": round(alu_peak, 2),
                          "frac": round(alu_frac, 4)},
-                 "skeleton_ms_per_step": round(prof_ms[1] / args.steps, 5)})
+                 "skeleton_ms_per_step": round(prof_ms[1] / args.steps, 5),
+                 # the paper's unit (Sec. 4.2 benchmark: 222 ns per node update and CPU rank)
+                 "ns_per_interior_node_update": round(launch_ms * 1e6 / interior_per_macro, 5)})
     out = {
         "metric": METRIC,
         "value": round(value, 3),
@@ -828,6 +914,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4)},
         "gpu_launches": int(prof_launches[0] + prof_launches[1]),
         "solve": solve,
+        "kernels": ktable,
         "stokes": stokes,
         "carreau": carreau,
         "bf16_coefficient": bf16,
