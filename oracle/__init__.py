@@ -17,10 +17,15 @@ quadrature, and builds each operator from its definition in the paper:
 * Stokes blocks B, B^T and the stabilisation C ... Sec. 5.2, stabilised P1-P1
 * nodal strain-rate least squares and Carreau ..... Sec. 3, eq. (minimization_problem);
                                                    Sec. 5.2.2, eq. (carreau)
+* inexact Uzawa multigrid for the saddle system .... Sec. 5.2 (the library's variant, step
+                                                   by step)
+* learned preconditioner (not in the paper) ...... its conv net, features, training pairs
+                                                   and combination rule
 
 Modules: ``mesh`` (refinement, node classification, transfer parents),
 ``fem`` (quadrature and element matrices), ``operators`` (global sparse
 operators), ``rows`` (one operator row at any level by local refinement),
 ``solvers`` (Dirichlet handling, PCG, Chebyshev, V-cycle, MINRES, iterative
-refinement), ``stokes``, ``carreau``.
+refinement), ``stokes`` (saddle operator, inexact Uzawa multigrid), ``carreau``,
+``learned``.
 """
