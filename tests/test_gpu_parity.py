@@ -114,12 +114,13 @@ def test_apply_and_residual_parity(name, builder, level, opt):
         ctx.close()
 
 
-def test_full_size_sampled_rows_cube_level7():
-    """The 6-macro cube at level 7 (129^3 nodes), the launch configuration of the benchmark:
-    sampled interior, face, edge and vertex rows against the single-row oracle (FP64 exact to
-    1e-12 of the row scale, FP32 within the stated bound)."""
+@pytest.mark.parametrize("level", [7, 8], ids=["level7", "level8"])
+def test_full_size_sampled_rows_cube(level):
+    """The 6-macro cube at level 7 (129^3 nodes, the launch configuration of the benchmark)
+    and level 8 (257^3 nodes, the Carreau and learned-evaluation size): sampled interior,
+    face, edge and vertex rows against the single-row oracle (FP64 exact to 1e-12 of the
+    row scale, FP32 within the stated bound)."""
     xyz, tets = hi.kuhn_cube(1)
-    level = 7
     ctx = Ctx(xyz, tets, level, dict(nu=0.3))
     try:
         t = ctx.torch
