@@ -36,7 +36,7 @@ LEVEL = 7
 NU = 0.3
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-# algorithmic cost of one macro-interior node of the FP32 apply (see DESIGN.md)
+# algorithmic cost of one macro-interior node of the FP32 apply
 BYTES_PER_NODE_F32 = 28  # read x (12 B) and k (4 B), write y (12 B)
 FLOPS_PER_NODE = 723     # FMA = 2 flops, as the kernel evaluates the scaled stencil
 METRIC = "scaled-stencil vector matvec GDoF/s & % of HBM peak; time to 1e-8 residual"

@@ -1,9 +1,11 @@
 """Parity of the CUDA operator apply / residual against the FP64 CPU oracle, through the C ABI.
 
-Tolerances (stated here, derived in the design doc):
-  FP64: max |y_gpu - y_oracle| / max |y_oracle| <= 1e-12.
+Tolerances:
+  FP64: max |y_gpu - y_oracle| / max |y_oracle| <= 1e-12 (rounding differences of sums of at
+        most a few hundred terms).
   FP32: per row, |y32 - y_oracle|_i <= 64 * 2^-24 * sum_j |A_ij| |x_j - x_i|  (the scale of the
-        row's terms in the difference form the kernels evaluate), on free rows; Dirichlet rows
+        row's terms in the difference form the kernels evaluate: FP32 rounding of x, k, the
+        stencil constants and about 64 accumulated products), on free rows; Dirichlet rows
         return x rounded to FP32.
 """
 
