@@ -464,16 +464,6 @@ DevMem* swork<float>(LevelHost& L) {
   return L.sw32;
 }
 template <typename T>
-const T* invm(LevelHost& L);
-template <>
-const double* invm<double>(LevelHost& L) {
-  return L.d_invm64.as<double>();
-}
-template <>
-const float* invm<float>(LevelHost& L) {
-  return L.d_invm32.as<float>();
-}
-template <typename T>
 const T* mass(LevelHost& L);
 template <>
 const double* mass<double>(LevelHost& L) {
