@@ -410,8 +410,10 @@ hhg_status hhg_learn_set_conv_kernel(hhg_ctx* ctx, int kernel);
  * the V-cycle) and z0 injected (coarse nodes are fine nodes), D is that level's point
  * diagonal, and its correction is prolongated back (P, linear interpolation) before the
  * 2x2 combination; training pairs are stored on the coarse grid with the error injected
- * there.  Pairs keep the coarsening they were reserved with; levels - coarsening must not
- * go below the coarsest level. */
+ * there.  Pairs keep the coarsening they were reserved with.  Errors: ARG for levels
+ * outside 0..3, UNSUPPORTED for levels > 0 on a Stokes problem; an application, a pair
+ * reservation or collection whose level minus the coarsening is below the coarsest level
+ * fails with ARG, and collecting into pairs reserved with another coarsening with STATE. */
 hhg_status hhg_learn_set_coarsening(hhg_ctx* ctx, int levels);
 /* He-normal initialisation (std sqrt(2/(27*fan_in)), last layer x0.1; BF16 values,
  * zero biases) from a seeded generator, with the input and output channels of the
@@ -423,7 +425,8 @@ hhg_status hhg_learn_get_params(hhg_ctx* ctx, float* params_host, int64_t n);
 hhg_status hhg_learn_set_params(hhg_ctx* ctx, const float* params_host, int64_t n);
 /* Node-grid dimensions (D, H, W) of a level and its number of voxels with a free node. */
 hhg_status hhg_learn_grid(hhg_ctx* ctx, int level, int* dhw_host, int64_t* free_voxels);
-/* Input and output channels (cin, cout) of the context's problem kind. */
+/* Input and output channels (cin, cout) of the context's problem kind (either pointer
+ * nullable; no error beyond a null context). */
 hhg_status hhg_learn_channels(hhg_ctx* ctx, int* cin_host, int* cout_host);
 /* Network forward pass on B grids of D x H x W voxels: x_dev FP32 [B][D][H][W][cin]
  * (cin <= 16, rounded to BF16), out_dev FP32 [B][D][H][W][cout] (cout 3 or 4: the first
