@@ -348,13 +348,16 @@ hhg_status hhg_picard(hhg_ctx* ctx, const hhg_picard_opts* opts, const void* f_d
  * exits.  It calls no cudaMalloc, cudaFree or other allocating routine; the
  * context must already be set up (hhg_refine etc. allocate, this call does not).
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Levels whose residual needs more than 262,144 partial
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life of
+ * the process, so resetting the device (cudaDeviceReset) while the library is
+ * loaded is not supported.  Every call waits for the stream (it polls the
+ * stream with cudaStreamQuery after copying the norm to pinned host memory),
+ * so it must not be called while the stream is being captured.  Levels whose residual needs more than 262,144 partial
  * sums (one per interior tile of each macro plus one per free skeleton node;
  * for the 6-macro cube: levels up to 7) are rejected with HHG_ERR_ARG.
  * All calls share the array: calls that overlap on the GPU (other streams,
- * other contexts on the same device) race on it.  Waits for the stream
- * (bounded wait). */
+ * other contexts on the same device) race on it.  The wait for the stream is
+ * bounded (hhg_set_timeout). */
 hhg_status hhg_residual_noalloc(hhg_ctx* ctx, int level, hhg_dtype dt, const void* f_dev, const void* x_dev,
                                 void* r_dev, double* norm2_host);
 

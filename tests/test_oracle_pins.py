@@ -186,6 +186,46 @@ def test_lemma_affine_coefficient(fixture, request):
     assert abs(Au - An).max() > 1e-4 * scale
 
 
+@pytest.mark.parametrize("fixture", ["cube3", "skew3"])
+def test_edge_mean_khat_equals_patch_mean_for_affine_coefficient(fixture, request):
+    """Remark after Sec. 2.2 (khat = (k_i + k_j)/2) against eq. (patchmean): the patch of an
+    edge inside a macro is point-symmetric about the edge midpoint (t -> t^m maps it onto
+    itself), so for an affine k the mean of the element means kbar^t is k at the midpoint,
+    i.e. (k_i + k_j)/2.  The two khat rules then give the same operator in both variants; for
+    a non-affine k they differ."""
+    mm, lv, K = request.getfixturevalue(fixture)
+    k = hi.affine_field(lv.coords, 2.0, [0.7, -0.4, 0.9])
+    scale = abs(op.nodal_integration(lv, K, k)).max()
+    for var in ("physical", "unphysical"):
+        Ap = op.scaled_operator(lv, K, k, var, khat="patch")
+        Ae = op.scaled_operator(lv, K, k, var, khat="edge")
+        assert abs(Ap - Ae).max() < 1e-13 * scale
+    rng = np.random.default_rng(17)
+    kr = rng.uniform(0.5, 3.0, lv.num_nodes)
+    assert abs(op.scaled_operator(lv, K, kr, khat="patch") - op.scaled_operator(lv, K, kr, khat="edge")).max() \
+        > 1e-4 * scale
+
+
+@pytest.mark.parametrize("fixture", ["cube3", "skew3"])
+def test_practical_interface_rule_pins(fixture, request):
+    """Sec. 2.2, practical interface rows (every skeleton row is the a_h row): for constant k
+    the whole operator is the Galerkin matrix (both a_h and the scaled blocks reproduce it,
+    Sec. 2); for affine k it is nodal integration everywhere (Lemma 2.1 on the macro-interior
+    rows, a_h on the skeleton rows)."""
+    mm, lv, K = request.getfixturevalue(fixture)
+    G = op.nodal_integration(lv, K, np.ones(lv.num_nodes))
+    A = op.scaled_operator(lv, K, np.full(lv.num_nodes, 1.7), iface="practical")
+    assert abs(A - 1.7 * G).max() < 1e-13 * abs(G).max()
+    k = hi.affine_field(lv.coords, 2.0, [0.3, 0.5, -0.2])
+    An = op.nodal_integration(lv, K, k)
+    for khat in ("patch", "edge"):
+        Ap = op.scaled_operator(lv, K, k, iface="practical", khat=khat)
+        assert abs(Ap - An).max() < 1e-13 * abs(An).max()
+    # the unphysical variant keeps the interior rows away from a_h (the pin can fail)
+    Au = op.scaled_operator(lv, K, k, "unphysical", iface="practical")
+    assert abs(Au - An).max() > 1e-4 * abs(An).max()
+
+
 def test_correction_is_antisymmetric_part_of_nodal_blocks(skew3):
     """eq. (corrtermgeneral): R_ij = 1/2 sum (kbar^t - kbar^{t^m}) antisym(a^t_ij) equals the
     antisymmetric part of the nodal-integration block, since the reflection pairs the patch; so
