@@ -310,7 +310,9 @@ typedef struct {
   int level;
   double picard_tol;     /* stop when max_i |u_i - u_i_prev| < picard_tol * max_i |u_i| (Alg. 1) */
   int max_picard;
-  double step_rtol;      /* relative tolerance of the inexact solve of each fixed-point step */
+  double step_rtol;      /* relative tolerance of the inexact solve of each fixed-point step (one FP64
+                            refinement step around FP32 MINRES to max(step_rtol, 1e-6); below 1e-6,
+                            further refinement steps, at most 50) */
   int step_max_iter;     /* MINRES iterations per step */
   double final_rtol;     /* final solve to this relative residual (Alg. 1: 1e-3) */
 } hhg_picard_opts;

@@ -7,6 +7,8 @@ affine polynomial over the node and its mesh neighbours (eq. minimization_proble
 m = 1); the fitted gradient gives eps(u) = (grad u + grad u^T)/2, |eps|^2 = eps : eps, and
 
     mu = eta_inf + (eta0 - eta_inf) (1 + kappa |eps|^2)^r          (eq. carreau).
+
+The fixed-point iteration of Alg. 1 (Sec. 5.2.2) is restated with exact linear solves.
 """
 
 from __future__ import annotations
@@ -55,3 +57,58 @@ def carreau(e2, eta0, eta_inf, kappa, r):
 
 def viscosity(lv: Level, u, eta0, eta_inf, kappa, r):
     return carreau(strain_rate_sq(lsq_gradients(lv, u)), eta0, eta_inf, kappa, r)
+
+
+# ------------------------------------------------------- fixed-point iteration (Alg. 1)
+
+
+def saddle_solve(mm, lv: Level, mu, f4, g4):
+    """Exact solution of the linearised saddle system (eq. fixpointsystem) for the viscosity
+    mu: K(mu) x = f with the velocity-Dirichlet values of g4 and the pressure fixed by a zero
+    mass-weighted mean (bordered system [[K, c], [c^T, 0]], c = (0, m), m the lumped mass).
+    f4, g4: (N, 4) node-major (u, v, w, p); returns x (N, 4)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+
+    from . import stokes as stk
+
+    N = lv.num_nodes
+    Kbc, _ = stk.stokes_operator(mm, lv, mu)
+    rhs = stk.pack4(f4)
+    d = np.asarray(lv.dirichlet)
+    g = np.asarray(g4, dtype=np.float64)
+    rhs[:3 * N].reshape(N, 3)[d] = g[d, :3]
+    c = np.concatenate([np.zeros(3 * N), stk.lumped_mass(lv)])
+    Kb = sp.bmat([[Kbc, sp.csr_matrix(c[:, None])], [sp.csr_matrix(c[None, :]), None]]).tocsc()
+    sol = spla.spsolve(Kb, np.concatenate([rhs, [0.0]]))
+    return stk.unpack4(sol[:4 * N], N)
+
+
+def picard(mm, lv: Level, f4, x0, eta0, eta_inf, kappa, r, tol=1e-3, max_picard=40):
+    """Alg. 1 (Sec. 5.2.2) with every linear system solved exactly (``saddle_solve``): the
+    method's inexact multigrid solves approximate these steps.
+
+        mu^(0) = mu(u^(0));  repeat: x^(n+1) = solve(mu^(n)), mu^(n+1) = mu(u^(n+1)), n += 1
+        until max_i |u_i^(n) - u_i^(n-1)|_2 < tol * max_i |u_i^(n)|_2;
+        final: x^(n+1) = solve(mu^(n)), mu^(n+1) = mu(u^(n+1)).
+
+    x0 (N, 4) holds u^(0) and the velocity-Dirichlet values.  Returns (x, mu, n, changes)
+    with n the number of fixed-point steps before the final solve and changes the relative
+    change of each step."""
+    x = np.array(x0, dtype=np.float64)
+    mu = viscosity(lv, x[:, :3], eta0, eta_inf, kappa, r)
+    changes = []
+    n = 0
+    while n < max_picard:
+        prev = x
+        x = saddle_solve(mm, lv, mu, f4, x0)
+        mu = viscosity(lv, x[:, :3], eta0, eta_inf, kappa, r)
+        n += 1
+        um = np.linalg.norm(x[:, :3], axis=1).max()
+        du = np.linalg.norm(x[:, :3] - prev[:, :3], axis=1).max()
+        changes.append(du / um if um > 0 else 0.0)
+        if changes[-1] < tol:
+            break
+    x = saddle_solve(mm, lv, mu, f4, x0)
+    mu = viscosity(lv, x[:, :3], eta0, eta_inf, kappa, r)
+    return x, mu, n, changes

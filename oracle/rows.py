@@ -55,8 +55,12 @@ def elements_around(mm: MacroMesh, level: int, macro: int, local_ijk):
 
 
 def row(mm: MacroMesh, level: int, macro: int, local_ijk, kfun, xfun, c_eps, c_div,
-        variant="physical", khat="patch", iface="symmetric", skeleton_diag="zero_row_sum"):
-    """(A x)_p for the node p = (macro, local_ijk); kfun(coords)->k, xfun(coords)->(.,3)."""
+        variant="physical", khat="patch", iface="symmetric", skeleton_diag="zero_row_sum",
+        want_scale=False):
+    """(A x)_p for the node p = (macro, local_ijk); kfun(coords)->k, xfun(coords)->(.,3).
+    Returns (y, key); with want_scale also the row's term scale
+    s_m = sum_{j != p} sum_l |A_pj[m, l]| |x_j[l] - x_p[l]| (the magnitude of the terms of the
+    difference form sum_j A_pj (x_j - x_p), for rounding bounds)."""
     n = 1 << level
     elems, pkey = elements_around(mm, level, macro, local_ijk)
     keys = []  # per element: list of 4 node keys
@@ -126,4 +130,9 @@ def row(mm: MacroMesh, level: int, macro: int, local_ijk, kfun, xfun, c_eps, c_d
     y = centre @ xval[pkey]
     for j, b in blocks.items():
         y = y + b @ xval[j]
+    if want_scale:
+        sc = np.zeros(3)
+        for j, b in blocks.items():
+            sc += np.abs(b) @ np.abs(xval[j] - xval[pkey])
+        return y, pkey, sc
     return y, pkey

@@ -1278,7 +1278,9 @@ hhg_status hhg_picard(hhg_ctx* c, const hhg_picard_opts* o, const void* f, void*
     so.level = l;
     so.dt = HHG_F64;
     so.rtol = o->step_rtol;
-    so.max_iter = 1;
+    // one refinement step when the FP32 inner solve reaches step_rtol by itself, more below
+    // what FP32 can reach
+    so.max_iter = o->step_rtol < 1e-6 ? 50 : 1;
     so.inner_rtol = std::max(o->step_rtol, 1e-6);
     so.inner_max_iter = o->step_max_iter;
     double change = 1.0;

@@ -62,3 +62,56 @@ def test_picard_lid_driven_cavity():
         assert np.allclose(xs[ctx.udir, :3], x0[ctx.udir, :3])
     finally:
         ctx.close()
+
+
+def test_picard_parity_with_exact_steps():
+    """Alg. 1 on the 6-macro cube, level 3, lid velocity on z = 1 and a seeded body force,
+    with each fixed-point step solved to 1e-11 (FP64 refinement): the GPU's fixed-point
+    count, final velocity, pressure and viscosity equal those of the oracle's Alg. 1 with
+    exact sparse solves (oracle.carreau.picard).  The oracle's change sequence keeps a
+    margin of 30% from the stopping threshold, so the count is not decided by rounding."""
+    from oracle import carreau as CA
+
+    xyz, tets = hi.kuhn_cube(1)
+    level = 3
+    mm = mesh.MacroMesh.build(xyz, tets)
+    lv = mesh.build_level(mm, level)
+    N = lv.num_nodes
+
+    def setup(coords, dirichlet):
+        x0 = np.zeros((len(coords), 4))
+        x0[:, :3] = hi.lid_velocity(coords)
+        x0[~dirichlet] = 0.0
+        f = np.zeros((len(coords), 4))
+        f[:, :3] = 20.0 * hi.node_noise(coords, seed=7)
+        f[dirichlet, :3] = 0.0
+        return x0, f
+
+    x0o, fo = setup(lv.coords, lv.dirichlet)
+    tol = 1e-3
+    xo, muo, no, ch = CA.picard(mm, lv, fo, x0o, tol=tol, **PAR)
+    assert all(abs(c / tol - 1.0) > 0.3 for c in ch)
+    ctx = Ctx(xyz, tets, level, dict(kind=B.STOKES))
+    try:
+        t = ctx.torch
+        perm = mesh.match_nodes(lv.coords, ctx.coords_u)
+        assert np.array_equal(ctx.udir[perm], lv.dirichlet)
+        ctx.set_k(np.ones(ctx.U))
+        x0, f = setup(ctx.coords_u, ctx.udir)
+        x = ctx.to_lib(x0, t.float64, 4)
+        fd = ctx.to_lib(f, t.float64, 4)
+        rep = B.hhg_picard(ctx.h, fd, x, level, picard_tol=tol, max_picard=40, step_rtol=1e-11,
+                           step_max_iter=400, final_rtol=1e-11, **PAR)
+        assert rep["picard_iterations"] == no, (rep, ch)
+        xg = ctx.from_lib(x, 4)[perm]
+        # the viscosity left as the coefficient is mu(u) of the final velocity
+        mu_d = t.empty(ctx.E, dtype=t.float64, device="cuda")
+        B.hhg_carreau_viscosity(ctx.h, level, x, mu_d, **PAR)
+        mug = ctx.from_lib(mu_d, 1)[perm, 0]
+        eu = np.abs(xg[:, :3] - xo[:, :3]).max() / np.abs(xo[:, :3]).max()
+        ep = np.abs(xg[:, 3] - xo[:, 3]).max() / np.abs(xo[:, 3]).max()
+        em = np.abs(mug - muo).max() / np.abs(muo).max()
+        assert eu < 1e-7 and ep < 1e-7 and em < 1e-7, (eu, ep, em)
+        assert abs(rep["mu_min"] - muo.min()) < 1e-7 and abs(rep["mu_max"] - muo.max()) < 1e-7
+    finally:
+        ctx.close()

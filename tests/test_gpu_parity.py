@@ -9,6 +9,8 @@ Tolerances:
         return x rounded to FP32.
 """
 
+import os
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -116,52 +118,112 @@ def test_apply_and_residual_parity(name, builder, level, opt):
         ctx.close()
 
 
+def _sample_rows(n, rng, nmacro=6):
+    """Macro-interior rows (macro, (i, j, k)) of every kind the kernels treat differently:
+    uniform over the interior, the last slices (k >= n - 8, where a slice holds few rows),
+    rows next to a macro face (i, j or k = 1, or i + j + k = n - 1) and the ends of slice
+    rows (i = n - 1 - j - k)."""
+    out = []
+
+    def rand_interior(kmin=1):
+        while True:
+            i, j, k = (int(v) for v in rng.integers(1, n, size=3))
+            if k >= kmin and i + j + k <= n - 1:
+                return i, j, k
+
+    for _ in range(1200):
+        out.append((int(rng.integers(nmacro)), rand_interior()))
+    for _ in range(400):
+        out.append((int(rng.integers(nmacro)), rand_interior(n - 8)))
+    for q in range(400):
+        i, j, k = rand_interior()
+        s = n - 1 - (i + j + k)
+        which = q % 4
+        if which == 0:
+            i = 1
+        elif which == 1:
+            j = 1
+        elif which == 2:
+            k = 1
+        else:
+            i += s
+        out.append((int(rng.integers(nmacro)), (i, j, k)))
+    for _ in range(200):
+        i, j, k = rand_interior()
+        out.append((int(rng.integers(nmacro)), (n - 1 - j - k, j, k)))
+    return out
+
+
 @pytest.mark.parametrize("level", [7, 8], ids=["level7", "level8"])
 def test_full_size_sampled_rows_cube(level):
     """The 6-macro cube at level 7 (129^3 nodes, the launch configuration of the benchmark)
-    and level 8 (257^3 nodes, the Carreau and learned-evaluation size): sampled interior,
-    face, edge and vertex rows against the single-row oracle (FP64 exact to 1e-12 of the
-    row scale, FP32 within the stated bound)."""
+    and level 8 (257^3 nodes): 2200 macro-interior rows (uniform, last slices, next to macro
+    faces, ends of slice rows) and skeleton rows of every multiplicity (face, edge, vertex
+    nodes) against the single-row oracle: FP64 within 1e-12 of the row scale, FP32 within
+    the per-row bound 64 * 2^-24 * sum_j |A_ij| |x_j - x_i| stated above."""
+    import multiprocessing as mpc
+
+    import oracle_rows_pool as orp
+
+    n = 1 << level
     xyz, tets = hi.kuhn_cube(1)
+    rng = np.random.default_rng(level)
+    interior = _sample_rows(n, rng)
     ctx = Ctx(xyz, tets, level, dict(nu=0.3))
     try:
         t = ctx.torch
-        grid_k = hi.lognormal_grid(1 << level, seed=2)
-        kf = lambda c: hi.sample_grid(grid_k[..., None], c)[:, 0]
-        grid_x = hi.uniform_grid(1 << level, seed=3)
-        xf = lambda c: hi.sample_grid(grid_x, c)
-        ctx.set_k(kf(ctx.coords_u))
-        xu = xf(ctx.coords_u)
-        ce, cd = fem.elasticity_coefficients(0.3)
-        mm = mesh.MacroMesh.build(xyz, tets)
-        rng = np.random.default_rng(0)
-        # pick rows: random interior entries + skeleton nodes of each kind
-        pick = list(rng.choice(ctx.U, 24, replace=False))
-        nodes_per_inc = np.bincount(ctx.e2u, minlength=ctx.U)
-        for cnt in np.unique(nodes_per_inc):
-            cand = np.nonzero((nodes_per_inc == cnt) & ~ctx.udir)[0]
-            if len(cand):
-                pick += list(rng.choice(cand, min(3, len(cand)), replace=False))
+        grid_k = hi.lognormal_grid(n, seed=2)
+        grid_x = hi.uniform_grid(n, seed=3)
+        ctx.set_k(hi.sample_grid(grid_k[..., None], ctx.coords_u)[:, 0])
+        xu = hi.sample_grid(grid_x, ctx.coords_u)
+        nt = ctx.E // 6
         first = np.full(ctx.U, -1, dtype=np.int64)
         first[ctx.e2u[::-1]] = np.arange(ctx.E)[::-1]
+        picks = [(int(ctx.e2u[m * nt + _lattice_index(n, *ijk)]), m, ijk) for m, ijk in interior]
+        # skeleton rows: three free nodes of every multiplicity (incident macros), 100 more
+        # random free face nodes
+        per_inc = np.bincount(ctx.e2u, minlength=ctx.U)
+        skel = []
+        for cnt in np.unique(per_inc):
+            cand = np.nonzero((per_inc == cnt) & ~ctx.udir)[0]
+            if cnt > 1 and len(cand):
+                skel += list(rng.choice(cand, min(3 if cnt > 2 else 103, len(cand)), replace=False))
+        for u in skel:
+            m, loc = divmod(int(first[u]), nt)
+            picks.append((int(u), m, _decode(n, loc)))
+        nproc = max(1, min(8, (os.cpu_count() or 1)))
+        chunks = [picks[q::nproc] for q in range(nproc)]
+        with mpc.get_context("spawn").Pool(nproc, initializer=orp.init, initargs=(level,)) as pool:
+            res = pool.map(orp.job, [[(m, ijk) for _, m, ijk in ch] for ch in chunks])
+        want = {}
+        for ch, rs in zip(chunks, res):
+            for (u, _, _), (y, sc) in zip(ch, rs):
+                want[u] = (y, sc)
+        assert len(want) >= 2000
         for dt, tdt in ((B.F64, t.float64), (B.F32, t.float32)):
             x = ctx.to_lib(xu, tdt, 3)
             y = t.empty_like(x)
             B.hhg_apply(ctx.h, level, dt, x, y)
             yg = ctx.from_lib(y, 3)
-            for u in pick:
-                u = int(u)
-                if ctx.udir[u]:
-                    continue
-                e = first[u]
-                nt = (ctx.E // 6)
-                m, loc = divmod(e, nt)
-                ijk = _decode(1 << level, loc)
-                yr, _ = rows.row(mm, level, m, ijk, kf, xf, ce, cd)
-                tol = 1e-12 * (np.abs(yr).max() + 1e-3) if dt == B.F64 else 2e-4 * (np.abs(yr).max() + 1e-3)
-                assert np.abs(yg[u] - yr).max() <= tol, (u, yg[u], yr)
+            worst = 0.0
+            for u, (yr, sc) in want.items():
+                err = np.abs(yg[u] - yr)
+                if dt == B.F64:
+                    assert err.max() <= 1e-12 * (sc.max() + np.abs(yr).max()), (u, yg[u], yr)
+                else:
+                    assert np.all(err <= FP32_C * sc + 1e-30), (u, yg[u], yr, sc)
+                    worst = max(worst, float((err / (sc + 1e-300)).max()))
+            if dt == B.F32:
+                print("level %d: %d rows, worst FP32 error / term scale %.3g (bound %.3g)"
+                      % (level, len(want), worst, FP32_C))
     finally:
         ctx.close()
+
+
+def _lattice_index(n, i, j, k):
+    m = n - k
+    T = lambda a: a * (a + 1) * (a + 2) // 6
+    return T(n + 1) - T(n + 1 - k) + j * (2 * m + 3 - j) // 2 + i
 
 
 def _decode(n, loc):

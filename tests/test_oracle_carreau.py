@@ -42,3 +42,67 @@ def test_carreau_law_limits():
     assert mu[0] == 140.764
     assert np.all(np.diff(mu) < 0)  # shear thinning
     assert abs(mu[-1] - 1.0) < 1e-2 * 140.0
+
+
+# ---------------------------------------------------------------- Alg. 1 (Sec. 5.2.2)
+
+PAR = dict(eta0=1.0, eta_inf=1e-3, kappa=1.0, r=-0.25)
+
+
+def _cube(level):
+    xyz, tets = hi.kuhn_cube(1)
+    mm = mesh.MacroMesh.build(xyz, tets)
+    return mm, mesh.build_level(mm, level)
+
+
+def test_picard_keeps_the_affine_shear_flow():
+    """u = (z, 0, 0), p = 0 solves the Carreau-Stokes problem with f = 0 and its own boundary
+    values: eps(u) is constant (|eps|^2 = 1/2), so mu is the constant
+    eta_inf + (eta0 - eta_inf)(1 + kappa/2)^r (the least-squares fit is exact for affine u),
+    div u = 0, and the P1 operator with a constant coefficient annihilates affine fields at
+    free nodes.  Started there, Alg. 1 stops after one step with no change; started from the
+    boundary values alone, it converges to the same flow."""
+    mm, lv = _cube(3)
+    N = lv.num_nodes
+    ex = np.zeros((N, 4))
+    ex[:, 0] = lv.coords[:, 2]
+    mu_ex = PAR["eta_inf"] + (PAR["eta0"] - PAR["eta_inf"]) * (1 + PAR["kappa"] / 2) ** PAR["r"]
+    f = np.zeros((N, 4))
+    x, mu, n, ch = CA.picard(mm, lv, f, ex, **PAR)
+    assert n == 1 and ch[0] < 1e-12
+    assert np.abs(x[:, :3] - ex[:, :3]).max() < 1e-12 and np.abs(x[:, 3]).max() < 1e-10
+    assert np.abs(mu - mu_ex).max() < 1e-12
+    x0 = np.zeros((N, 4))
+    x0[lv.dirichlet] = ex[lv.dirichlet]
+    x, mu, n, ch = CA.picard(mm, lv, f, x0, tol=1e-10, max_picard=60, **PAR)
+    assert n > 2 and ch[-1] < 1e-10
+    assert np.abs(x - ex).max() < 1e-8
+    assert np.abs(mu - mu_ex).max() < 1e-8
+
+
+def test_picard_constant_viscosity_is_one_stokes_solve():
+    """eta0 = eta_inf: mu does not depend on u, so the second step changes nothing (n = 2)
+    and the result is the Stokes solution for that viscosity (the saddle system holds with
+    it, and not with another)."""
+    mm, lv = _cube(3)
+    N = lv.num_nodes
+    x0 = np.zeros((N, 4))
+    x0[:, :3] = hi.lid_velocity(lv.coords)
+    x0[~lv.dirichlet] = 0.0
+    f = np.zeros((N, 4))
+    sols = {}
+    for m in (1.0, 3.0):
+        x, mu, n, ch = CA.picard(mm, lv, f, x0, eta0=m, eta_inf=m, kappa=1.0, r=-0.25)
+        assert n == 2 and ch[1] < 1e-12 and np.all(mu == m)
+        sols[m] = x
+    assert np.abs(sols[1.0][:, 3]).max() > 1e-2
+    # the saddle system holds: free velocity rows and all pressure rows vanish, zero mean
+    from oracle import stokes as stk
+
+    for m in (1.0, 3.0):
+        Kbc, _ = stk.stokes_operator(mm, lv, np.full(N, m))
+        r = stk.residual(Kbc, lv.dirichlet, stk.pack4(f), stk.pack4(sols[m]))
+        assert np.abs(r).max() < 1e-12
+        assert abs((stk.lumped_mass(lv) * sols[m][:, 3]).sum()) < 1e-14
+        Ko, _ = stk.stokes_operator(mm, lv, np.full(N, 4.0 - m))
+        assert np.abs(stk.residual(Ko, lv.dirichlet, stk.pack4(f), stk.pack4(sols[m]))).max() > 1e-3
