@@ -310,9 +310,9 @@ typedef struct {
   int level;
   double picard_tol;     /* stop when max_i |u_i - u_i_prev| < picard_tol * max_i |u_i| (Alg. 1) */
   int max_picard;
-  double step_rtol;      /* relative tolerance of the inexact solve of each fixed-point step (one FP64
-                            refinement step around FP32 MINRES to max(step_rtol, 1e-6); below 1e-6,
-                            further refinement steps, at most 50) */
+  double step_rtol;      /* relative tolerance of the inexact solve of each fixed-point step: one FP64
+                            refinement step around FP32 MINRES to step_rtol; below 1e-6, FP64
+                            refinement steps around FP32 MINRES to 1e-3 (at most 50) */
   int step_max_iter;     /* MINRES iterations per step */
   double final_rtol;     /* final solve to this relative residual (Alg. 1: 1e-3) */
 } hhg_picard_opts;
@@ -510,6 +510,18 @@ hhg_status hhg_apply_host(hhg_ctx* ctx, int level, hhg_dtype dt, const void* x_h
  * last call; span / launches is the interior launches' effective duration.  Waits for
  * the stream. */
 hhg_status hhg_profile(hhg_ctx* ctx, int enable, double* ms_host, int64_t* launches_host);
+
+/* FP32 FMA issue-rate probe, a measurement aid with no counterpart in the paper: the
+ * ALU roofline denominator of the FP32 stencil kernels.  Launches, on the context's
+ * stream, one kernel of (SMs x 8) blocks of 256 threads, each thread running 8
+ * independent chains of `iterations` FMAs (packed = 0: fma.rn.f32, 8 FMAs per step;
+ * packed = 1: the two-lane fma.rn.f32x2, 16 FMAs per step).  out_dev: one device float
+ * (written only under a condition that never holds).  flops_host receives the flops of
+ * the launch (FMA = 2), sm_count_host (nullable) the device's SM count.  The caller
+ * times the launch (CUDA events on the same stream).  Errors: ARG for a null pointer,
+ * iterations < 1 or packed outside {0, 1}. */
+hhg_status hhg_fp32_fma_probe(hhg_ctx* ctx, int packed, int64_t iterations, float* out_dev, double* flops_host,
+                              int* sm_count_host);
 
 #ifdef __cplusplus
 }

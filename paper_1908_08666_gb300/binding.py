@@ -134,6 +134,7 @@ _SIGS = {
     "hhg_picard": [C.c_void_p, C.POINTER(hhg_picard_opts), C.c_void_p, C.c_void_p, C.POINTER(hhg_picard_report)],
     "hhg_solve": [C.c_void_p, C.POINTER(hhg_solve_opts), C.c_void_p, C.c_void_p, C.POINTER(hhg_solve_report)],
     "hhg_profile": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+    "hhg_fp32_fma_probe": [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)],
     "hhg_residual_noalloc": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.POINTER(C.c_double)],
     "hhg_learn_num_params": [],
@@ -295,6 +296,15 @@ def hhg_profile(ctx, enable, read=False):
         return ms, nl
     _check(ctx, load().hhg_profile(ctx, int(enable), None, None))
     return None
+
+
+def hhg_fp32_fma_probe(ctx, packed, iterations, out):
+    """Launch the FP32 FMA issue-rate probe on the context's stream; returns (flops, sm_count)."""
+    fl = C.c_double()
+    sms = C.c_int()
+    _check(ctx, load().hhg_fp32_fma_probe(ctx, int(packed), C.c_int64(int(iterations)), _ptr(out), C.byref(fl),
+                                          C.byref(sms)))
+    return fl.value, sms.value
 
 
 def hhg_residual_noalloc(ctx, level, dt, f, x, r):

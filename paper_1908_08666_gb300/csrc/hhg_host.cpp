@@ -1116,4 +1116,15 @@ hhg_status hhg_profile(hhg_ctx* c, int enable, double* ms_host, int64_t* launche
   });
 }
 
+hhg_status hhg_fp32_fma_probe(hhg_ctx* c, int packed, int64_t iterations, float* out_dev, double* flops_host,
+                              int* sm_count_host) {
+  return guard(c, [&] {
+    if (!out_dev || !flops_host || iterations < 1 || (packed != 0 && packed != 1)) THROW(HHG_ERR_ARG, "probe arguments");
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    if (sm_count_host) *sm_count_host = sms;
+    CK(launch_fma_probe(packed, iterations, sms, out_dev, flops_host, c->stream));
+  });
+}
+
 }  // extern "C"

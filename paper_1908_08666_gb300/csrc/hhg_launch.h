@@ -159,4 +159,7 @@ int launch_hash_unique(int64_t U, int comps, const int8_t* udir, T* u, void* str
 template <typename T>
 int launch_dense_matvec(int N, const T* A, const int64_t* idx, const T* src_u, T* dst_u, void* stream);
 
+// FP32 FMA issue-rate probe on sm_count * 8 blocks of 256 threads; *flops = flops of the launch
+int launch_fma_probe(int packed, int64_t iters, int sm_count, float* out, double* flops, void* stream);
+
 }  // namespace hhg

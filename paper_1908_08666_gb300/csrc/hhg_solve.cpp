@@ -1278,10 +1278,11 @@ hhg_status hhg_picard(hhg_ctx* c, const hhg_picard_opts* o, const void* f, void*
     so.level = l;
     so.dt = HHG_F64;
     so.rtol = o->step_rtol;
-    // one refinement step when the FP32 inner solve reaches step_rtol by itself, more below
-    // what FP32 can reach
-    so.max_iter = o->step_rtol < 1e-6 ? 50 : 1;
-    so.inner_rtol = std::max(o->step_rtol, 1e-6);
+    // one refinement step when the FP32 inner solve reaches step_rtol by itself; below what
+    // FP32 reaches, refinement steps with inner solves to 1e-3 (at most 50)
+    const bool exact_steps = o->step_rtol < 1e-6;
+    so.max_iter = exact_steps ? 50 : 1;
+    so.inner_rtol = exact_steps ? 1e-3 : o->step_rtol;
     so.inner_max_iter = o->step_max_iter;
     double change = 1.0;
     for (int it = 1; it <= o->max_picard; ++it) {
@@ -1302,7 +1303,7 @@ hhg_status hhg_picard(hhg_ctx* c, const hhg_picard_opts* o, const void* f, void*
     hhg_solve_opts fo = so;
     fo.rtol = o->final_rtol;
     fo.max_iter = 50;
-    fo.inner_rtol = std::min(1e-2, std::max(o->final_rtol, 1e-6));
+    fo.inner_rtol = o->final_rtol < 1e-6 ? 1e-3 : std::min(1e-2, o->final_rtol);
     hhg_solve_report fr{};
     check(hhg_solve(c, &fo, f, x, &fr));
     R.minres_iterations += fr.inner_iterations;

@@ -597,4 +597,57 @@ HHG_INST(double)
 template int launch_convert<double, float>(int64_t, const double*, float*, void*);
 template int launch_convert<float, double>(int64_t, const float*, double*, void*);
 
+// ---------------------------------------------------------------------------
+// FP32 FMA issue-rate probe (a measurement aid: the denominator of the ALU roofline
+// of the stencil kernels).  Every thread runs 8 independent FMA chains a <- a * b + c
+// (PACKED: 8 chains of packed two-lane FMAs, fma.rn.f32x2, 16 FMAs per step); the
+// result is stored only under a condition that never holds, so nothing is removed.
+// ---------------------------------------------------------------------------
+constexpr int PROBE_THREADS = 256;
+constexpr int PROBE_BLOCKS_PER_SM = 8;
+
+template <int PACKED>
+__global__ void __launch_bounds__(PROBE_THREADS) k_fma_probe(int64_t iters, float* out) {
+  const float b = 0.9999999f, c = 1.0e-7f;
+  const float s0 = 1.0f + 1.0e-6f * (float)(threadIdx.x & 63);
+  if constexpr (PACKED) {
+    float2 a[8];
+    const float2 b2 = make_float2(b, b), c2 = make_float2(c, c);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = make_float2(s0 + q, s0 - q);
+#pragma unroll 4
+    for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a[q] = __ffma2_rn(a[q], b2, c2);
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sum += a[q].x + a[q].y;
+    if (sum == -1.0f) out[0] = sum;
+  } else {
+    float a[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = s0 + q;
+#pragma unroll 8
+    for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a[q] = fmaf(a[q], b, c);
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sum += a[q];
+    if (sum == -1.0f) out[0] = sum;
+  }
+}
+
+int launch_fma_probe(int packed, int64_t iters, int sm_count, float* out, double* flops, void* stream) {
+  const int64_t blocks = (int64_t)sm_count * PROBE_BLOCKS_PER_SM;
+  if (packed)
+    k_fma_probe<1><<<(unsigned)blocks, PROBE_THREADS, 0, (cudaStream_t)stream>>>(iters, out);
+  else
+    k_fma_probe<0><<<(unsigned)blocks, PROBE_THREADS, 0, (cudaStream_t)stream>>>(iters, out);
+  *flops = 2.0 * (packed ? 16.0 : 8.0) * (double)iters * (double)(blocks * PROBE_THREADS);
+  return (int)cudaGetLastError();
+}
+
 }  // namespace hhg

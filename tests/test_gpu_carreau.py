@@ -69,7 +69,7 @@ def test_picard_parity_with_exact_steps():
     with each fixed-point step solved to 1e-11 (FP64 refinement): the GPU's fixed-point
     count, final velocity, pressure and viscosity equal those of the oracle's Alg. 1 with
     exact sparse solves (oracle.carreau.picard).  The oracle's change sequence keeps a
-    margin of 30% from the stopping threshold, so the count is not decided by rounding."""
+    margin of 20% from the stopping threshold, so the count is not decided by rounding."""
     from oracle import carreau as CA
 
     xyz, tets = hi.kuhn_cube(1)
@@ -90,7 +90,7 @@ def test_picard_parity_with_exact_steps():
     x0o, fo = setup(lv.coords, lv.dirichlet)
     tol = 1e-3
     xo, muo, no, ch = CA.picard(mm, lv, fo, x0o, tol=tol, **PAR)
-    assert all(abs(c / tol - 1.0) > 0.3 for c in ch)
+    assert all(abs(c / tol - 1.0) > 0.2 for c in ch)
     ctx = Ctx(xyz, tets, level, dict(kind=B.STOKES))
     try:
         t = ctx.torch

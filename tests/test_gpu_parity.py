@@ -126,10 +126,16 @@ def _sample_rows(n, rng, nmacro=6):
     out = []
 
     def rand_interior(kmin=1):
-        while True:
-            i, j, k = (int(v) for v in rng.integers(1, n, size=3))
-            if k >= kmin and i + j + k <= n - 1:
-                return i, j, k
+        # slice k with probability proportional to its (M - 1) M / 2 interior points
+        # (M = n - 1 - k), row j proportional to its M - j points, then i uniform
+        ks = np.arange(kmin, n - 2)
+        Ms = n - 1 - ks
+        k = int(rng.choice(ks, p=(Ms - 1) * Ms / ((Ms - 1) * Ms).sum()))
+        M = n - 1 - k
+        js = np.arange(1, M)
+        j = int(rng.choice(js, p=(M - js) / (M - js).sum()))
+        i = int(rng.integers(1, M - j + 1))
+        return i, j, k
 
     for _ in range(1200):
         out.append((int(rng.integers(nmacro)), rand_interior()))
