@@ -480,7 +480,7 @@ void sweep(hhg_ctx* c, int level, OpKind op, SweepArgs<T> a, double* norm2) {
     c->prof_ev[0].push_back(pi);
     c->prof_ev[1].push_back(ps);
     c->prof_launches[0] += L.dev.ntiles_lin > 0 ? L.dev.nmacro : 0;
-    c->prof_launches[1] += (L.dev.nface_items > 0) + (L.dev.nface_nodes > 0) + (L.dev.nev > 0) + (L.dev.ndir > 0);
+    c->prof_launches[1] += (L.dev.nface_nodes > 0) + (L.dev.nev > 0) + (L.dev.ndir > 0);
   }
   for (int q = 0; q < 4; ++q) {
     CK(cudaEventRecord(c->ev_join[q], c->aux[q]));

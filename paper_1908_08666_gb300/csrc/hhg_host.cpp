@@ -264,6 +264,15 @@ void macro_constants(const MacroGeom& G, int n, double c_eps, double c_div, Macr
       out.st.s[d][c][1] = A[2];
       out.st.s[d][c][2] = A[3];
     }
+    // The stencil is point-symmetric: the correction stencils of d and -d are equal
+    // (the ring pairs of -d are those of d through the neighbour i - d, swapped, and the
+    // block of the edge (i, i - d) is the transpose of that of (i - d, i)).  The kernels use
+    // s[d] for both directions.
+    if (d >= 7)
+      for (int c = 0; c < ring_count(d); ++c)
+        for (int r = 0; r < 3; ++r)
+          if (std::fabs(out.st.s[d][c][r] - out.st.s[d - 7][c][r]) > 1e-13 * (cmax + 1e-300))
+            THROW(HHG_ERR_STATE, "correction stencils of directions %d and %d differ", d - 7, d);
     if (d < 7) {
       out.st.S[d][0] = Sh[0];
       out.st.S[d][1] = Sh[4];
@@ -490,17 +499,41 @@ void build_level(hhg_ctx* c, int level) {
       items.push_back(it);
     }
   };
+  std::vector<int64_t> free_face;
   for (int64_t s = 0; s < nskel; ++s) {
     if (L->skel_dir[s])
       L->dir_nodes.push_back((int32_t)s);
     else if (L->skel_support[s] == 3)
-      add_face(s, L->face_nodes, L->face_items);
+      free_face.push_back(s);
     else
       L->ev_nodes.push_back((int32_t)s);
     if (L->skel_support[s] == 3)
       add_face(s, L->face_nodes_all, L->face_items_all);
     else
       L->ev_all.push_back((int32_t)s);
+  }
+  // free face nodes ordered by their incidences (macro and face type of each), so that the
+  // lanes of a warp of the face-row kernel take the same face types
+  {
+    auto face_type = [&](const SkelInc& I) {
+      return (I.i + I.j + I.k == n) ? 0 : (I.i == 0) ? 1 : (I.j == 0) ? 2 : 3;
+    };
+    auto key = [&](int64_t s) {
+      std::array<int64_t, 5> kk{};
+      const int b0 = L->skel_ptr[s], b1 = L->skel_ptr[s + 1];
+      for (int q = 0; q < 2; ++q) {
+        if (b0 + q < b1) {
+          kk[2 * q] = L->skel_inc[b0 + q].macro;
+          kk[2 * q + 1] = face_type(L->skel_inc[b0 + q]);
+        } else {
+          kk[2 * q] = -1;
+        }
+      }
+      kk[4] = s;
+      return kk;
+    };
+    std::sort(free_face.begin(), free_face.end(), [&](int64_t a, int64_t b) { return key(a) < key(b); });
+    for (int64_t s : free_face) add_face(s, L->face_nodes, L->face_items);
   }
   // group the face items by macro and face type so that the lanes of a warp share the
   // candidate set (the unrolled candidate loop then does not diverge)

@@ -96,8 +96,116 @@ __device__ __forceinline__ void slice_decode(int M, int t, int& j, int& i) {
   i = t - (u * (2 * M - u - 1)) / 2 + 1;
 }
 
-// GEN = 0: physical scaling with the patch mean (the default operator, flags folded
-// at compile time); GEN = 1: variant and khat rule from the run-time flags.
+// The scaled-stencil row of one macro-interior node (Lemma 2.1, eq. correctionterm3D) from
+// the coefficients kk[d] = k_{i+d}, k0 = k_i and the neighbour differences
+// dx/dy/dz[d] = x_{i+d} - x_i of its 14 stencil directions: (A x)_i = (ax, ay, az) and, with
+// DIAG, the point diagonal (dgx, dgy, dgz) = -sum_d khat_d diag(Shat_d).
+// GEN = 0: physical scaling with the patch mean (flags folded at compile time); GEN = 1:
+// variant and khat rule from the run-time flags.
+// The neighbour values come through an accessor nb: nb.k(d) = k_{i+d}, nb.dx(d) = x_{i+d} - x_i
+// (likewise dy, dz); the accessor decides where they are read from (registers or shared
+// memory) and the compiler when.
+template <typename T>
+struct Diff3 {
+  T x, y, z;
+};
+
+template <typename T>
+struct RegNeighbours {
+  const T (&kk)[NDIR];
+  const T (&x)[NDIR];
+  const T (&y)[NDIR];
+  const T (&z)[NDIR];
+  __device__ __forceinline__ T k(int d) const { return kk[d]; }
+  __device__ __forceinline__ Diff3<T> diff(int d) const { return {x[d], y[d], z[d]}; }
+  __device__ __forceinline__ void next_pair() {}
+};
+
+template <typename T, bool DIAG, int GEN, typename NB>
+__device__ __forceinline__ void interior_row(const MacroStencil<T>& st, const OpFlags& fl, NB& nb, T k0,
+                                             T& ax, T& ay, T& az, T& dgx, T& dgy, T& dgz) {
+  const bool physical = GEN ? fl.physical != 0 : true;
+  const bool khat_edge = GEN ? fl.khat_edge != 0 : false;
+  ax = 0;
+  ay = 0;
+  az = 0;
+  dgx = 0;
+  dgy = 0;
+  dgz = 0;
+  const T k0q = (T)0.25 * k0;
+#pragma unroll
+  for (int d = 0; d < 7; ++d) {
+    nb.next_pair();
+    const int e = d + 7;
+    const T wr = dir_red(d) ? (T)(1.0 / 12.0) : (T)0.125;
+    T rsp = 0, rsm = 0;
+    T wpx = 0, wpy = 0, wpz = 0, wmx = 0, wmy = 0, wmz = 0;
+    // the correction stencils of d and -d are equal, s[d + 7] = s[d] (checked on the host
+    // when they are built), so one set of constants serves the pair
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (c < ring_count(d)) {
+        const T ka = nb.k(ring_a(d, c)), kb = nb.k(ring_b(d, c));
+        const T la = nb.k(ring_a(e, c)), lb = nb.k(ring_b(e, c));
+        rsp += ka + kb;
+        rsm += la + lb;
+        if (physical) {
+          const T dp = ka - kb, dm = la - lb;
+          wpx = fma(dp, st.s[d][c][0], wpx);
+          wpy = fma(dp, st.s[d][c][1], wpy);
+          wpz = fma(dp, st.s[d][c][2], wpz);
+          wmx = fma(dm, st.s[d][c][0], wmx);
+          wmy = fma(dm, st.s[d][c][1], wmy);
+          wmz = fma(dm, st.s[d][c][2], wmz);
+        }
+      }
+    }
+    T khp, khm;
+    if (khat_edge) {
+      khp = (T)0.5 * (k0 + nb.k(d));
+      khm = (T)0.5 * (k0 + nb.k(e));
+    } else {
+      khp = fma(wr, rsp, fma((T)0.25, nb.k(d), k0q));
+      khm = fma(wr, rsm, fma((T)0.25, nb.k(e), k0q));
+    }
+    const Diff3<T> p = nb.diff(d), m = nb.diff(e);
+    const T vx = fma(khp, p.x, khm * m.x);
+    const T vy = fma(khp, p.y, khm * m.y);
+    const T vz = fma(khp, p.z, khm * m.z);
+    const T* S = st.S[d];
+    ax = fma(S[0], vx, ax);
+    ax = fma(S[3], vy, ax);
+    ax = fma(S[4], vz, ax);
+    ay = fma(S[3], vx, ay);
+    ay = fma(S[1], vy, ay);
+    ay = fma(S[5], vz, ay);
+    az = fma(S[4], vx, az);
+    az = fma(S[5], vy, az);
+    az = fma(S[2], vz, az);
+    if (physical) {
+      // w x delta for both directions
+      ax = fma(wpy, p.z, ax);
+      ax = fma(-wpz, p.y, ax);
+      ax = fma(wmy, m.z, ax);
+      ax = fma(-wmz, m.y, ax);
+      ay = fma(wpz, p.x, ay);
+      ay = fma(-wpx, p.z, ay);
+      ay = fma(wmz, m.x, ay);
+      ay = fma(-wmx, m.z, ay);
+      az = fma(wpx, p.y, az);
+      az = fma(-wpy, p.x, az);
+      az = fma(wmx, m.y, az);
+      az = fma(-wmy, m.x, az);
+    }
+    if (DIAG) {
+      const T ks = khp + khm;
+      dgx = fma(-ks, S[0], dgx);
+      dgy = fma(-ks, S[1], dgy);
+      dgz = fma(-ks, S[2], dgz);
+    }
+  }
+}
+
 // Stokes epilogue (apply / residual) for one copy: velocity rows (identity on
 // velocity-Dirichlet nodes) and the pressure row.
 template <typename T, int OP>
@@ -132,8 +240,6 @@ __global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, c
   const int M = n - 1 - k;
   const int t = (tile & 0xFFFFF) + threadIdx.x;
   double r2 = 0.0;
-  const bool physical = GEN ? fl.physical != 0 : true;
-  const bool khat_edge = GEN ? fl.khat_edge != 0 : false;
   if (t < (M - 1) * M / 2) {
     int j, i;
     slice_decode(M, t, j, i);
@@ -210,75 +316,10 @@ __global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, c
       dy[d] -= y0;
       dz[d] -= z0;
     }
-    const T k0q = (T)0.25 * k0;
-    T ax = 0, ay = 0, az = 0, dgx = 0, dgy = 0, dgz = 0;
-#pragma unroll
-    for (int d = 0; d < 7; ++d) {
-      const int e = d + 7;
-      const T wr = dir_red(d) ? (T)(1.0 / 12.0) : (T)0.125;
-      T rsp = 0, rsm = 0;
-      T wpx = 0, wpy = 0, wpz = 0, wmx = 0, wmy = 0, wmz = 0;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        if (c < ring_count(d)) {
-          const T ka = kk[ring_a(d, c)], kb = kk[ring_b(d, c)];
-          const T la = kk[ring_a(e, c)], lb = kk[ring_b(e, c)];
-          rsp += ka + kb;
-          rsm += la + lb;
-          if (physical) {
-            const T dp = ka - kb, dm = la - lb;
-            wpx = fma(dp, st.s[d][c][0], wpx);
-            wpy = fma(dp, st.s[d][c][1], wpy);
-            wpz = fma(dp, st.s[d][c][2], wpz);
-            wmx = fma(dm, st.s[e][c][0], wmx);
-            wmy = fma(dm, st.s[e][c][1], wmy);
-            wmz = fma(dm, st.s[e][c][2], wmz);
-          }
-        }
-      }
-      T khp, khm;
-      if (khat_edge) {
-        khp = (T)0.5 * (k0 + kk[d]);
-        khm = (T)0.5 * (k0 + kk[e]);
-      } else {
-        khp = fma(wr, rsp, fma((T)0.25, kk[d], k0q));
-        khm = fma(wr, rsm, fma((T)0.25, kk[e], k0q));
-      }
-      const T vx = fma(khp, dx[d], khm * dx[e]);
-      const T vy = fma(khp, dy[d], khm * dy[e]);
-      const T vz = fma(khp, dz[d], khm * dz[e]);
-      const T* S = st.S[d];
-      ax = fma(S[0], vx, ax);
-      ax = fma(S[3], vy, ax);
-      ax = fma(S[4], vz, ax);
-      ay = fma(S[3], vx, ay);
-      ay = fma(S[1], vy, ay);
-      ay = fma(S[5], vz, ay);
-      az = fma(S[4], vx, az);
-      az = fma(S[5], vy, az);
-      az = fma(S[2], vz, az);
-      if (physical) {
-        // w x delta for both directions
-        ax = fma(wpy, dz[d], ax);
-        ax = fma(-wpz, dy[d], ax);
-        ax = fma(wmy, dz[e], ax);
-        ax = fma(-wmz, dy[e], ax);
-        ay = fma(wpz, dx[d], ay);
-        ay = fma(-wpx, dz[d], ay);
-        ay = fma(wmz, dx[e], ay);
-        ay = fma(-wmx, dz[e], ay);
-        az = fma(wpx, dy[d], az);
-        az = fma(-wpy, dx[d], az);
-        az = fma(wmx, dy[e], az);
-        az = fma(-wmy, dx[e], az);
-      }
-      if (OP == OP_JACOBI || OP == OP_CHEBY || OP == OP_DIAG) {
-        const T ks = khp + khm;
-        dgx = fma(-ks, S[0], dgx);
-        dgy = fma(-ks, S[1], dgy);
-        dgz = fma(-ks, S[2], dgz);
-      }
-    }
+    T ax, ay, az, dgx, dgy, dgz;
+    RegNeighbours<T> nb{kk, dx, dy, dz};
+    interior_row<T, OP == OP_JACOBI || OP == OP_CHEBY || OP == OP_DIAG, GEN>(st, fl, nb, k0, ax, ay, az, dgx, dgy,
+                                                                             dgz);
     if constexpr (STK) {
       T yp = 0;
 #pragma unroll
@@ -631,6 +672,197 @@ __global__ void __launch_bounds__(32 * FACE_PARTS) k_face_items(const LevelDev L
     for (int q = 0; q < 6; ++q)
       atomicAdd(acc + q, (red[0][q][lane] + red[1][q][lane]) + (red[2][q][lane] + red[3][q][lane]));
   }
+}
+
+// ---------------------------------------------------------------------------
+// Free face-interior skeleton nodes, one thread per node (k_face_rows).  A node on a macro
+// face has one incidence per macro sharing the face (two on an interior face); in macro T
+// the node sits on face F of T's lattice (F = 0: i + j + k = n, 1: i = 0, 2: j = 0,
+// 3: k = 0), so the elements of T around it, the stencil directions that stay in T and
+// those that can end at a macro-interior node are fixed by F.  face_incidence<F> evaluates
+// T's part of the row with those sets fixed at compile time (the representative
+// face-interior point of each face type, on a lattice with 16 intervals, decides them);
+// only whether a neighbour is macro-interior (next to the face's edges it is not) is
+// decided at run time.  The symmetric interface rule of Sec. 2.2: pairs of skeleton nodes
+// by nodal integration a_h over T's elements, pairs with a macro-interior neighbour by T's
+// scaled block; the practical rule: a_h for every pair.  Rows are in difference form, so
+// the centre block is minus the sum of the off-diagonal blocks.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void face_rep(int F, int& i, int& j, int& k) {
+  i = F == 1 ? 0 : 5;
+  j = F == 2 ? 0 : 5;
+  k = F == 3 ? 0 : (F == 0 ? 6 : 5);
+}
+// direction d stays in the macro's closed lattice from a face-interior point of face F
+__device__ __forceinline__ bool face_dir_valid(int F, int d) {
+  int i, j, k;
+  face_rep(F, i, j, k);
+  return lattice_inside(16, i + dir_di(d), j + dir_dj(d), k + dir_dk(d));
+}
+// direction d can end at a macro-interior point
+__device__ __forceinline__ bool face_dir_inward(int F, int d) {
+  int i, j, k;
+  face_rep(F, i, j, k);
+  return lattice_interior(16, i + dir_di(d), j + dir_dj(d), k + dir_dk(d));
+}
+// candidate element (bit 4 p + av: Kuhn permutation p, the point at vertex av) lies in the macro
+__device__ __forceinline__ bool face_cand_inside(int F, int bit) {
+  int i, j, k;
+  face_rep(F, i, j, k);
+  const int p = bit >> 2, av = bit & 3;
+  int a0, a1, a2;
+  kuhn_perm(p, a0, a1, a2);
+  const int X = i + j + k, Y = j + k, Z = k;
+  bool ok = true;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int VX = X + ((v >= 1 && a0 == 0) + (v >= 2 && a1 == 0) + (v >= 3 && a2 == 0)) -
+                   ((av >= 1 && a0 == 0) + (av >= 2 && a1 == 0) + (av >= 3 && a2 == 0));
+    const int VY = Y + ((v >= 1 && a0 == 1) + (v >= 2 && a1 == 1) + (v >= 3 && a2 == 1)) -
+                   ((av >= 1 && a0 == 1) + (av >= 2 && a1 == 1) + (av >= 3 && a2 == 1));
+    const int VZ = Z + ((v >= 1 && a0 == 2) + (v >= 2 && a1 == 2) + (v >= 3 && a2 == 2)) -
+                   ((av >= 1 && a0 == 2) + (av >= 2 && a1 == 2) + (av >= 3 && a2 == 2));
+    ok = ok && kuhn_inside(16, VX, VY, VZ);
+  }
+  return ok;
+}
+
+template <typename T, int F, bool DIAG>
+__device__ __forceinline__ void face_incidence(const MacroConsts<T>& C, const T* __restrict__ px,
+                                               const T* __restrict__ pk, int64_t E, int n, int i, int j, int k,
+                                               const OpFlags& fl, T x0, T y0, T z0, T& ax, T& ay, T& az, T& dgx,
+                                               T& dgy, T& dgz) {
+  int nb[NDIR];
+  lattice_neighbours(n, i, j, k, nb);
+  const T k0 = pk[lattice_index32(n, i, j, k)];
+  T kv[NDIR], dx[NDIR], dy[NDIR], dz[NDIR];
+  bool in[NDIR];
+#pragma unroll
+  for (int d = 0; d < NDIR; ++d) {
+    kv[d] = dx[d] = dy[d] = dz[d] = (T)0;
+    in[d] = false;
+    if (face_dir_valid(F, d)) {
+      const int q = nb[d];
+      kv[d] = pk[q];
+      dx[d] = px[q] - x0;
+      dy[d] = px[q + E] - y0;
+      dz[d] = px[q + 2 * E] - z0;
+      in[d] = face_dir_inward(F, d) && lattice_interior(n, i + dir_di(d), j + dir_dj(d), k + dir_dk(d));
+    }
+  }
+  // nodal-integration terms over the macro's elements around the point
+#pragma unroll
+  for (int bit = 0; bit < 24; ++bit) {
+    if (!face_cand_inside(F, bit)) continue;
+    const int p = bit >> 2, av = bit & 3;
+    int a0, a1, a2;
+    kuhn_perm(p, a0, a1, a2);
+    int dv[4];
+    T ks = k0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int oX = ((v >= 1 && a0 == 0) + (v >= 2 && a1 == 0) + (v >= 3 && a2 == 0)) -
+                     ((av >= 1 && a0 == 0) + (av >= 2 && a1 == 0) + (av >= 3 && a2 == 0));
+      const int oY = ((v >= 1 && a0 == 1) + (v >= 2 && a1 == 1) + (v >= 3 && a2 == 1)) -
+                     ((av >= 1 && a0 == 1) + (av >= 2 && a1 == 1) + (av >= 3 && a2 == 1));
+      const int oZ = ((v >= 1 && a0 == 2) + (v >= 2 && a1 == 2) + (v >= 3 && a2 == 2)) -
+                     ((av >= 1 && a0 == 2) + (av >= 2 && a1 == 2) + (av >= 3 && a2 == 2));
+      dv[v] = v == av ? -1 : dir_of_offset(oX - oY, oY - oZ, oZ);
+      if (v != av) ks += kv[dv[v]];
+    }
+    const T kb = (T)0.25 * ks;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      if (v == av) continue;
+      const int d = dv[v];
+      if (!fl.practical && in[d]) continue;
+      const T* K = C.ke[p][av][v];
+      ax = fma(kb, fma(K[0], dx[d], fma(K[1], dy[d], K[2] * dz[d])), ax);
+      ay = fma(kb, fma(K[3], dx[d], fma(K[4], dy[d], K[5] * dz[d])), ay);
+      az = fma(kb, fma(K[6], dx[d], fma(K[7], dy[d], K[8] * dz[d])), az);
+      if (DIAG) {
+        dgx = fma(-kb, K[0], dgx);
+        dgy = fma(-kb, K[4], dgy);
+        dgz = fma(-kb, K[8], dgz);
+      }
+    }
+  }
+  if (fl.practical) return;
+  // scaled blocks of the directions that end at a macro-interior point (their ring nodes
+  // are neighbours of that point, so they lie in the macro)
+#pragma unroll
+  for (int d = 0; d < NDIR; ++d) {
+    if (!face_dir_inward(F, d)) continue;
+    if (!in[d]) continue;
+    T rs = 0, wx = 0, wy = 0, wz = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (c >= ring_count(d)) continue;
+      const T ka = kv[ring_a(d, c)], kb = kv[ring_b(d, c)];
+      rs += ka + kb;
+      const T dk = ka - kb;
+      wx = fma(dk, C.st.s[d][c][0], wx);
+      wy = fma(dk, C.st.s[d][c][1], wy);
+      wz = fma(dk, C.st.s[d][c][2], wz);
+    }
+    const T kh = fl.khat_edge ? (T)0.5 * (k0 + kv[d])
+                              : fma((dir_red(d) ? (T)(1.0 / 12.0) : (T)0.125), rs, (T)0.25 * (k0 + kv[d]));
+    const T* S = C.st.S[d < 7 ? d : d - 7];
+    const T vx = kh * dx[d], vy = kh * dy[d], vz = kh * dz[d];
+    ax = fma(S[0], vx, fma(S[3], vy, fma(S[4], vz, ax)));
+    ay = fma(S[3], vx, fma(S[1], vy, fma(S[5], vz, ay)));
+    az = fma(S[4], vx, fma(S[5], vy, fma(S[2], vz, az)));
+    if (fl.physical) {
+      ax = fma(wy, dz[d], fma(-wz, dy[d], ax));
+      ay = fma(wz, dx[d], fma(-wx, dz[d], ay));
+      az = fma(wx, dy[d], fma(-wy, dx[d], az));
+    }
+    if (DIAG) {
+      dgx = fma(-kh, S[0], dgx);
+      dgy = fma(-kh, S[1], dgy);
+      dgz = fma(-kh, S[2], dgz);
+    }
+  }
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(128) k_face_rows(const LevelDev L, const MacroConsts<T>* __restrict__ mc,
+                                                    const OpFlags fl, const SweepArgs<T> a) {
+  constexpr bool DIAG = OP == OP_JACOBI || OP == OP_CHEBY || OP == OP_DIAG;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double r2 = 0.0;
+  if (t < L.nface_nodes) {
+    const int n = L.n;
+    const int64_t E = L.entries;
+    const int s = L.face_nodes[t];
+    const int b0 = L.skel_ptr[s], b1 = L.skel_ptr[s + 1];
+    const SkelInc I0 = L.skel_inc[b0];
+    const int64_t e0 = (int64_t)I0.macro * L.nt + lattice_index32(n, I0.i, I0.j, I0.k);
+    const T x0 = a.x[e0], y0 = a.x[e0 + E], z0 = a.x[e0 + 2 * E];
+    T ax = 0, ay = 0, az = 0, dgx = 0, dgy = 0, dgz = 0;
+    for (int q = b0; q < b1; ++q) {
+      const SkelInc I = L.skel_inc[q];
+      const int64_t base = (int64_t)I.macro * L.nt;
+      const T* px = a.x + base;
+      const T* pk = a.k + base;
+      const MacroConsts<T>& C = mc[I.macro];
+      const int f = (I.i + I.j + I.k == n) ? 0 : (I.i == 0) ? 1 : (I.j == 0) ? 2 : 3;
+      switch (f) {
+        case 0: face_incidence<T, 0, DIAG>(C, px, pk, E, n, I.i, I.j, I.k, fl, x0, y0, z0, ax, ay, az, dgx, dgy, dgz); break;
+        case 1: face_incidence<T, 1, DIAG>(C, px, pk, E, n, I.i, I.j, I.k, fl, x0, y0, z0, ax, ay, az, dgx, dgy, dgz); break;
+        case 2: face_incidence<T, 2, DIAG>(C, px, pk, E, n, I.i, I.j, I.k, fl, x0, y0, z0, ax, ay, az, dgx, dgy, dgz); break;
+        default: face_incidence<T, 3, DIAG>(C, px, pk, E, n, I.i, I.j, I.k, fl, x0, y0, z0, ax, ay, az, dgx, dgy, dgz); break;
+      }
+    }
+    for (int q = b0; q < b1; ++q) {
+      const SkelInc I = L.skel_inc[q];
+      const int64_t e = (int64_t)I.macro * L.nt + lattice_index32(n, I.i, I.j, I.k);
+      double tmp = 0.0;
+      epilogue<T, OP>(a, e, E, ax, ay, az, dgx, dgy, dgz, x0, y0, z0, tmp);
+      if (q == b0) r2 = tmp;
+    }
+  }
+  if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
 }
 
 // Face nodes: finish the row from the accumulator (which is reset to zero) and
@@ -990,20 +1222,16 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
     used += L.ntiles_lin;
   }
   if (parts & 2) {
-    if (L.nface_items > 0) {
-      const int nb = (L.nface_items + 31) / 32;
-      k_face_items<T><<<nb, 32 * FACE_PARTS, 0, s>>>(L, mc_dev, fl, a.x, a.k);
-    }
     if (L.nface_nodes > 0) {
       const int nb = (L.nface_nodes + 127) / 128;
       SweepArgs<T> am = a;
       if (a.partial) am.partial = a.partial + used;
       switch (op) {
-        case OP_APPLY: k_face_finalize<T, OP_APPLY><<<nb, 128, 0, s>>>(L, am); break;
-        case OP_RESID: k_face_finalize<T, OP_RESID><<<nb, 128, 0, s>>>(L, am); break;
-        case OP_JACOBI: k_face_finalize<T, OP_JACOBI><<<nb, 128, 0, s>>>(L, am); break;
-        case OP_CHEBY: k_face_finalize<T, OP_CHEBY><<<nb, 128, 0, s>>>(L, am); break;
-        case OP_DIAG: k_face_finalize<T, OP_DIAG><<<nb, 128, 0, s>>>(L, am); break;
+        case OP_APPLY: k_face_rows<T, OP_APPLY><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
+        case OP_RESID: k_face_rows<T, OP_RESID><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
+        case OP_JACOBI: k_face_rows<T, OP_JACOBI><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
+        case OP_CHEBY: k_face_rows<T, OP_CHEBY><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
+        case OP_DIAG: k_face_rows<T, OP_DIAG><<<nb, 128, 0, s>>>(L, mc_dev, fl, am); break;
       }
       used += nb;
     }
