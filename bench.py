@@ -34,8 +34,6 @@ import numpy as np  # noqa: E402
 
 LEVEL = 7
 NU = 0.3
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
 # algorithmic cost of one macro-interior node of the FP32 apply
 BYTES_PER_NODE_F32 = 28  # read x (12 B) and k (4 B), write y (12 B)
 FLOPS_PER_NODE = 723     # FMA = 2 flops, as the kernel evaluates the scaled stencil
@@ -46,7 +44,7 @@ WORKLOAD = "elasticity, 6-macro Kuhn unit cube, level 7 (129^3 nodes), lognormal
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--level", type=int, default=LEVEL)
@@ -143,6 +141,31 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def fp32_peak(B, torch, h, stream, reps=5):
+    """FP32 FMA issue rate measured by the library's probe kernel (hhg_fp32_fma_probe: 8
+    independent FMA chains per thread on SMs x 8 blocks of 256 threads), timed with CUDA events on
+    the context's stream: the best of `reps` launches of the plain (fma.rn.f32) and the packed
+    two-lane (fma.rn.f32x2) form.  Returns the higher rate, both rates and the SM count."""
+    out = torch.zeros(1, device="cuda")
+    res = {}
+    sms = None
+    for packed in (0, 1):
+        iters = 100000
+        B.hhg_fp32_fma_probe(h, packed, iters, out)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fl, sms = B.hhg_fp32_fma_probe(h, packed, iters, out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            r = fl / (a.elapsed_time(b) * 1e-3) / 1e12
+            best = r if best is None else max(best, r)
+        res["fma_f32x2" if packed else "fma_f32"] = round(best, 2)
+    return max(res.values()), res, sms
+
+
 # ---------------------------------------------------------------------------- workload
 
 
@@ -188,79 +211,135 @@ def _grids(level):
 
 _BW = {}
 
+# The CPU baseline applies the oracle's assembled operator on a level the oracle can assemble
+# in seconds (its element-record assembly needs about 2 GB at level 5 and grows 8x per level)
+BASELINE_LEVEL = 5
 
-def _baseline_init(level):
-    """Worker set-up of the CPU baseline (before timing): mesh, fields, constants."""
+
+def _baseline_operator(level, workload_level):
+    """The oracle's FP64 physical-scaling operator (scipy CSR, Dirichlet identity rows) of the
+    benchmark workload on the 6-macro cube at `level`: lognormal E of the workload's grid
+    (seed 2, correlation length 0.1), nu = 0.3; x from the workload's uniform field (seed 3)."""
     import hhg_inputs as hi
-    from oracle import fem, mesh
+    from oracle import fem, mesh, operators as op
 
     xyz, tets = hi.kuhn_cube(1)
-    kgrid, xgrid = _grids(level)
-    _BW.update(level=level, mm=mesh.MacroMesh.build(xyz, tets), kgrid=kgrid, xgrid=xgrid,
-               consts=fem.elasticity_coefficients(NU))
+    lv = mesh.build_level(mesh.MacroMesh.build(xyz, tets), level)
+    kgrid, xgrid = _grids(workload_level)
+    k = hi.sample_grid(kgrid[..., None], lv.coords)[:, 0]
+    x = hi.sample_grid(xgrid, lv.coords)
+    ce, cd = fem.elasticity_coefficients(NU)
+    K = fem.element_stiffness(lv.coords[lv.elems], ce, cd)
+    A = op.with_dirichlet_rows(op.scaled_operator(lv, K, k), lv.dirichlet)
+    return A.tocsr(), np.ascontiguousarray(x.reshape(-1)), lv
 
 
-def _baseline_rows(job):
-    """Random macro-interior rows of the workload by the FP64 single-row oracle for about
-    budget_s seconds; returns (rows, seconds)."""
-    import hhg_inputs as hi
-    from oracle import rows
+def _baseline_worker_init(path):
+    d = np.load(path, allow_pickle=True)
+    _BW.update(blocks=list(d["blocks"]), x=d["x"])
 
-    budget_s, seed = job
-    level = _BW["level"]
-    N = 1 << level
-    kgrid, xgrid = _BW["kgrid"], _BW["xgrid"]
-    kf = lambda c: hi.sample_grid(kgrid[..., None], c)[:, 0]
-    xf = lambda c: hi.sample_grid(xgrid, c)
-    ce, cd = _BW["consts"]
-    rng = np.random.default_rng(seed)
-    done = 0
-    t0 = time.perf_counter()
-    while time.perf_counter() - t0 < budget_s or done < 2:
-        m = int(rng.integers(0, 6))
-        while True:
-            i, j, k = (int(v) for v in rng.integers(1, N, size=3))
-            if i + j + k <= N - 1:
-                break
-        rows.row(_BW["mm"], level, m, (i, j, k), kf, xf, ce, cd)
-        done += 1
-    return done, time.perf_counter() - t0
+
+def _baseline_apply(job):
+    """reps applications of row block q of the oracle's operator (y_q = A_q x)."""
+    q, reps = job
+    A, x = _BW["blocks"][q], _BW["x"]
+    y = None
+    for _ in range(reps):
+        y = A @ x
+    return float(y[0]) if y is not None and len(y) else 0.0
 
 
 class CpuBaseline:
-    """The FP64 oracle (single-row definition by local refinement) on every host core: one
-    spawned process per core (spawn, not fork: the parent holds a CUDA context), each
-    evaluating random rows of the same workload; throughput = all rows / the longest
-    worker's time."""
+    """The oracle's FP64 operator apply (its assembled scipy CSR matrix, y = A x) on every host
+    core: the rows are split into one block per core, each block applied by its own spawned
+    process (spawn, not fork: the parent holds a CUDA context); throughput = 3 x nodes x reps /
+    the wall-clock time of the whole pool round (after an untimed warm-up round)."""
 
-    def __init__(self, level, cores=None):
+    def __init__(self, level=BASELINE_LEVEL, workload_level=7, cores=None):
         import multiprocessing as mp
+        import tempfile
 
         self.level = level
-        self.cores = cores or os.cpu_count() or 1
-        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_baseline_init, initargs=(level,))
+        self.cores = cores or len(os.sched_getaffinity(0))
+        t0 = time.perf_counter()
+        A, x, lv = _baseline_operator(level, workload_level)
+        self.setup_s = time.perf_counter() - t0
+        self.nodes = lv.num_nodes
+        self.nfree = int((~lv.dirichlet).sum())
+        rows = A.shape[0]
+        cuts = np.linspace(0, rows // 3, self.cores + 1).astype(np.int64) * 3
+        blocks = np.empty(self.cores, dtype=object)
+        for q in range(self.cores):
+            blocks[q] = A[cuts[q]:cuts[q + 1]]
+        self.tmp = tempfile.NamedTemporaryFile(suffix=".npz", delete=False)
+        self.tmp.close()
+        np.savez(self.tmp.name, blocks=blocks, x=x)
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_baseline_worker_init,
+                                                 initargs=(self.tmp.name,))
+        t0 = time.perf_counter()
+        self.pool.map(_baseline_apply, [(q, 1) for q in range(self.cores)])  # every worker initialised
+        self.round_s = max(1e-4, time.perf_counter() - t0)
 
-    def measure(self, budget_s, seed):
-        res = self.pool.map(_baseline_rows, [(budget_s, seed * 1009 + w) for w in range(self.cores)])
-        done = sum(r[0] for r in res)
-        dt = max(r[1] for r in res)
-        return {"value": 3.0 * done / dt / 1e9, "unit": "GDoF/s", "cores": self.cores, "kind": "oracle",
-                "sample": "%d random macro-interior rows of the level-%d cube operator, FP64 single-row oracle "
-                          "(local Bey refinement + definition of the scaled blocks), %.1f s on %d host cores "
-                          "(one process each)" % (done, self.level, dt, self.cores)}
+    def _round(self, reps):
+        t0 = time.perf_counter()
+        self.pool.map(_baseline_apply, [(q, reps) for q in range(self.cores)])
+        return time.perf_counter() - t0
+
+    def measure(self, budget_s):
+        reps = 1
+        while True:  # calibrate: a round long enough that the pool's dispatch cost is negligible
+            dt = self._round(reps)
+            if dt > 0.2 * budget_s or reps > 1 << 20:
+                break
+            reps *= 4
+        reps = max(1, int(reps * budget_s / dt))
+        dt = self._round(reps)
+        return {"value": 3.0 * self.nodes * reps / dt / 1e9, "unit": "GDoF/s", "cores": self.cores, "kind": "oracle",
+                "free_dof_value": 3.0 * self.nfree * reps / dt / 1e9,
+                "sample": "y = A x by the oracle's assembled FP64 physical-scaling operator (scipy CSR, built "
+                          "once in %.1f s outside the timing) of the same workload on the 6-macro cube at level "
+                          "%d (%d nodes; the level-%d lognormal E and x sampled at its nodes), rows split over "
+                          "%d spawned processes, %d applications each, %.2f s wall clock for the whole pool"
+                          % (self.setup_s, self.level, self.nodes, 7, self.cores, reps, dt)}
 
     def close(self):
         self.pool.close()
         self.pool.join()
+        os.unlink(self.tmp.name)
 
 
-def cpu_baseline(level, budget_s=15.0, seed=0):
-    """The oracle timed on this host's cores on a bounded random sample of rows."""
-    b = CpuBaseline(level)
+def c1_pcg_baseline():
+    """The oracle's Jacobi-preconditioned CG (textbook, Saad Alg. 9.1) on the single unit macro
+    tetrahedron at level 5 (6545 nodes), E = 1 + 0.5 sin sin sin, nu = 0.3, f ~ U[-1, 1] (seed 1),
+    to a relative residual of 1e-10; one host core."""
+    import hhg_inputs as hi
+    from oracle import fem, mesh, operators as op, solvers as S
+
+    xyz, tets = hi.unit_tet()
+    lv = mesh.build_level(mesh.MacroMesh.build(xyz, tets), 5)
+    ce, cd = fem.elasticity_coefficients(NU)
+    K = fem.element_stiffness(lv.coords[lv.elems], ce, cd)
+    A = op.with_dirichlet_rows(op.scaled_operator(lv, K, hi.young_sine(lv.coords)), lv.dirichlet)
+    f = hi.node_noise(lv.coords, seed=1)
+    f[lv.dirichlet] = 0.0
+    D = S.point_diagonal(A, lv.dirichlet)
+    t0 = time.perf_counter()
+    x, it = S.pcg(A, lv.dirichlet, f, np.zeros_like(f), lambda r: r / D, 1e-10, 5000)
+    dt = time.perf_counter() - t0
+    r = S.residual(A, lv.dirichlet, f, x)
+    return {"seconds": round(dt, 4), "iterations": int(it), "nodes": lv.num_nodes, "cores": 1,
+            "rel_residual": float(np.sqrt((r**2).sum() / (f[~lv.dirichlet]**2).sum()))}
+
+
+def cpu_baseline(budget_s=12.0):
+    """The oracle timed on this host's cores: the all-core operator apply, plus the C1 solve."""
+    b = CpuBaseline()
     try:
-        return b.measure(budget_s, seed)
+        out = b.measure(budget_s)
     finally:
         b.close()
+    out["c1_jacobi_pcg"] = c1_pcg_baseline()
+    return out
 
 
 def solve_times(B, torch, h, level, coords_u):
@@ -816,6 +895,7 @@ def run_ours(args):
     for _ in range(max(3, args.warmup)):
         B.hhg_apply(h, level, B.F32, x, y)
     torch.cuda.synchronize()
+    alu_peak, alu_probe, sm_count = fp32_peak(B, torch, h, stream)
 
     clocks = Clocks(dev)
     clocks.start()
@@ -837,6 +917,7 @@ def run_ours(args):
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     total_ms = max_over_ranks(float(sum(step_ms)), world)
+    median_ms = statistics.median(step_ms)
     # end-to-end: host buffers through the C ABI (H2D copy, apply, D2H copy, wait)
     xh = torch.empty(3 * E, dtype=torch.float32, pin_memory=True)
     xh.copy_(x.cpu())
@@ -876,6 +957,24 @@ def run_ours(args):
             "rel_error_vs_fp32_coefficient": float((yb.double() - y.double()).norm() / y.double().norm()),
             "max_abs_error_over_max_abs": float((yb - y).abs().max() / y.abs().max())}
     B.hhg_set_coefficient(h, kl, B.F64)
+    # the paper's arithmetic: the same apply in FP64 (x widened from the FP32 input)
+    x64 = x.double()
+    y64 = torch.empty_like(x64)
+    for _ in range(3):
+        B.hhg_apply(h, level, B.F64, x64, y64)
+    torch.cuda.synchronize()
+    ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+    for s_, (a0, a1) in enumerate(ev64):
+        flush.fill_(float(s_))
+        a0.record(stream)
+        B.hhg_apply(h, level, B.F64, x64, y64)
+        a1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = statistics.median(a0.elapsed_time(a1) for a0, a1 in ev64)
+    fp64 = {"ms_per_step": round(ms64, 5), "value": round(dofs / (ms64 * 1e-3) / 1e9, 3), "unit": "GDoF/s",
+            "free_dof_value": round(3 * F / (ms64 * 1e-3) / 1e9, 3), "steps": 20, "statistic": "median",
+            "rel_difference_fp32_vs_fp64": float((y.double() - y64).norm() / y64.norm())}
+    del x64, y64
     # the paper's comparison method: nodal integration a_h on the fly (same coefficient, same x)
     B.hhg_set_problem(h, nu=NU, variant=B.NODAL)
     yn = torch.empty_like(y)
@@ -913,8 +1012,6 @@ def run_ours(args):
     bytes_per_launch = interior_per_macro * BYTES_PER_NODE_F32
     flops_per_launch = interior_per_macro * FLOPS_PER_NODE
     hbm_achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
-    sm_mhz = clk.get("sm_mhz") or 2070.0
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     alu_achieved = flops_per_launch / (launch_ms * 1e-3) / 1e12
     traffic = profiled_traffic()
     hbm_frac = hbm_achieved / hbm_peak
@@ -922,8 +1019,9 @@ def run_ours(args):
     if alu_frac >= hbm_frac:
         roof = {"bound": "alu", "achieved": round(alu_achieved, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
                 "frac": round(alu_frac, 4),
-                "peak_source": "FP32 FMA lanes: %d SMs x %d lanes x 2 flop x median SM clock %.0f MHz"
-                               % (SM_COUNT, FP32_LANES_PER_SM, sm_mhz)}
+                "peak_source": "measured in this run: FP32 FMA probe kernel (hhg_fp32_fma_probe) on %d SMs, "
+                               "best of fma.rn.f32 %.1f / fma.rn.f32x2 %.1f TFLOP/s" %
+                               (sm_count, alu_probe["fma_f32"], alu_probe["fma_f32x2"])}
     else:
         roof = {"bound": "hbm", "achieved": round(hbm_achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(hbm_frac, 4), "peak_source": peak_kind}
@@ -934,7 +1032,9 @@ def run_ours(args):
                  "launch_ms": round(launch_ms, 5),
                  "hbm": {"achieved_gbs": round(hbm_achieved, 1), "peak_gbs": hbm_peak, "frac": round(hbm_frac, 4),
                          "peak_source": peak_kind},
+                 "sm_count": sm_count,
                  "alu": {"achieved_tflops": round(alu_achieved, 3), "peak_tflops": round(alu_peak, 2),
+                         "probe_tflops": alu_probe,
                          "frac": round(alu_frac, 4)},
                  "skeleton_ms_per_step": round(prof_ms[1] / args.steps, 5),
                  # the paper's unit (Sec. 4.2 benchmark: 222 ns per node update and CPU rank)
@@ -947,13 +1047,16 @@ def run_ours(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": round(ms_per_step, 5),
+        "ms_per_step_median": round(median_ms, 5),
+        "free_dof_value": round(job_value(3 * F, ms_per_step, world), 3),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "level": level, "macros": int(nmacro), "nodes": int(U),
-                   "dofs": int(dofs), "entries": int(E), "l2": "flushed before every step (256 MB write)",
+                   "dofs": int(dofs), "free_dofs": int(3 * F), "entries": int(E),
+                   "l2": "flushed before every step (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roof,
         "e2e": {"value": round(world * dofs / e2e_s / 1e9, 3), "unit": "GDoF/s",
@@ -964,13 +1067,14 @@ def run_ours(args):
         "stokes": stokes,
         "carreau": carreau,
         "bf16_coefficient": bf16,
+        "fp64_apply": fp64,
         "nodal_integration": nodal,
         "learned": learned,
         "learned_stokes": learned_stokes,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(level)
+        out["cpu_baseline"] = cpu_baseline()
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
@@ -984,16 +1088,15 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    level = args.level
-    base = CpuBaseline(level)
+    base = CpuBaseline()
     try:
         for _ in range(max(0, args.warmup)):
-            base.measure(0.5, 99)
-        per_step = max(1.0, min(8.0, 120.0 / max(1, args.steps)))
-        vals = [base.measure(per_step, s)["value"] for s in range(args.steps)]
+            base.measure(0.2)
+        per_step = max(0.5, min(6.0, 100.0 / max(1, args.steps)))
+        meas = [base.measure(per_step) for _ in range(args.steps)]
     finally:
         base.close()
-    value = statistics.mean(vals)
+    value = statistics.mean(m["value"] for m in meas)
     out = {
         "impl": "reference",
         "metric": METRIC,
@@ -1008,10 +1111,10 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD.replace("FP32", "FP64 oracle"), "level": level},
+        "config": {"workload": WORKLOAD.replace("FP32", "FP64 oracle"), "level": args.level,
+                   "sample_level": base.level},
         "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": base.cores, "kind": "oracle",
-                         "sample": "each step: random macro-interior rows for %.1f s via the FP64 single-row "
-                                   "oracle, one process per host core" % per_step},
+                         "sample": "each step: " + meas[-1]["sample"]},
         "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)

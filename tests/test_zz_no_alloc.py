@@ -20,13 +20,31 @@ from hhg_gpu import Ctx
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("builder,level", [(hi.kuhn_cube, 5), (hi.skewed_pair, 4)], ids=["cube_l5", "skewed_l4"])
-def test_residual_noalloc_matches_residual(builder, level):
+CASES = [
+    ("cube_l5", hi.kuhn_cube, 5, {}, False),
+    ("skewed_l4", hi.skewed_pair, 4, {}, False),
+    ("cube_l4_unphysical", hi.kuhn_cube, 4, {"variant": B.UNPHYSICAL}, False),
+    ("cube_l4_khat_edge", hi.kuhn_cube, 4, {"khat": B.KHAT_EDGE}, False),
+    ("cube_l4_practical", hi.kuhn_cube, 4, {"iface": B.IFACE_PRACTICAL}, False),
+    ("cube_l4_bf16_coefficient", hi.kuhn_cube, 4, {}, True),
+]
+
+
+@pytest.mark.parametrize("name,builder,level,problem,bf16", CASES, ids=[c[0] for c in CASES])
+def test_residual_noalloc_matches_residual(name, builder, level, problem, bf16):
+    """Every operator variant hhg_set_problem offers to this entry point (the no-alloc path
+    takes other kernels for the face nodes and, with a BF16 coefficient, reads its widened
+    values), two calls in a row, FP64 and FP32."""
     xyz, tets = builder()
-    ctx = Ctx(xyz, tets, level, dict(nu=0.3))
+    ctx = Ctx(xyz, tets, level, dict(nu=0.3, **problem))
     try:
         t = ctx.torch
-        ctx.set_k(1.0 + 0.5 * np.cos(3.0 * ctx.coords_u).prod(axis=1))
+        k = 1.0 + 0.5 * np.cos(3.0 * ctx.coords_u).prod(axis=1)
+        if bf16:
+            kl = ctx.to_lib(k, t.float32, 1).to(t.bfloat16)
+            B.hhg_set_coefficient(ctx.h, kl.view(t.int16), B.BF16)
+        else:
+            ctx.set_k(k)
         for dt, tdt, tol in ((B.F64, t.float64, 1e-12), (B.F32, t.float32, 64 * 2.0**-24)):
             for call in range(2):  # two calls in a row: the shared scratch keeps the last call's contents
                 x = ctx.to_lib(hi.node_noise(ctx.coords_u, seed=20 + call), tdt, 3)
