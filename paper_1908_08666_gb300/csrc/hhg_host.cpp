@@ -340,6 +340,13 @@ void build_level(hhg_ctx* c, int level) {
   for (int k = 0; k <= n; ++k)
     for (int j0 = 0; j0 <= n - k; j0 += TILE_J)
       for (int i0 = 0; i0 <= n - k - j0; i0 += TILE_I) L->tiles_all.push_back((k << 20) | (j0 << 10) | i0);
+  // pairs of neighbouring interior points (i, i + 1) of slice k, row by row, in chunks of
+  // INTERIOR_BLOCK: floor(M^2 / 4) pairs per slice (M = n - 1 - k)
+  for (int k = 1; k <= n - 3; ++k) {
+    const int M = n - 1 - k;
+    const int count = M * M / 4;
+    for (int start = 0; start < count; start += INTERIOR_BLOCK) L->tiles_pair.push_back((k << 20) | start);
+  }
   // interior points of slice k, enumerated row by row (j = 1..M-1, i = 1..M-j, M = n-1-k),
   // in chunks of INTERIOR_BLOCK
   for (int k = 1; k <= n - 3; ++k) {
@@ -615,6 +622,7 @@ void upload_level(hhg_ctx* c, LevelHost& L) {
   upload(L.d_tiles_int, L.tiles_int);
   upload(L.d_tiles_all, L.tiles_all);
   upload(L.d_tiles_lin, L.tiles_lin);
+  upload(L.d_tiles_pair, L.tiles_pair);
   upload(L.d_skel_ptr, L.skel_ptr);
   upload(L.d_skel_inc, L.skel_inc);
   upload(L.d_skel_dir, L.skel_dir);
@@ -666,6 +674,8 @@ void upload_level(hhg_ctx* c, LevelHost& L) {
   D.tiles_all = L.d_tiles_all.as<int32_t>();
   D.ntiles_lin = (int32_t)L.tiles_lin.size();
   D.tiles_lin = L.d_tiles_lin.as<int32_t>();
+  D.ntiles_pair = (int32_t)L.tiles_pair.size();
+  D.tiles_pair = L.d_tiles_pair.as<int32_t>();
   D.nskel = (int32_t)L.skel_dir.size();
   D.skel_ptr = L.d_skel_ptr.as<int32_t>();
   D.skel_inc = L.d_skel_inc.as<SkelInc>();

@@ -189,6 +189,8 @@ struct LevelDev {
   int32_t ntiles_all;  // tiles over all lattice points
   int32_t ntiles_lin;  // 128-node chunks of the interior points of each slice: (k << 20) | start
   const int32_t* tiles_lin;
+  int32_t ntiles_pair;  // 128-pair chunks of the point pairs of each slice (FP32 sweeps): (k << 20) | start
+  const int32_t* tiles_pair;
   const int32_t* tiles_int;  // packed (k << 20) | (j0 << 10) | i0
   const int32_t* tiles_all;
   int32_t nskel;

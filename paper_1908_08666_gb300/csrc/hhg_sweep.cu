@@ -121,8 +121,32 @@ struct RegNeighbours {
   __device__ __forceinline__ void next_pair() {}
 };
 
-template <typename T, bool DIAG, int GEN, typename NB>
-__device__ __forceinline__ void interior_row(const MacroStencil<T>& st, const OpFlags& fl, NB& nb, T k0,
+// Packed FP32 arithmetic (the two-point kernel below) has no negated operands: differences and
+// negations go through a packed subtraction.  For scalar types both are the plain forms (the
+// negation folds into the FMA).
+struct P2;
+template <typename T>
+struct Packed {
+  static constexpr bool value = false;
+};
+template <>
+struct Packed<P2> {
+  static constexpr bool value = true;
+};
+template <typename T>
+__device__ __forceinline__ T sub(T a, T b) {
+  return a - b;
+}
+template <typename T>
+__device__ __forceinline__ T neg(T a) {
+  if constexpr (Packed<T>::value)
+    return sub(T(0.0), a);
+  else
+    return -a;
+}
+
+template <typename T, bool DIAG, int GEN, typename NB, typename C>
+__device__ __forceinline__ void interior_row(const MacroStencil<C>& st, const OpFlags& fl, NB& nb, T k0,
                                              T& ax, T& ay, T& az, T& dgx, T& dgy, T& dgz) {
   const bool physical = GEN ? fl.physical != 0 : true;
   const bool khat_edge = GEN ? fl.khat_edge != 0 : false;
@@ -133,9 +157,16 @@ __device__ __forceinline__ void interior_row(const MacroStencil<T>& st, const Op
   dgy = 0;
   dgz = 0;
   const T k0q = (T)0.25 * k0;
+  // the vector differences of a direction pair are read one pair ahead of their use
+  Diff3<T> pn = nb.diff(0), mn = nb.diff(7);
 #pragma unroll
   for (int d = 0; d < 7; ++d) {
+    const Diff3<T> p = pn, m = mn;
     nb.next_pair();
+    if (d < 6) {
+      pn = nb.diff(d + 1);
+      mn = nb.diff(d + 8);
+    }
     const int e = d + 7;
     const T wr = dir_red(d) ? (T)(1.0 / 12.0) : (T)0.125;
     T rsp = 0, rsm = 0;
@@ -150,7 +181,7 @@ __device__ __forceinline__ void interior_row(const MacroStencil<T>& st, const Op
         rsp += ka + kb;
         rsm += la + lb;
         if (physical) {
-          const T dp = ka - kb, dm = la - lb;
+          const T dp = sub(ka, kb), dm = sub(la, lb);
           wpx = fma(dp, st.s[d][c][0], wpx);
           wpy = fma(dp, st.s[d][c][1], wpy);
           wpz = fma(dp, st.s[d][c][2], wpz);
@@ -168,11 +199,10 @@ __device__ __forceinline__ void interior_row(const MacroStencil<T>& st, const Op
       khp = fma(wr, rsp, fma((T)0.25, nb.k(d), k0q));
       khm = fma(wr, rsm, fma((T)0.25, nb.k(e), k0q));
     }
-    const Diff3<T> p = nb.diff(d), m = nb.diff(e);
     const T vx = fma(khp, p.x, khm * m.x);
     const T vy = fma(khp, p.y, khm * m.y);
     const T vz = fma(khp, p.z, khm * m.z);
-    const T* S = st.S[d];
+    const C* S = st.S[d];
     ax = fma(S[0], vx, ax);
     ax = fma(S[3], vy, ax);
     ax = fma(S[4], vz, ax);
@@ -184,24 +214,25 @@ __device__ __forceinline__ void interior_row(const MacroStencil<T>& st, const Op
     az = fma(S[2], vz, az);
     if (physical) {
       // w x delta for both directions
+      const Diff3<T> np{neg(p.x), neg(p.y), neg(p.z)}, nm{neg(m.x), neg(m.y), neg(m.z)};
       ax = fma(wpy, p.z, ax);
-      ax = fma(-wpz, p.y, ax);
+      ax = fma(wpz, np.y, ax);
       ax = fma(wmy, m.z, ax);
-      ax = fma(-wmz, m.y, ax);
+      ax = fma(wmz, nm.y, ax);
       ay = fma(wpz, p.x, ay);
-      ay = fma(-wpx, p.z, ay);
+      ay = fma(wpx, np.z, ay);
       ay = fma(wmz, m.x, ay);
-      ay = fma(-wmx, m.z, ay);
+      ay = fma(wmx, nm.z, ay);
       az = fma(wpx, p.y, az);
-      az = fma(-wpy, p.x, az);
+      az = fma(wpy, np.x, az);
       az = fma(wmx, m.y, az);
-      az = fma(-wmy, m.x, az);
+      az = fma(wmy, nm.x, az);
     }
     if (DIAG) {
-      const T ks = khp + khm;
-      dgx = fma(-ks, S[0], dgx);
-      dgy = fma(-ks, S[1], dgy);
-      dgz = fma(-ks, S[2], dgz);
+      const T nks = neg(khp + khm);
+      dgx = fma(nks, S[0], dgx);
+      dgy = fma(nks, S[1], dgy);
+      dgz = fma(nks, S[2], dgz);
     }
   }
 }
@@ -338,6 +369,169 @@ __global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, c
     }
   }
   if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 macro-interior sweep on pairs of points (k_interior_pair).  A thread takes the
+// neighbouring points A = (i, j, k) and B = (i + 1, j, k) of one lattice row and evaluates
+// both in the two lanes of packed FP32 arithmetic (fma.rn.f32x2 and friends): every
+// instruction of interior_row serves both points.  The two points share their seven row
+// addresses, and their neighbours overlap (the points of a row at column offsets -1..2).
+// A row of odd length pairs its last point with the face point after it, a lattice point
+// whose neighbours are lattice points or the next row's: its lane is computed and dropped.
+// Pairs are numbered densely per slice: slice k (M = n - 1 - k) has floor(M^2 / 4) pairs,
+// rows j = 1 .. M - 1 holding ceil((M - j) / 2) of them.
+// ---------------------------------------------------------------------------
+// the float/double fma stays visible next to the packed overloads below
+using ::fma;
+
+struct P2 {
+  float2 v;
+  __device__ __forceinline__ P2() {}
+  __device__ __forceinline__ P2(float2 a) : v(a) {}
+  __device__ __forceinline__ P2(double a) : v(make_float2((float)a, (float)a)) {}
+  __device__ __forceinline__ P2(float a, float b) : v(make_float2(a, b)) {}
+};
+__device__ __forceinline__ P2 operator+(P2 a, P2 b) { return P2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ P2 operator-(P2 a) { return P2(make_float2(-a.v.x, -a.v.y)); }
+__device__ __forceinline__ P2 operator-(P2 a, P2 b) { return P2(__fadd2_rn(a.v, (-b).v)); }
+__device__ __forceinline__ P2 operator*(P2 a, P2 b) { return P2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ P2& operator+=(P2& a, P2 b) { return a = a + b; }
+__device__ __forceinline__ P2 fma(P2 a, P2 b, P2 c) { return P2(__ffma2_rn(a.v, b.v, c.v)); }
+// packed subtraction (sub.rn.f32x2)
+template <>
+__device__ __forceinline__ P2 sub<P2>(P2 a, P2 b) {
+  unsigned long long r;
+  const unsigned long long x = *reinterpret_cast<const unsigned long long*>(&a.v);
+  const unsigned long long y = *reinterpret_cast<const unsigned long long*>(&b.v);
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+  return P2(*reinterpret_cast<const float2*>(&r));
+}
+__device__ __forceinline__ P2 fma(float a, P2 b, P2 c) { return fma(P2(a, a), b, c); }
+__device__ __forceinline__ P2 fma(P2 a, float b, P2 c) { return fma(a, P2(b, b), c); }
+// stencil constants stored as lane pairs (c, c)
+__device__ __forceinline__ P2 fma(float2 a, P2 b, P2 c) { return P2(__ffma2_rn(a, b.v, c.v)); }
+__device__ __forceinline__ P2 fma(P2 a, float2 b, P2 c) { return P2(__ffma2_rn(a.v, b, c.v)); }
+
+// the lane pair (p[0], p[1]) read from global memory (read-only path); one load per lane and
+// pair, so the two values land in the pair's own registers
+__device__ __forceinline__ P2 ldg2(const float* p) {
+  float a, b;
+  asm volatile("ld.global.nc.f32 %0, [%2];\n\tld.global.nc.f32 %1, [%2+4];" : "=f"(a), "=f"(b) : "l"(p));
+  return P2(a, b);
+}
+
+// pair number t of a slice with M = n - 1 - k -> row j and pair p (points i = 2p + 1, 2p + 2)
+__device__ __forceinline__ void pair_decode(int M, int t, int& j, int& p) {
+  const int R = (M * M) / 4 - t;  // pairs from the one of t to the end of the slice
+  int s = (int)ceilf(sqrtf(4.0f * (float)R));
+  if (s * s < 4 * R) ++s;
+  if ((s - 1) * (s - 1) >= 4 * R) --s;
+  j = M - s + 1;  // rows before j hold floor(M^2/4) - floor(s^2/4) pairs
+  p = t - ((M * M) / 4 - (s * s) / 4);
+}
+
+// neighbour values of a pair of points: coefficients held in registers, vector values read
+// from global memory per direction (next_pair() keeps the reads of later direction pairs
+// below it)
+struct PairNeighbours {
+  const float* __restrict__ X;
+  const float* __restrict__ Y;
+  const float* __restrict__ Z;
+  int row[7];   // entry (in the macro) of column 0 of the seven rows, relative to point A
+  P2 kk[NDIR];
+  P2 x0, y0, z0;
+  // row index and column offset (relative to point A) of direction d
+  __device__ __forceinline__ static int rowof(int d) {
+    const int t[NDIR] = {0, 1, 2, 1, 3, 2, 3, 0, 4, 5, 4, 6, 5, 6};
+    return t[d];
+  }
+  __device__ __forceinline__ static int colof(int d) {
+    const int t[NDIR] = {1, -1, 0, 0, -1, 1, 0, -1, 1, 0, 0, 1, -1, 0};
+    return t[d];
+  }
+  __device__ __forceinline__ P2 k(int d) const { return kk[d]; }
+  __device__ __forceinline__ Diff3<P2> diff(int d) const {
+    const int q = row[rowof(d)] + colof(d);
+    return {sub(ldg2(X + q), x0), sub(ldg2(Y + q), y0), sub(ldg2(Z + q), z0)};
+  }
+  __device__ __forceinline__ void next_pair() {
+    asm volatile("" : "+r"(row[0]), "+r"(row[1]), "+r"(row[2]), "+r"(row[3]), "+r"(row[4]), "+r"(row[5]),
+                 "+r"(row[6]));
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ float lane_x(T v) { return v.v.x; }
+
+template <int OP, int GEN, int KB>
+__global__ void __launch_bounds__(INTERIOR_BLOCK, 4) k_interior_pair(const LevelDev L, const MacroStencil<float2> st,
+                                                                   const int macro, const OpFlags fl,
+                                                                   const SweepArgs<float> a) {
+  const int32_t tile = L.tiles_pair[blockIdx.x];
+  const int n = L.n;
+  const int k = tile >> 20;
+  const int M = n - 1 - k;
+  const int t = (tile & 0xFFFFF) + threadIdx.x;
+  double r2 = 0.0;
+  if (t < (M * M) / 4) {
+    int j, pp;
+    pair_decode(M, t, j, pp);
+    const int i = 2 * pp + 1;
+    const bool second = i + 1 <= M - j;  // point B is macro-interior
+    const int64_t E = L.entries;
+    const int64_t base = (int64_t)macro * L.nt;
+    const int m = n - k;
+    const int r00 = (int)(tetnum(n + 1) - tetnum(n + 1 - k)) + j * (2 * m + 3 - j) / 2 + i;
+    const int r10 = r00 + (m + 1 - j);
+    const int rm0 = r00 - (m + 2 - j);
+    const int sz = (m + 1) * (m + 2) / 2;
+    const int szm = (m + 2) * (m + 3) / 2;
+    PairNeighbours nb;
+    nb.X = a.x + base;
+    nb.Y = nb.X + E;
+    nb.Z = nb.Y + E;
+    nb.row[0] = r00;
+    nb.row[1] = r10;
+    nb.row[2] = rm0 + sz - j + 1;  // rm1
+    nb.row[3] = r00 + sz - j;      // r01
+    nb.row[4] = rm0;
+    nb.row[5] = r10 - szm + j + 1; // r1m
+    nb.row[6] = r00 - szm + j;     // r0m
+    P2 k0;
+    {
+      const float* __restrict__ K = a.k + base;
+      const uint16_t* __restrict__ K16 = a.k16 + base;
+      auto kload = [&](int q) -> float {
+        if constexpr (KB)
+          return __uint_as_float((uint32_t)__ldg(K16 + q) << 16);
+        else
+          return __ldg(K + q);
+      };
+      auto kload2 = [&](int q) -> P2 {
+        if constexpr (KB)
+          return P2(kload(q), kload(q + 1));
+        else
+          return ldg2(K + q);
+      };
+      k0 = kload2(r00);
+#pragma unroll
+      for (int d = 0; d < NDIR; ++d) nb.kk[d] = kload2(nb.row[PairNeighbours::rowof(d)] + PairNeighbours::colof(d));
+    }
+    nb.x0 = ldg2(nb.X + r00);
+    nb.y0 = ldg2(nb.Y + r00);
+    nb.z0 = ldg2(nb.Z + r00);
+    P2 ax, ay, az, dgx, dgy, dgz;
+    interior_row<P2, OP == OP_JACOBI || OP == OP_CHEBY || OP == OP_DIAG, GEN>(st, fl, nb, k0, ax, ay, az, dgx, dgy,
+                                                                              dgz);
+    const int64_t e = base + r00;
+    epilogue<float, OP>(a, e, E, ax.v.x, ay.v.x, az.v.x, dgx.v.x, dgy.v.x, dgz.v.x, nb.x0.v.x, nb.y0.v.x, nb.z0.v.x,
+                        r2);
+    if (second)
+      epilogue<float, OP>(a, e + 1, E, ax.v.y, ay.v.y, az.v.y, dgx.v.y, dgy.v.y, dgz.v.y, nb.x0.v.y, nb.y0.v.y,
+                          nb.z0.v.y, r2);
+  }
+  if (OP == OP_RESID && a.partial != nullptr) block_sum_store<float>(r2, a.partial + blockIdx.x);
 }
 
 // Macro-interior rows by nodal integration (the NODAL variant, eq. nodalintegration):
@@ -622,58 +816,6 @@ __device__ __forceinline__ double* acc_of<double>(const LevelDev& L) {
   return L.acc64;
 }
 
-// Free face-interior skeleton nodes, four warps per 32 (node, incident macro) items: warp
-// q of the block evaluates, for the item of its lane, candidate elements [6q, 6q+6) and
-// the directions [0,4), [4,8), [8,11) or [11,14) of the macro's part of the row (the part
-// is uniform per warp, so the unrolled bodies do not diverge); the block adds the four
-// partial sums in a fixed order, (p0 + p1) + (p2 + p3), into the node's accumulator.  A
-// face node has at most two incidences, so 0 + a + b is the same in either order.
-constexpr int FACE_PARTS = 4;
-
-template <typename T>
-__global__ void __launch_bounds__(32 * FACE_PARTS) k_face_items(const LevelDev L, const MacroConsts<T>* __restrict__ mc,
-                                                                const OpFlags fl, const T* __restrict__ x,
-                                                                const T* __restrict__ kc) {
-  __shared__ T red[FACE_PARTS][6][32];
-  const int lane = threadIdx.x & 31, part = threadIdx.x >> 5;
-  const int64_t item = (int64_t)blockIdx.x * 32 + lane;
-  T ax = 0, ay = 0, az = 0, dgx = 0, dgy = 0, dgz = 0;
-  const bool valid = item < L.nface_items;
-  FaceItem it{};
-  if (valid) {
-    it = L.face_items[item];
-    const int n = L.n;
-    const int64_t E = L.entries;
-    const int64_t base = (int64_t)it.macro * L.nt;
-    const T* px = x + base;
-    const T* pk = kc + base;
-    const int c0 = lattice_index32(n, it.i, it.j, it.k);
-    const T x0 = px[c0], y0 = px[c0 + E], z0 = px[c0 + 2 * E];
-    const uint32_t cand = L.face_mask[it.f];
-    const uint32_t dirs = (1u << NDIR) - 1u;
-    const MacroConsts<T>& C = mc[it.macro];
-    switch (part) {
-      case 0: incidence_row<T, 0, 6, 0, 4>(C, px, pk, E, n, it.i, it.j, it.k, cand, dirs, x0, y0, z0, fl, ax, ay, az, dgx, dgy, dgz); break;
-      case 1: incidence_row<T, 6, 12, 4, 8>(C, px, pk, E, n, it.i, it.j, it.k, cand, dirs, x0, y0, z0, fl, ax, ay, az, dgx, dgy, dgz); break;
-      case 2: incidence_row<T, 12, 18, 8, 11>(C, px, pk, E, n, it.i, it.j, it.k, cand, dirs, x0, y0, z0, fl, ax, ay, az, dgx, dgy, dgz); break;
-      default: incidence_row<T, 18, 24, 11, 14>(C, px, pk, E, n, it.i, it.j, it.k, cand, dirs, x0, y0, z0, fl, ax, ay, az, dgx, dgy, dgz); break;
-    }
-  }
-  red[part][0][lane] = ax;
-  red[part][1][lane] = ay;
-  red[part][2][lane] = az;
-  red[part][3][lane] = dgx;
-  red[part][4][lane] = dgy;
-  red[part][5][lane] = dgz;
-  __syncthreads();
-  if (part == 0 && valid) {
-    T* acc = acc_of<T>(L) + 8 * (int64_t)it.node;
-#pragma unroll
-    for (int q = 0; q < 6; ++q)
-      atomicAdd(acc + q, (red[0][q][lane] + red[1][q][lane]) + (red[2][q][lane] + red[3][q][lane]));
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Free face-interior skeleton nodes, one thread per node (k_face_rows).  A node on a macro
 // face has one incidence per macro sharing the face (two on an interior face); in macro T
@@ -854,35 +996,6 @@ __global__ void __launch_bounds__(128) k_face_rows(const LevelDev L, const Macro
         default: face_incidence<T, 3, DIAG>(C, px, pk, E, n, I.i, I.j, I.k, fl, x0, y0, z0, ax, ay, az, dgx, dgy, dgz); break;
       }
     }
-    for (int q = b0; q < b1; ++q) {
-      const SkelInc I = L.skel_inc[q];
-      const int64_t e = (int64_t)I.macro * L.nt + lattice_index32(n, I.i, I.j, I.k);
-      double tmp = 0.0;
-      epilogue<T, OP>(a, e, E, ax, ay, az, dgx, dgy, dgz, x0, y0, z0, tmp);
-      if (q == b0) r2 = tmp;
-    }
-  }
-  if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
-}
-
-// Face nodes: finish the row from the accumulator (which is reset to zero) and
-// write every copy.
-template <typename T, int OP>
-__global__ void __launch_bounds__(128) k_face_finalize(const LevelDev L, const SweepArgs<T> a) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  double r2 = 0.0;
-  if (t < L.nface_nodes) {
-    const int n = L.n;
-    const int64_t E = L.entries;
-    T* acc = acc_of<T>(L) + 8 * (int64_t)t;
-    const T ax = acc[0], ay = acc[1], az = acc[2], dgx = acc[3], dgy = acc[4], dgz = acc[5];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) acc[c] = 0;
-    const int s = L.face_nodes[t];
-    const int b0 = L.skel_ptr[s], b1 = L.skel_ptr[s + 1];
-    const SkelInc I0 = L.skel_inc[b0];
-    const int64_t e0 = (int64_t)I0.macro * L.nt + lattice_index32(n, I0.i, I0.j, I0.k);
-    const T x0 = a.x[e0], y0 = a.x[e0 + E], z0 = a.x[e0 + 2 * E];
     for (int q = b0; q < b1; ++q) {
       const SkelInc I = L.skel_inc[q];
       const int64_t e = (int64_t)I.macro * L.nt + lattice_index32(n, I.i, I.j, I.k);
@@ -1150,19 +1263,40 @@ __global__ void __launch_bounds__(128) k_skeleton_ev_stk(const LevelDev L, const
 
 // one macro's interior launch: the BF16-coefficient kernel for FP32 sweeps of the default
 // operator when a.k16 is set, else the FP32/FP64 coefficient kernel
+// one macro's interior launch: FP32 sweeps on point pairs (the BF16-coefficient kernel for the
+// default operator when a.k16 is set), FP64 sweeps one point per thread; returns the number
+// of blocks (partial-sum slots)
+// the interior stencil with every value as a lane pair (c, c), the operand form of the packed
+// FP32 arithmetic
+inline MacroStencil<float2> lane_pairs(const MacroStencil<float>& st) {
+  MacroStencil<float2> p;
+  const float* a = &st.S[0][0];
+  float2* b = &p.S[0][0];
+  for (size_t q = 0; q < sizeof(st) / sizeof(float); ++q) b[q] = make_float2(a[q], a[q]);
+  return p;
+}
+
 template <typename T, int OP>
-void launch_interior(bool gen, const LevelDev& L, const MacroStencil<T>& st, int m, const OpFlags& fl,
-                     const SweepArgs<T>& am, cudaStream_t s) {
+int launch_interior(bool gen, const LevelDev& L, const MacroStencil<T>& st, int m, const OpFlags& fl,
+                    const SweepArgs<T>& am, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
-    if (am.k16 && !gen) {
-      k_interior<T, OP, 0, 0, 1><<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st, m, fl, am);
-      return;
-    }
+    if (L.ntiles_pair == 0) return 0;
+    const MacroStencil<float2> st2 = lane_pairs(st);
+    if (am.k16 && !gen)
+      k_interior_pair<OP, 0, 1><<<L.ntiles_pair, INTERIOR_BLOCK, 0, s>>>(L, st2, m, fl, am);
+    else if (gen)
+      k_interior_pair<OP, 1, 0><<<L.ntiles_pair, INTERIOR_BLOCK, 0, s>>>(L, st2, m, fl, am);
+    else
+      k_interior_pair<OP, 0, 0><<<L.ntiles_pair, INTERIOR_BLOCK, 0, s>>>(L, st2, m, fl, am);
+    return L.ntiles_pair;
+  } else {
+    if (L.ntiles_lin == 0) return 0;
+    if (gen)
+      k_interior<T, OP, 1><<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st, m, fl, am);
+    else
+      k_interior<T, OP, 0><<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st, m, fl, am);
+    return L.ntiles_lin;
   }
-  if (gen)
-    k_interior<T, OP, 1><<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st, m, fl, am);
-  else
-    k_interior<T, OP, 0><<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st, m, fl, am);
 }
 
 template <typename T>
@@ -1187,14 +1321,15 @@ int launch_sweep_macro(const LevelDev& L, const MacroStencil<T>* st_host, const 
     if (partial_count) *partial_count = L.ntiles_lin;
     return (int)cudaGetLastError();
   }
+  int nb = 0;
   switch (op) {
-    case OP_APPLY: launch_interior<T, OP_APPLY>(gen, L, st_host[m], m, fl, am, s); break;
-    case OP_RESID: launch_interior<T, OP_RESID>(gen, L, st_host[m], m, fl, am, s); break;
-    case OP_JACOBI: launch_interior<T, OP_JACOBI>(gen, L, st_host[m], m, fl, am, s); break;
-    case OP_CHEBY: launch_interior<T, OP_CHEBY>(gen, L, st_host[m], m, fl, am, s); break;
-    case OP_DIAG: launch_interior<T, OP_DIAG>(gen, L, st_host[m], m, fl, am, s); break;
+    case OP_APPLY: nb = launch_interior<T, OP_APPLY>(gen, L, st_host[m], m, fl, am, s); break;
+    case OP_RESID: nb = launch_interior<T, OP_RESID>(gen, L, st_host[m], m, fl, am, s); break;
+    case OP_JACOBI: nb = launch_interior<T, OP_JACOBI>(gen, L, st_host[m], m, fl, am, s); break;
+    case OP_CHEBY: nb = launch_interior<T, OP_CHEBY>(gen, L, st_host[m], m, fl, am, s); break;
+    case OP_DIAG: nb = launch_interior<T, OP_DIAG>(gen, L, st_host[m], m, fl, am, s); break;
   }
-  if (partial_count) *partial_count = L.ntiles_lin;
+  if (partial_count) *partial_count = nb;
   return (int)cudaGetLastError();
 }
 
@@ -1209,17 +1344,17 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
   int64_t used = partial_offset;
   const bool gen = !(fl.physical == 1 && fl.khat_edge == 0);
   for (int m = 0; m < L.nmacro && (parts & 1); ++m) {
-    if (L.ntiles_lin == 0) break;
     SweepArgs<T> am = a;
     if (a.partial) am.partial = a.partial + used;
+    int nb = 0;
     switch (op) {
-      case OP_APPLY: launch_interior<T, OP_APPLY>(gen, L, st_host[m], m, fl, am, s); break;
-      case OP_RESID: launch_interior<T, OP_RESID>(gen, L, st_host[m], m, fl, am, s); break;
-      case OP_JACOBI: launch_interior<T, OP_JACOBI>(gen, L, st_host[m], m, fl, am, s); break;
-      case OP_CHEBY: launch_interior<T, OP_CHEBY>(gen, L, st_host[m], m, fl, am, s); break;
-      case OP_DIAG: launch_interior<T, OP_DIAG>(gen, L, st_host[m], m, fl, am, s); break;
+      case OP_APPLY: nb = launch_interior<T, OP_APPLY>(gen, L, st_host[m], m, fl, am, s); break;
+      case OP_RESID: nb = launch_interior<T, OP_RESID>(gen, L, st_host[m], m, fl, am, s); break;
+      case OP_JACOBI: nb = launch_interior<T, OP_JACOBI>(gen, L, st_host[m], m, fl, am, s); break;
+      case OP_CHEBY: nb = launch_interior<T, OP_CHEBY>(gen, L, st_host[m], m, fl, am, s); break;
+      case OP_DIAG: nb = launch_interior<T, OP_DIAG>(gen, L, st_host[m], m, fl, am, s); break;
     }
-    used += L.ntiles_lin;
+    used += nb;
   }
   if (parts & 2) {
     if (L.nface_nodes > 0) {
