@@ -410,6 +410,13 @@ int64_t hhg_learn_num_params(void);
  * epilogue warpgroup draining one while the next tile's MMAs run).  All give the same
  * results up to FP32 summation order. */
 hhg_status hhg_learn_set_conv_kernel(hhg_ctx* ctx, int kernel);
+/* Bound of the tensor-core convolution's (kernel 1) wait for its MMAs, in polls about 100 ns
+ * apart; negative restores the default (2^24 polls).  Fault handling, not the paper: when the
+ * wait runs out the kernel records an error, still waits (with the default bound) for the MMAs
+ * it issued before freeing their tensor memory, skips its epilogue and returns; the call then
+ * fails with HHG_ERR_TIMEOUT and the context falls back to convolution kernel 0.  A short
+ * bound lets a test make the wait run out without a fault; the context stays usable. */
+hhg_status hhg_learn_set_conv_wait(hhg_ctx* ctx, int64_t polls);
 /* Coarse-grid mode (elasticity; levels = 0 default, 1..3): the network runs on the node
  * grid `levels` levels below the solve's.  Its inputs there are r1 restricted (P^T, as in
  * the V-cycle) and z0 injected (coarse nodes are fine nodes), D is that level's point

@@ -141,6 +141,7 @@ _SIGS = {
     "hhg_learn_init": [C.c_void_p, C.c_uint64],
     "hhg_learn_set_conv_kernel": [C.c_void_p, C.c_int],
     "hhg_learn_set_coarsening": [C.c_void_p, C.c_int],
+    "hhg_learn_set_conv_wait": [C.c_void_p, C.c_int64],
     "hhg_learn_get_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "hhg_learn_set_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "hhg_learn_grid": [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int64)],
@@ -403,6 +404,11 @@ def hhg_learn_num_params():
 def hhg_learn_set_conv_kernel(ctx, kernel):
     """0: warp-level MMA convolution (default), 1: tcgen05 per tile, 2: TMA + tcgen05 pipeline."""
     _check(ctx, load().hhg_learn_set_conv_kernel(ctx, int(kernel)))
+
+
+def hhg_learn_set_conv_wait(ctx, polls):
+    """Bound (polls) of the tensor-core convolution's wait for its MMAs; negative: the default."""
+    _check(ctx, load().hhg_learn_set_conv_wait(ctx, C.c_int64(int(polls))))
 
 
 def hhg_learn_init(ctx, seed=0):

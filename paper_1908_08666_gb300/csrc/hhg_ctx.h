@@ -180,6 +180,7 @@ struct LearnState {
   DevMem params, grad, m, v, fwd, bwd;  // LN_NPARAM floats; packed fragments LN_LAYERS * LN_PACK words
   DevMem fwd_u, bwd_u;                   // tcgen05 operands, LN_LAYERS * LN_UMMA bytes
   int conv_kernel = 0;                   // 0 warp MMA, 1 tcgen05 per tile, 2 TMA + tcgen05 pipeline
+  int64_t conv_wait_polls = -1;          // bound of kernel 1's wait for its MMAs (-1: the default)
   std::map<int, std::unique_ptr<LearnGrid>> grids;
   // training pairs of one level: inputs (ln_pair_in(pair_nc) BF16 per voxel) and targets
   // (pair_nc FP32), pair_nc = components of the problem they came from

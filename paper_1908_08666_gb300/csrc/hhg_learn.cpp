@@ -189,7 +189,8 @@ void conv(hhg_ctx* c, LearnState& S, int l, bool bwd, const void* X, const float
   if (S.conv_kernel == 2)
     CK(launch_conv_tma(X, wu, bias, Y, Yf, nf, mask, s, relu, c->stream));
   else
-    CK(launch_conv(X, wp, S.conv_kernel == 1 ? wu : nullptr, bias, Y, Yf, nf, mask, s, relu, c->stream));
+    CK(launch_conv(X, wp, S.conv_kernel == 1 ? wu : nullptr, bias, Y, Yf, nf, mask, s, relu, c->stream,
+                   S.conv_wait_polls));
 }
 
 // forward pass from act[0]: act[1..3] = hidden activations, out = the first nout FP32
@@ -789,6 +790,10 @@ hhg_status hhg_learn_set_conv_kernel(hhg_ctx* c, int kernel) {
     if (kernel < 0 || kernel > 2) THROW(HHG_ERR_ARG, "conv kernel 0 (warp MMA), 1 (tcgen05) or 2 (TMA + tcgen05)");
     state(c).conv_kernel = kernel;
   });
+}
+
+hhg_status hhg_learn_set_conv_wait(hhg_ctx* c, int64_t polls) {
+  return guard(c, [&] { state(c).conv_wait_polls = polls < 0 ? -1 : polls; });
 }
 
 hhg_status hhg_learn_set_coarsening(hhg_ctx* c, int levels) {

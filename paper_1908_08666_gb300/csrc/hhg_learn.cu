@@ -217,7 +217,7 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
 __global__ void __launch_bounds__(128) k_conv_umma(const uint4* __restrict__ X, const uint4* __restrict__ Wu,
                                                    const float* __restrict__ bias, uint4* __restrict__ Y,
                                                    float* __restrict__ Yf, int nf, const uint4* __restrict__ mask,
-                                                   int D, int H, int W, int ntz, int relu) {
+                                                   int D, int H, int W, int ntz, int relu, long long wait_polls) {
   extern __shared__ __align__(1024) unsigned char usm[];
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(usm);
   const uint32_t bar = sbase + U_BAR;
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(128) k_conv_umma(const uint4* __restrict__ X, 
   // bounded wait for the MMAs; a short sleep between polls leaves the issue slots to the
   // other blocks on the SM (their staging and epilogues)
   uint32_t done = 0;
-  for (long long it = 0; it < U_SPIN_LIMIT && !done; ++it) {
+  for (long long it = 0; it < wait_polls && !done; ++it) {
     asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
                  : "=r"(done)
                  : "r"(bar), "r"(0)
@@ -277,7 +277,20 @@ __global__ void __launch_bounds__(128) k_conv_umma(const uint4* __restrict__ X, 
     if (!done) __nanosleep(100);
   }
   done = __all_sync(0xffffffffu, done);
-  if (!done && lane == 0) atomicExch(&g_conv_error, 1);
+  if (!done) {
+    if (lane == 0) atomicExch(&g_conv_error, 1);
+    // drain: the MMAs this CTA issued must have completed before their tensor memory is
+    // freed below; this wait keeps the full bound whatever wait_polls was
+    uint32_t drained = 0;
+    for (long long it = 0; it < U_SPIN_LIMIT && !drained; ++it) {
+      asm volatile(
+          "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+          : "=r"(drained)
+          : "r"(bar), "r"(0)
+          : "memory");
+      if (!drained) __nanosleep(100);
+    }
+  }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   float bv[16];
 #pragma unroll
@@ -933,7 +946,7 @@ inline int64_t red_blocks(int64_t V) { return blocks_for(V, RED_BLOCK, RED_MAX_B
 }  // namespace
 
 int launch_conv(const void* X, const uint32_t* Wp, const void* Wu, const float* bias, void* Y, float* Yf, int nf,
-                const void* mask, GridShape s, int relu, void* stream) {
+                const void* mask, GridShape s, int relu, void* stream, int64_t wait_polls) {
   if (s.voxels() == 0) return 0;
   if (Wu) {
     static bool uattr[64] = {};
@@ -949,7 +962,8 @@ int launch_conv(const void* X, const uint32_t* Wp, const void* Wu, const float* 
     const int ntz = (s.D + UZ - 1) / UZ;
     dim3 grid((unsigned)((s.W + UX - 1) / UX), (unsigned)((s.H + UY - 1) / UY), (unsigned)(ntz * s.B));
     k_conv_umma<<<grid, 128, U_SMEM, (cudaStream_t)stream>>>((const uint4*)X, (const uint4*)Wu, bias, (uint4*)Y, Yf,
-                                                             nf, (const uint4*)mask, s.D, s.H, s.W, ntz, relu);
+                                                             nf, (const uint4*)mask, s.D, s.H, s.W, ntz, relu,
+                                                             wait_polls < 0 ? U_SPIN_LIMIT : (long long)wait_polls);
     return (int)cudaGetLastError();
   }
   static bool attr[64] = {};  // per device: dynamic shared memory above 48 KB

@@ -43,9 +43,11 @@ struct GridShape {
 // mask (BF16, 16 channels, optional): outputs where mask <= 0 are set to 0 (the ReLU
 // derivative in the backward pass).  relu: apply max(., 0) before the mask.
 // Wu (nullable): the layer's tcgen05 operands (launch_pack_umma); when given, the
-// tensor-memory kernel runs instead of the warp-MMA one.
+// tensor-memory kernel runs instead of the warp-MMA one, its wait for the MMAs bounded by
+// wait_polls polls (negative: the default bound).
 int launch_conv(const void* X, const uint32_t* Wp, const void* Wu, const float* bias, void* Y, float* Yf, int nf,
-                const void* mask, GridShape s, int relu, void* stream);
+                const void* mask, GridShape s, int relu, void* stream,
+                int64_t wait_polls = -1);
 // The same convolution as a persistent TMA + tcgen05 pipeline (Wu required)
 int launch_conv_tma(const void* X, const void* Wu, const float* bias, void* Y, float* Yf, int nf, const void* mask,
                     GridShape s, int relu, void* stream);

@@ -126,6 +126,36 @@ def cube4():
     p.close()
 
 
+def test_tcgen05_wait_runout_reports_timeout_and_keeps_the_context(ctx):
+    """Fault handling without a fault: with the tensor-core convolution's wait for its MMAs
+    bounded to zero polls, the wait runs out in every block; each block records the error,
+    still waits (with the default bound) for the MMAs it issued before freeing their tensor
+    memory, skips its epilogue and returns.  The call fails with HHG_ERR_TIMEOUT and the
+    context falls back to kernel 0; with the default bound restored, the tensor-core kernel
+    gives the oracle's result again in the same context."""
+    t = ctx.torch
+    Ws, bs = _params(2, 3)
+    B.hhg_learn_set_params(ctx.h, _flat(Ws, bs))
+    Bn, D, H, W = 1, 3, 4, 16
+    x = np.random.default_rng(7).normal(size=(Bn, D, H, W, 7)).astype(np.float32)
+    xd = ctx.dev(x, t.float32)
+    out = t.empty((Bn, D, H, W, 3), dtype=t.float32, device="cuda")
+    B.hhg_learn_set_conv_kernel(ctx.h, 1)
+    B.hhg_learn_set_conv_wait(ctx.h, 0)
+    try:
+        with pytest.raises(B.HhgError) as ei:
+            B.hhg_learn_forward(ctx.h, xd, 7, Bn, D, H, W, out, 3)
+        assert ei.value.status == 7 and "timed out" in str(ei.value)
+    finally:
+        B.hhg_learn_set_conv_wait(ctx.h, -1)
+    B.hhg_learn_set_conv_kernel(ctx.h, 1)
+    B.hhg_learn_forward(ctx.h, xd, 7, Bn, D, H, W, out, 3)
+    t.cuda.synchronize()
+    want, _ = LN.forward(x.astype(np.float64), Ws, bs, cout=3)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.abs(got - want).max() <= 1e-2 * np.abs(want).max()
+
+
 def test_grid_of_the_cube(cube4):
     B.hhg_learn_set_conv_kernel(cube4.ctx.h, 0)
     dims, nfree = B.hhg_learn_grid(cube4.ctx.h, 4)
