@@ -82,8 +82,15 @@ typedef enum { HHG_ELASTICITY = 0, HHG_STOKES = 1 } hhg_problem_kind;
  * (eq. nodalintegration; elasticity only): the paper's comparison method, whose
  * macro-interior rows sum kbar^t times the element stiffness over the 24 elements
  * around each node on the fly (skeleton rows are a_h rows in every variant's
- * practical interface rule; hhg_residual_noalloc rejects this variant). */
-typedef enum { HHG_PHYSICAL = 0, HHG_UNPHYSICAL = 1, HHG_NODAL = 2 } hhg_variant;
+ * practical interface rule; hhg_residual_noalloc rejects this variant).
+ * STORED (elasticity only) is the physical-scaling operator with the macro-interior rows
+ * stored, the paper's third method of Sec. 4 (Table memorytotal: 135 values per node):
+ * the first sweep on a level and precision after hhg_set_problem or hhg_set_coefficient
+ * computes the 15 3x3 blocks of every macro-interior row (in FP64 from the FP64
+ * coefficient, rounded to the sweep's precision; 135 * E values of that precision per
+ * level, owned by the library) and later sweeps read them; skeleton rows are computed
+ * as for PHYSICAL.  The operator equals PHYSICAL's up to rounding. */
+typedef enum { HHG_PHYSICAL = 0, HHG_UNPHYSICAL = 1, HHG_NODAL = 2, HHG_STORED = 3 } hhg_variant;
 
 /* khat: patch mean (eq. patchmean) or edge mean (k_i + k_j)/2 (Remark after Sec. 2.2). */
 typedef enum { HHG_KHAT_PATCH = 0, HHG_KHAT_EDGE = 1 } hhg_khat;

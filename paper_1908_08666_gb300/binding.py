@@ -19,7 +19,7 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_UNSUPPORTE
           6: "ERR_NUMERIC", 7: "ERR_TIMEOUT", 8: "ERR_STATE"}
 F64, F32, BF16 = 0, 1, 2
 ELASTICITY, STOKES = 0, 1
-PHYSICAL, UNPHYSICAL, NODAL = 0, 1, 2
+PHYSICAL, UNPHYSICAL, NODAL, STORED = 0, 1, 2, 3
 KHAT_PATCH, KHAT_EDGE = 0, 1
 IFACE_SYMMETRIC, IFACE_PRACTICAL = 0, 1
 

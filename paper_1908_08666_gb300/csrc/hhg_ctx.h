@@ -138,6 +138,10 @@ struct LevelHost {
   DevMem d_mc64, d_mc32;
   DevMem d_k64, d_k32;
   DevMem d_k16;  // BF16 bits of the coefficient (BF16 coefficient mode)
+  // stored stencil blocks of the macro-interior rows (STORED variant), per precision, and the
+  // (coefficient, problem) versions they were computed for
+  DevMem stencil32, stencil64;
+  int64_t stencil_version[2][2] = {{-1, -1}, {-1, -1}};
   std::vector<MacroStencil<double>> st64;
   std::vector<MacroStencil<float>> st32;
   std::vector<NodalConsts<double>> nc64;  // element stiffness per macro (NODAL variant)
@@ -226,6 +230,7 @@ struct hhg_ctx {
   bool have_problem = false;
   bool have_coeff = false;
   int64_t coeff_version = 0;  // incremented by hhg_set_coefficient
+  int64_t problem_version = 0;  // incremented by hhg_set_problem
   bool coeff_bf16 = false;     // the coefficient was given in BF16 (k16 holds it on every level)
   std::unique_ptr<LearnState> learn;
   OpFlags flags{1, 0, 0};
@@ -437,10 +442,26 @@ inline void join_side_streams(hhg_ctx* c) {
 // kernels run concurrently on aux[0] (they write disjoint entries and their own partial-sum
 // slots); both side streams are joined back into `stream`.  With profiling on, the
 // interior span (fork to join of the interior launches) and the skeleton span are timed.
+// The stored stencil blocks of a level in precision T (STORED variant), computed on the stream
+// when the coefficient or the problem changed since they were last computed.
+template <typename T>
+const T* stored_stencil(hhg_ctx* c, LevelHost& L) {
+  const int q = std::is_same<T, float>::value ? 0 : 1;
+  DevMem& S = q == 0 ? L.stencil32 : L.stencil64;
+  if (!S.p) CK(S.alloc((size_t)135 * L.entries * sizeof(T)));
+  if (L.stencil_version[q][0] != c->coeff_version || L.stencil_version[q][1] != c->problem_version) {
+    CK(launch_store_stencil<T>(L.dev, L.st64.data(), c->flags, L.d_k64.as<double>(), S.as<T>(), c->stream));
+    L.stencil_version[q][0] = c->coeff_version;
+    L.stencil_version[q][1] = c->problem_version;
+  }
+  return S.as<T>();
+}
+
 template <typename T>
 void sweep(hhg_ctx* c, int level, OpKind op, SweepArgs<T> a, double* norm2) {
   LevelHost& L = c->lv(level);
   a.k = kptr<T>(L);
+  if (c->flags.stored) a.stencil = stored_stencil<T>(c, L);
   if (std::is_same<T, float>::value && c->coeff_bf16) a.k16 = L.d_k16.as<uint16_t>();
   if (norm2) a.partial = c->scratch.as<double>();
   if (!c->aux[0]) {

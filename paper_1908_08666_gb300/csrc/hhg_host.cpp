@@ -836,10 +836,11 @@ hhg_status hhg_set_problem(hhg_ctx* c, const hhg_problem* p) {
     } else {
       THROW(HHG_ERR_ARG, "unknown problem kind");
     }
-    if (p->variant != HHG_PHYSICAL && p->variant != HHG_UNPHYSICAL && p->variant != HHG_NODAL)
+    if (p->variant != HHG_PHYSICAL && p->variant != HHG_UNPHYSICAL && p->variant != HHG_NODAL &&
+        p->variant != HHG_STORED)
       THROW(HHG_ERR_ARG, "bad variant");
-    if (p->variant == HHG_NODAL && p->kind != HHG_ELASTICITY)
-      THROW(HHG_ERR_UNSUPPORTED, "the nodal-integration variant is built for elasticity");
+    if ((p->variant == HHG_NODAL || p->variant == HHG_STORED) && p->kind != HHG_ELASTICITY)
+      THROW(HHG_ERR_UNSUPPORTED, "the nodal-integration and stored-stencil variants are built for elasticity");
     if (p->khat != HHG_KHAT_PATCH && p->khat != HHG_KHAT_EDGE) THROW(HHG_ERR_ARG, "bad khat");
     if (p->iface != HHG_IFACE_SYMMETRIC && p->iface != HHG_IFACE_PRACTICAL) THROW(HHG_ERR_ARG, "bad iface");
     for (int l = c->level_min; l <= c->level_max; ++l) {
@@ -904,7 +905,9 @@ hhg_status hhg_set_problem(hhg_ctx* c, const hhg_problem* p) {
       }
     }
     c->prob = *p;
-    c->flags.physical = p->variant == HHG_PHYSICAL ? 1 : 0;
+    c->flags.physical = (p->variant == HHG_PHYSICAL || p->variant == HHG_STORED) ? 1 : 0;
+    c->flags.stored = p->variant == HHG_STORED ? 1 : 0;
+    ++c->problem_version;
     c->flags.khat_edge = p->khat == HHG_KHAT_EDGE ? 1 : 0;
     // the nodal variant is a_h on every row: skeleton rows by the a_h (practical) rule
     c->flags.practical = (p->iface == HHG_IFACE_PRACTICAL || p->variant == HHG_NODAL) ? 1 : 0;

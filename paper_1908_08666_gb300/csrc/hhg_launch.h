@@ -14,6 +14,7 @@ struct OpFlags {
   int khat_edge;  // 1: khat = (k_i + k_j)/2; 0: patch mean
   int practical;  // 1: skeleton rows are the a_h rows; 0: symmetric interface rows
   int nodal = 0;  // 1: macro-interior rows by nodal integration a_h (the NODAL variant)
+  int stored = 0; // 1: macro-interior rows from the stored stencil blocks (the STORED variant)
 };
 
 // Arguments of one stencil sweep.  Vectors are component-major over the level
@@ -34,7 +35,17 @@ struct SweepArgs {
   // BF16 bits of the coefficient (FP32 sweeps only; nullable): the macro-interior kernels
   // read k from here (2 B per node); k holds the same values widened, for the others
   const uint16_t* k16 = nullptr;
+  // stored stencil blocks of the macro-interior rows (STORED variant): value r (row-major 3x3
+  // entry) of block q (direction q < 14, q = 14 the centre) of entry e at [(9 q + r) * entries + e]
+  const T* stencil = nullptr;
 };
+
+// The stored stencil blocks (layout of SweepArgs::stencil) of macro m's interior rows, computed in
+// FP64 from the FP64 coefficient and rounded to T: for each direction d the scaled block
+// khat_d Shat_d + [w_d]_x of Lemma 2.1, and the centre block minus their sum.
+template <typename T>
+int launch_store_stencil(const LevelDev& L, const MacroStencil<double>* st_host, const OpFlags& fl, const double* k64,
+                         T* out, void* stream);
 
 // parts: 1 = macro-interior kernels (one launch per macro), 2 = skeleton kernel, 3 = both.
 // partial_offset: first partial slot used (the interior launches take ntiles_lin slots per

@@ -1116,8 +1116,11 @@ hhg_status hhg_mg_setup(hhg_ctx* c) {
         else
           CK(launch_convert<double, float>(Lc.entries, Lc.d_k64.as<double>(), Lc.d_k32.as<float>(), c->stream));
         Lc.lambda_set = false;
+        Lc.stencil_version[0][0] = Lc.stencil_version[1][0] = -1;  // stored stencils of the old coefficient
       }
     }
+    // (with the STORED variant the diagonal sweeps below also compute every level's stored
+    // stencils, so that no V-cycle captured in a graph later has to)
     for (int l = c->level_min; l <= c->level_max; ++l) {
       compute_diag<double>(c, l);
       compute_diag<float>(c, l);

@@ -613,6 +613,112 @@ __global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior_nodal(const LevelDe
   if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
 }
 
+// ---------------------------------------------------------------------------
+// Stored stencils (Sec. 4, the paper's third method): the 15 blocks of every macro-interior
+// row (135 values, Table memorytotal) are computed once per coefficient by k_store_stencil and
+// streamed by k_interior_stored, which evaluates the row as the plain product
+// sum_q B_q x_{i+q} over the centre and the 14 neighbours.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(INTERIOR_BLOCK) k_store_stencil(const LevelDev L, const MacroStencil<double> st,
+                                                                   const int macro, const OpFlags fl,
+                                                                   const double* __restrict__ k64,
+                                                                   T* __restrict__ out) {
+  const int32_t tile = L.tiles_lin[blockIdx.x];
+  const int n = L.n;
+  const int k = tile >> 20;
+  const int M = n - 1 - k;
+  const int t = (tile & 0xFFFFF) + threadIdx.x;
+  if (t >= (M - 1) * M / 2) return;
+  int j, i;
+  slice_decode(M, t, j, i);
+  const int64_t E = L.entries;
+  const int64_t base = (int64_t)macro * L.nt;
+  int nb[NDIR];
+  lattice_neighbours(n, i, j, k, nb);
+  const int c0 = lattice_index32(n, i, j, k);
+  const int64_t e = base + c0;
+  const double k0 = k64[e];
+  double kk[NDIR];
+#pragma unroll
+  for (int d = 0; d < NDIR; ++d) kk[d] = k64[base + nb[d]];
+  double cen[9];
+#pragma unroll
+  for (int r = 0; r < 9; ++r) cen[r] = 0.0;
+#pragma unroll
+  for (int d = 0; d < NDIR; ++d) {
+    const int dd = d < 7 ? d : d - 7;  // Shat_{-d} = Shat_d, s[-d] = s[d]
+    double rs = 0.0, wx = 0.0, wy = 0.0, wz = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (c >= ring_count(d)) continue;
+      const double ka = kk[ring_a(d, c)], kb = kk[ring_b(d, c)];
+      rs += ka + kb;
+      wx = fma(ka - kb, st.s[dd][c][0], wx);
+      wy = fma(ka - kb, st.s[dd][c][1], wy);
+      wz = fma(ka - kb, st.s[dd][c][2], wz);
+    }
+    if (!fl.physical) wx = wy = wz = 0.0;
+    const double kh = fl.khat_edge ? 0.5 * (k0 + kk[d]) : 0.25 * (k0 + kk[d]) + (dir_red(d) ? 1.0 / 12.0 : 0.125) * rs;
+    const double* S = st.S[dd];
+    const double blk[9] = {kh * S[0], kh * S[3] - wz, kh * S[4] + wy,
+                           kh * S[3] + wz, kh * S[1], kh * S[5] - wx,
+                           kh * S[4] - wy, kh * S[5] + wx, kh * S[2]};
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+      out[(int64_t)(9 * d + r) * E + e] = (T)blk[r];
+      cen[r] -= blk[r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 9; ++r) out[(int64_t)(9 * NDIR + r) * E + e] = (T)cen[r];
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior_stored(const LevelDev L, const int macro,
+                                                                     const SweepArgs<T> a) {
+  const int32_t tile = L.tiles_lin[blockIdx.x];
+  const int n = L.n;
+  const int k = tile >> 20;
+  const int M = n - 1 - k;
+  const int t = (tile & 0xFFFFF) + threadIdx.x;
+  double r2 = 0.0;
+  if (t < (M - 1) * M / 2) {
+    int j, i;
+    slice_decode(M, t, j, i);
+    const int64_t E = L.entries;
+    const int64_t base = (int64_t)macro * L.nt;
+    int nb[NDIR];
+    lattice_neighbours(n, i, j, k, nb);
+    const int64_t e = base + lattice_index32(n, i, j, k);
+    const T* __restrict__ X = a.x + base;
+    const T* __restrict__ B = a.stencil + e;
+    const T x0 = a.x[e], y0 = a.x[e + E], z0 = a.x[e + 2 * E];
+    T ax = B[(int64_t)(9 * NDIR + 0) * E] * x0, ay = B[(int64_t)(9 * NDIR + 3) * E] * x0,
+      az = B[(int64_t)(9 * NDIR + 6) * E] * x0;
+    ax = fma(B[(int64_t)(9 * NDIR + 1) * E], y0, fma(B[(int64_t)(9 * NDIR + 2) * E], z0, ax));
+    ay = fma(B[(int64_t)(9 * NDIR + 4) * E], y0, fma(B[(int64_t)(9 * NDIR + 5) * E], z0, ay));
+    az = fma(B[(int64_t)(9 * NDIR + 7) * E], y0, fma(B[(int64_t)(9 * NDIR + 8) * E], z0, az));
+#pragma unroll
+    for (int d = 0; d < NDIR; ++d) {
+      const int q = nb[d];
+      const T vx = X[q], vy = X[q + E], vz = X[q + 2 * E];
+      const T* b = B + (int64_t)(9 * d) * E;
+      ax = fma(b[0], vx, fma(b[E], vy, fma(b[2 * E], vz, ax)));
+      ay = fma(b[3 * E], vx, fma(b[4 * E], vy, fma(b[5 * E], vz, ay)));
+      az = fma(b[6 * E], vx, fma(b[7 * E], vy, fma(b[8 * E], vz, az)));
+    }
+    T dgx = 0, dgy = 0, dgz = 0;
+    if (OP == OP_JACOBI || OP == OP_CHEBY || OP == OP_DIAG) {
+      dgx = B[(int64_t)(9 * NDIR + 0) * E];
+      dgy = B[(int64_t)(9 * NDIR + 4) * E];
+      dgz = B[(int64_t)(9 * NDIR + 8) * E];
+    }
+    epilogue<T, OP>(a, e, E, ax, ay, az, dgx, dgy, dgz, x0, y0, z0, r2);
+  }
+  if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
+}
+
 // Kuhn coordinates of corner (i, j, k): X = i+j+k, Y = j+k, Z = k.
 __device__ __forceinline__ bool kuhn_inside(int n, int X, int Y, int Z) {
   return 0 <= Z && Z <= Y && Y <= X && X <= n;
@@ -1309,6 +1415,18 @@ int launch_sweep_macro(const LevelDev& L, const MacroStencil<T>* st_host, const 
   const bool gen = !(fl.physical == 1 && fl.khat_edge == 0);
   SweepArgs<T> am = a;
   if (a.partial) am.partial = a.partial + partial_offset;
+  if (fl.stored) {
+    const dim3 g(L.ntiles_lin);
+    switch (op) {
+      case OP_APPLY: k_interior_stored<T, OP_APPLY><<<g, INTERIOR_BLOCK, 0, s>>>(L, m, am); break;
+      case OP_RESID: k_interior_stored<T, OP_RESID><<<g, INTERIOR_BLOCK, 0, s>>>(L, m, am); break;
+      case OP_JACOBI: k_interior_stored<T, OP_JACOBI><<<g, INTERIOR_BLOCK, 0, s>>>(L, m, am); break;
+      case OP_CHEBY: k_interior_stored<T, OP_CHEBY><<<g, INTERIOR_BLOCK, 0, s>>>(L, m, am); break;
+      case OP_DIAG: k_interior_stored<T, OP_DIAG><<<g, INTERIOR_BLOCK, 0, s>>>(L, m, am); break;
+    }
+    if (partial_count) *partial_count = L.ntiles_lin;
+    return (int)cudaGetLastError();
+  }
   if (fl.nodal) {
     const dim3 g(L.ntiles_lin);
     switch (op) {
@@ -1545,6 +1663,19 @@ int upload_direction_tables() {
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ring_n, rn, sizeof(rn));
   return (int)e;
 }
+
+template <typename T>
+int launch_store_stencil(const LevelDev& L, const MacroStencil<double>* st_host, const OpFlags& fl, const double* k64,
+                         T* out, void* stream) {
+  if (L.ntiles_lin == 0) return 0;
+  for (int m = 0; m < L.nmacro; ++m)
+    k_store_stencil<T><<<L.ntiles_lin, INTERIOR_BLOCK, 0, (cudaStream_t)stream>>>(L, st_host[m], m, fl, k64, out);
+  return (int)cudaGetLastError();
+}
+template int launch_store_stencil<float>(const LevelDev&, const MacroStencil<double>*, const OpFlags&, const double*,
+                                         float*, void*);
+template int launch_store_stencil<double>(const LevelDev&, const MacroStencil<double>*, const OpFlags&, const double*,
+                                          double*, void*);
 
 template int launch_sweep_macro<float>(const LevelDev&, const MacroStencil<float>*, const NodalConsts<float>*, int,
                                        OpKind, const OpFlags&, const SweepArgs<float>&, void*, int64_t, int64_t*);
