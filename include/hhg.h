@@ -180,7 +180,13 @@ hhg_status hhg_residual(hhg_ctx* ctx, int level, hhg_dtype dt, const void* f_dev
  * smoothing (bounds [lo, hi] * lambda_max(D^-1 A), lambda_max from power
  * iterations) and an exact dense solve on the coarsest level (level 2).
  * ------------------------------------------------------------------------- */
-typedef enum { HHG_SMOOTH_JACOBI = 0, HHG_SMOOTH_CHEBYSHEV = 1 } hhg_smoother;
+/* HYBRID_GS is the paper's smoother (Sec. 5): Gauss-Seidel inside the macros, Jacobi-like
+ * across their interfaces.  One step: a point-Jacobi step with weight omega on every node of
+ * the macro skeleton (faces, edges, vertices of the macro mesh), then Gauss-Seidel over the
+ * macro-interior nodes in eight colour passes, colour 4 (i % 2) + 2 (j % 2) + (k % 2) of the
+ * node's lattice coordinates in its macro, in that order, each node taking the newest values
+ * (no two nodes of a colour are neighbours, so a pass updates them all at once). */
+typedef enum { HHG_SMOOTH_JACOBI = 0, HHG_SMOOTH_CHEBYSHEV = 1, HHG_SMOOTH_HYBRID_GS = 2 } hhg_smoother;
 /* Coarse-level coefficient: injection (the reading of Sec. 5's rediscretisation),
  * or a local arithmetic / harmonic mean of the finer level's (for large jumps). */
 typedef enum { HHG_COARSE_INJECT = 0, HHG_COARSE_MEAN = 1, HHG_COARSE_HARMONIC = 2 } hhg_coarse_coeff;
@@ -188,7 +194,7 @@ typedef enum { HHG_COARSE_INJECT = 0, HHG_COARSE_MEAN = 1, HHG_COARSE_HARMONIC =
 typedef struct {
   hhg_smoother smoother;
   int pre, post;          /* smoothing steps before / after the coarse correction (default 2, 2) */
-  double omega;           /* Jacobi damping */
+  double omega;           /* Jacobi damping (also of the skeleton step of HYBRID_GS) */
   double cheby_lo, cheby_hi; /* Chebyshev interval as fractions of lambda_max (default 1/8, 1.1) */
   int power_iters;        /* power iterations for lambda_max */
   hhg_coarse_coeff coarse_coeff; /* coefficient of the coarse levels (default injection) */

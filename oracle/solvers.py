@@ -6,8 +6,9 @@ Sec. 5 solves with geometric multigrid: matrix-free linear interpolation between
 levels, its transpose as restriction, a smoother on every level and a coarse-grid
 solve; coarse operators are the scaled-stencil operators of the coarser meshes
 with the nodal coefficient evaluated at their nodes (which are fine nodes).  The
-smoothers here are point Jacobi and Chebyshev semi-iteration on D^-1 A (Saad,
-Iterative Methods for Sparse Linear Systems, 2nd ed., Sec. 12.3), the coarse
+smoothers here are point Jacobi, the paper's hybrid Gauss-Seidel, and Chebyshev
+semi-iteration on D^-1 A (Saad, Iterative Methods for Sparse Linear Systems, 2nd ed.,
+Sec. 12.3), the coarse
 solve is a dense direct solve, and CG is the textbook preconditioned conjugate
 gradient method (Saad, Alg. 9.1).  Vectors are node-major (N, 3).
 """
@@ -44,6 +45,37 @@ def jacobi(A, dirichlet, f, x, omega, steps):
     x = np.array(x, dtype=np.float64).reshape(-1, 3)
     for _ in range(steps):
         x = x + omega * residual(A, dirichlet, f, x) / D
+    return x
+
+
+def interior_colours(lv: M.Level):
+    """Colour of every macro-interior node, 4 (i % 2) + 2 (j % 2) + (k % 2) of its lattice
+    coordinates (i, j, k) in its macro; -1 on the macro skeleton.  Every stencil direction
+    changes at least one of the three parities, so no two neighbours share a colour."""
+    col = -np.ones(lv.num_nodes, dtype=np.int64)
+    for tab in lv.local_to_node:
+        I, J, K = np.nonzero(tab >= 0)
+        ids = tab[I, J, K]
+        inner = ~np.asarray(lv.skeleton)[ids]
+        col[ids[inner]] = 4 * (I[inner] % 2) + 2 * (J[inner] % 2) + K[inner] % 2
+    return col
+
+
+def hybrid_gauss_seidel(A, dirichlet, skeleton, colours, f, x, omega, steps):
+    """Hybrid Gauss-Seidel (Sec. 5: Gauss-Seidel inside the macros, Jacobi-like across their
+    interfaces).  One step: x_s += omega D_ss^-1 (f - A x)_s at every free skeleton node at once,
+    then for each colour c = 0..7 in turn x_i += D_ii^-1 (f - A x)_i at every macro-interior node
+    of colour c, with the x of that moment."""
+    D = point_diagonal(A, dirichlet)
+    x = np.array(x, dtype=np.float64).reshape(-1, 3)
+    skel = np.asarray(skeleton) & ~np.asarray(dirichlet)
+    for _ in range(steps):
+        r = residual(A, dirichlet, f, x)
+        x[skel] += omega * r[skel] / D[skel]
+        for c in range(8):
+            sel = colours == c
+            r = residual(A, dirichlet, f, x)
+            x[sel] += r[sel] / D[sel]
     return x
 
 
@@ -125,6 +157,9 @@ class Hierarchy:
                 return x
             if smoother == "jacobi":
                 return jacobi(A, d, f, x, omega, steps)
+            if smoother == "hybrid_gs":
+                lv = self.lv[l]
+                return hybrid_gauss_seidel(A, d, lv.skeleton, interior_colours(lv), f, x, omega, steps)
             return chebyshev(A, d, f, x, lam[l], lo, hi, steps)
 
         x = smooth(x, pre)

@@ -30,7 +30,7 @@ class HhgError(RuntimeError):
         self.status = status
 
 
-SMOOTH_JACOBI, SMOOTH_CHEBYSHEV = 0, 1
+SMOOTH_JACOBI, SMOOTH_CHEBYSHEV, SMOOTH_HYBRID_GS = 0, 1, 2
 COARSE_INJECT, COARSE_MEAN, COARSE_HARMONIC = 0, 1, 2
 SOLVE_PCG_JACOBI, SOLVE_MG_CG, SOLVE_IR_MG_CG, SOLVE_MG, SOLVE_STOKES_MINRES, SOLVE_STOKES_IR_MINRES = 0, 1, 2, 3, 4, 5
 SOLVE_IR_FCG_LEARNED, SOLVE_IR_FCG = 6, 7

@@ -92,7 +92,9 @@ struct KeyHash {
 struct LevelHost {
   int level = 0, n = 0;
   int64_t nt = 0, entries = 0;
-  std::vector<int32_t> tiles_int, tiles_all, tiles_lin, tiles_pair;
+  std::vector<int32_t> tiles_int, tiles_all, tiles_lin, tiles_pair, gs_chunks;
+  int32_t gs_ptr[9] = {0};
+  std::vector<int64_t> skel_entries;
   std::vector<int32_t> skel_ptr;
   std::vector<SkelInc> skel_inc;
   std::vector<int8_t> skel_dir;
@@ -113,7 +115,7 @@ struct LevelHost {
   std::vector<int64_t> rent;
   std::vector<double> rw;
   // device
-  DevMem d_tiles_pair;
+  DevMem d_tiles_pair, d_gs_chunks, d_skel_entries;
   DevMem d_tiles_int, d_tiles_all, d_tiles_lin, d_skel_ptr, d_skel_inc, d_skel_dir, d_mask, d_first, d_e2u;
   DevMem d_face_items, d_face_nodes, d_ev_nodes, d_dir_nodes, d_acc32, d_acc64;
   DevMem d_face_items_all, d_face_nodes_all, d_ev_all;

@@ -347,6 +347,21 @@ void build_level(hhg_ctx* c, int level) {
     const int count = M * M / 4;
     for (int start = 0; start < count; start += INTERIOR_BLOCK) L->tiles_pair.push_back((k << 20) | start);
   }
+  // hybrid Gauss-Seidel colour chunks: for colour (ci, cj, ck) the rows j = cj (mod 2) of the
+  // slices k = ck (mod 2), split into chunks of 32 points i = ci (mod 2)
+  for (int col = 0; col < 8; ++col) {
+    const int ci = col >> 2, cj = (col >> 1) & 1, ck = col & 1;
+    L->gs_ptr[col] = (int32_t)L->gs_chunks.size();
+    for (int k = 1; k <= n - 3; ++k) {
+      if ((k & 1) != ck) continue;
+      for (int j = 1; j <= n - 2 - k; ++j) {
+        if ((j & 1) != cj) continue;
+        const int last = n - 1 - j - k;
+        for (int i0 = ci ? 1 : 2; i0 <= last; i0 += 64) L->gs_chunks.push_back((k << 20) | (j << 10) | i0);
+      }
+    }
+  }
+  L->gs_ptr[8] = (int32_t)L->gs_chunks.size();
   // interior points of slice k, enumerated row by row (j = 1..M-1, i = 1..M-j, M = n-1-k),
   // in chunks of INTERIOR_BLOCK
   for (int k = 1; k <= n - 3; ++k) {
@@ -434,6 +449,7 @@ void build_level(hhg_ctx* c, int level) {
     }
     L->unique_dir[u] = L->skel_dir[s];
   }
+  for (const SkelInc& I : L->skel_inc) L->skel_entries.push_back((int64_t)I.macro * L->nt + lattice_index(n, I.i, I.j, I.k));
   L->nfree = L->nunique;
   for (int64_t s = 0; s < nskel; ++s) L->nfree -= L->skel_dir[s];
   L->mask_own.assign(L->entries, 0);
@@ -623,6 +639,8 @@ void upload_level(hhg_ctx* c, LevelHost& L) {
   upload(L.d_tiles_all, L.tiles_all);
   upload(L.d_tiles_lin, L.tiles_lin);
   upload(L.d_tiles_pair, L.tiles_pair);
+  upload(L.d_gs_chunks, L.gs_chunks);
+  upload(L.d_skel_entries, L.skel_entries);
   upload(L.d_skel_ptr, L.skel_ptr);
   upload(L.d_skel_inc, L.skel_inc);
   upload(L.d_skel_dir, L.skel_dir);
@@ -676,6 +694,10 @@ void upload_level(hhg_ctx* c, LevelHost& L) {
   D.tiles_lin = L.d_tiles_lin.as<int32_t>();
   D.ntiles_pair = (int32_t)L.tiles_pair.size();
   D.tiles_pair = L.d_tiles_pair.as<int32_t>();
+  for (int q = 0; q < 9; ++q) D.gs_ptr[q] = L.gs_ptr[q];
+  D.gs_chunks = L.d_gs_chunks.as<int32_t>();
+  D.nskel_entries = (int64_t)L.skel_entries.size();
+  D.skel_entries = L.d_skel_entries.as<int64_t>();
   D.nskel = (int32_t)L.skel_dir.size();
   D.skel_ptr = L.d_skel_ptr.as<int32_t>();
   D.skel_inc = L.d_skel_inc.as<SkelInc>();

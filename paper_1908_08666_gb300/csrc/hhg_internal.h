@@ -191,6 +191,13 @@ struct LevelDev {
   const int32_t* tiles_lin;
   int32_t ntiles_pair;  // 128-pair chunks of the point pairs of each slice (FP32 sweeps): (k << 20) | start
   const int32_t* tiles_pair;
+  // hybrid Gauss-Seidel: chunks of up to 32 macro-interior points of one colour along a row,
+  // (k << 20) | (j << 10) | i0 (points i0, i0 + 2, ...), colour c's at [gs_ptr[c], gs_ptr[c+1]);
+  // colour = 4 (i % 2) + 2 (j % 2) + (k % 2) of the point's lattice coordinates
+  int32_t gs_ptr[9];
+  const int32_t* gs_chunks;
+  int64_t nskel_entries;           // entries of skeleton nodes (every copy)
+  const int64_t* skel_entries;
   const int32_t* tiles_int;  // packed (k << 20) | (j0 << 10) | i0
   const int32_t* tiles_all;
   int32_t nskel;

@@ -271,6 +271,27 @@ void smooth(hhg_ctx* c, int l, int steps, const T* f, T* x) {
       dprev = dnext;
       dnext = dnext == W[4].as<T>() ? W[5].as<T>() : W[4].as<T>();
     }
+  } else if (c->mg.smoother == HHG_SMOOTH_HYBRID_GS) {
+    // hybrid Gauss-Seidel (Sec. 5): per step a damped Jacobi step on the macro skeleton (out of
+    // place, copied back to every copy), then Gauss-Seidel over the macro interiors in eight
+    // colour passes, each in place with the newest values
+    for (int s = 0; s < steps; ++s) {
+      SweepArgs<T> a{};
+      a.x = x;
+      a.f = f;
+      a.k = kptr<T>(L);
+      a.out = oth;
+      a.omega = c->mg.omega;
+      CK(launch_sweep<T>(L.dev, stencils<T>(L), consts_dev<T>(L), OP_JACOBI, c->flags, a, c->stream, 2, 0, nullptr));
+      CK(launch_copy_entries<T>(L.dev.nskel_entries, L.dev.skel_entries, 3, L.entries, oth, x, c->stream));
+      SweepArgs<T> g{};
+      g.x = x;
+      g.f = f;
+      g.k = kptr<T>(L);
+      g.out = x;
+      g.omega = 1.0;
+      for (int col = 0; col < 8; ++col) CK(launch_gs_colour<T>(L.dev, stencils<T>(L), c->flags, g, col, c->stream));
+    }
   } else {
     for (int s = 0; s < steps; ++s) {
       SweepArgs<T> a{};
@@ -1086,7 +1107,8 @@ hhg_status hhg_set_mg_params(hhg_ctx* c, const hhg_mg_params* p) {
   return guard(c, [&] {
     c->drop_graphs();
     if (!p) THROW(HHG_ERR_ARG, "null params");
-    if (p->smoother != HHG_SMOOTH_JACOBI && p->smoother != HHG_SMOOTH_CHEBYSHEV) THROW(HHG_ERR_ARG, "smoother");
+    if (p->smoother != HHG_SMOOTH_JACOBI && p->smoother != HHG_SMOOTH_CHEBYSHEV && p->smoother != HHG_SMOOTH_HYBRID_GS)
+      THROW(HHG_ERR_ARG, "smoother");
     if (p->pre < 0 || p->post < 0 || p->pre + p->post == 0) THROW(HHG_ERR_ARG, "smoothing steps");
     if (!(p->omega > 0.0 && p->omega < 2.0)) THROW(HHG_ERR_ARG, "omega");
     if (!(p->cheby_lo > 0.0 && p->cheby_hi > p->cheby_lo)) THROW(HHG_ERR_ARG, "Chebyshev interval");

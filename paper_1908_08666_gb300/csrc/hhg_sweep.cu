@@ -261,19 +261,36 @@ __device__ __forceinline__ void stokes_epilogue(const SweepArgs<T>& a, int64_t e
 // STK = 1: the Stokes saddle operator [[A(mu), B^T], [B, C]] on (u, v, w, p) (Sec. 5.2),
 // the velocity block being the scaled-stencil operator of the 2 mu eps(u) form.
 // KB = 1 (FP32, default operator only): the coefficient is read as BF16 bits from a.k16.
-template <typename T, int OP, int GEN, int STK = 0, int KB = 0>
+// GS = 1 (a colour pass of the hybrid Gauss-Seidel smoother): the block takes four chunks of
+// colour `colour`'s list (a warp each; lane l the point i0 + 2 l of the chunk's row) instead
+// of a slice chunk.
+template <typename T, int OP, int GEN, int STK = 0, int KB = 0, int GS = 0>
 __global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, const MacroStencil<T> st,
                                                               const int macro, const OpFlags fl,
-                                                              const SweepArgs<T> a) {
-  const int32_t tile = L.tiles_lin[blockIdx.x];
+                                                              const SweepArgs<T> a, const int colour) {
   const int n = L.n;
-  const int k = tile >> 20;
-  const int M = n - 1 - k;
-  const int t = (tile & 0xFFFFF) + threadIdx.x;
+  int i = 0, j = 0, k = 0;
+  bool valid;
+  if constexpr (GS) {
+    const int q = blockIdx.x * (INTERIOR_BLOCK / 32) + (threadIdx.x >> 5);
+    valid = q < L.gs_ptr[colour + 1] - L.gs_ptr[colour];
+    if (valid) {
+      const int32_t ch = L.gs_chunks[L.gs_ptr[colour] + q];
+      k = ch >> 20;
+      j = (ch >> 10) & 0x3FF;
+      i = (ch & 0x3FF) + 2 * (threadIdx.x & 31);
+      valid = i + j + k <= n - 1;
+    }
+  } else {
+    const int32_t tile = L.tiles_lin[blockIdx.x];
+    k = tile >> 20;
+    const int M = n - 1 - k;
+    const int t = (tile & 0xFFFFF) + threadIdx.x;
+    valid = t < (M - 1) * M / 2;
+    if (valid) slice_decode(M, t, j, i);
+  }
   double r2 = 0.0;
-  if (t < (M - 1) * M / 2) {
-    int j, i;
-    slice_decode(M, t, j, i);
+  if (valid) {
     const int64_t E = L.entries;
     const int64_t base = (int64_t)macro * L.nt;
     // starts of the seven lattice rows the stencil touches (plus i)
@@ -1398,9 +1415,9 @@ int launch_interior(bool gen, const LevelDev& L, const MacroStencil<T>& st, int 
   } else {
     if (L.ntiles_lin == 0) return 0;
     if (gen)
-      k_interior<T, OP, 1><<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st, m, fl, am);
+      k_interior<T, OP, 1><<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st, m, fl, am, 0);
     else
-      k_interior<T, OP, 0><<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st, m, fl, am);
+      k_interior<T, OP, 0><<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st, m, fl, am, 0);
     return L.ntiles_lin;
   }
 }
@@ -1558,7 +1575,7 @@ int launch_residual_noalloc(const LevelDev& L, const MacroStencil<T>* st_host, c
   for (int m = 0; m < L.nmacro && L.ntiles_lin > 0; ++m) {
     SweepArgs<T> am = a;
     am.partial = scratch + used;
-    (gen ? k_interior<T, OP_RESID, 1> : k_interior<T, OP_RESID, 0>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st_host[m], m, fl, am);
+    (gen ? k_interior<T, OP_RESID, 1> : k_interior<T, OP_RESID, 0>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, st_host[m], m, fl, am, 0);
     used += L.ntiles_lin;
   }
   if (L.nface_nodes > 0) {
@@ -1608,10 +1625,10 @@ int launch_stokes_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const
     cudaStream_t sm = m % 2 ? s_odd : s;
     if (op == OP_APPLY)
       (gen ? k_interior<T, OP_APPLY, 1, 1> : k_interior<T, OP_APPLY, 0, 1>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, sm>>>(
-          L, st_host[m], m, fl, am);
+          L, st_host[m], m, fl, am, 0);
     else
       (gen ? k_interior<T, OP_RESID, 1, 1> : k_interior<T, OP_RESID, 0, 1>)<<<L.ntiles_lin, INTERIOR_BLOCK, 0, sm>>>(
-          L, st_host[m], m, fl, am);
+          L, st_host[m], m, fl, am, 0);
     used += L.ntiles_lin;
   }
   if (L.nface_items_all > 0)
@@ -1663,6 +1680,29 @@ int upload_direction_tables() {
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ring_n, rn, sizeof(rn));
   return (int)e;
 }
+
+template <typename T>
+int launch_gs_colour(const LevelDev& L, const MacroStencil<T>* st_host, const OpFlags& fl, const SweepArgs<T>& a,
+                     int colour, void* stream) {
+  const int count = L.gs_ptr[colour + 1] - L.gs_ptr[colour];
+  if (count == 0) return 0;
+  const int per = INTERIOR_BLOCK / 32;
+  const dim3 g((count + per - 1) / per);
+  const bool gen = !(fl.physical == 1 && fl.khat_edge == 0);
+  for (int m = 0; m < L.nmacro; ++m) {
+    if (gen)
+      k_interior<T, OP_JACOBI, 1, 0, 0, 1><<<g, INTERIOR_BLOCK, 0, (cudaStream_t)stream>>>(L, st_host[m], m, fl, a,
+                                                                                            colour);
+    else
+      k_interior<T, OP_JACOBI, 0, 0, 0, 1><<<g, INTERIOR_BLOCK, 0, (cudaStream_t)stream>>>(L, st_host[m], m, fl, a,
+                                                                                            colour);
+  }
+  return (int)cudaGetLastError();
+}
+template int launch_gs_colour<float>(const LevelDev&, const MacroStencil<float>*, const OpFlags&,
+                                     const SweepArgs<float>&, int, void*);
+template int launch_gs_colour<double>(const LevelDev&, const MacroStencil<double>*, const OpFlags&,
+                                      const SweepArgs<double>&, int, void*);
 
 template <typename T>
 int launch_store_stencil(const LevelDev& L, const MacroStencil<double>* st_host, const OpFlags& fl, const double* k64,

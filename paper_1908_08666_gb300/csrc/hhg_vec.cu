@@ -597,6 +597,24 @@ HHG_INST(double)
 template int launch_convert<double, float>(int64_t, const double*, float*, void*);
 template int launch_convert<float, double>(int64_t, const float*, double*, void*);
 
+template <typename T>
+__global__ void k_copy_entries(int64_t count, const int64_t* __restrict__ idx, int comps, int64_t E,
+                               const T* __restrict__ src, T* __restrict__ dst) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= count) return;
+  const int64_t e = idx[u];
+  for (int c = 0; c < comps; ++c) dst[c * E + e] = src[c * E + e];
+}
+
+template <typename T>
+int launch_copy_entries(int64_t count, const int64_t* idx, int comps, int64_t E, const T* src, T* dst, void* stream) {
+  if (count == 0) return 0;
+  k_copy_entries<T><<<(unsigned)((count + 255) / 256), 256, 0, (cudaStream_t)stream>>>(count, idx, comps, E, src, dst);
+  return (int)cudaGetLastError();
+}
+template int launch_copy_entries<float>(int64_t, const int64_t*, int, int64_t, const float*, float*, void*);
+template int launch_copy_entries<double>(int64_t, const int64_t*, int, int64_t, const double*, double*, void*);
+
 // ---------------------------------------------------------------------------
 // FP32 FMA issue-rate probe (a measurement aid: the denominator of the ALU roofline
 // of the stencil kernels).  Every thread runs 8 independent FMA chains a <- a * b + c

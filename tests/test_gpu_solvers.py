@@ -61,6 +61,39 @@ def test_diagonal_and_transfers(name, request):
         assert np.abs(p.from_lib(l - 1, rc) - want).max() <= 1e-13 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("name", ["cube4", "skew4"])
+def test_hybrid_gauss_seidel_smoother_and_vcycle(name, request):
+    """The paper's smoother (Sec. 5): hybrid Gauss-Seidel steps (skeleton Jacobi with weight
+    omega, then eight colour passes over the macro interiors) and a V(3,3) cycle with it,
+    against oracle.solvers.hybrid_gauss_seidel (FP64 to 1e-11, FP32 to 2e-5)."""
+    p = request.getfixturevalue(name)
+    t = p.ctx.torch
+    h = p.ctx.h
+    l = 4
+    lv, A = p.H.lv[l], p.H.A[l]
+    col = S.interior_colours(lv)
+    f = hi.node_noise(lv.coords, seed=31)
+    x0 = hi.node_noise(lv.coords, seed=32)
+    try:
+        B.hhg_set_mg_params(h, smoother=B.SMOOTH_HYBRID_GS, omega=0.6, pre=3, post=3)
+        for steps in (1, 2):
+            want = S.hybrid_gauss_seidel(A, lv.dirichlet, lv.skeleton, col, f, x0, 0.6, steps)
+            x = p.to_lib(l, x0, t.float64)
+            B.hhg_smooth(h, l, B.F64, steps, p.to_lib(l, f, t.float64), x)
+            assert np.abs(p.from_lib(l, x) - want).max() <= 1e-11 * np.abs(want).max()
+            x32 = p.to_lib(l, x0, t.float32)
+            B.hhg_smooth(h, l, B.F32, steps, p.to_lib(l, f, t.float32), x32)
+            assert np.abs(p.from_lib(l, x32) - want).max() <= 2e-5 * np.abs(want).max()
+        f2 = f.copy()
+        f2[lv.dirichlet] = 0.0
+        x = t.zeros(3 * B.hhg_num_nodes(h, l)[0], dtype=t.float64, device="cuda")
+        B.hhg_vcycle(h, l, B.F64, p.to_lib(l, f2, t.float64), x)
+        want = p.H.vcycle(l, f2, np.zeros_like(f2), "hybrid_gs", 3, 3, omega=0.6)
+        assert np.abs(p.from_lib(l, x) - want).max() <= 1e-10 * np.abs(want).max()
+    finally:
+        B.hhg_set_mg_params(h)
+
+
 def test_lambda_estimate(cube4):
     p = cube4
     for l in (3, 4):

@@ -116,3 +116,89 @@ def test_vcycle_contracts():
             x = H.vcycle(l, f, x, "chebyshev", 2, 2, lam)
         r3 = np.linalg.norm(S.residual(A, lv.dirichlet, f, x))
         assert (r3 / r0) ** (1 / 3) < 0.35
+
+
+def test_colouring_separates_neighbours():
+    """No two macro-interior nodes of one colour share an element (so a colour pass of the
+    hybrid Gauss-Seidel smoother is independent of its order), and all eight colours occur."""
+    for builder, level in ((hi.kuhn_cube, 3), (hi.skewed_pair, 3)):
+        xyz, tets = builder()
+        lv = mesh.build_level(mesh.MacroMesh.build(xyz, tets), level)
+        col = S.interior_colours(lv)
+        assert set(col[~lv.skeleton].tolist()) == set(range(8)) and np.all(col[lv.skeleton] == -1)
+        E = lv.elems
+        for a in range(4):
+            for b in range(a + 1, 4):
+                ca, cb = col[E[:, a]], col[E[:, b]]
+                assert not np.any((ca >= 0) & (ca == cb))
+
+
+def test_hybrid_gauss_seidel_is_gauss_seidel_inside_a_macro():
+    """On the single unit macro tetrahedron every free node is macro-interior, so one hybrid
+    step is the Gauss-Seidel step x + M^-1 (f - A x) with M = D + L: D the point diagonal, L the
+    couplings to the nodes of earlier colours (the nodes taken colour by colour; the three
+    components of a node are updated together, so their coupling stays on the right-hand side).
+    Here M is assembled from A and the triangular system solved directly; and the step lowers
+    the energy norm of the error."""
+    H = _hier(hi.unit_tet, [3], lambda c: 1.0 + 0.5 * np.sin(3 * c[:, 0]) * np.cos(2 * c[:, 1]))
+    lv, A = H.lv[3], H.A[3]
+    d = lv.dirichlet
+    col = S.interior_colours(lv)
+    assert not np.any(lv.skeleton & ~d)
+    f = hi.node_noise(lv.coords, seed=3)
+    f[d] = 0.0
+    x0 = hi.node_noise(lv.coords, seed=4)
+    x0[d] = 0.0
+    x1 = S.hybrid_gauss_seidel(A, d, lv.skeleton, col, f, x0, 0.7, 1)
+    free = np.nonzero(~d)[0]
+    order = free[np.argsort(col[free], kind="stable")]
+    dofs = (3 * order[:, None] + np.arange(3)[None, :]).reshape(-1)
+    Aff = A.tocsr()[dofs][:, dofs].tocoo()
+    cdof = np.repeat(col[order], 3)
+    lower = cdof[Aff.row] > cdof[Aff.col]
+    diag = Aff.row == Aff.col
+    sel = lower | diag
+    M = sp.coo_matrix((Aff.data[sel], (Aff.row[sel], Aff.col[sel])), shape=Aff.shape).tocsr()
+    r = (f.reshape(-1) - A @ x0.reshape(-1))[dofs]
+    want = x0.reshape(-1).copy()
+    want[dofs] += sp.linalg.spsolve_triangular(M, r, lower=True)
+    assert np.abs(x1.reshape(-1) - want).max() < 1e-12 * np.abs(want).max()
+    xs = S.direct_solve(A, d, f, np.zeros_like(f))
+    en = lambda x: float((x - xs).reshape(-1) @ (A @ (x - xs).reshape(-1)))
+    assert en(x1) < en(x0)
+
+
+def test_hybrid_gs_vcycles_contract():
+    """Stationary V(3,3) cycles with the hybrid Gauss-Seidel smoother (the paper's solver,
+    Sec. 5) on the 6-macro cube reduce the residual by a level-independent factor."""
+    H = _hier(hi.kuhn_cube, [2, 3, 4], lambda c: 1.0 + 0.5 * np.sin(3 * c[:, 0]) * np.cos(2 * c[:, 1]))
+    for l in (3, 4):
+        lv, A = H.lv[l], H.A[l]
+        f = hi.node_noise(lv.coords, seed=2)
+        f[lv.dirichlet] = 0.0
+        x = np.zeros_like(f)
+        r0 = np.linalg.norm(S.residual(A, lv.dirichlet, f, x))
+        for _ in range(3):
+            x = H.vcycle(l, f, x, "hybrid_gs", 3, 3, omega=2 / 3)
+        r3 = np.linalg.norm(S.residual(A, lv.dirichlet, f, x))
+        assert (r3 / r0) ** (1 / 3) < 0.3
+
+
+def test_hybrid_gauss_seidel_skeleton_step_is_jacobi():
+    """Across the macro interfaces the step is Jacobi-like (Sec. 5): on the 6-macro cube the
+    free skeleton nodes move by exactly omega D^-1 (f - A x) of the old iterate, and the
+    macro-interior nodes by a Gauss-Seidel step that differs from the Jacobi one."""
+    H = _hier(hi.kuhn_cube, [3], lambda c: 1.0 + c[:, 0] * c[:, 2])
+    lv, A = H.lv[3], H.A[3]
+    d = lv.dirichlet
+    f = hi.node_noise(lv.coords, seed=5)
+    f[d] = 0.0
+    x0 = hi.node_noise(lv.coords, seed=6)
+    x0[d] = 0.0
+    x1 = S.hybrid_gauss_seidel(A, d, lv.skeleton, S.interior_colours(lv), f, x0, 0.6, 1)
+    jac = x0 + 0.6 * S.residual(A, d, f, x0) / S.point_diagonal(A, d)
+    skel = lv.skeleton & ~d
+    inner = ~lv.skeleton
+    assert skel.any() and np.abs(x1[skel] - jac[skel]).max() < 1e-14 * np.abs(jac).max()
+    assert np.abs(x1[inner] - (x0 + S.residual(A, d, f, x0) / S.point_diagonal(A, d))[inner]).max() > 1e-3
+    assert np.array_equal(x1[d], x0[d])
