@@ -531,6 +531,14 @@ hhg_status hhg_apply_host(hhg_ctx* ctx, int level, hhg_dtype dt, const void* x_h
  * the stream. */
 hhg_status hhg_profile(hhg_ctx* ctx, int enable, double* ms_host, int64_t* launches_host);
 
+/* Kernel of the macro-interior sweeps of the scaled-stencil variants (results equal up to
+ * rounding): 0 (default) one thread per point for FP64 and, for FP32, one thread per pair of
+ * neighbouring points of a lattice row in packed two-lane FP32 arithmetic, both reading the
+ * stencil neighbours straight from global memory; 1 a block per 30 x 4 x 4 box of lattice
+ * points that stages the box plus its one-point halo in shared memory (asynchronous copies)
+ * and reads every neighbour from there.  Errors: ARG for another value. */
+hhg_status hhg_set_interior_kernel(hhg_ctx* ctx, int kernel);
+
 /* FP32 FMA issue-rate probe, a measurement aid with no counterpart in the paper: the
  * ALU roofline denominator of the FP32 stencil kernels.  Launches, on the context's
  * stream, one kernel of (SMs x 8) blocks of 256 threads, each thread running 8

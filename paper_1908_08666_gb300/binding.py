@@ -134,6 +134,7 @@ _SIGS = {
     "hhg_picard": [C.c_void_p, C.POINTER(hhg_picard_opts), C.c_void_p, C.c_void_p, C.POINTER(hhg_picard_report)],
     "hhg_solve": [C.c_void_p, C.POINTER(hhg_solve_opts), C.c_void_p, C.c_void_p, C.POINTER(hhg_solve_report)],
     "hhg_profile": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+    "hhg_set_interior_kernel": [C.c_void_p, C.c_int],
     "hhg_fp32_fma_probe": [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)],
     "hhg_residual_noalloc": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.POINTER(C.c_double)],
@@ -297,6 +298,11 @@ def hhg_profile(ctx, enable, read=False):
         return ms, nl
     _check(ctx, load().hhg_profile(ctx, int(enable), None, None))
     return None
+
+
+def hhg_set_interior_kernel(ctx, kernel):
+    """0: direct global loads (FP32 on point pairs, packed arithmetic), 1: shared-memory tile."""
+    _check(ctx, load().hhg_set_interior_kernel(ctx, int(kernel)))
 
 
 def hhg_fp32_fma_probe(ctx, packed, iterations, out):

@@ -92,7 +92,7 @@ struct KeyHash {
 struct LevelHost {
   int level = 0, n = 0;
   int64_t nt = 0, entries = 0;
-  std::vector<int32_t> tiles_int, tiles_all, tiles_lin, tiles_pair, gs_chunks;
+  std::vector<int32_t> tiles_int, tiles_all, tiles_lin, tiles_pair, tiles3, gs_chunks;
   int32_t gs_ptr[9] = {0};
   std::vector<int64_t> skel_entries;
   std::vector<int32_t> skel_ptr;
@@ -115,7 +115,7 @@ struct LevelHost {
   std::vector<int64_t> rent;
   std::vector<double> rw;
   // device
-  DevMem d_tiles_pair, d_gs_chunks, d_skel_entries;
+  DevMem d_tiles_pair, d_tiles3, d_gs_chunks, d_skel_entries;
   DevMem d_tiles_int, d_tiles_all, d_tiles_lin, d_skel_ptr, d_skel_inc, d_skel_dir, d_mask, d_first, d_e2u;
   DevMem d_face_items, d_face_nodes, d_ev_nodes, d_dir_nodes, d_acc32, d_acc64;
   DevMem d_face_items_all, d_face_nodes_all, d_ev_all;
@@ -303,7 +303,7 @@ inline int64_t max_partials(hhg_ctx* c) {
   int64_t mx = 1024;
   for (int l = c->level_min; l <= c->level_max; ++l) {
     const LevelHost& L = *c->levels[l];
-    mx = std::max<int64_t>(mx, (int64_t)L.tiles_lin.size() * (int64_t)c->tets.size() +
+    mx = std::max<int64_t>(mx, (int64_t)std::max(L.tiles_lin.size(), L.tiles3.size()) * (int64_t)c->tets.size() +
                                    (L.face_nodes_all.size() + 127) / 128 + L.ev_all.size() + 8);
   }
   return mx;

@@ -347,6 +347,11 @@ void build_level(hhg_ctx* c, int level) {
     const int count = M * M / 4;
     for (int start = 0; start < count; start += INTERIOR_BLOCK) L->tiles_pair.push_back((k << 20) | start);
   }
+  // boxes of TILE3_I x TILE3_J x TILE3_K lattice points (i, j, k) with at least one
+  // macro-interior point, for the shared-memory tile kernel
+  for (int k0 = 1; k0 <= n - 3; k0 += TILE3_K)
+    for (int j0 = 1; j0 <= n - 2 - k0; j0 += TILE3_J)
+      for (int i0 = 1; i0 <= n - 1 - k0 - j0; i0 += TILE3_I) L->tiles3.push_back((k0 << 20) | (j0 << 10) | i0);
   // hybrid Gauss-Seidel colour chunks: for colour (ci, cj, ck) the rows j = cj (mod 2) of the
   // slices k = ck (mod 2), split into chunks of 32 points i = ci (mod 2)
   for (int col = 0; col < 8; ++col) {
@@ -639,6 +644,7 @@ void upload_level(hhg_ctx* c, LevelHost& L) {
   upload(L.d_tiles_all, L.tiles_all);
   upload(L.d_tiles_lin, L.tiles_lin);
   upload(L.d_tiles_pair, L.tiles_pair);
+  upload(L.d_tiles3, L.tiles3);
   upload(L.d_gs_chunks, L.gs_chunks);
   upload(L.d_skel_entries, L.skel_entries);
   upload(L.d_skel_ptr, L.skel_ptr);
@@ -694,6 +700,8 @@ void upload_level(hhg_ctx* c, LevelHost& L) {
   D.tiles_lin = L.d_tiles_lin.as<int32_t>();
   D.ntiles_pair = (int32_t)L.tiles_pair.size();
   D.tiles_pair = L.d_tiles_pair.as<int32_t>();
+  D.ntiles3 = (int32_t)L.tiles3.size();
+  D.tiles3 = L.d_tiles3.as<int32_t>();
   for (int q = 0; q < 9; ++q) D.gs_ptr[q] = L.gs_ptr[q];
   D.gs_chunks = L.d_gs_chunks.as<int32_t>();
   D.nskel_entries = (int64_t)L.skel_entries.size();
@@ -1181,6 +1189,14 @@ hhg_status hhg_profile(hhg_ctx* c, int enable, double* ms_host, int64_t* launche
       c->prof_launches[part] = 0;
     }
     c->prof = enable != 0;
+  });
+}
+
+hhg_status hhg_set_interior_kernel(hhg_ctx* c, int kernel) {
+  return guard(c, [&] {
+    if (kernel != 0 && kernel != 1) THROW(HHG_ERR_ARG, "interior kernel must be 0 or 1");
+    c->drop_graphs();
+    c->flags.tile = kernel;
   });
 }
 

@@ -191,6 +191,8 @@ struct LevelDev {
   const int32_t* tiles_lin;
   int32_t ntiles_pair;  // 128-pair chunks of the point pairs of each slice (FP32 sweeps): (k << 20) | start
   const int32_t* tiles_pair;
+  int32_t ntiles3;      // boxes of the shared-memory tile kernel: (k0 << 20) | (j0 << 10) | i0
+  const int32_t* tiles3;
   // hybrid Gauss-Seidel: chunks of up to 32 macro-interior points of one colour along a row,
   // (k << 20) | (j << 10) | i0 (points i0, i0 + 2, ...), colour c's at [gs_ptr[c], gs_ptr[c+1]);
   // colour = 4 (i % 2) + 2 (j % 2) + (k % 2) of the point's lattice coordinates
@@ -224,6 +226,9 @@ struct LevelDev {
 };
 
 constexpr int INTERIOR_BLOCK = 128;
+// boxes of the shared-memory tile kernel (k_interior_tile): 30 x 4 x 4 lattice points, so that a
+// box row plus its halo is 32 points, one warp
+constexpr int TILE3_I = 30, TILE3_J = 4, TILE3_K = 4;
 constexpr int TILE_I = 32;
 constexpr int TILE_J = 4;
 

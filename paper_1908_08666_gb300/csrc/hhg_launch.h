@@ -15,6 +15,7 @@ struct OpFlags {
   int practical;  // 1: skeleton rows are the a_h rows; 0: symmetric interface rows
   int nodal = 0;  // 1: macro-interior rows by nodal integration a_h (the NODAL variant)
   int stored = 0; // 1: macro-interior rows from the stored stencil blocks (the STORED variant)
+  int tile = 0;   // 1: macro-interior sweeps by the shared-memory tile kernel (k_interior_tile)
 };
 
 // Arguments of one stencil sweep.  Vectors are component-major over the level

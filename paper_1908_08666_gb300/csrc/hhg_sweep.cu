@@ -551,6 +551,161 @@ __global__ void __launch_bounds__(INTERIOR_BLOCK, 4) k_interior_pair(const Level
   if (OP == OP_RESID && a.partial != nullptr) block_sum_store<float>(r2, a.partial + blockIdx.x);
 }
 
+// Macro-interior sweep from a shared-memory tile.  Each block takes one box of
+// T3_I x T3_J x T3_K lattice points (i, j, k) of one macro and stages the box plus a
+// one-point halo in shared memory as (x, y, z, k) quadruples: one coalesced global read per
+// array and point (a warp per 32-point region row), then one 16-byte shared-memory read per
+// stencil neighbour (two in FP64), at offsets fixed at compile time.  The macro interior
+// i, j, k >= 1, i + j + k <= n - 1 is a tetrahedron, so boxes along its slanted face are
+// partly empty; the threads take the box's interior points densely (through a table of
+// (row, i) built with the staging), so no lane idles on an empty point.  The arithmetic per
+// point is interior_row, as in k_interior.
+constexpr int T3_I = TILE3_I, T3_J = TILE3_J, T3_K = TILE3_K;
+constexpr int R3_I = T3_I + 2, R3_J = T3_J + 2, R3_K = T3_K + 2;
+constexpr int T3_ROWS = T3_J * T3_K;
+constexpr int T3_THREADS = 256;
+static_assert(R3_I == 32, "a region row is one warp");
+
+template <typename T>
+struct alignas(4 * sizeof(T)) Quad {
+  T x, y, z, k;
+};
+
+// shared-memory offset of stencil direction d in the staged region
+__device__ __forceinline__ int region_offset(int d) {
+  return (dir_dk(d) * R3_J + dir_dj(d)) * R3_I + dir_di(d);
+}
+
+// shared-memory reads at a 32-bit shared-window address
+__device__ __forceinline__ float lds(uint32_t a, float) {
+  float v;
+  asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ double lds(uint32_t a, double) {
+  double v;
+  asm("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ Diff3<float> lds3(uint32_t a, float) {
+  float x, y, z, w;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x), "=f"(y), "=f"(z), "=f"(w) : "r"(a));
+  return {x, y, z};
+}
+__device__ __forceinline__ Diff3<double> lds3(uint32_t a, double) {
+  double x, y, z;
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%3];\n\tld.shared.f64 %2, [%4];" : "=d"(x), "=d"(y), "=d"(z) : "r"(a), "r"(a + 16));
+  return {x, y, z};
+}
+
+// Neighbour values of a point of the staged region (a: shared address of the point's own
+// quadruple): the 14 coefficients are held in registers, the vector values are read from
+// shared memory per direction pair; next_pair() redefines the address for the compiler, so
+// the reads of later pairs cannot move above it (which would hold all 42 values in registers
+// at once).
+template <typename T>
+struct SmemNeighbours {
+  uint32_t a;
+  T x0, y0, z0;
+  T kk[NDIR];
+  __device__ __forceinline__ T k(int d) const { return kk[d]; }
+  __device__ __forceinline__ Diff3<T> diff(int d) const {
+    const Diff3<T> v = lds3(a + region_offset(d) * (int)sizeof(Quad<T>), T());
+    return {v.x - x0, v.y - y0, v.z - z0};
+  }
+  __device__ __forceinline__ void next_pair() { asm volatile("" : "+r"(a)); }
+};
+
+// asynchronous copy of one FP32 / FP64 element from global to shared memory (zero-filled when
+// !valid: nothing is read then)
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(sizeof(T)),
+               "r"(valid ? (int)sizeof(T) : 0));
+}
+
+template <typename T, int OP, int GEN, int KB>
+__global__ void __launch_bounds__(T3_THREADS, sizeof(T) == 4 ? 3 : 1) k_interior_tile(const LevelDev L,
+                                                                                          const MacroStencil<T> st,
+                                                                                          const int macro,
+                                                                                          const OpFlags fl,
+                                                                                          const SweepArgs<T> a) {
+  __shared__ Quad<T> q[R3_K * R3_J * R3_I];
+  __shared__ int row_start[R3_K * R3_J];  // entry (in the macro) of point i = 0 of each region row
+  __shared__ int row_first[T3_ROWS + 1];  // dense numbering of the box's interior points, per row
+  __shared__ uint16_t point[T3_ROWS * T3_I];  // dense number -> (box row << 8) | i - i0
+  const int32_t tile = L.tiles3[blockIdx.x];
+  const int n = L.n;
+  const int i0 = tile & 0x3FF, j0 = (tile >> 10) & 0x3FF, k0 = tile >> 20;
+  const int64_t E = L.entries;
+  const int64_t base = (int64_t)macro * L.nt;
+  const int tid = threadIdx.x;
+  if (tid < R3_K * R3_J) {
+    const int j = j0 - 1 + tid % R3_J, k = k0 - 1 + tid / R3_J;
+    row_start[tid] = (j >= 0 && k >= 0 && j + k <= n) ? lattice_index32(n, 0, j, k) : -1;
+  }
+  if (tid == 0) {
+    // interior points of box row (tj, tk): i0 .. min(i0 + T3_I - 1, n - 1 - j - k)
+    int acc = 0;
+    for (int r = 0; r < T3_ROWS; ++r) {
+      row_first[r] = acc;
+      const int j = j0 + r % T3_J, k = k0 + r / T3_J;
+      acc += max(0, min(T3_I, n - j - k - i0));
+    }
+    row_first[T3_ROWS] = acc;
+  }
+  __syncthreads();
+  for (int s = tid; s < T3_ROWS * T3_I; s += T3_THREADS) {
+    const int r = s / T3_I, ti = s - r * T3_I;
+    if (row_first[r] + ti < row_first[r + 1]) point[row_first[r] + ti] = (uint16_t)((r << 8) | ti);
+  }
+  // stage the region: warp w takes region rows w, w + 8, ...; lane l the point i0 - 1 + l,
+  // copied asynchronously (cp.async) into the fields of its quadruple; points outside the
+  // macro's lattice are zero-filled (no interior point reads them)
+  {
+    const int lane = tid & 31;
+    const int i = i0 - 1 + lane;
+    const T* __restrict__ X = a.x + base;
+    for (int r = tid >> 5; r < R3_K * R3_J; r += T3_THREADS / 32) {
+      const int start = row_start[r];
+      const int imax = n - (j0 - 1 + r % R3_J) - (k0 - 1 + r / R3_J);
+      const bool valid = start >= 0 && i <= imax;
+      const int64_t off = valid ? (int64_t)start + i : 0;
+      Quad<T>* dst = q + r * R3_I + lane;
+      cp_async_elem(&dst->x, X + off, valid);
+      cp_async_elem(&dst->y, X + E + off, valid);
+      cp_async_elem(&dst->z, X + 2 * E + off, valid);
+      if constexpr (KB) {
+        dst->k = valid ? (T)__uint_as_float((uint32_t)a.k16[base + off] << 16) : (T)0;
+      } else {
+        cp_async_elem(&dst->k, a.k + base + off, valid);
+      }
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+  }
+  __syncthreads();
+  double r2 = 0.0;
+  const int count = row_first[T3_ROWS];
+#pragma unroll 1
+  for (int t = tid; t < count; t += T3_THREADS) {
+    const int pr = point[t];
+    const int r = pr >> 8, ti = pr & 0xFF;
+    const int tj = r % T3_J, tk = r / T3_J;
+    const Quad<T>* c = q + ((tk + 1) * R3_J + (tj + 1)) * R3_I + (ti + 1);
+    const Quad<T> c0 = c[0];
+    SmemNeighbours<T> nb{(uint32_t)__cvta_generic_to_shared(c), c0.x, c0.y, c0.z, {}};
+#pragma unroll
+    for (int d = 0; d < NDIR; ++d) nb.kk[d] = lds(nb.a + region_offset(d) * (int)sizeof(Quad<T>) + 3 * (int)sizeof(T), T());
+    T ax, ay, az, dgx, dgy, dgz;
+    interior_row<T, OP == OP_JACOBI || OP == OP_CHEBY || OP == OP_DIAG, GEN>(st, fl, nb, c0.k, ax, ay, az, dgx, dgy,
+                                                                             dgz);
+    const int64_t e = base + row_start[(tk + 1) * R3_J + (tj + 1)] + i0 + ti;
+    epilogue<T, OP>(a, e, E, ax, ay, az, dgx, dgy, dgz, c0.x, c0.y, c0.z, r2);
+  }
+  if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
+}
+
 // Macro-interior rows by nodal integration (the NODAL variant, eq. nodalintegration):
 // (A x)_i = sum over the 24 elements t around i of kbar^t sum_{b != a} K^t_ab (x_b - x_i),
 // kbar^t the mean of the element's 4 nodal coefficients, K^t the element stiffness of the
@@ -1402,6 +1557,16 @@ inline MacroStencil<float2> lane_pairs(const MacroStencil<float>& st) {
 template <typename T, int OP>
 int launch_interior(bool gen, const LevelDev& L, const MacroStencil<T>& st, int m, const OpFlags& fl,
                     const SweepArgs<T>& am, cudaStream_t s) {
+  if (fl.tile) {
+    if (L.ntiles3 == 0) return 0;
+    if (am.k16 && !gen)
+      k_interior_tile<T, OP, 0, 1><<<L.ntiles3, T3_THREADS, 0, s>>>(L, st, m, fl, am);
+    else if (gen)
+      k_interior_tile<T, OP, 1, 0><<<L.ntiles3, T3_THREADS, 0, s>>>(L, st, m, fl, am);
+    else
+      k_interior_tile<T, OP, 0, 0><<<L.ntiles3, T3_THREADS, 0, s>>>(L, st, m, fl, am);
+    return L.ntiles3;
+  }
   if constexpr (std::is_same<T, float>::value) {
     if (L.ntiles_pair == 0) return 0;
     const MacroStencil<float2> st2 = lane_pairs(st);

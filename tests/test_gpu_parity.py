@@ -59,6 +59,9 @@ CASES = [
     ("cube_l4_practical", hi.kuhn_cube, 4, {"iface": "practical"}),
     ("cube_l4_nodal", hi.kuhn_cube, 4, {"variant": "nodal"}),
     ("cube_l4_stored", hi.kuhn_cube, 4, {"variant": "stored"}),
+    ("cube_l4_tile", hi.kuhn_cube, 4, {"kernel": 1}),
+    ("skewed_l4_tile", hi.skewed_pair, 4, {"kernel": 1}),
+    ("cube_l4_unphysical_tile", hi.kuhn_cube, 4, {"variant": "unphysical", "kernel": 1}),
     ("skewed_l4_stored", hi.skewed_pair, 4, {"variant": "stored"}),
     ("skewed_l4_nodal", hi.skewed_pair, 4, {"variant": "nodal"}),
     ("skewed_l4", hi.skewed_pair, 4, {}),
@@ -82,6 +85,7 @@ def test_apply_and_residual_parity(name, builder, level, opt):
     ctx = Ctx(xyz, tets, level, dict(nu=0.3, variant=_VAR[variant], khat=_KH[khat], iface=_IF[iface]))
     try:
         t = ctx.torch
+        B.hhg_set_interior_kernel(ctx.h, opt.get("kernel", 0))
         perm = mesh.match_nodes(lv.coords, ctx.coords_u)  # oracle node i == gpu unique node perm[i]
         assert np.array_equal(ctx.udir[perm], lv.dirichlet)
         ctx.set_k(_kfun(ctx.coords_u))
