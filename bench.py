@@ -398,7 +398,9 @@ def solve_times(B, torch, h, level, coords_u):
 # + f for the residual and a Jacobi step; x, f, k, d read and x, d written for a Chebyshev step
 SWEEP_BYTES = {("apply", 8): 56, ("residual", 8): 80, ("jacobi", 8): 80, ("chebyshev", 8): 128,
                ("apply", 4): 28, ("residual", 4): 40, ("jacobi", 4): 40, ("chebyshev", 4): 64,
-               ("apply_bf16_k", 4): 26, ("apply_tile_kernel", 8): 56, ("apply_tile_kernel", 4): 28}
+               ("apply_bf16_k", 4): 26}
+for _name in ("apply_tile_kernel", "apply_per_macro_launches", "apply_one_launch"):
+    SWEEP_BYTES[(_name, 8)], SWEEP_BYTES[(_name, 4)] = 56, 28
 
 
 def kernel_table(B, torch, dev, stream, levels=(7, 8), reps=10):
@@ -468,11 +470,13 @@ def kernel_table(B, torch, dev, stream, levels=(7, 8), reps=10):
                     y.copy_(x)
                     row(kind, dt, timed(lambda: B.hhg_smooth(h, level, dt, 1, f, y)))
                 B.hhg_set_mg_params(h)
-            # the shared-memory tile kernel (interior kernel 1) on the same sweeps
-            B.hhg_set_interior_kernel(h, 1)
-            for dt in (B.F64, B.F32):
-                x, f, y = bufs[dt]
-                row("apply_tile_kernel", dt, timed(lambda: B.hhg_apply(h, level, dt, x, y)))
+            # the other macro-interior kernels on the same sweeps: the shared-memory tile kernel
+            # (1), the point kernels with one launch per macro (2) and with one launch for all (3)
+            for kern, name in ((1, "apply_tile_kernel"), (2, "apply_per_macro_launches"), (3, "apply_one_launch")):
+                B.hhg_set_interior_kernel(h, kern)
+                for dt in (B.F64, B.F32):
+                    x, f, y = bufs[dt]
+                    row(name, dt, timed(lambda: B.hhg_apply(h, level, dt, x, y)))
             B.hhg_set_interior_kernel(h, 0)
             x, f, y = bufs[B.F32]
             B.hhg_set_coefficient(h, kl.to(torch.bfloat16).view(torch.int16), B.BF16)
@@ -535,6 +539,18 @@ def stokes_bench(B, torch, level, dev, stream, steps=20):
             rep = B.hhg_solve(h, f, x, method=method, level=level, dt=B.F64, rtol=1e-8, max_iter=30,
                               inner_rtol=1e-3, inner_max_iter=inner, allow_not_converged=True)
             out[name] = {k: (float("%.4g" % v) if isinstance(v, float) else v) for k, v in rep.items()}
+        # the paper's solver settings (Sec. 5.2.1): hybrid Gauss-Seidel velocity smoothing, one
+        # step per Uzawa step, pressure relaxation 0.3, variable V(3,3) cycles with two more steps
+        # per coarser level
+        B.hhg_set_mg_params(h, smoother=B.SMOOTH_HYBRID_GS, uzawa_pre=3, uzawa_post=3, uzawa_extra=2,
+                            uzawa_vsteps=1, uzawa_omega=0.3)
+        for name, method, inner in (("ir_uzawa_mg_hybrid_gs", B.SOLVE_STOKES_IR_UZAWA, 40),
+                                    ("ir_fgcr_uzawa_mg_hybrid_gs", B.SOLVE_STOKES_IR_FGCR, 60)):
+            x = torch.zeros_like(f)
+            rep = B.hhg_solve(h, f, x, method=method, level=level, dt=B.F64, rtol=1e-8, max_iter=30,
+                              inner_rtol=1e-3, inner_max_iter=inner, allow_not_converged=True)
+            out[name] = {k: (float("%.4g" % v) if isinstance(v, float) else v) for k, v in rep.items()}
+        B.hhg_set_mg_params(h)
         return out
     finally:
         B.hhg_destroy(h)

@@ -112,6 +112,35 @@ def viscosity_sphere(x, mu_in=1.0, mu_out=1.0e3, radius=0.25, width=0.02):
     return mu_in + (mu_out - mu_in) * 0.5 * (1.0 + np.tanh((r - radius) / width))
 
 
+def plume_temperature(x):
+    """Temperature of the stationary plume workload (Sec. 5.2.1): a tilted Gaussian sheet
+    around the surface z = 3/10 - (3r/2 + 3/4)(r - 1/2) plus a column exp(-100 r^2) that
+    fades out above z of about 0.53 through a logistic factor, with the anisotropic radius
+    r^2 = 1.3 (x - 1/2)^2 + 2.7 (y - 1/2)^2 (so no rotational symmetry)."""
+    x = np.asarray(x, dtype=np.float64)
+    r2 = 1.3 * (x[..., 0] - 0.5) ** 2 + 2.7 * (x[..., 1] - 0.5) ** 2
+    r = np.sqrt(r2)
+    z = x[..., 2]
+    sheet = 0.89 * np.exp(-30.0 * (z + (1.5 * r + 0.75) * (r - 0.5) - 0.3) ** 2 - 10.0 * r2)
+    column = 0.98 * np.exp(-100.0 * r2) / (np.exp(17.0 * z - 9.095) + 1.0)
+    return sheet + column
+
+
+def plume_viscosity(x):
+    """exp(-theta) of the plume temperature, times 1e-2 above the plane z = 3/4 (a jump that a
+    macro mesh with a face on that plane resolves, e.g. kuhn_cube(4))."""
+    x = np.asarray(x, dtype=np.float64)
+    return np.exp(-plume_temperature(x)) * np.where(x[..., 2] > 0.75, 1e-2, 1.0)
+
+
+def plume_force(x):
+    """Buoyancy body force theta (0, 0, 10) of the plume workload."""
+    th = plume_temperature(x)
+    f = np.zeros(np.shape(th) + (3,))
+    f[..., 2] = 10.0 * th
+    return f
+
+
 def affine_field(x, a0, a):
     x = np.asarray(x)
     return a0 + x @ np.asarray(a)

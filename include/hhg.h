@@ -532,11 +532,18 @@ hhg_status hhg_apply_host(hhg_ctx* ctx, int level, hhg_dtype dt, const void* x_h
 hhg_status hhg_profile(hhg_ctx* ctx, int enable, double* ms_host, int64_t* launches_host);
 
 /* Kernel of the macro-interior sweeps of the scaled-stencil variants (results equal up to
- * rounding): 0 (default) one thread per point for FP64 and, for FP32, one thread per pair of
- * neighbouring points of a lattice row in packed two-lane FP32 arithmetic, both reading the
- * stencil neighbours straight from global memory; 1 a block per 30 x 4 x 4 box of lattice
- * points that stages the box plus its one-point halo in shared memory (asynchronous copies)
- * and reads every neighbour from there.  Errors: ARG for another value. */
+ * rounding).  The point kernels take one thread per point for FP64 and, for FP32, one thread
+ * per pair of neighbouring points of a lattice row in packed two-lane FP32 arithmetic, both
+ * reading the stencil neighbours straight from global memory; they run either as one launch
+ * per macro (the macro's stencil a kernel parameter) or as one launch over all macros (each
+ * block copies its macro's stencil to shared memory), which suits meshes of many small
+ * macros.  kernel: 0 (default) the point kernels, all macros in one launch when the mesh has
+ * several macros and one macro's launch would fill fewer than two waves of the GPU, else one
+ * launch per macro; 1 a block per 30 x 4 x 4 box of lattice points that stages the box plus
+ * its one-point halo in shared memory (asynchronous copies) and reads every neighbour from
+ * there; 2 the point kernels, one launch per macro; 3 the point kernels, all macros in one
+ * launch.  The Stokes sweeps follow the same choice of launch shape.  Errors: ARG for another
+ * value. */
 hhg_status hhg_set_interior_kernel(hhg_ctx* ctx, int kernel);
 
 /* FP32 FMA issue-rate probe, a measurement aid with no counterpart in the paper: the

@@ -98,7 +98,9 @@ def residual(Kbc, dirichlet, f, x):
 # V-cycles with more smoothing steps on coarser levels.  The library's choices, restated
 # here one step at a time (vectors (N, 4): velocity node-major, then the pressure):
 #   * velocity smoothing: `vsteps` Chebyshev steps on D^-1 A (A the velocity block with
-#     Dirichlet identity rows, interval [lo, hi] * lambda_max) for A du = r_u from du = 0;
+#     Dirichlet identity rows, interval [lo, hi] * lambda_max) for A du = r_u from du = 0, or
+#     (smoother "hybrid_gs", the paper's choice in Sec. 5.2.1) `vsteps` hybrid Gauss-Seidel
+#     steps with skeleton damping gs_omega;
 #   * pressure update: p -= omega (g - B u - C p) / s,  s_i = m_i / mu_i + (-C)_ii
 #     (m the lumped mass, a diagonal surrogate of -S);
 #   * V-cycle on level l: pre + extra (lmax - l) steps, restriction of the saddle residual
@@ -190,19 +192,26 @@ class UzawaHierarchy:
         x[keep] = np.linalg.solve(Kd, pack4(f4)[keep])
         return unpack4(x, N)
 
-    def uzawa_step(self, l, f4, x4, lam, vsteps=2, omega=0.5, lo=1 / 8, hi=1.1):
-        from .solvers import chebyshev
+    def uzawa_step(self, l, f4, x4, lam, vsteps=2, omega=0.5, lo=1 / 8, hi=1.1, smoother="chebyshev",
+                   gs_omega=2 / 3):
+        from .solvers import chebyshev, hybrid_gauss_seidel, interior_colours
 
-        d = self.lv[l].dirichlet
+        lv = self.lv[l]
+        d = lv.dirichlet
         x4 = np.array(x4, dtype=np.float64)
         r = self.residual(l, f4, x4)
-        du = chebyshev(self.A[l], d, r[:, :3], np.zeros((len(d), 3)), lam[l], lo, hi, vsteps)
+        z = np.zeros((len(d), 3))
+        if smoother == "hybrid_gs":
+            du = hybrid_gauss_seidel(self.A[l], d, lv.skeleton, interior_colours(lv), r[:, :3], z, gs_omega, vsteps)
+        else:
+            du = chebyshev(self.A[l], d, r[:, :3], z, lam[l], lo, hi, vsteps)
         x4[:, :3] += du
         r = self.residual(l, f4, x4)
         x4[:, 3] -= omega * r[:, 3] / self.s[l]
         return x4
 
-    def vcycle(self, l, f4, x4, lam, lmax, pre=3, post=3, extra=2, vsteps=2, omega=0.5, lo=1 / 8, hi=1.1):
+    def vcycle(self, l, f4, x4, lam, lmax, pre=3, post=3, extra=2, vsteps=2, omega=0.5, lo=1 / 8, hi=1.1,
+               smoother="chebyshev", gs_omega=2 / 3):
         """One variable V-cycle on level l (lmax: the finest level, for the extra steps)."""
         from .solvers import restrict
 
@@ -211,15 +220,16 @@ class UzawaHierarchy:
         x4 = np.array(x4, dtype=np.float64)
         ex = extra * (lmax - l)
         for _ in range(pre + ex):
-            x4 = self.uzawa_step(l, f4, x4, lam, vsteps, omega, lo, hi)
+            x4 = self.uzawa_step(l, f4, x4, lam, vsteps, omega, lo, hi, smoother, gs_omega)
         r = self.residual(l, f4, x4)
         Nc = self.lv[l - 1].num_nodes
         rc = np.zeros((Nc, 4))
         rc[:, :3] = restrict(self.P[l], r[:, :3], self.lv[l].dirichlet, self.lv[l - 1].dirichlet)
         rc[:, 3] = self.P[l].T @ r[:, 3]
-        ec = self.vcycle(l - 1, rc, np.zeros((Nc, 4)), lam, lmax, pre, post, extra, vsteps, omega, lo, hi)
+        ec = self.vcycle(l - 1, rc, np.zeros((Nc, 4)), lam, lmax, pre, post, extra, vsteps, omega, lo, hi, smoother,
+                         gs_omega)
         x4[:, :3] += self.P[l] @ ec[:, :3]
         x4[:, 3] += self.P[l] @ ec[:, 3]
         for _ in range(post + ex):
-            x4 = self.uzawa_step(l, f4, x4, lam, vsteps, omega, lo, hi)
+            x4 = self.uzawa_step(l, f4, x4, lam, vsteps, omega, lo, hi, smoother, gs_omega)
         return x4

@@ -236,6 +236,10 @@ struct hhg_ctx {
   bool coeff_bf16 = false;     // the coefficient was given in BF16 (k16 holds it on every level)
   std::unique_ptr<LearnState> learn;
   OpFlags flags{1, 0, 0};
+  // macro-interior kernel choice (hhg_set_interior_kernel): 0 automatic, 1 shared-memory tile,
+  // 2 one launch per macro, 3 all macros in one launch
+  int interior_kernel = 0;
+  int sm_count = 0;  // SMs of the device (read on first use)
   DevMem scratch;   // reduction partials
   DevMem scalar;    // device scalars
   double* pinned = nullptr;
@@ -459,6 +463,25 @@ const T* stored_stencil(hhg_ctx* c, LevelHost& L) {
   return S.as<T>();
 }
 
+// The operator flags of a sweep on level L, with the launch shape of its macro-interior part:
+// all macros in one launch when chosen (interior kernel 3) or, automatically, when the mesh has
+// several macros and one macro's launch (FP32 point pairs or one point per thread) fills
+// fewer than two waves of four 128-thread blocks per SM.
+inline OpFlags sweep_flags(hhg_ctx* c, const LevelHost& L, bool pairs) {
+  OpFlags f = c->flags;
+  f.batch = 0;
+  if (f.stored || f.nodal || f.tile || c->interior_kernel == 2) return f;
+  if (c->interior_kernel == 3) {
+    f.batch = 1;
+    return f;
+  }
+  if (L.dev.nmacro < 2) return f;
+  if (c->sm_count == 0) CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
+  const int per_macro = pairs ? L.dev.ntiles_pair : L.dev.ntiles_lin;
+  f.batch = per_macro < 2 * 4 * c->sm_count;
+  return f;
+}
+
 template <typename T>
 void sweep(hhg_ctx* c, int level, OpKind op, SweepArgs<T> a, double* norm2) {
   LevelHost& L = c->lv(level);
@@ -479,13 +502,19 @@ void sweep(hhg_ctx* c, int level, OpKind op, SweepArgs<T> a, double* norm2) {
   }
   CK(cudaEventRecord(c->ev_fork, c->stream));
   for (auto st : c->aux) CK(cudaStreamWaitEvent(st, c->ev_fork, 0));
-  // interior: macro m on stream (m even) or aux[1] (m odd); partial slots in macro order
+  // interior: all macros in one launch, or macro m on stream (m even) or aux[1] (m odd); partial
+  // slots in macro order
+  const OpFlags fl = sweep_flags(c, L, std::is_same<T, float>::value);
   int64_t used = 0;
-  for (int m = 0; m < L.dev.nmacro; ++m) {
-    int64_t cnt = 0;
-    CK(launch_sweep_macro<T>(L.dev, stencils<T>(L), nodal_consts<T>(L), m, op, c->flags, a,
-                             m % 2 ? c->aux[1] : c->stream, used, &cnt));
-    used += cnt;
+  if (fl.batch) {
+    CK(launch_sweep_batched<T>(L.dev, consts_dev<T>(L), op, fl, a, c->stream, 0, &used));
+  } else {
+    for (int m = 0; m < L.dev.nmacro; ++m) {
+      int64_t cnt = 0;
+      CK(launch_sweep_macro<T>(L.dev, stencils<T>(L), nodal_consts<T>(L), m, op, c->flags, a,
+                               m % 2 ? c->aux[1] : c->stream, used, &cnt));
+      used += cnt;
+    }
   }
   if (c->prof) {
     CK(cudaEventRecord(c->ev_join[1], c->aux[1]));
@@ -504,7 +533,7 @@ void sweep(hhg_ctx* c, int level, OpKind op, SweepArgs<T> a, double* norm2) {
     CK(cudaEventRecord(ps[1], c->aux[0]));
     c->prof_ev[0].push_back(pi);
     c->prof_ev[1].push_back(ps);
-    c->prof_launches[0] += L.dev.ntiles_lin > 0 ? L.dev.nmacro : 0;
+    c->prof_launches[0] += L.dev.ntiles_lin > 0 ? (fl.batch ? (L.dev.nmacro + 65534) / 65535 : L.dev.nmacro) : 0;
     c->prof_launches[1] += (L.dev.nface_nodes > 0) + (L.dev.nev > 0) + (L.dev.ndir > 0);
   }
   for (int q = 0; q < 4; ++q) {

@@ -1194,9 +1194,10 @@ hhg_status hhg_profile(hhg_ctx* c, int enable, double* ms_host, int64_t* launche
 
 hhg_status hhg_set_interior_kernel(hhg_ctx* c, int kernel) {
   return guard(c, [&] {
-    if (kernel != 0 && kernel != 1) THROW(HHG_ERR_ARG, "interior kernel must be 0 or 1");
+    if (kernel < 0 || kernel > 3) THROW(HHG_ERR_ARG, "interior kernel must be 0, 1, 2 or 3");
     c->drop_graphs();
-    c->flags.tile = kernel;
+    c->interior_kernel = kernel;
+    c->flags.tile = kernel == 1;
   });
 }
 

@@ -16,6 +16,7 @@ struct OpFlags {
   int nodal = 0;  // 1: macro-interior rows by nodal integration a_h (the NODAL variant)
   int stored = 0; // 1: macro-interior rows from the stored stencil blocks (the STORED variant)
   int tile = 0;   // 1: macro-interior sweeps by the shared-memory tile kernel (k_interior_tile)
+  int batch = 0;  // 1: the macro-interior sweeps of all macros in one launch (stencils staged in shared memory)
 };
 
 // Arguments of one stencil sweep.  Vectors are component-major over the level
@@ -57,6 +58,13 @@ template <typename T>
 int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev, OpKind op,
                  const OpFlags& fl, const SweepArgs<T>& a, void* stream, int parts, int64_t partial_offset,
                  int64_t* partial_count, void* stream_ev = nullptr, void* stream_dir = nullptr);
+
+// The macro-interior sweeps of all macros of the level in one launch (k_interior_pair_batched for
+// FP32, k_interior_batched for FP64; each block stages its macro's stencil from mc_dev in shared
+// memory), partial slots from partial_offset in the order of the per-macro launches.
+template <typename T>
+int launch_sweep_batched(const LevelDev& L, const MacroConsts<T>* mc_dev, OpKind op, const OpFlags& fl,
+                         const SweepArgs<T>& a, void* stream, int64_t partial_offset, int64_t* partial_count);
 
 // The macro-interior launch of macro m alone (partial slots from partial_offset; *partial_count
 // returns the slots used).

@@ -525,7 +525,8 @@ double stokes_sweep(hhg_ctx* c, int l, OpKind op, const T* f, const T* x, T* out
   int64_t np = 0;
   fork_side_streams(c);
   void* side[3] = {c->aux[0], c->aux[1], c->aux[2]};
-  CK(launch_stokes_sweep<T>(L.dev, stencils<T>(L), consts_dev<T>(L), op, c->flags, a, c->stream, &np, side));
+  CK(launch_stokes_sweep<T>(L.dev, stencils<T>(L), consts_dev<T>(L), op, sweep_flags(c, L, false), a, c->stream, &np,
+                            side));
   join_side_streams(c);
   if (!norm) return 0.0;
   CK(launch_reduce(c->scratch.as<double>(), np, c->scalar.as<double>(), c->stream));

@@ -20,6 +20,7 @@
 // sum.  With the practical interface rule the whole row is the a_h row.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
 
@@ -264,15 +265,17 @@ __device__ __forceinline__ void stokes_epilogue(const SweepArgs<T>& a, int64_t e
 // GS = 1 (a colour pass of the hybrid Gauss-Seidel smoother): the block takes four chunks of
 // colour `colour`'s list (a warp each; lane l the point i0 + 2 l of the chunk's row) instead
 // of a slice chunk.
-template <typename T, int OP, int GEN, int STK = 0, int KB = 0, int GS = 0>
-__global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, const MacroStencil<T> st,
-                                                              const int macro, const OpFlags fl,
-                                                              const SweepArgs<T> a, const int colour) {
+// The body takes its block's index among the macro's blocks (`block`) and the slot of its
+// partial sum (`partial`, nullable) from the kernel around it.
+template <typename T, int OP, int GEN, int STK, int KB, int GS>
+__device__ __forceinline__ void interior_point_body(const LevelDev& L, const MacroStencil<T>& st, const int macro,
+                                                    const int block, double* partial, const OpFlags& fl,
+                                                    const SweepArgs<T>& a, const int colour) {
   const int n = L.n;
   int i = 0, j = 0, k = 0;
   bool valid;
   if constexpr (GS) {
-    const int q = blockIdx.x * (INTERIOR_BLOCK / 32) + (threadIdx.x >> 5);
+    const int q = block * (INTERIOR_BLOCK / 32) + (threadIdx.x >> 5);
     valid = q < L.gs_ptr[colour + 1] - L.gs_ptr[colour];
     if (valid) {
       const int32_t ch = L.gs_chunks[L.gs_ptr[colour] + q];
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, c
       valid = i + j + k <= n - 1;
     }
   } else {
-    const int32_t tile = L.tiles_lin[blockIdx.x];
+    const int32_t tile = L.tiles_lin[block];
     k = tile >> 20;
     const int M = n - 1 - k;
     const int t = (tile & 0xFFFFF) + threadIdx.x;
@@ -385,7 +388,45 @@ __global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, c
       epilogue<T, OP>(a, base + r00, E, ax, ay, az, dgx, dgy, dgz, x0, y0, z0, r2);
     }
   }
-  if (OP == OP_RESID && a.partial != nullptr) block_sum_store<T>(r2, a.partial + blockIdx.x);
+  if (OP == OP_RESID && partial != nullptr) block_sum_store<T>(r2, partial);
+}
+
+// one launch per macro: the stencil is a kernel parameter
+template <typename T, int OP, int GEN, int STK = 0, int KB = 0, int GS = 0>
+__global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior(const LevelDev L, const MacroStencil<T> st,
+                                                              const int macro, const OpFlags fl,
+                                                              const SweepArgs<T> a, const int colour) {
+  interior_point_body<T, OP, GEN, STK, KB, GS>(L, st, macro, blockIdx.x, a.partial ? a.partial + blockIdx.x : nullptr,
+                                               fl, a, colour);
+}
+
+// The interior stencil of one macro copied into shared memory by the whole block, each value
+// as stored (C = T) or as the lane pair (v, v) of the packed FP32 arithmetic (C = float2).
+__device__ __forceinline__ float2 stencil_value(float v, float2) { return make_float2(v, v); }
+__device__ __forceinline__ float stencil_value(float v, float) { return v; }
+__device__ __forceinline__ double stencil_value(double v, double) { return v; }
+template <typename C, typename T>
+__device__ __forceinline__ void stage_stencil(MacroStencil<C>& dst, const MacroStencil<T>* __restrict__ src) {
+  const T* s = &src->S[0][0];
+  C* d = &dst.S[0][0];
+  for (int q = threadIdx.x; q < (int)(sizeof(MacroStencil<T>) / sizeof(T)); q += blockDim.x)
+    d[q] = stencil_value(__ldg(s + q), C());
+  __syncthreads();
+}
+
+// All macros of a level in one launch (grid: the macro's blocks x macros macro0 ..): each block
+// stages its macro's stencil in shared memory.  Partial-sum slots macro-major, as the per-macro
+// launches place them.
+template <typename T, int OP, int GEN, int STK = 0, int KB = 0>
+__global__ void __launch_bounds__(INTERIOR_BLOCK) k_interior_batched(const LevelDev L,
+                                                                      const MacroConsts<T>* __restrict__ mc,
+                                                                      const int macro0, const OpFlags fl,
+                                                                      const SweepArgs<T> a) {
+  __shared__ MacroStencil<T> sst;
+  const int m = macro0 + blockIdx.y;
+  stage_stencil(sst, &mc[m].st);
+  double* partial = a.partial ? a.partial + (int64_t)blockIdx.y * gridDim.x + blockIdx.x : nullptr;
+  interior_point_body<T, OP, GEN, STK, KB, 0>(L, sst, m, blockIdx.x, partial, fl, a, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -482,10 +523,10 @@ template <typename T>
 __device__ __forceinline__ float lane_x(T v) { return v.v.x; }
 
 template <int OP, int GEN, int KB>
-__global__ void __launch_bounds__(INTERIOR_BLOCK, 4) k_interior_pair(const LevelDev L, const MacroStencil<float2> st,
-                                                                   const int macro, const OpFlags fl,
-                                                                   const SweepArgs<float> a) {
-  const int32_t tile = L.tiles_pair[blockIdx.x];
+__device__ __forceinline__ void interior_pair_body(const LevelDev& L, const MacroStencil<float2>& st, const int macro,
+                                                   const int block, double* partial, const OpFlags& fl,
+                                                   const SweepArgs<float>& a) {
+  const int32_t tile = L.tiles_pair[block];
   const int n = L.n;
   const int k = tile >> 20;
   const int M = n - 1 - k;
@@ -548,7 +589,29 @@ __global__ void __launch_bounds__(INTERIOR_BLOCK, 4) k_interior_pair(const Level
       epilogue<float, OP>(a, e + 1, E, ax.v.y, ay.v.y, az.v.y, dgx.v.y, dgy.v.y, dgz.v.y, nb.x0.v.y, nb.y0.v.y,
                           nb.z0.v.y, r2);
   }
-  if (OP == OP_RESID && a.partial != nullptr) block_sum_store<float>(r2, a.partial + blockIdx.x);
+  if (OP == OP_RESID && partial != nullptr) block_sum_store<float>(r2, partial);
+}
+
+// one launch per macro: the stencil (as lane pairs) is a kernel parameter
+template <int OP, int GEN, int KB>
+__global__ void __launch_bounds__(INTERIOR_BLOCK, 4) k_interior_pair(const LevelDev L, const MacroStencil<float2> st,
+                                                                   const int macro, const OpFlags fl,
+                                                                   const SweepArgs<float> a) {
+  interior_pair_body<OP, GEN, KB>(L, st, macro, blockIdx.x, a.partial ? a.partial + blockIdx.x : nullptr, fl, a);
+}
+
+// all macros in one launch, as k_interior_batched: the block stages its macro's stencil as lane
+// pairs in shared memory
+template <int OP, int GEN, int KB>
+__global__ void __launch_bounds__(INTERIOR_BLOCK, 4) k_interior_pair_batched(const LevelDev L,
+                                                                           const MacroConsts<float>* __restrict__ mc,
+                                                                           const int macro0, const OpFlags fl,
+                                                                           const SweepArgs<float> a) {
+  __shared__ MacroStencil<float2> sst;
+  const int m = macro0 + blockIdx.y;
+  stage_stencil(sst, &mc[m].st);
+  double* partial = a.partial ? a.partial + (int64_t)blockIdx.y * gridDim.x + blockIdx.x : nullptr;
+  interior_pair_body<OP, GEN, KB>(L, sst, m, blockIdx.x, partial, fl, a);
 }
 
 // Macro-interior sweep from a shared-memory tile.  Each block takes one box of
@@ -1587,6 +1650,60 @@ int launch_interior(bool gen, const LevelDev& L, const MacroStencil<T>& st, int 
   }
 }
 
+// All macros' interior sweeps in launches of up to 65535 macros (grid.y); returns the number of
+// blocks (partial-sum slots, macro-major).
+constexpr int BATCH_MAX_MACROS = 65535;
+template <typename T, int OP>
+int64_t launch_interior_batched(bool gen, const LevelDev& L, const MacroConsts<T>* mc, const OpFlags& fl,
+                                const SweepArgs<T>& a, cudaStream_t s) {
+  const int nb = std::is_same<T, float>::value ? L.ntiles_pair : L.ntiles_lin;
+  if (nb == 0) return 0;
+  int64_t used = 0;
+  for (int m0 = 0; m0 < L.nmacro; m0 += BATCH_MAX_MACROS) {
+    const dim3 g(nb, std::min(BATCH_MAX_MACROS, L.nmacro - m0));
+    SweepArgs<T> am = a;
+    if (a.partial) am.partial = a.partial + used;
+    if constexpr (std::is_same<T, float>::value) {
+      if (am.k16 && !gen)
+        k_interior_pair_batched<OP, 0, 1><<<g, INTERIOR_BLOCK, 0, s>>>(L, mc, m0, fl, am);
+      else if (gen)
+        k_interior_pair_batched<OP, 1, 0><<<g, INTERIOR_BLOCK, 0, s>>>(L, mc, m0, fl, am);
+      else
+        k_interior_pair_batched<OP, 0, 0><<<g, INTERIOR_BLOCK, 0, s>>>(L, mc, m0, fl, am);
+    } else {
+      if (gen)
+        k_interior_batched<T, OP, 1><<<g, INTERIOR_BLOCK, 0, s>>>(L, mc, m0, fl, am);
+      else
+        k_interior_batched<T, OP, 0><<<g, INTERIOR_BLOCK, 0, s>>>(L, mc, m0, fl, am);
+    }
+    used += (int64_t)g.x * g.y;
+  }
+  return used;
+}
+
+template <typename T>
+int launch_sweep_batched(const LevelDev& L, const MacroConsts<T>* mc_dev, OpKind op, const OpFlags& fl,
+                         const SweepArgs<T>& a, void* stream, int64_t partial_offset, int64_t* partial_count) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool gen = !(fl.physical == 1 && fl.khat_edge == 0);
+  SweepArgs<T> am = a;
+  if (a.partial) am.partial = a.partial + partial_offset;
+  int64_t nb = 0;
+  switch (op) {
+    case OP_APPLY: nb = launch_interior_batched<T, OP_APPLY>(gen, L, mc_dev, fl, am, s); break;
+    case OP_RESID: nb = launch_interior_batched<T, OP_RESID>(gen, L, mc_dev, fl, am, s); break;
+    case OP_JACOBI: nb = launch_interior_batched<T, OP_JACOBI>(gen, L, mc_dev, fl, am, s); break;
+    case OP_CHEBY: nb = launch_interior_batched<T, OP_CHEBY>(gen, L, mc_dev, fl, am, s); break;
+    case OP_DIAG: nb = launch_interior_batched<T, OP_DIAG>(gen, L, mc_dev, fl, am, s); break;
+  }
+  if (partial_count) *partial_count = nb;
+  return (int)cudaGetLastError();
+}
+template int launch_sweep_batched<float>(const LevelDev&, const MacroConsts<float>*, OpKind, const OpFlags&,
+                                         const SweepArgs<float>&, void*, int64_t, int64_t*);
+template int launch_sweep_batched<double>(const LevelDev&, const MacroConsts<double>*, OpKind, const OpFlags&,
+                                          const SweepArgs<double>&, void*, int64_t, int64_t*);
+
 template <typename T>
 int launch_sweep_macro(const LevelDev& L, const MacroStencil<T>* st_host, const NodalConsts<T>* nc_host, int m,
                        OpKind op, const OpFlags& fl, const SweepArgs<T>& a, void* stream, int64_t partial_offset,
@@ -1643,6 +1760,13 @@ int launch_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const MacroC
   const dim3 blk(TILE_I, TILE_J);
   int64_t used = partial_offset;
   const bool gen = !(fl.physical == 1 && fl.khat_edge == 0);
+  if ((parts & 1) && fl.batch && !fl.tile) {
+    int64_t nb = 0;
+    const int e = launch_sweep_batched<T>(L, mc_dev, op, fl, a, stream, used, &nb);
+    if (e != 0) return e;
+    used += nb;
+    parts &= ~1;
+  }
   for (int m = 0; m < L.nmacro && (parts & 1); ++m) {
     SweepArgs<T> am = a;
     if (a.partial) am.partial = a.partial + used;
@@ -1784,7 +1908,23 @@ int launch_stokes_sweep(const LevelDev& L, const MacroStencil<T>* st_host, const
   cudaStream_t s_ev = side ? (cudaStream_t)side[2] : s;
   int64_t used = 0;
   const bool gen = !(fl.physical == 1 && fl.khat_edge == 0);
-  for (int m = 0; m < L.nmacro && L.ntiles_lin > 0; ++m) {
+  if (fl.batch && L.ntiles_lin > 0) {
+    for (int m0 = 0; m0 < L.nmacro; m0 += BATCH_MAX_MACROS) {
+      const dim3 g(L.ntiles_lin, std::min(BATCH_MAX_MACROS, L.nmacro - m0));
+      SweepArgs<T> am = a;
+      if (a.partial) am.partial = a.partial + used;
+      if (op == OP_APPLY)
+        (gen ? k_interior_batched<T, OP_APPLY, 1, 1> : k_interior_batched<T, OP_APPLY, 0, 1>)<<<g, INTERIOR_BLOCK, 0,
+                                                                                                s>>>(L, mc_dev, m0, fl,
+                                                                                                     am);
+      else
+        (gen ? k_interior_batched<T, OP_RESID, 1, 1> : k_interior_batched<T, OP_RESID, 0, 1>)<<<g, INTERIOR_BLOCK, 0,
+                                                                                                s>>>(L, mc_dev, m0, fl,
+                                                                                                     am);
+      used += (int64_t)g.x * g.y;
+    }
+  }
+  for (int m = 0; m < L.nmacro && L.ntiles_lin > 0 && !fl.batch; ++m) {
     SweepArgs<T> am = a;
     if (a.partial) am.partial = a.partial + used;
     cudaStream_t sm = m % 2 ? s_odd : s;

@@ -66,6 +66,13 @@ CASES = [
     ("skewed_l4_nodal", hi.skewed_pair, 4, {"variant": "nodal"}),
     ("skewed_l4", hi.skewed_pair, 4, {}),
     ("cube2_l3", lambda: hi.kuhn_cube(2), 3, {}),
+    # interior kernel 0 (automatic) launches all macros at once at these sizes; 2 forces one
+    # launch per macro, 3 one launch for all
+    ("cube_l4_per_macro", hi.kuhn_cube, 4, {"kernel": 2}),
+    ("skewed_l4_per_macro", hi.skewed_pair, 4, {"kernel": 2}),
+    ("cube_l4_unphysical_per_macro", hi.kuhn_cube, 4, {"variant": "unphysical", "kernel": 2}),
+    ("cube2_l3_per_macro", lambda: hi.kuhn_cube(2), 3, {"kernel": 2}),
+    ("unit_tet_l5_batched", hi.unit_tet, 5, {"kernel": 3}),
 ]
 
 _VAR = {"physical": B.PHYSICAL, "unphysical": B.UNPHYSICAL, "nodal": B.NODAL, "stored": B.STORED}

@@ -38,11 +38,14 @@ def _to_u(perm, u, p):
     return out
 
 
-@pytest.mark.parametrize("builder,level", [(hi.kuhn_cube, 4), (hi.skewed_pair, 3)], ids=["cube_l4", "skewed_l3"])
-def test_stokes_apply_residual_parity(builder, level):
+# interior kernel 0: automatic (all macros in one launch at these sizes); 2: one launch per macro
+@pytest.mark.parametrize("builder,level,kernel", [(hi.kuhn_cube, 4, 0), (hi.kuhn_cube, 4, 2), (hi.skewed_pair, 3, 0)],
+                         ids=["cube_l4", "cube_l4_per_macro", "skewed_l3"])
+def test_stokes_apply_residual_parity(builder, level, kernel):
     mm, lv, Kbc, K, ctx, perm = _setup(builder, level)
     try:
         t = ctx.torch
+        B.hhg_set_interior_kernel(ctx.h, kernel)
         N = lv.num_nodes
         xu, xp = hi.node_noise(lv.coords, 5), hi.node_noise(lv.coords, 6, comps=1)
         fu, fp = hi.node_noise(lv.coords, 7), hi.node_noise(lv.coords, 8, comps=1)
@@ -117,3 +120,46 @@ def test_stokes_minres_solve(cube4_solve, method):
     xd = d["xd"]
     assert np.abs(x_g - xd).max() <= 1e-5 * np.abs(xd).max(), rep
     assert abs((ST.lumped_mass(lv) * x_g[3 * N:]).sum()) <= 1e-10 * np.abs(x_g[3 * N:]).sum()
+
+
+def test_uzawa_with_hybrid_gauss_seidel_matches_oracle():
+    """The paper's Stokes solver settings (Sec. 5.2.1): inexact Uzawa with hybrid Gauss-Seidel
+    velocity smoothing (one step per Uzawa step), pressure relaxation 0.3 and variable V(3,3)
+    cycles with two more steps per coarser level.  One cycle from zero in FP64 equals the
+    oracle's cycle; the stationary iteration then reaches a relative residual of 1e-8 (the
+    oracle's cycles contract by about 0.7 each on this problem: about 50 cycles)."""
+    level = 4
+    xyz, tets = hi.kuhn_cube()
+    H = ST.UzawaHierarchy(mesh.MacroMesh.build(xyz, tets), list(range(2, level + 1)), _mu)
+    lv = H.lv[level]
+    N = lv.num_nodes
+    ctx = Ctx(xyz, tets, level, dict(kind=B.STOKES))
+    try:
+        t = ctx.torch
+        perm = mesh.match_nodes(lv.coords, ctx.coords_u)
+        ctx.set_k(_mu(ctx.coords_u))
+        B.hhg_set_mg_params(ctx.h, smoother=B.SMOOTH_HYBRID_GS, uzawa_pre=3, uzawa_post=3, uzawa_extra=2,
+                            uzawa_vsteps=1, uzawa_omega=0.3)
+        B.hhg_mg_setup(ctx.h)
+        f = np.zeros((N, 4))
+        f[:, :3] = hi.node_noise(lv.coords, 21)
+        f[:, 3] = hi.node_noise(lv.coords, 22, comps=1).reshape(-1)
+        f[:, 3] -= f[:, 3].mean()  # orthogonal to the constant-pressure kernel
+        f[lv.dirichlet, :3] = 0.0
+        want = H.project_pressure(level, H.vcycle(level, f, np.zeros_like(f), {}, level, vsteps=1, omega=0.3,
+                                                  smoother="hybrid_gs"))
+        fd = ctx.to_lib(_to_u(perm, f[:, :3], f[:, 3]), t.float64, 4)
+        x = t.zeros_like(fd)
+        rep = B.hhg_solve(ctx.h, fd, x, method=B.SOLVE_STOKES_UZAWA, level=level, dt=B.F64, rtol=1e-14, max_iter=1,
+                          allow_not_converged=True)
+        assert rep["iterations"] == 1
+        got = ctx.from_lib(x, 4)[perm]
+        assert np.abs(got[:, :3] - want[:, :3]).max() <= 1e-9 * np.abs(want[:, :3]).max()
+        assert np.abs(got[:, 3] - want[:, 3]).max() <= 1e-9 * np.abs(want[:, 3]).max()
+        x.zero_()
+        rep = B.hhg_solve(ctx.h, fd, x, method=B.SOLVE_STOKES_UZAWA, level=level, dt=B.F64, rtol=1e-8,
+                          max_iter=100)
+        assert rep["converged"], rep
+    finally:
+        B.hhg_set_mg_params(ctx.h)
+        ctx.close()

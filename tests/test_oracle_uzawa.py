@@ -90,6 +90,43 @@ def test_uzawa_step_without_pressure_relaxation_only_smooths_the_velocity(hier3)
     assert np.allclose(x1[:, :3], du, rtol=0, atol=1e-14 * np.abs(du).max())
 
 
+def test_uzawa_with_hybrid_gauss_seidel_converges_to_the_saddle_solution(hier3):
+    """The paper's solver settings (Sec. 5.2.1): hybrid Gauss-Seidel velocity smoothing, one
+    step per Uzawa step, pressure relaxation 0.3, V(3,3) cycles; the iterates reach the
+    bordered direct solution."""
+    H, lam = hier3
+    f = _rhs(H, 3, 13)
+    f[:, 3] -= f[:, 3].mean()
+    want = _bordered_solve(H, 3, f)
+    x = np.zeros_like(f)
+    norms = [np.linalg.norm(H.residual(3, f, x))]
+    for _ in range(40):
+        x = H.vcycle(3, f, x, lam, 3, vsteps=1, omega=0.3, smoother="hybrid_gs")
+        norms.append(np.linalg.norm(H.residual(3, f, x)))
+    rates = np.array(norms[1:]) / np.array(norms[:-1])
+    assert rates[1:].max() < 0.7, rates  # the first cycle may raise the mixed velocity-pressure norm
+    assert np.abs(H.project_pressure(3, x) - want).max() <= 1e-6 * np.abs(want).max()
+
+
+def test_hybrid_gauss_seidel_uzawa_step_smooths_then_relaxes_the_pressure(hier3):
+    """With the pressure fixed the velocity correction is the hybrid Gauss-Seidel step on
+    A du = r_u from du = 0; the pressure then moves by -omega (g - B u - C p) / s."""
+    H, lam = hier3
+    lv = H.lv[3]
+    f = _rhs(H, 3, 17)
+    x0 = np.zeros_like(f)
+    x0[:, 3] = hi.node_noise(lv.coords, 18, comps=1).reshape(-1)
+    x1 = H.uzawa_step(3, f, x0, lam, vsteps=1, omega=0.3, smoother="hybrid_gs")
+    r = H.residual(3, f, x0)
+    du = S.hybrid_gauss_seidel(H.A[3], lv.dirichlet, lv.skeleton, S.interior_colours(lv), r[:, :3],
+                               np.zeros_like(r[:, :3]), 2 / 3, 1)
+    assert np.allclose(x1[:, :3], du, rtol=0, atol=1e-14 * np.abs(du).max())
+    xu = x0.copy()
+    xu[:, :3] = du
+    rp = H.residual(3, f, xu)[:, 3]
+    assert np.allclose(x1[:, 3], x0[:, 3] - 0.3 * rp / H.s[3], rtol=0, atol=1e-13 * np.abs(x0[:, 3]).max())
+
+
 def _grid(H, l):
     return LN.grid_index(H.lv[l].coords, 1.0 / 2**l)
 
