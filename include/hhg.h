@@ -125,9 +125,20 @@ hhg_status hhg_set_timeout(hhg_ctx* ctx, int64_t milliseconds);
 hhg_status hhg_set_macro_mesh(hhg_ctx* ctx, const double* xyz_host, int64_t nverts, const int64_t* tets_host,
                               int64_t ntets, const int32_t* dirichlet_face_flags_host);
 
-/* Build levels 2..level_max (n = 4 .. 2^level_max intervals per macro edge;
- * level 2 has one interior node per macro, the coarsest level of Sec. 2). */
+/* Build levels coarsest..level_max (n = 2^level intervals per macro edge; the
+ * coarsest level is 2 unless hhg_set_coarsest_level chose another; level 2 has
+ * one interior node per macro).  Errors: ARG unless coarsest <= level_max <= 9. */
 hhg_status hhg_refine(hhg_ctx* ctx, int level_max);
+
+/* Coarsest level of the hierarchy that hhg_refine builds, and so of every
+ * multigrid cycle (Sec. 5: the coarsest grid is solved directly): 0 (the macro
+ * mesh itself), 1 (plus the edge midpoints: no macro-interior or face-interior
+ * nodes) or any level up to 9; default 2.  Meshes of many macros need 0 or 1,
+ * since the direct coarse solve takes at most 3000 free DoFs (elasticity: 3 per
+ * free node; Stokes: 3 per free node plus one pressure per node).  Call it after
+ * hhg_set_macro_mesh (which resets it to 2) and before hhg_refine.  Errors: ARG
+ * outside [0, 9]; STATE when the levels are already built. */
+hhg_status hhg_set_coarsest_level(hhg_ctx* ctx, int level);
 
 /* Select the operator (computes the per-macro reference stencils Shat and the
  * correction stencils S^1..3 of eq. correctionterm3D from element stiffness

@@ -829,15 +829,25 @@ hhg_status hhg_set_macro_mesh(hhg_ctx* c, const double* xyz, int64_t nverts, con
     c->have_mesh = true;
     c->levels.clear();
     c->level_max = -1;
+    c->level_min = 2;
     c->have_problem = false;
     c->have_coeff = false;
+  });
+}
+
+hhg_status hhg_set_coarsest_level(hhg_ctx* c, int level) {
+  return guard(c, [&] {
+    if (level < 0 || level > 9) THROW(HHG_ERR_ARG, "coarsest level must be in [0, 9]");
+    if (c->level_max >= 0) THROW(HHG_ERR_STATE, "set the coarsest level before hhg_refine");
+    c->level_min = level;
   });
 }
 
 hhg_status hhg_refine(hhg_ctx* c, int level_max) {
   return guard(c, [&] {
     if (!c->have_mesh) THROW(HHG_ERR_STATE, "mesh not set");
-    if (level_max < c->level_min || level_max > 9) THROW(HHG_ERR_ARG, "level_max must be in [2, 9]");
+    if (level_max < c->level_min || level_max > 9)
+      THROW(HHG_ERR_ARG, "level_max must be in [%d, 9] (the coarsest level to 9)", c->level_min);
     c->levels.clear();
     c->levels.resize(level_max + 1);
     c->level_max = level_max;

@@ -86,10 +86,11 @@ int launch_residual_noalloc(const LevelDev& L, const MacroStencil<T>* st_host, c
 
 // One colour pass of the hybrid Gauss-Seidel smoother on the macro interiors: every
 // macro-interior point of the colour, x_i += D_ii^-1 (f - A x)_i in place (a.x == a.out, a.omega
-// = 1); points of one colour are never neighbours.
+// = 1); points of one colour are never neighbours.  mc_dev non-null: one launch for all macros
+// (stencils staged in shared memory); null: one launch per macro with st_host[m].
 template <typename T>
-int launch_gs_colour(const LevelDev& L, const MacroStencil<T>* st_host, const OpFlags& fl, const SweepArgs<T>& a,
-                     int colour, void* stream);
+int launch_gs_colour(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev, const OpFlags& fl,
+                     const SweepArgs<T>& a, int colour, void* stream);
 // dst[c * E + idx[u]] = src[c * E + idx[u]] for u < count, c < comps
 template <typename T>
 int launch_copy_entries(int64_t count, const int64_t* idx, int comps, int64_t E, const T* src, T* dst, void* stream);

@@ -290,7 +290,8 @@ void smooth(hhg_ctx* c, int l, int steps, const T* f, T* x) {
       g.k = kptr<T>(L);
       g.out = x;
       g.omega = 1.0;
-      for (int col = 0; col < 8; ++col) CK(launch_gs_colour<T>(L.dev, stencils<T>(L), c->flags, g, col, c->stream));
+      for (int col = 0; col < 8; ++col)
+        CK(launch_gs_colour<T>(L.dev, stencils<T>(L), consts_dev<T>(L), c->flags, g, col, c->stream));
     }
   } else {
     for (int s = 0; s < steps; ++s) {

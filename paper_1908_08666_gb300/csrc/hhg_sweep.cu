@@ -600,6 +600,19 @@ __global__ void __launch_bounds__(INTERIOR_BLOCK, 4) k_interior_pair(const Level
   interior_pair_body<OP, GEN, KB>(L, st, macro, blockIdx.x, a.partial ? a.partial + blockIdx.x : nullptr, fl, a);
 }
 
+// a colour pass of the hybrid Gauss-Seidel smoother over all macros (grid.y), each block staging
+// its macro's stencil in shared memory
+template <typename T, int GEN>
+__global__ void __launch_bounds__(INTERIOR_BLOCK) k_gs_colour_batched(const LevelDev L,
+                                                                       const MacroConsts<T>* __restrict__ mc,
+                                                                       const int macro0, const OpFlags fl,
+                                                                       const SweepArgs<T> a, const int colour) {
+  __shared__ MacroStencil<T> sst;
+  const int m = macro0 + blockIdx.y;
+  stage_stencil(sst, &mc[m].st);
+  interior_point_body<T, OP_JACOBI, GEN, 0, 0, 1>(L, sst, m, blockIdx.x, nullptr, fl, a, colour);
+}
+
 // all macros in one launch, as k_interior_batched: the block stages its macro's stencil as lane
 // pairs in shared memory
 template <int OP, int GEN, int KB>
@@ -1987,13 +2000,25 @@ int upload_direction_tables() {
 }
 
 template <typename T>
-int launch_gs_colour(const LevelDev& L, const MacroStencil<T>* st_host, const OpFlags& fl, const SweepArgs<T>& a,
-                     int colour, void* stream) {
+int launch_gs_colour(const LevelDev& L, const MacroStencil<T>* st_host, const MacroConsts<T>* mc_dev, const OpFlags& fl,
+                     const SweepArgs<T>& a, int colour, void* stream) {
   const int count = L.gs_ptr[colour + 1] - L.gs_ptr[colour];
   if (count == 0) return 0;
   const int per = INTERIOR_BLOCK / 32;
-  const dim3 g((count + per - 1) / per);
   const bool gen = !(fl.physical == 1 && fl.khat_edge == 0);
+  // all macros of the level in one launch per colour (grid.y: macros), or one launch per macro
+  // when only the stencil-parameter kernel applies (mc_dev null)
+  if (mc_dev) {
+    for (int m0 = 0; m0 < L.nmacro; m0 += BATCH_MAX_MACROS) {
+      const dim3 g((count + per - 1) / per, std::min(BATCH_MAX_MACROS, L.nmacro - m0));
+      if (gen)
+        k_gs_colour_batched<T, 1><<<g, INTERIOR_BLOCK, 0, (cudaStream_t)stream>>>(L, mc_dev, m0, fl, a, colour);
+      else
+        k_gs_colour_batched<T, 0><<<g, INTERIOR_BLOCK, 0, (cudaStream_t)stream>>>(L, mc_dev, m0, fl, a, colour);
+    }
+    return (int)cudaGetLastError();
+  }
+  const dim3 g((count + per - 1) / per);
   for (int m = 0; m < L.nmacro; ++m) {
     if (gen)
       k_interior<T, OP_JACOBI, 1, 0, 0, 1><<<g, INTERIOR_BLOCK, 0, (cudaStream_t)stream>>>(L, st_host[m], m, fl, a,
@@ -2004,10 +2029,10 @@ int launch_gs_colour(const LevelDev& L, const MacroStencil<T>* st_host, const Op
   }
   return (int)cudaGetLastError();
 }
-template int launch_gs_colour<float>(const LevelDev&, const MacroStencil<float>*, const OpFlags&,
-                                     const SweepArgs<float>&, int, void*);
-template int launch_gs_colour<double>(const LevelDev&, const MacroStencil<double>*, const OpFlags&,
-                                      const SweepArgs<double>&, int, void*);
+template int launch_gs_colour<float>(const LevelDev&, const MacroStencil<float>*, const MacroConsts<float>*,
+                                     const OpFlags&, const SweepArgs<float>&, int, void*);
+template int launch_gs_colour<double>(const LevelDev&, const MacroStencil<double>*, const MacroConsts<double>*,
+                                      const OpFlags&, const SweepArgs<double>&, int, void*);
 
 template <typename T>
 int launch_store_stencil(const LevelDev& L, const MacroStencil<double>* st_host, const OpFlags& fl, const double* k64,

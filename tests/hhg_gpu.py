@@ -18,11 +18,13 @@ def torch_cuda():
 
 
 class Ctx:
-    def __init__(self, xyz, tets, level, problem=None, dirichlet_face_flags=None):
+    def __init__(self, xyz, tets, level, problem=None, dirichlet_face_flags=None, coarsest=None):
         self.torch = torch_cuda()
         self.stream = self.torch.cuda.current_stream().cuda_stream
         self.h = B.hhg_create(0, self.stream)
         B.hhg_set_macro_mesh(self.h, xyz, tets, dirichlet_face_flags)
+        if coarsest is not None:
+            B.hhg_set_coarsest_level(self.h, coarsest)
         B.hhg_refine(self.h, level)
         B.hhg_set_problem(self.h, **(problem or {}))
         self.level = level
@@ -113,14 +115,14 @@ def oracle_hier(builder, levels, kfun):
 class Pair:
     """GPU context and oracle hierarchy on the same mesh, with node permutations."""
 
-    def __init__(self, builder, level, kfun=kfun_smooth):
+    def __init__(self, builder, level, kfun=kfun_smooth, coarsest=2):
         self.xyz, self.tets = builder()
         self.level = level
-        self.H = oracle_hier(builder, list(range(2, level + 1)), kfun)
-        self.ctx = Ctx(self.xyz, self.tets, level, dict(nu=NU))
+        self.H = oracle_hier(builder, list(range(coarsest, level + 1)), kfun)
+        self.ctx = Ctx(self.xyz, self.tets, level, dict(nu=NU), coarsest=coarsest)
         self.ctx.set_k(kfun(self.ctx.coords_u))
         self.perm, self.dirs = {}, {}
-        for l in range(2, level + 1):
+        for l in range(coarsest, level + 1):
             cu, _, udir, _, _ = self.ctx.maps(l)
             self.perm[l] = mesh.match_nodes(self.H.lv[l].coords, cu)
             self.dirs[l] = udir

@@ -249,3 +249,77 @@ def test_full_size_ir_solve_cube_level7():
             assert np.abs(r_or - ru[u]).max() <= 1e-9 * np.abs(fu[u]).max()
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("coarsest", [0, 1])
+def test_coarser_hierarchies_on_a_48_macro_mesh(coarsest):
+    """Hierarchies that start below level 2 (hhg_set_coarsest_level): on the 48-macro cube the
+    coarsest levels 0 and 1 hold only skeleton nodes (vertices, and edge midpoints at level 1),
+    where the level-2 hierarchy's direct solve would take 7 x 7 x 7 x 3 free DoFs.  The
+    transfers and the operator of every level, one V(2,2) Chebyshev cycle and an MG-CG solve
+    equal the oracle's hierarchy on the same levels."""
+    p = Pair(lambda: hi.kuhn_cube(2), 3, coarsest=coarsest)
+    try:
+        t = p.ctx.torch
+        h = p.ctx.h
+        B.hhg_mg_setup(h)
+        lam = {q: S.lambda_max_DinvA(p.H.A[q], p.H.lv[q].dirichlet) for q in range(coarsest + 1, 4)}
+        for q, v in lam.items():
+            B.hhg_set_lambda_max(h, q, v)
+        for l in range(coarsest, 4):
+            lv = p.H.lv[l]
+            x = hi.node_noise(lv.coords, seed=30 + l)
+            y = t.empty(3 * B.hhg_num_nodes(h, l)[0], dtype=t.float64, device="cuda")
+            B.hhg_apply(h, l, B.F64, p.to_lib(l, x, t.float64), y)
+            want = op.apply(p.H.A[l], x)
+            assert np.abs(p.from_lib(l, y) - want).max() <= 1e-12 * np.abs(want).max(), l
+            if l == coarsest:
+                continue
+            lc = p.H.lv[l - 1]
+            xc = hi.node_noise(lc.coords, seed=40 + l)
+            xc[lc.dirichlet] = 0.0
+            xf = hi.node_noise(lv.coords, seed=50 + l)
+            xfd = p.to_lib(l, xf, t.float64)
+            B.hhg_prolongate_add(h, l, B.F64, p.to_lib(l - 1, xc, t.float64), xfd)
+            want = S.prolongate_add(p.H.P[l], xc, xf)
+            assert np.abs(p.from_lib(l, xfd) - want).max() <= 1e-14 * np.abs(want).max(), l
+            rf = hi.node_noise(lv.coords, seed=60 + l)
+            rf[lv.dirichlet] = 0.0
+            rc = t.empty(3 * B.hhg_num_nodes(h, l - 1)[0], dtype=t.float64, device="cuda")
+            B.hhg_restrict(h, l, B.F64, p.to_lib(l, rf, t.float64), rc)
+            want = S.restrict(p.H.P[l], rf, lv.dirichlet, lc.dirichlet)
+            assert np.abs(p.from_lib(l - 1, rc) - want).max() <= 1e-13 * np.abs(want).max(), l
+        lv = p.H.lv[3]
+        f = hi.node_noise(lv.coords, seed=71)
+        f[lv.dirichlet] = 0.0
+        x = t.zeros(3 * B.hhg_num_nodes(h, 3)[0], dtype=t.float64, device="cuda")
+        fd = p.to_lib(3, f, t.float64)
+        B.hhg_vcycle(h, 3, B.F64, fd, x)
+        want = p.H.vcycle(3, f, np.zeros_like(f), "chebyshev", 2, 2, lam)
+        assert np.abs(p.from_lib(3, x) - want).max() <= 1e-10 * np.abs(want).max()
+        x.zero_()
+        rep = B.hhg_solve(h, fd, x, method=B.SOLVE_MG_CG, level=3, dt=B.F64, rtol=1e-8, max_iter=100)
+        r = S.residual(p.H.A[3], lv.dirichlet, f, p.from_lib(3, x))
+        assert np.linalg.norm(r) <= 1.01e-8 * np.linalg.norm(f), rep
+    finally:
+        p.close()
+
+
+def test_coarsest_level_must_precede_refinement():
+    t = pytest.importorskip("torch")
+    xyz, tets = hi.kuhn_cube(1)
+    h = B.hhg_create(0, t.cuda.current_stream().cuda_stream)
+    try:
+        B.hhg_set_macro_mesh(h, xyz, tets)
+        with pytest.raises(B.HhgError):
+            B.hhg_set_coarsest_level(h, 10)
+        B.hhg_set_coarsest_level(h, 1)
+        with pytest.raises(B.HhgError):
+            B.hhg_refine(h, 0)
+        B.hhg_refine(h, 3)
+        with pytest.raises(B.HhgError) as ei:
+            B.hhg_set_coarsest_level(h, 0)
+        assert ei.value.status == 8  # HHG_ERR_STATE
+        assert B.hhg_num_nodes(h, 1)[1] == 3**3
+    finally:
+        B.hhg_destroy(h)

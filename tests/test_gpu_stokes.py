@@ -122,18 +122,21 @@ def test_stokes_minres_solve(cube4_solve, method):
     assert abs((ST.lumped_mass(lv) * x_g[3 * N:]).sum()) <= 1e-10 * np.abs(x_g[3 * N:]).sum()
 
 
-def test_uzawa_with_hybrid_gauss_seidel_matches_oracle():
+@pytest.mark.parametrize("builder,level,coarsest", [(hi.kuhn_cube, 4, 2), (lambda: hi.kuhn_cube(2), 3, 1)],
+                         ids=["cube_l4", "cube2_l3_coarsest1"])
+def test_uzawa_with_hybrid_gauss_seidel_matches_oracle(builder, level, coarsest):
     """The paper's Stokes solver settings (Sec. 5.2.1): inexact Uzawa with hybrid Gauss-Seidel
     velocity smoothing (one step per Uzawa step), pressure relaxation 0.3 and variable V(3,3)
     cycles with two more steps per coarser level.  One cycle from zero in FP64 equals the
     oracle's cycle; the stationary iteration then reaches a relative residual of 1e-8 (the
-    oracle's cycles contract by about 0.7 each on this problem: about 50 cycles)."""
-    level = 4
-    xyz, tets = hi.kuhn_cube()
-    H = ST.UzawaHierarchy(mesh.MacroMesh.build(xyz, tets), list(range(2, level + 1)), _mu)
+    oracle's cycles contract by about 0.7 each on the 6-macro cube: about 50 cycles).  Also on
+    the 48-macro cube with the coarsest level 1 (hhg_set_coarsest_level), whose direct
+    saddle solve holds the edge midpoints and macro vertices only."""
+    xyz, tets = builder()
+    H = ST.UzawaHierarchy(mesh.MacroMesh.build(xyz, tets), list(range(coarsest, level + 1)), _mu)
     lv = H.lv[level]
     N = lv.num_nodes
-    ctx = Ctx(xyz, tets, level, dict(kind=B.STOKES))
+    ctx = Ctx(xyz, tets, level, dict(kind=B.STOKES), coarsest=coarsest)
     try:
         t = ctx.torch
         perm = mesh.match_nodes(lv.coords, ctx.coords_u)
