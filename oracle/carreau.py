@@ -3,8 +3,8 @@
 Test infrastructure only (see the package docstring).
 
 At every node the velocity components are fitted in the least-squares sense by an
-affine polynomial over the node and its mesh neighbours (eq. minimization_problem,
-m = 1); the fitted gradient gives eps(u) = (grad u + grad u^T)/2, |eps|^2 = eps : eps, and
+affine polynomial (m = 1) or a quadratic one (m = 2) over the node and its mesh neighbours
+(eq. minimization_problem); the fitted gradient gives eps(u) = (grad u + grad u^T)/2, |eps|^2 = eps : eps, and
 
     mu = eta_inf + (eta0 - eta_inf) (1 + kappa |eps|^2)^r          (eq. carreau).
 
@@ -27,22 +27,35 @@ def neighbours(lv: Level):
     return [pairs[split[i]:split[i + 1], 1] for i in range(N)]
 
 
+# A quadratic fit is used only where the patch determines it: the columns 1, dx/rho and
+# dx_a dx_b / rho^2 (rho the patch radius) have a smallest singular value above QUAD_RANK_TOL
+# times the largest.  Elsewhere (patches one-sided in some direction, e.g. on the domain
+# boundary, where dz^2 and dz agree on the two layers of points) the quadratic terms are not
+# determined and would bias the gradient, and the fit is the affine one.  The paper (Sec. 3)
+# does not treat such patches.
+QUAD_RANK_TOL = 1e-6
+
+
 def lsq_gradients(lv: Level, u, degree=1):
-    """(N, 3, 3) array g[i, c, a] = d u_c / d x_a of the fitted polynomial at node i."""
+    """(N, 3, 3) array g[i, c, a] = d u_c / d x_a of the fitted polynomial at node i
+    (degree 1: affine; 2: quadratic where the patch determines it, else affine)."""
     u = np.asarray(u).reshape(-1, 3)
     nb = neighbours(lv)
     g = np.zeros((lv.num_nodes, 3, 3))
     for i in range(lv.num_nodes):
         pts = np.concatenate([[i], nb[i]])
         dx = lv.coords[pts] - lv.coords[i]
-        cols = [np.ones(len(pts)), dx[:, 0], dx[:, 1], dx[:, 2]]
+        rho = np.abs(dx).max()
+        y = dx / rho
+        cols = [np.ones(len(pts)), y[:, 0], y[:, 1], y[:, 2]]
         if degree == 2:
-            for a in range(3):
-                for b in range(a, 3):
-                    cols.append(dx[:, a] * dx[:, b])
+            quad = cols + [y[:, a] * y[:, b] for a in range(3) for b in range(a, 3)]
+            sv = np.linalg.svd(np.stack(quad, axis=1), compute_uv=False)
+            if len(pts) >= 10 and sv[-1] > QUAD_RANK_TOL * sv[0]:
+                cols = quad
         V = np.stack(cols, axis=1)
         coef, *_ = np.linalg.lstsq(V, u[pts], rcond=None)
-        g[i] = coef[1:4].T
+        g[i] = coef[1:4].T / rho
     return g
 
 
@@ -55,8 +68,8 @@ def carreau(e2, eta0, eta_inf, kappa, r):
     return eta_inf + (eta0 - eta_inf) * (1.0 + kappa * e2) ** r
 
 
-def viscosity(lv: Level, u, eta0, eta_inf, kappa, r):
-    return carreau(strain_rate_sq(lsq_gradients(lv, u)), eta0, eta_inf, kappa, r)
+def viscosity(lv: Level, u, eta0, eta_inf, kappa, r, degree=1):
+    return carreau(strain_rate_sq(lsq_gradients(lv, u, degree)), eta0, eta_inf, kappa, r)
 
 
 # ------------------------------------------------------- fixed-point iteration (Alg. 1)
