@@ -329,6 +329,17 @@ typedef struct {
 hhg_status hhg_carreau_viscosity(hhg_ctx* ctx, int level, const hhg_carreau* params, const void* u_dev,
                                  void* mu_dev);
 
+/* Degree m of the least-squares fit on the macro skeleton (eq. minimization_problem,
+ * m in {1, 2}; default 1), used by hhg_carreau_viscosity and hhg_picard.  m = 2 fits a
+ * quadratic in the monomials 1, x_a, x_a x_b over the node's patch where the patch
+ * determines it (at least 10 points and every Cholesky pivot of the normal equations in
+ * patch-scaled coordinates above 1e-10 of the largest diagonal entry) and the affine
+ * polynomial elsewhere (one-sided patches on the domain boundary, where the quadratic
+ * terms are not determined).  Macro-interior nodes keep the affine slope operator: on
+ * their point-symmetric patches both fits have the same gradient (Sec. 3).  Errors: ARG
+ * for another degree. */
+hhg_status hhg_set_strain_fit(hhg_ctx* ctx, int degree);
+
 typedef struct {
   hhg_carreau carreau;
   int level;

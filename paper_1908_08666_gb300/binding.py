@@ -110,6 +110,7 @@ _SIGS = {
     "hhg_set_macro_mesh": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p],
     "hhg_refine": [C.c_void_p, C.c_int],
     "hhg_set_coarsest_level": [C.c_void_p, C.c_int],
+    "hhg_set_strain_fit": [C.c_void_p, C.c_int],
     "hhg_set_problem": [C.c_void_p, C.POINTER(hhg_problem)],
     "hhg_num_nodes": [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "hhg_entry_coords": [C.c_void_p, C.c_int, C.c_void_p],
@@ -240,6 +241,10 @@ def hhg_refine(ctx, level_max):
 
 def hhg_set_coarsest_level(ctx, level):
     _check(ctx, load().hhg_set_coarsest_level(ctx, int(level)))
+
+
+def hhg_set_strain_fit(ctx, degree):
+    _check(ctx, load().hhg_set_strain_fit(ctx, int(degree)))
 
 
 def hhg_set_problem(ctx, kind=ELASTICITY, nu=0.3, variant=PHYSICAL, khat=KHAT_PATCH, iface=IFACE_SYMMETRIC):

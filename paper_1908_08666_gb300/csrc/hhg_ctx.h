@@ -240,6 +240,7 @@ struct hhg_ctx {
   // 2 one launch per macro, 3 all macros in one launch
   int interior_kernel = 0;
   int sm_count = 0;  // SMs of the device (read on first use)
+  int strain_degree = 1;  // least-squares strain-rate fit on the skeleton (hhg_set_strain_fit)
   DevMem scratch;   // reduction partials
   DevMem scalar;    // device scalars
   double* pinned = nullptr;

@@ -835,6 +835,13 @@ hhg_status hhg_set_macro_mesh(hhg_ctx* c, const double* xyz, int64_t nverts, con
   });
 }
 
+hhg_status hhg_set_strain_fit(hhg_ctx* c, int degree) {
+  return guard(c, [&] {
+    if (degree != 1 && degree != 2) THROW(HHG_ERR_ARG, "strain-rate fit degree must be 1 or 2");
+    c->strain_degree = degree;
+  });
+}
+
 hhg_status hhg_set_coarsest_level(hhg_ctx* c, int level) {
   return guard(c, [&] {
     if (level < 0 || level > 9) THROW(HHG_ERR_ARG, "coarsest level must be in [0, 9]");

@@ -122,8 +122,10 @@ struct PatchLists {
   const int64_t* ent;    // entry of each patch point (the node itself included)
   const double* dx;      // 3 per patch point: x_point - x_node
 };
+// degree 2: quadratic least squares on the skeleton where the patch determines it (affine
+// elsewhere); the interior slope operator serves both degrees (the fits agree there, Sec. 3)
 int launch_carreau(const LevelDev& L, const SlopeOp* q_host, const PatchLists& P, const CarreauParams& cp,
-                   const double* u, double* mu, void* stream);
+                   const double* u, double* mu, void* stream, int degree = 1);
 
 // out[0] = max over masked entries of |a - b|_2 over comps components (b nullable)
 int launch_node_maxnorm(const uint8_t* mask, int64_t E, int comps, const double* a, const double* b,

@@ -1010,7 +1010,7 @@ void carreau_viscosity(hhg_ctx* c, int l, const hhg_carreau& p, const double* u,
   carreau_setup(c, l);
   LevelHost& L = c->lv(l);
   CarreauParams cp{p.eta0, p.eta_inf, p.kappa, p.r};
-  CK(launch_carreau(L.dev, L.slope.data(), L.plist, cp, u, mu, c->stream));
+  CK(launch_carreau(L.dev, L.slope.data(), L.plist, cp, u, mu, c->stream, c->strain_degree));
 }
 
 void mg_check(hhg_ctx* c) {

@@ -312,13 +312,89 @@ __global__ void k_carreau_interior(const LevelDev L, const SlopeOp q, int macro,
   mu[c0] = carreau_mu(cp, g);
 }
 
+// Quadratic least squares (eq. minimization_problem, m = 2) over the patch of skeleton node t,
+// in the coordinates y = dx / rho (rho = the patch's largest |dx| component): Cholesky of the
+// 10 x 10 normal equations in the monomials 1, y_a, y_a y_b (a <= b).  Returns false, leaving
+// g untouched, when the patch does not determine the quadratic (fewer than 10 points or a
+// pivot at most QUAD_PIVOT_TOL times the largest diagonal entry: one-sided patches, on which
+// y_a and y_a^2 agree); else g[c][a] = d u_c / d x_a of the fit at the node.
+constexpr double QUAD_PIVOT_TOL = 1e-10;
+__device__ bool quadratic_gradient(const PatchLists& P, int t, int64_t E, const double* __restrict__ u,
+                                   double g[3][3]) {
+  const int q0 = P.ptr[t], q1 = P.ptr[t + 1];
+  if (q1 - q0 < 10) return false;
+  double rho = 0.0;
+  for (int q = q0; q < q1; ++q)
+    for (int a = 0; a < 3; ++a) rho = fmax(rho, fabs(P.dx[3 * q + a]));
+  if (!(rho > 0.0)) return false;
+  const double ir = 1.0 / rho;
+  double N[10][10], R[10][3];
+  for (int a = 0; a < 10; ++a) {
+    for (int b = 0; b < 10; ++b) N[a][b] = 0.0;
+    for (int c = 0; c < 3; ++c) R[a][c] = 0.0;
+  }
+  for (int q = q0; q < q1; ++q) {
+    const double y0 = P.dx[3 * q] * ir, y1 = P.dx[3 * q + 1] * ir, y2 = P.dx[3 * q + 2] * ir;
+    const double w[10] = {1.0, y0, y1, y2, y0 * y0, y0 * y1, y0 * y2, y1 * y1, y1 * y2, y2 * y2};
+    const int64_t e = P.ent[q];
+    const double uv[3] = {u[e], u[e + E], u[e + 2 * E]};
+    for (int a = 0; a < 10; ++a) {
+      for (int b = 0; b <= a; ++b) N[a][b] += w[a] * w[b];
+      for (int c = 0; c < 3; ++c) R[a][c] += w[a] * uv[c];
+    }
+  }
+  double dmax = 0.0;
+  for (int a = 0; a < 10; ++a) dmax = fmax(dmax, N[a][a]);
+  // Cholesky N = L L^T in place (lower triangle)
+  for (int k = 0; k < 10; ++k) {
+    double s = N[k][k];
+    for (int j = 0; j < k; ++j) s -= N[k][j] * N[k][j];
+    if (!(s > QUAD_PIVOT_TOL * dmax)) return false;
+    const double l = sqrt(s);
+    N[k][k] = l;
+    for (int r = k + 1; r < 10; ++r) {
+      double v = N[r][k];
+      for (int j = 0; j < k; ++j) v -= N[r][j] * N[k][j];
+      N[r][k] = v / l;
+    }
+  }
+  // forward (L z = R) and backward (L^T c = z) substitution, three right-hand sides
+  for (int k = 0; k < 10; ++k)
+    for (int c = 0; c < 3; ++c) {
+      double v = R[k][c];
+      for (int j = 0; j < k; ++j) v -= N[k][j] * R[j][c];
+      R[k][c] = v / N[k][k];
+    }
+  for (int k = 9; k >= 0; --k)
+    for (int c = 0; c < 3; ++c) {
+      double v = R[k][c];
+      for (int j = k + 1; j < 10; ++j) v -= N[j][k] * R[j][c];
+      R[k][c] = v / N[k][k];
+    }
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) g[c][a] = R[a + 1][c] * ir;
+  return true;
+}
+
 // skeleton nodes: general affine least squares min sum (c + b.dx - u)^2 over the patch
-// (normal equations, 4x4, Gaussian elimination with partial pivoting); every copy written
+// (normal equations, 4x4, Gaussian elimination with partial pivoting), or with QUAD the
+// quadratic fit where the patch determines it (affine elsewhere); every copy written
+template <int QUAD>
 __global__ void k_carreau_skeleton(const LevelDev L, const PatchLists P, CarreauParams cp,
                                    const double* __restrict__ u, double* __restrict__ mu) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= P.nnodes) return;
   const int64_t E = L.entries;
+  double g[3][3];
+  if (QUAD && quadratic_gradient(P, t, E, u, g)) {
+    const double m = carreau_mu(cp, g);
+    const int s = P.node[t];
+    for (int q = L.skel_ptr[s]; q < L.skel_ptr[s + 1]; ++q) {
+      const SkelInc I = L.skel_inc[q];
+      mu[(int64_t)I.macro * L.nt + lattice_index(L.n, I.i, I.j, I.k)] = m;
+    }
+    return;
+  }
   double A[4][4] = {{0}}, R[4][3] = {{0}};
   for (int q = P.ptr[t]; q < P.ptr[t + 1]; ++q) {
     const double w[4] = {1.0, P.dx[3 * q], P.dx[3 * q + 1], P.dx[3 * q + 2]};
@@ -356,7 +432,6 @@ __global__ void k_carreau_skeleton(const LevelDev L, const PatchLists P, Carreau
       for (int c = 0; c < 3; ++c) R[r][c] -= f * R[col][c];
     }
   }
-  double g[3][3];
   for (int a = 0; a < 3; ++a)
     for (int c = 0; c < 3; ++c) g[c][a] = R[a + 1][c] / A[a + 1][a + 1];
   const double m = carreau_mu(cp, g);
@@ -445,11 +520,16 @@ int launch_node_maxnorm(const uint8_t* mask, int64_t E, int comps, const double*
 }
 
 int launch_carreau(const LevelDev& L, const SlopeOp* q_host, const PatchLists& P, const CarreauParams& cp,
-                   const double* u, double* mu, void* stream) {
+                   const double* u, double* mu, void* stream, int degree) {
   cudaStream_t s = (cudaStream_t)stream;
   for (int m = 0; m < L.nmacro && L.ntiles_lin > 0; ++m)
     k_carreau_interior<<<L.ntiles_lin, INTERIOR_BLOCK, 0, s>>>(L, q_host[m], m, cp, u, mu);
-  if (P.nnodes > 0) k_carreau_skeleton<<<(P.nnodes + 127) / 128, 128, 0, s>>>(L, P, cp, u, mu);
+  if (P.nnodes > 0) {
+    if (degree == 2)
+      k_carreau_skeleton<1><<<(P.nnodes + 127) / 128, 128, 0, s>>>(L, P, cp, u, mu);
+    else
+      k_carreau_skeleton<0><<<(P.nnodes + 127) / 128, 128, 0, s>>>(L, P, cp, u, mu);
+  }
   return (int)cudaGetLastError();
 }
 

@@ -18,20 +18,30 @@ def _u(c):
     return np.stack([np.sin(2 * c[:, 0]) * c[:, 1] ** 2, np.cos(c[:, 1] + 2 * c[:, 2]), c[:, 0] * c[:, 2] ** 2], 1)
 
 
-@pytest.mark.parametrize("builder,level", [(hi.kuhn_cube, 4), (hi.skewed_pair, 3)], ids=["cube_l4", "skewed_l3"])
-def test_carreau_viscosity_parity(builder, level):
+@pytest.mark.parametrize("builder,level,degree", [(hi.kuhn_cube, 4, 1), (hi.skewed_pair, 3, 1), (hi.skewed_pair, 3, 2),
+                                                  (hi.skewed_pair, 4, 2), (lambda: hi.kuhn_cube(2), 3, 2)],
+                         ids=["cube_l4", "skewed_l3", "skewed_l3_quadratic", "skewed_l4_quadratic",
+                              "cube2_l3_quadratic"])
+def test_carreau_viscosity_parity(builder, level, degree):
+    """Affine (m = 1) and quadratic (m = 2, where the patch determines it) least-squares
+    strain rates (Sec. 3) against the oracle's; the quadratic fit differs from the affine one
+    at the skewed mesh's interface nodes."""
     xyz, tets = builder()
     lv = mesh.build_level(mesh.MacroMesh.build(xyz, tets), level)
     ctx = Ctx(xyz, tets, level, dict(kind=B.STOKES))
     try:
         t = ctx.torch
+        B.hhg_set_strain_fit(ctx.h, degree)
         perm = mesh.match_nodes(lv.coords, ctx.coords_u)
         u = ctx.to_lib(_u(ctx.coords_u), t.float64, 3)
         mu = t.empty(ctx.E, dtype=t.float64, device="cuda")
         B.hhg_carreau_viscosity(ctx.h, level, u, mu, **PAR)
         got = ctx.from_lib(mu, 1)[perm, 0]
-        want = CA.viscosity(lv, _u(lv.coords), **PAR)
-        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+        want = CA.viscosity(lv, _u(lv.coords), **PAR, degree=degree)
+        assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+        if degree == 2 and builder is hi.skewed_pair:
+            other = CA.viscosity(lv, _u(lv.coords), **PAR, degree=1)
+            assert np.abs(other - want).max() > 1e-8 * np.abs(want).max()
         full = mu.cpu().numpy()
         assert np.array_equal(full, ctx.from_lib(mu, 1)[ctx.e2u, 0])
     finally:
