@@ -66,6 +66,32 @@ def kuhn_cube(m: int = 1):
     return np.array(xyz, dtype=np.float64), np.array(tets, dtype=np.int64)
 
 
+def kuhn_box(nx: int, ny: int, nz: int):
+    """The box (0, nx) x (0, ny) x (0, nz) cut into unit cubes, each split into 6 Kuhn
+    tetrahedra as in kuhn_cube (kuhn_box(4, 2, 1) is the foam block of Sec. 5.1.3)."""
+    grid = {}
+    xyz = []
+
+    def vid(p):
+        if p not in grid:
+            grid[p] = len(xyz)
+            xyz.append([float(p[0]), float(p[1]), float(p[2])])
+        return grid[p]
+
+    tets = []
+    for cz in range(nz):
+        for cy in range(ny):
+            for cx in range(nx):
+                c = (cx, cy, cz)
+                for perm in KUHN_PERMS:
+                    p1 = list(c)
+                    p1[perm[0]] += 1
+                    p2 = list(p1)
+                    p2[perm[1]] += 1
+                    tets.append([vid(c), vid(tuple(p1)), vid(tuple(p2)), vid((cx + 1, cy + 1, cz + 1))])
+    return np.array(xyz, dtype=np.float64), np.array(tets, dtype=np.int64)
+
+
 def skewed_pair():
     """Two non-degenerate, non-axis-aligned macro tetrahedra sharing one face.
 
