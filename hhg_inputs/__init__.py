@@ -138,6 +138,18 @@ def viscosity_sphere(x, mu_in=1.0, mu_out=1.0e3, radius=0.25, width=0.02):
     return mu_in + (mu_out - mu_in) * 0.5 * (1.0 + np.tanh((r - radius) / width))
 
 
+def foam_modulus(x, cell=0.5, e_void=1e-2):
+    """Stand-in for the foam block's CT-derived Young's modulus (Sec. 5.1.3; the scan is not
+    available): material (E = 1) around the Schwarz P surface cos(2 pi x / cell) + cos(2 pi y /
+    cell) + cos(2 pi z / cell) = 0, a periodic open-cell structure, and E = e_void in the pores,
+    blended by a tanh of the level-set value."""
+    x = np.asarray(x, dtype=np.float64)
+    w = 2.0 * np.pi / cell
+    s = np.cos(w * x[..., 0]) + np.cos(w * x[..., 1]) + np.cos(w * x[..., 2])
+    solid = 0.5 * (1.0 - np.tanh((np.abs(s) - 0.8) / 0.2))
+    return e_void + (1.0 - e_void) * solid
+
+
 def plume_temperature(x):
     """Temperature of the stationary plume workload (Sec. 5.2.1): a tilted Gaussian sheet
     around the surface z = 3/10 - (3r/2 + 3/4)(r - 1/2) plus a column exp(-100 r^2) that

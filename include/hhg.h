@@ -329,6 +329,18 @@ typedef struct {
 hhg_status hhg_carreau_viscosity(hhg_ctx* ctx, int level, const hhg_carreau* params, const void* u_dev,
                                  void* mu_dev);
 
+/* Boundary traction (Neumann) load, the term int_{Gamma_N} t . v ds of the weak form
+ * (Sec. 5.1.3, the traction on the foam block's top plane): f += M_Gamma t on the free
+ * rows, with M_Gamma the exact P1 mass matrix of the refined triangles of the flagged
+ * macro faces and t the nodal traction interpolated on them.  face_flags_host: int32[4 *
+ * ntets], face f of tetrahedron t (the face opposite its vertex f) carries the traction
+ * when non-zero; it must be a boundary face (ARG otherwise).  t_dev and f_dev: 3
+ * components of stride E in dt (FP64 or FP32) at `level`; every copy of a node receives
+ * the same value; Dirichlet rows are left unchanged.  Allocates temporaries and waits for
+ * the stream. */
+hhg_status hhg_traction_load(hhg_ctx* ctx, int level, hhg_dtype dt, const int32_t* face_flags_host,
+                             const void* t_dev, void* f_dev);
+
 /* Degree m of the least-squares fit on the macro skeleton (eq. minimization_problem,
  * m in {1, 2}; default 1), used by hhg_carreau_viscosity and hhg_picard.  m = 2 fits a
  * quadratic in the monomials 1, x_a, x_a x_b over the node's patch where the patch

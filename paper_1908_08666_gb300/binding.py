@@ -111,6 +111,7 @@ _SIGS = {
     "hhg_refine": [C.c_void_p, C.c_int],
     "hhg_set_coarsest_level": [C.c_void_p, C.c_int],
     "hhg_set_strain_fit": [C.c_void_p, C.c_int],
+    "hhg_traction_load": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
     "hhg_set_problem": [C.c_void_p, C.POINTER(hhg_problem)],
     "hhg_num_nodes": [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "hhg_entry_coords": [C.c_void_p, C.c_int, C.c_void_p],
@@ -245,6 +246,11 @@ def hhg_set_coarsest_level(ctx, level):
 
 def hhg_set_strain_fit(ctx, degree):
     _check(ctx, load().hhg_set_strain_fit(ctx, int(degree)))
+
+
+def hhg_traction_load(ctx, level, dt, face_flags, t, f):
+    fl = np.ascontiguousarray(np.asarray(face_flags, dtype=np.int32).reshape(-1))
+    _check(ctx, load().hhg_traction_load(ctx, level, dt, fl.ctypes.data_as(C.c_void_p), _ptr(t), _ptr(f)))
 
 
 def hhg_set_problem(ctx, kind=ELASTICITY, nu=0.3, variant=PHYSICAL, khat=KHAT_PATCH, iface=IFACE_SYMMETRIC):

@@ -70,10 +70,19 @@ struct HhgError {
     }                                                                                                \
   } while (0)
 
+// Host -> device copy that has landed when it returns.  cudaMemcpy from pageable memory returns
+// once the data is staged, with the DMA into device memory possibly still running on the legacy
+// stream, which the library's non-blocking streams do not wait for; the synchronisation keeps a
+// kernel queued next on a library stream from reading the old contents.
+inline void copy_h2d(void* dst, const void* src, size_t bytes) {
+  CK(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+  CK(cudaStreamSynchronize(cudaStreamLegacy));
+}
+
 template <typename T>
 void upload(DevMem& d, const std::vector<T>& h) {
   CK(d.alloc(h.size() * sizeof(T)));
-  if (!h.empty()) CK(cudaMemcpy(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  if (!h.empty()) copy_h2d(d.p, h.data(), h.size() * sizeof(T));
 }
 
 struct Vec3d {
@@ -261,7 +270,8 @@ struct hhg_ctx {
   cudaStream_t cap_stream = nullptr;  // capture stream (the caller's may be the legacy one)
   bool graphs_ok = true;              // false after a failed capture: launch directly
   void drop_graphs() {
-    for (auto& kv : vc_graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : vc_graphs)
+      if (kv.second) cudaGraphExecDestroy(kv.second);  // null: the first-use marker
     vc_graphs.clear();
   }
   std::vector<cudaEvent_t> ev_pool;
@@ -304,8 +314,11 @@ struct hhg_ctx {
 namespace hhg {
 namespace host {
 
+// Slots of the partial-sum scratch: the largest sweep's blocks, and at least the partials of two
+// dot-product launches in a row (1024 blocks each: the Stokes inner product over the velocity and
+// the pressure components writes both before reducing them together).
 inline int64_t max_partials(hhg_ctx* c) {
-  int64_t mx = 1024;
+  int64_t mx = 2 * 1024;
   for (int l = c->level_min; l <= c->level_max; ++l) {
     const LevelHost& L = *c->levels[l];
     mx = std::max<int64_t>(mx, (int64_t)std::max(L.tiles_lin.size(), L.tiles3.size()) * (int64_t)c->tets.size() +

@@ -835,6 +835,105 @@ hhg_status hhg_set_macro_mesh(hhg_ctx* c, const double* xyz, int64_t nverts, con
   });
 }
 
+hhg_status hhg_traction_load(hhg_ctx* c, int level, hhg_dtype dt, const int32_t* face_flags, const void* t_dev,
+                             void* f_dev) {
+  return guard(c, [&] {
+    LevelHost& L = c->lv(level);
+    if (!face_flags || !t_dev || !f_dev) THROW(HHG_ERR_ARG, "null argument");
+    if (dt != HHG_F64 && dt != HHG_F32) THROW(HHG_ERR_ARG, "dtype");
+    const int n = L.n;
+    const int M = (int)c->tets.size();
+    std::map<std::array<int64_t, 3>, int> fcount;
+    auto face_key = [&](int t, int f) {
+      std::array<int64_t, 3> key;
+      int r = 0;
+      for (int q = 0; q < 4; ++q)
+        if (q != f) key[r++] = c->tets[t][q];
+      std::sort(key.begin(), key.end());
+      return key;
+    };
+    for (int t = 0; t < M; ++t)
+      for (int f = 0; f < 4; ++f) fcount[face_key(t, f)]++;
+    // flagged faces: their area per refined triangle and the entries of their lattice points
+    const int npf = (n + 1) * (n + 2) / 2;
+    std::vector<double> area;
+    std::vector<int64_t> pent;
+    for (int t = 0; t < M; ++t)
+      for (int f = 0; f < 4; ++f) {
+        if (!face_flags[4 * t + f]) continue;
+        if (fcount[face_key(t, f)] != 1) THROW(HHG_ERR_ARG, "face %d of tetrahedron %d is not on the boundary", f, t);
+        int v[3], r = 0;
+        for (int q = 0; q < 4; ++q)
+          if (q != f) v[r++] = (int)c->tets[t][q];
+        const Vec3d& A = c->xyz[v[0]];
+        const Vec3d& B = c->xyz[v[1]];
+        const Vec3d& C = c->xyz[v[2]];
+        const double ux = B.x - A.x, uy = B.y - A.y, uz = B.z - A.z;
+        const double wx = C.x - A.x, wy = C.y - A.y, wz = C.z - A.z;
+        const double cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
+        area.push_back(0.5 * std::sqrt(cx * cx + cy * cy + cz * cz) / ((double)n * n));
+        // face point (a, b) -> lattice point (i, j, k) of macro t on face f (f = 0: i + j + k = n,
+        // 1: i = 0, 2: j = 0, 3: k = 0)
+        for (int b = 0; b <= n; ++b)
+          for (int a = 0; a + b <= n; ++a) {
+            int i, j, k;
+            if (f == 0) {
+              j = a; k = b; i = n - a - b;
+            } else if (f == 1) {
+              i = 0; j = a; k = b;
+            } else if (f == 2) {
+              j = 0; i = a; k = b;
+            } else {
+              k = 0; i = a; j = b;
+            }
+            pent.push_back((int64_t)t * L.nt + lattice_index(n, i, j, k));
+          }
+      }
+    const int nslots = (int)area.size();
+    if (nslots == 0) return;
+    // per free boundary node: its contributions (slot-major order) and all its copies
+    std::map<int64_t, std::vector<int64_t>> contrib_of;
+    for (int64_t g = 0; g < (int64_t)pent.size(); ++g) {
+      const int64_t u = L.entry_to_unique[pent[g]];
+      if (!L.unique_dir[u]) contrib_of[u].push_back(g);
+    }
+    std::map<int64_t, std::vector<int64_t>> copies;
+    for (const auto& kv : contrib_of) copies[kv.first];
+    for (int64_t e = 0; e < L.entries; ++e) {
+      auto it = copies.find(L.entry_to_unique[e]);
+      if (it != copies.end()) it->second.push_back(e);
+    }
+    std::vector<int64_t> cptr{0}, cidx, eptr{0}, eidx;
+    for (const auto& kv : contrib_of) {
+      cidx.insert(cidx.end(), kv.second.begin(), kv.second.end());
+      cptr.push_back((int64_t)cidx.size());
+      const auto& cp = copies[kv.first];
+      eidx.insert(eidx.end(), cp.begin(), cp.end());
+      eptr.push_back((int64_t)eidx.size());
+    }
+    DevMem d_area, d_pent, d_contrib, d_cptr, d_cidx, d_eptr, d_eidx;
+    upload(d_area, area);
+    upload(d_pent, pent);
+    upload(d_cptr, cptr);
+    upload(d_cidx, cidx);
+    upload(d_eptr, eptr);
+    upload(d_eidx, eidx);
+    CK(d_contrib.alloc(3 * pent.size() * sizeof(double)));
+    const int64_t nn = (int64_t)contrib_of.size();
+    if (dt == HHG_F64)
+      CK(launch_traction_load<double>(n, nslots, d_area.as<double>(), d_pent.as<int64_t>(), L.entries,
+                                      (const double*)t_dev, d_contrib.as<double>(), nn, d_cptr.as<int64_t>(),
+                                      d_cidx.as<int64_t>(), d_eptr.as<int64_t>(), d_eidx.as<int64_t>(),
+                                      (double*)f_dev, c->stream));
+    else
+      CK(launch_traction_load<float>(n, nslots, d_area.as<double>(), d_pent.as<int64_t>(), L.entries,
+                                     (const float*)t_dev, d_contrib.as<double>(), nn, d_cptr.as<int64_t>(),
+                                     d_cidx.as<int64_t>(), d_eptr.as<int64_t>(), d_eidx.as<int64_t>(),
+                                     (float*)f_dev, c->stream));
+    wait_stream(c);  // the temporaries are freed on return
+  });
+}
+
 hhg_status hhg_set_strain_fit(hhg_ctx* c, int degree) {
   return guard(c, [&] {
     if (degree != 1 && degree != 2) THROW(HHG_ERR_ARG, "strain-rate fit degree must be 1 or 2");

@@ -127,6 +127,16 @@ struct PatchLists {
 int launch_carreau(const LevelDev& L, const SlopeOp* q_host, const PatchLists& P, const CarreauParams& cp,
                    const double* u, double* mu, void* stream, int degree = 1);
 
+// Boundary traction load: nslots flagged macro faces, each a lattice of (n+1)(n+2)/2 points whose
+// entries are pent[s * npf + p] and whose n^2 triangles have area area[s]; t: nodal traction (3
+// components of stride E); contrib: scratch of 3 doubles per face point; then for each of nnodes
+// boundary nodes the contributions cidx[cptr[u] .. cptr[u+1]) are summed and added to f at its
+// entries eidx[eptr[u] .. eptr[u+1]).
+template <typename T>
+int launch_traction_load(int n, int nslots, const double* area, const int64_t* pent, int64_t E, const T* t,
+                         double* contrib, int64_t nnodes, const int64_t* cptr, const int64_t* cidx,
+                         const int64_t* eptr, const int64_t* eidx, T* f, void* stream);
+
 // out[0] = max over masked entries of |a - b|_2 over comps components (b nullable)
 int launch_node_maxnorm(const uint8_t* mask, int64_t E, int comps, const double* a, const double* b,
                         double* partials, double* out, void* stream);

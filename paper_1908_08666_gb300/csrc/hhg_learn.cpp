@@ -338,7 +338,7 @@ LearnGrid& grid(hhg_ctx* c, int l) {
     const double mean = cnt ? sum / cnt : 0.0;
     for (int64_t g = 0; g < G->V; ++g)
       if (gent[g] >= 0) lk[g] = (float)(std::log(k[gent[g]]) - mean);
-    CK(cudaMemcpy(G->logk.p, lk.data(), G->V * sizeof(float), cudaMemcpyHostToDevice));
+    copy_h2d(G->logk.p, lk.data(), G->V * sizeof(float));
     G->coeff_version = c->coeff_version;
   }
   return *G;

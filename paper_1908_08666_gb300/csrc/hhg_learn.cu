@@ -1090,6 +1090,8 @@ int conv_take_error(int* flag) {
   if (v) {
     const int zero = 0;
     e = cudaMemcpyToSymbol(g_conv_error, &zero, sizeof(int));
+    // landed before a kernel on a (non-blocking) library stream can read the flag
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
   }
   *flag = v;
   return (int)e;

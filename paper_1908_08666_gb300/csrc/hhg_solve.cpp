@@ -543,6 +543,8 @@ double sdot(hhg_ctx* c, int l, const T* a, const T* b) {
   int64_t n1 = 0, n2 = 0;
   double* part = c->scratch.as<double>();
   CK(launch_dot_masked<T>(L.d_mask.as<uint8_t>(), L.entries, 3, a, b, part, &n1, c->stream));
+  if ((n1 + 1024) * (int64_t)sizeof(double) > (int64_t)c->scratch.bytes)
+    THROW(HHG_ERR_STATE, "partial-sum scratch too small for the Stokes inner product");
   CK(launch_dot_masked<T>(L.d_mask_own.as<uint8_t>(), L.entries, 1, a + 3 * L.entries, b + 3 * L.entries, part + n1,
                           &n2, c->stream));
   CK(launch_reduce(part, n1 + n2, c->scalar.as<double>(), c->stream));

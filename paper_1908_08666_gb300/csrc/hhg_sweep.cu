@@ -1996,6 +1996,8 @@ int upload_direction_tables() {
   cudaError_t e = cudaMemcpyToSymbol(c_dir, dir, sizeof(dir));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ring, ring, sizeof(ring));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ring_n, rn, sizeof(rn));
+  // the copies may still be landing on the legacy stream, which library streams do not wait for
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
   return (int)e;
 }
 

@@ -442,6 +442,62 @@ __global__ void k_carreau_skeleton(const LevelDev L, const PatchLists P, Carreau
   }
 }
 
+// ---------------------------------------------------------------------------
+// Boundary traction load (the Neumann term of the weak form, Sec. 5.1.3): on each flagged
+// macro face (slot s) the refined face is a triangular lattice of (n+1)(n+2)/2 points
+// (a, b), a + b <= n, point index b (n + 1) - b (b - 1) / 2 + a, split into n^2 congruent
+// triangles of area A_s: "up" (a, b), (a+1, b), (a, b+1) and "down" (a+1, b), (a, b+1),
+// (a+1, b+1).  With the P1 interpolant of the nodal traction t, each triangle adds
+// (A / 12) (2 t_p + t_q + t_r) to the load of its point p (exact P1 face mass matrix).
+// k_traction_face: one thread per face point, the sum over its (up to six) triangles of
+// its face, into contrib[3 (s npf + p) + c]; k_traction_gather: one thread per boundary
+// node, the sum of its contributions (fixed order) added to every copy of the node.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int face_point(int n, int a, int b) { return b * (n + 1) - b * (b - 1) / 2 + a; }
+
+template <typename T>
+__global__ void k_traction_face(int n, int nslots, const double* __restrict__ area, const int64_t* __restrict__ pent,
+                                int64_t E, const T* __restrict__ t, double* __restrict__ contrib) {
+  const int npf = (n + 1) * (n + 2) / 2;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= (int64_t)nslots * npf) return;
+  const int s = (int)(g / npf);
+  const int p = (int)(g % npf);
+  int b = 0;
+  while (face_point(n, 0, b + 1) <= p && b < n) ++b;
+  const int a = p - face_point(n, 0, b);
+  const int64_t* pe = pent + (int64_t)s * npf;
+  double acc[3] = {0.0, 0.0, 0.0};
+  auto add = [&](int a1, int b1, int a2, int b2) {  // triangle (a, b), (a1, b1), (a2, b2)
+    const int64_t e0 = pe[p], e1 = pe[face_point(n, a1, b1)], e2 = pe[face_point(n, a2, b2)];
+    for (int c = 0; c < 3; ++c)
+      acc[c] += 2.0 * (double)t[e0 + c * E] + (double)t[e1 + c * E] + (double)t[e2 + c * E];
+  };
+  // up triangles with (a, b) as their first, second or third vertex
+  if (a + b + 1 <= n) add(a + 1, b, a, b + 1);
+  if (a >= 1) add(a - 1, b, a - 1, b + 1);
+  if (b >= 1) add(a, b - 1, a + 1, b - 1);
+  // down triangles with (a, b) as their first, second or third vertex
+  if (a >= 1 && b >= 1) add(a - 1, b, a, b - 1);          // down(a-1, b-1): (a, b-1), (a-1, b), (a, b)
+  if (a >= 1 && a + b + 1 <= n) add(a - 1, b + 1, a, b + 1);  // down(a-1, b): (a, b), (a-1, b+1), (a, b+1)
+  if (b >= 1 && a + b + 1 <= n) add(a + 1, b - 1, a + 1, b);  // down(a, b-1): (a+1, b-1), (a, b), (a+1, b)
+  const double w = area[s] / 12.0;
+  for (int c = 0; c < 3; ++c) contrib[3 * g + c] = w * acc[c];
+}
+
+template <typename T>
+__global__ void k_traction_gather(int64_t nnodes, const int64_t* __restrict__ cptr, const int64_t* __restrict__ cidx,
+                                  const int64_t* __restrict__ eptr, const int64_t* __restrict__ eidx, int64_t E,
+                                  const double* __restrict__ contrib, T* __restrict__ f) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= nnodes) return;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t q = cptr[u]; q < cptr[u + 1]; ++q)
+    for (int c = 0; c < 3; ++c) v[c] += contrib[3 * cidx[q] + c];
+  for (int64_t q = eptr[u]; q < eptr[u + 1]; ++q)
+    for (int c = 0; c < 3; ++c) f[eidx[q] + c * E] += (T)v[c];
+}
+
 // max over masked entries of the 2-norm of (a - b) over `comps` components (b nullable)
 __global__ void k_node_maxnorm(const uint8_t* __restrict__ mask, int64_t E, int comps, const double* __restrict__ a,
                                const double* __restrict__ b, double* partials) {
@@ -488,6 +544,26 @@ inline int grid_for(int64_t n, int block) {
 }
 
 }  // namespace
+
+template <typename T>
+int launch_traction_load(int n, int nslots, const double* area, const int64_t* pent, int64_t E, const T* t,
+                         double* contrib, int64_t nnodes, const int64_t* cptr, const int64_t* cidx,
+                         const int64_t* eptr, const int64_t* eidx, T* f, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t pts = (int64_t)nslots * (n + 1) * (n + 2) / 2;
+  if (pts > 0) k_traction_face<T><<<(unsigned)((pts + 127) / 128), 128, 0, s>>>(n, nslots, area, pent, E, t, contrib);
+  if (nnodes > 0)
+    k_traction_gather<T><<<(unsigned)((nnodes + 127) / 128), 128, 0, s>>>(nnodes, cptr, cidx, eptr, eidx, E, contrib,
+                                                                          f);
+  return (int)cudaGetLastError();
+}
+template int launch_traction_load<float>(int, int, const double*, const int64_t*, int64_t, const float*, double*,
+                                         int64_t, const int64_t*, const int64_t*, const int64_t*, const int64_t*,
+                                         float*, void*);
+template int launch_traction_load<double>(int, int, const double*, const int64_t*, int64_t, const double*, double*,
+                                          int64_t, const int64_t*, const int64_t*, const int64_t*, const int64_t*,
+                                          double*, void*);
+
 
 int launch_reduce(const double* partials, int64_t count, double* out, void* stream) {
   k_reduce<<<1, 1024, 0, (cudaStream_t)stream>>>(partials, count, out);
