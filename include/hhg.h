@@ -341,6 +341,21 @@ hhg_status hhg_carreau_viscosity(hhg_ctx* ctx, int level, const hhg_carreau* par
 hhg_status hhg_traction_load(hhg_ctx* ctx, int level, hhg_dtype dt, const int32_t* face_flags_host,
                              const void* t_dev, void* f_dev);
 
+/* 2D variant of the stencil scaling (Sec. 2.1, Sec. 2.3): y = A x for the vector P1
+ * operator of E (1/(1+nu) (eps(u), eps(v)) + nu/((1+nu)(1-2nu)) (div u, div v)) on one
+ * macro triangle tri_host[6] = (x0, y0, x1, y1, x2, y2) refined uniformly to n = 2^level
+ * intervals per edge (level 1..14), with the scaled 7-point stencil of 2x2 blocks: per
+ * interior edge khat Shat plus, for variant HHG_PHYSICAL, the correction of eq.
+ * corrtermgeneral, whose antisymmetric block does not depend on the triangle's shape (eq.
+ * correction2d); HHG_UNPHYSICAL drops it.  Lattice points (i, j), i + j <= n, at v0 + (i (v1 -
+ * v0) + j (v2 - v0)) / n, index j (n + 1) - j (j - 1) / 2 + i, N = (n+1)(n+2)/2 of them;
+ * k_dev[N] the nodal coefficient, x_dev and y_dev 2 components of stride N (component-
+ * major), all in dt (FP64 or FP32) on the device.  The triangle's boundary is Dirichlet
+ * (y = x there).  Runs on the context's stream; needs no mesh.  Errors: ARG (null or
+ * aliased pointers, level, nu, degenerate triangle, dtype), UNSUPPORTED (other variants). */
+hhg_status hhg_apply_2d(hhg_ctx* ctx, const double* tri_host, int level, double nu, int variant, hhg_dtype dt,
+                        const void* k_dev, const void* x_dev, void* y_dev);
+
 /* Degree m of the least-squares fit on the macro skeleton (eq. minimization_problem,
  * m in {1, 2}; default 1), used by hhg_carreau_viscosity and hhg_picard.  m = 2 fits a
  * quadratic in the monomials 1, x_a, x_a x_b over the node's patch where the patch

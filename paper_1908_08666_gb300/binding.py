@@ -111,6 +111,8 @@ _SIGS = {
     "hhg_refine": [C.c_void_p, C.c_int],
     "hhg_set_coarsest_level": [C.c_void_p, C.c_int],
     "hhg_set_strain_fit": [C.c_void_p, C.c_int],
+    "hhg_apply_2d": [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                     C.c_void_p],
     "hhg_traction_load": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
     "hhg_set_problem": [C.c_void_p, C.POINTER(hhg_problem)],
     "hhg_num_nodes": [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
@@ -242,6 +244,12 @@ def hhg_refine(ctx, level_max):
 
 def hhg_set_coarsest_level(ctx, level):
     _check(ctx, load().hhg_set_coarsest_level(ctx, int(level)))
+
+
+def hhg_apply_2d(ctx, tri, level, nu, variant, dt, k, x, y):
+    t = np.ascontiguousarray(np.asarray(tri, dtype=np.float64).reshape(6))
+    _check(ctx, load().hhg_apply_2d(ctx, t.ctypes.data_as(C.c_void_p), int(level), float(nu), int(variant), int(dt),
+                                    _ptr(k), _ptr(x), _ptr(y)))
 
 
 def hhg_set_strain_fit(ctx, degree):

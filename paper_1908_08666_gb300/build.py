@@ -13,7 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhhgs.so")
 
-SOURCES = ["hhg_host.cpp", "hhg_solve.cpp", "hhg_learn.cpp", "hhg_sweep.cu", "hhg_vec.cu", "hhg_learn.cu"]
+SOURCES = ["hhg_host.cpp", "hhg_solve.cpp", "hhg_learn.cpp", "hhg_sweep.cu", "hhg_vec.cu", "hhg_learn.cu",
+           "hhg_twod.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-O2",
          "-I" + os.path.join(os.path.dirname(HERE), "include")]

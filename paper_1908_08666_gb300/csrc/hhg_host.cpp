@@ -934,6 +934,37 @@ hhg_status hhg_traction_load(hhg_ctx* c, int level, hhg_dtype dt, const int32_t*
   });
 }
 
+hhg_status hhg_apply_2d(hhg_ctx* c, const double* tri_host, int level, double nu, int variant, hhg_dtype dt,
+                        const void* k_dev, const void* x_dev, void* y_dev) {
+  return guard(c, [&] {
+    if (!tri_host || !k_dev || !x_dev || !y_dev) THROW(HHG_ERR_ARG, "null argument");
+    if (x_dev == y_dev) THROW(HHG_ERR_ARG, "x and y must be distinct buffers");
+    if (level < 1 || level > 14) THROW(HHG_ERR_ARG, "level must be in [1, 14]");
+    if (!(nu > -1.0 && nu < 0.5)) THROW(HHG_ERR_ARG, "Poisson ratio out of range");
+    if (variant != HHG_PHYSICAL && variant != HHG_UNPHYSICAL)
+      THROW(HHG_ERR_UNSUPPORTED, "the 2D variant is built for the physical and unphysical scalings");
+    const double ce = 1.0 / (1.0 + nu), cd = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    Stencil2D<double> st64{};
+    const int n = 1 << level;
+    if (stencil_2d(tri_host, n, ce, cd, variant == HHG_PHYSICAL, &st64) != 0)
+      THROW(HHG_ERR_ARG, "degenerate macro triangle");
+    if (dt == HHG_F64) {
+      CK(launch_apply_2d<double>(n, st64, (const double*)k_dev, (const double*)x_dev, (double*)y_dev, c->stream));
+    } else if (dt == HHG_F32) {
+      Stencil2D<float> st32{};
+      for (int d = 0; d < 6; ++d) {
+        for (int q = 0; q < 4; ++q) st32.S[d][q] = (float)st64.S[d][q];
+        st32.w[d] = (float)st64.w[d];
+        st32.p[d] = st64.p[d];
+        st32.pm[d] = st64.pm[d];
+      }
+      CK(launch_apply_2d<float>(n, st32, (const float*)k_dev, (const float*)x_dev, (float*)y_dev, c->stream));
+    } else {
+      THROW(HHG_ERR_ARG, "dtype");
+    }
+  });
+}
+
 hhg_status hhg_set_strain_fit(hhg_ctx* c, int degree) {
   return guard(c, [&] {
     if (degree != 1 && degree != 2) THROW(HHG_ERR_ARG, "strain-rate fit degree must be 1 or 2");

@@ -202,6 +202,22 @@ int launch_hash_unique(int64_t U, int comps, const int8_t* udir, T* u, void* str
 template <typename T>
 int launch_dense_matvec(int N, const T* A, const int64_t* idx, const T* src_u, T* dst_u, void* stream);
 
+// 2D variant (Sec. 2.3) on one refined macro triangle: per direction d of the 7-point stencil
+// the constant-coefficient 2x2 block S[d] (row-major), the weight w[d] of the correction
+// (k_p - k_pm) [[0, -w], [w, 0]], and the directions p[d], pm[d] of the third vertices of the
+// edge's two elements
+template <typename T>
+struct Stencil2D {
+  T S[6][4];
+  T w[6];
+  int p[6], pm[6];
+};
+// constants in FP64 for tri[6] at n intervals per edge; 0 on success
+int stencil_2d(const double* tri, int n, double c_eps, double c_div, int physical, Stencil2D<double>* out);
+// y = A x on the lattice (2 components of stride (n+1)(n+2)/2; k one value per point)
+template <typename T>
+int launch_apply_2d(int n, const Stencil2D<T>& st, const T* k, const T* x, T* y, void* stream);
+
 // FP32 FMA issue-rate probe on sm_count * 8 blocks of 256 threads; *flops = flops of the launch
 int launch_fma_probe(int packed, int64_t iters, int sm_count, float* out, double* flops, void* stream);
 
