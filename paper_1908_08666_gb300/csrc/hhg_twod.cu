@@ -58,10 +58,14 @@ __global__ void __launch_bounds__(128) k_apply_2d(int n, const Stencil2D<T> st, 
     y[e + N] = y0;
     return;
   }
+  // neighbour indices from the point's own: row j + 1 starts n + 1 - j entries after row j,
+  // row j starts n + 2 - j entries after row j - 1
+  const int up = n + 1 - j, dn = n + 2 - j;
+  const int off[6] = {1, up, up - 1, -1, -dn, -dn + 1};  // (1,0) (0,1) (-1,1) (-1,0) (0,-1) (1,-1)
   T kk[6], dx[6], dy[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
-    const int64_t q = idx2(n, i + d2_di(d), j + d2_dj(d));
+    const int64_t q = e + off[d];
     kk[d] = k[q];
     dx[d] = x[q] - x0;
     dy[d] = x[q + N] - y0;
