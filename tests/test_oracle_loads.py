@@ -63,3 +63,29 @@ def test_load_is_the_symmetric_boundary_mass_matrix():
     b2 = LD.traction_load(mm, lv, flags, t2)
     assert abs((b1 * t2).sum() - (b2 * t1).sum()) < 1e-12
     assert (b1 * t1).sum() > 0
+
+
+def test_total_force_on_slanted_faces():
+    """On the skewed two-macro mesh every boundary face is slanted: a constant traction gives a
+    total load of t times the flagged faces' area, computed from the macro vertices."""
+    xyz, tets = hi.skewed_pair()
+    mm = mesh.MacroMesh.build(xyz, tets)
+    lv = mesh.build_level(mm, 3)
+    count = {}
+    for t in tets:
+        for f in range(4):
+            key = tuple(sorted(int(t[q]) for q in range(4) if q != f))
+            count[key] = count.get(key, 0) + 1
+    flags = np.zeros((len(tets), 4), dtype=np.int32)
+    area = 0.0
+    for m, t in enumerate(tets):
+        for f in range(4):
+            key = tuple(sorted(int(t[q]) for q in range(4) if q != f))
+            if count[key] == 1 and (m + f) % 2 == 0:
+                flags[m, f] = 1
+                a, b, c = (np.asarray(xyz)[int(t[q])] for q in range(4) if q != f)
+                area += 0.5 * np.linalg.norm(np.cross(b - a, c - a))
+    assert flags.sum() >= 2
+    tval = np.array([0.3, -1.2, 0.7])
+    b = LD.traction_load(mm, lv, flags, np.tile(tval, (lv.num_nodes, 1)))
+    assert np.allclose(b.sum(axis=0), tval * area, rtol=0, atol=1e-12 * area)

@@ -93,3 +93,21 @@ def test_symmetry_and_rigid_modes_2d():
     assert np.abs(Ai - Ai.T).max() < 1e-13 * np.abs(Ai).max()
     for r in (np.tile([1.0, 0.0], (lat.N, 1)), np.tile([0.0, 1.0], (lat.N, 1)), np.stack([-c[:, 1], c[:, 0]], 1)):
         assert np.abs(T.apply(A, r)[~lat.boundary]).max() < 1e-12 * np.abs(A).max()
+
+
+def test_element_matrices_integrate_the_energy_of_affine_fields():
+    """For u = G x + b the strain is constant, so sum_e u_e^T K_e u_e equals the area of the macro
+    triangle times c_eps eps:eps + c_div (tr eps)^2 in closed form (no quadrature involved)."""
+    rng = np.random.default_rng(4)
+    for tri in TRIS:
+        lat = T.Lattice2D(tri, 2)
+        K = T.element_stiffness(lat.coords[lat.elems], CE, CD)
+        G = rng.normal(size=(2, 2))
+        u = lat.coords @ G.T + rng.normal(size=2)
+        ue = u[lat.elems]  # (E, 3, 2)
+        energy = np.einsum("eam,eabml,ebl->", ue, K, ue)
+        eps = 0.5 * (G + G.T)
+        t = np.asarray(tri, dtype=np.float64)
+        area = 0.5 * abs(np.linalg.det(np.stack([t[1] - t[0], t[2] - t[0]], 1)))
+        want = area * (CE * (eps**2).sum() + CD * np.trace(eps) ** 2)
+        assert abs(energy - want) < 1e-12 * abs(want)
