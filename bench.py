@@ -691,7 +691,7 @@ def foam_bench(B, torch, level, dev, stream):
 
 def twod_bench(B, torch, level, dev, stream, steps=20):
     """The 2D variant (Sec. 2.3) on one skewed macro triangle at 2^level intervals per edge:
-    FP32 and FP64 physical-scaling apply throughput (2 DoFs per point, L2 flushed before each
+    FP32 and FP64 physical-scaling and FP32 nodal-integration apply throughput (2 DoFs per point, L2 flushed before each
     call, median of the calls) and the algorithmic bytes per point (x 2, k 1 read; y 2 write)."""
     tri = np.array([[0.2, 0.1], [1.3, 0.4], [0.5, 1.7]])
     n = 1 << level
@@ -701,23 +701,26 @@ def twod_bench(B, torch, level, dev, stream, steps=20):
     out = {"workload": "2D physical scaling, one macro triangle, %d intervals per edge (%d points)" % (n, N)}
     try:
         g = torch.Generator(device="cuda").manual_seed(5)
-        for name, dt, tdt, size in (("f32", B.F32, torch.float32, 4), ("f64", B.F64, torch.float64, 8)):
+        for name, dt, tdt, size, var in (("f32", B.F32, torch.float32, 4, B.PHYSICAL),
+                                         ("f64", B.F64, torch.float64, 8, B.PHYSICAL),
+                                         ("f32_nodal", B.F32, torch.float32, 4, B.NODAL)):
             k = 1.0 + 0.5 * torch.rand(N, dtype=tdt, device="cuda", generator=g)
             x = torch.rand(2 * N, dtype=tdt, device="cuda", generator=g)
             y = torch.empty_like(x)
             for _ in range(3):
-                B.hhg_apply_2d(h, tri, level, 0.3, B.PHYSICAL, dt, k, x, y)
+                B.hhg_apply_2d(h, tri, level, 0.3, var, dt, k, x, y)
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
             for a, b in ev:
                 flush.fill_(1.0)
                 a.record(stream)
-                B.hhg_apply_2d(h, tri, level, 0.3, B.PHYSICAL, dt, k, x, y)
+                B.hhg_apply_2d(h, tri, level, 0.3, var, dt, k, x, y)
                 b.record(stream)
             torch.cuda.synchronize()
             ms = statistics.median(a.elapsed_time(b) for a, b in ev)
             bytes_pt = 5 * size
             out[name] = {"ms": round(ms, 5), "gdofs": round(2 * N / (ms * 1e-3) / 1e9, 3),
                          "bytes_per_point": bytes_pt, "gbs": round(bytes_pt * N / (ms * 1e-3) / 1e9, 1)}
+        out["rel_time_physical_over_nodal_f32"] = round(out["f32"]["ms"] / out["f32_nodal"]["ms"], 4)
         return out
     finally:
         B.hhg_destroy(h)

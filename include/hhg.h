@@ -347,12 +347,13 @@ hhg_status hhg_traction_load(hhg_ctx* ctx, int level, hhg_dtype dt, const int32_
  * intervals per edge (level 1..14), with the scaled 7-point stencil of 2x2 blocks: per
  * interior edge khat Shat plus, for variant HHG_PHYSICAL, the correction of eq.
  * corrtermgeneral, whose antisymmetric block does not depend on the triangle's shape (eq.
- * correction2d); HHG_UNPHYSICAL drops it.  Lattice points (i, j), i + j <= n, at v0 + (i (v1 -
+ * correction2d); HHG_UNPHYSICAL drops it; HHG_NODAL applies nodal integration a_h (each
+ * element block scaled by its element's vertex mean), the comparison method.  Lattice points (i, j), i + j <= n, at v0 + (i (v1 -
  * v0) + j (v2 - v0)) / n, index j (n + 1) - j (j - 1) / 2 + i, N = (n+1)(n+2)/2 of them;
  * k_dev[N] the nodal coefficient, x_dev and y_dev 2 components of stride N (component-
  * major), all in dt (FP64 or FP32) on the device.  The triangle's boundary is Dirichlet
  * (y = x there).  Runs on the context's stream; needs no mesh.  Errors: ARG (null or
- * aliased pointers, level, nu, degenerate triangle, dtype), UNSUPPORTED (other variants). */
+ * aliased pointers, level, nu, degenerate triangle, dtype), UNSUPPORTED (the STORED variant). */
 hhg_status hhg_apply_2d(hhg_ctx* ctx, const double* tri_host, int level, double nu, int variant, hhg_dtype dt,
                         const void* k_dev, const void* x_dev, void* y_dev);
 

@@ -941,12 +941,13 @@ hhg_status hhg_apply_2d(hhg_ctx* c, const double* tri_host, int level, double nu
     if (x_dev == y_dev) THROW(HHG_ERR_ARG, "x and y must be distinct buffers");
     if (level < 1 || level > 14) THROW(HHG_ERR_ARG, "level must be in [1, 14]");
     if (!(nu > -1.0 && nu < 0.5)) THROW(HHG_ERR_ARG, "Poisson ratio out of range");
-    if (variant != HHG_PHYSICAL && variant != HHG_UNPHYSICAL)
-      THROW(HHG_ERR_UNSUPPORTED, "the 2D variant is built for the physical and unphysical scalings");
+    if (variant != HHG_PHYSICAL && variant != HHG_UNPHYSICAL && variant != HHG_NODAL)
+      THROW(HHG_ERR_UNSUPPORTED, "the 2D variant is built for the physical and unphysical scalings and nodal "
+                                 "integration");
     const double ce = 1.0 / (1.0 + nu), cd = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
     Stencil2D<double> st64{};
     const int n = 1 << level;
-    if (stencil_2d(tri_host, n, ce, cd, variant == HHG_PHYSICAL, &st64) != 0)
+    if (stencil_2d(tri_host, n, ce, cd, variant == HHG_PHYSICAL ? 1 : variant == HHG_NODAL ? 2 : 0, &st64) != 0)
       THROW(HHG_ERR_ARG, "degenerate macro triangle");
     if (dt == HHG_F64) {
       CK(launch_apply_2d<double>(n, st64, (const double*)k_dev, (const double*)x_dev, (double*)y_dev, c->stream));
@@ -957,7 +958,12 @@ hhg_status hhg_apply_2d(hhg_ctx* c, const double* tri_host, int level, double nu
         st32.w[d] = (float)st64.w[d];
         st32.p[d] = st64.p[d];
         st32.pm[d] = st64.pm[d];
+        for (int q = 0; q < 4; ++q) {
+          st32.Kt[d][q] = (float)st64.Kt[d][q];
+          st32.Ktm[d][q] = (float)st64.Ktm[d][q];
+        }
       }
+      st32.nodal = st64.nodal;
       CK(launch_apply_2d<float>(n, st32, (const float*)k_dev, (const float*)x_dev, (float*)y_dev, c->stream));
     } else {
       THROW(HHG_ERR_ARG, "dtype");

@@ -211,9 +211,15 @@ struct Stencil2D {
   T S[6][4];
   T w[6];
   int p[6], pm[6];
+  // nodal integration (nodal = 1): the two element blocks of each direction's edge, of the
+  // element with third vertex p[d] (Kt) and of the one with third vertex pm[d] (Ktm), each
+  // scaled by its own vertex mean
+  int nodal;
+  T Kt[6][4], Ktm[6][4];
 };
 // constants in FP64 for tri[6] at n intervals per edge; 0 on success
 int stencil_2d(const double* tri, int n, double c_eps, double c_div, int physical, Stencil2D<double>* out);
+// variant: 0 unphysical, 1 physical, 2 nodal integration
 // y = A x on the lattice (2 components of stride (n+1)(n+2)/2; k one value per point)
 template <typename T>
 int launch_apply_2d(int n, const Stencil2D<T>& st, const T* k, const T* x, T* y, void* stream);

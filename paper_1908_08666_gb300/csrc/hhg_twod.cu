@@ -75,6 +75,15 @@ __global__ void __launch_bounds__(128) k_apply_2d(int n, const Stencil2D<T> st, 
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     const T kp = pick6(kk, st.p[d]), kpm = pick6(kk, st.pm[d]);
+    if (st.nodal) {
+      // a_h: each element block scaled by its own vertex mean
+      const T kt = (k0 + kk[d] + kp) * (T)(1.0 / 3.0), ktm = (k0 + kk[d] + kpm) * (T)(1.0 / 3.0);
+      const T* A = st.Kt[d];
+      const T* C = st.Ktm[d];
+      ax += kt * (A[0] * dx[d] + A[1] * dy[d]) + ktm * (C[0] * dx[d] + C[1] * dy[d]);
+      ay += kt * (A[2] * dx[d] + A[3] * dy[d]) + ktm * (C[2] * dx[d] + C[3] * dy[d]);
+      continue;
+    }
     const T khat = ((T)2 * (k0 + kk[d]) + kp + kpm) * (T)(1.0 / 6.0);
     const T dk = kp - kpm;
     const T* S = st.S[d];  // row-major 2x2
@@ -100,7 +109,8 @@ template int launch_apply_2d<double>(int, const Stencil2D<double>&, const double
 // The constants of Stencil2D for the macro triangle tri[6] = (x0, y0, x1, y1, x2, y2) at n
 // intervals per edge, in FP64: the element blocks of the up and down element types, then per
 // direction the sum of the two blocks of its edge and the antisymmetric weight w_d.
-// physical = 0 leaves w_d = 0 (the unphysical scaling).
+// physical = 0 leaves w_d = 0 (the unphysical scaling); physical = 2 selects nodal integration
+// (the two element blocks are kept apart).
 int stencil_2d(const double* tri, int n, double c_eps, double c_div, int physical, Stencil2D<double>* out) {
   const double e1x = (tri[2] - tri[0]) / n, e1y = (tri[3] - tri[1]) / n;
   const double e2x = (tri[4] - tri[0]) / n, e2y = (tri[5] - tri[1]) / n;
@@ -159,6 +169,9 @@ int stencil_2d(const double* tri, int n, double c_eps, double c_div, int physica
           block(type == 0 ? gu : gd, la, lb, K);
           for (int m = 0; m < 2; ++m)
             for (int l = 0; l < 2; ++l) S[m][l] += K[m][l];
+          if (found < 2)
+            for (int m = 0; m < 2; ++m)
+              for (int l = 0; l < 2; ++l) (found == 0 ? out->Kt : out->Ktm)[d][2 * m + l] = K[m][l];
           if (found < 2) {
             third[found][0] = bi + v[lt][0];
             third[found][1] = bj + v[lt][1];
@@ -179,8 +192,9 @@ int stencil_2d(const double* tri, int n, double c_eps, double c_div, int physica
     if (pdir < 0 || pmdir < 0) return 3;
     out->p[d] = pdir;
     out->pm[d] = pmdir;
-    out->w[d] = physical ? 0.5 * (A[0] - A[1]) / 3.0 : 0.0;
+    out->w[d] = physical == 1 ? 0.5 * (A[0] - A[1]) / 3.0 : 0.0;
   }
+  out->nodal = physical == 2;
   return 0;
 }
 

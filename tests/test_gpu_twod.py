@@ -17,7 +17,7 @@ TRIS = {"unit": [[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]], "skewed": [[0.2, 0.1], [1.
 
 @pytest.mark.parametrize("name", list(TRIS))
 @pytest.mark.parametrize("level", [3, 5])
-@pytest.mark.parametrize("variant", ["physical", "unphysical"])
+@pytest.mark.parametrize("variant", ["physical", "unphysical", "nodal"])
 def test_apply_2d_parity(name, level, variant):
     torch = torch_cuda()
     tri = np.array(TRIS[name])
@@ -38,7 +38,7 @@ def test_apply_2d_parity(name, level, variant):
     scale = scale.reshape(-1, 2)
     h = B.hhg_create(0, torch.cuda.current_stream().cuda_stream)
     try:
-        var = B.PHYSICAL if variant == "physical" else B.UNPHYSICAL
+        var = {"physical": B.PHYSICAL, "unphysical": B.UNPHYSICAL, "nodal": B.NODAL}[variant]
         for dt, tdt in ((B.F64, torch.float64), (B.F32, torch.float32)):
             kd = torch.as_tensor(k, dtype=tdt, device="cuda")
             xd = torch.as_tensor(np.ascontiguousarray(x.T).reshape(-1), dtype=tdt, device="cuda")
