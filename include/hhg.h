@@ -592,8 +592,9 @@ hhg_status hhg_profile(hhg_ctx* ctx, int enable, double* ms_host, int64_t* launc
  * launch per macro; 1 a block per 30 x 4 x 4 box of lattice points that stages the box plus
  * its one-point halo in shared memory (asynchronous copies) and reads every neighbour from
  * there; 2 the point kernels, one launch per macro; 3 the point kernels, all macros in one
- * launch.  The Stokes sweeps follow the same choice of launch shape.  Errors: ARG for another
- * value. */
+ * launch.  The Stokes sweeps follow the same choice of launch shape; the colour passes of the
+ * hybrid Gauss-Seidel smoother always run as one launch over all macros.  Errors: ARG for
+ * another value. */
 hhg_status hhg_set_interior_kernel(hhg_ctx* ctx, int kernel);
 
 /* FP32 FMA issue-rate probe, a measurement aid with no counterpart in the paper: the
